@@ -1,0 +1,635 @@
+/*
+ * LP-SIFT oracle -- TEST INFRASTRUCTURE, NOT PRODUCT CODE.
+ *
+ * Plain FP64 CPU statement of the LP-SIFT hot path (Sec. 2.1-2.5, Sec. 4 of
+ * the paper).  Each function cites the passage it follows and spells out the
+ * readings taken where the paper is silent or garbled.  No blocking, no
+ * vectorisation, no shortcuts: loops follow the definitions.  Only the tests,
+ * the smoke check and the benchmark's CPU-baseline leg may load this file's
+ * library; the CUDA path never does.
+ *
+ * Parity status of each function (pins live in tests/test_oracle_*.py):
+ *   or_gray_from_rgb   pinned (closed form, exhaustive integer identity)
+ *   or_detect          pinned (brute force, constant image, 2x replication)
+ *   or_region_ws       pinned (closed form)
+ *   or_orient_bin      pinned (exhaustive, high-precision angle)
+ *   or_orient_weight   pinned (exhaustive, integer square-root bracket)
+ *   or_orient          pinned (ramp images, 90-degree rotation)
+ *   or_describe        pinned (ramp closed forms, unit norm, 90-degree rotation)
+ *   or_match           pinned (brute force in numpy, permutation invariance)
+ *   or_philox4x32_10   pinned (published known-answer vectors)
+ *   or_dlt4 / or_refit pinned (known homographies, numpy SVD)
+ *   or_ransac          pinned (synthetic inliers + outliers)
+ */
+#include "lp_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_PI 3.14159265358979323846
+
+/* ------------------------------------------------------------------ */
+/* Sec. 2.1: the image matrix M_k.  The paper works on intensity matrices and
+ * is silent on colour; an RGB pixel becomes intensity with the integer form of
+ * the 0.299/0.587/0.114 weights, rounded half up. */
+int or_gray_from_rgb(const uint8_t* rgb, int H, int W, int pitch, uint8_t* gray)
+{
+    if (!rgb || !gray || H <= 0 || W <= 0 || pitch < 3 * W) return -1;
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            const uint8_t* p = rgb + (size_t)y * pitch + 3 * (size_t)x;
+            unsigned v = 299u * p[0] + 587u * p[1] + 114u * p[2] + 500u;
+            gray[(size_t)y * W + x] = (uint8_t)(v / 1000u);
+        }
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Eq. 2: every full L x L interrogation window yields one maximum and one
+ * minimum.  Reading: windows tile the image from (0, 0); a partial window at
+ * the right or bottom edge is dropped; no de-duplication across scales. */
+int64_t or_num_keypoints(int H, int W, const int* Ls, int nL)
+{
+    int64_t K = 0;
+    for (int l = 0; l < nL; ++l) {
+        if (Ls[l] < 2) return -1;
+        K += 2 * (int64_t)(H / Ls[l]) * (int64_t)(W / Ls[l]);
+    }
+    return K;
+}
+
+static int cmp_int(const void* a, const void* b)
+{
+    int x = *(const int*)a, y = *(const int*)b;
+    return (x > y) - (x < y);
+}
+
+/* Ramped intensity comparison of Eq. 1 in the limit alpha -> 0+:
+ * M_n = M + alpha*(y*W + x + 1).  A larger intensity always wins; between
+ * equal intensities the later raster position carries the larger ramp. */
+static int ramp_greater(int g1, int64_t i1, int g2, int64_t i2)
+{
+    return g1 > g2 || (g1 == g2 && i1 > i2);
+}
+
+/* Eq. 1 + Eq. 2.  Reading of "i, j in [0, L]": the L x L pixels of window p. */
+int or_detect(const uint8_t* gray, int H, int W, int pitch, const int* Ls_in, int nL,
+              double alpha, uint32_t* idx)
+{
+    if (!gray || !idx || !Ls_in || nL <= 0 || nL > 64 || H <= 0 || W <= 0 || pitch < W) return -1;
+    if ((int64_t)H * W > 0xFFFFFFFFll) return -1;
+    int Ls[64];
+    memcpy(Ls, Ls_in, sizeof(int) * nL);
+    qsort(Ls, nL, sizeof(int), cmp_int);
+    int64_t k = 0;
+    for (int l = 0; l < nL; ++l) {
+        int L = Ls[l];
+        if (L < 2) return -1;
+        int nwy = H / L, nwx = W / L;
+        for (int wy = 0; wy < nwy; ++wy)
+            for (int wx = 0; wx < nwx; ++wx) {
+                int64_t imax = -1, imin = -1;
+                int gmax = 0, gmin = 0;
+                double vmax = 0, vmin = 0;
+                for (int i = 0; i < L; ++i)
+                    for (int j = 0; j < L; ++j) {
+                        int y = wy * L + i, x = wx * L + j;
+                        int64_t r = (int64_t)y * W + x;
+                        int g = gray[(size_t)y * pitch + x];
+                        if (alpha > 0) {
+                            double v = (double)g + alpha * (double)(r + 1);
+                            if (imax < 0 || v > vmax) { vmax = v; imax = r; }
+                            if (imin < 0 || v < vmin) { vmin = v; imin = r; }
+                        } else {
+                            if (imax < 0 || ramp_greater(g, r, gmax, imax)) { gmax = g; imax = r; }
+                            if (imin < 0 || ramp_greater(gmin, imin, g, r)) { gmin = g; imin = r; }
+                        }
+                    }
+                idx[k++] = (uint32_t)imax;
+                idx[k++] = (uint32_t)imin;
+            }
+    }
+    return 0;
+}
+
+/* Eq. 3-4: w = beta*L*d, beta = beta0*(L/Lmax)^(-1/2), w_s = beta*L.
+ * Readings: w_s is rounded to the nearest integer (at least 1); the exponent
+ * printed in Eq. 4 contradicts Eq. 3, and w <= L for every L needs
+ * beta0 <= (1/d) sqrt(L/Lmax), which binds at Lmin, so the default beta0 is
+ * (1/d) sqrt(Lmin/Lmax). */
+int or_region_ws(const int* Ls, int nL, double beta0, int d, int* ws)
+{
+    if (!Ls || !ws || nL <= 0 || d <= 0) return -1;
+    int Lmin = Ls[0], Lmax = Ls[0];
+    for (int l = 1; l < nL; ++l) {
+        if (Ls[l] < Lmin) Lmin = Ls[l];
+        if (Ls[l] > Lmax) Lmax = Ls[l];
+    }
+    if (beta0 <= 0) beta0 = sqrt((double)Lmin / (double)Lmax) / (double)d;
+    for (int l = 0; l < nL; ++l) {
+        double beta = beta0 * pow((double)Ls[l] / (double)Lmax, -0.5);
+        int w = (int)floor(beta * (double)Ls[l] + 0.5);
+        ws[l] = w < 1 ? 1 : w;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Clamp-to-edge pixel access (reading: border pixels are repeated). */
+static int px(const uint8_t* g, int H, int W, int pitch, int y, int x)
+{
+    if (y < 0) y = 0;
+    if (y >= H) y = H - 1;
+    if (x < 0) x = 0;
+    if (x >= W) x = W - 1;
+    return g[(size_t)y * pitch + x];
+}
+
+/* Eq. 5: theta = "b/a" is read as the direction atan2(b, a), measured from
+ * the +row axis towards the +column axis, in [0, 360) degrees.  The
+ * orientation histogram has 36 bins of 10 degrees; bin k holds
+ * k*10 <= phi < (k+1)*10.  On the axes the direction is exact. */
+int or_orient_bin(int a, int b)
+{
+    if (a == 0 && b == 0) return 0;
+    if (b == 0) return a > 0 ? 0 : 18;
+    if (a == 0) return b > 0 ? 9 : 27;
+    double phi = atan2((double)b, (double)a);
+    if (phi < 0) phi += 2.0 * OR_PI;
+    int k = (int)floor(phi * 36.0 / (2.0 * OR_PI));
+    if (k > 35) k = 35;
+    if (k < 0) k = 0;
+    return k;
+}
+
+/* Magnitude f = sqrt(a^2 + b^2) of Eq. 5, in units of 2^-16, rounded. */
+uint32_t or_orient_weight(int s)
+{
+    return (uint32_t)floor(65536.0 * sqrt((double)s) + 0.5);
+}
+
+/* Orientation assignment (not in the paper; SIFT's, needed for the rotation
+ * invariance of Sec. 3.5).  Reading: one orientation per feature point, the
+ * peak of a 36-bin magnitude-weighted histogram of Eq. 5 gradients over the
+ * upright (4 w_s + 1)^2 window centred on the point; no Gaussian weight, no
+ * smoothing, no secondary peaks; the lowest bin wins exact ties. */
+int or_orient(const uint8_t* gray, int H, int W, int pitch, const uint32_t* idx, const int* ws,
+              int64_t K, uint8_t* ori, uint64_t* hist36)
+{
+    if (!gray || !idx || !ws || !ori || K < 0) return -1;
+    for (int64_t k = 0; k < K; ++k) {
+        int y = (int)(idx[k] / (uint32_t)W), x = (int)(idx[k] % (uint32_t)W);
+        int R = 2 * ws[k];
+        uint64_t h[36];
+        memset(h, 0, sizeof h);
+        for (int u = -R; u <= R; ++u)
+            for (int v = -R; v <= R; ++v) {
+                int yy = y + u, xx = x + v;
+                int a = px(gray, H, W, pitch, yy + 1, xx) - px(gray, H, W, pitch, yy - 1, xx);
+                int b = px(gray, H, W, pitch, yy, xx + 1) - px(gray, H, W, pitch, yy, xx - 1);
+                int s = a * a + b * b;
+                if (s == 0) continue;
+                h[or_orient_bin(a, b)] += or_orient_weight(s);
+            }
+        int best = 0;
+        for (int j = 1; j < 36; ++j)
+            if (h[j] > h[best]) best = j;
+        ori[k] = (uint8_t)best;
+        if (hist36) memcpy(hist36 + 36 * k, h, sizeof h);
+    }
+    return 0;
+}
+
+/* Bilinear intensity at real (row r, column c), clamp-to-edge taps. */
+static double bil(const uint8_t* g, int H, int W, int pitch, double r, double c)
+{
+    double r0 = floor(r), c0 = floor(c);
+    double fr = r - r0, fc = c - c0;
+    int y = (int)r0, x = (int)c0;
+    double v00 = px(g, H, W, pitch, y, x), v01 = px(g, H, W, pitch, y, x + 1);
+    double v10 = px(g, H, W, pitch, y + 1, x), v11 = px(g, H, W, pitch, y + 1, x + 1);
+    return (1 - fr) * ((1 - fc) * v00 + fc * v01) + fr * ((1 - fc) * v10 + fc * v11);
+}
+
+/* Sec. 2.3: a w x w region (w = d*w_s, d = 4) around the point, split into
+ * d x d sub-regions of w_s x w_s samples; Eq. 5 gradients in each sub-region
+ * feed an 8-direction histogram, giving 4*4*8 = 128 values.
+ * Readings (the paper defers to SIFT): the grid is turned by the point's
+ * orientation theta = (k + 0.5)*10 degrees; sample offsets are
+ * u, v in {-2w_s, ..., 2w_s - 1} along the rotated axes e_u = (cos, sin),
+ * e_v = (-sin, cos) in (row, column); intensities are bilinear; the gradient is
+ * Eq. 5 taken along e_u and e_v; directions are relative to e_u; each
+ * magnitude is split linearly between the two nearest of the 8 bins; the
+ * vector is L2-normalised, clamped at 0.2 and normalised again.  A point whose
+ * histogram is all zero is marked invalid (all-zero descriptor). */
+int or_describe(const uint8_t* gray, int H, int W, int pitch, const uint32_t* idx, const int* ws,
+                const uint8_t* ori, int64_t K, double* desc, uint8_t* valid)
+{
+    if (!gray || !idx || !ws || !desc || !valid || K < 0) return -1;
+    for (int64_t k = 0; k < K; ++k) {
+        double y = (double)(idx[k] / (uint32_t)W), x = (double)(idx[k] % (uint32_t)W);
+        int s_ = ws[k], R = 2 * ws[k];
+        double th = ori ? ((double)ori[k] + 0.5) * (10.0 * OR_PI / 180.0) : 0.0;
+        double c = ori ? cos(th) : 1.0, s = ori ? sin(th) : 0.0;
+        double h[128];
+        memset(h, 0, sizeof h);
+        for (int u = -R; u < R; ++u)
+            for (int v = -R; v < R; ++v) {
+                double py = y + u * c - v * s;
+                double pxx = x + u * s + v * c;
+                double a = bil(gray, H, W, pitch, py + c, pxx + s) - bil(gray, H, W, pitch, py - c, pxx - s);
+                double b = bil(gray, H, W, pitch, py - s, pxx + c) - bil(gray, H, W, pitch, py + s, pxx - c);
+                double m = sqrt(a * a + b * b);
+                if (m == 0) continue;
+                double o = 8.0 * atan2(b, a) / (2.0 * OR_PI);
+                if (o < 0) o += 8.0;
+                if (o >= 8.0) o -= 8.0;
+                double fo = floor(o);
+                double t = o - fo;
+                int b0 = (int)fo, b1 = (b0 + 1) % 8;
+                int cell = ((u + R) / s_) * 4 + (v + R) / s_;
+                h[cell * 8 + b0] += m * (1.0 - t);
+                h[cell * 8 + b1] += m * t;
+            }
+        double n = 0;
+        for (int j = 0; j < 128; ++j) n += h[j] * h[j];
+        n = sqrt(n);
+        double* out = desc + 128 * k;
+        if (n == 0) {
+            memset(out, 0, sizeof(double) * 128);
+            valid[k] = 0;
+            continue;
+        }
+        double n2 = 0;
+        for (int j = 0; j < 128; ++j) {
+            double q = h[j] / n;
+            if (q > 0.2) q = 0.2;
+            out[j] = q;
+            n2 += q * q;
+        }
+        n2 = sqrt(n2);
+        for (int j = 0; j < 128; ++j) out[j] /= n2;
+        valid[k] = 1;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Sec. 2.4, Eq. 6: Delta = |d_f1 - d_f2|.  Readings: every valid point of the
+ * reference image queries all valid points of the registered image; the
+ * nearest one (lowest index on ties) is kept when it passes the ratio test
+ * Delta_1 < ratio * Delta_2 (Delta_2 = the next nearest) and, when set,
+ * Delta_1 < Delta_s. */
+int or_match(const double* dA, const uint8_t* vA, int64_t NA, const double* dB, const uint8_t* vB,
+             int64_t NB, double ratio, double delta_s, const int64_t* rows, int64_t nrows,
+             int32_t* match, double* d1, double* d2, int32_t* j1o, int32_t* j2o)
+{
+    if (!dA || !vA || !dB || !vB || !match || !d1 || !d2 || NA < 0 || NB < 0) return -1;
+    int64_t nq = rows ? nrows : NA;
+    int64_t nbv = 0;
+    for (int64_t j = 0; j < NB; ++j) nbv += vB[j] != 0;
+    for (int64_t q = 0; q < nq; ++q) {
+        int64_t i = rows ? rows[q] : q;
+        if (i < 0 || i >= NA) return -1;
+        match[q] = -1;
+        d1[q] = INFINITY;
+        d2[q] = INFINITY;
+        if (j1o) j1o[q] = -1;
+        if (j2o) j2o[q] = -1;
+        if (!vA[i]) continue;
+        double b1 = INFINITY, b2 = INFINITY;
+        int64_t j1 = -1, j2 = -1;
+        for (int64_t j = 0; j < NB; ++j) {
+            if (!vB[j]) continue;
+            double e = 0;
+            for (int c = 0; c < 128; ++c) {
+                double t = dA[128 * i + c] - dB[128 * j + c];
+                e += t * t;
+            }
+            if (e < b1) {
+                b2 = b1; j2 = j1;
+                b1 = e; j1 = j;
+            } else if (e < b2) {
+                b2 = e; j2 = j;
+            }
+        }
+        d1[q] = sqrt(b1);
+        d2[q] = sqrt(b2);
+        if (j1o) j1o[q] = (int32_t)j1;
+        if (j2o) j2o[q] = (int32_t)j2;
+        int ok = nbv >= 2 && b1 < ratio * ratio * b2;
+        if (delta_s > 0 && isfinite(delta_s)) ok = ok && sqrt(b1) < delta_s;
+        if (ok) match[q] = (int32_t)j1;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32->64
+ * multiplications with a Weyl-sequence key schedule. */
+void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        uint64_t p0 = (uint64_t)0xD2511F53u * c0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* RANSAC's random draw (Fischler & Bolles; the paper cites RANSAC in
+ * Sec. 2.5 without details).  Reading: iteration t draws four distinct match
+ * indices from a Philox stream keyed by (lo32(seed), hi32(seed) ^ pair_id)
+ * with counter (t, block, 0, 0); word j of the stream is word j%4 of block
+ * j/4; index = floor(word * M / 2^32); repeated indices are redrawn, at most
+ * 64 words per iteration, after which the iteration is skipped. */
+int or_ransac_sample(int64_t M, uint64_t seed, uint32_t pair_id, int t, int32_t* idx4)
+{
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32) ^ pair_id};
+    uint32_t blk[4];
+    int n = 0;
+    for (int j = 0; j < 64 && n < 4; ++j) {
+        if (j % 4 == 0) {
+            uint32_t ctr[4] = {(uint32_t)t, (uint32_t)(j / 4), 0u, 0u};
+            or_philox4x32_10(ctr, key, blk);
+        }
+        int32_t i = (int32_t)(((uint64_t)blk[j % 4] * (uint64_t)M) >> 32);
+        int dup = 0;
+        for (int q = 0; q < n; ++q) dup |= idx4[q] == i;
+        if (!dup) idx4[n++] = i;
+    }
+    return n == 4 ? 0 : 1;
+}
+
+/* Hartley normalisation: centroid to 0, mean distance to sqrt(2). */
+static int hartley(const double* p, int stride, int n, double T[9])
+{
+    double cx = 0, cy = 0;
+    for (int i = 0; i < n; ++i) { cx += p[i * stride]; cy += p[i * stride + 1]; }
+    cx /= n; cy /= n;
+    double md = 0;
+    for (int i = 0; i < n; ++i) {
+        double dx = p[i * stride] - cx, dy = p[i * stride + 1] - cy;
+        md += sqrt(dx * dx + dy * dy);
+    }
+    md /= n;
+    if (!(md > 0)) return 1;
+    double s = sqrt(2.0) / md;
+    T[0] = s; T[1] = 0; T[2] = -s * cx;
+    T[3] = 0; T[4] = s; T[5] = -s * cy;
+    T[6] = 0; T[7] = 0; T[8] = 1;
+    return 0;
+}
+
+static void mat3_mul(const double* A, const double* B, double* C)
+{
+    double t[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double s = 0;
+            for (int k = 0; k < 3; ++k) s += A[3 * i + k] * B[3 * k + j];
+            t[3 * i + j] = s;
+        }
+    memcpy(C, t, sizeof t);
+}
+
+/* H = T_dst^-1 * Hn * T_src, scaled to h33 = 1. */
+static int denormalise(const double* Ts, const double* Td, const double* Hn, double* H)
+{
+    double Tdi[9] = {1.0 / Td[0], 0, -Td[2] / Td[0], 0, 1.0 / Td[4], -Td[5] / Td[4], 0, 0, 1};
+    double t[9];
+    mat3_mul(Hn, Ts, t);
+    mat3_mul(Tdi, t, H);
+    double mx = 0;
+    for (int i = 0; i < 9; ++i) mx = fmax(mx, fabs(H[i]));
+    if (!(fabs(H[8]) > 1e-12 * mx)) return 1;
+    double h = H[8];
+    for (int i = 0; i < 9; ++i) H[i] /= h;
+    return 0;
+}
+
+/* Eq. 7 from four correspondences: (x', y', 1)^T ~ H (x, y, 1)^T with h33 = 1,
+ * an 8x8 linear system in normalised coordinates, solved by Gaussian
+ * elimination with partial pivoting. */
+int or_dlt4(const double* src, const double* dst, double* H)
+{
+    double Ts[9], Td[9];
+    if (hartley(src, 2, 4, Ts) || hartley(dst, 2, 4, Td)) return 1;
+    double A[8][9];
+    for (int i = 0; i < 4; ++i) {
+        double x = Ts[0] * src[2 * i] + Ts[2], y = Ts[4] * src[2 * i + 1] + Ts[5];
+        double xp = Td[0] * dst[2 * i] + Td[2], yp = Td[4] * dst[2 * i + 1] + Td[5];
+        double r0[9] = {x, y, 1, 0, 0, 0, -x * xp, -y * xp, xp};
+        double r1[9] = {0, 0, 0, x, y, 1, -x * yp, -y * yp, yp};
+        memcpy(A[2 * i], r0, sizeof r0);
+        memcpy(A[2 * i + 1], r1, sizeof r1);
+    }
+    for (int c = 0; c < 8; ++c) {
+        int p = c;
+        for (int r = c + 1; r < 8; ++r)
+            if (fabs(A[r][c]) > fabs(A[p][c])) p = r;
+        if (!(fabs(A[p][c]) > 1e-10)) return 1;
+        if (p != c)
+            for (int j = 0; j < 9; ++j) { double t = A[c][j]; A[c][j] = A[p][j]; A[p][j] = t; }
+        for (int r = c + 1; r < 8; ++r) {
+            double f = A[r][c] / A[c][c];
+            for (int j = c; j < 9; ++j) A[r][j] -= f * A[c][j];
+        }
+    }
+    double h[9];
+    for (int r = 7; r >= 0; --r) {
+        double s = A[r][8];
+        for (int j = r + 1; j < 8; ++j) s -= A[r][j] * h[j];
+        h[r] = s / A[r][r];
+    }
+    h[8] = 1.0;
+    return denormalise(Ts, Td, h, H);
+}
+
+/* Cyclic Jacobi rotations until the off-diagonal part vanishes. */
+int or_eig_sym(int n, const double* Ain, double* evals, double* evecs)
+{
+    if (n <= 0 || n > 16) return -1;
+    double a[16][16], v[16][16];
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            a[i][j] = Ain[i * n + j];
+            v[i][j] = i == j;
+        }
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0, tot = 0;
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) {
+                tot += a[i][j] * a[i][j];
+                if (i != j) off += a[i][j] * a[i][j];
+            }
+        if (off == 0 || off < 1e-30 * tot) break;
+        for (int p = 0; p < n; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                if (a[p][q] == 0) continue;
+                double th = (a[q][q] - a[p][p]) / (2.0 * a[p][q]);
+                double t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+                double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+                for (int k = 0; k < n; ++k) {
+                    double akp = a[k][p], akq = a[k][q];
+                    a[k][p] = c * akp - s * akq;
+                    a[k][q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < n; ++k) {
+                    double apk = a[p][k], aqk = a[q][k];
+                    a[p][k] = c * apk - s * aqk;
+                    a[q][k] = s * apk + c * aqk;
+                }
+                for (int k = 0; k < n; ++k) {
+                    double vkp = v[k][p], vkq = v[k][q];
+                    v[k][p] = c * vkp - s * vkq;
+                    v[k][q] = s * vkp + c * vkq;
+                }
+            }
+    }
+    /* selection sort, ascending */
+    int ord[16];
+    for (int i = 0; i < n; ++i) ord[i] = i;
+    for (int i = 0; i < n; ++i)
+        for (int j = i + 1; j < n; ++j)
+            if (a[ord[j]][ord[j]] < a[ord[i]][ord[i]]) { int t = ord[i]; ord[i] = ord[j]; ord[j] = t; }
+    for (int i = 0; i < n; ++i) {
+        evals[i] = a[ord[i]][ord[i]];
+        for (int k = 0; k < n; ++k) evecs[k * n + i] = v[k][ord[i]];
+    }
+    return 0;
+}
+
+/* Eq. 7 over all masked correspondences: minimise |A h| with |h| = 1 in
+ * Hartley-normalised coordinates (the smallest eigenvector of A^T A), then
+ * undo the normalisation and scale to h33 = 1. */
+int or_refit(const double* pts, const uint8_t* mask, int64_t M, double* H)
+{
+    int64_t n = 0;
+    for (int64_t i = 0; i < M; ++i) n += mask[i] != 0;
+    if (n < 4) return 1;
+    double* sa = (double*)malloc(sizeof(double) * 2 * n);
+    double* sb = (double*)malloc(sizeof(double) * 2 * n);
+    int64_t q = 0;
+    for (int64_t i = 0; i < M; ++i)
+        if (mask[i]) {
+            sa[2 * q] = pts[4 * i]; sa[2 * q + 1] = pts[4 * i + 1];
+            sb[2 * q] = pts[4 * i + 2]; sb[2 * q + 1] = pts[4 * i + 3];
+            ++q;
+        }
+    double Ta[9], Tb[9];
+    int bad = hartley(sa, 2, (int)n, Ta) || hartley(sb, 2, (int)n, Tb);
+    double AtA[81];
+    memset(AtA, 0, sizeof AtA);
+    for (int64_t i = 0; i < n && !bad; ++i) {
+        double x = Ta[0] * sa[2 * i] + Ta[2], y = Ta[4] * sa[2 * i + 1] + Ta[5];
+        double xp = Tb[0] * sb[2 * i] + Tb[2], yp = Tb[4] * sb[2 * i + 1] + Tb[5];
+        double r0[9] = {-x, -y, -1, 0, 0, 0, x * xp, y * xp, xp};
+        double r1[9] = {0, 0, 0, -x, -y, -1, x * yp, y * yp, yp};
+        for (int j = 0; j < 9; ++j)
+            for (int k = 0; k < 9; ++k) AtA[9 * j + k] += r0[j] * r0[k] + r1[j] * r1[k];
+    }
+    free(sa);
+    free(sb);
+    if (bad) return 1;
+    double ev[9], V[81], h[9];
+    or_eig_sym(9, AtA, ev, V);
+    for (int j = 0; j < 9; ++j) h[j] = V[9 * j + 0];
+    return denormalise(Ta, Tb, h, H);
+}
+
+/* Reprojection error in the registered image, e^2 = |pi(H p_A) - p_B|^2;
+ * a point is an inlier when e < thresh; a point projected to w <= 0 is not. */
+int64_t or_score(const double* H, const double* pts, int64_t M, double thresh, uint8_t* mask)
+{
+    int64_t n = 0;
+    double t2 = thresh * thresh;
+    for (int64_t i = 0; i < M; ++i) {
+        double x = pts[4 * i], y = pts[4 * i + 1];
+        double w = H[6] * x + H[7] * y + H[8];
+        int in = 0;
+        if (w > 0) {
+            double u = (H[0] * x + H[1] * y + H[2]) / w - pts[4 * i + 2];
+            double v = (H[3] * x + H[4] * y + H[5]) / w - pts[4 * i + 3];
+            in = u * u + v * v < t2;
+        }
+        if (mask) mask[i] = (uint8_t)in;
+        n += in;
+    }
+    return n;
+}
+
+/* |cross(q - p, r - p)| relative to the spread: three points on one line. */
+static int collinear(const double* p, const double* q, const double* r)
+{
+    double ux = q[0] - p[0], uy = q[1] - p[1], vx = r[0] - p[0], vy = r[1] - p[1];
+    double cr = ux * vy - uy * vx;
+    return fabs(cr) <= 1e-9 * (ux * ux + uy * uy + vx * vx + vy * vy);
+}
+
+/* Sec. 2.5: RANSAC over the matched pairs with the homography of Eq. 7.
+ * Readings: a full 8-DOF homography (Eq. 8's rigid form is a special case);
+ * T iterations (no adaptive stop); a sample with three collinear points in
+ * either image, or a singular system, is skipped; the hypothesis with the most
+ * inliers wins, the earliest on ties; the winner's inliers are refitted once
+ * by least squares, and the final inlier set is taken from the refitted H. */
+int or_ransac(const double* pts, int64_t M, int T, double thresh, uint64_t seed, uint32_t pair_id,
+              double* H, uint8_t* inl, int32_t* n_in, int32_t* best_t, int32_t* counts, double* Hs)
+{
+    memset(H, 0, sizeof(double) * 9);
+    *n_in = 0;
+    *best_t = -1;
+    if (inl) memset(inl, 0, (size_t)M);
+    if (counts)
+        for (int t = 0; t < T; ++t) counts[t] = -1;
+    if (Hs) memset(Hs, 0, sizeof(double) * 9 * (size_t)T);
+    if (M < 4) return 1;
+    int64_t bestc = -1;
+    double Hb[9];
+    for (int t = 0; t < T; ++t) {
+        int32_t s[4];
+        if (or_ransac_sample(M, seed, pair_id, t, s)) continue;
+        double src[8], dst[8];
+        for (int j = 0; j < 4; ++j) {
+            src[2 * j] = pts[4 * s[j]]; src[2 * j + 1] = pts[4 * s[j] + 1];
+            dst[2 * j] = pts[4 * s[j] + 2]; dst[2 * j + 1] = pts[4 * s[j] + 3];
+        }
+        int deg = 0;
+        for (int a = 0; a < 4; ++a) {
+            int i0 = (a + 1) % 4, i1 = (a + 2) % 4, i2 = (a + 3) % 4;
+            deg |= collinear(src + 2 * i0, src + 2 * i1, src + 2 * i2);
+            deg |= collinear(dst + 2 * i0, dst + 2 * i1, dst + 2 * i2);
+        }
+        if (deg) continue;
+        double Ht[9];
+        if (or_dlt4(src, dst, Ht)) continue;
+        int64_t c = or_score(Ht, pts, M, thresh, NULL);
+        if (counts) counts[t] = (int32_t)c;
+        if (Hs) memcpy(Hs + 9 * t, Ht, sizeof Ht);
+        if (c > bestc) {
+            bestc = c;
+            *best_t = t;
+            memcpy(Hb, Ht, sizeof Hb);
+        }
+    }
+    if (bestc < 0) return 1;
+    uint8_t* m = (uint8_t*)malloc((size_t)M);
+    or_score(Hb, pts, M, thresh, m);
+    double Hf[9];
+    if (or_refit(pts, m, M, Hf)) memcpy(Hf, Hb, sizeof Hf);
+    *n_in = (int32_t)or_score(Hf, pts, M, thresh, m);
+    if (inl) memcpy(inl, m, (size_t)M);
+    free(m);
+    memcpy(H, Hf, sizeof Hf);
+    return 0;
+}

@@ -1,0 +1,85 @@
+/*
+ * LP-SIFT oracle -- TEST INFRASTRUCTURE, NOT PRODUCT CODE.
+ *
+ * A plain, slow, single-threaded FP64 CPU statement of what the LP-SIFT hot
+ * path computes (Li, Wang, Zhao & Zhao, "Local-peak scale-invariant feature
+ * transform for fast and random image stitching", Sec. 2 and Sec. 4).  Only the
+ * test-suite, the smoke check and the CPU-baseline leg of the benchmark may
+ * load it.  It shares no code, header, table or constant generator with the
+ * CUDA library.
+ *
+ * Conventions: images are uint8, row-major, `pitch` bytes per row; a keypoint
+ * is its raster index idx = y*W + x (x = column, y = row, 0-based).  All
+ * functions return 0 on success and a negative value on bad arguments.
+ */
+#ifndef LP_ORACLE_H
+#define LP_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Colour -> intensity matrix M_k (Sec. 2.1): g = (299R + 587G + 114B + 500) / 1000. */
+int or_gray_from_rgb(const uint8_t* rgb, int H, int W, int pitch, uint8_t* gray);
+
+/* Number of feature points: 2 per full L x L interrogation window per scale (Eq. 2). */
+int64_t or_num_keypoints(int H, int W, const int* Ls, int nL);
+
+/* Multiscale local peaks (Eq. 1 ramp + Eq. 2).  alpha == 0 takes the limit
+ * alpha -> 0+ (ties broken by the ramp only); alpha > 0 evaluates the FP64 ramp
+ * literally.  Output order: L ascending, windows row-major, max then min. */
+int or_detect(const uint8_t* gray, int H, int W, int pitch, const int* Ls, int nL,
+              double alpha, uint32_t* idx);
+
+/* Sub-region side w_s(L) (Eq. 3-4); beta0 <= 0 selects (1/d) sqrt(Lmin/Lmax). */
+int or_region_ws(const int* Ls, int nL, double beta0, int d, int* ws);
+
+/* Orientation helpers, exposed so they can be pinned on their own. */
+int      or_orient_bin(int a, int b);          /* 10-degree bin of atan2(b, a) in [0, 360) */
+uint32_t or_orient_weight(int s);             /* round(65536 * sqrt(s)) */
+
+/* Orientation bin per keypoint (36-bin histogram over the upright window). */
+int or_orient(const uint8_t* gray, int H, int W, int pitch, const uint32_t* idx, const int* ws,
+              int64_t K, uint8_t* ori, uint64_t* hist36 /* K*36 or NULL */);
+
+/* 128-d descriptor (Eq. 5 gradients on a rotated 4x4 grid, 8 soft bins).
+ * ori == NULL: upright (theta = 0). */
+int or_describe(const uint8_t* gray, int H, int W, int pitch, const uint32_t* idx, const int* ws,
+                const uint8_t* ori, int64_t K, double* desc, uint8_t* valid);
+
+/* Nearest-neighbour matching with Eq. 6 distance, the ratio test and Delta_s.
+ * rows == NULL: all NA rows; otherwise only rows[0..nrows) (outputs indexed by
+ * position in rows). */
+int or_match(const double* dA, const uint8_t* vA, int64_t NA, const double* dB, const uint8_t* vB,
+             int64_t NB, double ratio, double delta_s, const int64_t* rows, int64_t nrows,
+             int32_t* match, double* d1, double* d2, int32_t* j1, int32_t* j2);
+
+/* Philox4x32-10 block function (Salmon, Moraes, Dror & Shaw, SC'11). */
+void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+
+/* The four sample indices of RANSAC iteration t; returns 0, or 1 if skipped. */
+int or_ransac_sample(int64_t M, uint64_t seed, uint32_t pair_id, int t, int32_t* idx4);
+
+/* 4-point DLT (h33 = 1) with Hartley normalisation; returns 0, or 1 if singular. */
+int or_dlt4(const double* src /*4x2 (x,y)*/, const double* dst /*4x2*/, double* H /*9*/);
+
+/* Least-squares DLT over the masked correspondences; returns 0, or 1 on failure. */
+int or_refit(const double* pts /*M x 4: xA yA xB yB*/, const uint8_t* mask, int64_t M, double* H);
+
+/* Symmetric eigen-decomposition (cyclic Jacobi), ascending eigenvalues,
+ * eigenvectors in the columns of evecs (row-major n x n). */
+int or_eig_sym(int n, const double* A, double* evals, double* evecs);
+
+/* Inlier count of H at threshold thresh (pixels); writes the mask if non-NULL. */
+int64_t or_score(const double* H, const double* pts, int64_t M, double thresh, uint8_t* mask);
+
+/* RANSAC with a homography model (Sec. 2.5, Eq. 7).  Returns 0, or 1 when no
+ * model was found (H = 0, n_in = 0).  counts (T) and Hs (T*9) are optional. */
+int or_ransac(const double* pts, int64_t M, int T, double thresh, uint64_t seed, uint32_t pair_id,
+              double* H, uint8_t* inl, int32_t* n_in, int32_t* best_t, int32_t* counts, double* Hs);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
