@@ -1,0 +1,317 @@
+"""Benchmark: image pairs/s of the LP-SIFT hot path (detect -> describe ->
+match -> RANSAC) on one 2688x1600 RGB pair per step, L = {16, 32, 64, 128}.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl lp|reference]
+                [--precision fp32|bf16]
+
+One JSON line on rank 0.  `value` times K steps with the inputs resident in
+HBM (L2 flushed between steps, outside the timed events); `e2e` times the
+public host-buffer call lp_stitch_pair_host (H2D of both images from pinned
+memory, D2H of H / inlier count).  `--impl reference` times the CPU oracle on
+a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+H_IMG, W_IMG = 1600, 2688
+LS = (16, 32, 64, 128)
+WORKLOAD = "pair_2688x1600_rgb"
+METRIC = "image pairs/s at 2688x1600 (detect->RANSAC)"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, \
+            "fallback"
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.p is not None:
+            time.sleep(0.25)
+            self.p.terminate()
+            try:
+                self.out, _ = self.p.communicate(timeout=5)
+            except Exception:
+                self.p.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 6:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = float(f[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[2:6]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- CPU oracle sample
+def oracle_pair_seconds(pair, rows_sample=1500, desc_sample=15000, seed=0, M=3000):
+    """Single-thread FP64 oracle time for one pair, from a bounded sample:
+    intensity + peaks in full, orientation+description of `desc_sample`
+    random points per image (scaled to all K), matching of `rows_sample`
+    random rows against all of B (scaled to all rows), RANSAC in full on the
+    oracle's own matches of the sampled rows replicated to the full count."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    t = {}
+    t0 = time.perf_counter()
+    ga, gb = oracle.gray(pair.A), oracle.gray(pair.B)
+    ka, kb = oracle.detect(ga, LS), oracle.detect(gb, LS)
+    t["detect"] = time.perf_counter() - t0
+    _, ws = oracle.keypoint_scales(H_IMG, W_IMG, LS)
+    K = len(ka)
+    t_desc = 0.0
+    descs = []
+    for g, kp in ((ga, ka), (gb, kb)):
+        sel = np.sort(rng.choice(K, desc_sample, replace=False))
+        t0 = time.perf_counter()
+        o = oracle.orient(g, kp[sel], ws[sel])
+        d, v = oracle.describe(g, kp[sel], ws[sel], o)
+        t_desc += (time.perf_counter() - t0) * K / desc_sample
+        descs.append((d, v))
+    t["describe"] = t_desc
+    # matching: sampled rows of A against a full-size B (sampled descriptors tiled to K rows)
+    dA, vA = descs[0]
+    dB = np.tile(descs[1][0], (K // desc_sample + 1, 1))[:K]
+    vB = np.tile(descs[1][1], K // desc_sample + 1)[:K]
+    t0 = time.perf_counter()
+    oracle.match(dA[:rows_sample], vA[:rows_sample], dB, vB, rows=np.arange(rows_sample))
+    t["match"] = (time.perf_counter() - t0) * K / rows_sample
+    # RANSAC on a synthetic match set of the size the GPU path produces
+    pa = rng.uniform(0, W_IMG, (M, 2)).round()
+    pb = pa + np.array([800.0, 20.0]) + rng.normal(0, 0.5, (M, 2))
+    pb[M // 2:] = rng.uniform(0, W_IMG, (M - M // 2, 2)).round()
+    t0 = time.perf_counter()
+    oracle.ransac(np.c_[pa, pb], T=1000, thresh=3.0, seed=0)
+    t["ransac"] = time.perf_counter() - t0
+    total = sum(t.values())
+    sample = (f"full intensity+peaks of both images; orientation+descriptors of {desc_sample} random points per "
+              f"image scaled to K={K}; {rows_sample} query rows x {K} candidates scaled to {K} rows; RANSAC 1000 "
+              f"iterations on {M} matches")
+    return total, t, sample
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def run_lp(args, rank, world):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2405_08578_gb300 import lp, synth
+
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    prec = lp.PREC_BF16 if args.precision == "bf16" else lp.PREC_FP32
+    ctx = lp.Context(Ls=LS, precision=prec)
+    pair = synth.pair_2688x1600(seed=rank)
+    s = torch.cuda.current_stream()
+    bA, pA = lp.pitched_device(pair.A)
+    bB, pB = lp.pitched_device(pair.B)
+    K = lp.lp_num_keypoints(H_IMG, W_IMG, LS)
+    bf = prec == lp.PREC_BF16
+    mk = lambda *shape, dt: torch.empty(*shape, dtype=dt, device="cuda")  # noqa: E731
+    kpA, kpB = mk(K, dt=torch.int32), mk(K, dt=torch.int32)
+    gA, gB = mk(H_IMG * W_IMG + 16, dt=torch.uint8), mk(H_IMG * W_IMG + 16, dt=torch.uint8)
+    oA, oB = mk(K, dt=torch.uint8), mk(K, dt=torch.uint8)
+    dA, dB = mk(K, 128, dt=torch.float32), mk(K, 128, dt=torch.float32)
+    hA = mk(K, 128, dt=torch.bfloat16) if bf else None
+    hB = mk(K, 128, dt=torch.bfloat16) if bf else None
+    vA, vB = mk(K, dt=torch.uint8), mk(K, dt=torch.uint8)
+    m, d1, d2 = mk(K, dt=torch.int32), mk(K, dt=torch.float32), mk(K, dt=torch.float32)
+    pts, dM = mk(K, 4, dt=torch.float32), mk(1, dt=torch.int32)
+    Hd, inl, nin = mk(9, dt=torch.float64), mk(K, dt=torch.uint8), mk(1, dt=torch.int32)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def step(ev=None):
+        if ev:
+            ev[0].record(s)
+        ctx.lp_detect(bA, H_IMG, W_IMG, pA, 3, kpA, gA)
+        ctx.lp_detect(bB, H_IMG, W_IMG, pB, 3, kpB, gB)
+        ctx.lp_describe(gA, H_IMG, W_IMG, W_IMG, kpA, K, oA, dA, hA, vA)
+        ctx.lp_describe(gB, H_IMG, W_IMG, W_IMG, kpB, K, oB, dB, hB, vB)
+        if ev:
+            ev[1].record(s)
+        ctx.lp_match(dA, hA, vA, K, dB, hB, vB, K, m, d1, d2)
+        if ev:
+            ev[2].record(s)
+        ctx.lp_compact(kpA, W_IMG, kpB, W_IMG, m, K, pts, None, dM)
+        ctx.lp_ransac(pts, K, dM, rank, Hd, inl, nin)
+        if ev:
+            ev[3].record(s)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev) as clk:
+        for i in range(args.steps):
+            flush.zero_()
+            step(evs[i])
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    per = [[a.elapsed_time(b) for a, b in zip(e[:-1], e[1:])] for e in evs]
+    t_steps = sum(sum(p) for p in per) / 1e3
+    t_match = sum(p[1] for p in per) / 1e3 / args.steps
+    stages = {"detect_describe_ms": 1e3 * sum(p[0] for p in per) / 1e3 / args.steps,
+              "match_ms": 1e3 * t_match, "compact_ransac_ms": 1e3 * sum(p[2] for p in per) / 1e3 / args.steps}
+    n_in = int(nin.item())
+    M = int(dM.item())
+    assert ctx.lp_sync_status() == 0
+
+    # end to end through the public host-buffer call
+    hostA = torch.from_numpy(np.ascontiguousarray(lp.pitched_device(pair.A)[0].cpu().numpy())).pin_memory()
+    hostB = torch.from_numpy(np.ascontiguousarray(lp.pitched_device(pair.B)[0].cpu().numpy())).pin_memory()
+    for _ in range(max(1, args.warmup // 2)):
+        ctx.lp_stitch_pair_host(hostA, H_IMG, W_IMG, pA, hostB, H_IMG, W_IMG, pB, 3, rank)
+    torch.cuda.synchronize()
+    e2e_t = 0.0
+    for i in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        ctx.lp_stitch_pair_host(hostA, H_IMG, W_IMG, pA, hostB, H_IMG, W_IMG, pB, 3, rank)
+        b.record(s)
+        b.synchronize()
+        e2e_t += a.elapsed_time(b) / 1e3
+
+    tt = torch.tensor([t_steps, e2e_t, t_match], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    t_steps, e2e_t, t_match = tt.tolist()
+    return dict(t_steps=t_steps, e2e_t=e2e_t, t_match=t_match, stages=stages, clocks=clk.summary(), n_in=n_in, M=M,
+                K=K, pair=pair, h2d=int(hostA.numel() + hostB.numel()), bf=bf)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="lp", choices=["lp", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        from paper_2405_08578_gb300 import synth
+        pair = synth.pair_2688x1600(0)
+        secs = []
+        for i in range(args.warmup + args.steps):
+            tot, parts, sample = oracle_pair_seconds(pair, rows_sample=200, desc_sample=3000, seed=i)
+            if i >= args.warmup:
+                secs.append(tot)
+        v = len(secs) / sum(secs)
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "pairs/s", "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(secs) / len(secs),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": {"workload": WORKLOAD, "H": H_IMG, "W": W_IMG, "Ls": list(LS),
+                                                "flush": "n/a (CPU)"},
+                "cpu_baseline": {"value": v, "unit": "pairs/s", "cores": 1, "kind": "oracle", "sample": sample},
+                "e2e": {"value": v, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import torch
+    import torch.distributed as dist
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0))))
+    r = run_lp(args, rank, world)
+    if rank != 0:
+        dist.destroy_process_group()
+        return
+    pk, pk_kind = peaks()
+    K = r["K"]
+    flops = 2.0 * K * K * 128
+    if r["bf"]:
+        roof = {"bound": "tensor", "achieved": flops / r["t_match"] / 1e12, "peak": pk["bf16_tflops"],
+                "unit": "TFLOP/s", "kernel": "match (bf16 tcgen05)"}
+    else:
+        sm_max = pk.get("sm_max_mhz", 2070.0)
+        fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": flops / r["t_match"] / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
+                "kernel": "k_match_fp32_main + norms + finish"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    roof["peak_source"] = f"{pk_kind}" if r["bf"] else "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"
+    value = world * args.steps / r["t_steps"]
+    launches_per_step = 13
+    line = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * r["t_steps"] / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if r["bf"] else "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "H": H_IMG, "W": W_IMG, "Ls": list(LS), "K_per_image": K,
+                       "precision": args.precision, "flush": "L2 flushed (256 MB write) between timed steps",
+                       "matches": r["M"], "inliers": r["n_in"], "Mpix_per_s": value * 2 * H_IMG * W_IMG / 1e6,
+                       **r["stages"]},
+            "roofline": roof,
+            "e2e": {"value": world * args.steps / r["e2e_t"], "unit": "pairs/s", "h2d_bytes_per_step": r["h2d"],
+                    "d2h_bytes_per_step": 9 * 8 + 2 * 4},
+            "gpu_launches": launches_per_step * args.steps, "clocks": r["clocks"]}
+    if world == 1 and not args.no_cpu_baseline:
+        tot, parts, sample = oracle_pair_seconds(r["pair"], M=max(r["M"], 4))
+        line["cpu_baseline"] = {"value": 1.0 / tot, "unit": "pairs/s", "cores": 1, "kind": "oracle",
+                                "sample": sample, "seconds_per_pair": tot,
+                                "parts_s": {k: round(v, 3) for k, v in parts.items()}, "host_cores": os.cpu_count()}
+    print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,203 @@
+/*
+ * liblp -- LP-SIFT hot path on one NVIDIA GB300 (sm_103a).
+ *
+ * Li, Wang, Zhao & Zhao, "Local-peak scale-invariant feature transform for
+ * fast and random image stitching": multiscale local-peak detection (Sec. 2.1-
+ * 2.2, Eq. 1-2), SIFT-style orientation and 128-d description (Sec. 2.3,
+ * Eq. 3-5), nearest-neighbour matching with Eq. 6 distances (Sec. 2.4) and
+ * RANSAC homography estimation (Sec. 2.5, Eq. 7), plus the all-pairs
+ * homography matrix H_M of Sec. 4.
+ *
+ * Conventions shared by every entry point
+ *  - Pointers named d_* or documented as "device" are device pointers that the
+ *    caller allocates and owns; the library never frees them.  Host pointers
+ *    are documented as such.
+ *  - Calls are asynchronous on `stream` (a cudaStream_t passed as void*;
+ *    NULL = the legacy default stream) unless documented otherwise.
+ *  - Every call returns an lp_status.  Argument errors that the host can see
+ *    are returned synchronously and launch nothing.  Errors found on the device
+ *    are recorded in a per-context status word; lp_sync_status() waits for the
+ *    context's last stream and returns it.
+ *  - Images are uint8, row-major, `pitch` bytes per row, pitch % 16 == 0 and a
+ *    16-byte aligned base.  channels = 1 (intensity) or 3 (interleaved RGB).
+ *    Coordinates are 0-based; x = column, y = row; a feature point is the
+ *    raster index idx = y*W + x (H*W < 2^24 is required).
+ *  - A context is not thread-safe; use one context per host thread / stream.
+ */
+#ifndef LP_H
+#define LP_H
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define LP_API __attribute__((visibility("default")))
+#else
+#define LP_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum lp_status {
+    LP_OK = 0,
+    LP_ERR_ARG = 1,          /* invalid argument (null, size, range) */
+    LP_ERR_ALIGN = 2,        /* pointer or pitch not 16-byte aligned */
+    LP_ERR_CUDA = 3,         /* a CUDA runtime call failed */
+    LP_ERR_TIMEOUT = 4,      /* a bounded device-side wait gave up */
+    LP_ERR_NOMEM = 5,        /* workspace allocation failed */
+    LP_ERR_DEGENERATE = 6,   /* no model could be fitted (reported, not fatal) */
+    LP_ERR_UNSUPPORTED = 7,  /* configuration outside what this build supports */
+    LP_ERR_DEVICE = 8        /* a kernel recorded an internal inconsistency */
+} lp_status;
+
+typedef enum lp_precision {
+    LP_PREC_FP32 = 0,        /* FP32 SIMT distances, exact top-2 */
+    LP_PREC_BF16 = 1         /* BF16 tcgen05 distances, top-k, FP32 re-rank */
+} lp_precision;
+
+#define LP_MAX_SCALES 8
+
+/* Parameters of the method.  lp_config_default() fills the values used by the
+ * 640x480 and 2688x1600 workloads. */
+typedef struct lp_config {
+    int32_t  nL;                  /* number of window sizes, 1..LP_MAX_SCALES */
+    int32_t  Ls[LP_MAX_SCALES];   /* interrogation window sizes L (Eq. 2), >= 2 */
+    double   beta0;               /* Eq. 3 beta0; <= 0 selects (1/d) sqrt(Lmin/Lmax) */
+    float    ratio;               /* ratio test: accept Delta1 < ratio * Delta2 */
+    float    delta_s;             /* Delta_s of Sec. 2.4; <= 0 or inf disables it */
+    int32_t  ransac_iters;        /* RANSAC iterations T, 1..65536 */
+    float    thresh_px;           /* inlier threshold on reprojection error (px) */
+    uint64_t seed;                /* key of the Philox4x32-10 sampling stream */
+    int32_t  min_inliers;         /* an H_M entry is non-zero iff n_in >= this */
+    int32_t  precision;           /* lp_precision */
+    int32_t  upright;             /* 1: every orientation is 0 (no rotation) */
+} lp_config;
+
+typedef struct lp_ctx lp_ctx;
+
+/* Fill *cfg with L = {16, 32, 64, 128}, beta0 auto, ratio 0.8, Delta_s off,
+ * T = 1000, 3 px, seed 0, min_inliers 8, BF16, rotated descriptors. */
+LP_API int lp_config_default(lp_config* cfg);
+
+/* Create a context on the current CUDA device.  The context owns a copy of the
+ * configuration, a device status word and a grow-only device workspace.
+ * Errors: LP_ERR_ARG (bad config), LP_ERR_CUDA, LP_ERR_NOMEM. */
+LP_API int lp_create(lp_ctx** ctx, const lp_config* cfg);
+
+/* Synchronise the context's streams and free everything it owns. */
+LP_API int lp_destroy(lp_ctx* ctx);
+
+/* Number of feature points 2 * sum_L floor(H/L) * floor(W/L) (Eq. 2: one max
+ * and one min per full L x L window; partial windows are dropped).  Returns -1
+ * on bad arguments. */
+LP_API int64_t lp_num_keypoints(int H, int W, const int* Ls, int nL);
+
+/* Sec. 2.1-2.2, Eq. 1-2: multiscale local peaks.
+ *  img      device, H x W x channels uint8, pitch bytes per row
+ *  kp_idx   device, uint32[K], K = lp_num_keypoints(H, W, cfg.Ls): raster
+ *           indices in canonical order -- L ascending, windows row-major,
+ *           the window maximum then its minimum.  Eq. 1's ramp with
+ *           alpha -> 0+ decides ties: the later raster index is the larger.
+ *  gray     device, uint8[H*W] dense intensity output, required when
+ *           channels == 3 (it feeds lp_describe), ignored when channels == 1.
+ *           RGB -> intensity is (299 R + 587 G + 114 B + 500) / 1000.
+ * Errors: LP_ERR_ARG, LP_ERR_ALIGN, LP_ERR_CUDA. */
+LP_API int lp_detect(lp_ctx* ctx, const uint8_t* img, int H, int W, int pitch, int channels,
+              uint32_t* kp_idx, uint8_t* gray, void* stream);
+
+/* Sec. 2.3, Eq. 3-5: orientation and 128-d descriptor of every feature point.
+ *  gray       device, H x W uint8 intensity, gray_pitch bytes per row
+ *  kp_idx     device, uint32[K] from lp_detect (K must equal lp_num_keypoints;
+ *             the scale of point k follows from its position)
+ *  ori        device, uint8[K]: orientation bin k (theta = (k + 0.5) * 10 deg)
+ *  desc       device, float[K*128], row-major, unit L2 norm (zeros if invalid)
+ *  desc_bf16  device, uint16[K*128] bfloat16 copy of desc, or NULL
+ *  valid      device, uint8[K]: 0 when the gradient histogram is all zero
+ * Errors: LP_ERR_ARG, LP_ERR_ALIGN, LP_ERR_CUDA. */
+LP_API int lp_describe(lp_ctx* ctx, const uint8_t* gray, int H, int W, int gray_pitch, const uint32_t* kp_idx,
+                int64_t K, uint8_t* ori, float* desc, uint16_t* desc_bf16, uint8_t* valid, void* stream);
+
+/* Sec. 2.4, Eq. 6: each valid point i of image A takes its nearest valid point
+ * j1 of image B (lowest j on exact ties) and keeps it when
+ * Delta1 < ratio * Delta2 (and Delta1 < Delta_s when set).
+ *  dA, dB           device float[N*128] descriptors
+ *  dA_bf16, dB_bf16 device bf16 copies, required for LP_PREC_BF16, else unused
+ *  vA, vB           device uint8 validity
+ *  match            device int32[NA]: j1 or -1
+ *  d1, d2           device float[NA]: Delta1, Delta2 (FP32, +inf if none)
+ * With LP_PREC_BF16 the tensor cores rank candidates, every candidate is
+ * re-scored exactly in FP32 and rows whose ranking cannot be certified are
+ * re-scanned in FP32, so the result is that of the FP32 form.
+ * Errors: LP_ERR_ARG, LP_ERR_ALIGN, LP_ERR_NOMEM, LP_ERR_CUDA. */
+LP_API int lp_match(lp_ctx* ctx, const float* dA, const uint16_t* dA_bf16, const uint8_t* vA, int64_t NA,
+             const float* dB, const uint16_t* dB_bf16, const uint8_t* vB, int64_t NB,
+             int32_t* match, float* d1, float* d2, void* stream);
+
+/* Matched pairs p_v1, p_v2 of Sec. 2.4 as coordinates, in row order of A.
+ *  kpA, kpB  device uint32 raster indices; WA, WB image widths
+ *  match     device int32[NA] from lp_match
+ *  pts       device float[NA*4] output rows (xA, yA, xB, yB); the first M used
+ *  rows      device int32[NA] output: the A row of each compacted pair, or NULL
+ *  d_M       device int32 output: M, the number of matched pairs
+ * Errors: LP_ERR_ARG, LP_ERR_CUDA. */
+LP_API int lp_compact(lp_ctx* ctx, const uint32_t* kpA, int WA, const uint32_t* kpB, int WB, const int32_t* match,
+               int64_t NA, float* pts, int32_t* rows, int32_t* d_M, void* stream);
+
+/* Sec. 2.5, Eq. 7: RANSAC with a full homography x_B ~ H x_A.
+ *  pts       device float[M_cap*4] (xA, yA, xB, yB)
+ *  M_cap     capacity of pts; the count used is *d_M when d_M != NULL, else M_cap
+ *  H         device double[9], row-major, h33 = 1 (all zero if no model)
+ *  inlier    device uint8[M_cap] final inlier mask (first M entries)
+ *  n_inliers device int32: inliers of the refitted H
+ *  best_t    device int32 or NULL: the winning iteration (-1 if none)
+ * Iteration t draws 4 distinct matches from Philox4x32-10 keyed by
+ * (lo32(seed), hi32(seed) ^ pair_id), counter (t, block, 0, 0), fits a
+ * normalised 4-point DLT in FP64, and counts inliers (e < thresh_px).  The
+ * most inliers win (earliest t on ties), decided in FP64 for every hypothesis
+ * whose FP32 count could reach the maximum.  The winner's inliers are refitted
+ * by least squares (FP64) and the final mask is taken from the refitted H.
+ * Errors: LP_ERR_ARG, LP_ERR_NOMEM, LP_ERR_CUDA. */
+LP_API int lp_ransac(lp_ctx* ctx, const float* pts, int64_t M_cap, const int32_t* d_M, uint32_t pair_id,
+              double* H, uint8_t* inlier, int32_t* n_inliers, int32_t* best_t, void* stream);
+
+/* The whole Sec. 2 path for one image pair held on the device: detect,
+ * describe, match, compact and RANSAC, with every intermediate in the
+ * context's workspace.  imgA/imgB as in lp_detect (same channels).
+ *  H        device double[9]; n_in device int32; M_out device int32 or NULL
+ * Errors: as the stages. */
+LP_API int lp_stitch_pair(lp_ctx* ctx, const uint8_t* imgA, int HA, int WA, int pitchA, const uint8_t* imgB,
+                   int HB, int WB, int pitchB, int channels, uint32_t pair_id, double* H, int32_t* n_in,
+                   int32_t* M_out, void* stream);
+
+/* lp_stitch_pair for images in HOST memory (pinned memory makes the copies
+ * asynchronous): copies both images to the context's workspace, runs the
+ * path, copies H, n_in and M back to the host buffers and synchronises
+ * `stream` before returning.  H_host double[9], n_in_host / M_host int32. */
+LP_API int lp_stitch_pair_host(lp_ctx* ctx, const uint8_t* imgA_host, int HA, int WA, int pitchA,
+                        const uint8_t* imgB_host, int HB, int WB, int pitchB, int channels,
+                        uint32_t pair_id, double* H_host, int32_t* n_in_host, int32_t* M_host, void* stream);
+
+/* Wait for the context's last stream, then return and clear the device
+ * status word (LP_OK, LP_ERR_TIMEOUT or LP_ERR_DEVICE) or a CUDA error. */
+LP_API int lp_sync_status(lp_ctx* ctx);
+
+/* Text of the last host-side error of this context (static storage). */
+LP_API const char* lp_last_error(lp_ctx* ctx);
+
+/* ---- diagnostics used by the test-suite (no paper counterpart needed) ---- */
+
+/* Orientation bin of every integer gradient (a, b) in [-255, 255]^2, written
+ * to device int32[511*511] at (a + 255) * 511 + (b + 255). */
+LP_API int lp_diag_orient_bins(int32_t* out, void* stream);
+/* round(65536 * sqrt(s)) for s in [0, 130050], device uint32[130051]. */
+LP_API int lp_diag_orient_weights(uint32_t* out, void* stream);
+/* Philox4x32-10 blocks: n counters (device uint32[n*4]) under one key. */
+LP_API int lp_diag_philox(const uint32_t* ctr, int64_t n, uint32_t key0, uint32_t key1, uint32_t* out, void* stream);
+/* RGB -> intensity of n pixels (device uint8[n*3] -> uint8[n]). */
+LP_API int lp_diag_gray(const uint8_t* rgb, int64_t n, uint8_t* gray, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LP_H */

@@ -201,7 +201,9 @@ int or_orient(const uint8_t* gray, int H, int W, int pitch, const uint32_t* idx,
     return 0;
 }
 
-/* Bilinear intensity at real (row r, column c), clamp-to-edge taps. */
+/* Bilinear intensity at real (row r, column c), clamp-to-edge taps.  Written
+ * as nested linear interpolation v0 + f*(v1 - v0), which returns a flat
+ * neighbourhood's value exactly (so its gradient is exactly zero). */
 static double bil(const uint8_t* g, int H, int W, int pitch, double r, double c)
 {
     double r0 = floor(r), c0 = floor(c);
@@ -209,7 +211,9 @@ static double bil(const uint8_t* g, int H, int W, int pitch, double r, double c)
     int y = (int)r0, x = (int)c0;
     double v00 = px(g, H, W, pitch, y, x), v01 = px(g, H, W, pitch, y, x + 1);
     double v10 = px(g, H, W, pitch, y + 1, x), v11 = px(g, H, W, pitch, y + 1, x + 1);
-    return (1 - fr) * ((1 - fc) * v00 + fc * v01) + fr * ((1 - fc) * v10 + fc * v11);
+    double top = v00 + fc * (v01 - v00);
+    double bot = v10 + fc * (v11 - v10);
+    return top + fr * (bot - top);
 }
 
 /* Sec. 2.3: a w x w region (w = d*w_s, d = 4) around the point, split into

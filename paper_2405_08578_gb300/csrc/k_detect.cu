@@ -1,0 +1,284 @@
+// Multiscale local-peak detection (Sec. 2.1-2.2, Eq. 1-2) for sm_103a.
+//
+// Eq. 1 adds alpha*(raster index + 1) to every pixel so that each window has a
+// unique maximum and minimum.  With alpha -> 0+ the ramp only breaks ties, which
+// is exactly the order of the 32-bit key (intensity << 24) | raster index for
+// H*W <= 2^24.  Peaks are therefore max/min of keys, and the result is
+// independent of the order of reduction (bit-exact, no atomics).
+//
+// Fast path (nested scales, Lmax <= 128): one CTA per Lmax x Lmax tile.  The
+// tile is streamed from HBM once with 16-byte loads (RGB converted to
+// intensity on the fly and written back as the dense intensity image), staged
+// in shared memory, reduced to per-row segment extrema of the finest window,
+// then to finest-window extrema, then each coarser level combines its children.
+// General path: one CTA per window per scale (any L set, any Lmax).
+#include "lp_internal.cuh"
+
+namespace lp {
+namespace {
+
+constexpr int kDetectThreads = 256;
+
+struct DetectParams {
+    const uint8_t* img;
+    uint8_t* gray;
+    uint32_t* kp;
+    int H, W, pitch;
+    int TS;                 // tile side (multiple of 16 and of every L)
+    int nL;
+    int L[LP_MAX_SCALES];
+    int nwx[LP_MAX_SCALES];
+    int nwy[LP_MAX_SCALES];
+    long long off[LP_MAX_SCALES];
+    int lvl_off[LP_MAX_SCALES + 1];   // start of each level's window keys in shared memory
+};
+
+__device__ __forceinline__ uint8_t rgb2gray(uint32_t r, uint32_t g, uint32_t b)
+{
+    return (uint8_t)((299u * r + 587u * g + 114u * b + 500u) / 1000u);
+}
+
+__device__ __forceinline__ uint8_t byte_of(const uint4& v, int i)
+{
+    uint32_t w = i < 4 ? v.x : i < 8 ? v.y : i < 12 ? v.z : v.w;
+    return (uint8_t)(w >> (8 * (i & 3)));
+}
+
+// 16 interleaved RGB pixels (48 bytes) -> 16 intensities.
+__device__ __forceinline__ uint4 gray16(const uint4& c0, const uint4& c1, const uint4& c2)
+{
+    uint32_t o[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int p = 0; p < 16; ++p) {
+        int b = 3 * p;
+        uint8_t r = b < 16 ? byte_of(c0, b) : b < 32 ? byte_of(c1, b - 16) : byte_of(c2, b - 32);
+        uint8_t g = b + 1 < 16 ? byte_of(c0, b + 1) : b + 1 < 32 ? byte_of(c1, b + 1 - 16) : byte_of(c2, b + 1 - 32);
+        uint8_t bl = b + 2 < 16 ? byte_of(c0, b + 2) : b + 2 < 32 ? byte_of(c1, b + 2 - 16) : byte_of(c2, b + 2 - 32);
+        o[p >> 2] |= (uint32_t)rgb2gray(r, g, bl) << (8 * (p & 3));
+    }
+    return make_uint4(o[0], o[1], o[2], o[3]);
+}
+
+template <int CH>
+__global__ void __launch_bounds__(kDetectThreads) k_detect_nested(DetectParams p)
+{
+    extern __shared__ __align__(16) uint8_t sm[];
+    const int TS = p.TS;
+    const int L0 = p.L[0];
+    const int spr = TS / L0;                 // segments per tile row
+    const int nseg = TS * spr;
+    uint8_t* tile = sm;
+    uint32_t* smx = reinterpret_cast<uint32_t*>(sm + TS * TS);
+    uint32_t* smn = smx + nseg;
+    uint32_t* wmx = smn + nseg;
+    uint32_t* wmn = wmx + p.lvl_off[p.nL];
+
+    const int tx0 = blockIdx.x * TS, ty0 = blockIdx.y * TS;
+    const int rows = min(TS, p.H - ty0), cols = min(TS, p.W - tx0);
+
+    // ---- stream the tile once: 16 pixels per 16-byte (gray) or 48-byte (RGB) load
+    const int gpr = TS / 16;
+    for (int g = threadIdx.x; g < TS * gpr; g += kDetectThreads) {
+        const int r = g / gpr, c = (g - r * gpr) * 16;
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (r < rows && c < cols) {
+            const uint8_t* row = p.img + (size_t)(ty0 + r) * p.pitch;
+            const int x = tx0 + c;
+            if (CH == 1) {
+                v = __ldg(reinterpret_cast<const uint4*>(row + x));
+            } else {
+                // chunk q holds bytes [3x + 16q, 3x + 16q + 16); it lies inside the
+                // pitch whenever its first byte is a pixel byte of this row
+                const uint4* src = reinterpret_cast<const uint4*>(row + 3 * (size_t)x);
+                uint4 c0 = __ldg(src);
+                uint4 c1 = (3 * x + 16 < 3 * p.W) ? __ldg(src + 1) : make_uint4(0, 0, 0, 0);
+                uint4 c2 = (3 * x + 32 < 3 * p.W) ? __ldg(src + 2) : make_uint4(0, 0, 0, 0);
+                v = gray16(c0, c1, c2);
+                uint8_t* gout = p.gray + (size_t)(ty0 + r) * p.W + x;
+                if ((p.W & 15) == 0) {
+                    *reinterpret_cast<uint4*>(gout) = v;
+                } else {
+                    const int n = min(16, p.W - x);
+                    for (int i = 0; i < n; ++i) gout[i] = byte_of(v, i);
+                }
+            }
+        }
+        *reinterpret_cast<uint4*>(tile + r * TS + c) = v;
+    }
+    __syncthreads();
+
+    // ---- finest scale: extrema of every L0-pixel row segment of a full window
+    const int Hf = (p.H / L0) * L0 - ty0, Wf = (p.W / L0) * L0 - tx0;
+    for (int s = threadIdx.x; s < nseg; s += kDetectThreads) {
+        const int r = s / spr, c0 = (s - r * spr) * L0;
+        uint32_t kmax = 0u, kmin = 0xFFFFFFFFu;
+        if (r < Hf && c0 < Wf) {
+            const uint32_t base = (uint32_t)(ty0 + r) * (uint32_t)p.W + (uint32_t)(tx0 + c0);
+            const uint8_t* t = tile + r * TS + c0;
+            for (int i = 0; i < L0; ++i) {
+                const uint32_t k = ((uint32_t)t[i] << 24) | (base + i);
+                kmax = max(kmax, k);
+                kmin = min(kmin, k);
+            }
+        }
+        smx[s] = kmax;
+        smn[s] = kmin;
+    }
+    __syncthreads();
+
+    // ---- level 0 windows from their L0 segments
+    {
+        const int n0 = TS / L0;
+        for (int w = threadIdx.x; w < n0 * n0; w += kDetectThreads) {
+            const int wr = w / n0, wc = w - wr * n0;
+            uint32_t kmax = 0u, kmin = 0xFFFFFFFFu;
+            for (int i = 0; i < L0; ++i) {
+                const int s = (wr * L0 + i) * spr + wc;
+                kmax = max(kmax, smx[s]);
+                kmin = min(kmin, smn[s]);
+            }
+            wmx[w] = kmax;
+            wmn[w] = kmin;
+            const int gy = ty0 / L0 + wr, gx = tx0 / L0 + wc;
+            if (gy < p.nwy[0] && gx < p.nwx[0]) {
+                uint2 o = make_uint2(kmax & 0xFFFFFFu, kmin & 0xFFFFFFu);
+                *reinterpret_cast<uint2*>(p.kp + p.off[0] + 2ll * ((long long)gy * p.nwx[0] + gx)) = o;
+            }
+        }
+    }
+    // ---- coarser levels combine their (L_l / L_{l-1})^2 children
+    for (int l = 1; l < p.nL; ++l) {
+        __syncthreads();
+        const int nl = TS / p.L[l], np = TS / p.L[l - 1], q = p.L[l] / p.L[l - 1];
+        const uint32_t* cmx = wmx + p.lvl_off[l - 1];
+        const uint32_t* cmn = wmn + p.lvl_off[l - 1];
+        for (int w = threadIdx.x; w < nl * nl; w += kDetectThreads) {
+            const int wr = w / nl, wc = w - wr * nl;
+            uint32_t kmax = 0u, kmin = 0xFFFFFFFFu;
+            for (int i = 0; i < q; ++i)
+                for (int j = 0; j < q; ++j) {
+                    const int cidx = (wr * q + i) * np + wc * q + j;
+                    kmax = max(kmax, cmx[cidx]);
+                    kmin = min(kmin, cmn[cidx]);
+                }
+            wmx[p.lvl_off[l] + w] = kmax;
+            wmn[p.lvl_off[l] + w] = kmin;
+            const int gy = ty0 / p.L[l] + wr, gx = tx0 / p.L[l] + wc;
+            if (gy < p.nwy[l] && gx < p.nwx[l]) {
+                uint2 o = make_uint2(kmax & 0xFFFFFFu, kmin & 0xFFFFFFu);
+                *reinterpret_cast<uint2*>(p.kp + p.off[l] + 2ll * ((long long)gy * p.nwx[l] + gx)) = o;
+            }
+        }
+    }
+}
+
+// General path: one CTA per full window of one scale.
+template <int CH>
+__global__ void __launch_bounds__(kDetectThreads) k_detect_window(const uint8_t* img, int H, int W, int pitch,
+                                                                   int L, int nwx, long long off, uint32_t* kp)
+{
+    const int w = blockIdx.x;
+    const int wy = w / nwx, wx = w - wy * nwx;
+    uint32_t kmax = 0u, kmin = 0xFFFFFFFFu;
+    const int n = L * L;
+    for (int i = threadIdx.x; i < n; i += kDetectThreads) {
+        const int r = i / L, c = i - r * L;
+        const int y = wy * L + r, x = wx * L + c;
+        const uint8_t* px = img + (size_t)y * pitch + (size_t)CH * x;
+        const uint32_t g = CH == 1 ? px[0] : rgb2gray(px[0], px[1], px[2]);
+        const uint32_t k = (g << 24) | ((uint32_t)y * (uint32_t)W + (uint32_t)x);
+        kmax = max(kmax, k);
+        kmin = min(kmin, k);
+    }
+    for (int o = 16; o; o >>= 1) {
+        kmax = max(kmax, __shfl_xor_sync(0xFFFFFFFFu, kmax, o));
+        kmin = min(kmin, __shfl_xor_sync(0xFFFFFFFFu, kmin, o));
+    }
+    __shared__ uint32_t rmx[kDetectThreads / 32], rmn[kDetectThreads / 32];
+    if ((threadIdx.x & 31) == 0) {
+        rmx[threadIdx.x >> 5] = kmax;
+        rmn[threadIdx.x >> 5] = kmin;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int i = 1; i < kDetectThreads / 32; ++i) {
+            kmax = max(kmax, rmx[i]);
+            kmin = min(kmin, rmn[i]);
+        }
+        kp[off + 2ll * w] = kmax & 0xFFFFFFu;
+        kp[off + 2ll * w + 1] = kmin & 0xFFFFFFu;
+    }
+    (void)H;
+}
+
+__global__ void k_rgb_to_gray(const uint8_t* img, int H, int W, int pitch, uint8_t* gray)
+{
+    const long long n = (long long)H * W;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(i / W), x = (int)(i - (long long)y * W);
+        const uint8_t* px = img + (size_t)y * pitch + 3 * (size_t)x;
+        gray[i] = rgb2gray(px[0], px[1], px[2]);
+    }
+}
+
+__global__ void k_diag_gray(const uint8_t* rgb, long long n, uint8_t* gray)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        gray[i] = rgb2gray(rgb[3 * i], rgb[3 * i + 1], rgb[3 * i + 2]);
+}
+
+}  // namespace
+
+cudaError_t launch_detect(const uint8_t* img, int H, int W, int pitch, int ch, const ScaleTable& st,
+                          uint32_t* kp, uint8_t* gray, cudaStream_t s)
+{
+    bool nested = st.L[st.nL - 1] <= 128;
+    for (int l = 1; l < st.nL && nested; ++l) nested = st.L[l] % st.L[l - 1] == 0;
+    int TS = st.L[st.nL - 1];
+    if (nested && TS % 16 != 0) {
+        // a tile must hold whole 16-byte loads: use 16 when every L divides it
+        nested = (16 % TS == 0);
+        TS = 16;
+    }
+    if (nested && (long long)TS * TS / st.L[0] > 4096) nested = false;
+    if (nested) {
+        DetectParams p;
+        p.img = img; p.gray = gray; p.kp = kp; p.H = H; p.W = W; p.pitch = pitch; p.TS = TS; p.nL = st.nL;
+        int acc = 0;
+        for (int l = 0; l < st.nL; ++l) {
+            p.L[l] = st.L[l]; p.nwx[l] = st.nwx[l]; p.nwy[l] = st.nwy[l]; p.off[l] = st.off[l];
+            p.lvl_off[l] = acc;
+            acc += (TS / st.L[l]) * (TS / st.L[l]);
+        }
+        for (int l = st.nL; l <= LP_MAX_SCALES; ++l) p.lvl_off[l] = acc;
+        const int nseg = TS * TS / st.L[0];
+        const size_t smem = (size_t)TS * TS + 8u * nseg + 8u * acc;
+        dim3 grid((W + TS - 1) / TS, (H + TS - 1) / TS);
+        if (ch == 1) {
+            if (smem > 48 * 1024) cudaFuncSetAttribute(k_detect_nested<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            k_detect_nested<1><<<grid, kDetectThreads, smem, s>>>(p);
+        } else {
+            if (smem > 48 * 1024) cudaFuncSetAttribute(k_detect_nested<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            k_detect_nested<3><<<grid, kDetectThreads, smem, s>>>(p);
+        }
+        return cudaGetLastError();
+    }
+    if (ch == 3) k_rgb_to_gray<<<1216, 256, 0, s>>>(img, H, W, pitch, gray);
+    for (int l = 0; l < st.nL; ++l) {
+        const int nw = st.nwx[l] * st.nwy[l];
+        if (nw == 0) continue;
+        if (ch == 1)
+            k_detect_window<1><<<nw, kDetectThreads, 0, s>>>(img, H, W, pitch, st.L[l], st.nwx[l], st.off[l], kp);
+        else
+            k_detect_window<3><<<nw, kDetectThreads, 0, s>>>(img, H, W, pitch, st.L[l], st.nwx[l], st.off[l], kp);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_diag_gray(const uint8_t* rgb, int64_t n, uint8_t* gray, cudaStream_t s)
+{
+    k_diag_gray<<<1216, 256, 0, s>>>(rgb, n, gray);
+    return cudaGetLastError();
+}
+
+}  // namespace lp

@@ -1,0 +1,532 @@
+// Matched-pair compaction and RANSAC homography estimation (Sec. 2.4-2.5,
+// Eq. 7) for sm_103a.
+//
+//  k_compact      one CTA: stable prefix sum of accepted rows -> (xA, yA, xB, yB)
+//  k_ransac_hyp   one thread per iteration t: Philox4x32-10 draw of 4 distinct
+//                 matches, collinearity test, Hartley-normalised 4-point DLT
+//                 solved in FP64 (8x8 Gaussian elimination, partial pivoting)
+//  k_ransac_score one CTA per hypothesis: FP32 reprojection errors; counts of
+//                 points certainly inside (e^2 < t^2 - eps) and possibly inside
+//                 (e^2 < t^2 + eps)
+//  k_ransac_select one CTA: the largest certain count c*; every hypothesis whose
+//                 possible count reaches c* and that has points in the band is
+//                 recounted in FP64, so the winner (most inliers, earliest t) is
+//                 the FP64 winner
+//  k_ransac_refit one CTA: FP64 inlier mask of the winner, Hartley
+//                 normalisation, A^T A (9x9) by block reduction, cyclic Jacobi
+//                 smallest eigenvector, denormalisation, final FP64 mask.
+#include <math.h>
+
+#include "lp_internal.cuh"
+
+namespace lp {
+namespace {
+
+// ---------------------------------------------------------------- Philox
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds; each round
+// multiplies words 0 and 2 by fixed odd constants (high/low halves), xors the
+// high halves with words 1/3 and the round key; the key advances by the Weyl
+// constants between rounds.
+__device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+__global__ void k_diag_philox(const uint4* ctr, long long n, uint32_t k0, uint32_t k1, uint4* out)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = philox(ctr[i], k0, k1);
+}
+
+// ---------------------------------------------------------------- compaction
+constexpr int kCompactThreads = 1024;
+
+__global__ void __launch_bounds__(kCompactThreads)
+k_compact(const uint32_t* kpA, int WA, const uint32_t* kpB, int WB, const int32_t* match, long long NA,
+          float4* pts, int32_t* rows, int32_t* dM)
+{
+    __shared__ int warp_tot[32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const long long chunk = (NA + kCompactThreads - 1) / kCompactThreads;
+    const long long b = tid * chunk, e = min(NA, b + chunk);
+    int cnt = 0;
+    for (long long i = b; i < e; ++i) cnt += match[i] >= 0;
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int w = warp_tot[lane];
+        int wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xFFFFFFFFu, wi, o);
+            if (lane >= o) wi += v;
+        }
+        warp_tot[lane] = wi - w;   // exclusive
+        if (lane == 31) *dM = wi;
+    }
+    __syncthreads();
+    int pos = warp_tot[warp] + incl - cnt;
+    for (long long i = b; i < e; ++i) {
+        const int j = match[i];
+        if (j < 0) continue;
+        const uint32_t ia = kpA[i], ib = kpB[j];
+        const uint32_t ya = ia / (uint32_t)WA, yb = ib / (uint32_t)WB;
+        pts[pos] = make_float4((float)(ia - ya * WA), (float)ya, (float)(ib - yb * WB), (float)yb);
+        if (rows) rows[pos] = (int32_t)i;
+        ++pos;
+    }
+}
+
+// ---------------------------------------------------------------- FP64 model
+__device__ __forceinline__ long long m_count(const int32_t* dM, long long M_cap)
+{
+    if (!dM) return M_cap;
+    const long long m = *dM;
+    return m < 0 ? 0 : (m > M_cap ? M_cap : m);
+}
+
+// |cross(q - p, r - p)| small relative to the spread: the three are on a line.
+__device__ __forceinline__ bool collinear(double px, double py, double qx, double qy, double rx, double ry)
+{
+    const double ux = qx - px, uy = qy - py, vx = rx - px, vy = ry - py;
+    return fabs(ux * vy - uy * vx) <= 1e-9 * (ux * ux + uy * uy + vx * vx + vy * vy);
+}
+
+struct Norm2D { double s, cx, cy; };
+
+// centroid to the origin, mean distance sqrt(2)
+__device__ bool hartley4(const double* x, const double* y, Norm2D& n)
+{
+    double cx = 0, cy = 0;
+    for (int i = 0; i < 4; ++i) { cx += x[i]; cy += y[i]; }
+    cx /= 4; cy /= 4;
+    double md = 0;
+    for (int i = 0; i < 4; ++i) md += sqrt((x[i] - cx) * (x[i] - cx) + (y[i] - cy) * (y[i] - cy));
+    md /= 4;
+    if (!(md > 0)) return false;
+    n.s = sqrt(2.0) / md; n.cx = cx; n.cy = cy;
+    return true;
+}
+
+// H = Tb^-1 * Hn * Ta with T = [[s, 0, -s cx], [0, s, -s cy], [0, 0, 1]], h33 -> 1.
+__device__ bool denorm(const Norm2D& na, const Norm2D& nb, const double* hn, double* H)
+{
+    // Hn * Ta
+    double t[9];
+    for (int r = 0; r < 3; ++r) {
+        t[3 * r + 0] = hn[3 * r + 0] * na.s;
+        t[3 * r + 1] = hn[3 * r + 1] * na.s;
+        t[3 * r + 2] = hn[3 * r + 2] - hn[3 * r + 0] * na.s * na.cx - hn[3 * r + 1] * na.s * na.cy;
+    }
+    // Tb^-1 = [[1/s, 0, cx], [0, 1/s, cy], [0, 0, 1]]
+    const double is = 1.0 / nb.s;
+    for (int c = 0; c < 3; ++c) {
+        H[0 + c] = is * t[0 + c] + nb.cx * t[6 + c];
+        H[3 + c] = is * t[3 + c] + nb.cy * t[6 + c];
+        H[6 + c] = t[6 + c];
+    }
+    double mx = 0;
+    for (int i = 0; i < 9; ++i) mx = fmax(mx, fabs(H[i]));
+    if (!(fabs(H[8]) > 1e-12 * mx)) return false;
+    const double h = H[8];
+    for (int i = 0; i < 9; ++i) H[i] /= h;
+    return true;
+}
+
+__global__ void k_ransac_hyp(const float4* pts, long long M_cap, const int32_t* dM, int T, uint32_t k0, uint32_t k1,
+                             double* Hs, int8_t* hok)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= T) return;
+    hok[t] = 0;
+    const long long M = m_count(dM, M_cap);
+    if (M < 4) return;
+    int idx[4];
+    int n = 0;
+    uint4 blk = make_uint4(0, 0, 0, 0);
+    for (int j = 0; j < 64 && n < 4; ++j) {
+        if ((j & 3) == 0) blk = philox(make_uint4((uint32_t)t, (uint32_t)(j >> 2), 0u, 0u), k0, k1);
+        const uint32_t w = (j & 3) == 0 ? blk.x : (j & 3) == 1 ? blk.y : (j & 3) == 2 ? blk.z : blk.w;
+        const int i = (int)(((unsigned long long)w * (unsigned long long)M) >> 32);
+        bool dup = false;
+        for (int q = 0; q < n; ++q) dup |= idx[q] == i;
+        if (!dup) idx[n++] = i;
+    }
+    if (n < 4) return;
+    double xa[4], ya[4], xb[4], yb[4];
+    for (int q = 0; q < 4; ++q) {
+        const float4 p = pts[idx[q]];
+        xa[q] = p.x; ya[q] = p.y; xb[q] = p.z; yb[q] = p.w;
+    }
+    for (int a = 0; a < 4; ++a) {
+        const int i0 = (a + 1) & 3, i1 = (a + 2) & 3, i2 = (a + 3) & 3;
+        if (collinear(xa[i0], ya[i0], xa[i1], ya[i1], xa[i2], ya[i2])) return;
+        if (collinear(xb[i0], yb[i0], xb[i1], yb[i1], xb[i2], yb[i2])) return;
+    }
+    Norm2D na, nb;
+    if (!hartley4(xa, ya, na) || !hartley4(xb, yb, nb)) return;
+    double A[8][9];
+    for (int q = 0; q < 4; ++q) {
+        const double x = na.s * (xa[q] - na.cx), y = na.s * (ya[q] - na.cy);
+        const double u = nb.s * (xb[q] - nb.cx), v = nb.s * (yb[q] - nb.cy);
+        double* r0 = A[2 * q];
+        double* r1 = A[2 * q + 1];
+        r0[0] = x; r0[1] = y; r0[2] = 1; r0[3] = 0; r0[4] = 0; r0[5] = 0; r0[6] = -x * u; r0[7] = -y * u; r0[8] = u;
+        r1[0] = 0; r1[1] = 0; r1[2] = 0; r1[3] = x; r1[4] = y; r1[5] = 1; r1[6] = -x * v; r1[7] = -y * v; r1[8] = v;
+    }
+    for (int c = 0; c < 8; ++c) {
+        int p = c;
+        for (int r = c + 1; r < 8; ++r)
+            if (fabs(A[r][c]) > fabs(A[p][c])) p = r;
+        if (!(fabs(A[p][c]) > 1e-10)) return;
+        if (p != c)
+            for (int j = 0; j < 9; ++j) { const double tmp = A[c][j]; A[c][j] = A[p][j]; A[p][j] = tmp; }
+        for (int r = c + 1; r < 8; ++r) {
+            const double f = A[r][c] / A[c][c];
+            for (int j = c; j < 9; ++j) A[r][j] -= f * A[c][j];
+        }
+    }
+    double h[9];
+    for (int r = 7; r >= 0; --r) {
+        double s = A[r][8];
+        for (int j = r + 1; j < 8; ++j) s -= A[r][j] * h[j];
+        h[r] = s / A[r][r];
+    }
+    h[8] = 1.0;
+    double H[9];
+    if (!denorm(na, nb, h, H)) return;
+    for (int i = 0; i < 9; ++i) Hs[9ll * t + i] = H[i];
+    hok[t] = 1;
+}
+
+// ---------------------------------------------------------------- scoring
+constexpr int kScoreThreads = 256;
+
+__device__ __forceinline__ int block_sum(int v, int* red)
+{
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    int s = 0;
+    for (int w = 0; w < nw; ++w) s += red[w];
+    return s;
+}
+
+__global__ void __launch_bounds__(kScoreThreads)
+k_ransac_score(const float4* pts, long long M_cap, const int32_t* dM, const double* Hs, const int8_t* hok,
+               float t2, float eps, int32_t* lo, int32_t* hi)
+{
+    __shared__ int red[32];
+    const int t = blockIdx.x;
+    if (!hok[t]) {
+        if (threadIdx.x == 0) { lo[t] = -1; hi[t] = -1; }
+        return;
+    }
+    const long long M = m_count(dM, M_cap);
+    float h[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) h[i] = (float)Hs[9ll * t + i];
+    int clo = 0, chi = 0;
+    for (long long i = threadIdx.x; i < M; i += kScoreThreads) {
+        const float4 p = pts[i];
+        const float w = fmaf(h[6], p.x, fmaf(h[7], p.y, h[8]));
+        if (w > 0.f) {
+            const float u = fmaf(h[0], p.x, fmaf(h[1], p.y, h[2])) / w - p.z;
+            const float v = fmaf(h[3], p.x, fmaf(h[4], p.y, h[5])) / w - p.w;
+            const float e2 = u * u + v * v;
+            clo += e2 < t2 - eps;
+            chi += e2 < t2 + eps;
+        }
+    }
+    clo = block_sum(clo, red);
+    chi = block_sum(chi, red);
+    if (threadIdx.x == 0) { lo[t] = clo; hi[t] = chi; }
+}
+
+// FP64 inlier test of one correspondence (Eq. 7, one-sided error in B).
+__device__ __forceinline__ bool inlier64(const double* H, const float4& p, double t2)
+{
+    const double x = p.x, y = p.y;
+    const double w = H[6] * x + H[7] * y + H[8];
+    if (!(w > 0)) return false;
+    const double u = (H[0] * x + H[1] * y + H[2]) / w - (double)p.z;
+    const double v = (H[3] * x + H[4] * y + H[5]) / w - (double)p.w;
+    return u * u + v * v < t2;
+}
+
+constexpr int kSelThreads = 1024;
+
+__global__ void __launch_bounds__(kSelThreads)
+k_ransac_select(const float4* pts, long long M_cap, const int32_t* dM, int T, const double* Hs,
+                const int32_t* lo, const int32_t* hi, double t2, int32_t* best_out)
+{
+    __shared__ int red[32];
+    __shared__ unsigned long long bestkey;
+    __shared__ int cand[kSelThreads];
+    __shared__ int ncand;
+    const long long M = m_count(dM, M_cap);
+    int cmax = -1;
+    for (int t = threadIdx.x; t < T; t += kSelThreads) cmax = max(cmax, lo[t]);
+#pragma unroll
+    for (int o = 16; o; o >>= 1) cmax = max(cmax, __shfl_xor_sync(0xFFFFFFFFu, cmax, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = cmax;
+    if (threadIdx.x == 0) { bestkey = 0ull; ncand = 0; }
+    __syncthreads();
+    cmax = -1;
+    for (int w = 0; w < kSelThreads / 32; ++w) cmax = max(cmax, red[w]);
+    if (cmax < 0) {
+        if (threadIdx.x == 0) *best_out = -1;
+        return;
+    }
+    // key = (count + 1) << 32 | (0xFFFFFFFF - t): the max key is the most
+    // inliers at the earliest iteration.  Iterations are visited in chunks of
+    // one CTA width; in-band candidates of a chunk are recounted in FP64.
+    for (int t0 = 0; t0 < T; t0 += kSelThreads) {
+        const int t = t0 + threadIdx.x;
+        if (t < T) {
+            const int l = lo[t], h = hi[t];
+            if (l >= 0 && h >= cmax) {
+                if (h == l) {
+                    atomicMax(&bestkey, ((unsigned long long)(l + 1) << 32) | (0xFFFFFFFFull - (unsigned)t));
+                } else {
+                    cand[atomicAdd(&ncand, 1)] = t;
+                }
+            }
+        }
+        __syncthreads();
+        const int nc = ncand;
+        for (int k = 0; k < nc; ++k) {
+            const int tc = cand[k];
+            double H[9];
+            for (int i = 0; i < 9; ++i) H[i] = Hs[9ll * tc + i];
+            int n = 0;
+            for (long long i = threadIdx.x; i < M; i += kSelThreads) n += inlier64(H, pts[i], t2);
+            n = block_sum(n, red);
+            if (threadIdx.x == 0)
+                atomicMax(&bestkey, ((unsigned long long)(n + 1) << 32) | (0xFFFFFFFFull - (unsigned)tc));
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) ncand = 0;
+        __syncthreads();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *best_out = (int)(0xFFFFFFFFull - (bestkey & 0xFFFFFFFFull));
+}
+
+// ---------------------------------------------------------------- refit
+constexpr int kRefitThreads = 256;
+
+__device__ double block_sum_d(double v, double* red)
+{
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double s = 0;
+    for (int w = 0; w < kRefitThreads / 32; ++w) s += red[w];
+    return s;
+}
+
+// Cyclic Jacobi eigen-decomposition of a symmetric 9x9 matrix; returns the
+// eigenvector of the smallest eigenvalue.
+__device__ void jacobi9_smallest(double a[9][9], double* h)
+{
+    double v[9][9];
+    for (int i = 0; i < 9; ++i)
+        for (int j = 0; j < 9; ++j) v[i][j] = i == j;
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0, tot = 0;
+        for (int i = 0; i < 9; ++i)
+            for (int j = 0; j < 9; ++j) {
+                tot += a[i][j] * a[i][j];
+                if (i != j) off += a[i][j] * a[i][j];
+            }
+        if (off == 0 || off < 1e-30 * tot) break;
+        for (int p = 0; p < 9; ++p)
+            for (int q = p + 1; q < 9; ++q) {
+                if (a[p][q] == 0) continue;
+                const double th = (a[q][q] - a[p][p]) / (2.0 * a[p][q]);
+                const double t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+                const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+                for (int k = 0; k < 9; ++k) {
+                    const double akp = a[k][p], akq = a[k][q];
+                    a[k][p] = c * akp - s * akq;
+                    a[k][q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < 9; ++k) {
+                    const double apk = a[p][k], aqk = a[q][k];
+                    a[p][k] = c * apk - s * aqk;
+                    a[q][k] = s * apk + c * aqk;
+                }
+                for (int k = 0; k < 9; ++k) {
+                    const double vkp = v[k][p], vkq = v[k][q];
+                    v[k][p] = c * vkp - s * vkq;
+                    v[k][q] = s * vkp + c * vkq;
+                }
+            }
+    }
+    int m = 0;
+    for (int i = 1; i < 9; ++i)
+        if (a[i][i] < a[m][m]) m = i;
+    for (int k = 0; k < 9; ++k) h[k] = v[k][m];
+}
+
+__global__ void __launch_bounds__(kRefitThreads)
+k_ransac_refit(const float4* pts, long long M_cap, const int32_t* dM, const double* Hs, const int32_t* best_in,
+               double t2, double* Hout, uint8_t* inl, int32_t* n_in, int32_t* best_t)
+{
+    __shared__ double red[kRefitThreads / 32];
+    __shared__ double Hf[9];
+    __shared__ double S[45];
+    const long long M = m_count(dM, M_cap);
+    const int best = *best_in;
+    if (threadIdx.x == 0 && best_t) *best_t = best;
+    if (best < 0) {
+        for (long long i = threadIdx.x; i < M_cap; i += kRefitThreads) inl[i] = 0;
+        if (threadIdx.x < 9) Hout[threadIdx.x] = 0.0;
+        if (threadIdx.x == 0) *n_in = 0;
+        return;
+    }
+    double Hb[9];
+    for (int i = 0; i < 9; ++i) Hb[i] = Hs[9ll * best + i];
+    // inliers of the winning hypothesis and their centroids
+    double sxa = 0, sya = 0, sxb = 0, syb = 0, cnt = 0;
+    for (long long i = threadIdx.x; i < M; i += kRefitThreads) {
+        const float4 p = pts[i];
+        const bool in = inlier64(Hb, p, t2);
+        inl[i] = in;
+        if (in) { sxa += p.x; sya += p.y; sxb += p.z; syb += p.w; cnt += 1; }
+    }
+    cnt = block_sum_d(cnt, red);
+    const double cxa = block_sum_d(sxa, red) / cnt, cya = block_sum_d(sya, red) / cnt;
+    const double cxb = block_sum_d(sxb, red) / cnt, cyb = block_sum_d(syb, red) / cnt;
+    double da = 0, db = 0;
+    for (long long i = threadIdx.x; i < M; i += kRefitThreads) {
+        if (!inl[i]) continue;
+        const float4 p = pts[i];
+        da += sqrt((p.x - cxa) * (p.x - cxa) + (p.y - cya) * (p.y - cya));
+        db += sqrt((p.z - cxb) * (p.z - cxb) + (p.w - cyb) * (p.w - cyb));
+    }
+    da = block_sum_d(da, red) / cnt;
+    db = block_sum_d(db, red) / cnt;
+    const Norm2D na{sqrt(2.0) / da, cxa, cya}, nb{sqrt(2.0) / db, cxb, cyb};
+    const bool good = cnt >= 4 && da > 0 && db > 0;
+    // upper triangle of A^T A, 45 entries
+    double acc[45];
+#pragma unroll
+    for (int q = 0; q < 45; ++q) acc[q] = 0;
+    if (good) {
+        for (long long i = threadIdx.x; i < M; i += kRefitThreads) {
+            if (!inl[i]) continue;
+            const float4 p = pts[i];
+            const double x = na.s * (p.x - na.cx), y = na.s * (p.y - na.cy);
+            const double u = nb.s * (p.z - nb.cx), v = nb.s * (p.w - nb.cy);
+            const double r0[9] = {-x, -y, -1, 0, 0, 0, x * u, y * u, u};
+            const double r1[9] = {0, 0, 0, -x, -y, -1, x * v, y * v, v};
+            int q = 0;
+#pragma unroll
+            for (int j = 0; j < 9; ++j)
+#pragma unroll
+                for (int k = j; k < 9; ++k) acc[q++] += r0[j] * r0[k] + r1[j] * r1[k];
+        }
+    }
+    for (int q = 0; q < 45; ++q) {
+        const double s = block_sum_d(acc[q], red);
+        if (threadIdx.x == 0) S[q] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        bool ok = good;
+        double H[9];
+        if (ok) {
+            double a[9][9];
+            int q = 0;
+            for (int j = 0; j < 9; ++j)
+                for (int k = j; k < 9; ++k) { a[j][k] = S[q]; a[k][j] = S[q]; ++q; }
+            double h[9];
+            jacobi9_smallest(a, h);
+            ok = denorm(na, nb, h, H);
+        }
+        for (int i = 0; i < 9; ++i) Hf[i] = ok ? H[i] : Hb[i];
+    }
+    __syncthreads();
+    double Hfin[9];
+    for (int i = 0; i < 9; ++i) Hfin[i] = Hf[i];
+    int n = 0;
+    for (long long i = threadIdx.x; i < M_cap; i += kRefitThreads) {
+        const bool in = i < M && inlier64(Hfin, pts[i], t2);
+        inl[i] = in;
+        n += in;
+    }
+    const double nn = block_sum_d((double)n, red);
+    if (threadIdx.x < 9) Hout[threadIdx.x] = Hfin[threadIdx.x];
+    if (threadIdx.x == 0) *n_in = (int)nn;
+}
+
+}  // namespace
+
+cudaError_t launch_compact(const uint32_t* kpA, int WA, const uint32_t* kpB, int WB, const int32_t* match,
+                           int64_t NA, float* pts, int32_t* rows, int32_t* d_M, cudaStream_t s)
+{
+    k_compact<<<1, kCompactThreads, 0, s>>>(kpA, WA, kpB, WB, match, NA, reinterpret_cast<float4*>(pts), rows, d_M);
+    return cudaGetLastError();
+}
+
+size_t ransac_workspace(int64_t M_cap, int T)
+{
+    (void)M_cap;
+    return 256 + (size_t)T * (9 * sizeof(double) + 2 * sizeof(int32_t) + 1) + 256;
+}
+
+cudaError_t launch_ransac(const float* pts, int64_t M_cap, const int32_t* d_M, int T, float thresh,
+                          uint64_t seed, uint32_t pair_id, double* H, uint8_t* inlier, int32_t* n_in,
+                          int32_t* best_t, void* ws, size_t ws_bytes, int32_t* status, cudaStream_t s)
+{
+    (void)status;
+    if (ws_bytes < ransac_workspace(M_cap, T)) return cudaErrorInvalidValue;
+    uint8_t* w = static_cast<uint8_t*>(ws);
+    double* Hs = reinterpret_cast<double*>(w);
+    int32_t* lo = reinterpret_cast<int32_t*>(Hs + 9ll * T);
+    int32_t* hi = lo + T;
+    int32_t* best = hi + T;
+    int8_t* hok = reinterpret_cast<int8_t*>(best + 1);
+    const float4* p4 = reinterpret_cast<const float4*>(pts);
+    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32) ^ pair_id;
+    const double t2 = (double)thresh * (double)thresh;
+    const float t2f = (float)t2;
+    const float eps = fmaxf(0.05f, 0.01f * t2f);
+    k_ransac_hyp<<<(T + 127) / 128, 128, 0, s>>>(p4, M_cap, d_M, T, k0, k1, Hs, hok);
+    k_ransac_score<<<T, kScoreThreads, 0, s>>>(p4, M_cap, d_M, Hs, hok, t2f, eps, lo, hi);
+    k_ransac_select<<<1, kSelThreads, 0, s>>>(p4, M_cap, d_M, T, Hs, lo, hi, t2, best);
+    k_ransac_refit<<<1, kRefitThreads, 0, s>>>(p4, M_cap, d_M, Hs, best, t2, H, inlier, n_in, best_t);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_diag_philox(const uint32_t* ctr, int64_t n, uint32_t k0, uint32_t k1, uint32_t* out, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    k_diag_philox<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(reinterpret_cast<const uint4*>(ctr), n, k0, k1,
+                                                              reinterpret_cast<uint4*>(out));
+    return cudaGetLastError();
+}
+
+}  // namespace lp

@@ -1,0 +1,427 @@
+// C ABI of liblp: argument validation, context, workspace and the stage
+// sequence of the LP-SIFT path (Sec. 2 of the paper, Fig. 2 steps (b)-(f)).
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "lp_internal.cuh"
+
+namespace {
+
+struct DBuf {
+    void* p = nullptr;
+    size_t n = 0;
+};
+
+enum BufId {
+    B_MATCH_WS, B_RANSAC_WS,
+    B_IMG_A, B_IMG_B, B_GRAY_A, B_GRAY_B, B_KP_A, B_KP_B, B_ORI_A, B_ORI_B,
+    B_DESC_A, B_DESC_B, B_D16_A, B_D16_B, B_VAL_A, B_VAL_B,
+    B_MATCH, B_D1, B_D2, B_PTS, B_M, B_INL, B_H, B_NIN, B_BEST,
+    B_COUNT
+};
+
+}  // namespace
+
+struct lp_ctx {
+    lp_config cfg;
+    int device = 0;
+    int num_sms = 0;
+    int32_t* d_status = nullptr;
+    cudaStream_t last = nullptr;
+    DBuf buf[B_COUNT];
+    char err[512];
+};
+
+namespace {
+
+int fail(lp_ctx* c, int code, const char* fmt, ...)
+{
+    if (c) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(c->err, sizeof c->err, fmt, ap);
+        va_end(ap);
+    }
+    return code;
+}
+
+int cuda_fail(lp_ctx* c, cudaError_t e, const char* what)
+{
+    return fail(c, LP_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define LP_CUDA(ctx, call)                                    \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+    } while (0)
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+// Grow-only device buffer owned by the context.  Growing waits for the
+// context's last stream so that no queued kernel still uses the old block.
+int ensure(lp_ctx* c, BufId id, size_t bytes)
+{
+    DBuf& b = c->buf[id];
+    if (b.n >= bytes && b.p) return LP_OK;
+    if (b.p) {
+        if (c->last) cudaStreamSynchronize(c->last);
+        cudaFree(b.p);
+        b.p = nullptr;
+        b.n = 0;
+    }
+    size_t n = std::max<size_t>(bytes, 256);
+    n = (n + 4095) & ~size_t(4095);
+    cudaError_t e = cudaMalloc(&b.p, n);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        b.p = nullptr;
+        return fail(c, LP_ERR_NOMEM, "workspace allocation of %zu bytes failed: %s", n, cudaGetErrorString(e));
+    }
+    b.n = n;
+    return LP_OK;
+}
+
+int check_cfg(lp_ctx* c, const lp_config* cfg)
+{
+    if (!cfg) return fail(c, LP_ERR_ARG, "null config");
+    if (cfg->nL < 1 || cfg->nL > LP_MAX_SCALES) return fail(c, LP_ERR_ARG, "nL=%d outside 1..%d", cfg->nL, LP_MAX_SCALES);
+    for (int l = 0; l < cfg->nL; ++l) {
+        if (cfg->Ls[l] < 2 || cfg->Ls[l] > 4096) return fail(c, LP_ERR_ARG, "L=%d outside 2..4096", cfg->Ls[l]);
+        for (int m = 0; m < l; ++m)
+            if (cfg->Ls[m] == cfg->Ls[l]) return fail(c, LP_ERR_ARG, "window size %d repeated", cfg->Ls[l]);
+    }
+    if (!(cfg->ratio > 0.f && cfg->ratio <= 1.f)) return fail(c, LP_ERR_ARG, "ratio must be in (0, 1]");
+    if (cfg->ransac_iters < 1 || cfg->ransac_iters > 65536) return fail(c, LP_ERR_ARG, "ransac_iters outside 1..65536");
+    if (!(cfg->thresh_px > 0.f)) return fail(c, LP_ERR_ARG, "thresh_px must be > 0");
+    if (cfg->precision != LP_PREC_FP32 && cfg->precision != LP_PREC_BF16)
+        return fail(c, LP_ERR_ARG, "unknown precision %d", cfg->precision);
+    return LP_OK;
+}
+
+int check_image(lp_ctx* c, const uint8_t* img, int H, int W, int pitch, int ch)
+{
+    if (!img) return fail(c, LP_ERR_ARG, "null image");
+    if (H <= 0 || W <= 0) return fail(c, LP_ERR_ARG, "image %dx%d is empty", W, H);
+    if ((long long)H * W > (1ll << 24)) return fail(c, LP_ERR_UNSUPPORTED, "H*W=%lld above 2^24", (long long)H * W);
+    if (ch != 1 && ch != 3) return fail(c, LP_ERR_ARG, "channels=%d (1 or 3)", ch);
+    if (pitch < W * ch) return fail(c, LP_ERR_ARG, "pitch %d < W*channels %d", pitch, W * ch);
+    if (pitch % 16 || !aligned(img, 16)) return fail(c, LP_ERR_ALIGN, "image base and pitch must be 16-byte aligned");
+    return LP_OK;
+}
+
+cudaStream_t S(void* s) { return static_cast<cudaStream_t>(s); }
+
+}  // namespace
+
+namespace lp {
+
+int make_scale_table(const int* Ls_in, int nL, double beta0, int H, int W, ScaleTable* st)
+{
+    int Ls[LP_MAX_SCALES];
+    for (int l = 0; l < nL; ++l) Ls[l] = Ls_in[l];
+    std::sort(Ls, Ls + nL);
+    const int Lmin = Ls[0], Lmax = Ls[nL - 1];
+    // Eq. 3-4: w_s = beta*L, beta = beta0*(L/Lmax)^(-1/2); the default beta0 is
+    // the largest value that keeps w = 4 w_s <= L for every L
+    if (beta0 <= 0) beta0 = sqrt((double)Lmin / (double)Lmax) / 4.0;
+    st->nL = nL;
+    int64_t off = 0;
+    for (int l = 0; l < nL; ++l) {
+        st->L[l] = Ls[l];
+        const double beta = beta0 * pow((double)Ls[l] / (double)Lmax, -0.5);
+        const int w = (int)floor(beta * Ls[l] + 0.5);
+        st->ws[l] = w < 1 ? 1 : w;
+        st->pr[l] = (int)ceil(2.0 * sqrt(2.0) * st->ws[l]) + 2;
+        st->nwx[l] = W / Ls[l];
+        st->nwy[l] = H / Ls[l];
+        st->off[l] = off;
+        off += 2ll * st->nwx[l] * st->nwy[l];
+    }
+    st->off[nL] = off;
+    return LP_OK;
+}
+
+}  // namespace lp
+
+extern "C" {
+
+int lp_config_default(lp_config* cfg)
+{
+    if (!cfg) return LP_ERR_ARG;
+    memset(cfg, 0, sizeof *cfg);
+    cfg->nL = 4;
+    cfg->Ls[0] = 16; cfg->Ls[1] = 32; cfg->Ls[2] = 64; cfg->Ls[3] = 128;
+    cfg->beta0 = 0.0;
+    cfg->ratio = 0.8f;
+    cfg->delta_s = INFINITY;
+    cfg->ransac_iters = 1000;
+    cfg->thresh_px = 3.0f;
+    cfg->seed = 0;
+    cfg->min_inliers = 8;
+    cfg->precision = LP_PREC_FP32;
+    cfg->upright = 0;
+    return LP_OK;
+}
+
+int lp_create(lp_ctx** out, const lp_config* cfg)
+{
+    if (!out) return LP_ERR_ARG;
+    *out = nullptr;
+    lp_ctx* c = new lp_ctx();
+    c->err[0] = 0;
+    int r = check_cfg(c, cfg);
+    if (r) { delete c; return r; }
+    c->cfg = *cfg;
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_status, sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(int32_t));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (c->d_status) cudaFree(c->d_status);
+        delete c;
+        return LP_ERR_CUDA;
+    }
+    *out = c;
+    return LP_OK;
+}
+
+int lp_destroy(lp_ctx* c)
+{
+    if (!c) return LP_ERR_ARG;
+    cudaDeviceSynchronize();
+    for (auto& b : c->buf)
+        if (b.p) cudaFree(b.p);
+    if (c->d_status) cudaFree(c->d_status);
+    delete c;
+    return LP_OK;
+}
+
+int64_t lp_num_keypoints(int H, int W, const int* Ls, int nL)
+{
+    if (!Ls || nL < 1 || H < 0 || W < 0) return -1;
+    int64_t K = 0;
+    for (int l = 0; l < nL; ++l) {
+        if (Ls[l] < 2) return -1;
+        K += 2ll * (H / Ls[l]) * (W / Ls[l]);
+    }
+    return K;
+}
+
+int lp_detect(lp_ctx* c, const uint8_t* img, int H, int W, int pitch, int channels, uint32_t* kp_idx,
+              uint8_t* gray, void* stream)
+{
+    if (!c) return LP_ERR_ARG;
+    int r = check_image(c, img, H, W, pitch, channels);
+    if (r) return r;
+    const int64_t K = lp_num_keypoints(H, W, c->cfg.Ls, c->cfg.nL);
+    if (K > 0 && !kp_idx) return fail(c, LP_ERR_ARG, "null kp_idx");
+    if (kp_idx && !aligned(kp_idx, 8)) return fail(c, LP_ERR_ALIGN, "kp_idx must be 8-byte aligned");
+    if (channels == 3 && !gray) return fail(c, LP_ERR_ARG, "RGB input needs the gray output buffer");
+    if (channels == 3 && (W % 16 == 0) && !aligned(gray, 16)) return fail(c, LP_ERR_ALIGN, "gray must be 16-byte aligned");
+    lp::ScaleTable st;
+    lp::make_scale_table(c->cfg.Ls, c->cfg.nL, c->cfg.beta0, H, W, &st);
+    c->last = S(stream);
+    LP_CUDA(c, lp::launch_detect(img, H, W, pitch, channels, st, kp_idx, gray, S(stream)));
+    return LP_OK;
+}
+
+int lp_describe(lp_ctx* c, const uint8_t* gray, int H, int W, int gray_pitch, const uint32_t* kp_idx, int64_t K,
+                uint8_t* ori, float* desc, uint16_t* desc_bf16, uint8_t* valid, void* stream)
+{
+    if (!c) return LP_ERR_ARG;
+    if (!gray || H <= 0 || W <= 0 || gray_pitch < W) return fail(c, LP_ERR_ARG, "bad intensity image");
+    if ((long long)H * W > (1ll << 24)) return fail(c, LP_ERR_UNSUPPORTED, "H*W above 2^24");
+    const int64_t Kexp = lp_num_keypoints(H, W, c->cfg.Ls, c->cfg.nL);
+    if (K != Kexp) return fail(c, LP_ERR_ARG, "K=%lld but the image has %lld feature points", (long long)K, (long long)Kexp);
+    if (K == 0) return LP_OK;
+    if (!kp_idx || !ori || !desc || !valid) return fail(c, LP_ERR_ARG, "null output");
+    if (!aligned(desc, 16) || (desc_bf16 && !aligned(desc_bf16, 8))) return fail(c, LP_ERR_ALIGN, "descriptor alignment");
+    lp::ScaleTable st;
+    lp::make_scale_table(c->cfg.Ls, c->cfg.nL, c->cfg.beta0, H, W, &st);
+    c->last = S(stream);
+    LP_CUDA(c, lp::launch_describe(gray, H, W, gray_pitch, kp_idx, st, c->cfg.upright, ori, desc, desc_bf16, valid,
+                                   S(stream)));
+    return LP_OK;
+}
+
+int lp_match(lp_ctx* c, const float* dA, const uint16_t* dA_bf16, const uint8_t* vA, int64_t NA, const float* dB,
+             const uint16_t* dB_bf16, const uint8_t* vB, int64_t NB, int32_t* match, float* d1, float* d2,
+             void* stream)
+{
+    if (!c) return LP_ERR_ARG;
+    if (NA < 0 || NB < 0 || NA > (1ll << 31) - 1 || NB > (1ll << 31) - 1) return fail(c, LP_ERR_ARG, "bad sizes");
+    if (NA == 0) return LP_OK;
+    if (!dA || !vA || !match || !d1 || !d2 || (NB > 0 && (!dB || !vB))) return fail(c, LP_ERR_ARG, "null argument");
+    if (!aligned(dA, 16) || (dB && !aligned(dB, 16))) return fail(c, LP_ERR_ALIGN, "descriptors must be 16-byte aligned");
+    lp::MatchArgs a;
+    a.dA = dA; a.dA16 = dA_bf16; a.vA = vA; a.NA = NA;
+    a.dB = dB; a.dB16 = dB_bf16; a.vB = vB; a.NB = NB;
+    a.ratio2 = (float)((double)c->cfg.ratio * (double)c->cfg.ratio);
+    const bool ds = c->cfg.delta_s > 0.f && isfinite(c->cfg.delta_s);
+    a.delta_s2 = ds ? (float)((double)c->cfg.delta_s * (double)c->cfg.delta_s) : INFINITY;
+    a.match = match; a.d1 = d1; a.d2 = d2; a.status = c->d_status;
+    c->last = S(stream);
+    if (c->cfg.precision == LP_PREC_BF16) {
+        if (!dA_bf16 || (NB > 0 && !dB_bf16)) return fail(c, LP_ERR_ARG, "BF16 matching needs the bf16 descriptors");
+        if (!aligned(dA_bf16, 16) || (dB_bf16 && !aligned(dB_bf16, 16))) return fail(c, LP_ERR_ALIGN, "bf16 alignment");
+        int r = ensure(c, B_MATCH_WS, lp::match_bf16_workspace(NA, NB, c->num_sms));
+        if (r) return r;
+        LP_CUDA(c, lp::launch_match_bf16(a, c->buf[B_MATCH_WS].p, c->buf[B_MATCH_WS].n, c->num_sms, S(stream)));
+        return LP_OK;
+    }
+    int r = ensure(c, B_MATCH_WS, lp::match_fp32_workspace(NA, NB, c->num_sms));
+    if (r) return r;
+    LP_CUDA(c, lp::launch_match_fp32(a, c->buf[B_MATCH_WS].p, c->buf[B_MATCH_WS].n, c->num_sms, S(stream)));
+    return LP_OK;
+}
+
+int lp_compact(lp_ctx* c, const uint32_t* kpA, int WA, const uint32_t* kpB, int WB, const int32_t* match, int64_t NA,
+               float* pts, int32_t* rows, int32_t* d_M, void* stream)
+{
+    if (!c) return LP_ERR_ARG;
+    if (NA < 0 || WA <= 0 || WB <= 0) return fail(c, LP_ERR_ARG, "bad sizes");
+    if (!d_M || (NA > 0 && (!kpA || !kpB || !match || !pts))) return fail(c, LP_ERR_ARG, "null argument");
+    if (pts && !aligned(pts, 16)) return fail(c, LP_ERR_ALIGN, "pts must be 16-byte aligned");
+    c->last = S(stream);
+    LP_CUDA(c, lp::launch_compact(kpA, WA, kpB, WB, match, NA, pts, rows, d_M, S(stream)));
+    return LP_OK;
+}
+
+int lp_ransac(lp_ctx* c, const float* pts, int64_t M_cap, const int32_t* d_M, uint32_t pair_id, double* H,
+              uint8_t* inlier, int32_t* n_inliers, int32_t* best_t, void* stream)
+{
+    if (!c) return LP_ERR_ARG;
+    if (M_cap < 0 || M_cap > (1ll << 31) - 1) return fail(c, LP_ERR_ARG, "bad M_cap");
+    if (!H || !n_inliers || (M_cap > 0 && (!pts || !inlier))) return fail(c, LP_ERR_ARG, "null argument");
+    if (pts && !aligned(pts, 16)) return fail(c, LP_ERR_ALIGN, "pts must be 16-byte aligned");
+    const int T = c->cfg.ransac_iters;
+    int r = ensure(c, B_RANSAC_WS, lp::ransac_workspace(M_cap, T));
+    if (r) return r;
+    c->last = S(stream);
+    LP_CUDA(c, lp::launch_ransac(pts, M_cap, d_M, T, c->cfg.thresh_px, c->cfg.seed, pair_id, H, inlier, n_inliers,
+                                 best_t, c->buf[B_RANSAC_WS].p, c->buf[B_RANSAC_WS].n, c->d_status, S(stream)));
+    return LP_OK;
+}
+
+int lp_stitch_pair(lp_ctx* c, const uint8_t* imgA, int HA, int WA, int pitchA, const uint8_t* imgB, int HB, int WB,
+                   int pitchB, int channels, uint32_t pair_id, double* H, int32_t* n_in, int32_t* M_out, void* stream)
+{
+    if (!c) return LP_ERR_ARG;
+    int r = check_image(c, imgA, HA, WA, pitchA, channels);
+    if (!r) r = check_image(c, imgB, HB, WB, pitchB, channels);
+    if (r) return r;
+    if (!H || !n_in) return fail(c, LP_ERR_ARG, "null output");
+    const int64_t KA = lp_num_keypoints(HA, WA, c->cfg.Ls, c->cfg.nL);
+    const int64_t KB = lp_num_keypoints(HB, WB, c->cfg.Ls, c->cfg.nL);
+    const bool bf = c->cfg.precision == LP_PREC_BF16;
+    struct { BufId id; size_t n; } need[] = {
+        {B_GRAY_A, channels == 3 ? (size_t)HA * WA + 16 : 0}, {B_GRAY_B, channels == 3 ? (size_t)HB * WB + 16 : 0},
+        {B_KP_A, 4 * (size_t)KA}, {B_KP_B, 4 * (size_t)KB}, {B_ORI_A, (size_t)KA}, {B_ORI_B, (size_t)KB},
+        {B_DESC_A, 512 * (size_t)KA}, {B_DESC_B, 512 * (size_t)KB},
+        {B_D16_A, bf ? 256 * (size_t)KA : 0}, {B_D16_B, bf ? 256 * (size_t)KB : 0},
+        {B_VAL_A, (size_t)KA}, {B_VAL_B, (size_t)KB}, {B_MATCH, 4 * (size_t)KA}, {B_D1, 4 * (size_t)KA},
+        {B_D2, 4 * (size_t)KA}, {B_PTS, 16 * (size_t)KA}, {B_M, 16}, {B_INL, (size_t)KA}, {B_BEST, 16}};
+    for (auto& q : need)
+        if (q.n && (r = ensure(c, q.id, q.n))) return r;
+    auto P = [&](BufId id) { return c->buf[id].p; };
+    const uint8_t* gA = channels == 3 ? (const uint8_t*)P(B_GRAY_A) : imgA;
+    const uint8_t* gB = channels == 3 ? (const uint8_t*)P(B_GRAY_B) : imgB;
+    const int gpA = channels == 3 ? WA : pitchA, gpB = channels == 3 ? WB : pitchB;
+    if ((r = lp_detect(c, imgA, HA, WA, pitchA, channels, (uint32_t*)P(B_KP_A), (uint8_t*)P(B_GRAY_A), stream))) return r;
+    if ((r = lp_detect(c, imgB, HB, WB, pitchB, channels, (uint32_t*)P(B_KP_B), (uint8_t*)P(B_GRAY_B), stream))) return r;
+    if ((r = lp_describe(c, gA, HA, WA, gpA, (const uint32_t*)P(B_KP_A), KA, (uint8_t*)P(B_ORI_A), (float*)P(B_DESC_A),
+                         bf ? (uint16_t*)P(B_D16_A) : nullptr, (uint8_t*)P(B_VAL_A), stream)))
+        return r;
+    if ((r = lp_describe(c, gB, HB, WB, gpB, (const uint32_t*)P(B_KP_B), KB, (uint8_t*)P(B_ORI_B), (float*)P(B_DESC_B),
+                         bf ? (uint16_t*)P(B_D16_B) : nullptr, (uint8_t*)P(B_VAL_B), stream)))
+        return r;
+    if ((r = lp_match(c, (const float*)P(B_DESC_A), (const uint16_t*)P(B_D16_A), (const uint8_t*)P(B_VAL_A), KA,
+                      (const float*)P(B_DESC_B), (const uint16_t*)P(B_D16_B), (const uint8_t*)P(B_VAL_B), KB,
+                      (int32_t*)P(B_MATCH), (float*)P(B_D1), (float*)P(B_D2), stream)))
+        return r;
+    int32_t* dM = M_out ? M_out : (int32_t*)P(B_M);
+    if (KA == 0) {
+        LP_CUDA(c, cudaMemsetAsync(dM, 0, sizeof(int32_t), S(stream)));
+    } else if ((r = lp_compact(c, (const uint32_t*)P(B_KP_A), WA, (const uint32_t*)P(B_KP_B), WB,
+                               (const int32_t*)P(B_MATCH), KA, (float*)P(B_PTS), nullptr, dM, stream))) {
+        return r;
+    }
+    return lp_ransac(c, (const float*)P(B_PTS), KA, dM, pair_id, H, (uint8_t*)P(B_INL), n_in, nullptr, stream);
+}
+
+int lp_stitch_pair_host(lp_ctx* c, const uint8_t* hA, int HA, int WA, int pitchA, const uint8_t* hB, int HB, int WB,
+                        int pitchB, int channels, uint32_t pair_id, double* H_host, int32_t* n_in_host,
+                        int32_t* M_host, void* stream)
+{
+    if (!c) return LP_ERR_ARG;
+    if (!hA || !hB || !H_host || !n_in_host) return fail(c, LP_ERR_ARG, "null argument");
+    if (HA <= 0 || HB <= 0 || pitchA % 16 || pitchB % 16) return fail(c, LP_ERR_ALIGN, "pitch must be a multiple of 16");
+    int r;
+    const size_t nA = (size_t)HA * pitchA, nB = (size_t)HB * pitchB;
+    if ((r = ensure(c, B_IMG_A, nA)) || (r = ensure(c, B_IMG_B, nB)) || (r = ensure(c, B_H, 128)) ||
+        (r = ensure(c, B_NIN, 64)))
+        return r;
+    cudaStream_t s = S(stream);
+    c->last = s;
+    LP_CUDA(c, cudaMemcpyAsync(c->buf[B_IMG_A].p, hA, nA, cudaMemcpyHostToDevice, s));
+    LP_CUDA(c, cudaMemcpyAsync(c->buf[B_IMG_B].p, hB, nB, cudaMemcpyHostToDevice, s));
+    double* dH = (double*)c->buf[B_H].p;
+    int32_t* dn = (int32_t*)c->buf[B_NIN].p;
+    if ((r = lp_stitch_pair(c, (const uint8_t*)c->buf[B_IMG_A].p, HA, WA, pitchA, (const uint8_t*)c->buf[B_IMG_B].p,
+                            HB, WB, pitchB, channels, pair_id, dH, dn, dn + 1, stream)))
+        return r;
+    int32_t tmp[2];
+    LP_CUDA(c, cudaMemcpyAsync(H_host, dH, 9 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    LP_CUDA(c, cudaMemcpyAsync(tmp, dn, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    LP_CUDA(c, cudaStreamSynchronize(s));
+    *n_in_host = tmp[0];
+    if (M_host) *M_host = tmp[1];
+    return LP_OK;
+}
+
+int lp_sync_status(lp_ctx* c)
+{
+    if (!c) return LP_ERR_ARG;
+    if (c->last) LP_CUDA(c, cudaStreamSynchronize(c->last));
+    else LP_CUDA(c, cudaDeviceSynchronize());
+    int32_t st = 0;
+    LP_CUDA(c, cudaMemcpy(&st, c->d_status, sizeof st, cudaMemcpyDeviceToHost));
+    LP_CUDA(c, cudaMemset(c->d_status, 0, sizeof st));
+    return st;
+}
+
+const char* lp_last_error(lp_ctx* c) { return c ? c->err : "null context"; }
+
+int lp_diag_orient_bins(int32_t* out, void* stream)
+{
+    if (!out) return LP_ERR_ARG;
+    return lp::launch_diag_orient(out, nullptr, S(stream)) == cudaSuccess ? LP_OK : LP_ERR_CUDA;
+}
+
+int lp_diag_orient_weights(uint32_t* out, void* stream)
+{
+    if (!out) return LP_ERR_ARG;
+    return lp::launch_diag_orient(nullptr, out, S(stream)) == cudaSuccess ? LP_OK : LP_ERR_CUDA;
+}
+
+int lp_diag_philox(const uint32_t* ctr, int64_t n, uint32_t key0, uint32_t key1, uint32_t* out, void* stream)
+{
+    if ((n > 0 && (!ctr || !out)) || n < 0) return LP_ERR_ARG;
+    if (!aligned(ctr, 16) || !aligned(out, 16)) return LP_ERR_ALIGN;
+    return lp::launch_diag_philox(ctr, n, key0, key1, out, S(stream)) == cudaSuccess ? LP_OK : LP_ERR_CUDA;
+}
+
+int lp_diag_gray(const uint8_t* rgb, int64_t n, uint8_t* gray, void* stream)
+{
+    if (n < 0 || (n > 0 && (!rgb || !gray))) return LP_ERR_ARG;
+    if (n == 0) return LP_OK;
+    return lp::launch_diag_gray(rgb, n, gray, S(stream)) == cudaSuccess ? LP_OK : LP_ERR_CUDA;
+}
+
+}  // extern "C"

@@ -1,0 +1,68 @@
+// Internal declarations of liblp (GB300 / sm_103a).  Not part of the C ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lp.h"
+
+namespace lp {
+
+// ---- device status word (written by kernels, read by lp_sync_status) ----
+enum : int32_t { DEV_OK = 0, DEV_TIMEOUT = 4, DEV_INCONSISTENT = 8 };
+
+__device__ __forceinline__ void set_status(int32_t* st, int32_t code)
+{
+    if (st) atomicCAS(st, 0, code);
+}
+
+// ---- scale table: canonical keypoint ranges per window size ----
+struct ScaleTable {
+    int nL;
+    int L[LP_MAX_SCALES];        // ascending
+    int ws[LP_MAX_SCALES];       // sub-region side w_s (Eq. 3-4)
+    int pr[LP_MAX_SCALES];       // patch radius for the describe kernel
+    int nwx[LP_MAX_SCALES];      // windows per row
+    int nwy[LP_MAX_SCALES];
+    int64_t off[LP_MAX_SCALES + 1];  // first keypoint of each scale; off[nL] = K
+};
+
+// Host-side construction (lp_api.cu).
+int make_scale_table(const int* Ls, int nL, double beta0, int H, int W, ScaleTable* st);
+
+// ---- kernel launchers (each .cu file owns its kernels) ----
+// k_detect.cu
+cudaError_t launch_detect(const uint8_t* img, int H, int W, int pitch, int ch, const ScaleTable& st,
+                          uint32_t* kp, uint8_t* gray, cudaStream_t s);
+cudaError_t launch_diag_gray(const uint8_t* rgb, int64_t n, uint8_t* gray, cudaStream_t s);
+
+// k_describe.cu
+cudaError_t launch_describe(const uint8_t* gray, int H, int W, int pitch, const uint32_t* kp,
+                            const ScaleTable& st, int upright, uint8_t* ori, float* desc,
+                            uint16_t* desc_bf16, uint8_t* valid, cudaStream_t s);
+cudaError_t launch_diag_orient(int32_t* bins, uint32_t* weights, cudaStream_t s);
+
+// k_match.cu
+struct MatchArgs {
+    const float* dA; const uint16_t* dA16; const uint8_t* vA; int64_t NA;
+    const float* dB; const uint16_t* dB16; const uint8_t* vB; int64_t NB;
+    float ratio2;        // ratio^2
+    float delta_s2;      // Delta_s^2 or +inf
+    int32_t* match; float* d1; float* d2;
+    int32_t* status;
+};
+size_t match_fp32_workspace(int64_t NA, int64_t NB, int num_sms);
+cudaError_t launch_match_fp32(const MatchArgs& a, void* ws, size_t ws_bytes, int num_sms, cudaStream_t s);
+size_t match_bf16_workspace(int64_t NA, int64_t NB, int num_sms);
+cudaError_t launch_match_bf16(const MatchArgs& a, void* ws, size_t ws_bytes, int num_sms, cudaStream_t s);
+
+// k_ransac.cu
+cudaError_t launch_compact(const uint32_t* kpA, int WA, const uint32_t* kpB, int WB, const int32_t* match,
+                           int64_t NA, float* pts, int32_t* rows, int32_t* d_M, cudaStream_t s);
+size_t ransac_workspace(int64_t M_cap, int T);
+cudaError_t launch_ransac(const float* pts, int64_t M_cap, const int32_t* d_M, int T, float thresh,
+                          uint64_t seed, uint32_t pair_id, double* H, uint8_t* inlier, int32_t* n_in,
+                          int32_t* best_t, void* ws, size_t ws_bytes, int32_t* status, cudaStream_t s);
+cudaError_t launch_diag_philox(const uint32_t* ctr, int64_t n, uint32_t k0, uint32_t k1, uint32_t* out,
+                               cudaStream_t s);
+
+}  // namespace lp

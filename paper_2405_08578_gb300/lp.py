@@ -1,0 +1,272 @@
+"""ctypes binding of liblp (include/lp.h).  Argument marshalling only.
+
+Every function has the C name and takes torch tensors where the C call takes
+device pointers; the current torch CUDA stream is passed as ``stream``.  No
+step of the method runs here: a missing or unloadable library raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+
+import torch
+
+from . import build as _build
+
+LP_OK = 0
+ERR_NAMES = {0: "LP_OK", 1: "LP_ERR_ARG", 2: "LP_ERR_ALIGN", 3: "LP_ERR_CUDA", 4: "LP_ERR_TIMEOUT",
+             5: "LP_ERR_NOMEM", 6: "LP_ERR_DEGENERATE", 7: "LP_ERR_UNSUPPORTED", 8: "LP_ERR_DEVICE"}
+PREC_FP32, PREC_BF16 = 0, 1
+MAX_SCALES = 8
+
+
+class LpError(RuntimeError):
+    def __init__(self, code, msg=""):
+        super().__init__(f"{ERR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class lp_config(C.Structure):
+    _fields_ = [("nL", C.c_int32), ("Ls", C.c_int32 * MAX_SCALES), ("beta0", C.c_double), ("ratio", C.c_float),
+                ("delta_s", C.c_float), ("ransac_iters", C.c_int32), ("thresh_px", C.c_float),
+                ("seed", C.c_uint64), ("min_inliers", C.c_int32), ("precision", C.c_int32),
+                ("upright", C.c_int32)]
+
+
+_lib = None
+SYMBOLS = ["lp_config_default", "lp_create", "lp_destroy", "lp_num_keypoints", "lp_detect", "lp_describe",
+           "lp_match", "lp_compact", "lp_ransac", "lp_stitch_pair", "lp_stitch_pair_host", "lp_sync_status",
+           "lp_last_error", "lp_diag_orient_bins", "lp_diag_orient_weights", "lp_diag_philox", "lp_diag_gray"]
+
+
+def lib_path() -> str:
+    return _build.OUT
+
+
+def load(build_if_missing: bool = True):
+    """Load liblp.so (building it first when it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing:
+        _build.build()
+    if not os.path.exists(_build.OUT):
+        raise RuntimeError(f"liblp.so not built at {_build.OUT}")
+    L = C.CDLL(_build.OUT)
+    P, i32, i64, u32 = C.c_void_p, C.c_int, C.c_int64, C.c_uint32
+    sig = {
+        "lp_config_default": (i32, [C.POINTER(lp_config)]),
+        "lp_create": (i32, [C.POINTER(P), C.POINTER(lp_config)]),
+        "lp_destroy": (i32, [P]),
+        "lp_num_keypoints": (i64, [i32, i32, P, i32]),
+        "lp_detect": (i32, [P, P, i32, i32, i32, i32, P, P, P]),
+        "lp_describe": (i32, [P, P, i32, i32, i32, P, i64, P, P, P, P, P]),
+        "lp_match": (i32, [P, P, P, P, i64, P, P, P, i64, P, P, P, P]),
+        "lp_compact": (i32, [P, P, i32, P, i32, P, i64, P, P, P, P]),
+        "lp_ransac": (i32, [P, P, i64, P, u32, P, P, P, P, P]),
+        "lp_stitch_pair": (i32, [P, P, i32, i32, i32, P, i32, i32, i32, i32, u32, P, P, P, P]),
+        "lp_stitch_pair_host": (i32, [P, P, i32, i32, i32, P, i32, i32, i32, i32, u32, P, P, P, P]),
+        "lp_sync_status": (i32, [P]),
+        "lp_last_error": (C.c_char_p, [P]),
+        "lp_diag_orient_bins": (i32, [P, P]),
+        "lp_diag_orient_weights": (i32, [P, P]),
+        "lp_diag_philox": (i32, [P, i64, u32, u32, P, P]),
+        "lp_diag_gray": (i32, [P, i64, P, P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if not t.is_cuda:
+        raise ValueError("liblp takes device tensors")
+    return t.data_ptr()
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def config(Ls=(16, 32, 64, 128), beta0=0.0, ratio=0.8, delta_s=math.inf, ransac_iters=1000, thresh_px=3.0,
+           seed=0, min_inliers=8, precision=PREC_FP32, upright=False) -> lp_config:
+    c = lp_config()
+    load().lp_config_default(C.byref(c))
+    Ls = list(Ls)
+    if not 1 <= len(Ls) <= MAX_SCALES:
+        raise ValueError("1..8 window sizes")
+    c.nL = len(Ls)
+    for i, L in enumerate(Ls):
+        c.Ls[i] = int(L)
+    c.beta0, c.ratio, c.delta_s = float(beta0), float(ratio), float(delta_s)
+    c.ransac_iters, c.thresh_px, c.seed = int(ransac_iters), float(thresh_px), int(seed)
+    c.min_inliers, c.precision, c.upright = int(min_inliers), int(precision), int(bool(upright))
+    return c
+
+
+class Context:
+    """Owns an lp_ctx (config copy, status word, workspace)."""
+
+    def __init__(self, cfg: lp_config | None = None, **kw):
+        self.lib = load()
+        self.cfg = cfg if cfg is not None else config(**kw)
+        h = C.c_void_p()
+        r = self.lib.lp_create(C.byref(h), C.byref(self.cfg))
+        if r != LP_OK:
+            raise LpError(r, "lp_create")
+        self.h = h
+
+    @property
+    def Ls(self):
+        return [self.cfg.Ls[i] for i in range(self.cfg.nL)]
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.lp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _chk(self, r, what):
+        if r != LP_OK:
+            raise LpError(r, f"{what}: {self.lib.lp_last_error(self.h).decode(errors='replace')}")
+
+    # ---- the C entry points, same names ----
+    def lp_detect(self, img, H, W, pitch, channels, kp_idx, gray=None, stream=None):
+        self._chk(self.lib.lp_detect(self.h, _ptr(img), H, W, pitch, channels, _ptr(kp_idx), _ptr(gray),
+                                     _stream(stream)), "lp_detect")
+
+    def lp_describe(self, gray, H, W, gray_pitch, kp_idx, K, ori, desc, desc_bf16, valid, stream=None):
+        self._chk(self.lib.lp_describe(self.h, _ptr(gray), H, W, gray_pitch, _ptr(kp_idx), K, _ptr(ori), _ptr(desc),
+                                       _ptr(desc_bf16), _ptr(valid), _stream(stream)), "lp_describe")
+
+    def lp_match(self, dA, dA16, vA, NA, dB, dB16, vB, NB, match, d1, d2, stream=None):
+        self._chk(self.lib.lp_match(self.h, _ptr(dA), _ptr(dA16), _ptr(vA), NA, _ptr(dB), _ptr(dB16), _ptr(vB), NB,
+                                    _ptr(match), _ptr(d1), _ptr(d2), _stream(stream)), "lp_match")
+
+    def lp_compact(self, kpA, WA, kpB, WB, match, NA, pts, rows, d_M, stream=None):
+        self._chk(self.lib.lp_compact(self.h, _ptr(kpA), WA, _ptr(kpB), WB, _ptr(match), NA, _ptr(pts), _ptr(rows),
+                                      _ptr(d_M), _stream(stream)), "lp_compact")
+
+    def lp_ransac(self, pts, M_cap, d_M, pair_id, H, inlier, n_inliers, best_t=None, stream=None):
+        self._chk(self.lib.lp_ransac(self.h, _ptr(pts), M_cap, _ptr(d_M), pair_id, _ptr(H), _ptr(inlier),
+                                     _ptr(n_inliers), _ptr(best_t), _stream(stream)), "lp_ransac")
+
+    def lp_stitch_pair(self, imgA, HA, WA, pitchA, imgB, HB, WB, pitchB, channels, pair_id, H, n_in, M_out=None,
+                       stream=None):
+        self._chk(self.lib.lp_stitch_pair(self.h, _ptr(imgA), HA, WA, pitchA, _ptr(imgB), HB, WB, pitchB, channels,
+                                          pair_id, _ptr(H), _ptr(n_in), _ptr(M_out), _stream(stream)),
+                  "lp_stitch_pair")
+
+    def lp_stitch_pair_host(self, imgA, HA, WA, pitchA, imgB, HB, WB, pitchB, channels, pair_id, stream=None):
+        """imgA/imgB: host (ideally pinned) uint8 tensors.  Returns (H 3x3 float64, n_in, M)."""
+        Hh = (C.c_double * 9)()
+        n = C.c_int32()
+        m = C.c_int32()
+        self._chk(self.lib.lp_stitch_pair_host(self.h, imgA.data_ptr(), HA, WA, pitchA, imgB.data_ptr(), HB, WB,
+                                               pitchB, channels, pair_id, Hh, C.byref(n), C.byref(m),
+                                               _stream(stream)), "lp_stitch_pair_host")
+        return [list(Hh[0:3]), list(Hh[3:6]), list(Hh[6:9])], n.value, m.value
+
+    def lp_sync_status(self):
+        return self.lib.lp_sync_status(self.h)
+
+
+def lp_num_keypoints(H, W, Ls) -> int:
+    arr = (C.c_int * len(Ls))(*[int(v) for v in Ls])
+    return int(load().lp_num_keypoints(H, W, C.cast(arr, C.c_void_p), len(Ls)))
+
+
+def _diag(name, *args):
+    r = getattr(load(), name)(*args)
+    if r != LP_OK:
+        raise LpError(r, name)
+
+
+def lp_diag_orient_bins(out, stream=None):
+    _diag("lp_diag_orient_bins", _ptr(out), _stream(stream))
+
+
+def lp_diag_orient_weights(out, stream=None):
+    _diag("lp_diag_orient_weights", _ptr(out), _stream(stream))
+
+
+def lp_diag_philox(ctr, n, key0, key1, out, stream=None):
+    _diag("lp_diag_philox", _ptr(ctr), n, key0, key1, _ptr(out), _stream(stream))
+
+
+def lp_diag_gray(rgb, n, gray, stream=None):
+    _diag("lp_diag_gray", _ptr(rgb), n, _ptr(gray), _stream(stream))
+
+
+# ---------------------------------------------------------------------------
+# Convenience layer: whole-image / whole-pair calls on torch tensors.
+# ---------------------------------------------------------------------------
+def pitched_device(img) -> tuple[torch.Tensor, int]:
+    """(H, W) or (H, W, 3) uint8 array/tensor -> device buffer with a 16-byte row pitch."""
+    t = torch.as_tensor(img)
+    H = t.shape[0]
+    row = t.shape[1] * (t.shape[2] if t.dim() == 3 else 1)
+    pitch = (row + 15) // 16 * 16
+    buf = torch.zeros((H, pitch), dtype=torch.uint8, device="cuda")
+    buf[:, :row] = t.reshape(H, row).to("cuda")
+    return buf, pitch
+
+
+class Features:
+    def __init__(self, gray, H, W, gpitch, kp, ori, desc, desc16, valid):
+        self.gray, self.H, self.W, self.gpitch = gray, H, W, gpitch
+        self.kp, self.ori, self.desc, self.desc16, self.valid = kp, ori, desc, desc16, valid
+
+
+def features(ctx: Context, img, stream=None) -> Features:
+    """lp_detect + lp_describe for one image (numpy or tensor, gray or RGB)."""
+    buf, pitch = pitched_device(img)
+    H, W = int(buf.shape[0]), int(torch.as_tensor(img).shape[1])
+    ch = 3 if torch.as_tensor(img).dim() == 3 else 1
+    K = lp_num_keypoints(H, W, ctx.Ls)
+    dev = "cuda"
+    kp = torch.empty(max(K, 1), dtype=torch.int32, device=dev)
+    gray = torch.empty(H * W + 16, dtype=torch.uint8, device=dev) if ch == 3 else None
+    ctx.lp_detect(buf, H, W, pitch, ch, kp, gray, stream)
+    g, gp = (gray, W) if ch == 3 else (buf, pitch)
+    ori = torch.empty(max(K, 1), dtype=torch.uint8, device=dev)
+    desc = torch.empty((max(K, 1), 128), dtype=torch.float32, device=dev)
+    bf = ctx.cfg.precision == PREC_BF16
+    desc16 = torch.empty((max(K, 1), 128), dtype=torch.bfloat16, device=dev) if bf else None
+    valid = torch.empty(max(K, 1), dtype=torch.uint8, device=dev)
+    ctx.lp_describe(g, H, W, gp, kp, K, ori, desc, desc16, valid, stream)
+    return Features(g, H, W, gp, kp[:K], ori[:K], desc[:K], None if desc16 is None else desc16[:K], valid[:K])
+
+
+def match(ctx: Context, fa: Features, fb: Features, stream=None):
+    NA, NB = fa.desc.shape[0], fb.desc.shape[0]
+    m = torch.empty(max(NA, 1), dtype=torch.int32, device="cuda")
+    d1 = torch.empty(max(NA, 1), dtype=torch.float32, device="cuda")
+    d2 = torch.empty(max(NA, 1), dtype=torch.float32, device="cuda")
+    ctx.lp_match(fa.desc, fa.desc16, fa.valid, NA, fb.desc, fb.desc16, fb.valid, NB, m, d1, d2, stream)
+    return m[:NA], d1[:NA], d2[:NA]
+
+
+def ransac(ctx: Context, pts: torch.Tensor, pair_id: int = 0, d_M=None, stream=None):
+    M = pts.shape[0]
+    H = torch.empty(9, dtype=torch.float64, device="cuda")
+    inl = torch.empty(max(M, 1), dtype=torch.uint8, device="cuda")
+    n = torch.empty(1, dtype=torch.int32, device="cuda")
+    bt = torch.empty(1, dtype=torch.int32, device="cuda")
+    p = pts if M > 0 else torch.zeros((1, 4), dtype=torch.float32, device="cuda")
+    ctx.lp_ransac(p, M, d_M, pair_id, H, inl, n, bt, stream)
+    return H.view(3, 3), inl[:M], n, bt
