@@ -161,6 +161,34 @@ LP_API int lp_compact(lp_ctx* ctx, const uint32_t* kpA, int WA, const uint32_t* 
 LP_API int lp_ransac(lp_ctx* ctx, const float* pts, int64_t M_cap, const int32_t* d_M, uint32_t pair_id,
               double* H, uint8_t* inlier, int32_t* n_inliers, int32_t* best_t, void* stream);
 
+/* lp_ransac for callers that cannot allocate device memory.  The paper has
+ * no counterpart; this is a deployment variant of the same stage.
+ *
+ * Who needs it: code that may not call cudaMalloc -- a host application whose
+ * own caching allocator already holds the device's memory, a real-time loop
+ * that must not enter the driver's allocation path (it can synchronise the
+ * device and take unbounded time), or a plug-in host that forbids device
+ * allocations after start-up.  This call needs no lp_ctx (creating one
+ * allocates) and allocates nothing: its scratch is a fixed 384 KiB array
+ * compiled into the library, resident on every GPU that loads the library
+ * until the process exits.
+ *
+ * Arguments are those of lp_ransac, with the configuration values passed
+ * directly: iters = T (1..LP_RANSAC_STATIC_MAX_ITERS; more returns
+ * LP_ERR_ARG), thresh_px, seed and pair_id.  The results equal lp_ransac's for
+ * the same inputs and configuration.
+ *
+ * The first call on each device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  All calls share the one array, which keeps the last call's
+ * contents: calls that overlap on the GPU (different streams, or host threads
+ * without ordering) race on it and must be serialised by the caller.
+ * Errors: LP_ERR_ARG, LP_ERR_ALIGN, LP_ERR_CUDA. */
+#define LP_RANSAC_STATIC_MAX_ITERS 4096
+LP_API int lp_ransac_static(const float* pts, int64_t M_cap, const int32_t* d_M, int iters, float thresh_px,
+                            uint64_t seed, uint32_t pair_id, double* H, uint8_t* inlier, int32_t* n_inliers,
+                            int32_t* best_t, void* stream);
+
 /* The whole Sec. 2 path for one image pair held on the device: detect,
  * describe, match, compact and RANSAC, with every intermediate in the
  * context's workspace.  imgA/imgB as in lp_detect (same channels).

@@ -36,7 +36,7 @@ class lp_config(C.Structure):
 
 _lib = None
 SYMBOLS = ["lp_config_default", "lp_create", "lp_destroy", "lp_num_keypoints", "lp_detect", "lp_describe",
-           "lp_match", "lp_compact", "lp_ransac", "lp_stitch_pair", "lp_stitch_pair_host", "lp_sync_status",
+           "lp_match", "lp_compact", "lp_ransac", "lp_ransac_static", "lp_stitch_pair", "lp_stitch_pair_host", "lp_sync_status",
            "lp_last_error", "lp_diag_orient_bins", "lp_diag_orient_weights", "lp_diag_philox", "lp_diag_gray"]
 
 
@@ -65,6 +65,7 @@ def load(build_if_missing: bool = True):
         "lp_match": (i32, [P, P, P, P, i64, P, P, P, i64, P, P, P, P]),
         "lp_compact": (i32, [P, P, i32, P, i32, P, i64, P, P, P, P]),
         "lp_ransac": (i32, [P, P, i64, P, u32, P, P, P, P, P]),
+        "lp_ransac_static": (i32, [P, i64, P, i32, C.c_float, C.c_uint64, u32, P, P, P, P, P]),
         "lp_stitch_pair": (i32, [P, P, i32, i32, i32, P, i32, i32, i32, i32, u32, P, P, P, P]),
         "lp_stitch_pair_host": (i32, [P, P, i32, i32, i32, P, i32, i32, i32, i32, u32, P, P, P, P]),
         "lp_sync_status": (i32, [P]),
@@ -188,6 +189,16 @@ class Context:
 def lp_num_keypoints(H, W, Ls) -> int:
     arr = (C.c_int * len(Ls))(*[int(v) for v in Ls])
     return int(load().lp_num_keypoints(H, W, C.cast(arr, C.c_void_p), len(Ls)))
+
+
+def lp_ransac_static(pts, M_cap, d_M, iters, thresh_px, seed, pair_id, H, inlier, n_inliers, best_t=None,
+                     stream=None):
+    """The allocation-free RANSAC entry point (no context; fixed scratch in
+    the library).  Same results as Context.lp_ransac for the same settings."""
+    r = load().lp_ransac_static(_ptr(pts), M_cap, _ptr(d_M), int(iters), float(thresh_px), int(seed), int(pair_id),
+                                _ptr(H), _ptr(inlier), _ptr(n_inliers), _ptr(best_t), _stream(stream))
+    if r != LP_OK:
+        raise LpError(r, "lp_ransac_static")
 
 
 def _diag(name, *args):
