@@ -60,8 +60,9 @@ __device__ __forceinline__ void top2_merge(Top2& t, float d, int j)
 }
 
 __global__ void __launch_bounds__(kThreads, 2)
-k_match_fp32_main(const float* __restrict__ A, long long NA, const float* __restrict__ B, const float* __restrict__ nb,
-                  long long NB, int S, long long cols_per_split, float4* __restrict__ part)
+k_match_fp32_main(const float* __restrict__ A, long long NA, const int32_t* __restrict__ d_rows,
+                  const float* __restrict__ B, const float* __restrict__ nb, long long NB, int S,
+                  long long cols_per_split, float4* __restrict__ part)
 {
     extern __shared__ __align__(16) float smf[];
     float* AsT = smf;                                 // [128 k][128 + pad rows]
@@ -71,6 +72,10 @@ k_match_fp32_main(const float* __restrict__ A, long long NA, const float* __rest
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
     const long long row0 = (long long)blockIdx.x * kTile;
+    // rows beyond a device-side count (queued re-scan rows) have nothing to do;
+    // the partial layout keeps NA as its row capacity
+    const long long n_rows = d_rows ? min(NA, (long long)*d_rows) : NA;
+    if (row0 >= n_rows) return;
     const int split = blockIdx.y;
     const long long c_begin = (long long)split * cols_per_split;
     const long long c_end = min(NB, c_begin + cols_per_split);
@@ -79,7 +84,7 @@ k_match_fp32_main(const float* __restrict__ A, long long NA, const float* __rest
     for (int e = tid; e < kTile * 32; e += kThreads) {
         const int r = e >> 5, q = e & 31;
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (row0 + r < NA) v = __ldg(reinterpret_cast<const float4*>(A + (row0 + r) * 128) + q);
+        if (row0 + r < n_rows) v = __ldg(reinterpret_cast<const float4*>(A + (row0 + r) * 128) + q);
         AsT[(4 * q + 0) * (kTile + kPadA) + r] = v.x;
         AsT[(4 * q + 1) * (kTile + kPadA) + r] = v.y;
         AsT[(4 * q + 2) * (kTile + kPadA) + r] = v.z;
@@ -156,7 +161,7 @@ k_match_fp32_main(const float* __restrict__ A, long long NA, const float* __rest
             top2_merge(best[i], ob2, oj2);
         }
         const long long r = row0 + ty * 8 + i;
-        if (tx == 0 && r < NA)
+        if (tx == 0 && r < n_rows)
             part[(long long)split * NA + r] =
                 make_float4(best[i].b1, best[i].b2, __int_as_float(best[i].j1), __int_as_float(best[i].j2));
     }
@@ -238,11 +243,30 @@ cudaError_t launch_match_fp32(const MatchArgs& a, void* ws, size_t ws_bytes, int
     cudaFuncSetAttribute(k_match_fp32_main, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (a.NB > 0) {
         dim3 grid((unsigned)rowblocks, (unsigned)S);
-        k_match_fp32_main<<<grid, kThreads, smem, s>>>(a.dA, a.NA, a.dB, nb, a.NB, S, cps, part);
+        k_match_fp32_main<<<grid, kThreads, smem, s>>>(a.dA, a.NA, nullptr, a.dB, nb, a.NB, S, cps, part);
     }
     const int Sused = a.NB > 0 ? S : 0;
     k_match_finish<<<(unsigned)((a.NA + 255) / 256), 256, 0, s>>>(part, Sused, a.NA, na, a.vA, a.ratio2, a.delta_s2,
                                                                   a.match, a.d1, a.d2);
+    return cudaGetLastError();
+}
+
+// FP32 re-scan of up to NA_cap rows whose count lives on the device (rows of
+// the BF16 path that could not be certified).  part: [S][NA_cap].
+cudaError_t launch_match_fp32_rows(const float* A, long long NA_cap, const int32_t* d_rows, const float* B,
+                                   const float* nb, long long NB, int num_sms, float4* part, int* S_out,
+                                   cudaStream_t s)
+{
+    const long long rowblocks = (NA_cap + kTile - 1) / kTile;
+    const int S = pick_splits(rowblocks, NB, 2 * num_sms);
+    *S_out = S;
+    if (NA_cap == 0 || NB == 0) return cudaSuccess;
+    const long long tiles = (NB + kTile - 1) / kTile;
+    const long long cps = ((tiles + S - 1) / S) * kTile;
+    const size_t smem = smem_bytes();
+    cudaFuncSetAttribute(k_match_fp32_main, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    dim3 grid((unsigned)rowblocks, (unsigned)S);
+    k_match_fp32_main<<<grid, kThreads, smem, s>>>(A, NA_cap, d_rows, B, nb, NB, S, cps, part);
     return cudaGetLastError();
 }
 

@@ -1,18 +1,728 @@
-// BF16 tensor-core matching (tcgen05) -- under construction.
+// Nearest-neighbour matching (Sec. 2.4, Eq. 6) with BF16 tensor cores
+// (tcgen05) for sm_103a, re-ranked in FP32 so that every decision equals the
+// plain FP32 form's.
+//
+// Stage 1, k_match_tc (persistent, one CTA per SM, 10 warps):
+//   warp 0    TMA producer: per work unit a 256-row A block (2 x 32 KB boxes,
+//             128-byte swizzle), then 128-row B tiles (2 x 16 KB boxes) into a
+//             4-stage ring.
+//   warp 1    allocates all 512 TMEM columns; one lane issues
+//             tcgen05.mma.cta_group::1.kind::f16 (M = 128, N = 128, K = 16,
+//             BF16 x BF16 -> FP32): 2 row blocks x 8 K-steps per B tile, into
+//             one of two TMEM accumulator buffers; tcgen05.commit releases the
+//             B stage and hands the buffer to the epilogue.
+//   warps 2-9 epilogue: each thread owns one A row, reads its 128 FP32 dot
+//             products per tile with tcgen05.ld (32x32b.x32), forms
+//             v = |b~|^2 - 2 a~.b~ and keeps the row's 4 smallest v in
+//             registers; no distance matrix is written.
+//   A work unit is (256-row block of A, one of S column splits of B); units
+//   are dealt round-robin to the persistent CTAs.  Every mbarrier wait is
+//   bounded by a 2 s clock limit; on expiry the CTA records LP_ERR_TIMEOUT,
+//   drains, frees its TMEM and returns.
+//
+// Stage 2, k_rerank (one warp per row): candidates whose BF16 value lies
+//   within 2*delta of the row's second-smallest BF16 value are re-scored
+//   with exactly the FP32 form's arithmetic (sequential FMA over k, then
+//   fma(-2, dot, |b|^2)), so their values are bit-identical to the FP32
+//   form's.  With unit, non-negative descriptors and BF16 unit roundoff
+//   u = 2^-8, |v~_j - v_j| <= 3u + u^2 + 4e-5 = delta for every column j
+//   (derivation in the design doc).  The row is certified when the smallest
+//   fourth-best BF16 value over the splits, minus delta, exceeds the exact
+//   second-best: then no column outside the candidates can enter the top 2.
+//   Uncertified rows are queued.
+// Stage 3: queued rows are gathered and re-scanned by the FP32 SIMT kernel.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
 #include "lp_internal.cuh"
 
 namespace lp {
 
-size_t match_bf16_workspace(int64_t NA, int64_t NB, int num_sms)
+__global__ void k_row_norms(const float* d, const uint8_t* v, long long n, float* out, float invalid_value);
+__global__ void k_match_finish(const float4* part, int S, long long NA, const float* na, const uint8_t* vA,
+                               float ratio2, float delta_s2, int32_t* match, float* d1, float* d2);
+cudaError_t launch_match_fp32_rows(const float* A, long long NA_cap, const int32_t* d_rows, const float* B,
+                                   const float* nb, long long NB, int num_sms, float4* part, int* S_out,
+                                   cudaStream_t s);
+
+namespace {
+
+constexpr int kRowsPerUnit = 256;       // two M = 128 row blocks
+constexpr int kTileN = 128;             // B rows per tile (MMA N)
+constexpr int kStages = 4;              // B ring depth
+constexpr int kThreadsTC = 320;         // 10 warps
+constexpr int kEpiWarps = 8;
+constexpr uint32_t kABytes = kRowsPerUnit * 128 * 2;   // 64 KB
+constexpr uint32_t kBBytes = kTileN * 128 * 2;         // 32 KB per stage
+constexpr uint32_t kSmemTC = kABytes + kStages * kBBytes + 1024 /*barriers*/ + 1024 /*align slack*/;
+constexpr int kTopK = 4;
+constexpr float kDelta = 3.0f / 256.0f + 3.0f / 65536.0f + 1e-4f;   // 3u + 3u^2 + FP32 allowance
+
+// ------------------------------------------------------------------ PTX wrappers
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
 {
-    (void)NA; (void)NB; (void)num_sms;
-    return 256;
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t globaltimer()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait: true when the phase completed, false on abort/timeout.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, int32_t* status)
+{
+    if (mbar_try(bar, parity)) return true;
+    const uint64_t t0 = globaltimer();
+    for (uint32_t it = 1;; ++it) {
+        if (mbar_try(bar, parity)) return true;
+        if ((it & 255u) == 0) {
+            if (*abort_flag) return false;
+            if (globaltimer() - t0 > 2000000000ull) {   // 2 s
+                *abort_flag = 1;
+                set_status(status, DEV_TIMEOUT);
+                return false;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_prefetch_desc(const CUtensorMap* map)
+{
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row atoms of
+// 128 B stacked every 1024 B (SBO); LBO unused for this layout (set to 16 B);
+// descriptor version 1; swizzle mode 2 (128 B).
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)(16u >> 4) << 16;
+    d |= (uint64_t)(1024u >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+// Instruction descriptor, kind::f16: D = FP32, A = B = BF16, both K-major,
+// N = 128, M = 128.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTileN >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.u32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+        ::"r"(dtmem), "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v)
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// ------------------------------------------------------------------ work split
+struct TcParams {
+    long long NA, NB;
+    int nrp;               // number of 256-row blocks
+    int S;                 // column splits
+    long long cps;         // columns per split (multiple of kTileN)
+    const float* nb16;     // |b~_j|^2 (+inf when invalid), length NB
+    float4* pv;            // [S][NA] four smallest values
+    int4* pj;              // [S][NA] their columns (-1 = none)
+    int32_t* status;
+};
+
+__device__ __forceinline__ void unit_range(const TcParams& p, int u, int& rp, int& split, long long& c0, int& ntiles)
+{
+    rp = u % p.nrp;
+    split = u / p.nrp;
+    c0 = (long long)split * p.cps;
+    long long c1 = c0 + p.cps;
+    if (c1 > p.NB) c1 = p.NB;
+    ntiles = c1 > c0 ? (int)((c1 - c0 + kTileN - 1) / kTileN) : 0;
+}
+
+__device__ __forceinline__ void top4_insert(float x, int j, float (&v)[kTopK], int (&ix)[kTopK])
+{
+    const bool c0 = x < v[0], c1 = x < v[1], c2 = x < v[2], c3 = x < v[3];
+    v[3] = c2 ? v[2] : (c3 ? x : v[3]);
+    ix[3] = c2 ? ix[2] : (c3 ? j : ix[3]);
+    v[2] = c1 ? v[1] : (c2 ? x : v[2]);
+    ix[2] = c1 ? ix[1] : (c2 ? j : ix[2]);
+    v[1] = c0 ? v[0] : (c1 ? x : v[1]);
+    ix[1] = c0 ? ix[0] : (c1 ? j : ix[1]);
+    v[0] = c0 ? x : v[0];
+    ix[0] = c0 ? j : ix[0];
+}
+
+__global__ void __launch_bounds__(kThreadsTC, 1)
+k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcParams p)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t* sA = smem;
+    uint8_t* sB = smem + kABytes;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kABytes + kStages * kBBytes);
+    // barrier slots
+    uint64_t* full = bars;                 // [kStages]
+    uint64_t* empty = bars + kStages;      // [kStages]
+    uint64_t* tfull = bars + 2 * kStages;  // [2]
+    uint64_t* tempty = tfull + 2;          // [2]
+    uint64_t* afull = tempty + 2;          // [1]
+    uint64_t* aempty = afull + 1;          // [1]
+    uint64_t* drain = aempty + 1;          // [1]
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int U = p.nrp * p.S;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(smem_u32(&full[s]), 1);
+            mbar_init(smem_u32(&empty[s]), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(&tfull[b]), 1);
+            mbar_init(smem_u32(&tempty[b]), kEpiWarps);
+        }
+        mbar_init(smem_u32(afull), 1);
+        mbar_init(smem_u32(aempty), 1);
+        mbar_init(smem_u32(drain), 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        tma_prefetch_desc(&tmA);
+        tma_prefetch_desc(&tmB);
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tmem_slot))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        // ---------------------------------------------------------- TMA producer
+        if (lane == 0) {
+            long long n = 0;   // tile counter of this CTA (non-empty units only)
+            int v = 0;         // non-empty unit counter of this CTA
+            int armed[kStages];
+            int a_armed = -1;
+            for (int s = 0; s < kStages; ++s) armed[s] = -1;
+            bool ok = true;
+            for (int u = blockIdx.x; u < U && ok; u += gridDim.x) {
+                int rp, split, ntiles;
+                long long c0;
+                unit_range(p, u, rp, split, c0, ntiles);
+                if (ntiles == 0) continue;
+                ok = mbar_wait(smem_u32(aempty), (v & 1) ^ 1, abort_flag, p.status);
+                if (!ok) break;
+                mbar_expect_tx(smem_u32(afull), kABytes);
+                tma_load_2d(smem_u32(sA), &tmA, 0, rp * kRowsPerUnit, smem_u32(afull));
+                tma_load_2d(smem_u32(sA + kABytes / 2), &tmA, 64, rp * kRowsPerUnit, smem_u32(afull));
+                a_armed = v;
+                for (int t = 0; t < ntiles; ++t, ++n) {
+                    const int s = (int)(n % kStages);
+                    const uint32_t k = (uint32_t)(n / kStages);
+                    ok = mbar_wait(smem_u32(&empty[s]), (k & 1) ^ 1, abort_flag, p.status);
+                    if (!ok) break;
+                    uint8_t* dst = sB + s * kBBytes;
+                    const int y = (int)(c0 + (long long)t * kTileN);
+                    mbar_expect_tx(smem_u32(&full[s]), kBBytes);
+                    tma_load_2d(smem_u32(dst), &tmB, 0, y, smem_u32(&full[s]));
+                    tma_load_2d(smem_u32(dst + kBBytes / 2), &tmB, 64, y, smem_u32(&full[s]));
+                    armed[s] = (int)k;
+                }
+                ++v;
+            }
+            if (!ok) {
+                // drain: wait (bounded) for the copies this thread issued to land
+                for (int s = 0; s < kStages; ++s) {
+                    if (armed[s] < 0) continue;
+                    const uint64_t t0 = globaltimer();
+                    while (!mbar_try(smem_u32(&full[s]), (uint32_t)armed[s] & 1u) && globaltimer() - t0 < 200000000ull) {
+                    }
+                }
+                if (a_armed >= 0) {
+                    const uint64_t t0 = globaltimer();
+                    while (!mbar_try(smem_u32(afull), (uint32_t)a_armed & 1u) && globaltimer() - t0 < 200000000ull) {
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            long long n = 0;
+            int v = 0;
+            bool ok = true;
+            for (int u = blockIdx.x; u < U && ok; u += gridDim.x) {
+                int rp, split, ntiles;
+                long long c0;
+                unit_range(p, u, rp, split, c0, ntiles);
+                if (ntiles == 0) continue;
+                ok = mbar_wait(smem_u32(afull), v & 1, abort_flag, p.status);
+                ++v;
+                if (!ok) break;
+                tc_fence_after();
+                for (int t = 0; t < ntiles; ++t, ++n) {
+                    const int s = (int)(n % kStages);
+                    const uint32_t k = (uint32_t)(n / kStages);
+                    const int b = (int)(n & 1);
+                    const uint32_t kb = (uint32_t)(n >> 1);
+                    ok = mbar_wait(smem_u32(&tempty[b]), (kb & 1) ^ 1, abort_flag, p.status);
+                    if (!ok) break;
+                    ok = mbar_wait(smem_u32(&full[s]), k & 1, abort_flag, p.status);
+                    if (!ok) break;
+                    tc_fence_after();
+                    const uint32_t bbase = smem_u32(sB + s * kBBytes);
+#pragma unroll
+                    for (int rb = 0; rb < 2; ++rb) {
+                        const uint32_t d = tmem + (uint32_t)((b * 2 + rb) * kTileN);
+                        const uint32_t abase = smem_u32(sA) + rb * (128 * 128);
+#pragma unroll
+                        for (int h = 0; h < 2; ++h)
+#pragma unroll
+                            for (int kk = 0; kk < 4; ++kk) {
+                                const uint64_t ad = sdesc(abase + h * (kABytes / 2) + kk * 32);
+                                const uint64_t bd = sdesc(bbase + h * (kBBytes / 2) + kk * 32);
+                                mma_bf16(d, ad, bd, (h | kk) ? 1u : 0u);
+                            }
+                    }
+                    mma_commit(smem_u32(&empty[s]));
+                    mma_commit(smem_u32(&tfull[b]));
+                }
+                if (!ok) break;
+                mma_commit(smem_u32(aempty));
+            }
+            // wait (bounded) for every MMA this thread issued before TMEM is freed
+            mma_commit(smem_u32(drain));
+            const uint64_t t0 = globaltimer();
+            while (!mbar_try(smem_u32(drain), 0) && globaltimer() - t0 < 2000000000ull) {
+            }
+        }
+    } else {
+        // ---------------------------------------------------------- epilogue
+        const int q = warp & 3;                 // TMEM lane quarter this warp may access
+        const int rb = (warp - 2) >> 2;         // row block 0 (warps 2-5) or 1 (warps 6-9)
+        const int row_in_unit = rb * 128 + q * 32 + lane;
+        long long n = 0;
+        bool ok = true;
+        for (int u = blockIdx.x; u < U && ok; u += gridDim.x) {
+            int rp, split, ntiles;
+            long long c0;
+            unit_range(p, u, rp, split, c0, ntiles);
+            long long c1 = c0 + p.cps;
+            if (c1 > p.NB) c1 = p.NB;
+            float bv[kTopK] = {INFINITY, INFINITY, INFINITY, INFINITY};
+            int bj[kTopK] = {-1, -1, -1, -1};
+            for (int t = 0; t < ntiles; ++t, ++n) {
+                const int b = (int)(n & 1);
+                const uint32_t kb = (uint32_t)(n >> 1);
+                ok = mbar_wait(smem_u32(&tfull[b]), kb & 1, abort_flag, p.status);
+                if (!ok) break;
+                tc_fence_after();
+                const long long cbase = c0 + (long long)t * kTileN;
+#pragma unroll 1
+                for (int ch = 0; ch < kTileN / 32; ++ch) {
+                    float acc[32];
+                    const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)((b * 2 + rb) * kTileN + ch * 32);
+                    tmem_ld32(taddr, acc);
+                    const long long j0 = cbase + ch * 32;
+                    float nbv[32];
+                    if (j0 + 32 <= c1) {
+                        const float4* src = reinterpret_cast<const float4*>(p.nb16 + j0);
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            const float4 w = __ldg(src + i);
+                            nbv[4 * i] = w.x; nbv[4 * i + 1] = w.y; nbv[4 * i + 2] = w.z; nbv[4 * i + 3] = w.w;
+                        }
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) nbv[i] = (j0 + i < c1) ? __ldg(p.nb16 + j0 + i) : INFINITY;
+                    }
+                    float mn = INFINITY;
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) {
+                        acc[i] = fmaf(-2.f, acc[i], nbv[i]);
+                        mn = fminf(mn, acc[i]);
+                    }
+                    if (mn < bv[3]) {
+#pragma unroll
+                        for (int i = 0; i < 32; ++i)
+                            if (acc[i] < bv[3]) top4_insert(acc[i], (int)(j0 + i), bv, bj);
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&tempty[b]));
+            }
+            if (!ok) break;
+            const long long row = (long long)rp * kRowsPerUnit + row_in_unit;
+            if (row < p.NA) {
+                p.pv[(long long)split * p.NA + row] = make_float4(bv[0], bv[1], bv[2], bv[3]);
+                p.pj[(long long)split * p.NA + row] = make_int4(bj[0], bj[1], bj[2], bj[3]);
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+}
+
+// |b~|^2 of the bf16 rows in FP32 (+inf when invalid).
+__global__ void k_row_norms_bf16(const __nv_bfloat16* d, const uint8_t* v, long long n, float* out)
+{
+    const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= n) return;
+    const uint2 raw = reinterpret_cast<const uint2*>(d + w * 128)[lane];
+    const __nv_bfloat162 lo = *reinterpret_cast<const __nv_bfloat162*>(&raw.x);
+    const __nv_bfloat162 hi = *reinterpret_cast<const __nv_bfloat162*>(&raw.y);
+    const float2 a = __bfloat1622float2(lo), b = __bfloat1622float2(hi);
+    float s = a.x * a.x + a.y * a.y + b.x * b.x + b.y * b.y;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
+    if (lane == 0) out[w] = v[w] ? s : INFINITY;
+}
+
+// ------------------------------------------------------------------ re-rank
+// FP32-form value of column j for query a: exactly the FP32 kernel's
+// arithmetic (sequential fmaf over k = 0..127, then fmaf(-2, dot, |b|^2)).
+__device__ __forceinline__ float fp32_form_value(const float* a, const float* b, float nbj)
+{
+    float acc = 0.f;
+    const float4* b4 = reinterpret_cast<const float4*>(b);
+#pragma unroll 8
+    for (int k4 = 0; k4 < 32; ++k4) {
+        const float4 w = __ldg(b4 + k4);
+        acc = fmaf(a[4 * k4 + 0], w.x, acc);
+        acc = fmaf(a[4 * k4 + 1], w.y, acc);
+        acc = fmaf(a[4 * k4 + 2], w.z, acc);
+        acc = fmaf(a[4 * k4 + 3], w.w, acc);
+    }
+    return fmaf(-2.f, acc, nbj);
+}
+
+constexpr int kRerankWarps = 8;
+
+__global__ void __launch_bounds__(kRerankWarps * 32)
+k_rerank(const float* A, const float* B, const float* nb32, const float4* pv, const int4* pj, int S, long long NA,
+         float delta, float4* out_part, int32_t* rescan_rows, int32_t* rescan_count)
+{
+    __shared__ __align__(16) float qa[kRerankWarps][128];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long i = (long long)blockIdx.x * kRerankWarps + warp;
+    if (i >= NA) return;
+    reinterpret_cast<float4*>(qa[warp])[lane] = reinterpret_cast<const float4*>(A + i * 128)[lane];
+    // gather the S x 4 candidates: lane c holds candidates 4c .. 4c+3 of split c (S <= 32)
+    float cv[kTopK];
+    int cj[kTopK];
+    float t4 = INFINITY;   // smallest fourth-best value over the splits
+    if (lane < S) {
+        const float4 v = pv[(long long)lane * NA + i];
+        const int4 j = pj[(long long)lane * NA + i];
+        cv[0] = v.x; cv[1] = v.y; cv[2] = v.z; cv[3] = v.w;
+        cj[0] = j.x; cj[1] = j.y; cj[2] = j.z; cj[3] = j.w;
+        t4 = v.w;
+    } else {
+#pragma unroll
+        for (int k = 0; k < kTopK; ++k) { cv[k] = INFINITY; cj[k] = -1; }
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) t4 = fminf(t4, __shfl_xor_sync(0xFFFFFFFFu, t4, o));
+    // second-smallest BF16 value over all candidates
+    float m1 = cv[0], m2 = cv[1];
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        const float o1 = __shfl_xor_sync(0xFFFFFFFFu, m1, o);
+        const float o2 = __shfl_xor_sync(0xFFFFFFFFu, m2, o);
+        const float n1 = fminf(m1, o1);
+        const float n2 = fminf(fmaxf(m1, o1), fminf(m2, o2));
+        m1 = n1;
+        m2 = n2;
+    }
+    const float window = m2 + 2.f * delta;
+    __syncwarp();
+    // exact FP32-form values of the candidates inside the window
+    float b1 = INFINITY, b2 = INFINITY;
+    int j1 = -1, j2 = -1;
+#pragma unroll
+    for (int k = 0; k < kTopK; ++k) {
+        if (cj[k] >= 0 && cv[k] <= window) {
+            const int j = cj[k];
+            const float x = fp32_form_value(qa[warp], B + (long long)j * 128, __ldg(nb32 + j));
+            if (x < b1 || (x == b1 && j < j1)) {
+                b2 = b1; j2 = j1; b1 = x; j1 = j;
+            } else if (x < b2 || (x == b2 && j < j2)) {
+                b2 = x; j2 = j;
+            }
+        }
+    }
+    // merge the lanes' top-2 lists, (value, column) order
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        const float ob1 = __shfl_xor_sync(0xFFFFFFFFu, b1, o), ob2 = __shfl_xor_sync(0xFFFFFFFFu, b2, o);
+        const int oj1 = __shfl_xor_sync(0xFFFFFFFFu, j1, o), oj2 = __shfl_xor_sync(0xFFFFFFFFu, j2, o);
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const float x = r ? ob2 : ob1;
+            const int j = r ? oj2 : oj1;
+            if (j < 0) continue;
+            if (x < b1 || (x == b1 && (unsigned)j < (unsigned)j1)) {
+                b2 = b1; j2 = j1; b1 = x; j1 = j;
+            } else if ((x < b2 || (x == b2 && (unsigned)j < (unsigned)j2)) && j != j1) {
+                b2 = x; j2 = j;
+            }
+        }
+    }
+    if (lane == 0) {
+        // every column outside the candidates has an FP32-form value >= t4 - delta
+        // t4 = inf: no split saw more than 4 valid columns, so every column
+        // was a candidate
+        const bool certified = isinf(t4) || b2 < t4 - delta;
+        if (certified) {
+            out_part[i] = make_float4(b1, b2, __int_as_float(j1), __int_as_float(j2));
+        } else {
+            const int slot = atomicAdd(rescan_count, 1);
+            rescan_rows[slot] = (int32_t)i;
+        }
+    }
+}
+
+// Gather the queued A rows (FP32) into a dense block for the FP32 re-scan.
+__global__ void k_gather_rows(const float* A, const int32_t* rows, const int32_t* count, float* out)
+{
+    const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= *count) return;
+    reinterpret_cast<float4*>(out + w * 128)[lane] = reinterpret_cast<const float4*>(A + (long long)rows[w] * 128)[lane];
+}
+
+// Merge the re-scan partials of queued row r into the row's single partial.
+__global__ void k_rescan_merge(const float4* part, int S, long long cap, const int32_t* rows, const int32_t* count,
+                               float4* out_part)
+{
+    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= *count) return;
+    float b1 = INFINITY, b2 = INFINITY;
+    int j1 = -1, j2 = -1;
+    for (int s = 0; s < S; ++s) {
+        const float4 q = part[(long long)s * cap + r];
+        for (int t = 0; t < 2; ++t) {
+            const float x = t ? q.y : q.x;
+            const int j = __float_as_int(t ? q.w : q.z);
+            if (j < 0) continue;
+            if (x < b1 || (x == b1 && j < j1)) {
+                b2 = b1; j2 = j1; b1 = x; j1 = j;
+            } else if (x < b2 || (x == b2 && j < j2)) {
+                b2 = x; j2 = j;
+            }
+        }
+    }
+    out_part[rows[r]] = make_float4(b1, b2, __int_as_float(j1), __int_as_float(j2));
+}
+
+// ------------------------------------------------------------------ host side
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+bool make_map(CUtensorMap* m, const void* base, long long rows, uint32_t box_rows)
+{
+    auto fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {128, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {256};
+    cuuint32_t box[2] = {64, box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Column splits S: minimise (rounds of units per CTA) x (tiles per unit + ~2
+// tiles of per-unit A reload and pipeline refill).
+int pick_tc_splits(int nrp, long long NB, int sms)
+{
+    const long long tiles = (NB + kTileN - 1) / kTileN;
+    int best = 1;
+    double best_cost = 1e300;
+    for (int S = 1; S <= 32 && S <= tiles; ++S) {
+        const long long U = (long long)nrp * S;
+        const double rounds = (double)((U + sms - 1) / sms);
+        const double cost = rounds * (double)((tiles + S - 1) / S + 2);
+        if (cost < best_cost - 1e-9) { best_cost = cost; best = S; }
+    }
+    return best;
+}
+
+struct TcLayout {
+    int S;
+    size_t off_nb16, off_na, off_nb32, off_pv, off_pj, off_part1, off_rows, off_cnt, off_ar, off_part_r, total;
+};
+
+TcLayout tc_layout(long long NA, long long NB, int sms)
+{
+    TcLayout L;
+    const int nrp = (int)((NA + kRowsPerUnit - 1) / kRowsPerUnit);
+    L.S = pick_tc_splits(nrp, NB, sms);
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t r = o; o += (bytes + 255) & ~size_t(255); return r; };
+    L.off_nb16 = take(sizeof(float) * (size_t)NB + 64);
+    L.off_na = take(sizeof(float) * (size_t)NA);
+    L.off_nb32 = take(sizeof(float) * (size_t)NB);
+    L.off_pv = take(sizeof(float4) * (size_t)L.S * NA);
+    L.off_pj = take(sizeof(int4) * (size_t)L.S * NA);
+    L.off_part1 = take(sizeof(float4) * (size_t)NA);
+    L.off_rows = take(sizeof(int32_t) * (size_t)NA);
+    L.off_cnt = take(64);
+    L.off_ar = take(sizeof(float) * 128 * (size_t)NA);
+    L.off_part_r = take(sizeof(float4) * 32 * (size_t)NA);
+    L.total = o + 256;
+    return L;
+}
+
+}  // namespace
+
+size_t match_bf16_workspace(int64_t NA, int64_t NB, int num_sms) { return tc_layout(NA, NB, num_sms).total; }
 
 cudaError_t launch_match_bf16(const MatchArgs& a, void* ws, size_t ws_bytes, int num_sms, cudaStream_t s)
 {
-    (void)a; (void)ws; (void)ws_bytes; (void)num_sms; (void)s;
-    return cudaErrorNotSupported;
+    if (a.NA == 0) return cudaSuccess;
+    const TcLayout L = tc_layout(a.NA, a.NB, num_sms);
+    if (ws_bytes < L.total) return cudaErrorInvalidValue;
+    uint8_t* w = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(ws) + 255) & ~uintptr_t(255));
+    float* nb16 = reinterpret_cast<float*>(w + L.off_nb16);
+    float* na = reinterpret_cast<float*>(w + L.off_na);
+    float* nb32 = reinterpret_cast<float*>(w + L.off_nb32);
+    float4* pv = reinterpret_cast<float4*>(w + L.off_pv);
+    int4* pj = reinterpret_cast<int4*>(w + L.off_pj);
+    float4* part1 = reinterpret_cast<float4*>(w + L.off_part1);
+    int32_t* rows = reinterpret_cast<int32_t*>(w + L.off_rows);
+    int32_t* cnt = reinterpret_cast<int32_t*>(w + L.off_cnt);
+    float* ar = reinterpret_cast<float*>(w + L.off_ar);
+    float4* part_r = reinterpret_cast<float4*>(w + L.off_part_r);
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(cnt, 0, sizeof(int32_t), s)) != cudaSuccess) return e;
+    k_row_norms<<<(unsigned)((a.NA * 32 + 255) / 256), 256, 0, s>>>(a.dA, a.vA, a.NA, na, 0.f);
+    if (a.NB > 0) {
+        k_row_norms<<<(unsigned)((a.NB * 32 + 255) / 256), 256, 0, s>>>(a.dB, a.vB, a.NB, nb32, INFINITY);
+        k_row_norms_bf16<<<(unsigned)((a.NB * 32 + 255) / 256), 256, 0, s>>>(
+            reinterpret_cast<const __nv_bfloat16*>(a.dB16), a.vB, a.NB, nb16);
+        CUtensorMap tA, tB;
+        if (!make_map(&tA, a.dA16, a.NA, kRowsPerUnit) || !make_map(&tB, a.dB16, a.NB, kTileN))
+            return cudaErrorInvalidValue;
+        TcParams p;
+        p.NA = a.NA;
+        p.NB = a.NB;
+        p.nrp = (int)((a.NA + kRowsPerUnit - 1) / kRowsPerUnit);
+        p.S = L.S;
+        const long long tiles = (a.NB + kTileN - 1) / kTileN;
+        p.cps = ((tiles + L.S - 1) / L.S) * kTileN;
+        p.nb16 = nb16;
+        p.pv = pv;
+        p.pj = pj;
+        p.status = a.status;
+        const int U = p.nrp * p.S;
+        const int grid = U < num_sms ? U : num_sms;
+        if ((e = cudaFuncSetAttribute(k_match_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTC)) !=
+            cudaSuccess)
+            return e;
+        k_match_tc<<<grid, kThreadsTC, kSmemTC, s>>>(tA, tB, p);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        k_rerank<<<(unsigned)((a.NA + kRerankWarps - 1) / kRerankWarps), kRerankWarps * 32, 0, s>>>(
+            a.dA, a.dB, nb32, pv, pj, L.S, a.NA, kDelta, part1, rows, cnt);
+        k_gather_rows<<<(unsigned)((a.NA * 32 + 255) / 256), 256, 0, s>>>(a.dA, rows, cnt, ar);
+        int Sr = 0;
+        if ((e = launch_match_fp32_rows(ar, a.NA, cnt, a.dB, nb32, a.NB, num_sms, part_r, &Sr, s)) != cudaSuccess)
+            return e;
+        k_rescan_merge<<<(unsigned)((a.NA + 255) / 256), 256, 0, s>>>(part_r, Sr, a.NA, rows, cnt, part1);
+        k_match_finish<<<(unsigned)((a.NA + 255) / 256), 256, 0, s>>>(part1, 1, a.NA, na, a.vA, a.ratio2, a.delta_s2,
+                                                                      a.match, a.d1, a.d2);
+    } else {
+        k_match_finish<<<(unsigned)((a.NA + 255) / 256), 256, 0, s>>>(part1, 0, a.NA, na, a.vA, a.ratio2, a.delta_s2,
+                                                                      a.match, a.d1, a.d2);
+    }
+    return cudaGetLastError();
 }
 
 }  // namespace lp

@@ -332,71 +332,98 @@ k_ransac_select(const float4* pts, long long M_cap, const int32_t* dM, int T, co
 
 // ---------------------------------------------------------------- refit
 constexpr int kRefitThreads = 256;
+constexpr int kRefitWarps = kRefitThreads / 32;
 
-__device__ double block_sum_d(double v, double* red)
+// Sum N per-thread doubles over the CTA in one pass: warp shuffles, then the
+// warps' partials in a fixed order.  Every thread receives the N totals.
+template <int N>
+__device__ void block_sum_n(double* v, double (*part)[N], double* tot)
 {
-#pragma unroll
-    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+        double x = v[q];
+#pragma unroll
+        for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
+        v[q] = x;
+    }
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < N; ++q) part[warp][q] = v[q];
     __syncthreads();
-    if (lane == 0) red[warp] = v;
+    for (int q = threadIdx.x; q < N; q += kRefitThreads) {
+        double s = 0;
+        for (int w = 0; w < kRefitWarps; ++w) s += part[w][q];
+        tot[q] = s;
+    }
     __syncthreads();
-    double s = 0;
-    for (int w = 0; w < kRefitThreads / 32; ++w) s += red[w];
-    return s;
 }
 
-// Cyclic Jacobi eigen-decomposition of a symmetric 9x9 matrix; returns the
-// eigenvector of the smallest eigenvalue.
-__device__ void jacobi9_smallest(double a[9][9], double* h)
+// Cyclic Jacobi eigen-decomposition of the symmetric 9x9 matrix `a` (shared
+// memory) by one warp: the rotation sequence of the sequential algorithm, each
+// rotation's row/column updates spread over lanes 0..8.  Writes the
+// eigenvector of the smallest eigenvalue to h.
+__device__ void jacobi9_smallest_warp(double (*a)[9], double (*v)[9], double* h)
 {
-    double v[9][9];
-    for (int i = 0; i < 9; ++i)
-        for (int j = 0; j < 9; ++j) v[i][j] = i == j;
+    const int lane = threadIdx.x & 31;
+    if (lane < 9)
+        for (int j = 0; j < 9; ++j) v[lane][j] = lane == j;
+    __syncwarp();
     for (int sweep = 0; sweep < 100; ++sweep) {
         double off = 0, tot = 0;
-        for (int i = 0; i < 9; ++i)
+        if (lane < 9)
             for (int j = 0; j < 9; ++j) {
-                tot += a[i][j] * a[i][j];
-                if (i != j) off += a[i][j] * a[i][j];
+                const double x = a[lane][j] * a[lane][j];
+                tot += x;
+                if (j != lane) off += x;
             }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            off += __shfl_xor_sync(0xFFFFFFFFu, off, o);
+            tot += __shfl_xor_sync(0xFFFFFFFFu, tot, o);
+        }
         if (off == 0 || off < 1e-30 * tot) break;
         for (int p = 0; p < 9; ++p)
             for (int q = p + 1; q < 9; ++q) {
-                if (a[p][q] == 0) continue;
-                const double th = (a[q][q] - a[p][p]) / (2.0 * a[p][q]);
+                const double apq = a[p][q];
+                if (apq == 0) continue;
+                const double th = (a[q][q] - a[p][p]) / (2.0 * apq);
                 const double t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
                 const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
-                for (int k = 0; k < 9; ++k) {
-                    const double akp = a[k][p], akq = a[k][q];
-                    a[k][p] = c * akp - s * akq;
-                    a[k][q] = s * akp + c * akq;
+                __syncwarp();
+                if (lane < 9) {
+                    const double akp = a[lane][p], akq = a[lane][q];
+                    a[lane][p] = c * akp - s * akq;
+                    a[lane][q] = s * akp + c * akq;
                 }
-                for (int k = 0; k < 9; ++k) {
-                    const double apk = a[p][k], aqk = a[q][k];
-                    a[p][k] = c * apk - s * aqk;
-                    a[q][k] = s * apk + c * aqk;
+                __syncwarp();
+                if (lane < 9) {
+                    const double apk = a[p][lane], aqk = a[q][lane];
+                    a[p][lane] = c * apk - s * aqk;
+                    a[q][lane] = s * apk + c * aqk;
+                    const double vkp = v[lane][p], vkq = v[lane][q];
+                    v[lane][p] = c * vkp - s * vkq;
+                    v[lane][q] = s * vkp + c * vkq;
                 }
-                for (int k = 0; k < 9; ++k) {
-                    const double vkp = v[k][p], vkq = v[k][q];
-                    v[k][p] = c * vkp - s * vkq;
-                    v[k][q] = s * vkp + c * vkq;
-                }
+                __syncwarp();
             }
     }
     int m = 0;
     for (int i = 1; i < 9; ++i)
         if (a[i][i] < a[m][m]) m = i;
-    for (int k = 0; k < 9; ++k) h[k] = v[k][m];
+    if (lane < 9) h[lane] = v[lane][m];
+    __syncwarp();
 }
 
 __global__ void __launch_bounds__(kRefitThreads)
 k_ransac_refit(const float4* pts, long long M_cap, const int32_t* dM, const double* Hs, const int32_t* best_in,
                double t2, double* Hout, uint8_t* inl, int32_t* n_in, int32_t* best_t)
 {
-    __shared__ double red[kRefitThreads / 32];
-    __shared__ double Hf[9];
-    __shared__ double S[45];
+    __shared__ double part[kRefitWarps][45];
+    __shared__ double tot[45];
+    __shared__ double A9[9][9], V9[9][9];
+    __shared__ double hs[9], Hf[9];
+    __shared__ int ok_s;
     const long long M = m_count(dM, M_cap);
     const int best = *best_in;
     if (threadIdx.x == 0 && best_t) *best_t = best;
@@ -407,30 +434,31 @@ k_ransac_refit(const float4* pts, long long M_cap, const int32_t* dM, const doub
         return;
     }
     double Hb[9];
+#pragma unroll
     for (int i = 0; i < 9; ++i) Hb[i] = Hs[9ll * best + i];
     // inliers of the winning hypothesis and their centroids
-    double sxa = 0, sya = 0, sxb = 0, syb = 0, cnt = 0;
+    double v5[5] = {0, 0, 0, 0, 0};
     for (long long i = threadIdx.x; i < M; i += kRefitThreads) {
         const float4 p = pts[i];
         const bool in = inlier64(Hb, p, t2);
         inl[i] = in;
-        if (in) { sxa += p.x; sya += p.y; sxb += p.z; syb += p.w; cnt += 1; }
+        if (in) { v5[0] += 1; v5[1] += p.x; v5[2] += p.y; v5[3] += p.z; v5[4] += p.w; }
     }
-    cnt = block_sum_d(cnt, red);
-    const double cxa = block_sum_d(sxa, red) / cnt, cya = block_sum_d(sya, red) / cnt;
-    const double cxb = block_sum_d(sxb, red) / cnt, cyb = block_sum_d(syb, red) / cnt;
-    double da = 0, db = 0;
+    block_sum_n<5>(v5, reinterpret_cast<double(*)[5]>(&part[0][0]), tot);
+    const double cnt = tot[0];
+    const double cxa = tot[1] / cnt, cya = tot[2] / cnt, cxb = tot[3] / cnt, cyb = tot[4] / cnt;
+    double v2[2] = {0, 0};
     for (long long i = threadIdx.x; i < M; i += kRefitThreads) {
         if (!inl[i]) continue;
         const float4 p = pts[i];
-        da += sqrt((p.x - cxa) * (p.x - cxa) + (p.y - cya) * (p.y - cya));
-        db += sqrt((p.z - cxb) * (p.z - cxb) + (p.w - cyb) * (p.w - cyb));
+        v2[0] += sqrt((p.x - cxa) * (p.x - cxa) + (p.y - cya) * (p.y - cya));
+        v2[1] += sqrt((p.z - cxb) * (p.z - cxb) + (p.w - cyb) * (p.w - cyb));
     }
-    da = block_sum_d(da, red) / cnt;
-    db = block_sum_d(db, red) / cnt;
+    block_sum_n<2>(v2, reinterpret_cast<double(*)[2]>(&part[0][0]), tot);
+    const double da = tot[0] / cnt, db = tot[1] / cnt;
     const Norm2D na{sqrt(2.0) / da, cxa, cya}, nb{sqrt(2.0) / db, cxb, cyb};
     const bool good = cnt >= 4 && da > 0 && db > 0;
-    // upper triangle of A^T A, 45 entries
+    // upper triangle of A^T A (45 entries), A rows of Eq. 7 in normalised coordinates
     double acc[45];
 #pragma unroll
     for (int q = 0; q < 45; ++q) acc[q] = 0;
@@ -449,37 +477,35 @@ k_ransac_refit(const float4* pts, long long M_cap, const int32_t* dM, const doub
                 for (int k = j; k < 9; ++k) acc[q++] += r0[j] * r0[k] + r1[j] * r1[k];
         }
     }
-    for (int q = 0; q < 45; ++q) {
-        const double s = block_sum_d(acc[q], red);
-        if (threadIdx.x == 0) S[q] = s;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        bool ok = good;
-        double H[9];
-        if (ok) {
-            double a[9][9];
+    block_sum_n<45>(acc, part, tot);
+    if (threadIdx.x < 32) {
+        if (threadIdx.x == 0) {
             int q = 0;
             for (int j = 0; j < 9; ++j)
-                for (int k = j; k < 9; ++k) { a[j][k] = S[q]; a[k][j] = S[q]; ++q; }
-            double h[9];
-            jacobi9_smallest(a, h);
-            ok = denorm(na, nb, h, H);
+                for (int k = j; k < 9; ++k) { A9[j][k] = tot[q]; A9[k][j] = tot[q]; ++q; }
         }
-        for (int i = 0; i < 9; ++i) Hf[i] = ok ? H[i] : Hb[i];
+        __syncwarp();
+        if (good) jacobi9_smallest_warp(A9, V9, hs);
+        if (threadIdx.x == 0) {
+            double H[9];
+            bool ok = good && denorm(na, nb, hs, H);
+            for (int i = 0; i < 9; ++i) Hf[i] = ok ? H[i] : Hb[i];
+            ok_s = ok;
+        }
     }
     __syncthreads();
     double Hfin[9];
+#pragma unroll
     for (int i = 0; i < 9; ++i) Hfin[i] = Hf[i];
-    int n = 0;
+    double n1[1] = {0};
     for (long long i = threadIdx.x; i < M_cap; i += kRefitThreads) {
         const bool in = i < M && inlier64(Hfin, pts[i], t2);
         inl[i] = in;
-        n += in;
+        n1[0] += in;
     }
-    const double nn = block_sum_d((double)n, red);
+    block_sum_n<1>(n1, reinterpret_cast<double(*)[1]>(&part[0][0]), tot);
     if (threadIdx.x < 9) Hout[threadIdx.x] = Hfin[threadIdx.x];
-    if (threadIdx.x == 0) *n_in = (int)nn;
+    if (threadIdx.x == 0) *n_in = (int)tot[0];
 }
 
 }  // namespace
@@ -514,7 +540,7 @@ cudaError_t launch_ransac(const float* pts, int64_t M_cap, const int32_t* d_M, i
     const double t2 = (double)thresh * (double)thresh;
     const float t2f = (float)t2;
     const float eps = fmaxf(0.05f, 0.01f * t2f);
-    k_ransac_hyp<<<(T + 127) / 128, 128, 0, s>>>(p4, M_cap, d_M, T, k0, k1, Hs, hok);
+    k_ransac_hyp<<<(T + 31) / 32, 32, 0, s>>>(p4, M_cap, d_M, T, k0, k1, Hs, hok);
     k_ransac_score<<<T, kScoreThreads, 0, s>>>(p4, M_cap, d_M, Hs, hok, t2f, eps, lo, hi);
     k_ransac_select<<<1, kSelThreads, 0, s>>>(p4, M_cap, d_M, T, Hs, lo, hi, t2, best);
     k_ransac_refit<<<1, kRefitThreads, 0, s>>>(p4, M_cap, d_M, Hs, best, t2, H, inlier, n_in, best_t);

@@ -187,8 +187,8 @@ def _unit(rng, n):
     return d / np.linalg.norm(d, axis=1, keepdims=True)
 
 
-@pytest.mark.parametrize("precision", [lp.PREC_FP32])
-@pytest.mark.parametrize("NA,NB", [(1, 2), (130, 1), (300, 517), (1000, 777), (2049, 4099)])
+@pytest.mark.parametrize("precision", [lp.PREC_FP32, lp.PREC_BF16])
+@pytest.mark.parametrize("NA,NB", [(1, 2), (130, 1), (300, 517), (1000, 777), (2049, 4099), (257, 129)])
 def test_match_synthetic(NA, NB, precision):
     rng = np.random.default_rng(NA + NB)
     A = _unit(rng, NA)
@@ -202,7 +202,7 @@ def test_match_synthetic(NA, NB, precision):
     _match_parity(ctx, A, vA, B, vB)
 
 
-@pytest.mark.parametrize("precision", [lp.PREC_FP32])
+@pytest.mark.parametrize("precision", [lp.PREC_FP32, lp.PREC_BF16])
 def test_match_640x480_stage_isolated(precision):
     p = synth.pair_640x480(0)
     Ls = synth.PAIR_640x480_LS
@@ -214,6 +214,41 @@ def test_match_640x480_stage_isolated(precision):
     ctx = ctx_for(Ls, precision=precision)
     near, acc = _match_parity(ctx, dA, fa["valid"], dB, fb["valid"], rows=rows)
     assert acc > 50 and near <= 2
+
+
+def _same(a, b):
+    return np.array_equal(a, b, equal_nan=True)
+
+
+@pytest.mark.parametrize("NA,NB", [(5, 7), (700, 1300), (5000, 4500)])
+def test_match_bf16_bitidentical_to_fp32(NA, NB):
+    # the BF16 form re-ranks exactly with the FP32 form's arithmetic: identical
+    # outputs, bit for bit, on every row
+    rng = np.random.default_rng(NA * 3 + NB)
+    A = _unit(rng, NA)
+    B = _unit(rng, NB)
+    k = min(NA, NB) // 3
+    B[:k] = A[:k] + 0.05 * rng.standard_normal((k, 128)).astype(np.float32)
+    B[:k] = np.abs(B[:k]) / np.linalg.norm(B[:k], axis=1, keepdims=True)
+    vA = (rng.uniform(size=NA) > 0.03).astype(np.uint8)
+    vB = (rng.uniform(size=NB) > 0.03).astype(np.uint8)
+    r32 = G.match(ctx_for((16,), precision=lp.PREC_FP32), A, vA, B, vB)
+    r16 = G.match(ctx_for((16,), precision=lp.PREC_BF16), A, vA, B, vB)
+    for x, y in zip(r32, r16):
+        assert _same(x, y)
+
+
+def test_match_bf16_bitidentical_2688x1600():
+    p = synth.pair_2688x1600(0)
+    out = {}
+    for prec in (lp.PREC_FP32, lp.PREC_BF16):
+        ctx = ctx_for(synth.PAIR_2688x1600_LS, precision=prec)
+        fa = lp.features(ctx, p.A)
+        fb = lp.features(ctx, p.B)
+        out[prec] = [G.host(t) for t in lp.match(ctx, fa, fb)]
+    for x, y in zip(out[lp.PREC_FP32], out[lp.PREC_BF16]):
+        assert _same(x, y)
+    assert (out[lp.PREC_BF16][0] >= 0).sum() > 500
 
 
 def test_match_edge_cases():
