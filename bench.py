@@ -207,6 +207,7 @@ def run_lp(args, rank, world):
     n_in = int(nin.item())
     M = int(dM.item())
     assert ctx.lp_sync_status() == 0
+    rescans = ctx.lp_diag_last_rescans()
 
     # end to end through the public host-buffer call
     hostA = torch.from_numpy(np.ascontiguousarray(lp.pitched_device(pair.A)[0].cpu().numpy())).pin_memory()
@@ -231,7 +232,7 @@ def run_lp(args, rank, world):
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
     t_steps, e2e_t, t_match = tt.tolist()
     return dict(t_steps=t_steps, e2e_t=e2e_t, t_match=t_match, stages=stages, clocks=clk.summary(), n_in=n_in, M=M,
-                K=K, pair=pair, h2d=int(hostA.numel() + hostB.numel()), bf=bf)
+                K=K, pair=pair, h2d=int(hostA.numel() + hostB.numel()), bf=bf, rescans=rescans)
 
 
 def main():
@@ -297,7 +298,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if r["bf"] else "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "H": H_IMG, "W": W_IMG, "Ls": list(LS), "K_per_image": K,
                        "precision": args.precision, "flush": "L2 flushed (256 MB write) between timed steps",
-                       "matches": r["M"], "inliers": r["n_in"], "Mpix_per_s": value * 2 * H_IMG * W_IMG / 1e6,
+                       "matches": r["M"], "inliers": r["n_in"], "rescanned_rows": r["rescans"], "Mpix_per_s": value * 2 * H_IMG * W_IMG / 1e6,
                        **r["stages"]},
             "roofline": roof,
             "e2e": {"value": world * args.steps / r["e2e_t"], "unit": "pairs/s", "h2d_bytes_per_step": r["h2d"],

@@ -215,6 +215,10 @@ LP_API const char* lp_last_error(lp_ctx* ctx);
 
 /* ---- diagnostics used by the test-suite (no paper counterpart needed) ---- */
 
+/* Rows that the last LP_PREC_BF16 lp_match of this context re-scanned in FP32
+ * because their BF16 ranking could not be certified (waits for the stream). */
+LP_API int lp_diag_last_rescans(lp_ctx* ctx, int64_t* out);
+
 /* Orientation bin of every integer gradient (a, b) in [-255, 255]^2, written
  * to device int32[511*511] at (a + 255) * 511 + (b + 255). */
 LP_API int lp_diag_orient_bins(int32_t* out, void* stream);

@@ -257,8 +257,13 @@ cudaError_t launch_match_fp32_rows(const float* A, long long NA_cap, const int32
                                    const float* nb, long long NB, int num_sms, float4* part, int* S_out,
                                    cudaStream_t s)
 {
+    // the row count is only known on the device and is usually a few percent
+    // of NA_cap: split the columns as finely as the partial layout allows so
+    // that a few row blocks still fill the GPU
     const long long rowblocks = (NA_cap + kTile - 1) / kTile;
-    const int S = pick_splits(rowblocks, NB, 2 * num_sms);
+    const long long maxS = (NB + kTile - 1) / kTile;
+    const int S = (int)(maxS < 32 ? maxS : 32);
+    (void)num_sms;
     *S_out = S;
     if (NA_cap == 0 || NB == 0) return cudaSuccess;
     const long long tiles = (NB + kTile - 1) / kTile;

@@ -55,9 +55,12 @@ constexpr int kThreadsTC = 320;         // 10 warps
 constexpr int kEpiWarps = 8;
 constexpr uint32_t kABytes = kRowsPerUnit * 128 * 2;   // 64 KB
 constexpr uint32_t kBBytes = kTileN * 128 * 2;         // 32 KB per stage
-constexpr uint32_t kSmemTC = kABytes + kStages * kBBytes + 1024 /*barriers*/ + 1024 /*align slack*/;
+constexpr uint32_t kNbBytes = kEpiWarps * kTileN * 4;   // per-warp copy of one tile's |b~|^2
+constexpr uint32_t kSmemTC = kABytes + kStages * kBBytes + kNbBytes + 1024 /*barriers*/ + 1024 /*align slack*/;
 constexpr int kTopK = 4;
-constexpr float kDelta = 3.0f / 256.0f + 3.0f / 65536.0f + 1e-4f;   // 3u + 3u^2 + FP32 allowance
+// 3u + 3u^2 (BF16 rounding) + FP32 accumulation allowance + the column tag
+// that the epilogue writes into the 5 low mantissa bits (<= 31 ulp)
+constexpr float kDelta = 3.0f / 256.0f + 3.0f / 65536.0f + 1e-4f + 1e-5f;
 
 // ------------------------------------------------------------------ PTX wrappers
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
@@ -167,9 +170,9 @@ __device__ __forceinline__ void mma_commit(uint32_t bar)
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v)
+// Issue a 32-column TMEM load (lane = row, 32 consecutive FP32 columns).
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
 {
-    uint32_t r[32];
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
         "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
@@ -179,9 +182,21 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v)
           "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
           "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
         : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Wait for this thread's outstanding TMEM loads.  The registers of the load
+// being waited for are in/out operands, so no use of them can be scheduled
+// above the wait.
+__device__ __forceinline__ void tmem_wait(uint32_t (&r)[32])
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                   "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
+                   "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),
+                   "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+                 :
+                 : "memory");
 }
 
 // ------------------------------------------------------------------ work split
@@ -206,17 +221,30 @@ __device__ __forceinline__ void unit_range(const TcParams& p, int u, int& rp, in
     ntiles = c1 > c0 ? (int)((c1 - c0 + kTileN - 1) / kTileN) : 0;
 }
 
-__device__ __forceinline__ void top4_insert(float x, int j, float (&v)[kTopK], int (&ix)[kTopK])
+// Sorted top-4 (ascending) in scalar registers.
+struct Top4 {
+    float v0, v1, v2, v3;
+    int j0, j1, j2, j3;
+};
+
+__device__ __forceinline__ void top4_insert(Top4& t, float x, int j)
 {
-    const bool c0 = x < v[0], c1 = x < v[1], c2 = x < v[2], c3 = x < v[3];
-    v[3] = c2 ? v[2] : (c3 ? x : v[3]);
-    ix[3] = c2 ? ix[2] : (c3 ? j : ix[3]);
-    v[2] = c1 ? v[1] : (c2 ? x : v[2]);
-    ix[2] = c1 ? ix[1] : (c2 ? j : ix[2]);
-    v[1] = c0 ? v[0] : (c1 ? x : v[1]);
-    ix[1] = c0 ? ix[0] : (c1 ? j : ix[1]);
-    v[0] = c0 ? x : v[0];
-    ix[0] = c0 ? j : ix[0];
+    const bool c0 = x < t.v0, c1 = x < t.v1, c2 = x < t.v2, c3 = x < t.v3;
+    t.v3 = c2 ? t.v2 : (c3 ? x : t.v3);
+    t.j3 = c2 ? t.j2 : (c3 ? j : t.j3);
+    t.v2 = c1 ? t.v1 : (c2 ? x : t.v2);
+    t.j2 = c1 ? t.j1 : (c2 ? j : t.j2);
+    t.v1 = c0 ? t.v0 : (c1 ? x : t.v1);
+    t.j1 = c0 ? t.j0 : (c1 ? j : t.j1);
+    t.v0 = c0 ? x : t.v0;
+    t.j0 = c0 ? j : t.j0;
+}
+
+// v with its 5 low mantissa bits replaced by the column's position i in the
+// chunk: the chunk minimum then also names its column.
+__device__ __forceinline__ float tag(float v, int i)
+{
+    return __uint_as_float((__float_as_uint(v) & ~31u) | (uint32_t)i);
 }
 
 __global__ void __launch_bounds__(kThreadsTC, 1)
@@ -226,7 +254,8 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t* sA = smem;
     uint8_t* sB = smem + kABytes;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kABytes + kStages * kBBytes);
+    float* snb = reinterpret_cast<float*>(smem + kABytes + kStages * kBBytes);   // [kEpiWarps][kTileN]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kABytes + kStages * kBBytes + kNbBytes);
     // barrier slots
     uint64_t* full = bars;                 // [kStages]
     uint64_t* empty = bars + kStages;      // [kStages]
@@ -381,44 +410,74 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
             unit_range(p, u, rp, split, c0, ntiles);
             long long c1 = c0 + p.cps;
             if (c1 > p.NB) c1 = p.NB;
-            float bv[kTopK] = {INFINITY, INFINITY, INFINITY, INFINITY};
-            int bj[kTopK] = {-1, -1, -1, -1};
+            Top4 tk{INFINITY, INFINITY, INFINITY, INFINITY, -1, -1, -1, -1};
+            float* wnb = snb + (warp - 2) * kTileN;
+            // |b~|^2 of tile t, lane l holding columns 4l .. 4l+3 (+inf past the split)
+            auto load_nb = [&](int t) {
+                const long long j = c0 + (long long)t * kTileN + 4 * lane;
+                if (j + 4 <= c1) return __ldg(reinterpret_cast<const float4*>(p.nb16 + j));
+                float4 w;
+                w.x = j + 0 < c1 ? __ldg(p.nb16 + j + 0) : INFINITY;
+                w.y = j + 1 < c1 ? __ldg(p.nb16 + j + 1) : INFINITY;
+                w.z = j + 2 < c1 ? __ldg(p.nb16 + j + 2) : INFINITY;
+                w.w = j + 3 < c1 ? __ldg(p.nb16 + j + 3) : INFINITY;
+                return w;
+            };
+            float4 nb_next = ntiles > 0 ? load_nb(0) : make_float4(0.f, 0.f, 0.f, 0.f);
             for (int t = 0; t < ntiles; ++t, ++n) {
                 const int b = (int)(n & 1);
                 const uint32_t kb = (uint32_t)(n >> 1);
+                // stage this tile's norms, start fetching the next tile's
+                __syncwarp();
+                const float4 nb_cur = nb_next;
+                reinterpret_cast<float4*>(wnb)[lane] = nb_cur;
+                if (t + 1 < ntiles) nb_next = load_nb(t + 1);
+                __syncwarp();
                 ok = mbar_wait(smem_u32(&tfull[b]), kb & 1, abort_flag, p.status);
                 if (!ok) break;
                 tc_fence_after();
                 const long long cbase = c0 + (long long)t * kTileN;
-#pragma unroll 1
+                const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)((b * 2 + rb) * kTileN);
+                uint32_t ra[32], rb2[32];
+                tmem_ld32(tbase, ra);
+                tmem_wait(ra);
+#pragma unroll
                 for (int ch = 0; ch < kTileN / 32; ++ch) {
-                    float acc[32];
-                    const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)((b * 2 + rb) * kTileN + ch * 32);
-                    tmem_ld32(taddr, acc);
-                    const long long j0 = cbase + ch * 32;
-                    float nbv[32];
-                    if (j0 + 32 <= c1) {
-                        const float4* src = reinterpret_cast<const float4*>(p.nb16 + j0);
+                    uint32_t (&cur)[32] = (ch & 1) ? rb2 : ra;
+                    uint32_t (&nxt)[32] = (ch & 1) ? ra : rb2;
+                    if (ch + 1 < kTileN / 32) tmem_ld32(tbase + (uint32_t)((ch + 1) * 32), nxt);
+                    // tagged v_j = |b~_j|^2 - 2 s_j and the chunk minimum
+                    float kv[32];
+                    const float4* nb4 = reinterpret_cast<const float4*>(wnb + ch * 32);
 #pragma unroll
-                        for (int i = 0; i < 8; ++i) {
-                            const float4 w = __ldg(src + i);
-                            nbv[4 * i] = w.x; nbv[4 * i + 1] = w.y; nbv[4 * i + 2] = w.z; nbv[4 * i + 3] = w.w;
-                        }
-                    } else {
-#pragma unroll
-                        for (int i = 0; i < 32; ++i) nbv[i] = (j0 + i < c1) ? __ldg(p.nb16 + j0 + i) : INFINITY;
+                    for (int i = 0; i < 8; ++i) {
+                        const float4 w = nb4[i];
+                        kv[4 * i + 0] = tag(fmaf(-2.f, __uint_as_float(cur[4 * i + 0]), w.x), 4 * i + 0);
+                        kv[4 * i + 1] = tag(fmaf(-2.f, __uint_as_float(cur[4 * i + 1]), w.y), 4 * i + 1);
+                        kv[4 * i + 2] = tag(fmaf(-2.f, __uint_as_float(cur[4 * i + 2]), w.z), 4 * i + 2);
+                        kv[4 * i + 3] = tag(fmaf(-2.f, __uint_as_float(cur[4 * i + 3]), w.w), 4 * i + 3);
                     }
-                    float mn = INFINITY;
+                    float m16[16];
 #pragma unroll
-                    for (int i = 0; i < 32; ++i) {
-                        acc[i] = fmaf(-2.f, acc[i], nbv[i]);
-                        mn = fminf(mn, acc[i]);
-                    }
-                    if (mn < bv[3]) {
+                    for (int i = 0; i < 16; ++i) m16[i] = fminf(kv[i], kv[i + 16]);
 #pragma unroll
-                        for (int i = 0; i < 32; ++i)
-                            if (acc[i] < bv[3]) top4_insert(acc[i], (int)(j0 + i), bv, bj);
+                    for (int i = 0; i < 8; ++i) m16[i] = fminf(m16[i], m16[i + 8]);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) m16[i] = fminf(m16[i], m16[i + 4]);
+                    float cand = fminf(fminf(m16[0], m16[2]), fminf(m16[1], m16[3]));
+                    // insert this row's qualifying columns, smallest first; the
+                    // loop runs only while some row of the warp still qualifies
+                    bool act = cand < tk.v3;
+                    const int j0 = (int)(cbase + ch * 32);
+                    while (__any_sync(0xFFFFFFFFu, act)) {
+                        if (act) top4_insert(tk, cand, j0 + (int)(__float_as_uint(cand) & 31u));
+                        float nx = INFINITY;
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) nx = fminf(nx, kv[i] > cand ? kv[i] : INFINITY);
+                        cand = nx;
+                        act = act && cand < tk.v3;
                     }
+                    if (ch + 1 < kTileN / 32) tmem_wait(nxt);
                 }
                 tc_fence_before();
                 __syncwarp();
@@ -427,8 +486,8 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
             if (!ok) break;
             const long long row = (long long)rp * kRowsPerUnit + row_in_unit;
             if (row < p.NA) {
-                p.pv[(long long)split * p.NA + row] = make_float4(bv[0], bv[1], bv[2], bv[3]);
-                p.pj[(long long)split * p.NA + row] = make_int4(bj[0], bj[1], bj[2], bj[3]);
+                p.pv[(long long)split * p.NA + row] = make_float4(tk.v0, tk.v1, tk.v2, tk.v3);
+                p.pj[(long long)split * p.NA + row] = make_int4(tk.j0, tk.j1, tk.j2, tk.j3);
             }
         }
     }
@@ -475,13 +534,17 @@ __device__ __forceinline__ float fp32_form_value(const float* a, const float* b,
 constexpr int kRerankWarps = 8;
 
 __global__ void __launch_bounds__(kRerankWarps * 32)
-k_rerank(const float* A, const float* B, const float* nb32, const float4* pv, const int4* pj, int S, long long NA,
-         float delta, float4* out_part, int32_t* rescan_rows, int32_t* rescan_count)
+k_rerank(const float* A, const uint8_t* vA, const float* B, const float* nb32, const float4* pv, const int4* pj, int S,
+         long long NA, float delta, float4* out_part, int32_t* rescan_rows, int32_t* rescan_count)
 {
     __shared__ __align__(16) float qa[kRerankWarps][128];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long i = (long long)blockIdx.x * kRerankWarps + warp;
     if (i >= NA) return;
+    if (!vA[i]) {   // an invalid query is never matched: nothing to rank
+        if (lane == 0) out_part[i] = make_float4(INFINITY, INFINITY, __int_as_float(-1), __int_as_float(-1));
+        return;
+    }
     reinterpret_cast<float4*>(qa[warp])[lane] = reinterpret_cast<const float4*>(A + i * 128)[lane];
     // gather the S x 4 candidates: lane c holds candidates 4c .. 4c+3 of split c (S <= 32)
     float cv[kTopK];
@@ -665,6 +728,17 @@ TcLayout tc_layout(long long NA, long long NB, int sms)
 
 size_t match_bf16_workspace(int64_t NA, int64_t NB, int num_sms) { return tc_layout(NA, NB, num_sms).total; }
 
+// Number of rows the last BF16 match re-scanned in FP32 (synchronous read).
+int64_t match_bf16_rescans(const void* ws, int64_t NA, int64_t NB, int num_sms, cudaStream_t s)
+{
+    const TcLayout L = tc_layout(NA, NB, num_sms);
+    const uint8_t* w = reinterpret_cast<const uint8_t*>((reinterpret_cast<uintptr_t>(ws) + 255) & ~uintptr_t(255));
+    int32_t c = -1;
+    if (cudaMemcpyAsync(&c, w + L.off_cnt, sizeof c, cudaMemcpyDeviceToHost, s) != cudaSuccess) return -1;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return -1;
+    return c;
+}
+
 cudaError_t launch_match_bf16(const MatchArgs& a, void* ws, size_t ws_bytes, int num_sms, cudaStream_t s)
 {
     if (a.NA == 0) return cudaSuccess;
@@ -710,7 +784,7 @@ cudaError_t launch_match_bf16(const MatchArgs& a, void* ws, size_t ws_bytes, int
         k_match_tc<<<grid, kThreadsTC, kSmemTC, s>>>(tA, tB, p);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         k_rerank<<<(unsigned)((a.NA + kRerankWarps - 1) / kRerankWarps), kRerankWarps * 32, 0, s>>>(
-            a.dA, a.dB, nb32, pv, pj, L.S, a.NA, kDelta, part1, rows, cnt);
+            a.dA, a.vA, a.dB, nb32, pv, pj, L.S, a.NA, kDelta, part1, rows, cnt);
         k_gather_rows<<<(unsigned)((a.NA * 32 + 255) / 256), 256, 0, s>>>(a.dA, rows, cnt, ar);
         int Sr = 0;
         if ((e = launch_match_fp32_rows(ar, a.NA, cnt, a.dB, nb32, a.NB, num_sms, part_r, &Sr, s)) != cudaSuccess)

@@ -195,8 +195,9 @@ __global__ void k_ransac_hyp(const float4* pts, long long M_cap, const int32_t* 
         if (!(fabs(A[p][c]) > 1e-10)) return;
         if (p != c)
             for (int j = 0; j < 9; ++j) { const double tmp = A[c][j]; A[c][j] = A[p][j]; A[p][j] = tmp; }
+        const double ip = 1.0 / A[c][c];
         for (int r = c + 1; r < 8; ++r) {
-            const double f = A[r][c] / A[c][c];
+            const double f = A[r][c] * ip;
             for (int j = c; j < 9; ++j) A[r][j] -= f * A[c][j];
         }
     }
@@ -246,13 +247,14 @@ k_ransac_score(const float4* pts, long long M_cap, const int32_t* dM, const doub
     int clo = 0, chi = 0;
     for (long long i = threadIdx.x; i < M; i += kScoreThreads) {
         const float4 p = pts[i];
+        // e^2 < t^2  <=>  |(u, v) - w p_B|^2 < t^2 w^2  for w > 0 (no division)
         const float w = fmaf(h[6], p.x, fmaf(h[7], p.y, h[8]));
         if (w > 0.f) {
-            const float u = fmaf(h[0], p.x, fmaf(h[1], p.y, h[2])) / w - p.z;
-            const float v = fmaf(h[3], p.x, fmaf(h[4], p.y, h[5])) / w - p.w;
-            const float e2 = u * u + v * v;
-            clo += e2 < t2 - eps;
-            chi += e2 < t2 + eps;
+            const float du = fmaf(-p.z, w, fmaf(h[0], p.x, fmaf(h[1], p.y, h[2])));
+            const float dv = fmaf(-p.w, w, fmaf(h[3], p.x, fmaf(h[4], p.y, h[5])));
+            const float d2 = du * du + dv * dv, w2 = w * w;
+            clo += d2 < (t2 - eps) * w2;
+            chi += d2 < (t2 + eps) * w2;
         }
     }
     clo = block_sum(clo, red);
@@ -260,15 +262,17 @@ k_ransac_score(const float4* pts, long long M_cap, const int32_t* dM, const doub
     if (threadIdx.x == 0) { lo[t] = clo; hi[t] = chi; }
 }
 
-// FP64 inlier test of one correspondence (Eq. 7, one-sided error in B).
+// FP64 inlier test of one correspondence (Eq. 7, one-sided error in B):
+// |pi(H p_A) - p_B|^2 < t^2, written for w > 0 as |(u, v) - w p_B|^2 < t^2 w^2,
+// which needs no division.
 __device__ __forceinline__ bool inlier64(const double* H, const float4& p, double t2)
 {
     const double x = p.x, y = p.y;
     const double w = H[6] * x + H[7] * y + H[8];
     if (!(w > 0)) return false;
-    const double u = (H[0] * x + H[1] * y + H[2]) / w - (double)p.z;
-    const double v = (H[3] * x + H[4] * y + H[5]) / w - (double)p.w;
-    return u * u + v * v < t2;
+    const double du = H[0] * x + H[1] * y + H[2] - (double)p.z * w;
+    const double dv = H[3] * x + H[4] * y + H[5] - (double)p.w * w;
+    return du * du + dv * dv < t2 * (w * w);
 }
 
 constexpr int kSelThreads = 1024;
@@ -382,14 +386,23 @@ __device__ void jacobi9_smallest_warp(double (*a)[9], double (*v)[9], double* h)
             off += __shfl_xor_sync(0xFFFFFFFFu, off, o);
             tot += __shfl_xor_sync(0xFFFFFFFFu, tot, o);
         }
-        if (off == 0 || off < 1e-30 * tot) break;
+        // converged: off-diagonal norm below 1e-14 of the total
+        if (off == 0 || off < 1e-28 * tot) break;
         for (int p = 0; p < 9; ++p)
             for (int q = p + 1; q < 9; ++q) {
                 const double apq = a[p][q];
                 if (apq == 0) continue;
-                const double th = (a[q][q] - a[p][p]) / (2.0 * apq);
-                const double t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
-                const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+                // one lane forms the rotation (FP64 division and square root are
+                // long instruction sequences); the others receive c and s
+                double c = 0, s = 0;
+                if (lane == 0) {
+                    const double th = (a[q][q] - a[p][p]) / (2.0 * apq);
+                    const double t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+                    c = 1.0 / sqrt(t * t + 1.0);
+                    s = t * c;
+                }
+                c = __shfl_sync(0xFFFFFFFFu, c, 0);
+                s = __shfl_sync(0xFFFFFFFFu, s, 0);
                 __syncwarp();
                 if (lane < 9) {
                     const double akp = a[lane][p], akq = a[lane][q];
@@ -423,7 +436,6 @@ k_ransac_refit(const float4* pts, long long M_cap, const int32_t* dM, const doub
     __shared__ double tot[45];
     __shared__ double A9[9][9], V9[9][9];
     __shared__ double hs[9], Hf[9];
-    __shared__ int ok_s;
     const long long M = m_count(dM, M_cap);
     const int best = *best_in;
     if (threadIdx.x == 0 && best_t) *best_t = best;
@@ -490,7 +502,6 @@ k_ransac_refit(const float4* pts, long long M_cap, const int32_t* dM, const doub
             double H[9];
             bool ok = good && denorm(na, nb, hs, H);
             for (int i = 0; i < 9; ++i) Hf[i] = ok ? H[i] : Hb[i];
-            ok_s = ok;
         }
     }
     __syncthreads();

@@ -28,6 +28,7 @@ enum BufId {
 
 struct lp_ctx {
     lp_config cfg;
+    int64_t last_NA = 0, last_NB = 0;   // sizes of the last BF16 match (for diagnostics)
     int device = 0;
     int num_sms = 0;
     int32_t* d_status = nullptr;
@@ -272,6 +273,8 @@ int lp_match(lp_ctx* c, const float* dA, const uint16_t* dA_bf16, const uint8_t*
         if (!aligned(dA_bf16, 16) || (dB_bf16 && !aligned(dB_bf16, 16))) return fail(c, LP_ERR_ALIGN, "bf16 alignment");
         int r = ensure(c, B_MATCH_WS, lp::match_bf16_workspace(NA, NB, c->num_sms));
         if (r) return r;
+        c->last_NA = NA;
+        c->last_NB = NB;
         LP_CUDA(c, lp::launch_match_bf16(a, c->buf[B_MATCH_WS].p, c->buf[B_MATCH_WS].n, c->num_sms, S(stream)));
         return LP_OK;
     }
@@ -397,6 +400,15 @@ int lp_sync_status(lp_ctx* c)
 }
 
 const char* lp_last_error(lp_ctx* c) { return c ? c->err : "null context"; }
+
+int lp_diag_last_rescans(lp_ctx* c, int64_t* out)
+{
+    if (!c || !out) return LP_ERR_ARG;
+    *out = 0;
+    if (c->cfg.precision != LP_PREC_BF16 || !c->buf[B_MATCH_WS].p || c->last_NA == 0) return LP_OK;
+    *out = lp::match_bf16_rescans(c->buf[B_MATCH_WS].p, c->last_NA, c->last_NB, c->num_sms, c->last);
+    return *out < 0 ? LP_ERR_CUDA : LP_OK;
+}
 
 int lp_diag_orient_bins(int32_t* out, void* stream)
 {

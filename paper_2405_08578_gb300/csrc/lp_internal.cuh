@@ -54,6 +54,7 @@ size_t match_fp32_workspace(int64_t NA, int64_t NB, int num_sms);
 cudaError_t launch_match_fp32(const MatchArgs& a, void* ws, size_t ws_bytes, int num_sms, cudaStream_t s);
 size_t match_bf16_workspace(int64_t NA, int64_t NB, int num_sms);
 cudaError_t launch_match_bf16(const MatchArgs& a, void* ws, size_t ws_bytes, int num_sms, cudaStream_t s);
+int64_t match_bf16_rescans(const void* ws, int64_t NA, int64_t NB, int num_sms, cudaStream_t s);
 
 // k_ransac.cu
 cudaError_t launch_compact(const uint32_t* kpA, int WA, const uint32_t* kpB, int WB, const int32_t* match,

@@ -37,7 +37,7 @@ class lp_config(C.Structure):
 _lib = None
 SYMBOLS = ["lp_config_default", "lp_create", "lp_destroy", "lp_num_keypoints", "lp_detect", "lp_describe",
            "lp_match", "lp_compact", "lp_ransac", "lp_ransac_static", "lp_stitch_pair", "lp_stitch_pair_host", "lp_sync_status",
-           "lp_last_error", "lp_diag_orient_bins", "lp_diag_orient_weights", "lp_diag_philox", "lp_diag_gray"]
+           "lp_last_error", "lp_diag_last_rescans", "lp_diag_orient_bins", "lp_diag_orient_weights", "lp_diag_philox", "lp_diag_gray"]
 
 
 def lib_path() -> str:
@@ -70,6 +70,7 @@ def load(build_if_missing: bool = True):
         "lp_stitch_pair_host": (i32, [P, P, i32, i32, i32, P, i32, i32, i32, i32, u32, P, P, P, P]),
         "lp_sync_status": (i32, [P]),
         "lp_last_error": (C.c_char_p, [P]),
+        "lp_diag_last_rescans": (i32, [P, C.POINTER(C.c_int64)]),
         "lp_diag_orient_bins": (i32, [P, P]),
         "lp_diag_orient_weights": (i32, [P, P]),
         "lp_diag_philox": (i32, [P, i64, u32, u32, P, P]),
@@ -184,6 +185,11 @@ class Context:
 
     def lp_sync_status(self):
         return self.lib.lp_sync_status(self.h)
+
+    def lp_diag_last_rescans(self) -> int:
+        v = C.c_int64()
+        self._chk(self.lib.lp_diag_last_rescans(self.h, C.byref(v)), "lp_diag_last_rescans")
+        return v.value
 
 
 def lp_num_keypoints(H, W, Ls) -> int:
