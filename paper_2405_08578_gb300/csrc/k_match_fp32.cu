@@ -251,28 +251,4 @@ cudaError_t launch_match_fp32(const MatchArgs& a, void* ws, size_t ws_bytes, int
     return cudaGetLastError();
 }
 
-// FP32 re-scan of up to NA_cap rows whose count lives on the device (rows of
-// the BF16 path that could not be certified).  part: [S][NA_cap].
-cudaError_t launch_match_fp32_rows(const float* A, long long NA_cap, const int32_t* d_rows, const float* B,
-                                   const float* nb, long long NB, int num_sms, float4* part, int* S_out,
-                                   cudaStream_t s)
-{
-    // the row count is only known on the device and is usually a few percent
-    // of NA_cap: split the columns as finely as the partial layout allows so
-    // that a few row blocks still fill the GPU
-    const long long rowblocks = (NA_cap + kTile - 1) / kTile;
-    const long long maxS = (NB + kTile - 1) / kTile;
-    const int S = (int)(maxS < 32 ? maxS : 32);
-    (void)num_sms;
-    *S_out = S;
-    if (NA_cap == 0 || NB == 0) return cudaSuccess;
-    const long long tiles = (NB + kTile - 1) / kTile;
-    const long long cps = ((tiles + S - 1) / S) * kTile;
-    const size_t smem = smem_bytes();
-    cudaFuncSetAttribute(k_match_fp32_main, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    dim3 grid((unsigned)rowblocks, (unsigned)S);
-    k_match_fp32_main<<<grid, kThreads, smem, s>>>(A, NA_cap, d_rows, B, nb, NB, S, cps, part);
-    return cudaGetLastError();
-}
-
 }  // namespace lp

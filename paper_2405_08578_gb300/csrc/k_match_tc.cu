@@ -13,7 +13,7 @@
 //             B stage and hands the buffer to the epilogue.
 //   warps 2-9 epilogue: each thread owns one A row, reads its 128 FP32 dot
 //             products per tile with tcgen05.ld (32x32b.x32), forms
-//             v = |b~|^2 - 2 a~.b~ and keeps the row's 4 smallest v in
+//             v = |b~|^2 - 2 a~.b~ and keeps the row's 8 smallest v in
 //             registers; no distance matrix is written.
 //   A work unit is (256-row block of A, one of S column splits of B); units
 //   are dealt round-robin to the persistent CTAs.  Every mbarrier wait is
@@ -25,12 +25,12 @@
 //   with exactly the FP32 form's arithmetic (sequential FMA over k, then
 //   fma(-2, dot, |b|^2)), so their values are bit-identical to the FP32
 //   form's.  With unit, non-negative descriptors and BF16 unit roundoff
-//   u = 2^-8, |v~_j - v_j| <= 3u + u^2 + 4e-5 = delta for every column j
+//   u = 2^-8, |v~_j - v_j| <= 3u + 3u^2 + 1.1e-4 = delta for every column j
 //   (derivation in the design doc).  The row is certified when the smallest
-//   fourth-best BF16 value over the splits, minus delta, exceeds the exact
+//   eighth-best BF16 value over the splits, minus delta, exceeds the exact
 //   second-best: then no column outside the candidates can enter the top 2.
 //   Uncertified rows are queued.
-// Stage 3: queued rows are gathered and re-scanned by the FP32 SIMT kernel.
+// Stage 3: queued rows are re-scanned with the FP32 form's arithmetic.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -42,9 +42,6 @@ namespace lp {
 __global__ void k_row_norms(const float* d, const uint8_t* v, long long n, float* out, float invalid_value);
 __global__ void k_match_finish(const float4* part, int S, long long NA, const float* na, const uint8_t* vA,
                                float ratio2, float delta_s2, int32_t* match, float* d1, float* d2);
-cudaError_t launch_match_fp32_rows(const float* A, long long NA_cap, const int32_t* d_rows, const float* B,
-                                   const float* nb, long long NB, int num_sms, float4* part, int* S_out,
-                                   cudaStream_t s);
 
 namespace {
 
@@ -57,7 +54,7 @@ constexpr uint32_t kABytes = kRowsPerUnit * 128 * 2;   // 64 KB
 constexpr uint32_t kBBytes = kTileN * 128 * 2;         // 32 KB per stage
 constexpr uint32_t kNbBytes = kEpiWarps * kTileN * 4;   // per-warp copy of one tile's |b~|^2
 constexpr uint32_t kSmemTC = kABytes + kStages * kBBytes + kNbBytes + 1024 /*barriers*/ + 1024 /*align slack*/;
-constexpr int kTopK = 4;
+constexpr int kTopK = 8;
 // 3u + 3u^2 (BF16 rounding) + FP32 accumulation allowance + the column tag
 // that the epilogue writes into the 5 low mantissa bits (<= 31 ulp)
 constexpr float kDelta = 3.0f / 256.0f + 3.0f / 65536.0f + 1e-4f + 1e-5f;
@@ -206,38 +203,44 @@ struct TcParams {
     int S;                 // column splits
     long long cps;         // columns per split (multiple of kTileN)
     const float* nb16;     // |b~_j|^2 (+inf when invalid), length NB
-    float4* pv;            // [S][NA] four smallest values
-    int4* pj;              // [S][NA] their columns (-1 = none)
+    float4* pv;            // [S][NA][2] the kTopK smallest values
+    int4* pj;              // [S][NA][2] their columns (-1 = none)
     int32_t* status;
 };
 
+// Unit u = (256-row block rp, column split): consecutive units share a row
+// block, and each CTA takes a contiguous run of units, so the A block is
+// usually reused and each split's list can start from the previous split's
+// k-th best.
 __device__ __forceinline__ void unit_range(const TcParams& p, int u, int& rp, int& split, long long& c0, int& ntiles)
 {
-    rp = u % p.nrp;
-    split = u / p.nrp;
+    rp = u / p.S;
+    split = u - rp * p.S;
     c0 = (long long)split * p.cps;
     long long c1 = c0 + p.cps;
     if (c1 > p.NB) c1 = p.NB;
     ntiles = c1 > c0 ? (int)((c1 - c0 + kTileN - 1) / kTileN) : 0;
 }
 
-// Sorted top-4 (ascending) in scalar registers.
-struct Top4 {
-    float v0, v1, v2, v3;
-    int j0, j1, j2, j3;
+// Sorted top-k (ascending) in registers; every index is a compile-time
+// constant after unrolling.
+struct TopK {
+    float v[kTopK];
+    int j[kTopK];
 };
 
-__device__ __forceinline__ void top4_insert(Top4& t, float x, int j)
+__device__ __forceinline__ void topk_insert(TopK& t, float x, int jx)
 {
-    const bool c0 = x < t.v0, c1 = x < t.v1, c2 = x < t.v2, c3 = x < t.v3;
-    t.v3 = c2 ? t.v2 : (c3 ? x : t.v3);
-    t.j3 = c2 ? t.j2 : (c3 ? j : t.j3);
-    t.v2 = c1 ? t.v1 : (c2 ? x : t.v2);
-    t.j2 = c1 ? t.j1 : (c2 ? j : t.j2);
-    t.v1 = c0 ? t.v0 : (c1 ? x : t.v1);
-    t.j1 = c0 ? t.j0 : (c1 ? j : t.j1);
-    t.v0 = c0 ? x : t.v0;
-    t.j0 = c0 ? j : t.j0;
+    bool c[kTopK];
+#pragma unroll
+    for (int i = 0; i < kTopK; ++i) c[i] = x < t.v[i];
+#pragma unroll
+    for (int i = kTopK - 1; i > 0; --i) {
+        t.v[i] = c[i - 1] ? t.v[i - 1] : (c[i] ? x : t.v[i]);
+        t.j[i] = c[i - 1] ? t.j[i - 1] : (c[i] ? jx : t.j[i]);
+    }
+    t.v[0] = c[0] ? x : t.v[0];
+    t.j[0] = c[0] ? jx : t.j[0];
 }
 
 // v with its 5 low mantissa bits replaced by the column's position i in the
@@ -269,6 +272,9 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int U = p.nrp * p.S;
+    const int per = U / (int)gridDim.x, rem = U % (int)gridDim.x;
+    const int u_begin = (int)blockIdx.x * per + min((int)blockIdx.x, rem);
+    const int u_end = u_begin + per + ((int)blockIdx.x < rem ? 1 : 0);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
@@ -306,17 +312,22 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
             int a_armed = -1;
             for (int s = 0; s < kStages; ++s) armed[s] = -1;
             bool ok = true;
-            for (int u = blockIdx.x; u < U && ok; u += gridDim.x) {
+            int prev_rp = -1;
+            for (int u = u_begin; u < u_end && ok; ++u) {
                 int rp, split, ntiles;
                 long long c0;
                 unit_range(p, u, rp, split, c0, ntiles);
                 if (ntiles == 0) continue;
-                ok = mbar_wait(smem_u32(aempty), (v & 1) ^ 1, abort_flag, p.status);
-                if (!ok) break;
-                mbar_expect_tx(smem_u32(afull), kABytes);
-                tma_load_2d(smem_u32(sA), &tmA, 0, rp * kRowsPerUnit, smem_u32(afull));
-                tma_load_2d(smem_u32(sA + kABytes / 2), &tmA, 64, rp * kRowsPerUnit, smem_u32(afull));
-                a_armed = v;
+                if (rp != prev_rp) {
+                    ok = mbar_wait(smem_u32(aempty), (v & 1) ^ 1, abort_flag, p.status);
+                    if (!ok) break;
+                    mbar_expect_tx(smem_u32(afull), kABytes);
+                    tma_load_2d(smem_u32(sA), &tmA, 0, rp * kRowsPerUnit, smem_u32(afull));
+                    tma_load_2d(smem_u32(sA + kABytes / 2), &tmA, 64, rp * kRowsPerUnit, smem_u32(afull));
+                    a_armed = v;
+                    ++v;
+                    prev_rp = rp;
+                }
                 for (int t = 0; t < ntiles; ++t, ++n) {
                     const int s = (int)(n % kStages);
                     const uint32_t k = (uint32_t)(n / kStages);
@@ -329,7 +340,6 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
                     tma_load_2d(smem_u32(dst + kBBytes / 2), &tmB, 64, y, smem_u32(&full[s]));
                     armed[s] = (int)k;
                 }
-                ++v;
             }
             if (!ok) {
                 // drain: wait (bounded) for the copies this thread issued to land
@@ -352,15 +362,22 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
             long long n = 0;
             int v = 0;
             bool ok = true;
-            for (int u = blockIdx.x; u < U && ok; u += gridDim.x) {
+            int prev_rp = -1;
+            for (int u = u_begin; u < u_end && ok; ++u) {
                 int rp, split, ntiles;
                 long long c0;
                 unit_range(p, u, rp, split, c0, ntiles);
                 if (ntiles == 0) continue;
-                ok = mbar_wait(smem_u32(afull), v & 1, abort_flag, p.status);
-                ++v;
-                if (!ok) break;
-                tc_fence_after();
+                if (rp != prev_rp) {
+                    // release the previous A block once its MMAs are done, then
+                    // wait for the new one
+                    if (v > 0) mma_commit(smem_u32(aempty));
+                    ok = mbar_wait(smem_u32(afull), v & 1, abort_flag, p.status);
+                    ++v;
+                    prev_rp = rp;
+                    if (!ok) break;
+                    tc_fence_after();
+                }
                 for (int t = 0; t < ntiles; ++t, ++n) {
                     const int s = (int)(n % kStages);
                     const uint32_t k = (uint32_t)(n / kStages);
@@ -388,8 +405,6 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
                     mma_commit(smem_u32(&empty[s]));
                     mma_commit(smem_u32(&tfull[b]));
                 }
-                if (!ok) break;
-                mma_commit(smem_u32(aempty));
             }
             // wait (bounded) for every MMA this thread issued before TMEM is freed
             mma_commit(smem_u32(drain));
@@ -404,13 +419,22 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
         const int row_in_unit = rb * 128 + q * 32 + lane;
         long long n = 0;
         bool ok = true;
-        for (int u = blockIdx.x; u < U && ok; u += gridDim.x) {
+        int prev_rp = -1;
+        float warm = INFINITY;
+        for (int u = u_begin; u < u_end && ok; ++u) {
             int rp, split, ntiles;
             long long c0;
             unit_range(p, u, rp, split, c0, ntiles);
             long long c1 = c0 + p.cps;
             if (c1 > p.NB) c1 = p.NB;
-            Top4 tk{INFINITY, INFINITY, INFINITY, INFINITY, -1, -1, -1, -1};
+            // a split of the same row block starts from the previous split's
+            // k-th best: placeholders (column -1) at that value.  Columns never
+            // stored are then still >= the list's last value, the bound the
+            // re-rank uses.
+            const float t0 = (rp == prev_rp && ntiles > 0) ? warm : INFINITY;
+            TopK tk;
+#pragma unroll
+            for (int i = 0; i < kTopK; ++i) { tk.v[i] = t0; tk.j[i] = -1; }
             float* wnb = snb + (warp - 2) * kTileN;
             // |b~|^2 of tile t, lane l holding columns 4l .. 4l+3 (+inf past the split)
             auto load_nb = [&](int t) {
@@ -467,15 +491,15 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
                     float cand = fminf(fminf(m16[0], m16[2]), fminf(m16[1], m16[3]));
                     // insert this row's qualifying columns, smallest first; the
                     // loop runs only while some row of the warp still qualifies
-                    bool act = cand < tk.v3;
+                    bool act = cand < tk.v[kTopK - 1];
                     const int j0 = (int)(cbase + ch * 32);
                     while (__any_sync(0xFFFFFFFFu, act)) {
-                        if (act) top4_insert(tk, cand, j0 + (int)(__float_as_uint(cand) & 31u));
+                        if (act) topk_insert(tk, cand, j0 + (int)(__float_as_uint(cand) & 31u));
                         float nx = INFINITY;
 #pragma unroll
                         for (int i = 0; i < 32; ++i) nx = fminf(nx, kv[i] > cand ? kv[i] : INFINITY);
                         cand = nx;
-                        act = act && cand < tk.v3;
+                        act = act && cand < tk.v[kTopK - 1];
                     }
                     if (ch + 1 < kTileN / 32) tmem_wait(nxt);
                 }
@@ -486,8 +510,16 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
             if (!ok) break;
             const long long row = (long long)rp * kRowsPerUnit + row_in_unit;
             if (row < p.NA) {
-                p.pv[(long long)split * p.NA + row] = make_float4(tk.v0, tk.v1, tk.v2, tk.v3);
-                p.pj[(long long)split * p.NA + row] = make_int4(tk.j0, tk.j1, tk.j2, tk.j3);
+                float4* pv = p.pv + ((long long)split * p.NA + row) * 2;
+                int4* pj = p.pj + ((long long)split * p.NA + row) * 2;
+                pv[0] = make_float4(tk.v[0], tk.v[1], tk.v[2], tk.v[3]);
+                pv[1] = make_float4(tk.v[4], tk.v[5], tk.v[6], tk.v[7]);
+                pj[0] = make_int4(tk.j[0], tk.j[1], tk.j[2], tk.j[3]);
+                pj[1] = make_int4(tk.j[4], tk.j[5], tk.j[6], tk.j[7]);
+            }
+            if (ntiles > 0) {
+                prev_rp = rp;
+                warm = tk.v[kTopK - 1];
             }
         }
     }
@@ -549,13 +581,17 @@ k_rerank(const float* A, const uint8_t* vA, const float* B, const float* nb32, c
     // gather the S x 4 candidates: lane c holds candidates 4c .. 4c+3 of split c (S <= 32)
     float cv[kTopK];
     int cj[kTopK];
-    float t4 = INFINITY;   // smallest fourth-best value over the splits
+    float t4 = INFINITY;   // smallest k-th best value over the splits
     if (lane < S) {
-        const float4 v = pv[(long long)lane * NA + i];
-        const int4 j = pj[(long long)lane * NA + i];
-        cv[0] = v.x; cv[1] = v.y; cv[2] = v.z; cv[3] = v.w;
-        cj[0] = j.x; cj[1] = j.y; cj[2] = j.z; cj[3] = j.w;
-        t4 = v.w;
+        const float4* v = pv + ((long long)lane * NA + i) * 2;
+        const int4* j = pj + ((long long)lane * NA + i) * 2;
+        const float4 v0 = v[0], v1 = v[1];
+        const int4 j0 = j[0], j1 = j[1];
+        cv[0] = v0.x; cv[1] = v0.y; cv[2] = v0.z; cv[3] = v0.w;
+        cv[4] = v1.x; cv[5] = v1.y; cv[6] = v1.z; cv[7] = v1.w;
+        cj[0] = j0.x; cj[1] = j0.y; cj[2] = j0.z; cj[3] = j0.w;
+        cj[4] = j1.x; cj[5] = j1.y; cj[6] = j1.z; cj[7] = j1.w;
+        t4 = v1.w;
     } else {
 #pragma unroll
         for (int k = 0; k < kTopK; ++k) { cv[k] = INFINITY; cj[k] = -1; }
@@ -621,37 +657,132 @@ k_rerank(const float* A, const uint8_t* vA, const float* B, const float* nb32, c
     }
 }
 
-// Gather the queued A rows (FP32) into a dense block for the FP32 re-scan.
-__global__ void k_gather_rows(const float* A, const int32_t* rows, const int32_t* count, float* out)
+// FP32 re-scan of the queued rows.  A CTA owns a chunk of B columns (one
+// column per thread) and a group of up to kRescanRows queued rows (in shared
+// memory); each thread reads its column once and forms the FP32 form's value
+// for every row of the group (per row: sequential FMA over k, then
+// fma(-2, dot, |b|^2)).  Per row, the CTA keeps the chunk's two smallest
+// (value, column) pairs.
+constexpr int kRescanThreads = 128;
+constexpr int kRescanRows = 32;
+
+__device__ __forceinline__ void top2_lex(float& b1, int& j1, float& b2, int& j2, float x, int j)
 {
-    const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (w >= *count) return;
-    reinterpret_cast<float4*>(out + w * 128)[lane] = reinterpret_cast<const float4*>(A + (long long)rows[w] * 128)[lane];
+    if (j < 0) return;
+    if (x < b1 || (x == b1 && (unsigned)j < (unsigned)j1)) {
+        b2 = b1; j2 = j1; b1 = x; j1 = j;
+    } else if (x < b2 || (x == b2 && (unsigned)j < (unsigned)j2)) {
+        b2 = x; j2 = j;
+    }
+}
+
+constexpr int kRescanGroups = 64;   // column groups per queued row (partials per row)
+
+__global__ void __launch_bounds__(kRescanThreads)
+k_rescan(const float* A, const float* B, const float* nb32, long long NB, const int32_t* rows, const int32_t* count,
+         float4* part_r)
+{
+    __shared__ __align__(16) float qa[kRescanRows][128];
+    __shared__ float sv[kRescanRows][kRescanThreads];
+    __shared__ float4 run[kRescanRows];   // running (b1, b2, j1, j2) per row
+    const int R = *count;
+    const int groups = (R + kRescanRows - 1) / kRescanRows;
+    const long long items = (long long)groups * kRescanGroups;
+    const long long nchunks = (NB + kRescanThreads - 1) / kRescanThreads;
+    const long long cpg = (nchunks + kRescanGroups - 1) / kRescanGroups;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (long long it = blockIdx.x; it < items; it += gridDim.x) {
+        const int g = (int)(it / kRescanGroups);
+        const int cg = (int)(it - (long long)g * kRescanGroups);
+        const int r0 = g * kRescanRows, nr = min(kRescanRows, R - r0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < nr * 32; e += kRescanThreads) {
+            const int r = e >> 5, q = e & 31;
+            reinterpret_cast<float4*>(qa[r])[q] = reinterpret_cast<const float4*>(A + (long long)rows[r0 + r] * 128)[q];
+        }
+        if (threadIdx.x < kRescanRows)
+            run[threadIdx.x] = make_float4(INFINITY, INFINITY, __int_as_float(-1), __int_as_float(-1));
+        for (long long ch = (long long)cg * cpg; ch < min(nchunks, (long long)(cg + 1) * cpg); ++ch) {
+            __syncthreads();
+            const long long j = ch * kRescanThreads + threadIdx.x;
+            const bool colok = j < NB && !isinf(__ldg(nb32 + (j < NB ? j : 0)));
+            if (colok) {
+                float acc[kRescanRows];
+#pragma unroll
+                for (int r = 0; r < kRescanRows; ++r) acc[r] = 0.f;
+                const float4* b4 = reinterpret_cast<const float4*>(B + j * 128);
+#pragma unroll 2
+                for (int k4 = 0; k4 < 32; ++k4) {
+                    const float4 w = __ldg(b4 + k4);
+#pragma unroll
+                    for (int r = 0; r < kRescanRows; ++r) {
+                        const float4 a = reinterpret_cast<const float4*>(qa[r])[k4];
+                        acc[r] = fmaf(a.x, w.x, acc[r]);
+                        acc[r] = fmaf(a.y, w.y, acc[r]);
+                        acc[r] = fmaf(a.z, w.z, acc[r]);
+                        acc[r] = fmaf(a.w, w.w, acc[r]);
+                    }
+                }
+                const float nbj = __ldg(nb32 + j);
+#pragma unroll
+                for (int r = 0; r < kRescanRows; ++r) sv[r][threadIdx.x] = fmaf(-2.f, acc[r], nbj);
+            } else {
+#pragma unroll
+                for (int r = 0; r < kRescanRows; ++r) sv[r][threadIdx.x] = INFINITY;
+            }
+            __syncthreads();
+            // warp w merges rows w, w + 4, ... of this chunk into the running lists
+            for (int r = warp; r < nr; r += kRescanThreads / 32) {
+                float b1 = INFINITY, b2 = INFINITY;
+                int j1 = -1, j2 = -1;
+                for (int c = lane; c < kRescanThreads; c += 32) {
+                    const float x = sv[r][c];
+                    if (!isinf(x)) top2_lex(b1, j1, b2, j2, x, (int)(ch * kRescanThreads + c));
+                }
+#pragma unroll
+                for (int o = 16; o; o >>= 1) {
+                    const float ob1 = __shfl_xor_sync(0xFFFFFFFFu, b1, o), ob2 = __shfl_xor_sync(0xFFFFFFFFu, b2, o);
+                    const int oj1 = __shfl_xor_sync(0xFFFFFFFFu, j1, o), oj2 = __shfl_xor_sync(0xFFFFFFFFu, j2, o);
+                    top2_lex(b1, j1, b2, j2, ob1, oj1);
+                    top2_lex(b1, j1, b2, j2, ob2, oj2);
+                }
+                if (lane == 0) {
+                    float4 q = run[r];
+                    float c1 = q.x, c2 = q.y;
+                    int i1 = __float_as_int(q.z), i2 = __float_as_int(q.w);
+                    top2_lex(c1, i1, c2, i2, b1, j1);
+                    top2_lex(c1, i1, c2, i2, b2, j2);
+                    run[r] = make_float4(c1, c2, __int_as_float(i1), __int_as_float(i2));
+                }
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x < nr) part_r[(long long)(r0 + threadIdx.x) * kRescanGroups + cg] = run[threadIdx.x];
+    }
 }
 
 // Merge the re-scan partials of queued row r into the row's single partial.
-__global__ void k_rescan_merge(const float4* part, int S, long long cap, const int32_t* rows, const int32_t* count,
+__global__ void k_rescan_merge(const float4* part_r, int nchunks, const int32_t* rows, const int32_t* count,
                                float4* out_part)
 {
-    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long r = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
     if (r >= *count) return;
     float b1 = INFINITY, b2 = INFINITY;
     int j1 = -1, j2 = -1;
-    for (int s = 0; s < S; ++s) {
-        const float4 q = part[(long long)s * cap + r];
-        for (int t = 0; t < 2; ++t) {
-            const float x = t ? q.y : q.x;
-            const int j = __float_as_int(t ? q.w : q.z);
-            if (j < 0) continue;
-            if (x < b1 || (x == b1 && j < j1)) {
-                b2 = b1; j2 = j1; b1 = x; j1 = j;
-            } else if (x < b2 || (x == b2 && j < j2)) {
-                b2 = x; j2 = j;
-            }
-        }
+    for (int c = lane; c < nchunks; c += 32) {
+        const float4 q = part_r[r * nchunks + c];
+        top2_lex(b1, j1, b2, j2, q.x, __float_as_int(q.z));
+        top2_lex(b1, j1, b2, j2, q.y, __float_as_int(q.w));
     }
-    out_part[rows[r]] = make_float4(b1, b2, __int_as_float(j1), __int_as_float(j2));
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        const float ob1 = __shfl_xor_sync(0xFFFFFFFFu, b1, o), ob2 = __shfl_xor_sync(0xFFFFFFFFu, b2, o);
+        const int oj1 = __shfl_xor_sync(0xFFFFFFFFu, j1, o), oj2 = __shfl_xor_sync(0xFFFFFFFFu, j2, o);
+        top2_lex(b1, j1, b2, j2, ob1, oj1);
+        top2_lex(b1, j1, b2, j2, ob2, oj2);
+    }
+    if (lane == 0) out_part[rows[r]] = make_float4(b1, b2, __int_as_float(j1), __int_as_float(j2));
 }
 
 // ------------------------------------------------------------------ host side
@@ -700,7 +831,7 @@ int pick_tc_splits(int nrp, long long NB, int sms)
 
 struct TcLayout {
     int S;
-    size_t off_nb16, off_na, off_nb32, off_pv, off_pj, off_part1, off_rows, off_cnt, off_ar, off_part_r, total;
+    size_t off_nb16, off_na, off_nb32, off_pv, off_pj, off_part1, off_rows, off_cnt, off_part_r, total;
 };
 
 TcLayout tc_layout(long long NA, long long NB, int sms)
@@ -713,13 +844,12 @@ TcLayout tc_layout(long long NA, long long NB, int sms)
     L.off_nb16 = take(sizeof(float) * (size_t)NB + 64);
     L.off_na = take(sizeof(float) * (size_t)NA);
     L.off_nb32 = take(sizeof(float) * (size_t)NB);
-    L.off_pv = take(sizeof(float4) * (size_t)L.S * NA);
-    L.off_pj = take(sizeof(int4) * (size_t)L.S * NA);
+    L.off_pv = take(sizeof(float4) * 2 * (size_t)L.S * NA);
+    L.off_pj = take(sizeof(int4) * 2 * (size_t)L.S * NA);
     L.off_part1 = take(sizeof(float4) * (size_t)NA);
     L.off_rows = take(sizeof(int32_t) * (size_t)NA);
     L.off_cnt = take(64);
-    L.off_ar = take(sizeof(float) * 128 * (size_t)NA);
-    L.off_part_r = take(sizeof(float4) * 32 * (size_t)NA);
+    L.off_part_r = take(sizeof(float4) * kRescanGroups * (size_t)NA);
     L.total = o + 256;
     return L;
 }
@@ -753,7 +883,6 @@ cudaError_t launch_match_bf16(const MatchArgs& a, void* ws, size_t ws_bytes, int
     float4* part1 = reinterpret_cast<float4*>(w + L.off_part1);
     int32_t* rows = reinterpret_cast<int32_t*>(w + L.off_rows);
     int32_t* cnt = reinterpret_cast<int32_t*>(w + L.off_cnt);
-    float* ar = reinterpret_cast<float*>(w + L.off_ar);
     float4* part_r = reinterpret_cast<float4*>(w + L.off_part_r);
     cudaError_t e;
     if ((e = cudaMemsetAsync(cnt, 0, sizeof(int32_t), s)) != cudaSuccess) return e;
@@ -785,11 +914,8 @@ cudaError_t launch_match_bf16(const MatchArgs& a, void* ws, size_t ws_bytes, int
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         k_rerank<<<(unsigned)((a.NA + kRerankWarps - 1) / kRerankWarps), kRerankWarps * 32, 0, s>>>(
             a.dA, a.vA, a.dB, nb32, pv, pj, L.S, a.NA, kDelta, part1, rows, cnt);
-        k_gather_rows<<<(unsigned)((a.NA * 32 + 255) / 256), 256, 0, s>>>(a.dA, rows, cnt, ar);
-        int Sr = 0;
-        if ((e = launch_match_fp32_rows(ar, a.NA, cnt, a.dB, nb32, a.NB, num_sms, part_r, &Sr, s)) != cudaSuccess)
-            return e;
-        k_rescan_merge<<<(unsigned)((a.NA + 255) / 256), 256, 0, s>>>(part_r, Sr, a.NA, rows, cnt, part1);
+        k_rescan<<<(unsigned)(4 * num_sms), kRescanThreads, 0, s>>>(a.dA, a.dB, nb32, a.NB, rows, cnt, part_r);
+        k_rescan_merge<<<(unsigned)((a.NA + 7) / 8), 256, 0, s>>>(part_r, kRescanGroups, rows, cnt, part1);
         k_match_finish<<<(unsigned)((a.NA + 255) / 256), 256, 0, s>>>(part1, 1, a.NA, na, a.vA, a.ratio2, a.delta_s2,
                                                                       a.match, a.d1, a.d2);
     } else {

@@ -17,6 +17,8 @@
 //                 smallest eigenvector, denormalisation, final FP64 mask.
 #include <math.h>
 
+#include <algorithm>
+
 #include "lp_internal.cuh"
 
 namespace lp {
@@ -335,11 +337,19 @@ k_ransac_select(const float4* pts, long long M_cap, const int32_t* dM, int T, co
 }
 
 // ---------------------------------------------------------------- refit
+// Least-squares refit of the winner's inliers (Eq. 7), spread over kRefitCTAs
+// CTAs.  Each pass writes per-CTA partial sums; the next pass reduces them in
+// a fixed order, so results do not depend on scheduling.
 constexpr int kRefitThreads = 256;
 constexpr int kRefitWarps = kRefitThreads / 32;
+constexpr int kRefitCTAs = 32;
+constexpr int kPartStride = 64;   // doubles per CTA partial row
 
-// Sum N per-thread doubles over the CTA in one pass: warp shuffles, then the
-// warps' partials in a fixed order.  Every thread receives the N totals.
+struct RefitWS {
+    double* part;     // [kRefitCTAs][kPartStride]
+    double* Hf;       // [9] refitted homography
+};
+
 template <int N>
 __device__ void block_sum_n(double* v, double (*part)[N], double* tot)
 {
@@ -363,119 +373,116 @@ __device__ void block_sum_n(double* v, double (*part)[N], double* tot)
     __syncthreads();
 }
 
-// Cyclic Jacobi eigen-decomposition of the symmetric 9x9 matrix `a` (shared
-// memory) by one warp: the rotation sequence of the sequential algorithm, each
-// rotation's row/column updates spread over lanes 0..8.  Writes the
-// eigenvector of the smallest eigenvalue to h.
-__device__ void jacobi9_smallest_warp(double (*a)[9], double (*v)[9], double* h)
+__device__ __forceinline__ void cta_range(long long M, long long& b, long long& e)
 {
-    const int lane = threadIdx.x & 31;
-    if (lane < 9)
-        for (int j = 0; j < 9; ++j) v[lane][j] = lane == j;
-    __syncwarp();
-    for (int sweep = 0; sweep < 100; ++sweep) {
-        double off = 0, tot = 0;
-        if (lane < 9)
-            for (int j = 0; j < 9; ++j) {
-                const double x = a[lane][j] * a[lane][j];
-                tot += x;
-                if (j != lane) off += x;
-            }
-#pragma unroll
-        for (int o = 16; o; o >>= 1) {
-            off += __shfl_xor_sync(0xFFFFFFFFu, off, o);
-            tot += __shfl_xor_sync(0xFFFFFFFFu, tot, o);
-        }
-        // converged: off-diagonal norm below 1e-14 of the total
-        if (off == 0 || off < 1e-28 * tot) break;
-        for (int p = 0; p < 9; ++p)
-            for (int q = p + 1; q < 9; ++q) {
-                const double apq = a[p][q];
-                if (apq == 0) continue;
-                // one lane forms the rotation (FP64 division and square root are
-                // long instruction sequences); the others receive c and s
-                double c = 0, s = 0;
-                if (lane == 0) {
-                    const double th = (a[q][q] - a[p][p]) / (2.0 * apq);
-                    const double t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
-                    c = 1.0 / sqrt(t * t + 1.0);
-                    s = t * c;
-                }
-                c = __shfl_sync(0xFFFFFFFFu, c, 0);
-                s = __shfl_sync(0xFFFFFFFFu, s, 0);
-                __syncwarp();
-                if (lane < 9) {
-                    const double akp = a[lane][p], akq = a[lane][q];
-                    a[lane][p] = c * akp - s * akq;
-                    a[lane][q] = s * akp + c * akq;
-                }
-                __syncwarp();
-                if (lane < 9) {
-                    const double apk = a[p][lane], aqk = a[q][lane];
-                    a[p][lane] = c * apk - s * aqk;
-                    a[q][lane] = s * apk + c * aqk;
-                    const double vkp = v[lane][p], vkq = v[lane][q];
-                    v[lane][p] = c * vkp - s * vkq;
-                    v[lane][q] = s * vkp + c * vkq;
-                }
-                __syncwarp();
-            }
-    }
-    int m = 0;
-    for (int i = 1; i < 9; ++i)
-        if (a[i][i] < a[m][m]) m = i;
-    if (lane < 9) h[lane] = v[lane][m];
-    __syncwarp();
+    const long long chunk = (M + kRefitCTAs - 1) / kRefitCTAs;
+    b = min(M, (long long)blockIdx.x * chunk);
+    e = min(M, b + chunk);
 }
 
-__global__ void __launch_bounds__(kRefitThreads)
-k_ransac_refit(const float4* pts, long long M_cap, const int32_t* dM, const double* Hs, const int32_t* best_in,
-               double t2, double* Hout, uint8_t* inl, int32_t* n_in, int32_t* best_t)
+// fixed-order sum of the CTAs' partials, columns [c0, c0 + n)
+__device__ void sum_parts(const double* part, int c0, int n, double* out)
 {
-    __shared__ double part[kRefitWarps][45];
-    __shared__ double tot[45];
-    __shared__ double A9[9][9], V9[9][9];
-    __shared__ double hs[9], Hf[9];
-    const long long M = m_count(dM, M_cap);
-    const int best = *best_in;
-    if (threadIdx.x == 0 && best_t) *best_t = best;
-    if (best < 0) {
-        for (long long i = threadIdx.x; i < M_cap; i += kRefitThreads) inl[i] = 0;
-        if (threadIdx.x < 9) Hout[threadIdx.x] = 0.0;
-        if (threadIdx.x == 0) *n_in = 0;
-        return;
+    for (int q = 0; q < n; ++q) {
+        double s = 0;
+        for (int c = 0; c < kRefitCTAs; ++c) s += part[c * kPartStride + c0 + q];
+        out[q] = s;
     }
+}
+
+// pass 1: inlier mask of the winning hypothesis, count and coordinate sums
+__global__ void __launch_bounds__(kRefitThreads)
+k_refit_p1(const float4* pts, long long M_cap, const int32_t* dM, const double* Hs, const int32_t* best_in,
+           double t2, uint8_t* inl, RefitWS ws)
+{
+    __shared__ double part[kRefitWarps][5];
+    __shared__ double tot[5];
+    const int best = *best_in;
+    if (best < 0) return;
+    const long long M = m_count(dM, M_cap);
+    long long b, e;
+    cta_range(M, b, e);
     double Hb[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) Hb[i] = Hs[9ll * best + i];
-    // inliers of the winning hypothesis and their centroids
     double v5[5] = {0, 0, 0, 0, 0};
-    for (long long i = threadIdx.x; i < M; i += kRefitThreads) {
+    for (long long i = b + threadIdx.x; i < e; i += kRefitThreads) {
         const float4 p = pts[i];
         const bool in = inlier64(Hb, p, t2);
         inl[i] = in;
         if (in) { v5[0] += 1; v5[1] += p.x; v5[2] += p.y; v5[3] += p.z; v5[4] += p.w; }
     }
-    block_sum_n<5>(v5, reinterpret_cast<double(*)[5]>(&part[0][0]), tot);
-    const double cnt = tot[0];
-    const double cxa = tot[1] / cnt, cya = tot[2] / cnt, cxb = tot[3] / cnt, cyb = tot[4] / cnt;
+    block_sum_n<5>(v5, part, tot);
+    if (threadIdx.x < 5) ws.part[blockIdx.x * kPartStride + threadIdx.x] = tot[threadIdx.x];
+}
+
+// pass 2: mean distances to the centroids (Hartley normalisation)
+__global__ void __launch_bounds__(kRefitThreads)
+k_refit_p2(const float4* pts, long long M_cap, const int32_t* dM, const int32_t* best_in, const uint8_t* inl,
+           RefitWS ws)
+{
+    __shared__ double part[kRefitWarps][2];
+    __shared__ double tot[2];
+    __shared__ double c5[5];
+    if (*best_in < 0) return;
+    const long long M = m_count(dM, M_cap);
+    if (threadIdx.x == 0) sum_parts(ws.part, 0, 5, c5);
+    __syncthreads();
+    const double n = c5[0];
+    const double cxa = c5[1] / n, cya = c5[2] / n, cxb = c5[3] / n, cyb = c5[4] / n;
+    long long b, e;
+    cta_range(M, b, e);
     double v2[2] = {0, 0};
-    for (long long i = threadIdx.x; i < M; i += kRefitThreads) {
+    for (long long i = b + threadIdx.x; i < e; i += kRefitThreads) {
         if (!inl[i]) continue;
         const float4 p = pts[i];
         v2[0] += sqrt((p.x - cxa) * (p.x - cxa) + (p.y - cya) * (p.y - cya));
         v2[1] += sqrt((p.z - cxb) * (p.z - cxb) + (p.w - cyb) * (p.w - cyb));
     }
-    block_sum_n<2>(v2, reinterpret_cast<double(*)[2]>(&part[0][0]), tot);
-    const double da = tot[0] / cnt, db = tot[1] / cnt;
-    const Norm2D na{sqrt(2.0) / da, cxa, cya}, nb{sqrt(2.0) / db, cxb, cyb};
-    const bool good = cnt >= 4 && da > 0 && db > 0;
-    // upper triangle of A^T A (45 entries), A rows of Eq. 7 in normalised coordinates
+    block_sum_n<2>(v2, part, tot);
+    if (threadIdx.x < 2) ws.part[blockIdx.x * kPartStride + 5 + threadIdx.x] = tot[threadIdx.x];
+}
+
+__device__ void norms_from_parts(const double* part, Norm2D& na, Norm2D& nb, double& n, bool& good)
+{
+    double c7[7];
+    sum_parts(part, 0, 7, c7);
+    n = c7[0];
+    const double cxa = c7[1] / n, cya = c7[2] / n, cxb = c7[3] / n, cyb = c7[4] / n;
+    const double da = c7[5] / n, db = c7[6] / n;
+    na = Norm2D{sqrt(2.0) / da, cxa, cya};
+    nb = Norm2D{sqrt(2.0) / db, cxb, cyb};
+    good = n >= 4 && da > 0 && db > 0;
+}
+
+// pass 3: upper triangle of A^T A (45 entries) in normalised coordinates
+__global__ void __launch_bounds__(kRefitThreads)
+k_refit_p3(const float4* pts, long long M_cap, const int32_t* dM, const int32_t* best_in, const uint8_t* inl,
+           RefitWS ws)
+{
+    __shared__ double part[kRefitWarps][45];
+    __shared__ double tot[45];
+    __shared__ double nrm[6];
+    __shared__ int good_s;
+    if (*best_in < 0) return;
+    const long long M = m_count(dM, M_cap);
+    if (threadIdx.x == 0) {
+        Norm2D na, nb;
+        double n;
+        bool good;
+        norms_from_parts(ws.part, na, nb, n, good);
+        nrm[0] = na.s; nrm[1] = na.cx; nrm[2] = na.cy; nrm[3] = nb.s; nrm[4] = nb.cx; nrm[5] = nb.cy;
+        good_s = good;
+    }
+    __syncthreads();
+    const Norm2D na{nrm[0], nrm[1], nrm[2]}, nb{nrm[3], nrm[4], nrm[5]};
+    long long b, e;
+    cta_range(M, b, e);
     double acc[45];
 #pragma unroll
     for (int q = 0; q < 45; ++q) acc[q] = 0;
-    if (good) {
-        for (long long i = threadIdx.x; i < M; i += kRefitThreads) {
+    if (good_s) {
+        for (long long i = b + threadIdx.x; i < e; i += kRefitThreads) {
             if (!inl[i]) continue;
             const float4 p = pts[i];
             const double x = na.s * (p.x - na.cx), y = na.s * (p.y - na.cy);
@@ -490,33 +497,129 @@ k_ransac_refit(const float4* pts, long long M_cap, const int32_t* dM, const doub
         }
     }
     block_sum_n<45>(acc, part, tot);
-    if (threadIdx.x < 32) {
-        if (threadIdx.x == 0) {
-            int q = 0;
-            for (int j = 0; j < 9; ++j)
-                for (int k = j; k < 9; ++k) { A9[j][k] = tot[q]; A9[k][j] = tot[q]; ++q; }
-        }
-        __syncwarp();
-        if (good) jacobi9_smallest_warp(A9, V9, hs);
-        if (threadIdx.x == 0) {
-            double H[9];
-            bool ok = good && denorm(na, nb, hs, H);
-            for (int i = 0; i < 9; ++i) Hf[i] = ok ? H[i] : Hb[i];
+    if (threadIdx.x < 45) ws.part[blockIdx.x * kPartStride + 8 + threadIdx.x] = tot[threadIdx.x];
+}
+
+// Smallest eigenvector of the symmetric positive semi-definite 9x9 matrix S by
+// shifted inverse iteration: Cholesky of S + mu I (mu = 1e-12 trace S), then
+// repeated solves.  The shift keeps the factorisation positive definite for
+// exact data and leaves the eigenvectors unchanged.  Returns false if the
+// factorisation fails.
+__device__ bool smallest_eigvec9(const double (*S)[9], double* h)
+{
+    double L[9][9];
+    double tr = 0;
+    for (int i = 0; i < 9; ++i) tr += S[i][i];
+    const double mu = 1e-12 * tr;
+    double inv_d[9];
+    for (int j = 0; j < 9; ++j) {
+        double d = S[j][j] + mu;
+        for (int k = 0; k < j; ++k) d -= L[j][k] * L[j][k];
+        if (!(d > 0)) return false;
+        L[j][j] = sqrt(d);
+        inv_d[j] = 1.0 / L[j][j];
+        for (int i = j + 1; i < 9; ++i) {
+            double sum = S[i][j];
+            for (int k = 0; k < j; ++k) sum -= L[i][k] * L[j][k];
+            L[i][j] = sum * inv_d[j];
         }
     }
-    __syncthreads();
-    double Hfin[9];
+    double x[9];
+    for (int i = 0; i < 9; ++i) x[i] = 1.0;
+    for (int it = 0; it < 24; ++it) {
+        double y[9];
+        for (int i = 0; i < 9; ++i) {   // L y = x
+            double sum = x[i];
+            for (int k = 0; k < i; ++k) sum -= L[i][k] * y[k];
+            y[i] = sum * inv_d[i];
+        }
+        double z[9];
+        for (int i = 8; i >= 0; --i) {  // L^T z = y
+            double sum = y[i];
+            for (int k = i + 1; k < 9; ++k) sum -= L[k][i] * z[k];
+            z[i] = sum * inv_d[i];
+        }
+        double nz = 0;
+        for (int i = 0; i < 9; ++i) nz += z[i] * z[i];
+        const double inv = 1.0 / sqrt(nz);
+        double diff = 0;
+        // align the sign with the previous iterate before comparing
+        double dot = 0;
+        for (int i = 0; i < 9; ++i) dot += z[i] * x[i];
+        const double sg = dot < 0 ? -inv : inv;
+        for (int i = 0; i < 9; ++i) {
+            const double xn = z[i] * sg;
+            diff = fmax(diff, fabs(xn - x[i]));
+            x[i] = xn;
+        }
+        if (it >= 2 && diff < 1e-15) break;
+    }
+    for (int i = 0; i < 9; ++i) h[i] = x[i];
+    return true;
+}
+
+__global__ void k_refit_solve(const double* Hs, const int32_t* best_in, RefitWS ws, double* Hout, int32_t* n_in,
+                              int32_t* best_t)
+{
+    if (threadIdx.x != 0) return;
+    const int best = *best_in;
+    if (best_t) *best_t = best;
+    *n_in = 0;
+    if (best < 0) {
+        for (int i = 0; i < 9; ++i) { Hout[i] = 0.0; ws.Hf[i] = 0.0; }
+        return;
+    }
+    Norm2D na, nb;
+    double n;
+    bool good;
+    norms_from_parts(ws.part, na, nb, n, good);
+    double H[9];
+    bool ok = good;
+    if (ok) {
+        double t[45];
+        sum_parts(ws.part, 8, 45, t);
+        double S[9][9];
+        int q = 0;
+        for (int j = 0; j < 9; ++j)
+            for (int k = j; k < 9; ++k) { S[j][k] = t[q]; S[k][j] = t[q]; ++q; }
+        double h[9];
+        ok = smallest_eigvec9(S, h) && denorm(na, nb, h, H);
+    }
+    for (int i = 0; i < 9; ++i) {
+        const double v = ok ? H[i] : Hs[9ll * best + i];
+        ws.Hf[i] = v;
+        Hout[i] = v;
+    }
+}
+
+// final inlier set of the refitted H
+__global__ void __launch_bounds__(kRefitThreads)
+k_refit_final(const float4* pts, long long M_cap, const int32_t* dM, RefitWS ws, double t2, uint8_t* inl,
+              int32_t* n_in)
+{
+    __shared__ int red[kRefitWarps];
+    const long long M = m_count(dM, M_cap);
+    double H[9];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) Hfin[i] = Hf[i];
-    double n1[1] = {0};
-    for (long long i = threadIdx.x; i < M_cap; i += kRefitThreads) {
-        const bool in = i < M && inlier64(Hfin, pts[i], t2);
+    for (int i = 0; i < 9; ++i) H[i] = ws.Hf[i];
+    const bool have = H[8] != 0.0;
+    const long long chunk = (M_cap + gridDim.x - 1) / gridDim.x;
+    const long long b = min(M_cap, (long long)blockIdx.x * chunk), e = min(M_cap, b + chunk);
+    int n = 0;
+    for (long long i = b + threadIdx.x; i < e; i += kRefitThreads) {
+        const bool in = have && i < M && inlier64(H, pts[i], t2);
         inl[i] = in;
-        n1[0] += in;
+        n += in;
     }
-    block_sum_n<1>(n1, reinterpret_cast<double(*)[1]>(&part[0][0]), tot);
-    if (threadIdx.x < 9) Hout[threadIdx.x] = Hfin[threadIdx.x];
-    if (threadIdx.x == 0) *n_in = (int)tot[0];
+#pragma unroll
+    for (int o = 16; o; o >>= 1) n += __shfl_xor_sync(0xFFFFFFFFu, n, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = n;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int s = 0;
+        for (int w = 0; w < kRefitWarps; ++w) s += red[w];
+        if (s) atomicAdd(n_in, s);
+    }
 }
 
 }  // namespace
@@ -531,7 +634,8 @@ cudaError_t launch_compact(const uint32_t* kpA, int WA, const uint32_t* kpB, int
 size_t ransac_workspace(int64_t M_cap, int T)
 {
     (void)M_cap;
-    return 256 + (size_t)T * (9 * sizeof(double) + 2 * sizeof(int32_t) + 1) + 256;
+    return 256 + (size_t)T * (9 * sizeof(double) + 2 * sizeof(int32_t) + 1) + 256 +
+           sizeof(double) * (kRefitCTAs * kPartStride + 16) + 256;
 }
 
 cudaError_t launch_ransac(const float* pts, int64_t M_cap, const int32_t* d_M, int T, float thresh,
@@ -540,21 +644,29 @@ cudaError_t launch_ransac(const float* pts, int64_t M_cap, const int32_t* d_M, i
 {
     (void)status;
     if (ws_bytes < ransac_workspace(M_cap, T)) return cudaErrorInvalidValue;
-    uint8_t* w = static_cast<uint8_t*>(ws);
+    uint8_t* w = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(ws) + 255) & ~uintptr_t(255));
     double* Hs = reinterpret_cast<double*>(w);
     int32_t* lo = reinterpret_cast<int32_t*>(Hs + 9ll * T);
     int32_t* hi = lo + T;
     int32_t* best = hi + T;
     int8_t* hok = reinterpret_cast<int8_t*>(best + 1);
+    RefitWS rw;
+    rw.part = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(hok + T) + 255) & ~uintptr_t(255));
+    rw.Hf = rw.part + kRefitCTAs * kPartStride + 1;
     const float4* p4 = reinterpret_cast<const float4*>(pts);
     const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32) ^ pair_id;
     const double t2 = (double)thresh * (double)thresh;
     const float t2f = (float)t2;
     const float eps = fmaxf(0.05f, 0.01f * t2f);
-    k_ransac_hyp<<<(T + 31) / 32, 32, 0, s>>>(p4, M_cap, d_M, T, k0, k1, Hs, hok);
+    k_ransac_hyp<<<(T + 15) / 16, 16, 0, s>>>(p4, M_cap, d_M, T, k0, k1, Hs, hok);
     k_ransac_score<<<T, kScoreThreads, 0, s>>>(p4, M_cap, d_M, Hs, hok, t2f, eps, lo, hi);
     k_ransac_select<<<1, kSelThreads, 0, s>>>(p4, M_cap, d_M, T, Hs, lo, hi, t2, best);
-    k_ransac_refit<<<1, kRefitThreads, 0, s>>>(p4, M_cap, d_M, Hs, best, t2, H, inlier, n_in, best_t);
+    k_refit_p1<<<kRefitCTAs, kRefitThreads, 0, s>>>(p4, M_cap, d_M, Hs, best, t2, inlier, rw);
+    k_refit_p2<<<kRefitCTAs, kRefitThreads, 0, s>>>(p4, M_cap, d_M, best, inlier, rw);
+    k_refit_p3<<<kRefitCTAs, kRefitThreads, 0, s>>>(p4, M_cap, d_M, best, inlier, rw);
+    k_refit_solve<<<1, 32, 0, s>>>(Hs, best, rw, H, n_in, best_t);
+    const unsigned gfin = (unsigned)std::max<long long>(1, std::min<long long>(kRefitCTAs, (M_cap + 1023) / 1024));
+    k_refit_final<<<gfin, kRefitThreads, 0, s>>>(p4, M_cap, d_M, rw, t2, inlier, n_in);
     return cudaGetLastError();
 }
 
