@@ -1,24 +1,28 @@
 // Orientation and 128-d description of feature points (Sec. 2.3, Eq. 3-5)
 // for sm_103a.
 //
-// One warp per feature point; four points per 128-thread CTA, heaviest scale
-// first so that the long descriptors do not form the tail.  The warp copies
-// the point's clamped neighbourhood (radius ceil(2*sqrt(2)*w_s) + 2) from the
-// L2-resident intensity image into shared memory once; every tap afterwards is
-// a shared-memory read.
+// One warp per feature point, four points per 128-thread CTA; scales are
+// grouped into launches by shared-memory footprint, heaviest first.  The warp
+// copies the point's clamped neighbourhood (radius ceil(2*sqrt(2)*w_s + 1.5) +
+// 1) from the L2-resident intensity image into shared memory once.
 //
 // Orientation (integer, exact): 36-bin histogram over the upright
-// (4 w_s + 1)^2 window of Eq. 5 gradients, weight round(65536*sqrt(a^2+b^2))
-// computed with an integer square root, bin = 10-degree sector of
-// atan2(b, a) (axes decided by sign; every other integer gradient lies more
-// than 6e-5 bins from a sector edge, far above FP32 atan2 error).  Sums are
-// 64-bit integer shared atomics, so the argmax (lowest bin on ties) is exact.
+// (4 w_s + 1)^2 window of Eq. 5 gradients.  Bin and weight come from two
+// tables that tabulate the exact functions below (10-degree sector of
+// atan2(b, a); round(65536*sqrt(a^2+b^2)) by integer square root), built once
+// per context on the device.  Each weight (< 2^25) is added to two 32-bit
+// shared counters per bin, its low 16 and its high 9 bits (for w_s <= 15 at
+// most 61^2 samples: no overflow), recombined in 64 bits; the argmax (lowest
+// bin on ties) is therefore exact.  Larger scales take a global-memory kernel
+// with per-lane 64-bit histogram columns.
 //
-// Descriptor (FP32): the 4 w_s x 4 w_s grid turned by theta = (k + 0.5)*10
-// degrees, bilinear taps, Eq. 5 gradient along the turned axes, 8 soft
-// direction bins.  Lane 2c and 2c+1 own cell c and sum its samples in a private
-// shared-memory slice (no atomics, fixed order, deterministic); the vector is
-// L2-normalised, clamped at 0.2 and normalised again with warp reductions.
+// Descriptor (FP32): the gradient taps p +- e_u, p +- e_v of grid point (u, v)
+// are the grid points (u +- 1, v), (u, v +- 1) of the same turned grid, so the
+// warp first interpolates the intensity once at every point of the grid
+// extended by one sample on each side, then takes Eq. 5 differences.  Lanes 2c
+// and 2c+1 own cell c and sum its samples in a private slice (no atomics,
+// fixed order); the vector is L2-normalised, clamped at 0.2 and normalised
+// again with warp reductions.
 #include <cuda_bf16.h>
 
 #include "lp_internal.cuh"
@@ -27,22 +31,26 @@ namespace lp {
 namespace {
 
 constexpr int kWarps = 4;
-constexpr int kHistBytes = 36 * 8;
 constexpr int kAccStride = 9;                  // 8 bins + 1 pad word per lane
 constexpr int kAccBytes = 32 * kAccStride * 4;
+constexpr int kHistBytes = 36 * 32 * 4;        // [bin][lane] u32
+constexpr int kLutBins = 511 * 511;
+constexpr int kLutWeights = 2 * 255 * 255 + 1;
 
 struct DescParams {
     const uint8_t* gray;
     int H, W, pitch;
     const uint32_t* kp;
-    long long K;
-    int nL;
+    long long k0, n;        // first point and number of points of this launch
+    int ws, P;              // scale of a single-scale launch
+    int nl;                 // scales of a multi-scale launch
     long long off[LP_MAX_SCALES + 1];
-    int ws[LP_MAX_SCALES];
-    int pr[LP_MAX_SCALES];
-    float cs[36][2];       // cos, sin of (k + 0.5) * 10 degrees
+    int wsl[LP_MAX_SCALES], Pl[LP_MAX_SCALES];
+    float cs[36][2];        // cos, sin of (k + 0.5) * 10 degrees
     int upright;
-    int warp_bytes;
+    int warp_bytes, patch_bytes, mid_bytes;
+    const uint8_t* lut_bin;
+    const uint32_t* lut_w;
     uint8_t* ori;
     float* desc;
     __nv_bfloat16* desc16;
@@ -50,6 +58,8 @@ struct DescParams {
 };
 
 // 10-degree sector of the direction atan2(b, a) in [0, 360); (a, b) != 0.
+// Axes are decided by sign; every other integer gradient with |a|, |b| <= 255
+// lies more than 6e-5 sectors from an edge, far above the FP32 error here.
 __device__ __forceinline__ int orient_bin(int a, int b)
 {
     if (b == 0) return a > 0 ? 0 : 18;
@@ -72,78 +82,147 @@ __device__ __forceinline__ uint32_t orient_weight(int s)
     return (uint32_t)(r + (N > r * r + r ? 1ull : 0ull));
 }
 
-struct PatchTap {
-    const uint8_t* patch;
-    int S, P;
-    __device__ __forceinline__ float at(int r, int c) const { return (float)patch[(P + r) * S + P + c]; }
-    __device__ __forceinline__ int iat(int r, int c) const { return patch[(P + r) * S + P + c]; }
-};
-
-struct GlobalTap {
-    const uint8_t* g;
-    int H, W, pitch, y, x;
-    __device__ __forceinline__ int iat(int r, int c) const
-    {
-        const int yy = min(max(y + r, 0), H - 1), xx = min(max(x + c, 0), W - 1);
-        return __ldg(g + (size_t)yy * pitch + xx);
+__global__ void k_build_luts(uint8_t* bins, uint32_t* weights)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < kLutBins) {
+        const int a = i / 511 - 255, b = i % 511 - 255;
+        bins[i] = (uint8_t)((a == 0 && b == 0) ? 0 : orient_bin(a, b));
     }
-    __device__ __forceinline__ float at(int r, int c) const { return (float)iat(r, c); }
-};
+    if (i < kLutWeights) weights[i] = orient_weight(i);
+}
 
-// Bilinear intensity at (row, col) offsets relative to the point.
-template <class Tap>
-__device__ __forceinline__ float bilinear(const Tap& t, float r, float c)
+__global__ void k_diag_orient(int32_t* bins, uint32_t* weights)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (bins && i < kLutBins) {
+        const int a = i / 511 - 255, b = i % 511 - 255;
+        bins[i] = (a == 0 && b == 0) ? 0 : orient_bin(a, b);
+    }
+    if (weights && i < kLutWeights) weights[i] = orient_weight(i);
+}
+
+// Bilinear intensity at (row, col) offsets relative to the patch centre;
+// nested linear interpolation, exact on flat neighbourhoods.
+__device__ __forceinline__ float bilinear(const uint8_t* patch, int S, int P, float r, float c)
 {
     const float r0 = floorf(r), c0 = floorf(c);
     const float fr = r - r0, fc = c - c0;
-    const int y = (int)r0, x = (int)c0;
-    const float v00 = t.at(y, x), v01 = t.at(y, x + 1), v10 = t.at(y + 1, x), v11 = t.at(y + 1, x + 1);
+    const uint8_t* q = patch + ((int)r0 + P) * S + (int)c0 + P;
+    const float v00 = q[0], v01 = q[1], v10 = q[S], v11 = q[S + 1];
     const float top = v00 + fc * (v01 - v00);
     const float bot = v10 + fc * (v11 - v10);
     return top + fr * (bot - top);
 }
 
-template <class Tap>
-__device__ __forceinline__ void describe_point(const DescParams& p, const Tap& tap, long long k, int ws,
-                                               unsigned long long* hist, float* acc, int lane)
+// Walk the flattened index e = lane, lane + 32, ... of an n-wide 2-D range
+// without divisions.
+struct Walk2D {
+    int r, c, dr, dc, n;
+    __device__ __forceinline__ Walk2D(int lane, int n_) : n(n_)
+    {
+        r = lane / n_; c = lane - r * n_;
+        dr = 32 / n_; dc = 32 - dr * n_;
+    }
+    __device__ __forceinline__ void next()
+    {
+        r += dr; c += dc;
+        if (c >= n) { c -= n; ++r; }
+    }
+};
+
+__global__ void __launch_bounds__(kWarps * 32) k_describe_all(const DescParams p)
 {
-    const int R = 2 * ws;
+    extern __shared__ __align__(16) uint8_t sm[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // heaviest points (last in canonical order) first
+    const long long idx = (long long)blockIdx.x * kWarps + warp;
+    if (idx >= p.n) return;
+    const long long k = p.k0 + p.n - 1 - idx;
+    int l = 0;
+    while (l + 1 < p.nl && k >= p.off[l + 1]) ++l;
+    uint8_t* base = sm + warp * p.warp_bytes;
+    uint8_t* patch = base;
+    float* grid = reinterpret_cast<float*>(base + p.patch_bytes);
+    uint32_t* hlo = reinterpret_cast<uint32_t*>(base + p.patch_bytes + p.mid_bytes);   // [36]
+    uint32_t* hhi = hlo + 36;                                                          // [36]
+    float* acc = reinterpret_cast<float*>(base + p.patch_bytes + p.mid_bytes + 2 * 36 * 4);
+    const int ws = p.wsl[l], R = 2 * ws, P = p.Pl[l], S = 2 * P + 1;
+    const uint32_t id = __ldg(p.kp + k);
+    const int y = (int)(id / (uint32_t)p.W), x = (int)(id - (uint32_t)y * (uint32_t)p.W);
+
+    // clamped neighbourhood
+    {
+        Walk2D w(lane, S);
+#pragma unroll 4
+        for (; w.r < S; w.next()) {
+            const int yy = min(max(y - P + w.r, 0), p.H - 1), xx = min(max(x - P + w.c, 0), p.W - 1);
+            patch[w.r * S + w.c] = __ldg(p.gray + (size_t)yy * p.pitch + xx);
+        }
+    }
+    if (lane < 36) { hlo[lane] = 0u; hhi[lane] = 0u; }
+    if (lane < 4) { hlo[lane + 32] = 0u; hhi[lane + 32] = 0u; }
+    __syncwarp();
+
+    // ---- orientation: exact integer histogram over the upright window; each
+    // weight (< 2^25) is added as its low 16 and high 9 bits to two 32-bit
+    // counters, which cannot overflow for w_s <= 15
     int best = 0;
     if (!p.upright) {
-        for (int j = lane; j < 36; j += 32) hist[j] = 0ull;
-        __syncwarp();
         const int n = 2 * R + 1;
-        for (int e = lane; e < n * n; e += 32) {
-            const int u = e / n - R, v = e - (e / n) * n - R;
-            const int a = tap.iat(u + 1, v) - tap.iat(u - 1, v);
-            const int b = tap.iat(u, v + 1) - tap.iat(u, v - 1);
-            const int s = a * a + b * b;
-            if (s) atomicAdd(&hist[orient_bin(a, b)], (unsigned long long)orient_weight(s));
+        const uint8_t* c0 = patch + (P - R) * S + (P - R);
+        Walk2D w(lane, n);
+        for (; w.r < n; w.next()) {
+            const uint8_t* q = c0 + w.r * S + w.c;
+            const int a = (int)q[S] - (int)q[-S];
+            const int b = (int)q[1] - (int)q[-1];
+            if (a | b) {
+                const int bin = __ldg(p.lut_bin + (a + 255) * 511 + (b + 255));
+                const uint32_t wt = __ldg(p.lut_w + a * a + b * b);
+                atomicAdd(&hlo[bin], wt & 0xFFFFu);
+                atomicAdd(&hhi[bin], wt >> 16);
+            }
         }
         __syncwarp();
-        if (lane == 0) {
-            unsigned long long bv = hist[0];
-            for (int j = 1; j < 36; ++j)
-                if (hist[j] > bv) { bv = hist[j]; best = j; }
+        unsigned long long bv = ((unsigned long long)hhi[lane] << 16) + hlo[lane];
+        int bb = lane;
+        if (lane < 4) {
+            const unsigned long long t1 = ((unsigned long long)hhi[lane + 32] << 16) + hlo[lane + 32];
+            if (t1 > bv) { bv = t1; bb = lane + 32; }
         }
-        best = __shfl_sync(0xFFFFFFFFu, best, 0);
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            const unsigned long long ov = __shfl_xor_sync(0xFFFFFFFFu, bv, o);
+            const int ob = __shfl_xor_sync(0xFFFFFFFFu, bb, o);
+            if (ov > bv || (ov == bv && ob < bb)) { bv = ov; bb = ob; }
+        }
+        best = bb;
     }
     const float c = p.upright ? 1.f : p.cs[best][0];
     const float s = p.upright ? 0.f : p.cs[best][1];
 
+    // ---- intensities of the turned grid, extended by one sample on each side
+    const int G = 2 * R + 2;
+    {
+        Walk2D w(lane, G);
+        for (; w.r < G; w.next()) {
+            const float fu = (float)(w.r - R - 1), fv = (float)(w.c - R - 1);
+            grid[w.r * G + w.c] = bilinear(patch, S, P, fu * c - fv * s, fu * s + fv * c);
+        }
+    }
     float* mine = acc + lane * kAccStride;
 #pragma unroll
     for (int q = 0; q < 8; ++q) mine[q] = 0.f;
+    __syncwarp();
+
+    // ---- descriptor samples: Eq. 5 differences along the turned axes
     const int cell = lane >> 1, cr = cell >> 2, cc = cell & 3;
-    const int u0 = -R + cr * ws, v0 = -R + cc * ws;
     int iu = 0, iv = lane & 1;
     while (iv >= ws) { iv -= ws; ++iu; }
     for (; iu < ws;) {
-        const float fu = (float)(u0 + iu), fv = (float)(v0 + iv);
-        const float dy = fu * c - fv * s;
-        const float dx = fu * s + fv * c;
-        const float a = bilinear(tap, dy + c, dx + s) - bilinear(tap, dy - c, dx - s);
-        const float b = bilinear(tap, dy - s, dx + c) - bilinear(tap, dy + s, dx - c);
+        const float* g = grid + (cr * ws + iu + 1) * G + cc * ws + iv + 1;
+        const float a = g[G] - g[-G];
+        const float b = g[1] - g[-1];
         const float m = sqrtf(a * a + b * b);
         if (m > 0.f) {
             float o = atan2f(b, a) * 1.27323954473516268615f;   // 8 / (2 pi)
@@ -170,12 +249,12 @@ __device__ __forceinline__ void describe_point(const DescParams& p, const Tap& t
     }
 #pragma unroll
     for (int o = 16; o; o >>= 1) ss += __shfl_xor_sync(0xFFFFFFFFu, ss, o);
-    const float n = sqrtf(ss);
-    const bool ok = n > 0.f;
+    const float nrm = sqrtf(ss);
+    const bool ok = nrm > 0.f;
     float ss2 = 0.f;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        v[q] = ok ? fminf(v[q] / n, 0.2f) : 0.f;
+        v[q] = ok ? fminf(v[q] / nrm, 0.2f) : 0.f;
         ss2 += v[q] * v[q];
     }
 #pragma unroll
@@ -198,91 +277,196 @@ __device__ __forceinline__ void describe_point(const DescParams& p, const Tap& t
     }
 }
 
-template <bool PATCH>
-__global__ void __launch_bounds__(kWarps * 32) k_describe(const DescParams p)
+// Fallback for scales whose neighbourhood does not fit in shared memory: the
+// same arithmetic with clamped reads from the (L2-resident) intensity image
+// and four bilinear evaluations per descriptor sample.
+__global__ void __launch_bounds__(kWarps * 32) k_describe_global(const DescParams p)
 {
     extern __shared__ __align__(16) uint8_t sm[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    uint8_t* base = sm + warp * p.warp_bytes;
-    unsigned long long* hist = reinterpret_cast<unsigned long long*>(base);
-    float* acc = reinterpret_cast<float*>(base + kHistBytes);
-    const long long k = p.K - 1 - ((long long)blockIdx.x * kWarps + warp);
-    if (k < 0) return;
-    int l = 0;
-    while (l + 1 < p.nL && k >= p.off[l + 1]) ++l;
-    const int ws = p.ws[l];
+    const long long idx = (long long)blockIdx.x * kWarps + warp;
+    if (idx >= p.n) return;
+    const long long k = p.k0 + idx;
+    unsigned long long* hist = reinterpret_cast<unsigned long long*>(sm + warp * (2 * kHistBytes + kAccBytes));
+    float* acc = reinterpret_cast<float*>(sm + warp * (2 * kHistBytes + kAccBytes) + 2 * kHistBytes);
+    const int ws = p.ws, R = 2 * ws;
     const uint32_t id = __ldg(p.kp + k);
     const int y = (int)(id / (uint32_t)p.W), x = (int)(id - (uint32_t)y * (uint32_t)p.W);
-    if (PATCH) {
-        uint8_t* patch = base + kHistBytes + kAccBytes;
-        const int P = p.pr[l], S = 2 * P + 1;
-        for (int r = 0; r < S; ++r) {
-            const int yy = min(max(y - P + r, 0), p.H - 1);
-            const uint8_t* row = p.gray + (size_t)yy * p.pitch;
-            for (int c = lane; c < S; c += 32) {
-                const int xx = min(max(x - P + c, 0), p.W - 1);
-                patch[r * S + c] = __ldg(row + xx);
+    auto px = [&](int r, int c) -> int {
+        const int yy = min(max(y + r, 0), p.H - 1), xx = min(max(x + c, 0), p.W - 1);
+        return __ldg(p.gray + (size_t)yy * p.pitch + xx);
+    };
+    auto bil = [&](float r, float c) -> float {
+        const float r0 = floorf(r), c0 = floorf(c);
+        const float fr = r - r0, fc = c - c0;
+        const int yi = (int)r0, xi = (int)c0;
+        const float v00 = px(yi, xi), v01 = px(yi, xi + 1), v10 = px(yi + 1, xi), v11 = px(yi + 1, xi + 1);
+        const float top = v00 + fc * (v01 - v00);
+        const float bot = v10 + fc * (v11 - v10);
+        return top + fr * (bot - top);
+    };
+    int best = 0;
+    if (!p.upright) {
+        for (int b = 0; b < 36; ++b) hist[b * 32 + lane] = 0ull;
+        for (int u = -R; u <= R; ++u)
+            for (int v = lane - R; v <= R; v += 32) {
+                const int a = px(u + 1, v) - px(u - 1, v);
+                const int b = px(u, v + 1) - px(u, v - 1);
+                if (a | b) hist[__ldg(p.lut_bin + (a + 255) * 511 + (b + 255)) * 32 + lane] += __ldg(p.lut_w + a * a + b * b);
             }
-        }
         __syncwarp();
-        PatchTap t{patch, S, P};
-        describe_point(p, t, k, ws, hist, acc, lane);
-    } else {
-        GlobalTap t{p.gray, p.H, p.W, p.pitch, y, x};
-        describe_point(p, t, k, ws, hist, acc, lane);
+        unsigned long long t0 = 0, t1 = 0;
+        for (int l = 0; l < 32; ++l) t0 += hist[lane * 32 + ((l + lane) & 31)];
+        if (lane < 4)
+            for (int l = 0; l < 32; ++l) t1 += hist[(lane + 32) * 32 + ((l + lane) & 31)];
+        unsigned long long bv = t0;
+        int bb = lane;
+        if (lane < 4 && t1 > t0) { bv = t1; bb = lane + 32; }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            const unsigned long long ov = __shfl_xor_sync(0xFFFFFFFFu, bv, o);
+            const int ob = __shfl_xor_sync(0xFFFFFFFFu, bb, o);
+            if (ov > bv || (ov == bv && ob < bb)) { bv = ov; bb = ob; }
+        }
+        best = bb;
     }
-}
-
-__global__ void k_diag_orient(int32_t* bins, uint32_t* weights)
-{
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (bins && i < 511 * 511) {
-        const int a = i / 511 - 255, b = i % 511 - 255;
-        bins[i] = (a == 0 && b == 0) ? 0 : orient_bin(a, b);
+    const float c = p.upright ? 1.f : p.cs[best][0];
+    const float s = p.upright ? 0.f : p.cs[best][1];
+    float* mine = acc + lane * kAccStride;
+    for (int q = 0; q < 8; ++q) mine[q] = 0.f;
+    const int cell = lane >> 1, cr = cell >> 2, cc = cell & 3;
+    for (int i = lane & 1; i < ws * ws; i += 2) {
+        const float fu = (float)(-R + cr * ws + i / ws), fv = (float)(-R + cc * ws + i % ws);
+        const float dy = fu * c - fv * s, dx = fu * s + fv * c;
+        const float a = bil(dy + c, dx + s) - bil(dy - c, dx - s);
+        const float b = bil(dy - s, dx + c) - bil(dy + s, dx - c);
+        const float m = sqrtf(a * a + b * b);
+        if (m > 0.f) {
+            float o = atan2f(b, a) * 1.27323954473516268615f;
+            if (o < 0.f) o += 8.f;
+            if (o >= 8.f) o -= 8.f;
+            const int b0 = (int)o;
+            const float t = o - (float)b0;
+            mine[b0] += m * (1.f - t);
+            mine[(b0 + 1) & 7] += m * t;
+        }
     }
-    if (weights && i <= 2 * 255 * 255) weights[i] = orient_weight(i);
+    __syncwarp();
+    const float* e0 = acc + (2 * cell) * kAccStride + 4 * (lane & 1);
+    const float* e1 = e0 + kAccStride;
+    float v[4];
+    float ss = 0.f;
+    for (int q = 0; q < 4; ++q) { v[q] = e0[q] + e1[q]; ss += v[q] * v[q]; }
+    for (int o = 16; o; o >>= 1) ss += __shfl_xor_sync(0xFFFFFFFFu, ss, o);
+    const float nrm = sqrtf(ss);
+    const bool ok = nrm > 0.f;
+    float ss2 = 0.f;
+    for (int q = 0; q < 4; ++q) { v[q] = ok ? fminf(v[q] / nrm, 0.2f) : 0.f; ss2 += v[q] * v[q]; }
+    for (int o = 16; o; o >>= 1) ss2 += __shfl_xor_sync(0xFFFFFFFFu, ss2, o);
+    const float n2 = sqrtf(ss2);
+    for (int q = 0; q < 4; ++q) v[q] = ok ? v[q] / n2 : 0.f;
+    reinterpret_cast<float4*>(p.desc + k * 128)[lane] = make_float4(v[0], v[1], v[2], v[3]);
+    if (p.desc16) {
+        __nv_bfloat162 lo = __floats2bfloat162_rn(v[0], v[1]);
+        __nv_bfloat162 hi = __floats2bfloat162_rn(v[2], v[3]);
+        uint2 w;
+        w.x = *reinterpret_cast<uint32_t*>(&lo);
+        w.y = *reinterpret_cast<uint32_t*>(&hi);
+        reinterpret_cast<uint2*>(p.desc16 + k * 128)[lane] = w;
+    }
+    if (lane == 0) {
+        p.ori[k] = (uint8_t)best;
+        p.valid[k] = ok ? 1 : 0;
+    }
 }
 
 }  // namespace
 
+size_t describe_lut_bytes() { return (size_t)kLutWeights * 4 + 256 + (size_t)kLutBins + 256; }
+
+cudaError_t launch_build_luts(void* luts, cudaStream_t s)
+{
+    uint32_t* w = reinterpret_cast<uint32_t*>(luts);
+    uint8_t* b = reinterpret_cast<uint8_t*>(luts) + (((size_t)kLutWeights * 4 + 255) & ~size_t(255));
+    k_build_luts<<<(kLutBins + 255) / 256, 256, 0, s>>>(b, w);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_describe(const uint8_t* gray, int H, int W, int pitch, const uint32_t* kp,
-                            const ScaleTable& st, int upright, uint8_t* ori, float* desc,
+                            const ScaleTable& st, int upright, const void* luts, uint8_t* ori, float* desc,
                             uint16_t* desc_bf16, uint8_t* valid, cudaStream_t s)
 {
     DescParams p;
-    p.gray = gray; p.H = H; p.W = W; p.pitch = pitch; p.kp = kp; p.K = st.off[st.nL]; p.nL = st.nL;
-    int pmax = 0;
-    for (int l = 0; l <= st.nL; ++l) p.off[l] = st.off[l];
-    for (int l = 0; l < st.nL; ++l) {
-        p.ws[l] = st.ws[l];
-        p.pr[l] = st.pr[l];
-        pmax = pmax > st.pr[l] ? pmax : st.pr[l];
-    }
+    p.gray = gray; p.H = H; p.W = W; p.pitch = pitch; p.kp = kp;
     for (int k = 0; k < 36; ++k) {
         const double th = (k + 0.5) * 10.0 * 3.14159265358979323846 / 180.0;
         p.cs[k][0] = (float)cos(th);
         p.cs[k][1] = (float)sin(th);
     }
     p.upright = upright;
+    p.lut_w = reinterpret_cast<const uint32_t*>(luts);
+    p.lut_bin = reinterpret_cast<const uint8_t*>(luts) + (((size_t)kLutWeights * 4 + 255) & ~size_t(255));
     p.ori = ori; p.desc = desc; p.desc16 = reinterpret_cast<__nv_bfloat16*>(desc_bf16); p.valid = valid;
-    if (p.K == 0) return cudaSuccess;
-    const int S = 2 * pmax + 1;
-    const bool patch = (size_t)S * S <= 12 * 1024;
-    p.warp_bytes = kHistBytes + kAccBytes + (patch ? ((S * S + 15) / 16) * 16 : 0);
-    const size_t smem = (size_t)kWarps * p.warp_bytes;
-    const unsigned grid = (unsigned)((p.K + kWarps - 1) / kWarps);
-    if (patch) {
-        if (smem > 48 * 1024) cudaFuncSetAttribute(k_describe<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_describe<true><<<grid, kWarps * 32, smem, s>>>(p);
-    } else {
-        k_describe<false><<<grid, kWarps * 32, smem, s>>>(p);
+    // Scales with w_s <= 15 run in launches of consecutive scales whose
+    // per-warp shared memory fits kSmallWarpBytes (high occupancy), every larger
+    // footprint in a launch of its own; larger footprints are launched first.
+    // Scales with w_s > 15 take the global-memory kernel.
+    int m = 0;
+    while (m < st.nL && st.ws[m] <= 15) ++m;
+    auto warp_bytes = [&](int l) {
+        const int S = 2 * st.pr[l] + 1, G = 4 * st.ws[l] + 2;
+        return ((S * S + 15) / 16) * 16 + ((G * G * 4 + 15) / 16) * 16 + 2 * 36 * 4 + kAccBytes;
+    };
+    constexpr int kSmallWarpBytes = 7680;
+    int first_big = 0;
+    while (first_big < m && warp_bytes(first_big) <= kSmallWarpBytes) ++first_big;
+    auto launch_group = [&](int l0, int l1) -> cudaError_t {
+        int Pmax = 0, Gmax = 0;
+        for (int l = l0; l < l1; ++l) {
+            Pmax = Pmax > st.pr[l] ? Pmax : st.pr[l];
+            Gmax = Gmax > 4 * st.ws[l] + 2 ? Gmax : 4 * st.ws[l] + 2;
+        }
+        p.nl = l1 - l0;
+        for (int l = l0; l <= l1; ++l) p.off[l - l0] = st.off[l];
+        for (int l = l0; l < l1; ++l) { p.wsl[l - l0] = st.ws[l]; p.Pl[l - l0] = st.pr[l]; }
+        p.k0 = st.off[l0];
+        p.n = st.off[l1] - st.off[l0];
+        if (p.n == 0) return cudaSuccess;
+        const int S = 2 * Pmax + 1;
+        p.patch_bytes = ((S * S + 15) / 16) * 16;
+        p.mid_bytes = ((Gmax * Gmax * 4) + 15) / 16 * 16;
+        p.warp_bytes = p.patch_bytes + p.mid_bytes + 2 * 36 * 4 + kAccBytes;
+        const size_t smem = (size_t)kWarps * p.warp_bytes;
+        if (smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(k_describe_all, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        k_describe_all<<<(unsigned)((p.n + kWarps - 1) / kWarps), kWarps * 32, smem, s>>>(p);
+        return cudaGetLastError();
+    };
+    for (int l = m - 1; l >= first_big; --l) {
+        cudaError_t e = launch_group(l, l + 1);
+        if (e != cudaSuccess) return e;
+    }
+    if (first_big > 0) {
+        cudaError_t e = launch_group(0, first_big);
+        if (e != cudaSuccess) return e;
+    }
+    for (int l = m; l < st.nL; ++l) {
+        p.k0 = st.off[l];
+        p.n = st.off[l + 1] - st.off[l];
+        if (p.n == 0) continue;
+        p.ws = st.ws[l];
+        p.P = st.pr[l];
+        const unsigned grid = (unsigned)((p.n + kWarps - 1) / kWarps);
+        k_describe_global<<<grid, kWarps * 32, (size_t)kWarps * (2 * kHistBytes + kAccBytes), s>>>(p);
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_diag_orient(int32_t* bins, uint32_t* weights, cudaStream_t s)
 {
-    k_diag_orient<<<(511 * 511 + 255) / 256, 256, 0, s>>>(bins, weights);
+    k_diag_orient<<<(kLutBins + 255) / 256, 256, 0, s>>>(bins, weights);
     return cudaGetLastError();
 }
 

@@ -20,7 +20,7 @@ enum BufId {
     B_MATCH_WS, B_RANSAC_WS,
     B_IMG_A, B_IMG_B, B_GRAY_A, B_GRAY_B, B_KP_A, B_KP_B, B_ORI_A, B_ORI_B,
     B_DESC_A, B_DESC_B, B_D16_A, B_D16_B, B_VAL_A, B_VAL_B,
-    B_MATCH, B_D1, B_D2, B_PTS, B_M, B_INL, B_H, B_NIN, B_BEST,
+    B_MATCH, B_D1, B_D2, B_PTS, B_M, B_INL, B_H, B_NIN, B_BEST, B_LUTS,
     B_COUNT
 };
 
@@ -29,6 +29,7 @@ enum BufId {
 struct lp_ctx {
     lp_config cfg;
     int64_t last_NA = 0, last_NB = 0;   // sizes of the last BF16 match (for diagnostics)
+    bool luts_ready = false;            // orientation tables built on this context's device
     int device = 0;
     int num_sms = 0;
     int32_t* d_status = nullptr;
@@ -137,7 +138,9 @@ int make_scale_table(const int* Ls_in, int nL, double beta0, int H, int W, Scale
         const double beta = beta0 * pow((double)Ls[l] / (double)Lmax, -0.5);
         const int w = (int)floor(beta * Ls[l] + 0.5);
         st->ws[l] = w < 1 ? 1 : w;
-        st->pr[l] = (int)ceil(2.0 * sqrt(2.0) * st->ws[l]) + 2;
+        // neighbourhood radius: turned-grid points reach sqrt(2) (2 w_s + 1);
+        // bilinear taps add one pixel
+        st->pr[l] = (int)ceil(2.0 * sqrt(2.0) * st->ws[l] + 1.5) + 1;
         st->nwx[l] = W / Ls[l];
         st->nwy[l] = H / Ls[l];
         st->off[l] = off;
@@ -246,8 +249,14 @@ int lp_describe(lp_ctx* c, const uint8_t* gray, int H, int W, int gray_pitch, co
     lp::ScaleTable st;
     lp::make_scale_table(c->cfg.Ls, c->cfg.nL, c->cfg.beta0, H, W, &st);
     c->last = S(stream);
-    LP_CUDA(c, lp::launch_describe(gray, H, W, gray_pitch, kp_idx, st, c->cfg.upright, ori, desc, desc_bf16, valid,
-                                   S(stream)));
+    if (!c->luts_ready) {
+        int r = ensure(c, B_LUTS, lp::describe_lut_bytes());
+        if (r) return r;
+        LP_CUDA(c, lp::launch_build_luts(c->buf[B_LUTS].p, S(stream)));
+        c->luts_ready = true;
+    }
+    LP_CUDA(c, lp::launch_describe(gray, H, W, gray_pitch, kp_idx, st, c->cfg.upright, c->buf[B_LUTS].p, ori, desc,
+                                   desc_bf16, valid, S(stream)));
     return LP_OK;
 }
 

@@ -36,8 +36,10 @@ cudaError_t launch_detect(const uint8_t* img, int H, int W, int pitch, int ch, c
 cudaError_t launch_diag_gray(const uint8_t* rgb, int64_t n, uint8_t* gray, cudaStream_t s);
 
 // k_describe.cu
+size_t describe_lut_bytes();
+cudaError_t launch_build_luts(void* luts, cudaStream_t s);
 cudaError_t launch_describe(const uint8_t* gray, int H, int W, int pitch, const uint32_t* kp,
-                            const ScaleTable& st, int upright, uint8_t* ori, float* desc,
+                            const ScaleTable& st, int upright, const void* luts, uint8_t* ori, float* desc,
                             uint16_t* desc_bf16, uint8_t* valid, cudaStream_t s);
 cudaError_t launch_diag_orient(int32_t* bins, uint32_t* weights, cudaStream_t s);
 
