@@ -55,6 +55,10 @@ constexpr uint32_t kBBytes = kTileN * 128 * 2;         // 32 KB per stage
 constexpr uint32_t kNbBytes = kEpiWarps * kTileN * 4;   // per-warp copy of one tile's |b~|^2
 constexpr uint32_t kSmemTC = kABytes + kStages * kBBytes + kNbBytes + 1024 /*barriers*/ + 1024 /*align slack*/;
 constexpr int kTopK = 8;
+// |b~|^2 of an invalid or masked column: finite (so that the column tag below
+// never turns it into a NaN) and far above any real value; treated as +inf by
+// the re-rank.
+constexpr float kNoColumn = 3.0e38f;
 // 3u + 3u^2 (BF16 rounding) + FP32 accumulation allowance + the column tag
 // that the epilogue writes into the 5 low mantissa bits (<= 31 ulp)
 constexpr float kDelta = 3.0f / 256.0f + 3.0f / 65536.0f + 1e-4f + 1e-5f;
@@ -441,10 +445,10 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
                 const long long j = c0 + (long long)t * kTileN + 4 * lane;
                 if (j + 4 <= c1) return __ldg(reinterpret_cast<const float4*>(p.nb16 + j));
                 float4 w;
-                w.x = j + 0 < c1 ? __ldg(p.nb16 + j + 0) : INFINITY;
-                w.y = j + 1 < c1 ? __ldg(p.nb16 + j + 1) : INFINITY;
-                w.z = j + 2 < c1 ? __ldg(p.nb16 + j + 2) : INFINITY;
-                w.w = j + 3 < c1 ? __ldg(p.nb16 + j + 3) : INFINITY;
+                w.x = j + 0 < c1 ? __ldg(p.nb16 + j + 0) : kNoColumn;
+                w.y = j + 1 < c1 ? __ldg(p.nb16 + j + 1) : kNoColumn;
+                w.z = j + 2 < c1 ? __ldg(p.nb16 + j + 2) : kNoColumn;
+                w.w = j + 3 < c1 ? __ldg(p.nb16 + j + 3) : kNoColumn;
                 return w;
             };
             float4 nb_next = ntiles > 0 ? load_nb(0) : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -542,7 +546,7 @@ __global__ void k_row_norms_bf16(const __nv_bfloat16* d, const uint8_t* v, long 
     float s = a.x * a.x + a.y * a.y + b.x * b.x + b.y * b.y;
 #pragma unroll
     for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
-    if (lane == 0) out[w] = v[w] ? s : INFINITY;
+    if (lane == 0) out[w] = v[w] ? s : kNoColumn;
 }
 
 // ------------------------------------------------------------------ re-rank
@@ -591,7 +595,10 @@ k_rerank(const float* A, const uint8_t* vA, const float* B, const float* nb32, c
         cv[4] = v1.x; cv[5] = v1.y; cv[6] = v1.z; cv[7] = v1.w;
         cj[0] = j0.x; cj[1] = j0.y; cj[2] = j0.z; cj[3] = j0.w;
         cj[4] = j1.x; cj[5] = j1.y; cj[6] = j1.z; cj[7] = j1.w;
-        t4 = v1.w;
+#pragma unroll
+        for (int k = 0; k < kTopK; ++k)
+            if (cv[k] >= 1.0e38f) { cv[k] = INFINITY; cj[k] = -1; }
+        t4 = cv[kTopK - 1];
     } else {
 #pragma unroll
         for (int k = 0; k < kTopK; ++k) { cv[k] = INFINITY; cj[k] = -1; }
