@@ -277,6 +277,136 @@ __global__ void __launch_bounds__(kWarps * 32) k_describe_all(const DescParams p
     }
 }
 
+// Large scales (few points, long loops): one 128-thread CTA per point, the
+// same arithmetic as k_describe_all with the loops spread over four warps.
+// Cell c's samples are split over threads 8c .. 8c+7 (one warp holds four
+// cells); their partial histograms are added in a fixed shuffle order.
+constexpr int kCtaThreads = 128;
+
+__global__ void __launch_bounds__(kCtaThreads) k_describe_cta(const DescParams p)
+{
+    extern __shared__ __align__(16) uint8_t sm[];
+    __shared__ uint32_t hlo[36], hhi[36];
+    __shared__ unsigned long long wbest[kCtaThreads / 32];
+    __shared__ int wbin[kCtaThreads / 32];
+    __shared__ float red[kCtaThreads / 32];
+    __shared__ int best_s;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const long long k = p.k0 + p.n - 1 - blockIdx.x;   // heaviest first
+    const int ws = p.ws, R = 2 * ws, P = p.P, S = 2 * P + 1, G = 2 * R + 2;
+    uint8_t* patch = sm;
+    float* grid = reinterpret_cast<float*>(sm + p.patch_bytes);
+    const uint32_t id = __ldg(p.kp + k);
+    const int y = (int)(id / (uint32_t)p.W), x = (int)(id - (uint32_t)y * (uint32_t)p.W);
+    for (int e = tid; e < S * S; e += kCtaThreads) {
+        const int r = e / S, c = e - (e / S) * S;
+        const int yy = min(max(y - P + r, 0), p.H - 1), xx = min(max(x - P + c, 0), p.W - 1);
+        patch[e] = __ldg(p.gray + (size_t)yy * p.pitch + xx);
+    }
+    if (tid < 36) { hlo[tid] = 0u; hhi[tid] = 0u; }
+    __syncthreads();
+    int best = 0;
+    if (!p.upright) {
+        const int n = 2 * R + 1;
+        const uint8_t* c0 = patch + (P - R) * S + (P - R);
+        for (int e = tid; e < n * n; e += kCtaThreads) {
+            const int r = e / n, c = e - (e / n) * n;
+            const uint8_t* q = c0 + r * S + c;
+            const int a = (int)q[S] - (int)q[-S];
+            const int b = (int)q[1] - (int)q[-1];
+            if (a | b) {
+                const int bin = __ldg(p.lut_bin + (a + 255) * 511 + (b + 255));
+                const uint32_t wt = __ldg(p.lut_w + a * a + b * b);
+                atomicAdd(&hlo[bin], wt & 0xFFFFu);
+                atomicAdd(&hhi[bin], wt >> 16);
+            }
+        }
+        __syncthreads();
+        if (warp == 0) {
+            unsigned long long bv = ((unsigned long long)hhi[lane] << 16) + hlo[lane];
+            int bb = lane;
+            if (lane < 4) {
+                const unsigned long long t1 = ((unsigned long long)hhi[lane + 32] << 16) + hlo[lane + 32];
+                if (t1 > bv) { bv = t1; bb = lane + 32; }
+            }
+#pragma unroll
+            for (int o = 16; o; o >>= 1) {
+                const unsigned long long ov = __shfl_xor_sync(0xFFFFFFFFu, bv, o);
+                const int ob = __shfl_xor_sync(0xFFFFFFFFu, bb, o);
+                if (ov > bv || (ov == bv && ob < bb)) { bv = ov; bb = ob; }
+            }
+            if (lane == 0) best_s = bb;
+        }
+        __syncthreads();
+        best = best_s;
+    }
+    (void)wbest; (void)wbin;
+    const float c = p.upright ? 1.f : p.cs[best][0];
+    const float s = p.upright ? 0.f : p.cs[best][1];
+    for (int e = tid; e < G * G; e += kCtaThreads) {
+        const int iu = e / G, iv = e - (e / G) * G;
+        const float fu = (float)(iu - R - 1), fv = (float)(iv - R - 1);
+        grid[e] = bilinear(patch, S, P, fu * c - fv * s, fu * s + fv * c);
+    }
+    __syncthreads();
+    const int cell = tid >> 3, sub = tid & 7, cr = cell >> 2, cc = cell & 3;
+    float h[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) h[q] = 0.f;
+    for (int i = sub; i < ws * ws; i += 8) {
+        const int iu = i / ws, iv = i - (i / ws) * ws;
+        const float* g = grid + (cr * ws + iu + 1) * G + cc * ws + iv + 1;
+        const float a = g[G] - g[-G];
+        const float b = g[1] - g[-1];
+        const float m = sqrtf(a * a + b * b);
+        if (m > 0.f) {
+            float o = atan2f(b, a) * 1.27323954473516268615f;
+            if (o < 0.f) o += 8.f;
+            if (o >= 8.f) o -= 8.f;
+            const int b0 = (int)o;
+            const float t = o - (float)b0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                h[q] += (q == b0) ? m * (1.f - t) : 0.f;
+                h[q] += (q == ((b0 + 1) & 7)) ? m * t : 0.f;
+            }
+        }
+    }
+    // sum the 8 threads of the cell (fixed shuffle order)
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) h[q] += __shfl_xor_sync(0xFFFFFFFFu, h[q], o);
+    // thread t keeps output (cell t/8, bin t%8)
+    float v = 0.f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v = (q == sub) ? h[q] : v;
+    float ss = v * v;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) ss += __shfl_xor_sync(0xFFFFFFFFu, ss, o);
+    if (lane == 0) red[warp] = ss;
+    __syncthreads();
+    ss = red[0] + red[1] + red[2] + red[3];
+    const float nrm = sqrtf(ss);
+    const bool ok = nrm > 0.f;
+    v = ok ? fminf(v / nrm, 0.2f) : 0.f;
+    float ss2 = v * v;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) ss2 += __shfl_xor_sync(0xFFFFFFFFu, ss2, o);
+    __syncthreads();
+    if (lane == 0) red[warp] = ss2;
+    __syncthreads();
+    ss2 = red[0] + red[1] + red[2] + red[3];
+    const float n2 = sqrtf(ss2);
+    v = ok ? v / n2 : 0.f;
+    p.desc[k * 128 + tid] = v;
+    if (p.desc16) p.desc16[k * 128 + tid] = __float2bfloat16_rn(v);
+    if (tid == 0) {
+        p.ori[k] = (uint8_t)best;
+        p.valid[k] = ok ? 1 : 0;
+    }
+}
+
 // Fallback for scales whose neighbourhood does not fit in shared memory: the
 // same arithmetic with clamped reads from the (L2-resident) intensity image
 // and four bilinear evaluations per descriptor sample.
@@ -445,7 +575,20 @@ cudaError_t launch_describe(const uint8_t* gray, int H, int W, int pitch, const 
         return cudaGetLastError();
     };
     for (int l = m - 1; l >= first_big; --l) {
-        cudaError_t e = launch_group(l, l + 1);
+        p.k0 = st.off[l];
+        p.n = st.off[l + 1] - st.off[l];
+        if (p.n == 0) continue;
+        p.ws = st.ws[l];
+        p.P = st.pr[l];
+        const int S = 2 * p.P + 1, G = 4 * p.ws + 2;
+        p.patch_bytes = ((S * S + 15) / 16) * 16;
+        const size_t smem = (size_t)p.patch_bytes + (size_t)G * G * 4;
+        if (smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(k_describe_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        k_describe_cta<<<(unsigned)p.n, kCtaThreads, smem, s>>>(p);
+        cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
     if (first_big > 0) {
