@@ -206,6 +206,31 @@ LP_API int lp_stitch_pair_host(lp_ctx* ctx, const uint8_t* imgA_host, int HA, in
                         const uint8_t* imgB_host, int HB, int WB, int pitchB, int channels,
                         uint32_t pair_id, double* H_host, int32_t* n_in_host, int32_t* M_host, void* stream);
 
+/* One image of a batch: device data plus its geometry (lp_detect's rules). */
+typedef struct lp_image {
+    const uint8_t* data;     /* device, H x W x channels, pitch bytes per row */
+    int32_t H, W, pitch, channels;
+} lp_image;
+
+/* Sec. 4: the homography matrix H_M of a set of images, one entry per pair.
+ *  imgs     host array of N image descriptors (device pixel pointers); every
+ *           image uses the same channel count
+ *  pairs    host int32[P*2] (i, j) with image i the reference of Eq. 7, or
+ *           NULL for all N(N-1)/2 pairs i < j in row-major order (then P is
+ *           ignored and the pair count is N(N-1)/2)
+ *  HM       device double[P*9]: H of each pair (all zero without a model)
+ *  n_in     device int32[P]: inliers of each pair
+ *  valid    device uint8[P]: 1 iff n_in >= cfg.min_inliers (a non-zero H_M
+ *           entry)
+ *  M_out    device int32[P] matched pairs per image pair, or NULL
+ * Every image is detected and described once; then each pair is matched,
+ * compacted and fitted with RANSAC (Philox pair_id = pair index).  The whole
+ * sequence is captured once as a CUDA graph and replayed while the images,
+ * pairs and outputs stay the same.
+ * Errors: as the stages; LP_ERR_ARG for N < 2 or a bad pair index. */
+LP_API int lp_stitch_pairs(lp_ctx* ctx, const lp_image* imgs, int N, const int32_t* pairs, int P, double* HM,
+                           int32_t* n_in, uint8_t* valid, int32_t* M_out, void* stream);
+
 /* Wait for the context's last stream, then return and clear the device
  * status word (LP_OK, LP_ERR_TIMEOUT or LP_ERR_DEVICE) or a CUDA error. */
 LP_API int lp_sync_status(lp_ctx* ctx);

@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "lp_internal.cuh"
 
@@ -20,7 +21,7 @@ enum BufId {
     B_MATCH_WS, B_RANSAC_WS,
     B_IMG_A, B_IMG_B, B_GRAY_A, B_GRAY_B, B_KP_A, B_KP_B, B_ORI_A, B_ORI_B,
     B_DESC_A, B_DESC_B, B_D16_A, B_D16_B, B_VAL_A, B_VAL_B,
-    B_MATCH, B_D1, B_D2, B_PTS, B_M, B_INL, B_H, B_NIN, B_BEST, B_LUTS,
+    B_MATCH, B_D1, B_D2, B_PTS, B_M, B_INL, B_H, B_NIN, B_BEST, B_LUTS, B_BATCH,
     B_COUNT
 };
 
@@ -30,6 +31,8 @@ struct lp_ctx {
     lp_config cfg;
     int64_t last_NA = 0, last_NB = 0;   // sizes of the last BF16 match (for diagnostics)
     bool luts_ready = false;            // orientation tables built on this context's device
+    std::vector<long long> graph_key;   // lp_stitch_pairs: what the cached graph was captured for
+    cudaGraphExec_t graph_exec = nullptr;
     int device = 0;
     int num_sms = 0;
     int32_t* d_status = nullptr;
@@ -118,6 +121,17 @@ int check_image(lp_ctx* c, const uint8_t* img, int H, int W, int pitch, int ch)
 
 cudaStream_t S(void* s) { return static_cast<cudaStream_t>(s); }
 
+int build_luts(lp_ctx* c, cudaStream_t s)
+{
+    int r = ensure(c, B_LUTS, lp::describe_lut_bytes());
+    if (r) return r;
+    LP_CUDA(c, lp::launch_build_luts(c->buf[B_LUTS].p, s));
+    c->luts_ready = true;
+    return LP_OK;
+}
+
+size_t al256(size_t n) { return (n + 255) & ~size_t(255); }
+
 }  // namespace
 
 namespace lp {
@@ -199,6 +213,7 @@ int lp_destroy(lp_ctx* c)
 {
     if (!c) return LP_ERR_ARG;
     cudaDeviceSynchronize();
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
     for (auto& b : c->buf)
         if (b.p) cudaFree(b.p);
     if (c->d_status) cudaFree(c->d_status);
@@ -250,10 +265,8 @@ int lp_describe(lp_ctx* c, const uint8_t* gray, int H, int W, int gray_pitch, co
     lp::make_scale_table(c->cfg.Ls, c->cfg.nL, c->cfg.beta0, H, W, &st);
     c->last = S(stream);
     if (!c->luts_ready) {
-        int r = ensure(c, B_LUTS, lp::describe_lut_bytes());
+        int r = build_luts(c, S(stream));
         if (r) return r;
-        LP_CUDA(c, lp::launch_build_luts(c->buf[B_LUTS].p, S(stream)));
-        c->luts_ready = true;
     }
     LP_CUDA(c, lp::launch_describe(gray, H, W, gray_pitch, kp_idx, st, c->cfg.upright, c->buf[B_LUTS].p, ori, desc,
                                    desc_bf16, valid, S(stream)));
@@ -394,6 +407,154 @@ int lp_stitch_pair_host(lp_ctx* c, const uint8_t* hA, int HA, int WA, int pitchA
     LP_CUDA(c, cudaStreamSynchronize(s));
     *n_in_host = tmp[0];
     if (M_host) *M_host = tmp[1];
+    return LP_OK;
+}
+
+namespace {
+
+__global__ void k_pair_valid(const int32_t* n_in, int P, int min_inl, uint8_t* valid)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < P) valid[p] = n_in[p] >= min_inl ? 1 : 0;
+}
+
+struct ImgBufs {
+    size_t gray, kp, ori, desc, d16, val;
+    int64_t K;
+};
+
+}  // namespace
+
+int lp_stitch_pairs(lp_ctx* c, const lp_image* imgs, int N, const int32_t* pairs, int P, double* HM, int32_t* n_in,
+                    uint8_t* valid, int32_t* M_out, void* stream)
+{
+    if (!c) return LP_ERR_ARG;
+    if (!imgs || N < 2) return fail(c, LP_ERR_ARG, "need at least two images");
+    if (!HM || !n_in || !valid) return fail(c, LP_ERR_ARG, "null output");
+    const int ch = imgs[0].channels;
+    for (int i = 0; i < N; ++i) {
+        int r = check_image(c, imgs[i].data, imgs[i].H, imgs[i].W, imgs[i].pitch, imgs[i].channels);
+        if (r) return r;
+        if (imgs[i].channels != ch) return fail(c, LP_ERR_ARG, "images differ in channel count");
+    }
+    std::vector<int32_t> pl;
+    if (!pairs) {
+        for (int i = 0; i < N; ++i)
+            for (int j = i + 1; j < N; ++j) { pl.push_back(i); pl.push_back(j); }
+        P = N * (N - 1) / 2;
+    } else {
+        if (P < 1) return fail(c, LP_ERR_ARG, "P=%d", P);
+        pl.assign(pairs, pairs + 2 * (size_t)P);
+        for (int q = 0; q < 2 * P; ++q)
+            if (pl[q] < 0 || pl[q] >= N) return fail(c, LP_ERR_ARG, "pair index %d outside 0..%d", pl[q], N - 1);
+    }
+    // ---- plan: per-image feature buffers in one block, per-pair scratch reused
+    const bool bf = c->cfg.precision == LP_PREC_BF16;
+    std::vector<ImgBufs> ib(N);
+    size_t o = 0;
+    int64_t Kmax = 0;
+    for (int i = 0; i < N; ++i) {
+        const int64_t K = lp_num_keypoints(imgs[i].H, imgs[i].W, c->cfg.Ls, c->cfg.nL);
+        ib[i].K = K;
+        Kmax = std::max(Kmax, K);
+        ib[i].gray = o; o += ch == 3 ? al256((size_t)imgs[i].H * imgs[i].W + 16) : 0;
+        ib[i].kp = o; o += al256(4 * (size_t)K + 8);
+        ib[i].ori = o; o += al256((size_t)K + 8);
+        ib[i].desc = o; o += al256(512 * (size_t)K + 16);
+        ib[i].d16 = o; o += bf ? al256(256 * (size_t)K + 16) : 0;
+        ib[i].val = o; o += al256((size_t)K + 8);
+    }
+    const size_t o_match = o; o += al256(4 * (size_t)Kmax + 8);
+    const size_t o_d1 = o; o += al256(4 * (size_t)Kmax + 8);
+    const size_t o_d2 = o; o += al256(4 * (size_t)Kmax + 8);
+    const size_t o_pts = o; o += al256(16 * (size_t)Kmax + 16);
+    const size_t o_inl = o; o += al256((size_t)Kmax + 8);
+    const size_t o_M = o; o += al256(4 * (size_t)P + 8);
+    int r = ensure(c, B_BATCH, o + 256);
+    if (r) return r;
+    size_t mws = 0;
+    for (int q = 0; q < P; ++q) {
+        const int64_t KA = ib[pl[2 * q]].K, KB = ib[pl[2 * q + 1]].K;
+        mws = std::max(mws, bf ? lp::match_bf16_workspace(KA, KB, c->num_sms) : lp::match_fp32_workspace(KA, KB, c->num_sms));
+    }
+    if ((r = ensure(c, B_MATCH_WS, mws)) || (r = ensure(c, B_RANSAC_WS, lp::ransac_workspace(Kmax, c->cfg.ransac_iters))))
+        return r;
+    cudaStream_t s = S(stream);
+    if (!c->luts_ready && (r = build_luts(c, s))) return r;
+    uint8_t* base = reinterpret_cast<uint8_t*>(al256(reinterpret_cast<uintptr_t>(c->buf[B_BATCH].p)));
+    int32_t* Mbuf = M_out ? M_out : reinterpret_cast<int32_t*>(base + o_M);
+
+    std::vector<long long> key = {N, P, ch, (long long)(uintptr_t)HM, (long long)(uintptr_t)n_in,
+                                  (long long)(uintptr_t)valid, (long long)(uintptr_t)Mbuf,
+                                  (long long)(uintptr_t)c->buf[B_BATCH].p, (long long)(uintptr_t)c->buf[B_MATCH_WS].p,
+                                  (long long)(uintptr_t)c->buf[B_RANSAC_WS].p};
+    for (int i = 0; i < N; ++i) {
+        key.push_back((long long)(uintptr_t)imgs[i].data);
+        key.push_back(imgs[i].H); key.push_back(imgs[i].W); key.push_back(imgs[i].pitch);
+    }
+    key.insert(key.end(), pl.begin(), pl.end());
+    c->last = s;
+    if (s && c->graph_exec && key == c->graph_key) {
+        LP_CUDA(c, cudaGraphLaunch(c->graph_exec, s));
+        return LP_OK;
+    }
+
+    auto enqueue = [&]() -> int {
+        int rr;
+        for (int i = 0; i < N; ++i) {
+            uint8_t* g = ch == 3 ? base + ib[i].gray : nullptr;
+            if ((rr = lp_detect(c, imgs[i].data, imgs[i].H, imgs[i].W, imgs[i].pitch, ch, (uint32_t*)(base + ib[i].kp), g,
+                                stream)))
+                return rr;
+            const uint8_t* gsrc = ch == 3 ? g : imgs[i].data;
+            const int gp = ch == 3 ? imgs[i].W : imgs[i].pitch;
+            if ((rr = lp_describe(c, gsrc, imgs[i].H, imgs[i].W, gp, (const uint32_t*)(base + ib[i].kp), ib[i].K,
+                                  base + ib[i].ori, (float*)(base + ib[i].desc),
+                                  bf ? (uint16_t*)(base + ib[i].d16) : nullptr, base + ib[i].val, stream)))
+                return rr;
+        }
+        for (int q = 0; q < P; ++q) {
+            const int a = pl[2 * q], b = pl[2 * q + 1];
+            const ImgBufs &A = ib[a], &B = ib[b];
+            if (A.K == 0) {
+                LP_CUDA(c, cudaMemsetAsync(Mbuf + q, 0, sizeof(int32_t), s));
+            } else {
+                if ((rr = lp_match(c, (const float*)(base + A.desc), bf ? (const uint16_t*)(base + A.d16) : nullptr,
+                                   base + A.val, A.K, (const float*)(base + B.desc),
+                                   bf ? (const uint16_t*)(base + B.d16) : nullptr, base + B.val, B.K,
+                                   (int32_t*)(base + o_match), (float*)(base + o_d1), (float*)(base + o_d2), stream)))
+                    return rr;
+                if ((rr = lp_compact(c, (const uint32_t*)(base + A.kp), imgs[a].W, (const uint32_t*)(base + B.kp),
+                                     imgs[b].W, (const int32_t*)(base + o_match), A.K, (float*)(base + o_pts), nullptr,
+                                     Mbuf + q, stream)))
+                    return rr;
+            }
+            if ((rr = lp_ransac(c, (const float*)(base + o_pts), A.K, Mbuf + q, (uint32_t)q, HM + 9 * (size_t)q,
+                                base + o_inl, n_in + q, nullptr, stream)))
+                return rr;
+        }
+        k_pair_valid<<<(P + 127) / 128, 128, 0, s>>>(n_in, P, c->cfg.min_inliers, valid);
+        LP_CUDA(c, cudaGetLastError());
+        return LP_OK;
+    };
+    // first call for this key: run eagerly, then record the same sequence as a
+    // graph for later calls (not on the legacy default stream)
+    if ((r = enqueue())) return r;
+    if (s) {
+        if (c->graph_exec) { cudaGraphExecDestroy(c->graph_exec); c->graph_exec = nullptr; }
+        c->graph_key.clear();
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+            const int er = enqueue();
+            const cudaError_t ee = cudaStreamEndCapture(s, &g);
+            if (er == LP_OK && ee == cudaSuccess && g) {
+                if (cudaGraphInstantiate(&c->graph_exec, g, 0) == cudaSuccess) c->graph_key = key;
+                else c->graph_exec = nullptr;
+            }
+            if (g) cudaGraphDestroy(g);
+        }
+        cudaGetLastError();
+    }
     return LP_OK;
 }
 

@@ -27,6 +27,11 @@ class LpError(RuntimeError):
         self.code = code
 
 
+class lp_image(C.Structure):
+    _fields_ = [("data", C.c_void_p), ("H", C.c_int32), ("W", C.c_int32), ("pitch", C.c_int32),
+                ("channels", C.c_int32)]
+
+
 class lp_config(C.Structure):
     _fields_ = [("nL", C.c_int32), ("Ls", C.c_int32 * MAX_SCALES), ("beta0", C.c_double), ("ratio", C.c_float),
                 ("delta_s", C.c_float), ("ransac_iters", C.c_int32), ("thresh_px", C.c_float),
@@ -36,7 +41,7 @@ class lp_config(C.Structure):
 
 _lib = None
 SYMBOLS = ["lp_config_default", "lp_create", "lp_destroy", "lp_num_keypoints", "lp_detect", "lp_describe",
-           "lp_match", "lp_compact", "lp_ransac", "lp_ransac_static", "lp_stitch_pair", "lp_stitch_pair_host", "lp_sync_status",
+           "lp_match", "lp_compact", "lp_ransac", "lp_ransac_static", "lp_stitch_pair", "lp_stitch_pair_host", "lp_stitch_pairs", "lp_sync_status",
            "lp_last_error", "lp_diag_last_rescans", "lp_diag_orient_bins", "lp_diag_orient_weights", "lp_diag_philox", "lp_diag_gray"]
 
 
@@ -68,6 +73,7 @@ def load(build_if_missing: bool = True):
         "lp_ransac_static": (i32, [P, i64, P, i32, C.c_float, C.c_uint64, u32, P, P, P, P, P]),
         "lp_stitch_pair": (i32, [P, P, i32, i32, i32, P, i32, i32, i32, i32, u32, P, P, P, P]),
         "lp_stitch_pair_host": (i32, [P, P, i32, i32, i32, P, i32, i32, i32, i32, u32, P, P, P, P]),
+        "lp_stitch_pairs": (i32, [P, P, i32, P, i32, P, P, P, P, P]),
         "lp_sync_status": (i32, [P]),
         "lp_last_error": (C.c_char_p, [P]),
         "lp_diag_last_rescans": (i32, [P, C.POINTER(C.c_int64)]),
@@ -182,6 +188,17 @@ class Context:
                                                pitchB, channels, pair_id, Hh, C.byref(n), C.byref(m),
                                                _stream(stream)), "lp_stitch_pair_host")
         return [list(Hh[0:3]), list(Hh[3:6]), list(Hh[6:9])], n.value, m.value
+
+    def lp_stitch_pairs(self, images, HM, n_in, valid, pairs=None, M_out=None, stream=None):
+        """images: list of (device uint8 tensor, H, W, pitch, channels)."""
+        arr = (lp_image * len(images))(*[lp_image(_ptr(t), H, W, p, ch) for (t, H, W, p, ch) in images])
+        if pairs is None:
+            pp, P = None, 0
+        else:
+            flat = (C.c_int32 * (2 * len(pairs)))(*[int(v) for pr in pairs for v in pr])
+            pp, P = C.cast(flat, C.c_void_p), len(pairs)
+        self._chk(self.lib.lp_stitch_pairs(self.h, C.cast(arr, C.c_void_p), len(images), pp, P, _ptr(HM), _ptr(n_in),
+                                           _ptr(valid), _ptr(M_out), _stream(stream)), "lp_stitch_pairs")
 
     def lp_sync_status(self):
         return self.lib.lp_sync_status(self.h)

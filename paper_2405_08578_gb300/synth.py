@@ -195,3 +195,59 @@ def pitched(img: np.ndarray, pitch_multiple: int = 16) -> tuple[np.ndarray, int]
     buf = np.zeros((h, pitch), np.uint8)
     buf[:, :row] = img.reshape(h, row)
     return buf, pitch
+
+
+@dataclass
+class Batch:
+    images: list           # uint8 tiles (h, w, 3), shuffled order
+    H: dict                # (a, b) -> 3x3 homography from tile a to tile b (shuffled indices)
+    order: np.ndarray      # order[k] = original grid position (row-major) of shuffled tile k
+
+
+def batch_3x3(seed: int = 1, h: int = 1600, w: int = 2688, canvas_h: int = 4200, canvas_w: int = 7200,
+              rgb: bool = True) -> Batch:
+    """Nine h x w tiles of one scene on a 3 x 3 layout.
+
+    Seam overlaps ~ U[0.20, 0.35] of the tile side; each tile sees the scene
+    through its own perturbation (rotation U[-3, 3] deg, scale U[0.98, 1.02]
+    about the tile centre); the tiles are then shuffled.  Tile k's pixel q maps
+    to scene point C_k q; the homography from tile a to tile b is C_b^-1 C_a.
+    """
+    rng = np.random.default_rng(seed)
+    ox = rng.uniform(0.20, 0.35, 2)
+    oy = rng.uniform(0.20, 0.35, 2)
+    xs = [0.0, w * (1 - ox[0]), w * (1 - ox[0]) + w * (1 - ox[1])]
+    ys = [0.0, h * (1 - oy[0]), h * (1 - oy[0]) + h * (1 - oy[1])]
+    span_x, span_y = xs[2] + w, ys[2] + h
+    x0, y0 = (canvas_w - span_x) / 2.0, (canvas_h - span_y) / 2.0
+    base = scene(canvas_h, canvas_w, seed)
+    chans = None
+    if rgb:
+        nrng = np.random.default_rng(seed + 7919)
+        chans = [128.0 + g * (base - 128.0) + band_noise(nrng, canvas_h, canvas_w, 2.0) for g in (1.0, 0.9, 1.1)]
+    Cs, tiles = [], []
+    yy, xx = np.mgrid[0:h, 0:w].astype(np.float64)
+    for r in range(3):
+        for c in range(3):
+            th = rng.uniform(-3.0, 3.0)
+            sc = rng.uniform(0.98, 1.02)
+            tx, ty = x0 + xs[c], y0 + ys[r]
+            C = np.array([[1.0, 0, tx], [0, 1.0, ty], [0, 0, 1.0]]) @ similarity(th, sc, 0.0, 0.0, w / 2.0, h / 2.0)
+            X, Y = _apply(C, xx, yy)
+            if rgb:
+                t = np.empty((h, w, 3), np.uint8)
+                for k in range(3):
+                    t[:, :, k] = to_u8(bilinear(chans[k], X, Y))
+            else:
+                t = to_u8(bilinear(base, X, Y))
+            Cs.append(C)
+            tiles.append(t)
+    order = np.random.default_rng(seed).permutation(9)
+    images = [tiles[k] for k in order]
+    Hs = {}
+    for a in range(9):
+        for b in range(9):
+            if a != b:
+                Hab = np.linalg.inv(Cs[order[b]]) @ Cs[order[a]]
+                Hs[(a, b)] = Hab / Hab[2, 2]
+    return Batch(images, Hs, order)

@@ -1,0 +1,104 @@
+"""H_M of Sec. 4 through lp_stitch_pairs: every entry equals the single-pair
+path with the same pair index, the captured graph replays identically, and on
+the 3 x 3 tile batch the neighbouring tiles are registered to their true
+homographies."""
+import numpy as np
+import pytest
+
+from paper_2405_08578_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2405_08578_gb300 import lp  # noqa: E402
+import gpu_util as G  # noqa: E402
+
+
+def _outputs(P):
+    return (torch.zeros((P, 9), dtype=torch.float64, device="cuda"), torch.zeros(P, dtype=torch.int32, device="cuda"),
+            torch.zeros(P, dtype=torch.uint8, device="cuda"), torch.zeros(P, dtype=torch.int32, device="cuda"))
+
+
+@pytest.mark.parametrize("precision", [lp.PREC_FP32, lp.PREC_BF16])
+def test_stitch_pairs_equals_single_pair_path(precision):
+    h, w = 240, 320
+    base = synth.small_pair(h, w, seed=21, theta_deg=3.0, scale=1.02, shift=0.25)
+    other = synth.small_pair(h, w, seed=22, theta_deg=-2.0, scale=0.99, shift=0.2)
+    imgs = [base.A, base.B, other.A, other.B]
+    bufs = [lp.pitched_device(im) for im in imgs]
+    ctx = lp.Context(Ls=(8, 16, 32), precision=precision, seed=5)
+    images = [(b, h, w, p, 1) for (b, p) in bufs]
+    P = 6
+    HM, n_in, valid, M = _outputs(P)
+    ctx.lp_stitch_pairs(images, HM, n_in, valid, M_out=M)
+    torch.cuda.synchronize()
+    first = [t.clone() for t in (HM, n_in, valid, M)]
+    q = 0
+    for i in range(4):
+        for j in range(i + 1, 4):
+            H1 = torch.zeros(9, dtype=torch.float64, device="cuda")
+            n1 = torch.zeros(1, dtype=torch.int32, device="cuda")
+            M1 = torch.zeros(1, dtype=torch.int32, device="cuda")
+            ctx.lp_stitch_pair(bufs[i][0], h, w, bufs[i][1], bufs[j][0], h, w, bufs[j][1], 1, q, H1, n1, M1)
+            torch.cuda.synchronize()
+            assert torch.equal(HM[q], H1) and int(n_in[q]) == int(n1) and int(M[q]) == int(M1)
+            assert int(valid[q]) == int(int(n1) >= 8)
+            q += 1
+    assert int(valid[0]) == 1 and int(valid[5]) == 1          # (A, B) pairs of each scene
+    # graph replay: same outputs
+    for t in (HM, n_in, valid, M):
+        t.zero_()
+    ctx.lp_stitch_pairs(images, HM, n_in, valid, M_out=M)
+    torch.cuda.synchronize()
+    for a, b in zip(first, (HM, n_in, valid, M)):
+        assert torch.equal(a, b)
+
+
+def test_stitch_pairs_explicit_pair_list_and_errors():
+    h, w = 160, 224
+    p = synth.small_pair(h, w, seed=3)
+    bufs = [lp.pitched_device(im) for im in (p.A, p.B)]
+    ctx = lp.Context(Ls=(8, 16))
+    images = [(b, h, w, q, 1) for (b, q) in bufs]
+    HM, n_in, valid, M = _outputs(2)
+    ctx.lp_stitch_pairs(images, HM, n_in, valid, pairs=[(0, 1), (1, 0)], M_out=M)
+    torch.cuda.synchronize()
+    H01 = HM[0].cpu().numpy().reshape(3, 3)
+    H10 = HM[1].cpu().numpy().reshape(3, 3)
+    q = np.array([[60.0, 50], [150, 50], [150, 120], [60, 120]])
+    assert np.abs(G.proj(H10, G.proj(H01, q)) - q).max() < 1.0   # the two directions invert each other
+    with pytest.raises(lp.LpError):
+        ctx.lp_stitch_pairs(images, HM, n_in, valid, pairs=[(0, 2)])
+    with pytest.raises(lp.LpError):
+        ctx.lp_stitch_pairs(images[:1], HM, n_in, valid)
+
+
+def test_stitch_pairs_3x3_tiles():
+    b = synth.batch_3x3(seed=1)
+    ctx = lp.Context(Ls=synth.PAIR_2688x1600_LS, precision=lp.PREC_BF16)
+    bufs = [lp.pitched_device(im) for im in b.images]
+    images = [(t, 1600, 2688, p, 3) for (t, p) in bufs]
+    HM, n_in, valid, M = _outputs(36)
+    ctx.lp_stitch_pairs(images, HM, n_in, valid, M_out=M)
+    torch.cuda.synchronize()
+    HMh, v = HM.cpu().numpy().reshape(36, 3, 3), valid.cpu().numpy()
+    q = 0
+    found = 0
+    for i in range(9):
+        for j in range(i + 1, 9):
+            gi, gj = divmod(int(b.order[i]), 3), divmod(int(b.order[j]), 3)
+            neighbour = abs(gi[0] - gj[0]) + abs(gi[1] - gj[1]) == 1
+            if neighbour:
+                assert v[q] == 1, (i, j)
+                Ht = b.H[(i, j)]
+                ys, xs = np.mgrid[0:1600:40, 0:2688:40]
+                pts = np.c_[xs.ravel(), ys.ravel()].astype(np.float64)
+                pb = G.proj(Ht, pts)
+                ov = (pb[:, 0] >= 0) & (pb[:, 0] < 2688) & (pb[:, 1] >= 0) & (pb[:, 1] < 1600)
+                assert np.abs(G.proj(HMh[q], pts[ov]) - pb[ov]).max() < 2.0, (i, j)
+                found += 1
+            q += 1
+    assert found == 12
