@@ -59,6 +59,13 @@ def lib():
             "or_eig_sym": (i32, [i32, P, P, P]),
             "or_score": (i64, [P, P, i64, f64, P]),
             "or_ransac": (i32, [P, i64, i32, f64, C.c_uint64, u32, P, P, P, P, P, P]),
+            "or_mlp_features": (i32, [i64, P, P, P, i32, P, P, P, i32, i32, i32, i32, P]),
+            "or_mlp_forward": (i32, [P, P, i64, P, P]),
+            "or_mlp_loss_grad": (i32, [P, P, P, i64, P, P]),
+            "or_mlp_adam": (i32, [P, P, P, P, i32, i32, f64, f64, f64, f64]),
+            "or_guided_weights": (i32, [P, i64, P]),
+            "or_ransac_sample_guided": (i32, [i64, P, C.c_uint64, u32, i32, P]),
+            "or_ransac_prior": (i32, [P, i64, P, i32, f64, C.c_uint64, u32, P, P, P, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -275,3 +282,87 @@ def stitch_pair(imgA, imgB, Ls, ratio=0.8, T=1000, thresh=3.0, seed=0, pair_id=0
     r = ransac(pts, T, thresh, seed, pair_id)
     r.update(fa=fa, fb=fb, match=m, d1=d1, d2=d2, pts=pts, rows=rows)
     return r
+
+
+# ---------------------------------------------------------------------------
+# Learned RANSAC proposal (not in the paper)
+# ---------------------------------------------------------------------------
+MLP_NPARAM = 4801
+
+
+def mlp_split(params):
+    """Views W1 (64x8), b1, W2 (64x64), b2, w3 (64), b3 of a flat parameter vector."""
+    p = np.asarray(params)
+    return (p[:512].reshape(64, 8), p[512:576], p[576:4672].reshape(64, 64), p[4672:4736], p[4736:4800],
+            p[4800:4801])
+
+
+def mlp_features(d1, d2, LA, Lmax, oriA, oriB, pts, WA, HA, WB, HB):
+    d1 = _c(d1, np.float64)
+    d2 = _c(d2, np.float64)
+    LA = _c(LA, np.int32)
+    oA = _c(oriA, np.uint8)
+    oB = _c(oriB, np.uint8)
+    p = _c(pts, np.float64).reshape(-1, 4)
+    M = len(d1)
+    f = np.empty((M, 8), np.float64)
+    assert lib().or_mlp_features(M, _p(d1), _p(d2), _p(LA), int(Lmax), _p(oA), _p(oB), _p(p), WA, HA, WB, HB,
+                                 _p(f)) == 0
+    return f
+
+
+def mlp_forward(params, x):
+    P = _c(params, np.float64)
+    x = _c(x, np.float64).reshape(-1, 8)
+    z = np.empty(len(x), np.float64)
+    pr = np.empty(len(x), np.float64)
+    lib().or_mlp_forward(_p(P), _p(x), len(x), _p(z), _p(pr))
+    return z, pr
+
+
+def mlp_loss_grad(params, x, y):
+    P = _c(params, np.float64)
+    x = _c(x, np.float64).reshape(-1, 8)
+    y = _c(y, np.uint8)
+    g = np.empty(MLP_NPARAM, np.float64)
+    L = C.c_double()
+    assert lib().or_mlp_loss_grad(_p(P), _p(x), _p(y), len(x), C.byref(L), _p(g)) == 0
+    return L.value, g
+
+
+def mlp_adam(params, m, v, grad, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+    """In place on float64 arrays params, m, v."""
+    assert params.dtype == m.dtype == v.dtype == np.float64
+    g = _c(grad, np.float64)
+    assert lib().or_mlp_adam(_p(params), _p(m), _p(v), _p(g), len(params), int(t), lr, b1, b2, eps) == 0
+
+
+def guided_weights(prob):
+    pr = _c(prob, np.float32)
+    out = np.empty(len(pr), np.uint64)
+    lib().or_guided_weights(_p(pr), len(pr), _p(out))
+    return out
+
+
+def ransac_sample_guided(prefix, seed, pair_id, t):
+    pf = _c(prefix, np.uint64)
+    s = np.empty(4, np.int32)
+    r = lib().or_ransac_sample_guided(len(pf), _p(pf), seed, pair_id, t, _p(s))
+    return None if r else s
+
+
+def ransac_prior(pts, prob, T=1000, thresh=3.0, seed=0, pair_id=0, want_counts=False):
+    p = _c(pts, np.float64).reshape(-1, 4)
+    pr = _c(prob, np.float32)
+    M = len(p)
+    H = np.empty(9, np.float64)
+    inl = np.empty(max(M, 1), np.uint8)
+    n_in = C.c_int32()
+    bt = C.c_int32()
+    counts = np.empty(T, np.int32) if want_counts else None
+    lib().or_ransac_prior(_p(p), M, _p(pr), T, float(thresh), seed, pair_id, _p(H), _p(inl), C.byref(n_in),
+                          C.byref(bt), _p(counts))
+    out = dict(H=H.reshape(3, 3), inliers=inl[:M], n_in=int(n_in.value), best_t=int(bt.value))
+    if want_counts:
+        out["counts"] = counts
+    return out

@@ -637,3 +637,221 @@ int or_ransac(const double* pts, int64_t M, int T, double thresh, uint64_t seed,
     memcpy(H, Hf, sizeof Hf);
     return 0;
 }
+
+/* ------------------------------------------------------------------ */
+/* Learned RANSAC proposal (not in the paper).  A small network scores each
+ * tentative match; RANSAC then draws its samples with probability
+ * proportional to the score.  The scoring of hypotheses is unchanged, so the
+ * winner is still judged by all matches. */
+
+/* Features of one match: the ratio-test quantities, the scale of the
+ * reference point, the orientation difference and both positions. */
+int or_mlp_features(int64_t M, const double* d1, const double* d2, const int32_t* LA, int Lmax,
+                    const uint8_t* oriA, const uint8_t* oriB, const double* pts, int WA, int HA, int WB, int HB,
+                    double* feat)
+{
+    if (M < 0 || Lmax < 2) return -1;
+    for (int64_t i = 0; i < M; ++i) {
+        double* f = feat + 8 * i;
+        f[0] = d2[i] > 0 ? d1[i] / d2[i] : 1.0;
+        f[1] = d1[i];
+        f[2] = log2((double)LA[i]) / log2((double)Lmax);
+        int dk = ((int)oriB[i] - (int)oriA[i]) % 36;
+        if (dk < 0) dk += 36;
+        double dth = 10.0 * dk;                 /* degrees in [0, 360) */
+        if (dth >= 180.0) dth -= 360.0;         /* [-180, 180) */
+        f[3] = dth / 180.0;
+        f[4] = pts[4 * i] / WA;
+        f[5] = pts[4 * i + 1] / HA;
+        f[6] = pts[4 * i + 2] / WB;
+        f[7] = pts[4 * i + 3] / HB;
+    }
+    return 0;
+}
+
+static double sigmoid(double z)
+{
+    if (z >= 0) return 1.0 / (1.0 + exp(-z));
+    double e = exp(z);
+    return e / (1.0 + e);
+}
+
+/* One forward pass, keeping the hidden activations. */
+static double mlp_fwd1(const double* P, const double* x, double* h1, double* h2)
+{
+    const double *W1 = P, *b1 = P + 512, *W2 = P + 576, *b2 = P + 4672, *w3 = P + 4736, *b3 = P + 4800;
+    for (int i = 0; i < 64; ++i) {
+        double s = b1[i];
+        for (int j = 0; j < 8; ++j) s += W1[8 * i + j] * x[j];
+        h1[i] = s > 0 ? s : 0;
+    }
+    for (int i = 0; i < 64; ++i) {
+        double s = b2[i];
+        for (int j = 0; j < 64; ++j) s += W2[64 * i + j] * h1[j];
+        h2[i] = s > 0 ? s : 0;
+    }
+    double z = b3[0];
+    for (int j = 0; j < 64; ++j) z += w3[j] * h2[j];
+    return z;
+}
+
+int or_mlp_forward(const double* params, const double* x, int64_t M, double* logit, double* prob)
+{
+    double h1[64], h2[64];
+    for (int64_t i = 0; i < M; ++i) {
+        double z = mlp_fwd1(params, x + 8 * i, h1, h2);
+        if (logit) logit[i] = z;
+        if (prob) prob[i] = sigmoid(z);
+    }
+    return 0;
+}
+
+/* L = (1/B) sum_i max(z_i, 0) - z_i y_i + log(1 + exp(-|z_i|)); dL/dz_i =
+ * (sigmoid(z_i) - y_i) / B, propagated back through the two ReLU layers. */
+int or_mlp_loss_grad(const double* params, const double* x, const uint8_t* y, int64_t B, double* loss, double* grad)
+{
+    if (B <= 0) return -1;
+    const double *W2 = params + 576, *w3 = params + 4736;
+    double *gW1 = grad, *gb1 = grad + 512, *gW2 = grad + 576, *gb2 = grad + 4672, *gw3 = grad + 4736, *gb3 = grad + 4800;
+    memset(grad, 0, sizeof(double) * OR_MLP_NPARAM);
+    double L = 0;
+    for (int64_t n = 0; n < B; ++n) {
+        const double* xn = x + 8 * n;
+        double h1[64], h2[64], d2[64], d1[64];
+        double z = mlp_fwd1(params, xn, h1, h2);
+        double yn = y[n] ? 1.0 : 0.0;
+        L += (z > 0 ? z : 0) - z * yn + log1p(exp(-fabs(z)));
+        double dz = (sigmoid(z) - yn) / (double)B;
+        gb3[0] += dz;
+        for (int j = 0; j < 64; ++j) {
+            gw3[j] += dz * h2[j];
+            d2[j] = h2[j] > 0 ? dz * w3[j] : 0;
+        }
+        for (int i = 0; i < 64; ++i) {
+            gb2[i] += d2[i];
+            for (int j = 0; j < 64; ++j) gW2[64 * i + j] += d2[i] * h1[j];
+        }
+        for (int j = 0; j < 64; ++j) {
+            double s = 0;
+            for (int i = 0; i < 64; ++i) s += W2[64 * i + j] * d2[i];
+            d1[j] = h1[j] > 0 ? s : 0;
+        }
+        for (int i = 0; i < 64; ++i) {
+            gb1[i] += d1[i];
+            for (int j = 0; j < 8; ++j) gW1[8 * i + j] += d1[i] * xn[j];
+        }
+    }
+    if (loss) *loss = L / (double)B;
+    return 0;
+}
+
+/* Adam (Kingma & Ba): bias-corrected first and second moments. */
+int or_mlp_adam(double* params, double* m, double* v, const double* grad, int n, int t, double lr, double b1,
+                double b2, double eps)
+{
+    if (t < 1) return -1;
+    double c1 = 1.0 - pow(b1, t), c2 = 1.0 - pow(b2, t);
+    for (int i = 0; i < n; ++i) {
+        m[i] = b1 * m[i] + (1 - b1) * grad[i];
+        v[i] = b2 * v[i] + (1 - b2) * grad[i] * grad[i];
+        params[i] -= lr * (m[i] / c1) / (sqrt(v[i] / c2) + eps);
+    }
+    return 0;
+}
+
+/* Guided sampling weights: q_i = round(65536 * max(p_i, 1e-3)) with p_i the
+ * FP32 prior and 1e-3 the FP32 constant, as integers (no rounding can differ
+ * between implementations); prefix holds the inclusive prefix sums. */
+int or_guided_weights(const float* prob, int64_t M, uint64_t* prefix)
+{
+    uint64_t acc = 0;
+    for (int64_t i = 0; i < M; ++i) {
+        double p = (double)prob[i];
+        double lo = (double)1e-3f;
+        if (!(p > lo)) p = lo;      /* also maps NaN to the floor */
+        acc += (uint64_t)floor(65536.0 * p + 0.5);
+        prefix[i] = acc;
+    }
+    return 0;
+}
+
+/* Word j of iteration t's Philox stream (as or_ransac_sample) picks the
+ * match whose prefix interval contains floor(word * total / 2^32): probability
+ * proportional to q_i.  Repeated indices are redrawn (sampling without
+ * replacement), at most 64 words. */
+int or_ransac_sample_guided(int64_t M, const uint64_t* prefix, uint64_t seed, uint32_t pair_id, int t, int32_t* idx4)
+{
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32) ^ pair_id};
+    uint32_t blk[4];
+    const uint64_t total = prefix[M - 1];
+    int n = 0;
+    for (int j = 0; j < 64 && n < 4; ++j) {
+        if (j % 4 == 0) {
+            uint32_t ctr[4] = {(uint32_t)t, (uint32_t)(j / 4), 0u, 0u};
+            or_philox4x32_10(ctr, key, blk);
+        }
+        uint64_t target = (uint64_t)(((unsigned __int128)blk[j % 4] * total) >> 32);
+        int64_t lo = 0, hi = M - 1;   /* first i with prefix[i] > target */
+        while (lo < hi) {
+            int64_t mid = (lo + hi) / 2;
+            if (prefix[mid] > target) hi = mid; else lo = mid + 1;
+        }
+        int32_t i = (int32_t)lo;
+        int dup = 0;
+        for (int q = 0; q < n; ++q) dup |= idx4[q] == i;
+        if (!dup) idx4[n++] = i;
+    }
+    return n == 4 ? 0 : 1;
+}
+
+int or_ransac_prior(const double* pts, int64_t M, const float* prob, int T, double thresh, uint64_t seed,
+                    uint32_t pair_id, double* H, uint8_t* inl, int32_t* n_in, int32_t* best_t, int32_t* counts)
+{
+    memset(H, 0, sizeof(double) * 9);
+    *n_in = 0;
+    *best_t = -1;
+    if (inl) memset(inl, 0, (size_t)M);
+    if (counts)
+        for (int t = 0; t < T; ++t) counts[t] = -1;
+    if (M < 4) return 1;
+    uint64_t* prefix = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)M);
+    or_guided_weights(prob, M, prefix);
+    int64_t bestc = -1;
+    double Hb[9];
+    for (int t = 0; t < T; ++t) {
+        int32_t s[4];
+        if (or_ransac_sample_guided(M, prefix, seed, pair_id, t, s)) continue;
+        double src[8], dst[8];
+        for (int j = 0; j < 4; ++j) {
+            src[2 * j] = pts[4 * s[j]]; src[2 * j + 1] = pts[4 * s[j] + 1];
+            dst[2 * j] = pts[4 * s[j] + 2]; dst[2 * j + 1] = pts[4 * s[j] + 3];
+        }
+        int deg = 0;
+        for (int a = 0; a < 4; ++a) {
+            int i0 = (a + 1) % 4, i1 = (a + 2) % 4, i2 = (a + 3) % 4;
+            deg |= collinear(src + 2 * i0, src + 2 * i1, src + 2 * i2);
+            deg |= collinear(dst + 2 * i0, dst + 2 * i1, dst + 2 * i2);
+        }
+        if (deg) continue;
+        double Ht[9];
+        if (or_dlt4(src, dst, Ht)) continue;
+        int64_t c = or_score(Ht, pts, M, thresh, NULL);
+        if (counts) counts[t] = (int32_t)c;
+        if (c > bestc) {
+            bestc = c;
+            *best_t = t;
+            memcpy(Hb, Ht, sizeof Hb);
+        }
+    }
+    free(prefix);
+    if (bestc < 0) return 1;
+    uint8_t* m = (uint8_t*)malloc((size_t)M);
+    or_score(Hb, pts, M, thresh, m);
+    double Hf[9];
+    if (or_refit(pts, m, M, Hf)) memcpy(Hf, Hb, sizeof Hf);
+    *n_in = (int32_t)or_score(Hf, pts, M, thresh, m);
+    if (inl) memcpy(inl, m, (size_t)M);
+    free(m);
+    memcpy(H, Hf, sizeof Hf);
+    return 0;
+}

@@ -79,6 +79,37 @@ int64_t or_score(const double* H, const double* pts, int64_t M, double thresh, u
 int or_ransac(const double* pts, int64_t M, int T, double thresh, uint64_t seed, uint32_t pair_id,
               double* H, uint8_t* inl, int32_t* n_in, int32_t* best_t, int32_t* counts, double* Hs);
 
+
+/* ---- learned RANSAC proposal (not in the paper) -- TEST INFRASTRUCTURE ---- */
+#define OR_MLP_NPARAM 4801
+/* Parameter layout: W1[64][8], b1[64], W2[64][64], b2[64], w3[64], b3. */
+
+/* Eight features of one match (A point -> B point):
+ * d1/d2, d1, log2(L_A)/log2(Lmax), wrap(theta_B - theta_A)/pi,
+ * x_A/W_A, y_A/H_A, x_B/W_B, y_B/H_B. */
+int or_mlp_features(int64_t M, const double* d1, const double* d2, const int32_t* LA, int Lmax,
+                    const uint8_t* oriA, const uint8_t* oriB, const double* pts /*M x 4*/, int WA, int HA, int WB,
+                    int HB, double* feat /*M x 8*/);
+
+/* z = w3 . relu(W2 relu(W1 x + b1) + b2) + b3, p = sigmoid(z). */
+int or_mlp_forward(const double* params, const double* x, int64_t M, double* logit, double* prob);
+
+/* Mean binary cross-entropy with logits and its gradient. */
+int or_mlp_loss_grad(const double* params, const double* x, const uint8_t* y, int64_t B, double* loss, double* grad);
+
+/* One Adam step (t >= 1): m, v updated in place. */
+int or_mlp_adam(double* params, double* m, double* v, const double* grad, int n, int t, double lr, double b1,
+                double b2, double eps);
+
+/* Guided draw of four distinct matches from integer weights (see lp_oracle.c). */
+int or_ransac_sample_guided(int64_t M, const uint64_t* prefix /* inclusive prefix sums of q */, uint64_t seed,
+                            uint32_t pair_id, int t, int32_t* idx4);
+int or_guided_weights(const float* prob, int64_t M, uint64_t* prefix);
+
+/* RANSAC as or_ransac, drawing samples with probability proportional to the
+ * prior (prob != NULL) instead of uniformly; scoring is unchanged. */
+int or_ransac_prior(const double* pts, int64_t M, const float* prob, int T, double thresh, uint64_t seed,
+                    uint32_t pair_id, double* H, uint8_t* inl, int32_t* n_in, int32_t* best_t, int32_t* counts);
 #ifdef __cplusplus
 }
 #endif
