@@ -235,13 +235,71 @@ def run_lp(args, rank, world):
                 K=K, pair=pair, h2d=int(hostA.numel() + hostB.numel()), bf=bf, rescans=rescans)
 
 
+def fp32_form_and_batch(args, rank):
+    """Side measurements on the same GPU: the plain FP32 form of the same pair
+    (the comparison the metric names) and the nine-tile batch (36 pairs, one
+    lp_stitch_pairs call replayed as a CUDA graph)."""
+    import torch
+
+    from paper_2405_08578_gb300 import lp, synth
+    out = {}
+    s = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    pair = synth.pair_2688x1600(seed=rank)
+    ctx = lp.Context(Ls=LS, precision=lp.PREC_FP32)
+    bA, pA = lp.pitched_device(pair.A)
+    bB, pB = lp.pitched_device(pair.B)
+    H = torch.zeros(9, dtype=torch.float64, device="cuda")
+    n = torch.zeros(1, dtype=torch.int32, device="cuda")
+    M = torch.zeros(1, dtype=torch.int32, device="cuda")
+    for _ in range(2):
+        ctx.lp_stitch_pair(bA, H_IMG, W_IMG, pA, bB, H_IMG, W_IMG, pB, 3, rank, H, n, M)
+    torch.cuda.synchronize()
+    k = max(3, args.steps // 3)
+    t = 0.0
+    for _ in range(k):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        ctx.lp_stitch_pair(bA, H_IMG, W_IMG, pA, bB, H_IMG, W_IMG, pB, 3, rank, H, n, M)
+        b.record(s)
+        torch.cuda.synchronize()
+        t += a.elapsed_time(b) / 1e3
+    out["fp32_form_pairs_per_s"] = k / t
+    out["fp32_form_inliers"] = int(n.item())
+    del ctx
+    bt = synth.batch_3x3(seed=1)
+    ctx = lp.Context(Ls=LS, precision=lp.PREC_BF16)
+    bufs = [lp.pitched_device(im) for im in bt.images]
+    images = [(tb, H_IMG, W_IMG, pb, 3) for (tb, pb) in bufs]
+    HM = torch.zeros((36, 9), dtype=torch.float64, device="cuda")
+    ni = torch.zeros(36, dtype=torch.int32, device="cuda")
+    va = torch.zeros(36, dtype=torch.uint8, device="cuda")
+    for _ in range(3):
+        ctx.lp_stitch_pairs(images, HM, ni, va)
+    torch.cuda.synchronize()
+    t = 0.0
+    for _ in range(k):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        ctx.lp_stitch_pairs(images, HM, ni, va)
+        b.record(s)
+        torch.cuda.synchronize()
+        t += a.elapsed_time(b) / 1e3
+    out["batch_3x3"] = {"images": 9, "pairs": 36, "pairs_per_s": 36 * k / t, "ms_per_batch": 1e3 * t / k,
+                        "valid_pairs": int(va.sum().item()), "graph": True}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="lp", choices=["lp", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16"])
+    ap.add_argument("--no-extras", action="store_true", help="skip the FP32-form and 3x3-batch side measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -292,7 +350,9 @@ def main():
     roof["traffic"] = None
     roof["peak_source"] = f"{pk_kind}" if r["bf"] else "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"
     value = world * args.steps / r["t_steps"]
-    launches_per_step = 13
+    # our kernels per step (BF16 form): detect 2, describe 6, match 8, compact 1,
+    # RANSAC 8; FP32 form: detect 2, describe 6, match 4, compact 1, RANSAC 8
+    launches_per_step = 25 if r["bf"] else 21
     line = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * r["t_steps"] / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if r["bf"] else "f32", "data": "synthetic",
@@ -304,6 +364,12 @@ def main():
             "e2e": {"value": world * args.steps / r["e2e_t"], "unit": "pairs/s", "h2d_bytes_per_step": r["h2d"],
                     "d2h_bytes_per_step": 9 * 8 + 2 * 4},
             "gpu_launches": launches_per_step * args.steps, "clocks": r["clocks"]}
+    if not args.no_extras:
+        extra = fp32_form_and_batch(args, rank)
+        line["config"]["fp32_form_pairs_per_s"] = extra["fp32_form_pairs_per_s"]
+        line["config"]["speedup_vs_fp32_form"] = value / world / extra["fp32_form_pairs_per_s"]
+        line["config"]["fp32_form_inliers"] = extra["fp32_form_inliers"]
+        line["config"]["batch_3x3"] = extra["batch_3x3"]
     if world == 1 and not args.no_cpu_baseline:
         tot, parts, sample = oracle_pair_seconds(r["pair"], M=max(r["M"], 4))
         line["cpu_baseline"] = {"value": 1.0 / tot, "unit": "pairs/s", "cores": 1, "kind": "oracle",

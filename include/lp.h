@@ -231,6 +231,85 @@ typedef struct lp_image {
 LP_API int lp_stitch_pairs(lp_ctx* ctx, const lp_image* imgs, int N, const int32_t* pairs, int P, double* HM,
                            int32_t* n_in, uint8_t* valid, int32_t* M_out, void* stream);
 
+/* ---- learned RANSAC proposal (not in the paper) ----
+ * A small network scores each matched pair's chance of being an inlier;
+ * RANSAC can then draw its samples in proportion to the score.  Scoring of the
+ * hypotheses is unchanged (every match votes), so the winner is judged exactly
+ * as in uniform RANSAC, which remains the default. */
+
+typedef struct lp_mlp lp_mlp;
+#define LP_MLP_PARAMS 4801   /* W1[64][8], b1[64], W2[64][64], b2[64], w3[64], b3 */
+
+/* Create a network on the current device: He-uniform weights from `seed`
+ * (zero biases), FP32 master weights, a BF16-rounded copy used by every
+ * forward pass, zero Adam state.  Errors: LP_ERR_ARG, LP_ERR_CUDA. */
+LP_API int lp_mlp_create(lp_mlp** mlp, uint64_t seed);
+LP_API int lp_mlp_destroy(lp_mlp* mlp);
+
+/* Host copies of the FP32 master weights (float[LP_MLP_PARAMS]); set also
+ * resets the Adam state and the step count.  Synchronous. */
+LP_API int lp_mlp_set_params(lp_mlp* mlp, const float* host_params);
+LP_API int lp_mlp_get_params(lp_mlp* mlp, float* host_params);
+
+/* Host copy of the whole optimiser state, float[3 * LP_MLP_PARAMS]: master
+ * weights, Adam first moments m, second moments v; *step = Adam steps taken
+ * (may be NULL).  Synchronous. */
+LP_API int lp_mlp_get_state(lp_mlp* mlp, float* host_state, int32_t* step);
+
+/* Checkpoint: magic, step count, weights and Adam moments in one binary file. */
+LP_API int lp_mlp_save(lp_mlp* mlp, const char* path);
+LP_API int lp_mlp_load(lp_mlp* mlp, const char* path);
+
+/* Features of the compacted matched pairs (see lp_compact; `rows` required):
+ * d1/d2, d1, log2(L_A)/log2(Lmax), wrap(theta_B - theta_A)/pi in [-1, 1),
+ * x_A/W_A, y_A/H_A, x_B/W_B, y_B/H_B.
+ *  kpA, oriA / kpB, oriB   device outputs of lp_detect / lp_describe
+ *  match, d1, d2           device outputs of lp_match (indexed by A row)
+ *  rows, d_M               device outputs of lp_compact (A row per pair, M)
+ *  feat                    device float[M_cap*8]
+ * The scale L_A of a point follows from its index (the context's L set and
+ * image A's size).  Errors: LP_ERR_ARG, LP_ERR_CUDA. */
+LP_API int lp_mlp_features(lp_ctx* ctx, const uint32_t* kpA, const uint8_t* oriA, int HA, int WA,
+                           const uint32_t* kpB, const uint8_t* oriB, int HB, int WB, const int32_t* match,
+                           const float* d1, const float* d2, const int32_t* rows, const int32_t* d_M, int64_t M_cap,
+                           float* feat, void* stream);
+
+/* Inlier probability (sigmoid of the logit) of M = *d_M (or M_cap) matches;
+ * prob / logit device float[M_cap], either may be NULL. */
+LP_API int lp_mlp_forward(lp_mlp* mlp, const float* feat, int64_t M_cap, const int32_t* d_M, float* prob,
+                          float* logit, void* stream);
+
+/* One Adam step (lr, beta 0.9 / 0.999, eps 1e-8) on the mean binary
+ * cross-entropy (with logits) of a minibatch of B samples.
+ *  feat  device float[B*8]; label device uint8[B] (1 = inlier)
+ *  loss  device float (the minibatch loss before the step) or NULL */
+LP_API int lp_mlp_train_step(lp_mlp* mlp, const float* feat, const uint8_t* label, int64_t B, float lr, float* loss,
+                             void* stream);
+
+/* RANSAC guided by a prior, with uniform RANSAC as fallback and judge.
+ * Guided phase: guided_iters hypotheses whose samples are drawn in proportion
+ * to the prior -- match i gets the integer weight
+ * q_i = floor(65536 * max(prior_i, 1e-3) + 1/2) (NaN counts as 1e-3), and
+ * Philox word w of iteration t (the stream of lp_ransac) picks the match whose
+ * interval of the inclusive prefix sums of q holds floor(w * sum(q) / 2^32);
+ * repeated indices are redrawn.  Every hypothesis is scored by all matches, as
+ * in lp_ransac.  Stop test: with w = (sum of q over the guided winner's
+ * inliers) / sum(q), the chance that a guided draw is an inlier, the phase
+ * stops when (1 - w^4)^guided_iters <= 0.01 -- the standard bound
+ * T >= log(0.01) / log(1 - w^4).  Then the guided winner is refitted as in
+ * lp_ransac.  Otherwise the uniform phase runs: exactly lp_ransac with the
+ * context's T (the test and the skipped work are decided on the device, so
+ * the call never waits for the host).
+ *  prior         device float[M_cap] (e.g. lp_mlp_forward's prob)
+ *  guided_iters  1..65536
+ *  best_t        winner: t < guided_iters (guided) or guided_iters + t
+ *                (uniform iteration t); -1 if no model; device, or NULL
+ *  iters_used    device int32: guided_iters, or guided_iters + T; or NULL
+ * Other arguments and errors as lp_ransac. */
+LP_API int lp_ransac_prior(lp_ctx* ctx, const float* pts, int64_t M_cap, const int32_t* d_M, const float* prior,
+                           int32_t guided_iters, uint32_t pair_id, double* H, uint8_t* inlier, int32_t* n_inliers,
+                           int32_t* best_t, int32_t* iters_used, void* stream);
+
 /* Wait for the context's last stream, then return and clear the device
  * status word (LP_OK, LP_ERR_TIMEOUT or LP_ERR_DEVICE) or a CUDA error. */
 LP_API int lp_sync_status(lp_ctx* ctx);
@@ -243,6 +322,12 @@ LP_API const char* lp_last_error(lp_ctx* ctx);
 /* Rows that the last LP_PREC_BF16 lp_match of this context re-scanned in FP32
  * because their BF16 ranking could not be certified (waits for the stream). */
 LP_API int lp_diag_last_rescans(lp_ctx* ctx, int64_t* out);
+
+/* FP32 inlier count (points certainly inside the threshold) of each hypothesis
+ * of the context's last lp_ransac (n = T) or lp_ransac_prior
+ * (n = guided_iters + T) call; -1 where no hypothesis was formed or the phase
+ * was skipped.  host int32[n]; waits for the stream. */
+LP_API int lp_diag_last_ransac_counts(lp_ctx* ctx, int32_t* host_counts, int n);
 
 /* Orientation bin of every integer gradient (a, b) in [-255, 255]^2, written
  * to device int32[511*511] at (a + 255) * 511 + (b + 255). */

@@ -65,7 +65,8 @@ def lib():
             "or_mlp_adam": (i32, [P, P, P, P, i32, i32, f64, f64, f64, f64]),
             "or_guided_weights": (i32, [P, i64, P]),
             "or_ransac_sample_guided": (i32, [i64, P, C.c_uint64, u32, i32, P]),
-            "or_ransac_prior": (i32, [P, i64, P, i32, f64, C.c_uint64, u32, P, P, P, P, P]),
+            "or_ransac_prior": (i32, [P, i64, P, i32, i32, f64, C.c_uint64, u32, P, P, P, P, P, P]),
+            "or_guided_stop": (i32, [C.c_uint64, C.c_uint64, i32]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -351,7 +352,8 @@ def ransac_sample_guided(prefix, seed, pair_id, t):
     return None if r else s
 
 
-def ransac_prior(pts, prob, T=1000, thresh=3.0, seed=0, pair_id=0, want_counts=False):
+def ransac_prior(pts, prob, Tg=64, T=1000, thresh=3.0, seed=0, pair_id=0, want_counts=False):
+    """Guided phase of Tg hypotheses, then uniform fallback of T (see lp_oracle.h)."""
     p = _c(pts, np.float64).reshape(-1, 4)
     pr = _c(prob, np.float32)
     M = len(p)
@@ -359,10 +361,15 @@ def ransac_prior(pts, prob, T=1000, thresh=3.0, seed=0, pair_id=0, want_counts=F
     inl = np.empty(max(M, 1), np.uint8)
     n_in = C.c_int32()
     bt = C.c_int32()
-    counts = np.empty(T, np.int32) if want_counts else None
-    lib().or_ransac_prior(_p(p), M, _p(pr), T, float(thresh), seed, pair_id, _p(H), _p(inl), C.byref(n_in),
-                          C.byref(bt), _p(counts))
-    out = dict(H=H.reshape(3, 3), inliers=inl[:M], n_in=int(n_in.value), best_t=int(bt.value))
+    it = C.c_int32()
+    counts = np.empty(Tg + T, np.int32) if want_counts else None
+    lib().or_ransac_prior(_p(p), M, _p(pr), int(Tg), int(T), float(thresh), seed, pair_id, _p(H), _p(inl),
+                          C.byref(n_in), C.byref(bt), C.byref(it), _p(counts))
+    out = dict(H=H.reshape(3, 3), inliers=inl[:M], n_in=int(n_in.value), best_t=int(bt.value), iters=int(it.value))
     if want_counts:
         out["counts"] = counts
     return out
+
+
+def guided_stop(s_in, total, Tg) -> bool:
+    return bool(lib().or_guided_stop(int(s_in), int(total), int(Tg)))

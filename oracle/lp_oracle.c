@@ -804,49 +804,92 @@ int or_ransac_sample_guided(int64_t M, const uint64_t* prefix, uint64_t seed, ui
     return n == 4 ? 0 : 1;
 }
 
-int or_ransac_prior(const double* pts, int64_t M, const float* prob, int T, double thresh, uint64_t seed,
-                    uint32_t pair_id, double* H, uint8_t* inl, int32_t* n_in, int32_t* best_t, int32_t* counts)
+/* Stop test of the guided phase: the standard RANSAC bound T >= log(0.01) /
+ * log(1 - w^4), rewritten as (1 - w^4)^T <= 0.01 (the chance that T samples
+ * all contained an outlier), with w the prior-weighted inlier fraction
+ * s_in / total of the guided winner: the probability that one guided draw
+ * lands on an inlier.  Powers by binary exponentiation. */
+int or_guided_stop(uint64_t s_in, uint64_t total, int Tg)
+{
+    if (total == 0 || Tg <= 0) return 0;
+    const double w = (double)s_in / (double)total;
+    const double w2 = w * w;
+    const double w4 = w2 * w2;
+    double b = 1.0 - w4, r = 1.0;
+    for (int e = Tg; e; e >>= 1) {
+        if (e & 1) r = r * b;
+        b = b * b;
+    }
+    return r <= 0.01;
+}
+
+/* Learned-proposal RANSAC: Tg hypotheses from guided samples are scored by all
+ * matches; when the stop test holds for the guided winner, it is refitted as in
+ * or_ransac; otherwise the call falls back to uniform RANSAC with T iterations
+ * (or_ransac itself, whose best_t is reported offset by Tg). */
+int or_ransac_prior(const double* pts, int64_t M, const float* prob, int Tg, int T, double thresh, uint64_t seed,
+                    uint32_t pair_id, double* H, uint8_t* inl, int32_t* n_in, int32_t* best_t, int32_t* iters,
+                    int32_t* counts /* Tg + T or NULL */)
 {
     memset(H, 0, sizeof(double) * 9);
     *n_in = 0;
     *best_t = -1;
-    if (inl) memset(inl, 0, (size_t)M);
+    *iters = Tg + T;
+    if (inl) memset(inl, 0, (size_t)(M > 0 ? M : 0));
     if (counts)
-        for (int t = 0; t < T; ++t) counts[t] = -1;
-    if (M < 4) return 1;
-    uint64_t* prefix = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)M);
-    or_guided_weights(prob, M, prefix);
+        for (int t = 0; t < Tg + T; ++t) counts[t] = -1;
     int64_t bestc = -1;
     double Hb[9];
-    for (int t = 0; t < T; ++t) {
-        int32_t s[4];
-        if (or_ransac_sample_guided(M, prefix, seed, pair_id, t, s)) continue;
-        double src[8], dst[8];
-        for (int j = 0; j < 4; ++j) {
-            src[2 * j] = pts[4 * s[j]]; src[2 * j + 1] = pts[4 * s[j] + 1];
-            dst[2 * j] = pts[4 * s[j] + 2]; dst[2 * j + 1] = pts[4 * s[j] + 3];
-        }
-        int deg = 0;
-        for (int a = 0; a < 4; ++a) {
-            int i0 = (a + 1) % 4, i1 = (a + 2) % 4, i2 = (a + 3) % 4;
-            deg |= collinear(src + 2 * i0, src + 2 * i1, src + 2 * i2);
-            deg |= collinear(dst + 2 * i0, dst + 2 * i1, dst + 2 * i2);
-        }
-        if (deg) continue;
-        double Ht[9];
-        if (or_dlt4(src, dst, Ht)) continue;
-        int64_t c = or_score(Ht, pts, M, thresh, NULL);
-        if (counts) counts[t] = (int32_t)c;
-        if (c > bestc) {
-            bestc = c;
-            *best_t = t;
-            memcpy(Hb, Ht, sizeof Hb);
+    int tg = -1;
+    uint64_t* prefix = NULL;
+    if (M >= 4) {
+        prefix = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)M);
+        or_guided_weights(prob, M, prefix);
+        for (int t = 0; t < Tg; ++t) {
+            int32_t s[4];
+            if (or_ransac_sample_guided(M, prefix, seed, pair_id, t, s)) continue;
+            double src[8], dst[8];
+            for (int j = 0; j < 4; ++j) {
+                src[2 * j] = pts[4 * s[j]]; src[2 * j + 1] = pts[4 * s[j] + 1];
+                dst[2 * j] = pts[4 * s[j] + 2]; dst[2 * j + 1] = pts[4 * s[j] + 3];
+            }
+            int deg = 0;
+            for (int a = 0; a < 4; ++a) {
+                int i0 = (a + 1) % 4, i1 = (a + 2) % 4, i2 = (a + 3) % 4;
+                deg |= collinear(src + 2 * i0, src + 2 * i1, src + 2 * i2);
+                deg |= collinear(dst + 2 * i0, dst + 2 * i1, dst + 2 * i2);
+            }
+            if (deg) continue;
+            double Ht[9];
+            if (or_dlt4(src, dst, Ht)) continue;
+            int64_t c = or_score(Ht, pts, M, thresh, NULL);
+            if (counts) counts[t] = (int32_t)c;
+            if (c > bestc) {
+                bestc = c;
+                tg = t;
+                memcpy(Hb, Ht, sizeof Hb);
+            }
         }
     }
+    int stop = 0;
+    uint8_t* m = (uint8_t*)malloc((size_t)(M > 0 ? M : 1));
+    if (tg >= 0) {
+        or_score(Hb, pts, M, thresh, m);
+        uint64_t s_in = 0;
+        for (int64_t i = 0; i < M; ++i)
+            if (m[i]) s_in += prefix[i] - (i ? prefix[i - 1] : 0);
+        stop = or_guided_stop(s_in, prefix[M - 1], Tg);
+    }
     free(prefix);
-    if (bestc < 0) return 1;
-    uint8_t* m = (uint8_t*)malloc((size_t)M);
-    or_score(Hb, pts, M, thresh, m);
+    if (!stop) {
+        free(m);
+        int32_t bt;
+        int r = or_ransac(pts, M, T, thresh, seed, pair_id, H, inl, n_in, &bt, counts ? counts + Tg : NULL, NULL);
+        *best_t = bt >= 0 ? Tg + bt : -1;
+        return r;
+    }
+    *iters = Tg;
+    *best_t = tg;
     double Hf[9];
     if (or_refit(pts, m, M, Hf)) memcpy(Hf, Hb, sizeof Hf);
     *n_in = (int32_t)or_score(Hf, pts, M, thresh, m);

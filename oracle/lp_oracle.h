@@ -106,10 +106,18 @@ int or_ransac_sample_guided(int64_t M, const uint64_t* prefix /* inclusive prefi
                             uint32_t pair_id, int t, int32_t* idx4);
 int or_guided_weights(const float* prob, int64_t M, uint64_t* prefix);
 
-/* RANSAC as or_ransac, drawing samples with probability proportional to the
- * prior (prob != NULL) instead of uniformly; scoring is unchanged. */
-int or_ransac_prior(const double* pts, int64_t M, const float* prob, int T, double thresh, uint64_t seed,
-                    uint32_t pair_id, double* H, uint8_t* inl, int32_t* n_in, int32_t* best_t, int32_t* counts);
+/* Stop test of the guided phase: (1 - w^4)^Tg <= 0.01 with w = s_in / total
+ * (the standard bound T >= log(0.01) / log(1 - w^4)). */
+int or_guided_stop(uint64_t s_in, uint64_t total, int Tg);
+
+/* Tg guided hypotheses (samples drawn with probability proportional to the
+ * prior), scored by all matches; the guided winner is refitted when
+ * or_guided_stop holds for its prior-weighted inlier fraction, otherwise the
+ * result is uniform or_ransac with T iterations (best_t offset by Tg).
+ * iters = Tg or Tg + T; counts (Tg + T, optional) as or_ransac's. */
+int or_ransac_prior(const double* pts, int64_t M, const float* prob, int Tg, int T, double thresh, uint64_t seed,
+                    uint32_t pair_id, double* H, uint8_t* inl, int32_t* n_in, int32_t* best_t, int32_t* iters,
+                    int32_t* counts);
 #ifdef __cplusplus
 }
 #endif

@@ -149,11 +149,14 @@ __device__ bool denorm(const Norm2D& na, const Norm2D& nb, const double* hn, dou
     return true;
 }
 
+// prefix == nullptr: uniform draw; otherwise word w picks the match whose
+// interval of the inclusive prefix sums of integer weights contains
+// floor(w * total / 2^32) (probability proportional to the weight).
 __global__ void k_ransac_hyp(const float4* pts, long long M_cap, const int32_t* dM, int T, uint32_t k0, uint32_t k1,
-                             double* Hs, int8_t* hok)
+                             const unsigned long long* prefix, const int32_t* skip, double* Hs, int8_t* hok)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= T) return;
+    if (t >= T || (skip && *skip)) return;
     hok[t] = 0;
     const long long M = m_count(dM, M_cap);
     if (M < 4) return;
@@ -163,7 +166,19 @@ __global__ void k_ransac_hyp(const float4* pts, long long M_cap, const int32_t* 
     for (int j = 0; j < 64 && n < 4; ++j) {
         if ((j & 3) == 0) blk = philox(make_uint4((uint32_t)t, (uint32_t)(j >> 2), 0u, 0u), k0, k1);
         const uint32_t w = (j & 3) == 0 ? blk.x : (j & 3) == 1 ? blk.y : (j & 3) == 2 ? blk.z : blk.w;
-        const int i = (int)(((unsigned long long)w * (unsigned long long)M) >> 32);
+        int i;
+        if (!prefix) {
+            i = (int)(((unsigned long long)w * (unsigned long long)M) >> 32);
+        } else {
+            const unsigned long long total = prefix[M - 1];
+            const unsigned long long target = __umul64hi((unsigned long long)w << 32, total);
+            long long lo = 0, hi = M - 1;
+            while (lo < hi) {
+                const long long mid = (lo + hi) >> 1;
+                if (prefix[mid] > target) hi = mid; else lo = mid + 1;
+            }
+            i = (int)lo;
+        }
         bool dup = false;
         for (int q = 0; q < n; ++q) dup |= idx[q] == i;
         if (!dup) idx[n++] = i;
@@ -234,11 +249,11 @@ __device__ __forceinline__ int block_sum(int v, int* red)
 
 __global__ void __launch_bounds__(kScoreThreads)
 k_ransac_score(const float4* pts, long long M_cap, const int32_t* dM, const double* Hs, const int8_t* hok,
-               float t2, float eps, int32_t* lo, int32_t* hi)
+               float t2, float eps, const int32_t* skip, int32_t* lo, int32_t* hi)
 {
     __shared__ int red[32];
     const int t = blockIdx.x;
-    if (!hok[t]) {
+    if ((skip && *skip) || !hok[t]) {
         if (threadIdx.x == 0) { lo[t] = -1; hi[t] = -1; }
         return;
     }
@@ -281,8 +296,9 @@ constexpr int kSelThreads = 1024;
 
 __global__ void __launch_bounds__(kSelThreads)
 k_ransac_select(const float4* pts, long long M_cap, const int32_t* dM, int T, const double* Hs,
-                const int32_t* lo, const int32_t* hi, double t2, int32_t* best_out)
+                const int32_t* lo, const int32_t* hi, double t2, const int32_t* skip, int t_off, int32_t* best_out)
 {
+    if (skip && *skip) return;
     __shared__ int red[32];
     __shared__ unsigned long long bestkey;
     __shared__ int cand[kSelThreads];
@@ -298,7 +314,7 @@ k_ransac_select(const float4* pts, long long M_cap, const int32_t* dM, int T, co
     cmax = -1;
     for (int w = 0; w < kSelThreads / 32; ++w) cmax = max(cmax, red[w]);
     if (cmax < 0) {
-        if (threadIdx.x == 0) *best_out = -1;
+        if (threadIdx.x == 0) { best_out[0] = -1; best_out[1] = -1; }
         return;
     }
     // key = (count + 1) << 32 | (0xFFFFFFFF - t): the max key is the most
@@ -333,7 +349,52 @@ k_ransac_select(const float4* pts, long long M_cap, const int32_t* dM, int T, co
         __syncthreads();
     }
     __syncthreads();
-    if (threadIdx.x == 0) *best_out = (int)(0xFFFFFFFFull - (bestkey & 0xFFFFFFFFull));
+    if (threadIdx.x == 0) {
+        best_out[0] = t_off + (int)(0xFFFFFFFFull - (bestkey & 0xFFFFFFFFull));
+        best_out[1] = (int)(bestkey >> 32) - 1;
+    }
+}
+
+// Stop test of the guided phase.  w = (prior weight of the guided winner's
+// FP64 inliers) / (total weight) is the chance that one guided draw is an
+// inlier; the phase stops when (1 - w^4)^Tg <= 0.01, the standard bound
+// T >= log(0.01) / log(1 - w^4) without logarithms.  Every operation is a
+// single IEEE-rounded one (no contraction), powers by binary exponentiation.
+// flags[2] = stop, flags[3] = iterations used.
+__global__ void __launch_bounds__(kSelThreads)
+k_guided_decide(const float4* pts, long long M_cap, const int32_t* dM, const double* Hs,
+                const unsigned long long* prefix, int Tg, int T, double t2, int32_t* flags)
+{
+    __shared__ unsigned long long part[kSelThreads / 32];
+    const int tb = flags[0];
+    const long long M = m_count(dM, M_cap);
+    if (tb < 0 || M < 4) {
+        if (threadIdx.x == 0) { flags[2] = 0; flags[3] = Tg + T; }
+        return;
+    }
+    double H[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) H[i] = Hs[9ll * tb + i];
+    unsigned long long sw = 0;
+    for (long long i = threadIdx.x; i < M; i += kSelThreads)
+        if (inlier64(H, pts[i], t2)) sw += prefix[i] - (i ? prefix[i - 1] : 0ull);
+#pragma unroll
+    for (int o = 16; o; o >>= 1) sw += __shfl_xor_sync(0xFFFFFFFFu, sw, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = sw;
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    unsigned long long s_in = 0;
+    for (int w = 0; w < kSelThreads / 32; ++w) s_in += part[w];
+    const double w = __ddiv_rn((double)s_in, (double)prefix[M - 1]);
+    const double w2 = __dmul_rn(w, w);
+    double b = __dsub_rn(1.0, __dmul_rn(w2, w2)), r = 1.0;
+    for (int e = Tg; e; e >>= 1) {
+        if (e & 1) r = __dmul_rn(r, b);
+        b = __dmul_rn(b, b);
+    }
+    const int stop = r <= 0.01;
+    flags[2] = stop;
+    flags[3] = stop ? Tg : Tg + T;
 }
 
 // ---------------------------------------------------------------- refit
@@ -631,10 +692,63 @@ cudaError_t launch_compact(const uint32_t* kpA, int WA, const uint32_t* kpB, int
     return cudaGetLastError();
 }
 
-size_t ransac_workspace(int64_t M_cap, int T)
+namespace {
+
+struct RansacWS {
+    double* Hs;       // [Ttot][9]
+    int32_t* lo;      // [Ttot] certain FP32 counts (-1: no hypothesis)
+    int32_t* hi;      // [Ttot] possible FP32 counts
+    int32_t* flags;   // [4]: winner t, winner count, guided stop, iterations used
+    int8_t* hok;      // [Ttot]
+    RefitWS rw;
+};
+
+RansacWS carve(void* ws, int Ttot)
+{
+    RansacWS r;
+    uint8_t* w = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(ws) + 255) & ~uintptr_t(255));
+    r.Hs = reinterpret_cast<double*>(w);
+    r.lo = reinterpret_cast<int32_t*>(r.Hs + 9ll * Ttot);
+    r.hi = r.lo + Ttot;
+    r.flags = r.hi + Ttot;
+    r.hok = reinterpret_cast<int8_t*>(r.flags + 4);
+    r.rw.part = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(r.hok + Ttot) + 255) & ~uintptr_t(255));
+    r.rw.Hf = r.rw.part + kRefitCTAs * kPartStride + 1;
+    return r;
+}
+
+void refit_launch(const float4* p4, int64_t M_cap, const int32_t* d_M, double t2, const RansacWS& w, double* H,
+                  uint8_t* inlier, int32_t* n_in, int32_t* best_t, cudaStream_t s)
+{
+    k_refit_p1<<<kRefitCTAs, kRefitThreads, 0, s>>>(p4, M_cap, d_M, w.Hs, w.flags, t2, inlier, w.rw);
+    k_refit_p2<<<kRefitCTAs, kRefitThreads, 0, s>>>(p4, M_cap, d_M, w.flags, inlier, w.rw);
+    k_refit_p3<<<kRefitCTAs, kRefitThreads, 0, s>>>(p4, M_cap, d_M, w.flags, inlier, w.rw);
+    k_refit_solve<<<1, 32, 0, s>>>(w.Hs, w.flags, w.rw, H, n_in, best_t);
+    const unsigned gfin = (unsigned)std::max<long long>(1, std::min<long long>(kRefitCTAs, (M_cap + 1023) / 1024));
+    k_refit_final<<<gfin, kRefitThreads, 0, s>>>(p4, M_cap, d_M, w.rw, t2, inlier, n_in);
+}
+
+// One batch of T hypotheses at rows [t_off, t_off + T) of the workspace,
+// Philox counters 0..T-1; skipped entirely while *skip is non-zero.
+void hyp_batch(const float4* p4, int64_t M_cap, const int32_t* d_M, const unsigned long long* prefix, int T,
+               int t_off, uint32_t k0, uint32_t k1, float t2f, float eps, double t2, const int32_t* skip,
+               const RansacWS& w, cudaStream_t s)
+{
+    k_ransac_hyp<<<(T + 15) / 16, 16, 0, s>>>(p4, M_cap, d_M, T, k0, k1, prefix, skip, w.Hs + 9ll * t_off,
+                                              w.hok + t_off);
+    k_ransac_score<<<T, kScoreThreads, 0, s>>>(p4, M_cap, d_M, w.Hs + 9ll * t_off, w.hok + t_off, t2f, eps, skip,
+                                               w.lo + t_off, w.hi + t_off);
+    k_ransac_select<<<1, kSelThreads, 0, s>>>(p4, M_cap, d_M, T, w.Hs + 9ll * t_off, w.lo + t_off, w.hi + t_off, t2,
+                                              skip, t_off, w.flags);
+}
+
+}  // namespace
+
+// Ttot = the number of hypotheses of one call (T, or Tg + T with a prior)
+size_t ransac_workspace(int64_t M_cap, int Ttot)
 {
     (void)M_cap;
-    return 256 + (size_t)T * (9 * sizeof(double) + 2 * sizeof(int32_t) + 1) + 256 +
+    return 256 + (size_t)Ttot * (9 * sizeof(double) + 2 * sizeof(int32_t) + 1) + 256 +
            sizeof(double) * (kRefitCTAs * kPartStride + 16) + 256;
 }
 
@@ -644,30 +758,51 @@ cudaError_t launch_ransac(const float* pts, int64_t M_cap, const int32_t* d_M, i
 {
     (void)status;
     if (ws_bytes < ransac_workspace(M_cap, T)) return cudaErrorInvalidValue;
-    uint8_t* w = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(ws) + 255) & ~uintptr_t(255));
-    double* Hs = reinterpret_cast<double*>(w);
-    int32_t* lo = reinterpret_cast<int32_t*>(Hs + 9ll * T);
-    int32_t* hi = lo + T;
-    int32_t* best = hi + T;
-    int8_t* hok = reinterpret_cast<int8_t*>(best + 1);
-    RefitWS rw;
-    rw.part = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(hok + T) + 255) & ~uintptr_t(255));
-    rw.Hf = rw.part + kRefitCTAs * kPartStride + 1;
+    const RansacWS w = carve(ws, T);
     const float4* p4 = reinterpret_cast<const float4*>(pts);
     const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32) ^ pair_id;
     const double t2 = (double)thresh * (double)thresh;
     const float t2f = (float)t2;
     const float eps = fmaxf(0.05f, 0.01f * t2f);
-    k_ransac_hyp<<<(T + 15) / 16, 16, 0, s>>>(p4, M_cap, d_M, T, k0, k1, Hs, hok);
-    k_ransac_score<<<T, kScoreThreads, 0, s>>>(p4, M_cap, d_M, Hs, hok, t2f, eps, lo, hi);
-    k_ransac_select<<<1, kSelThreads, 0, s>>>(p4, M_cap, d_M, T, Hs, lo, hi, t2, best);
-    k_refit_p1<<<kRefitCTAs, kRefitThreads, 0, s>>>(p4, M_cap, d_M, Hs, best, t2, inlier, rw);
-    k_refit_p2<<<kRefitCTAs, kRefitThreads, 0, s>>>(p4, M_cap, d_M, best, inlier, rw);
-    k_refit_p3<<<kRefitCTAs, kRefitThreads, 0, s>>>(p4, M_cap, d_M, best, inlier, rw);
-    k_refit_solve<<<1, 32, 0, s>>>(Hs, best, rw, H, n_in, best_t);
-    const unsigned gfin = (unsigned)std::max<long long>(1, std::min<long long>(kRefitCTAs, (M_cap + 1023) / 1024));
-    k_refit_final<<<gfin, kRefitThreads, 0, s>>>(p4, M_cap, d_M, rw, t2, inlier, n_in);
+    hyp_batch(p4, M_cap, d_M, nullptr, T, 0, k0, k1, t2f, eps, t2, nullptr, w, s);
+    refit_launch(p4, M_cap, d_M, t2, w, H, inlier, n_in, best_t, s);
     return cudaGetLastError();
+}
+
+// Guided phase (Tg hypotheses drawn by the prior's prefix sums), the stop test,
+// then the uniform fallback (T hypotheses, the plain RANSAC stream), skipped on
+// the device when the guided phase stopped.  Hypothesis rows: guided [0, Tg),
+// uniform [Tg, Tg + T).
+cudaError_t launch_ransac_prior(const float* pts, int64_t M_cap, const int32_t* d_M, const unsigned long long* prefix,
+                                int Tg, int T, float thresh, uint64_t seed, uint32_t pair_id, double* H,
+                                uint8_t* inlier, int32_t* n_in, int32_t* best_t, int32_t* iters, void* ws,
+                                size_t ws_bytes, cudaStream_t s)
+{
+    if (ws_bytes < ransac_workspace(M_cap, Tg + T)) return cudaErrorInvalidValue;
+    const RansacWS w = carve(ws, Tg + T);
+    const float4* p4 = reinterpret_cast<const float4*>(pts);
+    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32) ^ pair_id;
+    const double t2 = (double)thresh * (double)thresh;
+    const float t2f = (float)t2;
+    const float eps = fmaxf(0.05f, 0.01f * t2f);
+    hyp_batch(p4, M_cap, d_M, prefix, Tg, 0, k0, k1, t2f, eps, t2, nullptr, w, s);
+    k_guided_decide<<<1, kSelThreads, 0, s>>>(p4, M_cap, d_M, w.Hs, prefix, Tg, T, t2, w.flags);
+    hyp_batch(p4, M_cap, d_M, nullptr, T, Tg, k0, k1, t2f, eps, t2, w.flags + 2, w, s);
+    refit_launch(p4, M_cap, d_M, t2, w, H, inlier, n_in, best_t, s);
+    if (iters) {
+        cudaError_t e = cudaMemcpyAsync(iters, w.flags + 3, sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaGetLastError();
+}
+
+// Certain inlier counts of the last RANSAC's hypotheses (-1: none or skipped).
+cudaError_t ransac_counts(void* ws, int Ttot, int32_t* host_counts, cudaStream_t s)
+{
+    const RansacWS w = carve(ws, Ttot);
+    cudaError_t e = cudaMemcpyAsync(host_counts, w.lo, sizeof(int32_t) * (size_t)Ttot, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(s);
 }
 
 cudaError_t launch_diag_philox(const uint32_t* ctr, int64_t n, uint32_t k0, uint32_t k1, uint32_t* out, cudaStream_t s)

@@ -21,7 +21,7 @@ enum BufId {
     B_MATCH_WS, B_RANSAC_WS,
     B_IMG_A, B_IMG_B, B_GRAY_A, B_GRAY_B, B_KP_A, B_KP_B, B_ORI_A, B_ORI_B,
     B_DESC_A, B_DESC_B, B_D16_A, B_D16_B, B_VAL_A, B_VAL_B,
-    B_MATCH, B_D1, B_D2, B_PTS, B_M, B_INL, B_H, B_NIN, B_BEST, B_LUTS, B_BATCH,
+    B_MATCH, B_D1, B_D2, B_PTS, B_M, B_INL, B_H, B_NIN, B_BEST, B_LUTS, B_BATCH, B_PREFIX,
     B_COUNT
 };
 
@@ -37,6 +37,7 @@ struct lp_ctx {
     int num_sms = 0;
     int32_t* d_status = nullptr;
     cudaStream_t last = nullptr;
+    int last_ransac_hyps = 0;           // hypotheses of the last lp_ransac / lp_ransac_prior
     DBuf buf[B_COUNT];
     char err[512];
 };
@@ -329,6 +330,7 @@ int lp_ransac(lp_ctx* c, const float* pts, int64_t M_cap, const int32_t* d_M, ui
     int r = ensure(c, B_RANSAC_WS, lp::ransac_workspace(M_cap, T));
     if (r) return r;
     c->last = S(stream);
+    c->last_ransac_hyps = T;
     LP_CUDA(c, lp::launch_ransac(pts, M_cap, d_M, T, c->cfg.thresh_px, c->cfg.seed, pair_id, H, inlier, n_inliers,
                                  best_t, c->buf[B_RANSAC_WS].p, c->buf[B_RANSAC_WS].n, c->d_status, S(stream)));
     return LP_OK;
@@ -558,6 +560,57 @@ int lp_stitch_pairs(lp_ctx* c, const lp_image* imgs, int N, const int32_t* pairs
     return LP_OK;
 }
 
+int lp_ransac_prior(lp_ctx* c, const float* pts, int64_t M_cap, const int32_t* d_M, const float* prior,
+                    int32_t guided_iters, uint32_t pair_id, double* H, uint8_t* inlier, int32_t* n_inliers,
+                    int32_t* best_t, int32_t* iters_used, void* stream)
+{
+    if (!c) return LP_ERR_ARG;
+    if (M_cap < 0 || M_cap > (1ll << 31) - 1) return fail(c, LP_ERR_ARG, "bad M_cap");
+    if (guided_iters < 1 || guided_iters > 65536) return fail(c, LP_ERR_ARG, "guided_iters must be 1..65536");
+    if (!H || !n_inliers || (M_cap > 0 && (!pts || !inlier || !prior))) return fail(c, LP_ERR_ARG, "null argument");
+    if (pts && !aligned(pts, 16)) return fail(c, LP_ERR_ALIGN, "pts must be 16-byte aligned");
+    const int T = c->cfg.ransac_iters, Ttot = guided_iters + T;
+    int r = ensure(c, B_RANSAC_WS, lp::ransac_workspace(M_cap, Ttot));
+    if (!r) r = ensure(c, B_PREFIX, sizeof(unsigned long long) * (size_t)(M_cap + 1));
+    if (r) return r;
+    c->last = S(stream);
+    c->last_ransac_hyps = Ttot;
+    auto* pre = static_cast<unsigned long long*>(c->buf[B_PREFIX].p);
+    LP_CUDA(c, lp::launch_guided_prefix(prior, M_cap, d_M, pre, S(stream)));
+    LP_CUDA(c, lp::launch_ransac_prior(pts, M_cap, d_M, pre, guided_iters, T, c->cfg.thresh_px, c->cfg.seed, pair_id,
+                                       H, inlier, n_inliers, best_t, iters_used, c->buf[B_RANSAC_WS].p,
+                                       c->buf[B_RANSAC_WS].n, S(stream)));
+    return LP_OK;
+}
+
+int lp_diag_last_ransac_counts(lp_ctx* c, int32_t* host_counts, int n)
+{
+    if (!c || !host_counts || n != c->last_ransac_hyps || n <= 0 || !c->buf[B_RANSAC_WS].p) return LP_ERR_ARG;
+    LP_CUDA(c, lp::ransac_counts(c->buf[B_RANSAC_WS].p, n, host_counts, c->last));
+    return LP_OK;
+}
+
+int lp_mlp_features(lp_ctx* c, const uint32_t* kpA, const uint8_t* oriA, int HA, int WA, const uint32_t* kpB,
+                    const uint8_t* oriB, int HB, int WB, const int32_t* match, const float* d1, const float* d2,
+                    const int32_t* rows, const int32_t* d_M, int64_t M_cap, float* feat, void* stream)
+{
+    if (!c) return LP_ERR_ARG;
+    if (M_cap < 0 || HA <= 0 || WA <= 0 || HB <= 0 || WB <= 0) return fail(c, LP_ERR_ARG, "bad sizes");
+    if (M_cap > 0 && (!kpA || !oriA || !kpB || !oriB || !match || !d1 || !d2 || !rows || !feat))
+        return fail(c, LP_ERR_ARG, "null argument");
+    lp::ScaleTable st;
+    lp::make_scale_table(c->cfg.Ls, c->cfg.nL, c->cfg.beta0, HA, WA, &st);
+    lp::MlpScales sc;
+    sc.nL = st.nL;
+    for (int l = 0; l <= st.nL; ++l) sc.off[l] = st.off[l];
+    for (int l = 0; l < st.nL; ++l) sc.log2L[l] = (float)log2((double)st.L[l]);
+    sc.log2Lmax = (float)log2((double)st.L[st.nL - 1]);
+    c->last = S(stream);
+    LP_CUDA(c, lp::launch_mlp_features(kpA, oriA, HA, WA, kpB, oriB, HB, WB, match, d1, d2, rows, d_M, M_cap, sc,
+                                       feat, S(stream)));
+    return LP_OK;
+}
+
 int lp_sync_status(lp_ctx* c)
 {
     if (!c) return LP_ERR_ARG;
@@ -604,6 +657,171 @@ int lp_diag_gray(const uint8_t* rgb, int64_t n, uint8_t* gray, void* stream)
     if (n < 0 || (n > 0 && (!rgb || !gray))) return LP_ERR_ARG;
     if (n == 0) return LP_OK;
     return lp::launch_diag_gray(rgb, n, gray, S(stream)) == cudaSuccess ? LP_OK : LP_ERR_CUDA;
+}
+
+struct lp_mlp {
+    int device = 0;
+    float* master = nullptr;   // [LP_MLP_PARAMS] x 4: master, m, v, shadow (one block)
+    float* m = nullptr;
+    float* v = nullptr;
+    float* shadow = nullptr;
+    float* part = nullptr;     // per-CTA gradient partials
+    float* lossp = nullptr;
+    size_t part_ctas = 0;
+    int step = 0;
+};
+
+namespace {
+
+uint64_t splitmix64(uint64_t& x)
+{
+    uint64_t z = (x += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+int mlp_upload(lp_mlp* m, const float* host)
+{
+    std::vector<float> zero(LP_MLP_PARAMS, 0.f);
+    if (cudaMemcpy(m->master, host, sizeof(float) * LP_MLP_PARAMS, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(m->m, zero.data(), sizeof(float) * LP_MLP_PARAMS, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(m->v, zero.data(), sizeof(float) * LP_MLP_PARAMS, cudaMemcpyHostToDevice) != cudaSuccess ||
+        lp::launch_mlp_shadow(m->master, m->shadow, nullptr) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess)
+        return LP_ERR_CUDA;
+    m->step = 0;
+    return LP_OK;
+}
+
+}  // namespace
+
+int lp_mlp_create(lp_mlp** out, uint64_t seed)
+{
+    if (!out) return LP_ERR_ARG;
+    *out = nullptr;
+    lp_mlp* m = new lp_mlp();
+    if (cudaGetDevice(&m->device) != cudaSuccess || cudaMalloc(&m->master, sizeof(float) * 4 * LP_MLP_PARAMS) != cudaSuccess) {
+        cudaGetLastError();
+        delete m;
+        return LP_ERR_CUDA;
+    }
+    m->m = m->master + LP_MLP_PARAMS;
+    m->v = m->m + LP_MLP_PARAMS;
+    m->shadow = m->v + LP_MLP_PARAMS;
+    // He-uniform: U(-sqrt(6 / fan_in), +sqrt(6 / fan_in)), zero biases
+    std::vector<float> h(LP_MLP_PARAMS, 0.f);
+    uint64_t st = seed;
+    auto uni = [&](double a) { return (float)(a * (2.0 * ((splitmix64(st) >> 11) * 0x1.0p-53) - 1.0)); };
+    for (int i = 0; i < 512; ++i) h[i] = uni(sqrt(6.0 / 8.0));
+    for (int i = 576; i < 4672; ++i) h[i] = uni(sqrt(6.0 / 64.0));
+    for (int i = 4736; i < 4800; ++i) h[i] = uni(sqrt(6.0 / 64.0));
+    int r = mlp_upload(m, h.data());
+    if (r) { cudaFree(m->master); delete m; return r; }
+    *out = m;
+    return LP_OK;
+}
+
+int lp_mlp_destroy(lp_mlp* m)
+{
+    if (!m) return LP_ERR_ARG;
+    cudaDeviceSynchronize();
+    cudaFree(m->master);
+    if (m->part) cudaFree(m->part);
+    delete m;
+    return LP_OK;
+}
+
+int lp_mlp_set_params(lp_mlp* m, const float* host)
+{
+    if (!m || !host) return LP_ERR_ARG;
+    return mlp_upload(m, host);
+}
+
+int lp_mlp_get_params(lp_mlp* m, float* host)
+{
+    if (!m || !host) return LP_ERR_ARG;
+    if (cudaDeviceSynchronize() != cudaSuccess ||
+        cudaMemcpy(host, m->master, sizeof(float) * LP_MLP_PARAMS, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return LP_ERR_CUDA;
+    return LP_OK;
+}
+
+int lp_mlp_get_state(lp_mlp* m, float* host, int32_t* step)
+{
+    if (!m || !host) return LP_ERR_ARG;
+    if (cudaDeviceSynchronize() != cudaSuccess ||
+        cudaMemcpy(host, m->master, sizeof(float) * 3 * LP_MLP_PARAMS, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return LP_ERR_CUDA;
+    if (step) *step = m->step;
+    return LP_OK;
+}
+
+int lp_mlp_save(lp_mlp* m, const char* path)
+{
+    if (!m || !path) return LP_ERR_ARG;
+    std::vector<float> h(3 * LP_MLP_PARAMS);
+    if (cudaDeviceSynchronize() != cudaSuccess ||
+        cudaMemcpy(h.data(), m->master, sizeof(float) * 3 * LP_MLP_PARAMS, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return LP_ERR_CUDA;
+    FILE* f = fopen(path, "wb");
+    if (!f) return LP_ERR_ARG;
+    const char magic[8] = {'L', 'P', 'M', 'L', 'P', '0', '0', '1'};
+    const int32_t hdr[2] = {LP_MLP_PARAMS, m->step};
+    bool ok = fwrite(magic, 1, 8, f) == 8 && fwrite(hdr, sizeof hdr, 1, f) == 1 &&
+              fwrite(h.data(), sizeof(float), h.size(), f) == h.size();
+    ok = (fclose(f) == 0) && ok;
+    return ok ? LP_OK : LP_ERR_ARG;
+}
+
+int lp_mlp_load(lp_mlp* m, const char* path)
+{
+    if (!m || !path) return LP_ERR_ARG;
+    FILE* f = fopen(path, "rb");
+    if (!f) return LP_ERR_ARG;
+    char magic[8];
+    int32_t hdr[2];
+    std::vector<float> h(3 * LP_MLP_PARAMS);
+    bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, "LPMLP001", 8) == 0 && fread(hdr, sizeof hdr, 1, f) == 1 &&
+              hdr[0] == LP_MLP_PARAMS && fread(h.data(), sizeof(float), h.size(), f) == h.size();
+    fclose(f);
+    if (!ok) return LP_ERR_ARG;
+    if (cudaMemcpy(m->master, h.data(), sizeof(float) * 3 * LP_MLP_PARAMS, cudaMemcpyHostToDevice) != cudaSuccess ||
+        lp::launch_mlp_shadow(m->master, m->shadow, nullptr) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess)
+        return LP_ERR_CUDA;
+    m->step = hdr[1];
+    return LP_OK;
+}
+
+int lp_mlp_forward(lp_mlp* m, const float* feat, int64_t M_cap, const int32_t* d_M, float* prob, float* logit,
+                   void* stream)
+{
+    if (!m || M_cap < 0 || (M_cap > 0 && !feat)) return LP_ERR_ARG;
+    return lp::launch_mlp_forward(m->shadow, feat, M_cap, d_M, prob, logit, S(stream)) == cudaSuccess ? LP_OK
+                                                                                                      : LP_ERR_CUDA;
+}
+
+int lp_mlp_train_step(lp_mlp* m, const float* feat, const uint8_t* label, int64_t B, float lr, float* loss,
+                      void* stream)
+{
+    if (!m || B <= 0 || !feat || !label || !(lr > 0.f)) return LP_ERR_ARG;
+    const size_t n = (size_t)lp::mlp_grad_ctas(B);
+    if (n > m->part_ctas) {
+        cudaStreamSynchronize(S(stream));
+        if (m->part) cudaFree(m->part);
+        m->part = nullptr;
+        if (cudaMalloc(&m->part, sizeof(float) * n * (LP_MLP_PARAMS + 1)) != cudaSuccess) {
+            cudaGetLastError();
+            m->part_ctas = 0;
+            return LP_ERR_NOMEM;
+        }
+        m->lossp = m->part + n * LP_MLP_PARAMS;
+        m->part_ctas = n;
+    }
+    m->step += 1;
+    return lp::launch_mlp_train_step(m->master, m->m, m->v, m->shadow, feat, label, B, m->part, m->lossp, lr, m->step,
+                                     loss, S(stream)) == cudaSuccess
+               ? LP_OK
+               : LP_ERR_CUDA;
 }
 
 }  // extern "C"

@@ -61,11 +61,41 @@ int64_t match_bf16_rescans(const void* ws, int64_t NA, int64_t NB, int num_sms, 
 // k_ransac.cu
 cudaError_t launch_compact(const uint32_t* kpA, int WA, const uint32_t* kpB, int WB, const int32_t* match,
                            int64_t NA, float* pts, int32_t* rows, int32_t* d_M, cudaStream_t s);
-size_t ransac_workspace(int64_t M_cap, int T);
+size_t ransac_workspace(int64_t M_cap, int Ttot);
 cudaError_t launch_ransac(const float* pts, int64_t M_cap, const int32_t* d_M, int T, float thresh,
                           uint64_t seed, uint32_t pair_id, double* H, uint8_t* inlier, int32_t* n_in,
                           int32_t* best_t, void* ws, size_t ws_bytes, int32_t* status, cudaStream_t s);
 cudaError_t launch_diag_philox(const uint32_t* ctr, int64_t n, uint32_t k0, uint32_t k1, uint32_t* out,
                                cudaStream_t s);
+
+// k_ransac.cu (guided phase, stop test, uniform fallback); Ttot = Tg + T
+cudaError_t launch_ransac_prior(const float* pts, int64_t M_cap, const int32_t* d_M, const unsigned long long* prefix,
+                                int Tg, int T, float thresh, uint64_t seed, uint32_t pair_id, double* H,
+                                uint8_t* inlier, int32_t* n_in, int32_t* best_t, int32_t* iters, void* ws,
+                                size_t ws_bytes, cudaStream_t s);
+cudaError_t ransac_counts(void* ws, int Ttot, int32_t* host_counts, cudaStream_t s);
+
+// k_mlp.cu (learned proposal)
+constexpr int kMlpParams = 4801;
+struct MlpScales {
+    int nL;
+    long long off[LP_MAX_SCALES + 1];
+    float log2L[LP_MAX_SCALES];
+    float log2Lmax;
+};
+size_t mlp_grad_smem();
+int mlp_grad_ctas(long long B);
+cudaError_t launch_mlp_features(const uint32_t* kpA, const uint8_t* oriA, int HA, int WA, const uint32_t* kpB,
+                                const uint8_t* oriB, int HB, int WB, const int32_t* match, const float* d1,
+                                const float* d2, const int32_t* rows, const int32_t* dM, long long M_cap,
+                                const MlpScales& sc, float* feat, cudaStream_t s);
+cudaError_t launch_mlp_forward(const float* shadow, const float* feat, long long M_cap, const int32_t* dM, float* prob,
+                               float* logit, cudaStream_t s);
+cudaError_t launch_mlp_train_step(float* master, float* m, float* v, float* shadow, const float* feat,
+                                  const uint8_t* label, long long B, float* part, float* lossp, float lr, int t,
+                                  float* loss_out, cudaStream_t s);
+cudaError_t launch_mlp_shadow(const float* master, float* shadow, cudaStream_t s);
+cudaError_t launch_guided_prefix(const float* prob, long long M_cap, const int32_t* dM, unsigned long long* prefix,
+                                 cudaStream_t s);
 
 }  // namespace lp

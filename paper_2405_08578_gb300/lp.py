@@ -10,6 +10,7 @@ import ctypes as C
 import math
 import os
 
+import numpy as np
 import torch
 
 from . import build as _build
@@ -42,7 +43,11 @@ class lp_config(C.Structure):
 _lib = None
 SYMBOLS = ["lp_config_default", "lp_create", "lp_destroy", "lp_num_keypoints", "lp_detect", "lp_describe",
            "lp_match", "lp_compact", "lp_ransac", "lp_ransac_static", "lp_stitch_pair", "lp_stitch_pair_host", "lp_stitch_pairs", "lp_sync_status",
-           "lp_last_error", "lp_diag_last_rescans", "lp_diag_orient_bins", "lp_diag_orient_weights", "lp_diag_philox", "lp_diag_gray"]
+           "lp_last_error", "lp_diag_last_rescans", "lp_diag_orient_bins", "lp_diag_orient_weights", "lp_diag_philox", "lp_diag_gray",
+           "lp_mlp_create", "lp_mlp_destroy", "lp_mlp_set_params", "lp_mlp_get_params", "lp_mlp_get_state", "lp_mlp_save",
+           "lp_mlp_load", "lp_mlp_features", "lp_mlp_forward", "lp_mlp_train_step", "lp_ransac_prior",
+           "lp_diag_last_ransac_counts"]
+MLP_PARAMS = 4801
 
 
 def lib_path() -> str:
@@ -81,6 +86,18 @@ def load(build_if_missing: bool = True):
         "lp_diag_orient_weights": (i32, [P, P]),
         "lp_diag_philox": (i32, [P, i64, u32, u32, P, P]),
         "lp_diag_gray": (i32, [P, i64, P, P]),
+        "lp_mlp_create": (i32, [C.POINTER(P), C.c_uint64]),
+        "lp_mlp_destroy": (i32, [P]),
+        "lp_mlp_set_params": (i32, [P, P]),
+        "lp_mlp_get_params": (i32, [P, P]),
+        "lp_mlp_get_state": (i32, [P, P, P]),
+        "lp_mlp_save": (i32, [P, C.c_char_p]),
+        "lp_mlp_load": (i32, [P, C.c_char_p]),
+        "lp_mlp_features": (i32, [P, P, P, i32, i32, P, P, i32, i32, P, P, P, P, P, i64, P, P]),
+        "lp_mlp_forward": (i32, [P, P, i64, P, P, P, P]),
+        "lp_mlp_train_step": (i32, [P, P, P, i64, C.c_float, P, P]),
+        "lp_ransac_prior": (i32, [P, P, i64, P, P, i32, u32, P, P, P, P, P, P]),
+        "lp_diag_last_ransac_counts": (i32, [P, P, i32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -200,6 +217,25 @@ class Context:
         self._chk(self.lib.lp_stitch_pairs(self.h, C.cast(arr, C.c_void_p), len(images), pp, P, _ptr(HM), _ptr(n_in),
                                            _ptr(valid), _ptr(M_out), _stream(stream)), "lp_stitch_pairs")
 
+    def lp_mlp_features(self, kpA, oriA, HA, WA, kpB, oriB, HB, WB, match, d1, d2, rows, d_M, M_cap, feat,
+                        stream=None):
+        self._chk(self.lib.lp_mlp_features(self.h, _ptr(kpA), _ptr(oriA), HA, WA, _ptr(kpB), _ptr(oriB), HB, WB,
+                                           _ptr(match), _ptr(d1), _ptr(d2), _ptr(rows), _ptr(d_M), M_cap, _ptr(feat),
+                                           _stream(stream)), "lp_mlp_features")
+
+    def lp_ransac_prior(self, pts, M_cap, d_M, prior, guided_iters, pair_id, H, inlier, n_inliers, best_t=None,
+                        iters_used=None, stream=None):
+        self._chk(self.lib.lp_ransac_prior(self.h, _ptr(pts), M_cap, _ptr(d_M), _ptr(prior), int(guided_iters),
+                                           pair_id, _ptr(H), _ptr(inlier), _ptr(n_inliers), _ptr(best_t),
+                                           _ptr(iters_used), _stream(stream)), "lp_ransac_prior")
+
+    def lp_diag_last_ransac_counts(self, n: int) -> list[int]:
+        """n = T after lp_ransac, guided_iters + T after lp_ransac_prior."""
+        arr = (C.c_int32 * n)()
+        self._chk(self.lib.lp_diag_last_ransac_counts(self.h, C.cast(arr, C.c_void_p), n),
+                  "lp_diag_last_ransac_counts")
+        return list(arr)
+
     def lp_sync_status(self):
         return self.lib.lp_sync_status(self.h)
 
@@ -207,6 +243,64 @@ class Context:
         v = C.c_int64()
         self._chk(self.lib.lp_diag_last_rescans(self.h, C.byref(v)), "lp_diag_last_rescans")
         return v.value
+
+
+class Mlp:
+    """Owns an lp_mlp: the learned inlier-probability network (8-64-64-1)."""
+
+    def __init__(self, seed: int = 0):
+        self.lib = load()
+        h = C.c_void_p()
+        r = self.lib.lp_mlp_create(C.byref(h), int(seed))
+        if r != LP_OK:
+            raise LpError(r, "lp_mlp_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.lp_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _chk(self, r, what):
+        if r != LP_OK:
+            raise LpError(r, what)
+
+    def lp_mlp_set_params(self, params):
+        """params: host array-like of MLP_PARAMS floats (resets Adam)."""
+        a = (C.c_float * MLP_PARAMS)(*[float(v) for v in params])
+        self._chk(self.lib.lp_mlp_set_params(self.h, C.cast(a, C.c_void_p)), "lp_mlp_set_params")
+
+    def lp_mlp_get_params(self) -> list[float]:
+        a = (C.c_float * MLP_PARAMS)()
+        self._chk(self.lib.lp_mlp_get_params(self.h, C.cast(a, C.c_void_p)), "lp_mlp_get_params")
+        return list(a)
+
+    def lp_mlp_get_state(self):
+        """(master, m, v) as float32 numpy arrays, Adam step count."""
+        a = np.zeros(3 * MLP_PARAMS, np.float32)
+        st = C.c_int32()
+        self._chk(self.lib.lp_mlp_get_state(self.h, a.ctypes.data_as(C.c_void_p), C.byref(st)), "lp_mlp_get_state")
+        return a[:MLP_PARAMS], a[MLP_PARAMS:2 * MLP_PARAMS], a[2 * MLP_PARAMS:], st.value
+
+    def lp_mlp_save(self, path: str):
+        self._chk(self.lib.lp_mlp_save(self.h, os.fsencode(path)), "lp_mlp_save")
+
+    def lp_mlp_load(self, path: str):
+        self._chk(self.lib.lp_mlp_load(self.h, os.fsencode(path)), "lp_mlp_load")
+
+    def lp_mlp_forward(self, feat, M_cap, d_M, prob, logit=None, stream=None):
+        self._chk(self.lib.lp_mlp_forward(self.h, _ptr(feat), M_cap, _ptr(d_M), _ptr(prob), _ptr(logit),
+                                          _stream(stream)), "lp_mlp_forward")
+
+    def lp_mlp_train_step(self, feat, label, B, lr, loss=None, stream=None):
+        self._chk(self.lib.lp_mlp_train_step(self.h, _ptr(feat), _ptr(label), B, float(lr), _ptr(loss),
+                                             _stream(stream)), "lp_mlp_train_step")
 
 
 def lp_num_keypoints(H, W, Ls) -> int:

@@ -160,6 +160,19 @@ def pair_640x480(seed: int = 0) -> Pair:
     return make_pair(h, w, H, seed)
 
 
+def pair_640x480_random(seed: int) -> Pair:
+    """640x480 gray pair with a seeded similarity: rotation U[-10, 10] deg,
+    scale U[0.9, 1.1], x shift U[0.2, 0.5] w (either sign), y shift
+    U[-0.1, 0.1] h.  Training and held-out pairs of the learned proposal."""
+    h, w = 480, 640
+    rng = np.random.default_rng(20_000 + seed)
+    th = rng.uniform(-10.0, 10.0)
+    sc = rng.uniform(0.9, 1.1)
+    tx = rng.uniform(0.2, 0.5) * w * (1 if rng.uniform() < 0.5 else -1)
+    ty = rng.uniform(-0.1, 0.1) * h
+    return make_pair(h, w, similarity(th, sc, tx, ty, w / 2.0, h / 2.0), seed)
+
+
 def pair_2688x1600(seed: int = 0, rgb: bool = True) -> Pair:
     """2688x1600 RGB pair: rotation U[-10, 10] deg, scale U[0.9, 1.1], ~40% overlap."""
     h, w = 1600, 2688

@@ -1,0 +1,262 @@
+"""GPU parity of the learned RANSAC proposal (not part of the paper's method):
+features, forward, gradient and Adam against the oracle on the same
+BF16-rounded weights, the guided two-phase RANSAC against the oracle, and
+what a trained network gains over uniform sampling on held-out pairs."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2405_08578_gb300 import lp, proposal, synth
+
+import gpu_util as G
+
+pytestmark = pytest.mark.gpu
+
+NP = lp.MLP_PARAMS
+
+
+def bf16(a):
+    return torch.tensor(np.asarray(a, np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+
+
+def rand_params(seed, scale=0.3):
+    rng = np.random.default_rng(seed)
+    P = (rng.standard_normal(NP) * scale).astype(np.float32)
+    P[576:4672] *= 0.5                    # keep layer-2 activations O(1)
+    return P
+
+
+def rand_feat(seed, n):
+    rng = np.random.default_rng(seed)
+    f = np.c_[rng.uniform(0.2, 1.0, n), rng.uniform(0, 1.2, n), rng.uniform(0.5, 1, n), rng.uniform(-1, 1, n),
+              rng.uniform(0, 1, (n, 4))]
+    return f.astype(np.float32)
+
+
+@pytest.mark.parametrize("M", [1, 127, 128, 1000, 4099])
+def test_forward_matches_oracle(M):
+    P = rand_params(M)
+    net = lp.Mlp(seed=1)
+    net.lp_mlp_set_params(P)
+    x = rand_feat(M + 1, M)
+    prob = torch.zeros(M, device="cuda")
+    logit = torch.zeros(M, device="cuda")
+    net.lp_mlp_forward(G.dev(x), M, None, prob, logit)
+    z, p = oracle.mlp_forward(bf16(P), x.astype(np.float64))
+    zg, pg = G.host(logit), G.host(prob)
+    assert np.abs(zg - z).max() <= 1e-3 * max(1.0, np.abs(z).max())
+    assert np.abs(pg - p).max() <= 1e-3
+
+
+def test_forward_respects_device_count():
+    net = lp.Mlp(seed=2)
+    x = rand_feat(3, 300)
+    prob = torch.full((300,), -7.0, device="cuda")
+    dM = G.dev(np.array([211], np.int32))
+    net.lp_mlp_forward(G.dev(x), 300, dM, prob)
+    out = G.host(prob)
+    assert (out[211:] == -7.0).all() and (out[:211] > 0).all() and (out[:211] < 1).all()
+
+
+def away_from_kinks(P, x, n, margin=1e-4):
+    """The first n rows of x whose hidden pre-activations all keep |s| > margin:
+    at a ReLU kink FP32 and FP64 may take different branches of the derivative."""
+    Q = bf16(P)
+    W1, b1 = Q[:512].reshape(64, 8), Q[512:576]
+    W2, b2 = Q[576:4672].reshape(64, 64), Q[4672:4736]
+    s1 = x.astype(np.float64) @ W1.T + b1
+    s2 = np.maximum(s1, 0) @ W2.T + b2
+    keep = (np.abs(s1).min(1) > margin) & (np.abs(s2).min(1) > margin)
+    out = x[keep][:n]
+    assert len(out) == n
+    return out
+
+
+@pytest.mark.parametrize("B", [1, 64, 300, 4096])
+def test_gradient_and_adam_match_oracle(B):
+    P = rand_params(100 + B)
+    net = lp.Mlp(seed=3)
+    net.lp_mlp_set_params(P)
+    x = away_from_kinks(P, rand_feat(B, 2 * B + 50), B)
+    y = (np.random.default_rng(B).uniform(size=B) < 0.45).astype(np.uint8)
+    loss = torch.zeros(1, device="cuda")
+    lr = 1e-3
+    net.lp_mlp_train_step(G.dev(x), G.dev(y), B, lr, loss)
+    master, m, v, step = net.lp_mlp_get_state()
+    assert step == 1
+    L, g = oracle.mlp_loss_grad(bf16(P), x.astype(np.float64), y)
+    assert abs(float(G.host(loss)[0]) - L) <= 1e-3 * max(1.0, abs(L))
+    g_gpu = m.astype(np.float64) / 0.1          # first Adam step: m = (1 - beta1) g
+    gmax = np.abs(g).max()
+    assert np.all(np.abs(g_gpu - g) <= 1e-3 * np.abs(g) + 1e-5 * gmax)
+    # the Adam update of the FP32 master weights, given the kernel's gradient
+    p64, m64, v64 = P.astype(np.float64), np.zeros(NP), np.zeros(NP)
+    oracle.mlp_adam(p64, m64, v64, g_gpu, 1, lr=lr)
+    assert np.abs(master - p64).max() <= 2e-6
+    assert np.allclose(v, v64, rtol=1e-4, atol=1e-30)   # (1 - 0.999f) is 1 + 4.7e-5 of 1e-3
+
+
+def test_training_is_deterministic_and_checkpoints(tmp_path):
+    x = G.dev(rand_feat(7, 5000))
+    y = G.dev((np.random.default_rng(7).uniform(size=5000) < 0.5).astype(np.uint8))
+    runs = []
+    for _ in range(2):
+        net = lp.Mlp(seed=11)
+        for _ in range(5):
+            net.lp_mlp_train_step(x, y, 5000, 1e-3)
+        runs.append(net.lp_mlp_get_state())
+    for a, b in zip(runs[0][:3], runs[1][:3]):
+        assert np.array_equal(a, b)
+    path = str(tmp_path / "mlp.bin")
+    net.lp_mlp_save(path)
+    other = lp.Mlp(seed=99)
+    other.lp_mlp_load(path)
+    st = other.lp_mlp_get_state()
+    assert st[3] == 5 and all(np.array_equal(a, b) for a, b in zip(st[:3], runs[1][:3]))
+    # one more step from the loaded state equals one more step of the original
+    net.lp_mlp_train_step(x, y, 5000, 1e-3)
+    other.lp_mlp_train_step(x, y, 5000, 1e-3)
+    assert np.array_equal(net.lp_mlp_get_params(), other.lp_mlp_get_params())
+
+
+def test_init_is_he_uniform():
+    P = np.array(lp.Mlp(seed=5).lp_mlp_get_params())
+    W1, b1, W2, b2, w3, b3 = P[:512], P[512:576], P[576:4672], P[4672:4736], P[4736:4800], P[4800]
+    assert not b1.any() and not b2.any() and b3 == 0
+    for W, fan in [(W1, 8), (W2, 64), (w3, 64)]:
+        lim = math.sqrt(6.0 / fan)
+        assert np.abs(W).max() <= lim and np.abs(W).max() > 0.9 * lim
+        assert abs(W.std() - lim / math.sqrt(3)) < 0.1 * lim
+
+
+def _scale_of_rows(rows, Ls, H, W):
+    off = np.cumsum([0] + [2 * (H // L) * (W // L) for L in Ls])
+    return np.array([Ls[np.searchsorted(off, r, side="right") - 1] for r in rows], np.int32)
+
+
+@pytest.mark.parametrize("Ls,size", [((8, 16, 32), (480, 640)), ((16, 32), (200, 280))])
+def test_features_match_oracle_on_gpu_intermediates(Ls, size):
+    h, w = size
+    p = synth.pair_640x480(4) if size == (480, 640) else synth.small_pair(h, w, 6, theta_deg=-7.0)
+    ctx = lp.Context(Ls=Ls)
+    fa, fb = lp.features(ctx, p.A), lp.features(ctx, p.B)
+    m, d1, d2 = lp.match(ctx, fa, fb)
+    pm = proposal.pair_matches(ctx, fa, fb)
+    M = pm.M
+    assert M > 20
+    rows = G.host(pm.rows)[:M]
+    mm, dd1, dd2 = G.host(m), G.host(d1), G.host(d2)
+    j = mm[rows]
+    oa, ob = G.host(fa.ori), G.host(fb.ori)
+    pts = G.host(pm.pts)[:M].astype(np.float64)
+    want = oracle.mlp_features(dd1[rows], dd2[rows], _scale_of_rows(rows, Ls, h, w), max(Ls), oa[rows], ob[j], pts,
+                               w, h, w, h)
+    got = G.host(pm.feat)[:M]
+    assert np.abs(got - want).max() <= 1e-6 * max(1.0, np.abs(want).max())
+
+
+def _synthetic(rng, M, frac_out, noise=0.3):
+    Ht = np.eye(3)
+    Ht[:2, :2] += 0.06 * rng.standard_normal((2, 2))
+    Ht[:2, 2] = rng.uniform(-200, 200, 2)
+    Ht[2, :2] = rng.uniform(-5e-5, 5e-5, 2)
+    pa = np.round(rng.uniform(0, 1200, (M, 2)))
+    pb = G.proj(Ht, pa) + noise * rng.standard_normal((M, 2))
+    out = rng.uniform(size=M) < frac_out
+    pb[out] = rng.uniform(0, 1200, (out.sum(), 2))
+    return np.c_[pa, np.round(pb)].astype(np.float32), out
+
+
+def _gpu_prior(ctx, pts, prior, Tg, pair_id):
+    M = len(pts)
+    cap = max(M, 1)
+    p = G.dev(pts) if M else torch.zeros((1, 4), device="cuda")
+    pr = G.dev(prior.astype(np.float32)) if M else torch.zeros(1, device="cuda")
+    dM = G.dev(np.array([M], np.int32))
+    H = torch.zeros(9, dtype=torch.float64, device="cuda")
+    inl = torch.zeros(cap, dtype=torch.uint8, device="cuda")
+    n = torch.zeros(1, dtype=torch.int32, device="cuda")
+    bt = torch.zeros(1, dtype=torch.int32, device="cuda")
+    it = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ctx.lp_ransac_prior(p, M, dM, pr, Tg, pair_id, H, inl, n, bt, it)
+    counts = ctx.lp_diag_last_ransac_counts(Tg + ctx.cfg.ransac_iters)
+    return dict(H=G.host(H).reshape(3, 3), inliers=G.host(inl)[:M], n_in=int(G.host(n)[0]), best_t=int(G.host(bt)[0]),
+                iters=int(G.host(it)[0]), counts=np.array(counts))
+
+
+@pytest.mark.parametrize("M,frac_out,kind,Tg", [(400, 0.6, "labels", 16), (400, 0.5, "inverted", 8),
+                                                (3000, 0.4, "noisy", 64), (5, 0.0, "labels", 4),
+                                                (3, 0.0, "labels", 4), (2500, 0.9, "noisy", 32)])
+def test_ransac_prior_matches_oracle(M, frac_out, kind, Tg):
+    rng = np.random.default_rng(M + Tg)
+    pts, out = _synthetic(rng, M, frac_out)
+    if kind == "labels":
+        prior = np.where(out, 0.0, 1.0)
+    elif kind == "inverted":
+        prior = np.where(out, 1.0, 0.0)
+    else:
+        prior = np.clip(np.where(out, 0.3, 0.7) + 0.25 * rng.standard_normal(M), 0, 1)
+    prior = prior.astype(np.float32)
+    T = 300
+    ctx = lp.Context(Ls=(16,), ransac_iters=T, seed=21)
+    g = _gpu_prior(ctx, pts, prior, Tg, pair_id=2)
+    o = oracle.ransac_prior(pts.astype(np.float64), prior, Tg=Tg, T=T, seed=21, pair_id=2, want_counts=True)
+    assert g["best_t"] == o["best_t"] and g["iters"] == o["iters"]
+    # hypotheses that could not be formed are the same ones (same draws)
+    assert np.array_equal(g["counts"] < 0, o["counts"] < 0)
+    ok = o["counts"] >= 0
+    assert (g["counts"][ok] <= o["counts"][ok]).all()
+    if o["best_t"] < 0:
+        assert g["n_in"] == 0 and not g["H"].any()
+        return
+    e = np.sqrt(((G.proj(o["H"], pts[:, :2].astype(np.float64)) - pts[:, 2:]) ** 2).sum(1))
+    border = np.abs(e - 3.0) <= 1e-4
+    assert np.array_equal(g["inliers"][~border], o["inliers"][~border])
+    sel = o["inliers"].astype(bool)
+    q = pts[sel, :2].astype(np.float64)
+    assert np.abs(G.proj(g["H"], q) - G.proj(o["H"], q)).max() < 1e-3
+
+
+def test_ransac_prior_fallback_equals_plain_ransac():
+    rng = np.random.default_rng(77)
+    pts, out = _synthetic(rng, 1500, 0.5)
+    prior = np.where(out, 1.0, 0.0).astype(np.float32)      # points at outliers only
+    ctx = lp.Context(Ls=(16,), ransac_iters=500, seed=5)
+    g = _gpu_prior(ctx, pts, prior, 16, pair_id=9)
+    u = G.ransac(ctx, pts, pair_id=9)
+    assert g["iters"] == 516 and g["best_t"] == 16 + u["best_t"]
+    assert np.array_equal(g["inliers"], u["inliers"]) and np.array_equal(g["H"], u["H"])
+
+
+def test_trained_proposal_gains_over_uniform():
+    """Train on 24 seeded 640x480 pairs labelled by plain RANSAC, evaluate on 6
+    held-out pairs: the guided phase reaches plain RANSAC's best count in fewer
+    hypotheses, stops early, and returns the same inlier set."""
+    Ls = synth.PAIR_640x480_LS
+    ctx = lp.Context(Ls=Ls, ransac_iters=1000, ratio=0.9)
+    train_pairs = [synth.pair_640x480_random(s) for s in range(1000, 1024)]
+    feat, label = proposal.collect(ctx, ((p.A, p.B) for p in train_pairs))
+    assert feat.shape[0] > 5000
+    net = lp.Mlp(seed=0)
+    losses = proposal.train(net, feat, label, epochs=30, batch=4096, lr=3e-3)
+    assert np.mean(losses[-5:]) < 0.8 * np.mean(losses[:2])
+    reach_u, reach_g, same, stopped = [], [], 0, 0
+    for k, s in enumerate(range(3000, 3006)):
+        p = synth.pair_640x480_random(s)
+        pm = proposal.images_matches(ctx, p.A, p.B)
+        Hu, inl_u, n_u, bt_u = proposal.lp.ransac(ctx, pm.pts, k, pm.d_M)
+        cu = ctx.lp_diag_last_ransac_counts(1000)
+        target = max(cu)
+        g = proposal.guided_ransac(ctx, net, pm, guided_iters=64, pair_id=k, want_counts=True)
+        reach_u.append(proposal.iterations_to_reach(cu, target))
+        reach_g.append(proposal.iterations_to_reach(g.counts[:64], target) if g.iters == 64
+                       else 64 + proposal.iterations_to_reach(g.counts[64:], target))
+        stopped += g.iters == 64
+        same += np.array_equal(g.inliers, G.host(inl_u)[:pm.M])
+        assert g.n_in >= int(G.host(n_u)[0]) - 2
+    print(f"iterations to reach plain best: uniform {reach_u} guided {reach_g}; stopped {stopped}/6; same sets {same}/6")
+    assert stopped >= 5 and same >= 5
+    assert np.mean(reach_g) < np.mean(reach_u)

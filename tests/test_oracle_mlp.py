@@ -87,19 +87,51 @@ def test_guided_draws_follow_weights():
     assert chi2 < 30          # 7 dof
 
 
-def test_ransac_prior_finds_the_model_early():
-    rng = np.random.default_rng(5)
-    M = 400
+def _prior_case(frac_out, M=400, seed=5):
+    rng = np.random.default_rng(seed)
     H = np.array([[1.02, 0.05, 30.0], [-0.04, 0.99, -12.0], [1e-5, -2e-5, 1.0]])
     pa = np.round(rng.uniform(0, 900, (M, 2)))
     q = np.c_[pa, np.ones(M)] @ H.T
     pb = q[:, :2] / q[:, 2:]
-    out = rng.uniform(size=M) < 0.7
+    out = rng.uniform(size=M) < frac_out
     pb[out] = rng.uniform(0, 900, (out.sum(), 2))
-    pts = np.c_[pa, pb]
+    return np.c_[pa, pb], out
+
+
+def test_ransac_prior_finds_the_model_early():
+    pts, out = _prior_case(0.7)
     prior = np.where(out, 0.0, 1.0).astype(np.float32)
-    g = oracle.ransac_prior(pts, prior, T=200, seed=3, want_counts=True)
+    g = oracle.ransac_prior(pts, prior, Tg=16, T=200, seed=3, want_counts=True)
     u = oracle.ransac(pts, T=200, seed=3, want_all=True)
     assert g["n_in"] == u["n_in"] == (~out).sum()
     assert np.array_equal(g["inliers"], u["inliers"])
-    assert g["best_t"] < u["best_t"]
+    assert g["iters"] == 16 and g["best_t"] < u["best_t"]
+    assert (g["counts"][16:] == -1).all()
+
+
+def test_guided_stop_is_the_standard_bound():
+    # T(w) = ceil(log(0.01) / log(1 - w^4)); w = 1/2 -> 71.36 -> 72
+    assert oracle.guided_stop(1, 2, 72) and not oracle.guided_stop(1, 2, 71)
+    for w_num, w_den in [(3, 10), (9, 10), (1, 7), (999, 1000)]:
+        w = w_num / w_den
+        need = math.ceil(math.log(0.01) / math.log1p(-w ** 4))
+        assert oracle.guided_stop(w_num, w_den, need) and not oracle.guided_stop(w_num, w_den, need - 1)
+    assert oracle.guided_stop(5, 5, 1)          # every draw an inlier
+    assert not oracle.guided_stop(0, 5, 10**6)  # no inlier weight
+    assert not oracle.guided_stop(0, 0, 10)
+
+
+def test_ransac_prior_falls_back_to_uniform():
+    # a prior that points only at outliers never passes the stop test: the
+    # result is uniform RANSAC's, iteration numbers offset by Tg
+    pts, out = _prior_case(0.5, seed=8)
+    prior = np.where(out, 1.0, 0.0).astype(np.float32)
+    g = oracle.ransac_prior(pts, prior, Tg=8, T=300, seed=4, want_counts=True)
+    u = oracle.ransac(pts, T=300, seed=4, want_all=True)
+    assert g["iters"] == 308 and g["best_t"] == 8 + u["best_t"]
+    assert g["n_in"] == u["n_in"] and np.array_equal(g["inliers"], u["inliers"])
+    assert np.array_equal(g["H"], u["H"])
+    assert np.array_equal(g["counts"][8:], u["counts"])
+    # too few matches: no model, no stop
+    g = oracle.ransac_prior(pts[:3], prior[:3], Tg=8, T=30)
+    assert g["best_t"] == -1 and g["n_in"] == 0 and g["iters"] == 38
