@@ -289,7 +289,67 @@ def fp32_form_and_batch(args, rank):
         t += a.elapsed_time(b) / 1e3
     out["batch_3x3"] = {"images": 9, "pairs": 36, "pairs_per_s": 36 * k / t, "ms_per_batch": 1e3 * t / k,
                         "valid_pairs": int(va.sum().item()), "graph": True}
+    if args.train_pairs > 0:
+        out["learned_proposal"] = learned_proposal(args, bt, images, ctx, HM, ni, va, flush, k)
     return out
+
+
+def learned_proposal(args, bt, images, ctx, HM, ni, va, flush, k):
+    """Train the inlier-probability network on seeded 640x480 pairs labelled by
+    plain RANSAC, then run the nine-tile batch with it guiding RANSAC: the
+    iterations each pair needs to reach plain RANSAC's best count, whether the
+    inlier sets agree, and the batch's pairs/s with the network attached."""
+    import torch
+
+    from paper_2405_08578_gb300 import lp, proposal, synth
+    t0 = time.time()
+    ctx_t = lp.Context(Ls=synth.PAIR_640x480_LS)
+    seeds = range(1000, 1000 + args.train_pairs)
+    feat, label = proposal.collect(ctx_t, ((p.A, p.B) for p in map(synth.pair_640x480_random, seeds)))
+    net = lp.Mlp(seed=0)
+    losses = proposal.train(net, feat, label, epochs=20, batch=4096, lr=3e-3)
+    train_s = time.time() - t0
+    Tg, T = 64, ctx.cfg.ransac_iters
+    feats = [lp.features(ctx, im) for im in bt.images]
+    reach_u, reach_g, stopped, same, nvalid, q = [], [], 0, 0, 0, 0
+    for a in range(9):
+        for b in range(a + 1, 9):
+            pm = proposal.pair_matches(ctx, feats[a], feats[b])
+            _, inl_u, n_u, _ = lp.ransac(ctx, pm.pts, q, pm.d_M)
+            cu = ctx.lp_diag_last_ransac_counts(T)
+            g = proposal.guided_ransac(ctx, net, pm, Tg, q, want_counts=True)
+            q += 1
+            if int(n_u.item()) < ctx.cfg.min_inliers:
+                continue
+            nvalid += 1
+            target = max(cu)
+            reach_u.append(proposal.iterations_to_reach(cu, target))
+            reach_g.append(proposal.iterations_to_reach(g.counts[:Tg], target) if g.iters == Tg
+                           else Tg + proposal.iterations_to_reach(g.counts[Tg:], target))
+            stopped += g.iters == Tg
+            same += bool(np.array_equal(g.inliers, inl_u[:pm.M].cpu().numpy()))
+    ctx.lp_set_proposal(net, Tg)
+    s = torch.cuda.current_stream()
+    for _ in range(3):
+        ctx.lp_stitch_pairs(images, HM, ni, va)
+    torch.cuda.synchronize()
+    t = 0.0
+    for _ in range(k):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        ctx.lp_stitch_pairs(images, HM, ni, va)
+        e1.record(s)
+        torch.cuda.synchronize()
+        t += e0.elapsed_time(e1) / 1e3
+    ctx.lp_set_proposal(None)
+    return {"train_pairs": args.train_pairs, "train_matches": int(feat.shape[0]),
+            "inlier_label_frac": float(label.float().mean().item()), "loss_first": losses[0], "loss_last": losses[-1],
+            "train_s": round(train_s, 1), "guided_iters": Tg, "valid_pairs": nvalid,
+            "mean_iters_to_plain_best": {"uniform": float(np.mean(reach_u)) if reach_u else None,
+                                         "guided": float(np.mean(reach_g)) if reach_g else None},
+            "guided_stopped": stopped, "identical_inlier_sets": same,
+            "batch_pairs_per_s": 36 * k / t, "batch_valid_pairs": int(va.sum().item())}
 
 
 def main():
@@ -300,6 +360,8 @@ def main():
     ap.add_argument("--impl", default="lp", choices=["lp", "reference"])
     ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16"])
     ap.add_argument("--no-extras", action="store_true", help="skip the FP32-form and 3x3-batch side measurements")
+    ap.add_argument("--train-pairs", type=int, default=64,
+                    help="640x480 pairs that train the learned RANSAC proposal (0 skips it)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -370,6 +432,8 @@ def main():
         line["config"]["speedup_vs_fp32_form"] = value / world / extra["fp32_form_pairs_per_s"]
         line["config"]["fp32_form_inliers"] = extra["fp32_form_inliers"]
         line["config"]["batch_3x3"] = extra["batch_3x3"]
+        if "learned_proposal" in extra:
+            line["config"]["learned_proposal"] = extra["learned_proposal"]
     if world == 1 and not args.no_cpu_baseline:
         tot, parts, sample = oracle_pair_seconds(r["pair"], M=max(r["M"], 4))
         line["cpu_baseline"] = {"value": 1.0 / tot, "unit": "pairs/s", "cores": 1, "kind": "oracle",

@@ -323,6 +323,13 @@ LP_API const char* lp_last_error(lp_ctx* ctx);
  * because their BF16 ranking could not be certified (waits for the stream). */
 LP_API int lp_diag_last_rescans(lp_ctx* ctx, int64_t* out);
 
+/* Attach a network to the context (NULL detaches it): lp_stitch_pair and
+ * lp_stitch_pairs then score every pair's matches with it (lp_mlp_features,
+ * lp_mlp_forward) and run lp_ransac_prior with guided_iters instead of
+ * lp_ransac.  The context does not own the network; keep it alive while it is
+ * attached.  Errors: LP_ERR_ARG (guided_iters outside 1..65536). */
+LP_API int lp_set_proposal(lp_ctx* ctx, lp_mlp* mlp, int32_t guided_iters);
+
 /* FP32 inlier count (points certainly inside the threshold) of each hypothesis
  * of the context's last lp_ransac (n = T) or lp_ransac_prior
  * (n = guided_iters + T) call; -1 where no hypothesis was formed or the phase

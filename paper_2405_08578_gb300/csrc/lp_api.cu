@@ -22,10 +22,23 @@ enum BufId {
     B_IMG_A, B_IMG_B, B_GRAY_A, B_GRAY_B, B_KP_A, B_KP_B, B_ORI_A, B_ORI_B,
     B_DESC_A, B_DESC_B, B_D16_A, B_D16_B, B_VAL_A, B_VAL_B,
     B_MATCH, B_D1, B_D2, B_PTS, B_M, B_INL, B_H, B_NIN, B_BEST, B_LUTS, B_BATCH, B_PREFIX,
+    B_ROWS, B_FEAT, B_PROB,
     B_COUNT
 };
 
 }  // namespace
+
+struct lp_mlp {
+    int device = 0;
+    float* master = nullptr;   // [LP_MLP_PARAMS] x 4: master, m, v, shadow (one block)
+    float* m = nullptr;
+    float* v = nullptr;
+    float* shadow = nullptr;
+    float* part = nullptr;     // per-CTA gradient partials
+    float* lossp = nullptr;
+    size_t part_ctas = 0;
+    int step = 0;
+};
 
 struct lp_ctx {
     lp_config cfg;
@@ -38,6 +51,8 @@ struct lp_ctx {
     int32_t* d_status = nullptr;
     cudaStream_t last = nullptr;
     int last_ransac_hyps = 0;           // hypotheses of the last lp_ransac / lp_ransac_prior
+    lp_mlp* proposal = nullptr;         // lp_set_proposal: network guiding the stitch calls' RANSAC
+    int32_t guided_iters = 0;
     DBuf buf[B_COUNT];
     char err[512];
 };
@@ -336,6 +351,32 @@ int lp_ransac(lp_ctx* c, const float* pts, int64_t M_cap, const int32_t* d_M, ui
     return LP_OK;
 }
 
+namespace {
+
+// features -> inlier probabilities -> guided RANSAC, for one compacted pair
+int guided_tail(lp_ctx* c, const uint32_t* kpA, const uint8_t* oriA, int HA, int WA, const uint32_t* kpB,
+                const uint8_t* oriB, int HB, int WB, const int32_t* match, const float* d1, const float* d2,
+                const int32_t* rows, float* feat, float* prob, const float* pts, int64_t M_cap, const int32_t* dM,
+                uint32_t pair_id, double* H, uint8_t* inl, int32_t* n_in, void* stream)
+{
+    int r = lp_mlp_features(c, kpA, oriA, HA, WA, kpB, oriB, HB, WB, match, d1, d2, rows, dM, M_cap, feat, stream);
+    if (r) return r;
+    if ((r = lp_mlp_forward(c->proposal, feat, M_cap, dM, prob, nullptr, stream)))
+        return fail(c, r, "lp_mlp_forward failed");
+    return lp_ransac_prior(c, pts, M_cap, dM, prob, c->guided_iters, pair_id, H, inl, n_in, nullptr, nullptr, stream);
+}
+
+}  // namespace
+
+int lp_set_proposal(lp_ctx* c, lp_mlp* mlp, int32_t guided_iters)
+{
+    if (!c) return LP_ERR_ARG;
+    if (mlp && (guided_iters < 1 || guided_iters > 65536)) return fail(c, LP_ERR_ARG, "guided_iters must be 1..65536");
+    c->proposal = mlp;
+    c->guided_iters = mlp ? guided_iters : 0;
+    return LP_OK;
+}
+
 int lp_stitch_pair(lp_ctx* c, const uint8_t* imgA, int HA, int WA, int pitchA, const uint8_t* imgB, int HB, int WB,
                    int pitchB, int channels, uint32_t pair_id, double* H, int32_t* n_in, int32_t* M_out, void* stream)
 {
@@ -353,7 +394,9 @@ int lp_stitch_pair(lp_ctx* c, const uint8_t* imgA, int HA, int WA, int pitchA, c
         {B_DESC_A, 512 * (size_t)KA}, {B_DESC_B, 512 * (size_t)KB},
         {B_D16_A, bf ? 256 * (size_t)KA : 0}, {B_D16_B, bf ? 256 * (size_t)KB : 0},
         {B_VAL_A, (size_t)KA}, {B_VAL_B, (size_t)KB}, {B_MATCH, 4 * (size_t)KA}, {B_D1, 4 * (size_t)KA},
-        {B_D2, 4 * (size_t)KA}, {B_PTS, 16 * (size_t)KA}, {B_M, 16}, {B_INL, (size_t)KA}, {B_BEST, 16}};
+        {B_D2, 4 * (size_t)KA}, {B_PTS, 16 * (size_t)KA}, {B_M, 16}, {B_INL, (size_t)KA}, {B_BEST, 16},
+        {B_ROWS, c->proposal ? 4 * (size_t)KA + 16 : 0}, {B_FEAT, c->proposal ? 32 * (size_t)KA + 32 : 0},
+        {B_PROB, c->proposal ? 4 * (size_t)KA + 16 : 0}};
     for (auto& q : need)
         if (q.n && (r = ensure(c, q.id, q.n))) return r;
     auto P = [&](BufId id) { return c->buf[id].p; };
@@ -376,9 +419,15 @@ int lp_stitch_pair(lp_ctx* c, const uint8_t* imgA, int HA, int WA, int pitchA, c
     if (KA == 0) {
         LP_CUDA(c, cudaMemsetAsync(dM, 0, sizeof(int32_t), S(stream)));
     } else if ((r = lp_compact(c, (const uint32_t*)P(B_KP_A), WA, (const uint32_t*)P(B_KP_B), WB,
-                               (const int32_t*)P(B_MATCH), KA, (float*)P(B_PTS), nullptr, dM, stream))) {
+                               (const int32_t*)P(B_MATCH), KA, (float*)P(B_PTS),
+                               c->proposal ? (int32_t*)P(B_ROWS) : nullptr, dM, stream))) {
         return r;
     }
+    if (c->proposal && KA > 0)
+        return guided_tail(c, (const uint32_t*)P(B_KP_A), (const uint8_t*)P(B_ORI_A), HA, WA, (const uint32_t*)P(B_KP_B),
+                           (const uint8_t*)P(B_ORI_B), HB, WB, (const int32_t*)P(B_MATCH), (const float*)P(B_D1),
+                           (const float*)P(B_D2), (int32_t*)P(B_ROWS), (float*)P(B_FEAT), (float*)P(B_PROB),
+                           (const float*)P(B_PTS), KA, dM, pair_id, H, (uint8_t*)P(B_INL), n_in, stream);
     return lp_ransac(c, (const float*)P(B_PTS), KA, dM, pair_id, H, (uint8_t*)P(B_INL), n_in, nullptr, stream);
 }
 
@@ -472,6 +521,10 @@ int lp_stitch_pairs(lp_ctx* c, const lp_image* imgs, int N, const int32_t* pairs
     const size_t o_pts = o; o += al256(16 * (size_t)Kmax + 16);
     const size_t o_inl = o; o += al256((size_t)Kmax + 8);
     const size_t o_M = o; o += al256(4 * (size_t)P + 8);
+    const bool guided = c->proposal != nullptr;
+    const size_t o_rows = o; o += guided ? al256(4 * (size_t)Kmax + 8) : 0;
+    const size_t o_feat = o; o += guided ? al256(32 * (size_t)Kmax + 32) : 0;
+    const size_t o_prob = o; o += guided ? al256(4 * (size_t)Kmax + 8) : 0;
     int r = ensure(c, B_BATCH, o + 256);
     if (r) return r;
     size_t mws = 0;
@@ -479,7 +532,9 @@ int lp_stitch_pairs(lp_ctx* c, const lp_image* imgs, int N, const int32_t* pairs
         const int64_t KA = ib[pl[2 * q]].K, KB = ib[pl[2 * q + 1]].K;
         mws = std::max(mws, bf ? lp::match_bf16_workspace(KA, KB, c->num_sms) : lp::match_fp32_workspace(KA, KB, c->num_sms));
     }
-    if ((r = ensure(c, B_MATCH_WS, mws)) || (r = ensure(c, B_RANSAC_WS, lp::ransac_workspace(Kmax, c->cfg.ransac_iters))))
+    const int Ttot = c->cfg.ransac_iters + (guided ? c->guided_iters : 0);
+    if ((r = ensure(c, B_MATCH_WS, mws)) || (r = ensure(c, B_RANSAC_WS, lp::ransac_workspace(Kmax, Ttot))) ||
+        (guided && (r = ensure(c, B_PREFIX, sizeof(unsigned long long) * (size_t)(Kmax + 1)))))
         return r;
     cudaStream_t s = S(stream);
     if (!c->luts_ready && (r = build_luts(c, s))) return r;
@@ -489,7 +544,9 @@ int lp_stitch_pairs(lp_ctx* c, const lp_image* imgs, int N, const int32_t* pairs
     std::vector<long long> key = {N, P, ch, (long long)(uintptr_t)HM, (long long)(uintptr_t)n_in,
                                   (long long)(uintptr_t)valid, (long long)(uintptr_t)Mbuf,
                                   (long long)(uintptr_t)c->buf[B_BATCH].p, (long long)(uintptr_t)c->buf[B_MATCH_WS].p,
-                                  (long long)(uintptr_t)c->buf[B_RANSAC_WS].p};
+                                  (long long)(uintptr_t)c->buf[B_RANSAC_WS].p,
+                                  (long long)(uintptr_t)c->proposal, c->guided_iters,
+                                  (long long)(uintptr_t)c->buf[B_PREFIX].p};
     for (int i = 0; i < N; ++i) {
         key.push_back((long long)(uintptr_t)imgs[i].data);
         key.push_back(imgs[i].H); key.push_back(imgs[i].W); key.push_back(imgs[i].pitch);
@@ -527,13 +584,21 @@ int lp_stitch_pairs(lp_ctx* c, const lp_image* imgs, int N, const int32_t* pairs
                                    (int32_t*)(base + o_match), (float*)(base + o_d1), (float*)(base + o_d2), stream)))
                     return rr;
                 if ((rr = lp_compact(c, (const uint32_t*)(base + A.kp), imgs[a].W, (const uint32_t*)(base + B.kp),
-                                     imgs[b].W, (const int32_t*)(base + o_match), A.K, (float*)(base + o_pts), nullptr,
-                                     Mbuf + q, stream)))
+                                     imgs[b].W, (const int32_t*)(base + o_match), A.K, (float*)(base + o_pts),
+                                     guided ? (int32_t*)(base + o_rows) : nullptr, Mbuf + q, stream)))
                     return rr;
             }
-            if ((rr = lp_ransac(c, (const float*)(base + o_pts), A.K, Mbuf + q, (uint32_t)q, HM + 9 * (size_t)q,
-                                base + o_inl, n_in + q, nullptr, stream)))
-                return rr;
+            if (guided && A.K > 0)
+                rr = guided_tail(c, (const uint32_t*)(base + A.kp), base + A.ori, imgs[a].H, imgs[a].W,
+                                 (const uint32_t*)(base + B.kp), base + B.ori, imgs[b].H, imgs[b].W,
+                                 (const int32_t*)(base + o_match), (const float*)(base + o_d1),
+                                 (const float*)(base + o_d2), (int32_t*)(base + o_rows), (float*)(base + o_feat),
+                                 (float*)(base + o_prob), (const float*)(base + o_pts), A.K, Mbuf + q, (uint32_t)q,
+                                 HM + 9 * (size_t)q, base + o_inl, n_in + q, stream);
+            else
+                rr = lp_ransac(c, (const float*)(base + o_pts), A.K, Mbuf + q, (uint32_t)q, HM + 9 * (size_t)q,
+                               base + o_inl, n_in + q, nullptr, stream);
+            if (rr) return rr;
         }
         k_pair_valid<<<(P + 127) / 128, 128, 0, s>>>(n_in, P, c->cfg.min_inliers, valid);
         LP_CUDA(c, cudaGetLastError());
@@ -659,17 +724,6 @@ int lp_diag_gray(const uint8_t* rgb, int64_t n, uint8_t* gray, void* stream)
     return lp::launch_diag_gray(rgb, n, gray, S(stream)) == cudaSuccess ? LP_OK : LP_ERR_CUDA;
 }
 
-struct lp_mlp {
-    int device = 0;
-    float* master = nullptr;   // [LP_MLP_PARAMS] x 4: master, m, v, shadow (one block)
-    float* m = nullptr;
-    float* v = nullptr;
-    float* shadow = nullptr;
-    float* part = nullptr;     // per-CTA gradient partials
-    float* lossp = nullptr;
-    size_t part_ctas = 0;
-    int step = 0;
-};
 
 namespace {
 

@@ -46,7 +46,7 @@ SYMBOLS = ["lp_config_default", "lp_create", "lp_destroy", "lp_num_keypoints", "
            "lp_last_error", "lp_diag_last_rescans", "lp_diag_orient_bins", "lp_diag_orient_weights", "lp_diag_philox", "lp_diag_gray",
            "lp_mlp_create", "lp_mlp_destroy", "lp_mlp_set_params", "lp_mlp_get_params", "lp_mlp_get_state", "lp_mlp_save",
            "lp_mlp_load", "lp_mlp_features", "lp_mlp_forward", "lp_mlp_train_step", "lp_ransac_prior",
-           "lp_diag_last_ransac_counts"]
+           "lp_diag_last_ransac_counts", "lp_set_proposal"]
 MLP_PARAMS = 4801
 
 
@@ -98,6 +98,7 @@ def load(build_if_missing: bool = True):
         "lp_mlp_train_step": (i32, [P, P, P, i64, C.c_float, P, P]),
         "lp_ransac_prior": (i32, [P, P, i64, P, P, i32, u32, P, P, P, P, P, P]),
         "lp_diag_last_ransac_counts": (i32, [P, P, i32]),
+        "lp_set_proposal": (i32, [P, P, i32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -235,6 +236,12 @@ class Context:
         self._chk(self.lib.lp_diag_last_ransac_counts(self.h, C.cast(arr, C.c_void_p), n),
                   "lp_diag_last_ransac_counts")
         return list(arr)
+
+    def lp_set_proposal(self, mlp, guided_iters: int = 64):
+        """Guide the stitch calls' RANSAC with an Mlp (None detaches it)."""
+        self._proposal = mlp                  # keep the network alive while attached
+        self._chk(self.lib.lp_set_proposal(self.h, mlp.h if mlp is not None else None, int(guided_iters)),
+                  "lp_set_proposal")
 
     def lp_sync_status(self):
         return self.lib.lp_sync_status(self.h)

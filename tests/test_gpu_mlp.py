@@ -260,3 +260,54 @@ def test_trained_proposal_gains_over_uniform():
     print(f"iterations to reach plain best: uniform {reach_u} guided {reach_g}; stopped {stopped}/6; same sets {same}/6")
     assert stopped >= 5 and same >= 5
     assert np.mean(reach_g) < np.mean(reach_u)
+
+
+def _stitch_one(ctx, A, B, pair_id):
+    bA, pA = lp.pitched_device(A)
+    bB, pB = lp.pitched_device(B)
+    H = torch.zeros(9, dtype=torch.float64, device="cuda")
+    n = torch.zeros(1, dtype=torch.int32, device="cuda")
+    M = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ctx.lp_stitch_pair(bA, A.shape[0], A.shape[1], pA, bB, B.shape[0], B.shape[1], pB, 1, pair_id, H, n, M)
+    return G.host(H).reshape(3, 3), int(G.host(n)[0]), int(G.host(M)[0])
+
+
+def test_attached_proposal_drives_the_stitch_calls():
+    """lp_stitch_pair / lp_stitch_pairs with a network attached equal the
+    step-by-step calls (features, forward, lp_ransac_prior), graph replays
+    included; detaching restores plain RANSAC."""
+    Ls = (16, 32)
+    ctx = lp.Context(Ls=Ls, ransac_iters=400, ratio=0.9)
+    net = lp.Mlp(seed=4)
+    imgs = [synth.small_pair(240, 320, s, theta_deg=3.0 * s, shift=0.25).A for s in (1, 2)]
+    p = synth.small_pair(240, 320, 3, theta_deg=-4.0, shift=0.3)
+    imgs = imgs + [p.A, p.B]
+    pairs = [(0, 1), (2, 3), (3, 2), (1, 3)]
+    want = []
+    for q, (a, b) in enumerate(pairs):
+        pm = proposal.images_matches(ctx, imgs[a], imgs[b])
+        g = proposal.guided_ransac(ctx, net, pm, guided_iters=32, pair_id=q)
+        want.append((g.H, g.n_in, pm.M))
+    ctx.lp_set_proposal(net, 32)
+    for q, (a, b) in enumerate(pairs):
+        H, n, M = _stitch_one(ctx, imgs[a], imgs[b], q)
+        assert np.array_equal(H, want[q][0]) and n == want[q][1] and M == want[q][2]
+    bufs = [lp.pitched_device(im) for im in imgs]
+    images = [(b, im.shape[0], im.shape[1], pt, 1) for (b, pt), im in zip(bufs, imgs)]
+    HM = torch.zeros((len(pairs), 9), dtype=torch.float64, device="cuda")
+    nin = torch.zeros(len(pairs), dtype=torch.int32, device="cuda")
+    val = torch.zeros(len(pairs), dtype=torch.uint8, device="cuda")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        for _ in range(3):                          # eager, then captured graph replays
+            HM.zero_()
+            nin.zero_()
+            ctx.lp_stitch_pairs(images, HM, nin, val, pairs=pairs, stream=s)
+            s.synchronize()
+            for q in range(len(pairs)):
+                assert np.array_equal(G.host(HM[q]).reshape(3, 3), want[q][0]) and int(G.host(nin)[q]) == want[q][1]
+    ctx.lp_set_proposal(None)
+    H, n, M = _stitch_one(ctx, imgs[2], imgs[3], 1)
+    pm = proposal.images_matches(ctx, imgs[2], imgs[3])
+    Hu, _, nu, _ = lp.ransac(ctx, pm.pts, 1, pm.d_M)
+    assert np.array_equal(H, G.host(Hu).reshape(3, 3)) and n == int(G.host(nu)[0])
