@@ -330,6 +330,16 @@ LP_API int lp_diag_last_rescans(lp_ctx* ctx, int64_t* out);
  * attached.  Errors: LP_ERR_ARG (guided_iters outside 1..65536). */
 LP_API int lp_set_proposal(lp_ctx* ctx, lp_mlp* mlp, int32_t guided_iters);
 
+/* Kernel timing for benchmarks.  With profiling on, every lp_match call that
+ * is not being captured into a CUDA graph records two CUDA events on its
+ * stream, immediately before and after its distance kernel (the tensor-core
+ * kernel of LP_PREC_BF16, the FP32 kernel of LP_PREC_FP32).
+ * lp_diag_last_match_kernel_ms waits for the second event and returns the
+ * elapsed milliseconds of the last such call.  Errors: LP_ERR_ARG (profiling
+ * off, or no recorded call), LP_ERR_CUDA. */
+LP_API int lp_set_profiling(lp_ctx* ctx, int on);
+LP_API int lp_diag_last_match_kernel_ms(lp_ctx* ctx, float* ms);
+
 /* FP32 inlier count (points certainly inside the threshold) of each hypothesis
  * of the context's last lp_ransac (n = T) or lp_ransac_prior
  * (n = guided_iters + T) call; -1 where no hypothesis was formed or the phase

@@ -243,7 +243,9 @@ cudaError_t launch_match_fp32(const MatchArgs& a, void* ws, size_t ws_bytes, int
     cudaFuncSetAttribute(k_match_fp32_main, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (a.NB > 0) {
         dim3 grid((unsigned)rowblocks, (unsigned)S);
+        if (a.ev0) cudaEventRecord(a.ev0, s);
         k_match_fp32_main<<<grid, kThreads, smem, s>>>(a.dA, a.NA, nullptr, a.dB, nb, a.NB, S, cps, part);
+        if (a.ev1) cudaEventRecord(a.ev1, s);
     }
     const int Sused = a.NB > 0 ? S : 0;
     k_match_finish<<<(unsigned)((a.NA + 255) / 256), 256, 0, s>>>(part, Sused, a.NA, na, a.vA, a.ratio2, a.delta_s2,

@@ -917,7 +917,9 @@ cudaError_t launch_match_bf16(const MatchArgs& a, void* ws, size_t ws_bytes, int
         if ((e = cudaFuncSetAttribute(k_match_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTC)) !=
             cudaSuccess)
             return e;
+        if (a.ev0) cudaEventRecord(a.ev0, s);
         k_match_tc<<<grid, kThreadsTC, kSmemTC, s>>>(tA, tB, p);
+        if (a.ev1) cudaEventRecord(a.ev1, s);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         k_rerank<<<(unsigned)((a.NA + kRerankWarps - 1) / kRerankWarps), kRerankWarps * 32, 0, s>>>(
             a.dA, a.vA, a.dB, nb32, pv, pj, L.S, a.NA, kDelta, part1, rows, cnt);

@@ -52,6 +52,8 @@ struct lp_ctx {
     cudaStream_t last = nullptr;
     int last_ransac_hyps = 0;           // hypotheses of the last lp_ransac / lp_ransac_prior
     lp_mlp* proposal = nullptr;         // lp_set_proposal: network guiding the stitch calls' RANSAC
+    cudaEvent_t prof_ev[2] = {nullptr, nullptr};   // lp_set_profiling: around the last distance kernel
+    bool prof_recorded = false;
     int32_t guided_iters = 0;
     DBuf buf[B_COUNT];
     char err[512];
@@ -233,6 +235,8 @@ int lp_destroy(lp_ctx* c)
     for (auto& b : c->buf)
         if (b.p) cudaFree(b.p);
     if (c->d_status) cudaFree(c->d_status);
+    for (auto& e : c->prof_ev)
+        if (e) cudaEventDestroy(e);
     delete c;
     return LP_OK;
 }
@@ -306,6 +310,14 @@ int lp_match(lp_ctx* c, const float* dA, const uint16_t* dA_bf16, const uint8_t*
     a.delta_s2 = ds ? (float)((double)c->cfg.delta_s * (double)c->cfg.delta_s) : INFINITY;
     a.match = match; a.d1 = d1; a.d2 = d2; a.status = c->d_status;
     c->last = S(stream);
+    if (c->prof_ev[0] && NB > 0) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(S(stream), &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone) {
+            a.ev0 = c->prof_ev[0];
+            a.ev1 = c->prof_ev[1];
+            c->prof_recorded = true;
+        }
+    }
     if (c->cfg.precision == LP_PREC_BF16) {
         if (!dA_bf16 || (NB > 0 && !dB_bf16)) return fail(c, LP_ERR_ARG, "BF16 matching needs the bf16 descriptors");
         if (!aligned(dA_bf16, 16) || (dB_bf16 && !aligned(dB_bf16, 16))) return fail(c, LP_ERR_ALIGN, "bf16 alignment");
@@ -673,6 +685,33 @@ int lp_mlp_features(lp_ctx* c, const uint32_t* kpA, const uint8_t* oriA, int HA,
     c->last = S(stream);
     LP_CUDA(c, lp::launch_mlp_features(kpA, oriA, HA, WA, kpB, oriB, HB, WB, match, d1, d2, rows, d_M, M_cap, sc,
                                        feat, S(stream)));
+    return LP_OK;
+}
+
+int lp_set_profiling(lp_ctx* c, int on)
+{
+    if (!c) return LP_ERR_ARG;
+    if (on && !c->prof_ev[0]) {
+        if (cudaEventCreate(&c->prof_ev[0]) != cudaSuccess || cudaEventCreate(&c->prof_ev[1]) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, LP_ERR_CUDA, "cudaEventCreate failed");
+        }
+    } else if (!on && c->prof_ev[0]) {
+        cudaEventSynchronize(c->prof_ev[1]);
+        cudaEventDestroy(c->prof_ev[0]);
+        cudaEventDestroy(c->prof_ev[1]);
+        c->prof_ev[0] = c->prof_ev[1] = nullptr;
+    }
+    c->prof_recorded = false;
+    return LP_OK;
+}
+
+int lp_diag_last_match_kernel_ms(lp_ctx* c, float* ms)
+{
+    if (!c || !ms) return LP_ERR_ARG;
+    if (!c->prof_ev[0] || !c->prof_recorded) return fail(c, LP_ERR_ARG, "no profiled lp_match call");
+    LP_CUDA(c, cudaEventSynchronize(c->prof_ev[1]));
+    LP_CUDA(c, cudaEventElapsedTime(ms, c->prof_ev[0], c->prof_ev[1]));
     return LP_OK;
 }
 

@@ -51,6 +51,7 @@ struct MatchArgs {
     float delta_s2;      // Delta_s^2 or +inf
     int32_t* match; float* d1; float* d2;
     int32_t* status;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;   // recorded around the distance kernel when set
 };
 size_t match_fp32_workspace(int64_t NA, int64_t NB, int num_sms);
 cudaError_t launch_match_fp32(const MatchArgs& a, void* ws, size_t ws_bytes, int num_sms, cudaStream_t s);

@@ -46,7 +46,7 @@ SYMBOLS = ["lp_config_default", "lp_create", "lp_destroy", "lp_num_keypoints", "
            "lp_last_error", "lp_diag_last_rescans", "lp_diag_orient_bins", "lp_diag_orient_weights", "lp_diag_philox", "lp_diag_gray",
            "lp_mlp_create", "lp_mlp_destroy", "lp_mlp_set_params", "lp_mlp_get_params", "lp_mlp_get_state", "lp_mlp_save",
            "lp_mlp_load", "lp_mlp_features", "lp_mlp_forward", "lp_mlp_train_step", "lp_ransac_prior",
-           "lp_diag_last_ransac_counts", "lp_set_proposal"]
+           "lp_diag_last_ransac_counts", "lp_set_proposal", "lp_set_profiling", "lp_diag_last_match_kernel_ms"]
 MLP_PARAMS = 4801
 
 
@@ -99,6 +99,8 @@ def load(build_if_missing: bool = True):
         "lp_ransac_prior": (i32, [P, P, i64, P, P, i32, u32, P, P, P, P, P, P]),
         "lp_diag_last_ransac_counts": (i32, [P, P, i32]),
         "lp_set_proposal": (i32, [P, P, i32]),
+        "lp_set_profiling": (i32, [P, i32]),
+        "lp_diag_last_match_kernel_ms": (i32, [P, C.POINTER(C.c_float)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -242,6 +244,14 @@ class Context:
         self._proposal = mlp                  # keep the network alive while attached
         self._chk(self.lib.lp_set_proposal(self.h, mlp.h if mlp is not None else None, int(guided_iters)),
                   "lp_set_proposal")
+
+    def lp_set_profiling(self, on: bool = True):
+        self._chk(self.lib.lp_set_profiling(self.h, int(bool(on))), "lp_set_profiling")
+
+    def lp_diag_last_match_kernel_ms(self) -> float:
+        v = C.c_float()
+        self._chk(self.lib.lp_diag_last_match_kernel_ms(self.h, C.byref(v)), "lp_diag_last_match_kernel_ms")
+        return v.value
 
     def lp_sync_status(self):
         return self.lib.lp_sync_status(self.h)
