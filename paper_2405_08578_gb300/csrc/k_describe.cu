@@ -287,8 +287,6 @@ __global__ void __launch_bounds__(kCtaThreads) k_describe_cta(const DescParams p
 {
     extern __shared__ __align__(16) uint8_t sm[];
     __shared__ uint32_t hlo[36], hhi[36];
-    __shared__ unsigned long long wbest[kCtaThreads / 32];
-    __shared__ int wbin[kCtaThreads / 32];
     __shared__ float red[kCtaThreads / 32];
     __shared__ int best_s;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -340,7 +338,6 @@ __global__ void __launch_bounds__(kCtaThreads) k_describe_cta(const DescParams p
         __syncthreads();
         best = best_s;
     }
-    (void)wbest; (void)wbin;
     const float c = p.upright ? 1.f : p.cs[best][0];
     const float s = p.upright ? 0.f : p.cs[best][1];
     for (int e = tid; e < G * G; e += kCtaThreads) {

@@ -568,12 +568,38 @@ __device__ __forceinline__ float fp32_form_value(const float* a, const float* b,
 }
 
 constexpr int kRerankWarps = 8;
+constexpr int kMaxCand = 32 * kTopK;   // S <= 32 splits of kTopK candidates
 
+__device__ __forceinline__ void top2_lex(float& b1, int& j1, float& b2, int& j2, float x, int j)
+{
+    if (j < 0) return;
+    if (x < b1 || (x == b1 && (unsigned)j < (unsigned)j1)) {
+        b2 = b1; j2 = j1; b1 = x; j1 = j;
+    } else if (x < b2 || (x == b2 && (unsigned)j < (unsigned)j2)) {
+        b2 = x; j2 = j;
+    }
+}
+
+__device__ __forceinline__ void warp_top2(float& b1, int& j1, float& b2, int& j2)
+{
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        const float ob1 = __shfl_xor_sync(0xFFFFFFFFu, b1, o), ob2 = __shfl_xor_sync(0xFFFFFFFFu, b2, o);
+        const int oj1 = __shfl_xor_sync(0xFFFFFFFFu, j1, o), oj2 = __shfl_xor_sync(0xFFFFFFFFu, j2, o);
+        top2_lex(b1, j1, b2, j2, ob1, oj1);
+        top2_lex(b1, j1, b2, j2, ob2, oj2);
+    }
+}
+
+// One warp per row.  The candidates of all splits whose BF16 value lies in the
+// window are pooled in shared memory and re-scored one per lane, so the row
+// costs about one FP32-form evaluation whatever the split they came from.
 __global__ void __launch_bounds__(kRerankWarps * 32)
 k_rerank(const float* A, const uint8_t* vA, const float* B, const float* nb32, const float4* pv, const int4* pj, int S,
          long long NA, float delta, float4* out_part, int32_t* rescan_rows, int32_t* rescan_count)
 {
     __shared__ __align__(16) float qa[kRerankWarps][128];
+    __shared__ int pool[kRerankWarps][kMaxCand];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long i = (long long)blockIdx.x * kRerankWarps + warp;
     if (i >= NA) return;
@@ -582,7 +608,7 @@ k_rerank(const float* A, const uint8_t* vA, const float* B, const float* nb32, c
         return;
     }
     reinterpret_cast<float4*>(qa[warp])[lane] = reinterpret_cast<const float4*>(A + i * 128)[lane];
-    // gather the S x 4 candidates: lane c holds candidates 4c .. 4c+3 of split c (S <= 32)
+    // lane c holds the kTopK candidates of split c (S <= 32)
     float cv[kTopK];
     int cj[kTopK];
     float t4 = INFINITY;   // smallest k-th best value over the splits
@@ -617,43 +643,34 @@ k_rerank(const float* A, const uint8_t* vA, const float* B, const float* nb32, c
         m2 = n2;
     }
     const float window = m2 + 2.f * delta;
+    // pool the window's candidates (lane order, then list order)
+    int mine = 0;
+#pragma unroll
+    for (int k = 0; k < kTopK; ++k) mine += (cj[k] >= 0 && cv[k] <= window);
+    int off = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xFFFFFFFFu, off, o);
+        if (lane >= o) off += v;
+    }
+    const int n = __shfl_sync(0xFFFFFFFFu, off, 31);
+    off -= mine;
+#pragma unroll
+    for (int k = 0; k < kTopK; ++k)
+        if (cj[k] >= 0 && cv[k] <= window) pool[warp][off++] = cj[k];
     __syncwarp();
-    // exact FP32-form values of the candidates inside the window
+    // exact FP32-form values, one candidate per lane
     float b1 = INFINITY, b2 = INFINITY;
     int j1 = -1, j2 = -1;
-#pragma unroll
-    for (int k = 0; k < kTopK; ++k) {
-        if (cj[k] >= 0 && cv[k] <= window) {
-            const int j = cj[k];
-            const float x = fp32_form_value(qa[warp], B + (long long)j * 128, __ldg(nb32 + j));
-            if (x < b1 || (x == b1 && j < j1)) {
-                b2 = b1; j2 = j1; b1 = x; j1 = j;
-            } else if (x < b2 || (x == b2 && j < j2)) {
-                b2 = x; j2 = j;
-            }
-        }
+    for (int c = lane; c < n; c += 32) {
+        const int j = pool[warp][c];
+        top2_lex(b1, j1, b2, j2, fp32_form_value(qa[warp], B + (long long)j * 128, __ldg(nb32 + j)), j);
     }
-    // merge the lanes' top-2 lists, (value, column) order
-#pragma unroll
-    for (int o = 16; o; o >>= 1) {
-        const float ob1 = __shfl_xor_sync(0xFFFFFFFFu, b1, o), ob2 = __shfl_xor_sync(0xFFFFFFFFu, b2, o);
-        const int oj1 = __shfl_xor_sync(0xFFFFFFFFu, j1, o), oj2 = __shfl_xor_sync(0xFFFFFFFFu, j2, o);
-#pragma unroll
-        for (int r = 0; r < 2; ++r) {
-            const float x = r ? ob2 : ob1;
-            const int j = r ? oj2 : oj1;
-            if (j < 0) continue;
-            if (x < b1 || (x == b1 && (unsigned)j < (unsigned)j1)) {
-                b2 = b1; j2 = j1; b1 = x; j1 = j;
-            } else if ((x < b2 || (x == b2 && (unsigned)j < (unsigned)j2)) && j != j1) {
-                b2 = x; j2 = j;
-            }
-        }
-    }
+    warp_top2(b1, j1, b2, j2);
     if (lane == 0) {
         // every column outside the candidates has an FP32-form value >= t4 - delta
-        // t4 = inf: no split saw more than 4 valid columns, so every column
-        // was a candidate
+        // t4 = inf: no split saw more than kTopK valid columns, so every
+        // column was a candidate
         const bool certified = isinf(t4) || b2 < t4 - delta;
         if (certified) {
             out_part[i] = make_float4(b1, b2, __int_as_float(j1), __int_as_float(j2));
@@ -664,95 +681,95 @@ k_rerank(const float* A, const uint8_t* vA, const float* B, const float* nb32, c
     }
 }
 
-// FP32 re-scan of the queued rows.  A CTA owns a chunk of B columns (one
-// column per thread) and a group of up to kRescanRows queued rows (in shared
-// memory); each thread reads its column once and forms the FP32 form's value
-// for every row of the group (per row: sequential FMA over k, then
-// fma(-2, dot, |b|^2)).  Per row, the CTA keeps the chunk's two smallest
-// (value, column) pairs.
+// FP32 re-scan of the queued rows.  Work item = (group of up to kRescanRows
+// queued rows, one of kRescanGroups column ranges).  The range is walked in
+// chunks of 128 columns: the chunk is staged in shared memory with coalesced
+// loads (column pitch 132 floats: conflict-free 16-byte reads), then each
+// thread forms the FP32 form's value of its column for every row of the group
+// (sequential FMA over k, then fma(-2, dot, |b|^2)).  Per row, the item keeps
+// the range's two smallest (value, column) pairs.
 constexpr int kRescanThreads = 128;
-constexpr int kRescanRows = 32;
-
-__device__ __forceinline__ void top2_lex(float& b1, int& j1, float& b2, int& j2, float x, int j)
-{
-    if (j < 0) return;
-    if (x < b1 || (x == b1 && (unsigned)j < (unsigned)j1)) {
-        b2 = b1; j2 = j1; b1 = x; j1 = j;
-    } else if (x < b2 || (x == b2 && (unsigned)j < (unsigned)j2)) {
-        b2 = x; j2 = j;
-    }
-}
-
-constexpr int kRescanGroups = 64;   // column groups per queued row (partials per row)
+constexpr int kRescanRows = 8;
+constexpr int kRescanPitch = 132;
+constexpr int kRescanGroups = 64;   // column ranges per queued row (partials per row)
+constexpr size_t kRescanSmem = sizeof(float) * (kRescanThreads * kRescanPitch + 2 * kRescanRows * 128);
 
 __global__ void __launch_bounds__(kRescanThreads)
 k_rescan(const float* A, const float* B, const float* nb32, long long NB, const int32_t* rows, const int32_t* count,
          float4* part_r)
 {
-    __shared__ __align__(16) float qa[kRescanRows][128];
-    __shared__ float sv[kRescanRows][kRescanThreads];
+    extern __shared__ __align__(16) float rsm[];
+    float* tb = rsm;                                   // [128 columns][kRescanPitch]
+    float* qa = tb + kRescanThreads * kRescanPitch;    // [kRescanRows][128]
+    float* sv = qa + kRescanRows * 128;                // [kRescanRows][128]
     __shared__ float4 run[kRescanRows];   // running (b1, b2, j1, j2) per row
     const int R = *count;
     const int groups = (R + kRescanRows - 1) / kRescanRows;
     const long long items = (long long)groups * kRescanGroups;
     const long long nchunks = (NB + kRescanThreads - 1) / kRescanThreads;
     const long long cpg = (nchunks + kRescanGroups - 1) / kRescanGroups;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const float4* B4 = reinterpret_cast<const float4*>(B);
     for (long long it = blockIdx.x; it < items; it += gridDim.x) {
         const int g = (int)(it / kRescanGroups);
         const int cg = (int)(it - (long long)g * kRescanGroups);
         const int r0 = g * kRescanRows, nr = min(kRescanRows, R - r0);
         __syncthreads();
-        for (int e = threadIdx.x; e < nr * 32; e += kRescanThreads) {
+        for (int e = tid; e < kRescanRows * 32; e += kRescanThreads) {
             const int r = e >> 5, q = e & 31;
-            reinterpret_cast<float4*>(qa[r])[q] = reinterpret_cast<const float4*>(A + (long long)rows[r0 + r] * 128)[q];
+            reinterpret_cast<float4*>(qa)[e] =
+                r < nr ? reinterpret_cast<const float4*>(A + (long long)rows[r0 + r] * 128)[q] : make_float4(0, 0, 0, 0);
         }
-        if (threadIdx.x < kRescanRows)
-            run[threadIdx.x] = make_float4(INFINITY, INFINITY, __int_as_float(-1), __int_as_float(-1));
+        if (tid < kRescanRows)
+            run[tid] = make_float4(INFINITY, INFINITY, __int_as_float(-1), __int_as_float(-1));
         for (long long ch = (long long)cg * cpg; ch < min(nchunks, (long long)(cg + 1) * cpg); ++ch) {
+            const long long jb = ch * kRescanThreads;
             __syncthreads();
-            const long long j = ch * kRescanThreads + threadIdx.x;
-            const bool colok = j < NB && !isinf(__ldg(nb32 + (j < NB ? j : 0)));
-            if (colok) {
+#pragma unroll 8
+            for (int q = 0; q < 32; ++q) {   // float4 e = tid + 128 q: column e / 32, quarter e % 32
+                const int e = tid + kRescanThreads * q;
+                const int col = e >> 5, k4 = e & 31;
+                const long long j = jb + col;
+                const float4 w = j < NB ? __ldg(B4 + j * 32 + k4) : make_float4(0, 0, 0, 0);
+                *reinterpret_cast<float4*>(tb + col * kRescanPitch + 4 * k4) = w;
+            }
+            __syncthreads();
+            const long long j = jb + tid;
+            const float nbj = j < NB ? __ldg(nb32 + j) : INFINITY;
+            if (!isinf(nbj)) {
                 float acc[kRescanRows];
 #pragma unroll
                 for (int r = 0; r < kRescanRows; ++r) acc[r] = 0.f;
-                const float4* b4 = reinterpret_cast<const float4*>(B + j * 128);
-#pragma unroll 2
+                const float4* b4 = reinterpret_cast<const float4*>(tb + tid * kRescanPitch);
+#pragma unroll 4
                 for (int k4 = 0; k4 < 32; ++k4) {
-                    const float4 w = __ldg(b4 + k4);
+                    const float4 w = b4[k4];
 #pragma unroll
                     for (int r = 0; r < kRescanRows; ++r) {
-                        const float4 a = reinterpret_cast<const float4*>(qa[r])[k4];
+                        const float4 a = reinterpret_cast<const float4*>(qa + r * 128)[k4];
                         acc[r] = fmaf(a.x, w.x, acc[r]);
                         acc[r] = fmaf(a.y, w.y, acc[r]);
                         acc[r] = fmaf(a.z, w.z, acc[r]);
                         acc[r] = fmaf(a.w, w.w, acc[r]);
                     }
                 }
-                const float nbj = __ldg(nb32 + j);
 #pragma unroll
-                for (int r = 0; r < kRescanRows; ++r) sv[r][threadIdx.x] = fmaf(-2.f, acc[r], nbj);
+                for (int r = 0; r < kRescanRows; ++r) sv[r * 128 + tid] = fmaf(-2.f, acc[r], nbj);
             } else {
 #pragma unroll
-                for (int r = 0; r < kRescanRows; ++r) sv[r][threadIdx.x] = INFINITY;
+                for (int r = 0; r < kRescanRows; ++r) sv[r * 128 + tid] = INFINITY;
             }
             __syncthreads();
-            // warp w merges rows w, w + 4, ... of this chunk into the running lists
+            // warp w merges rows w and w + 4 of this chunk into the running lists
             for (int r = warp; r < nr; r += kRescanThreads / 32) {
                 float b1 = INFINITY, b2 = INFINITY;
                 int j1 = -1, j2 = -1;
-                for (int c = lane; c < kRescanThreads; c += 32) {
-                    const float x = sv[r][c];
-                    if (!isinf(x)) top2_lex(b1, j1, b2, j2, x, (int)(ch * kRescanThreads + c));
-                }
 #pragma unroll
-                for (int o = 16; o; o >>= 1) {
-                    const float ob1 = __shfl_xor_sync(0xFFFFFFFFu, b1, o), ob2 = __shfl_xor_sync(0xFFFFFFFFu, b2, o);
-                    const int oj1 = __shfl_xor_sync(0xFFFFFFFFu, j1, o), oj2 = __shfl_xor_sync(0xFFFFFFFFu, j2, o);
-                    top2_lex(b1, j1, b2, j2, ob1, oj1);
-                    top2_lex(b1, j1, b2, j2, ob2, oj2);
+                for (int c = lane; c < kRescanThreads; c += 32) {
+                    const float x = sv[r * 128 + c];
+                    if (!isinf(x)) top2_lex(b1, j1, b2, j2, x, (int)(jb + c));
                 }
+                warp_top2(b1, j1, b2, j2);
                 if (lane == 0) {
                     float4 q = run[r];
                     float c1 = q.x, c2 = q.y;
@@ -764,7 +781,7 @@ k_rescan(const float* A, const float* B, const float* nb32, long long NB, const 
             }
         }
         __syncthreads();
-        if (threadIdx.x < nr) part_r[(long long)(r0 + threadIdx.x) * kRescanGroups + cg] = run[threadIdx.x];
+        if (tid < nr) part_r[(long long)(r0 + tid) * kRescanGroups + cg] = run[tid];
     }
 }
 
@@ -782,13 +799,7 @@ __global__ void k_rescan_merge(const float4* part_r, int nchunks, const int32_t*
         top2_lex(b1, j1, b2, j2, q.x, __float_as_int(q.z));
         top2_lex(b1, j1, b2, j2, q.y, __float_as_int(q.w));
     }
-#pragma unroll
-    for (int o = 16; o; o >>= 1) {
-        const float ob1 = __shfl_xor_sync(0xFFFFFFFFu, b1, o), ob2 = __shfl_xor_sync(0xFFFFFFFFu, b2, o);
-        const int oj1 = __shfl_xor_sync(0xFFFFFFFFu, j1, o), oj2 = __shfl_xor_sync(0xFFFFFFFFu, j2, o);
-        top2_lex(b1, j1, b2, j2, ob1, oj1);
-        top2_lex(b1, j1, b2, j2, ob2, oj2);
-    }
+    warp_top2(b1, j1, b2, j2);
     if (lane == 0) out_part[rows[r]] = make_float4(b1, b2, __int_as_float(j1), __int_as_float(j2));
 }
 
@@ -923,7 +934,11 @@ cudaError_t launch_match_bf16(const MatchArgs& a, void* ws, size_t ws_bytes, int
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         k_rerank<<<(unsigned)((a.NA + kRerankWarps - 1) / kRerankWarps), kRerankWarps * 32, 0, s>>>(
             a.dA, a.vA, a.dB, nb32, pv, pj, L.S, a.NA, kDelta, part1, rows, cnt);
-        k_rescan<<<(unsigned)(4 * num_sms), kRescanThreads, 0, s>>>(a.dA, a.dB, nb32, a.NB, rows, cnt, part_r);
+        if ((e = cudaFuncSetAttribute(k_rescan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRescanSmem)) !=
+            cudaSuccess)
+            return e;
+        k_rescan<<<(unsigned)(4 * num_sms), kRescanThreads, kRescanSmem, s>>>(a.dA, a.dB, nb32, a.NB, rows, cnt,
+                                                                               part_r);
         k_rescan_merge<<<(unsigned)((a.NA + 7) / 8), 256, 0, s>>>(part_r, kRescanGroups, rows, cnt, part1);
         k_match_finish<<<(unsigned)((a.NA + 255) / 256), 256, 0, s>>>(part1, 1, a.NA, na, a.vA, a.ratio2, a.delta_s2,
                                                                       a.match, a.d1, a.d2);

@@ -1,20 +1,24 @@
 // Matched-pair compaction and RANSAC homography estimation (Sec. 2.4-2.5,
 // Eq. 7) for sm_103a.
 //
-//  k_compact      one CTA: stable prefix sum of accepted rows -> (xA, yA, xB, yB)
-//  k_ransac_hyp   one thread per iteration t: Philox4x32-10 draw of 4 distinct
-//                 matches, collinearity test, Hartley-normalised 4-point DLT
-//                 solved in FP64 (8x8 Gaussian elimination, partial pivoting)
+//  k_compact_count / k_compact_write  stable compaction of accepted rows into
+//                 (xA, yA, xB, yB), tiles of 2048 rows: per-tile counts, then
+//                 each tile adds the counts before it and writes in row order
+//  k_ransac_hyp   eight lanes per iteration t: Philox4x32-10 draw of 4 distinct
+//                 matches, collinearity test, Hartley normalisation, and the
+//                 8x9 DLT system solved in FP64 with one row per lane (partial
+//                 pivoting by warp shuffles, row-parallel back substitution)
 //  k_ransac_score one CTA per hypothesis: FP32 reprojection errors; counts of
 //                 points certainly inside (e^2 < t^2 - eps) and possibly inside
-//                 (e^2 < t^2 + eps)
-//  k_ransac_select one CTA: the largest certain count c*; every hypothesis whose
-//                 possible count reaches c* and that has points in the band is
-//                 recounted in FP64, so the winner (most inliers, earliest t) is
-//                 the FP64 winner
-//  k_ransac_refit one CTA: FP64 inlier mask of the winner, Hartley
-//                 normalisation, A^T A (9x9) by block reduction, cyclic Jacobi
-//                 smallest eigenvector, denormalisation, final FP64 mask.
+//                 (e^2 < t^2 + eps); the largest certain count c* by atomicMax
+//  k_ransac_recount one CTA per hypothesis whose possible count reaches c*:
+//                 the points in the band are re-tested in FP64, giving the
+//                 exact FP64 inlier count
+//  k_ransac_argmax most exact inliers, earliest t
+//  k_refit_*      least-squares refit of the winner's FP64 inliers (Eq. 7):
+//                 per-CTA partial sums reduced in a fixed order, the 9x9
+//                 normal matrix's smallest eigenvector by Cholesky and shifted
+//                 inverse iteration on one warp, denormalisation, final mask
 #include <math.h>
 
 #include <algorithm>
@@ -49,48 +53,85 @@ __global__ void k_diag_philox(const uint4* ctr, long long n, uint32_t k0, uint32
 }
 
 // ---------------------------------------------------------------- compaction
-constexpr int kCompactThreads = 1024;
+constexpr int kCompactThreads = 256;
+constexpr int kCompactPer = 8;                                  // consecutive rows per thread
+constexpr int kCompactRows = kCompactThreads * kCompactPer;    // rows per tile
 
-__global__ void __launch_bounds__(kCompactThreads)
-k_compact(const uint32_t* kpA, int WA, const uint32_t* kpB, int WB, const int32_t* match, long long NA,
-          float4* pts, int32_t* rows, int32_t* dM)
+__device__ __forceinline__ int compact_rows(const int32_t* match, long long NA, long long r0, int (&m)[kCompactPer])
 {
-    __shared__ int warp_tot[32];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const long long chunk = (NA + kCompactThreads - 1) / kCompactThreads;
-    const long long b = tid * chunk, e = min(NA, b + chunk);
-    int cnt = 0;
-    for (long long i = b; i < e; ++i) cnt += match[i] >= 0;
-    int incl = cnt;
+    int c = 0;
+#pragma unroll
+    for (int k = 0; k < kCompactPer; ++k) {
+        const long long i = r0 + k;
+        m[k] = i < NA ? match[i] : -1;
+        c += m[k] >= 0;
+    }
+    return c;
+}
+
+// exclusive prefix of v over the CTA (thread order) and the CTA total
+__device__ __forceinline__ int compact_scan(int v, int* wsum, int& total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int incl = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        const int v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-        if (lane >= o) incl += v;
+        const int u = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += u;
     }
-    if (lane == 31) warp_tot[warp] = incl;
+    if (lane == 31) wsum[warp] = incl;
     __syncthreads();
-    if (warp == 0) {
-        int w = warp_tot[lane];
-        int wi = w;
+    int before = 0;
+    total = 0;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int v = __shfl_up_sync(0xFFFFFFFFu, wi, o);
-            if (lane >= o) wi += v;
-        }
-        warp_tot[lane] = wi - w;   // exclusive
-        if (lane == 31) *dM = wi;
+    for (int w = 0; w < kCompactThreads / 32; ++w) {
+        const int x = wsum[w];
+        before += w < warp ? x : 0;
+        total += x;
     }
+    return before + incl - v;
+}
+
+__global__ void __launch_bounds__(kCompactThreads)
+k_compact_count(const int32_t* match, long long NA, int32_t* tile_cnt)
+{
+    __shared__ int wsum[kCompactThreads / 32];
+    int m[kCompactPer];
+    const long long r0 = (long long)blockIdx.x * kCompactRows + (long long)threadIdx.x * kCompactPer;
+    int total;
+    compact_scan(compact_rows(match, NA, r0, m), wsum, total);
+    if (threadIdx.x == 0) tile_cnt[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kCompactThreads)
+k_compact_write(const uint32_t* kpA, int WA, const uint32_t* kpB, int WB, const int32_t* match, long long NA,
+                const int32_t* tile_cnt, float4* pts, int32_t* rows, int32_t* dM)
+{
+    __shared__ int wsum[kCompactThreads / 32];
+    __shared__ int before_s;
+    int pre = 0;
+    for (int b = threadIdx.x; b < (int)blockIdx.x; b += kCompactThreads) pre += tile_cnt[b];
+    int tot_pre;
+    compact_scan(pre, wsum, tot_pre);
+    if (threadIdx.x == 0) before_s = tot_pre;
     __syncthreads();
-    int pos = warp_tot[warp] + incl - cnt;
-    for (long long i = b; i < e; ++i) {
-        const int j = match[i];
+    const int before = before_s;
+    int m[kCompactPer];
+    const long long r0 = (long long)blockIdx.x * kCompactRows + (long long)threadIdx.x * kCompactPer;
+    const int c = compact_rows(match, NA, r0, m);
+    int total;
+    int pos = before + compact_scan(c, wsum, total);
+#pragma unroll
+    for (int k = 0; k < kCompactPer; ++k) {
+        const int j = m[k];
         if (j < 0) continue;
-        const uint32_t ia = kpA[i], ib = kpB[j];
+        const uint32_t ia = kpA[r0 + k], ib = kpB[j];
         const uint32_t ya = ia / (uint32_t)WA, yb = ib / (uint32_t)WB;
         pts[pos] = make_float4((float)(ia - ya * WA), (float)ya, (float)(ib - yb * WB), (float)yb);
-        if (rows) rows[pos] = (int32_t)i;
+        if (rows) rows[pos] = (int32_t)(r0 + k);
         ++pos;
     }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) *dM = before + total;
 }
 
 // ---------------------------------------------------------------- FP64 model
@@ -149,18 +190,33 @@ __device__ bool denorm(const Norm2D& na, const Norm2D& nb, const double* hn, dou
     return true;
 }
 
+// Slots of the per-call flags word array (int32).
+constexpr int kFlagBest = 0, kFlagCount = 1, kFlagStop = 2, kFlagIters = 3, kFlagCmax = 4, kFlagWords = 8;
+
+// Eight lanes per hypothesis, lane r owning row r of the normalised 8x9 DLT
+// system (two rows per correspondence).
+constexpr int kHypThreads = 64;
+
 // prefix == nullptr: uniform draw; otherwise word w picks the match whose
 // interval of the inclusive prefix sums of integer weights contains
 // floor(w * total / 2^32) (probability proportional to the weight).
-__global__ void k_ransac_hyp(const float4* pts, long long M_cap, const int32_t* dM, int T, uint32_t k0, uint32_t k1,
-                             const unsigned long long* prefix, const int32_t* skip, double* Hs, int8_t* hok)
+__global__ void __launch_bounds__(kHypThreads)
+k_ransac_hyp(const float4* pts, long long M_cap, const int32_t* dM, int T, uint32_t k0, uint32_t k1,
+             const unsigned long long* prefix, const int32_t* skip, double* Hs, int8_t* hok, int32_t* flags)
 {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= T || (skip && *skip)) return;
-    hok[t] = 0;
+    const int g = (blockIdx.x * kHypThreads + threadIdx.x) >> 3;   // hypothesis t
+    const int r = threadIdx.x & 7;
+    const int base = threadIdx.x & 31 & ~7;                          // first lane of the group
+    const unsigned gm = 0xFFu << base;
+    if (skip && *skip) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) flags[kFlagCmax] = -1;
+    if (g >= T) return;                                              // whole groups
+    const int t = g;
+    if (r == 0) hok[t] = 0;
     const long long M = m_count(dM, M_cap);
     if (M < 4) return;
-    int idx[4];
+    // every lane of the group draws the same four indices
+    int idx[4] = {0, 0, 0, 0};
     int n = 0;
     uint4 blk = make_uint4(0, 0, 0, 0);
     for (int j = 0; j < 64 && n < 4; ++j) {
@@ -179,16 +235,20 @@ __global__ void k_ransac_hyp(const float4* pts, long long M_cap, const int32_t* 
             }
             i = (int)lo;
         }
-        bool dup = false;
-        for (int q = 0; q < n; ++q) dup |= idx[q] == i;
-        if (!dup) idx[n++] = i;
+        const bool dup = (n > 0 && idx[0] == i) || (n > 1 && idx[1] == i) || (n > 2 && idx[2] == i);
+        if (!dup) {
+            if (n == 0) idx[0] = i; else if (n == 1) idx[1] = i; else if (n == 2) idx[2] = i; else idx[3] = i;
+            ++n;
+        }
     }
     if (n < 4) return;
     double xa[4], ya[4], xb[4], yb[4];
+#pragma unroll
     for (int q = 0; q < 4; ++q) {
         const float4 p = pts[idx[q]];
         xa[q] = p.x; ya[q] = p.y; xb[q] = p.z; yb[q] = p.w;
     }
+#pragma unroll
     for (int a = 0; a < 4; ++a) {
         const int i0 = (a + 1) & 3, i1 = (a + 2) & 3, i2 = (a + 3) & 3;
         if (collinear(xa[i0], ya[i0], xa[i1], ya[i1], xa[i2], ya[i2])) return;
@@ -196,35 +256,61 @@ __global__ void k_ransac_hyp(const float4* pts, long long M_cap, const int32_t* 
     }
     Norm2D na, nb;
     if (!hartley4(xa, ya, na) || !hartley4(xb, yb, nb)) return;
-    double A[8][9];
-    for (int q = 0; q < 4; ++q) {
-        const double x = na.s * (xa[q] - na.cx), y = na.s * (ya[q] - na.cy);
-        const double u = nb.s * (xb[q] - nb.cx), v = nb.s * (yb[q] - nb.cy);
-        double* r0 = A[2 * q];
-        double* r1 = A[2 * q + 1];
-        r0[0] = x; r0[1] = y; r0[2] = 1; r0[3] = 0; r0[4] = 0; r0[5] = 0; r0[6] = -x * u; r0[7] = -y * u; r0[8] = u;
-        r1[0] = 0; r1[1] = 0; r1[2] = 0; r1[3] = x; r1[4] = y; r1[5] = 1; r1[6] = -x * v; r1[7] = -y * v; r1[8] = v;
+    // this lane's row: correspondence q = r / 2, the u row (even) or v row (odd)
+    const int q = r >> 1;
+    const double pxa = q == 0 ? xa[0] : q == 1 ? xa[1] : q == 2 ? xa[2] : xa[3];
+    const double pya = q == 0 ? ya[0] : q == 1 ? ya[1] : q == 2 ? ya[2] : ya[3];
+    const double pxb = q == 0 ? xb[0] : q == 1 ? xb[1] : q == 2 ? xb[2] : xb[3];
+    const double pyb = q == 0 ? yb[0] : q == 1 ? yb[1] : q == 2 ? yb[2] : yb[3];
+    const double x = na.s * (pxa - na.cx), y = na.s * (pya - na.cy);
+    const double u = nb.s * (pxb - nb.cx), v = nb.s * (pyb - nb.cy);
+    double a[9];
+    if ((r & 1) == 0) {
+        a[0] = x; a[1] = y; a[2] = 1; a[3] = 0; a[4] = 0; a[5] = 0; a[6] = -x * u; a[7] = -y * u; a[8] = u;
+    } else {
+        a[0] = 0; a[1] = 0; a[2] = 0; a[3] = x; a[4] = y; a[5] = 1; a[6] = -x * v; a[7] = -y * v; a[8] = v;
     }
+    // Gaussian elimination with partial pivoting (largest |a_rc| over rows
+    // r >= c, the lowest row on ties); decisions are taken on group-uniform
+    // values so the eight lanes never diverge around a shuffle
+#pragma unroll
     for (int c = 0; c < 8; ++c) {
-        int p = c;
-        for (int r = c + 1; r < 8; ++r)
-            if (fabs(A[r][c]) > fabs(A[p][c])) p = r;
-        if (!(fabs(A[p][c]) > 1e-10)) return;
-        if (p != c)
-            for (int j = 0; j < 9; ++j) { const double tmp = A[c][j]; A[c][j] = A[p][j]; A[p][j] = tmp; }
-        const double ip = 1.0 / A[c][c];
-        for (int r = c + 1; r < 8; ++r) {
-            const double f = A[r][c] * ip;
-            for (int j = c; j < 9; ++j) A[r][j] -= f * A[c][j];
+        double pv = r >= c ? fabs(a[c]) : -1.0;
+        int pr = r;
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) {
+            const double ov = __shfl_xor_sync(gm, pv, o);
+            const int orr = __shfl_xor_sync(gm, pr, o);
+            if (ov > pv || (ov == pv && orr < pr)) { pv = ov; pr = orr; }
+        }
+        pv = __shfl_sync(gm, pv, base);
+        pr = __shfl_sync(gm, pr, base);
+        if (!(pv > 1e-10)) return;
+        const int src = base + (r == c ? pr : (r == pr ? c : r));
+#pragma unroll
+        for (int j = c; j < 9; ++j) a[j] = __shfl_sync(gm, a[j], src);
+        double prow[9];
+#pragma unroll
+        for (int j = c; j < 9; ++j) prow[j] = __shfl_sync(gm, a[j], base + c);
+        const double ip = 1.0 / prow[c];
+        if (r > c) {
+            const double f = a[c] * ip;
+#pragma unroll
+            for (int j = c; j < 9; ++j) a[j] -= f * prow[j];
         }
     }
+    // back substitution, h_7 first; each h_k is broadcast as soon as known
+    double acc = a[8];
     double h[9];
-    for (int r = 7; r >= 0; --r) {
-        double s = A[r][8];
-        for (int j = r + 1; j < 8; ++j) s -= A[r][j] * h[j];
-        h[r] = s / A[r][r];
+#pragma unroll
+    for (int k = 7; k >= 0; --k) {
+        double hk = r == k ? acc / a[k] : 0.0;
+        hk = __shfl_sync(gm, hk, base + k);
+        h[k] = hk;
+        if (r < k) acc -= a[k] * hk;
     }
     h[8] = 1.0;
+    if (r != 0) return;
     double H[9];
     if (!denorm(na, nb, h, H)) return;
     for (int i = 0; i < 9; ++i) Hs[9ll * t + i] = H[i];
@@ -247,9 +333,22 @@ __device__ __forceinline__ int block_sum(int v, int* red)
     return s;
 }
 
+// FP32 inlier test against the band: 2 = certainly inside (e^2 < t^2 - eps),
+// 1 = in the band, 0 = outside or w <= 0.  e^2 < t^2 <=> |(u, v) - w p_B|^2 <
+// t^2 w^2 for w > 0 (no division).
+__device__ __forceinline__ int band32(const float* h, const float4& p, float t2, float eps)
+{
+    const float w = fmaf(h[6], p.x, fmaf(h[7], p.y, h[8]));
+    if (!(w > 0.f)) return 0;
+    const float du = fmaf(-p.z, w, fmaf(h[0], p.x, fmaf(h[1], p.y, h[2])));
+    const float dv = fmaf(-p.w, w, fmaf(h[3], p.x, fmaf(h[4], p.y, h[5])));
+    const float d2 = du * du + dv * dv, w2 = w * w;
+    return d2 < (t2 - eps) * w2 ? 2 : (d2 < (t2 + eps) * w2 ? 1 : 0);
+}
+
 __global__ void __launch_bounds__(kScoreThreads)
 k_ransac_score(const float4* pts, long long M_cap, const int32_t* dM, const double* Hs, const int8_t* hok,
-               float t2, float eps, const int32_t* skip, int32_t* lo, int32_t* hi)
+               float t2, float eps, const int32_t* skip, int32_t* lo, int32_t* hi, int32_t* flags)
 {
     __shared__ int red[32];
     const int t = blockIdx.x;
@@ -263,20 +362,17 @@ k_ransac_score(const float4* pts, long long M_cap, const int32_t* dM, const doub
     for (int i = 0; i < 9; ++i) h[i] = (float)Hs[9ll * t + i];
     int clo = 0, chi = 0;
     for (long long i = threadIdx.x; i < M; i += kScoreThreads) {
-        const float4 p = pts[i];
-        // e^2 < t^2  <=>  |(u, v) - w p_B|^2 < t^2 w^2  for w > 0 (no division)
-        const float w = fmaf(h[6], p.x, fmaf(h[7], p.y, h[8]));
-        if (w > 0.f) {
-            const float du = fmaf(-p.z, w, fmaf(h[0], p.x, fmaf(h[1], p.y, h[2])));
-            const float dv = fmaf(-p.w, w, fmaf(h[3], p.x, fmaf(h[4], p.y, h[5])));
-            const float d2 = du * du + dv * dv, w2 = w * w;
-            clo += d2 < (t2 - eps) * w2;
-            chi += d2 < (t2 + eps) * w2;
-        }
+        const int b = band32(h, pts[i], t2, eps);
+        clo += b == 2;
+        chi += b != 0;
     }
     clo = block_sum(clo, red);
     chi = block_sum(chi, red);
-    if (threadIdx.x == 0) { lo[t] = clo; hi[t] = chi; }
+    if (threadIdx.x == 0) {
+        lo[t] = clo;
+        hi[t] = chi;
+        atomicMax(flags + kFlagCmax, clo);
+    }
 }
 
 // FP64 inlier test of one correspondence (Eq. 7, one-sided error in B):
@@ -292,66 +388,68 @@ __device__ __forceinline__ bool inlier64(const double* H, const float4& p, doubl
     return du * du + dv * dv < t2 * (w * w);
 }
 
+// Exact count of every hypothesis that can still win: its possible count
+// reaches c* (the largest certain count).  Points certainly inside count as
+// inliers, points in the band are decided in FP64.  hi[t] <- the exact count,
+// or -1 for a hypothesis that cannot win.
+constexpr int kRecountThreads = 256;
+
+__global__ void __launch_bounds__(kRecountThreads)
+k_ransac_recount(const float4* pts, long long M_cap, const int32_t* dM, const double* Hs, const int32_t* lo,
+                 int32_t* hi, const int32_t* flags, float t2f, float eps, double t2, const int32_t* skip)
+{
+    __shared__ int red[32];
+    __shared__ int mode;
+    const int t = blockIdx.x;
+    if (skip && *skip) return;
+    if (threadIdx.x == 0) {
+        const int l = lo[t], h = hi[t], cmax = flags[kFlagCmax];
+        mode = (l < 0 || h < cmax) ? 0 : (h == l ? 1 : 2);
+        if (mode == 0) hi[t] = -1;
+    }
+    __syncthreads();
+    if (mode != 2) return;   // mode 1: no point in the band, hi[t] is already exact
+    const long long M = m_count(dM, M_cap);
+    double H[9];
+    float h[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) { H[i] = Hs[9ll * t + i]; h[i] = (float)H[i]; }
+    int n = 0;
+    for (long long i = threadIdx.x; i < M; i += kRecountThreads) {
+        const float4 p = pts[i];
+        const int b = band32(h, p, t2f, eps);
+        n += b == 2 ? 1 : (b == 1 ? (int)inlier64(H, p, t2) : 0);
+    }
+    n = block_sum(n, red);
+    if (threadIdx.x == 0) hi[t] = n;
+}
+
 constexpr int kSelThreads = 1024;
 
+// key = (count + 1) << 32 | (0xFFFFFFFF - t): the largest key is the most
+// inliers at the earliest iteration.
 __global__ void __launch_bounds__(kSelThreads)
-k_ransac_select(const float4* pts, long long M_cap, const int32_t* dM, int T, const double* Hs,
-                const int32_t* lo, const int32_t* hi, double t2, const int32_t* skip, int t_off, int32_t* best_out)
+k_ransac_argmax(const int32_t* exact, int T, const int32_t* skip, int t_off, int32_t* flags)
 {
+    __shared__ unsigned long long part[kSelThreads / 32];
     if (skip && *skip) return;
-    __shared__ int red[32];
-    __shared__ unsigned long long bestkey;
-    __shared__ int cand[kSelThreads];
-    __shared__ int ncand;
-    const long long M = m_count(dM, M_cap);
-    int cmax = -1;
-    for (int t = threadIdx.x; t < T; t += kSelThreads) cmax = max(cmax, lo[t]);
+    unsigned long long key = 0;
+    for (int t = threadIdx.x; t < T; t += kSelThreads) {
+        const int c = exact[t];
+        if (c >= 0) key = max(key, ((unsigned long long)(c + 1) << 32) | (0xFFFFFFFFull - (unsigned)t));
+    }
 #pragma unroll
-    for (int o = 16; o; o >>= 1) cmax = max(cmax, __shfl_xor_sync(0xFFFFFFFFu, cmax, o));
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = cmax;
-    if (threadIdx.x == 0) { bestkey = 0ull; ncand = 0; }
+    for (int o = 16; o; o >>= 1) key = max(key, __shfl_xor_sync(0xFFFFFFFFu, key, o));
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = key;
     __syncthreads();
-    cmax = -1;
-    for (int w = 0; w < kSelThreads / 32; ++w) cmax = max(cmax, red[w]);
-    if (cmax < 0) {
-        if (threadIdx.x == 0) { best_out[0] = -1; best_out[1] = -1; }
-        return;
-    }
-    // key = (count + 1) << 32 | (0xFFFFFFFF - t): the max key is the most
-    // inliers at the earliest iteration.  Iterations are visited in chunks of
-    // one CTA width; in-band candidates of a chunk are recounted in FP64.
-    for (int t0 = 0; t0 < T; t0 += kSelThreads) {
-        const int t = t0 + threadIdx.x;
-        if (t < T) {
-            const int l = lo[t], h = hi[t];
-            if (l >= 0 && h >= cmax) {
-                if (h == l) {
-                    atomicMax(&bestkey, ((unsigned long long)(l + 1) << 32) | (0xFFFFFFFFull - (unsigned)t));
-                } else {
-                    cand[atomicAdd(&ncand, 1)] = t;
-                }
-            }
-        }
-        __syncthreads();
-        const int nc = ncand;
-        for (int k = 0; k < nc; ++k) {
-            const int tc = cand[k];
-            double H[9];
-            for (int i = 0; i < 9; ++i) H[i] = Hs[9ll * tc + i];
-            int n = 0;
-            for (long long i = threadIdx.x; i < M; i += kSelThreads) n += inlier64(H, pts[i], t2);
-            n = block_sum(n, red);
-            if (threadIdx.x == 0)
-                atomicMax(&bestkey, ((unsigned long long)(n + 1) << 32) | (0xFFFFFFFFull - (unsigned)tc));
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) ncand = 0;
-        __syncthreads();
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        best_out[0] = t_off + (int)(0xFFFFFFFFull - (bestkey & 0xFFFFFFFFull));
-        best_out[1] = (int)(bestkey >> 32) - 1;
+    if (threadIdx.x != 0) return;
+    for (int w = 0; w < kSelThreads / 32; ++w) key = max(key, part[w]);
+    if (key == 0) {
+        flags[kFlagBest] = -1;
+        flags[kFlagCount] = -1;
+    } else {
+        flags[kFlagBest] = t_off + (int)(0xFFFFFFFFull - (key & 0xFFFFFFFFull));
+        flags[kFlagCount] = (int)(key >> 32) - 1;
     }
 }
 
@@ -360,16 +458,16 @@ k_ransac_select(const float4* pts, long long M_cap, const int32_t* dM, int T, co
 // inlier; the phase stops when (1 - w^4)^Tg <= 0.01, the standard bound
 // T >= log(0.01) / log(1 - w^4) without logarithms.  Every operation is a
 // single IEEE-rounded one (no contraction), powers by binary exponentiation.
-// flags[2] = stop, flags[3] = iterations used.
+// flags[kFlagStop] = stop, flags[kFlagIters] = iterations used.
 __global__ void __launch_bounds__(kSelThreads)
 k_guided_decide(const float4* pts, long long M_cap, const int32_t* dM, const double* Hs,
                 const unsigned long long* prefix, int Tg, int T, double t2, int32_t* flags)
 {
     __shared__ unsigned long long part[kSelThreads / 32];
-    const int tb = flags[0];
+    const int tb = flags[kFlagBest];
     const long long M = m_count(dM, M_cap);
     if (tb < 0 || M < 4) {
-        if (threadIdx.x == 0) { flags[2] = 0; flags[3] = Tg + T; }
+        if (threadIdx.x == 0) { flags[kFlagStop] = 0; flags[kFlagIters] = Tg + T; }
         return;
     }
     double H[9];
@@ -393,8 +491,8 @@ k_guided_decide(const float4* pts, long long M_cap, const int32_t* dM, const dou
         b = __dmul_rn(b, b);
     }
     const int stop = r <= 0.01;
-    flags[2] = stop;
-    flags[3] = stop ? Tg : Tg + T;
+    flags[kFlagStop] = stop;
+    flags[kFlagIters] = stop ? Tg : Tg + T;
 }
 
 // ---------------------------------------------------------------- refit
@@ -441,14 +539,13 @@ __device__ __forceinline__ void cta_range(long long M, long long& b, long long& 
     e = min(M, b + chunk);
 }
 
-// fixed-order sum of the CTAs' partials, columns [c0, c0 + n)
-__device__ void sum_parts(const double* part, int c0, int n, double* out)
+// fixed-order sum of column q of the CTAs' partial rows
+__device__ __forceinline__ double sum_col(const double* part, int q)
 {
-    for (int q = 0; q < n; ++q) {
-        double s = 0;
-        for (int c = 0; c < kRefitCTAs; ++c) s += part[c * kPartStride + c0 + q];
-        out[q] = s;
-    }
+    double s = 0;
+#pragma unroll 8
+    for (int c = 0; c < kRefitCTAs; ++c) s += part[c * kPartStride + q];
+    return s;
 }
 
 // pass 1: inlier mask of the winning hypothesis, count and coordinate sums
@@ -487,7 +584,7 @@ k_refit_p2(const float4* pts, long long M_cap, const int32_t* dM, const int32_t*
     __shared__ double c5[5];
     if (*best_in < 0) return;
     const long long M = m_count(dM, M_cap);
-    if (threadIdx.x == 0) sum_parts(ws.part, 0, 5, c5);
+    if (threadIdx.x < 5) c5[threadIdx.x] = sum_col(ws.part, threadIdx.x);
     __syncthreads();
     const double n = c5[0];
     const double cxa = c5[1] / n, cya = c5[2] / n, cxb = c5[3] / n, cyb = c5[4] / n;
@@ -504,10 +601,10 @@ k_refit_p2(const float4* pts, long long M_cap, const int32_t* dM, const int32_t*
     if (threadIdx.x < 2) ws.part[blockIdx.x * kPartStride + 5 + threadIdx.x] = tot[threadIdx.x];
 }
 
-__device__ void norms_from_parts(const double* part, Norm2D& na, Norm2D& nb, double& n, bool& good)
+// Hartley normalisations of the inliers from the summed columns 0..6
+// (count, coordinate sums, distance sums)
+__device__ void norms_from_sums(const double* c7, Norm2D& na, Norm2D& nb, double& n, bool& good)
 {
-    double c7[7];
-    sum_parts(part, 0, 7, c7);
     n = c7[0];
     const double cxa = c7[1] / n, cya = c7[2] / n, cxb = c7[3] / n, cyb = c7[4] / n;
     const double da = c7[5] / n, db = c7[6] / n;
@@ -524,14 +621,17 @@ k_refit_p3(const float4* pts, long long M_cap, const int32_t* dM, const int32_t*
     __shared__ double part[kRefitWarps][45];
     __shared__ double tot[45];
     __shared__ double nrm[6];
+    __shared__ double c7[7];
     __shared__ int good_s;
     if (*best_in < 0) return;
     const long long M = m_count(dM, M_cap);
+    if (threadIdx.x < 7) c7[threadIdx.x] = sum_col(ws.part, threadIdx.x);
+    __syncthreads();
     if (threadIdx.x == 0) {
         Norm2D na, nb;
         double n;
         bool good;
-        norms_from_parts(ws.part, na, nb, n, good);
+        norms_from_sums(c7, na, nb, n, good);
         nrm[0] = na.s; nrm[1] = na.cx; nrm[2] = na.cy; nrm[3] = nb.s; nrm[4] = nb.cx; nrm[5] = nb.cy;
         good_s = good;
     }
@@ -561,91 +661,105 @@ k_refit_p3(const float4* pts, long long M_cap, const int32_t* dM, const int32_t*
     if (threadIdx.x < 45) ws.part[blockIdx.x * kPartStride + 8 + threadIdx.x] = tot[threadIdx.x];
 }
 
-// Smallest eigenvector of the symmetric positive semi-definite 9x9 matrix S by
-// shifted inverse iteration: Cholesky of S + mu I (mu = 1e-12 trace S), then
-// repeated solves.  The shift keeps the factorisation positive definite for
-// exact data and leaves the eigenvectors unchanged.  Returns false if the
-// factorisation fails.
-__device__ bool smallest_eigvec9(const double (*S)[9], double* h)
-{
-    double L[9][9];
-    double tr = 0;
-    for (int i = 0; i < 9; ++i) tr += S[i][i];
-    const double mu = 1e-12 * tr;
-    double inv_d[9];
-    for (int j = 0; j < 9; ++j) {
-        double d = S[j][j] + mu;
-        for (int k = 0; k < j; ++k) d -= L[j][k] * L[j][k];
-        if (!(d > 0)) return false;
-        L[j][j] = sqrt(d);
-        inv_d[j] = 1.0 / L[j][j];
-        for (int i = j + 1; i < 9; ++i) {
-            double sum = S[i][j];
-            for (int k = 0; k < j; ++k) sum -= L[i][k] * L[j][k];
-            L[i][j] = sum * inv_d[j];
-        }
-    }
-    double x[9];
-    for (int i = 0; i < 9; ++i) x[i] = 1.0;
-    for (int it = 0; it < 24; ++it) {
-        double y[9];
-        for (int i = 0; i < 9; ++i) {   // L y = x
-            double sum = x[i];
-            for (int k = 0; k < i; ++k) sum -= L[i][k] * y[k];
-            y[i] = sum * inv_d[i];
-        }
-        double z[9];
-        for (int i = 8; i >= 0; --i) {  // L^T z = y
-            double sum = y[i];
-            for (int k = i + 1; k < 9; ++k) sum -= L[k][i] * z[k];
-            z[i] = sum * inv_d[i];
-        }
-        double nz = 0;
-        for (int i = 0; i < 9; ++i) nz += z[i] * z[i];
-        const double inv = 1.0 / sqrt(nz);
-        double diff = 0;
-        // align the sign with the previous iterate before comparing
-        double dot = 0;
-        for (int i = 0; i < 9; ++i) dot += z[i] * x[i];
-        const double sg = dot < 0 ? -inv : inv;
-        for (int i = 0; i < 9; ++i) {
-            const double xn = z[i] * sg;
-            diff = fmax(diff, fabs(xn - x[i]));
-            x[i] = xn;
-        }
-        if (it >= 2 && diff < 1e-15) break;
-    }
-    for (int i = 0; i < 9; ++i) h[i] = x[i];
-    return true;
-}
+// Smallest eigenvector of the symmetric positive semi-definite 9x9 normal
+// matrix S (upper triangle in the summed columns 8..52) by shifted inverse
+// iteration: Cholesky of S + mu I (mu = 1e-12 trace S), then repeated pairs of
+// triangular solves.  The shift keeps the factorisation positive definite for
+// exact data and leaves the eigenvectors unchanged.  One warp; lane i owns row
+// i of L and component i of the iterate.
+constexpr int kSolveThreads = 64;
 
-__global__ void k_refit_solve(const double* Hs, const int32_t* best_in, RefitWS ws, double* Hout, int32_t* n_in,
-                              int32_t* best_t)
+__global__ void __launch_bounds__(kSolveThreads)
+k_refit_solve(const double* Hs, const int32_t* best_in, RefitWS ws, double* Hout, int32_t* n_in, int32_t* best_t)
 {
-    if (threadIdx.x != 0) return;
+    __shared__ double col[56];
+    __shared__ double L[9][10];
+    __shared__ double invd[9];
+    const int tid = threadIdx.x, lane = tid & 31;
     const int best = *best_in;
-    if (best_t) *best_t = best;
-    *n_in = 0;
     if (best < 0) {
-        for (int i = 0; i < 9; ++i) { Hout[i] = 0.0; ws.Hf[i] = 0.0; }
+        if (tid == 0) {
+            if (best_t) *best_t = best;
+            *n_in = 0;
+        }
+        if (tid < 9) { Hout[tid] = 0.0; ws.Hf[tid] = 0.0; }
         return;
     }
+    if (tid < 7) col[tid] = sum_col(ws.part, tid);
+    if (tid >= 8 && tid < 53) col[tid] = sum_col(ws.part, tid);
+    __syncthreads();
+    if (tid >= 32) return;
     Norm2D na, nb;
     double n;
     bool good;
-    norms_from_parts(ws.part, na, nb, n, good);
-    double H[9];
+    norms_from_sums(col, na, nb, n, good);
+    // S[j][k] for k >= j sits in column 8 + (upper-triangle position of (j, k))
+    auto S = [&](int j, int k) {
+        if (k < j) { const int x = j; j = k; k = x; }
+        return col[8 + j * 9 - (j * (j - 1)) / 2 + (k - j)];
+    };
     bool ok = good;
-    if (ok) {
-        double t[45];
-        sum_parts(ws.part, 8, 45, t);
-        double S[9][9];
-        int q = 0;
-        for (int j = 0; j < 9; ++j)
-            for (int k = j; k < 9; ++k) { S[j][k] = t[q]; S[k][j] = t[q]; ++q; }
-        double h[9];
-        ok = smallest_eigvec9(S, h) && denorm(na, nb, h, H);
+    double tr = 0;
+    for (int i = 0; i < 9; ++i) tr += S(i, i);
+    const double mu = 1e-12 * tr;
+    for (int j = 0; j < 9 && ok; ++j) {
+        if (lane == j) {
+            double d = S(j, j) + mu;
+            for (int k = 0; k < j; ++k) d -= L[j][k] * L[j][k];
+            L[j][j] = d > 0 ? sqrt(d) : 0.0;
+            invd[j] = d > 0 ? 1.0 / L[j][j] : 0.0;
+        }
+        __syncwarp();
+        ok = invd[j] != 0.0;
+        if (ok && lane > j && lane < 9) {
+            double sum = S(lane, j);
+            for (int k = 0; k < j; ++k) sum -= L[lane][k] * L[j][k];
+            L[lane][j] = sum * invd[j];
+        }
+        __syncwarp();
     }
+    double x = 1.0;   // lane i < 9: component i of the iterate
+    if (ok) {
+        for (int it = 0; it < 24; ++it) {
+            double rr = x;   // L y = x, columns in order
+            double y = 0.0;
+            for (int k = 0; k < 9; ++k) {
+                const double yk = __shfl_sync(0xFFFFFFFFu, rr * (lane < 9 ? invd[lane < 9 ? lane : 0] : 0.0), k);
+                if (lane == k) y = yk;
+                if (lane > k && lane < 9) rr -= L[lane][k] * yk;
+            }
+            double r2 = y;   // L^T z = y, columns from the last
+            double z = 0.0;
+            for (int k = 8; k >= 0; --k) {
+                const double zk = __shfl_sync(0xFFFFFFFFu, r2 * (lane < 9 ? invd[lane < 9 ? lane : 0] : 0.0), k);
+                if (lane == k) z = zk;
+                if (lane < k) r2 -= L[k][lane] * zk;
+            }
+            if (lane >= 9) z = 0.0;
+            double nz = z * z, dot = z * x;
+#pragma unroll
+            for (int o = 16; o; o >>= 1) {
+                nz += __shfl_xor_sync(0xFFFFFFFFu, nz, o);
+                dot += __shfl_xor_sync(0xFFFFFFFFu, dot, o);
+            }
+            // align the sign with the previous iterate before comparing
+            const double sg = (dot < 0 ? -1.0 : 1.0) / sqrt(nz);
+            const double xn = lane < 9 ? z * sg : 1.0;
+            double diff = fabs(xn - x);
+#pragma unroll
+            for (int o = 16; o; o >>= 1) diff = fmax(diff, __shfl_xor_sync(0xFFFFFFFFu, diff, o));
+            x = xn;
+            if (it >= 2 && diff < 1e-15) break;
+        }
+    }
+    double h[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) h[i] = __shfl_sync(0xFFFFFFFFu, x, i);
+    if (lane != 0) return;
+    if (best_t) *best_t = best;
+    *n_in = 0;
+    double H[9];
+    ok = ok && denorm(na, nb, h, H);
     for (int i = 0; i < 9; ++i) {
         const double v = ok ? H[i] : Hs[9ll * best + i];
         ws.Hf[i] = v;
@@ -685,10 +799,15 @@ k_refit_final(const float4* pts, long long M_cap, const int32_t* dM, RefitWS ws,
 
 }  // namespace
 
+size_t compact_workspace(int64_t NA) { return sizeof(int32_t) * (size_t)((NA + kCompactRows - 1) / kCompactRows + 1); }
+
 cudaError_t launch_compact(const uint32_t* kpA, int WA, const uint32_t* kpB, int WB, const int32_t* match,
-                           int64_t NA, float* pts, int32_t* rows, int32_t* d_M, cudaStream_t s)
+                           int64_t NA, float* pts, int32_t* rows, int32_t* d_M, int32_t* tile_cnt, cudaStream_t s)
 {
-    k_compact<<<1, kCompactThreads, 0, s>>>(kpA, WA, kpB, WB, match, NA, reinterpret_cast<float4*>(pts), rows, d_M);
+    const unsigned tiles = (unsigned)std::max<long long>(1, (NA + kCompactRows - 1) / kCompactRows);
+    k_compact_count<<<tiles, kCompactThreads, 0, s>>>(match, NA, tile_cnt);
+    k_compact_write<<<tiles, kCompactThreads, 0, s>>>(kpA, WA, kpB, WB, match, NA, tile_cnt,
+                                                      reinterpret_cast<float4*>(pts), rows, d_M);
     return cudaGetLastError();
 }
 
@@ -711,7 +830,7 @@ RansacWS carve(void* ws, int Ttot)
     r.lo = reinterpret_cast<int32_t*>(r.Hs + 9ll * Ttot);
     r.hi = r.lo + Ttot;
     r.flags = r.hi + Ttot;
-    r.hok = reinterpret_cast<int8_t*>(r.flags + 4);
+    r.hok = reinterpret_cast<int8_t*>(r.flags + kFlagWords);
     r.rw.part = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(r.hok + Ttot) + 255) & ~uintptr_t(255));
     r.rw.Hf = r.rw.part + kRefitCTAs * kPartStride + 1;
     return r;
@@ -723,7 +842,7 @@ void refit_launch(const float4* p4, int64_t M_cap, const int32_t* d_M, double t2
     k_refit_p1<<<kRefitCTAs, kRefitThreads, 0, s>>>(p4, M_cap, d_M, w.Hs, w.flags, t2, inlier, w.rw);
     k_refit_p2<<<kRefitCTAs, kRefitThreads, 0, s>>>(p4, M_cap, d_M, w.flags, inlier, w.rw);
     k_refit_p3<<<kRefitCTAs, kRefitThreads, 0, s>>>(p4, M_cap, d_M, w.flags, inlier, w.rw);
-    k_refit_solve<<<1, 32, 0, s>>>(w.Hs, w.flags, w.rw, H, n_in, best_t);
+    k_refit_solve<<<1, kSolveThreads, 0, s>>>(w.Hs, w.flags, w.rw, H, n_in, best_t);
     const unsigned gfin = (unsigned)std::max<long long>(1, std::min<long long>(kRefitCTAs, (M_cap + 1023) / 1024));
     k_refit_final<<<gfin, kRefitThreads, 0, s>>>(p4, M_cap, d_M, w.rw, t2, inlier, n_in);
 }
@@ -734,12 +853,14 @@ void hyp_batch(const float4* p4, int64_t M_cap, const int32_t* d_M, const unsign
                int t_off, uint32_t k0, uint32_t k1, float t2f, float eps, double t2, const int32_t* skip,
                const RansacWS& w, cudaStream_t s)
 {
-    k_ransac_hyp<<<(T + 15) / 16, 16, 0, s>>>(p4, M_cap, d_M, T, k0, k1, prefix, skip, w.Hs + 9ll * t_off,
-                                              w.hok + t_off);
+    const unsigned gh = (unsigned)((8ll * T + kHypThreads - 1) / kHypThreads);
+    k_ransac_hyp<<<gh, kHypThreads, 0, s>>>(p4, M_cap, d_M, T, k0, k1, prefix, skip, w.Hs + 9ll * t_off,
+                                            w.hok + t_off, w.flags);
     k_ransac_score<<<T, kScoreThreads, 0, s>>>(p4, M_cap, d_M, w.Hs + 9ll * t_off, w.hok + t_off, t2f, eps, skip,
-                                               w.lo + t_off, w.hi + t_off);
-    k_ransac_select<<<1, kSelThreads, 0, s>>>(p4, M_cap, d_M, T, w.Hs + 9ll * t_off, w.lo + t_off, w.hi + t_off, t2,
-                                              skip, t_off, w.flags);
+                                               w.lo + t_off, w.hi + t_off, w.flags);
+    k_ransac_recount<<<T, kRecountThreads, 0, s>>>(p4, M_cap, d_M, w.Hs + 9ll * t_off, w.lo + t_off, w.hi + t_off,
+                                                   w.flags, t2f, eps, t2, skip);
+    k_ransac_argmax<<<1, kSelThreads, 0, s>>>(w.hi + t_off, T, skip, t_off, w.flags);
 }
 
 }  // namespace
@@ -787,10 +908,10 @@ cudaError_t launch_ransac_prior(const float* pts, int64_t M_cap, const int32_t* 
     const float eps = fmaxf(0.05f, 0.01f * t2f);
     hyp_batch(p4, M_cap, d_M, prefix, Tg, 0, k0, k1, t2f, eps, t2, nullptr, w, s);
     k_guided_decide<<<1, kSelThreads, 0, s>>>(p4, M_cap, d_M, w.Hs, prefix, Tg, T, t2, w.flags);
-    hyp_batch(p4, M_cap, d_M, nullptr, T, Tg, k0, k1, t2f, eps, t2, w.flags + 2, w, s);
+    hyp_batch(p4, M_cap, d_M, nullptr, T, Tg, k0, k1, t2f, eps, t2, w.flags + kFlagStop, w, s);
     refit_launch(p4, M_cap, d_M, t2, w, H, inlier, n_in, best_t, s);
     if (iters) {
-        cudaError_t e = cudaMemcpyAsync(iters, w.flags + 3, sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
+        cudaError_t e = cudaMemcpyAsync(iters, w.flags + kFlagIters, sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
         if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();

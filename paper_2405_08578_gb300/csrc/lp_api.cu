@@ -22,7 +22,7 @@ enum BufId {
     B_IMG_A, B_IMG_B, B_GRAY_A, B_GRAY_B, B_KP_A, B_KP_B, B_ORI_A, B_ORI_B,
     B_DESC_A, B_DESC_B, B_D16_A, B_D16_B, B_VAL_A, B_VAL_B,
     B_MATCH, B_D1, B_D2, B_PTS, B_M, B_INL, B_H, B_NIN, B_BEST, B_LUTS, B_BATCH, B_PREFIX,
-    B_ROWS, B_FEAT, B_PROB,
+    B_ROWS, B_FEAT, B_PROB, B_COMPACT,
     B_COUNT
 };
 
@@ -341,8 +341,11 @@ int lp_compact(lp_ctx* c, const uint32_t* kpA, int WA, const uint32_t* kpB, int 
     if (NA < 0 || WA <= 0 || WB <= 0) return fail(c, LP_ERR_ARG, "bad sizes");
     if (!d_M || (NA > 0 && (!kpA || !kpB || !match || !pts))) return fail(c, LP_ERR_ARG, "null argument");
     if (pts && !aligned(pts, 16)) return fail(c, LP_ERR_ALIGN, "pts must be 16-byte aligned");
+    int r = ensure(c, B_COMPACT, lp::compact_workspace(NA));
+    if (r) return r;
     c->last = S(stream);
-    LP_CUDA(c, lp::launch_compact(kpA, WA, kpB, WB, match, NA, pts, rows, d_M, S(stream)));
+    LP_CUDA(c, lp::launch_compact(kpA, WA, kpB, WB, match, NA, pts, rows, d_M, (int32_t*)c->buf[B_COMPACT].p,
+                                  S(stream)));
     return LP_OK;
 }
 
@@ -546,6 +549,7 @@ int lp_stitch_pairs(lp_ctx* c, const lp_image* imgs, int N, const int32_t* pairs
     }
     const int Ttot = c->cfg.ransac_iters + (guided ? c->guided_iters : 0);
     if ((r = ensure(c, B_MATCH_WS, mws)) || (r = ensure(c, B_RANSAC_WS, lp::ransac_workspace(Kmax, Ttot))) ||
+        (r = ensure(c, B_COMPACT, lp::compact_workspace(Kmax))) ||
         (guided && (r = ensure(c, B_PREFIX, sizeof(unsigned long long) * (size_t)(Kmax + 1)))))
         return r;
     cudaStream_t s = S(stream);
@@ -558,7 +562,8 @@ int lp_stitch_pairs(lp_ctx* c, const lp_image* imgs, int N, const int32_t* pairs
                                   (long long)(uintptr_t)c->buf[B_BATCH].p, (long long)(uintptr_t)c->buf[B_MATCH_WS].p,
                                   (long long)(uintptr_t)c->buf[B_RANSAC_WS].p,
                                   (long long)(uintptr_t)c->proposal, c->guided_iters,
-                                  (long long)(uintptr_t)c->buf[B_PREFIX].p};
+                                  (long long)(uintptr_t)c->buf[B_PREFIX].p,
+                                  (long long)(uintptr_t)c->buf[B_COMPACT].p};
     for (int i = 0; i < N; ++i) {
         key.push_back((long long)(uintptr_t)imgs[i].data);
         key.push_back(imgs[i].H); key.push_back(imgs[i].W); key.push_back(imgs[i].pitch);

@@ -60,8 +60,9 @@ cudaError_t launch_match_bf16(const MatchArgs& a, void* ws, size_t ws_bytes, int
 int64_t match_bf16_rescans(const void* ws, int64_t NA, int64_t NB, int num_sms, cudaStream_t s);
 
 // k_ransac.cu
+size_t compact_workspace(int64_t NA);
 cudaError_t launch_compact(const uint32_t* kpA, int WA, const uint32_t* kpB, int WB, const int32_t* match,
-                           int64_t NA, float* pts, int32_t* rows, int32_t* d_M, cudaStream_t s);
+                           int64_t NA, float* pts, int32_t* rows, int32_t* d_M, int32_t* tile_cnt, cudaStream_t s);
 size_t ransac_workspace(int64_t M_cap, int Ttot);
 cudaError_t launch_ransac(const float* pts, int64_t M_cap, const int32_t* d_M, int T, float thresh,
                           uint64_t seed, uint32_t pair_id, double* H, uint8_t* inlier, int32_t* n_in,
