@@ -5,31 +5,36 @@
 // Stage 1, k_match_tc (persistent, one CTA per SM, 10 warps):
 //   warp 0    TMA producer: per work unit a 256-row A block (2 x 32 KB boxes,
 //             128-byte swizzle), then 128-row B tiles (2 x 16 KB boxes) into a
-//             4-stage ring.
+//             3-stage ring.
 //   warp 1    allocates all 512 TMEM columns; one lane issues
 //             tcgen05.mma.cta_group::1.kind::f16 (M = 128, N = 128, K = 16,
 //             BF16 x BF16 -> FP32): 2 row blocks x 8 K-steps per B tile, into
 //             one of two TMEM accumulator buffers; tcgen05.commit releases the
 //             B stage and hands the buffer to the epilogue.
 //   warps 2-9 epilogue: each thread owns one A row, reads its 128 FP32 dot
-//             products per tile with tcgen05.ld (32x32b.x32), forms
-//             v = |b~|^2 - 2 a~.b~ and keeps the row's 8 smallest v in
-//             registers; no distance matrix is written.
+//             products per tile with tcgen05.ld (32x32b.x32) and forms
+//             v = |b~|^2 - 2 a~.b~.  Per 32-column chunk it takes the minimum
+//             (three-input min tree) and keeps the row's two smallest chunk
+//             minima m1 <= m2; columns with v <= m2 + 2 delta go into the row's
+//             candidate buffer in shared memory.  No distance matrix is
+//             written; a split's output is its candidates (at most 8) and its
+//             own two smallest chunk minima.
 //   A work unit is (256-row block of A, one of S column splits of B); units
 //   are dealt round-robin to the persistent CTAs.  Every mbarrier wait is
 //   bounded by a 2 s clock limit; on expiry the CTA records LP_ERR_TIMEOUT,
 //   drains, frees its TMEM and returns.
 //
-// Stage 2, k_rerank (one warp per row): candidates whose BF16 value lies
-//   within 2*delta of the row's second-smallest BF16 value are re-scored
-//   with exactly the FP32 form's arithmetic (sequential FMA over k, then
-//   fma(-2, dot, |b|^2)), so their values are bit-identical to the FP32
-//   form's.  With unit, non-negative descriptors and BF16 unit roundoff
-//   u = 2^-8, |v~_j - v_j| <= 3u + 3u^2 + 1.1e-4 = delta for every column j
-//   (derivation in the design doc).  The row is certified when the smallest
-//   eighth-best BF16 value over the splits, minus delta, exceeds the exact
-//   second-best: then no column outside the candidates can enter the top 2.
-//   Uncertified rows are queued.
+// Stage 2, k_rerank (one warp per row): candidates within 2*delta of m2 (the
+//   second-smallest chunk minimum over all splits) are re-scored with exactly
+//   the FP32 form's arithmetic (sequential FMA over k, then
+//   fma(-2, dot, |b|^2)), so their values are bit-identical to the FP32 form's.
+//   With unit, non-negative descriptors and BF16 unit roundoff u = 2^-8,
+//   |v~_j - v_j| <= 3u + 3u^2 + 1.1e-4 = delta for every column j.  m2 is at
+//   least the row's second-smallest BF16 value B, and every column with
+//   v~ <= B + 2 delta is a candidate, so every other column has v > B + delta,
+//   which is at least the exact second-best: the exact top 2 are found among
+//   the candidates.  A row whose candidate buffer overflowed in some split is
+//   queued.
 // Stage 3: queued rows are re-scanned with the FP32 form's arithmetic.
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -52,15 +57,27 @@ constexpr int kThreadsTC = 320;         // 10 warps
 constexpr int kEpiWarps = 8;
 constexpr uint32_t kABytes = kRowsPerUnit * 128 * 2;   // 64 KB
 constexpr uint32_t kBBytes = kTileN * 128 * 2;         // 32 KB per stage
-constexpr uint32_t kNbBytes = kEpiWarps * kTileN * 4;   // per-warp copy of one tile's |b~|^2
-constexpr uint32_t kSmemTC = kABytes + kStages * kBBytes + kNbBytes + 1024 /*barriers*/ + 1024 /*align slack*/;
-constexpr int kTopK = 8;
+// Ninth K-step: A rows extended by (1, 1, 1, 0, ..., 0), B rows by
+// (-h1, -h2, -h3, 0, ..., 0) with h1 + h2 + h3 = |b~|^2 / 2 (three BF16 terms),
+// so the accumulator holds D = a~.b~ - |b~|^2 / 2 = -v / 2.  16 BF16 per
+// extension row, 32-byte swizzle.
+constexpr uint32_t kExtRowBytes = 32;
+constexpr uint32_t kAExtBytes = kRowsPerUnit * kExtRowBytes;   // 8 KB, loaded once
+constexpr uint32_t kBExtBytes = kTileN * kExtRowBytes;         // 4 KB per stage
+constexpr uint32_t kSmemTC =
+    kABytes + kStages * kBBytes + kAExtBytes + kStages * kBExtBytes + 1024 /*barriers*/ + 1024 /*align slack*/;
+constexpr int kCandCapacity = 32;                      // pass-2 candidates kept per row
+// largest value a candidate may have: invalid columns (kNoColumn) never qualify
+constexpr float kCandCap = 1.0e38f;
+// margin of the candidate window above m2 + delta (about five standard
+// deviations of the BF16 rounding error of a value); a row whose exact
+// second-best exceeds m2 + kMargin is not certified and is re-scanned
+constexpr float kMargin = 4.0e-3f;
 // |b~|^2 of an invalid or masked column: finite (so that the column tag below
 // never turns it into a NaN) and far above any real value; treated as +inf by
 // the re-rank.
 constexpr float kNoColumn = 3.0e38f;
-// 3u + 3u^2 (BF16 rounding) + FP32 accumulation allowance + the column tag
-// that the epilogue writes into the 5 low mantissa bits (<= 31 ulp)
+// 3u + 3u^2 (BF16 rounding) + FP32 accumulation allowance (+ 1e-5 margin)
 constexpr float kDelta = 3.0f / 256.0f + 3.0f / 65536.0f + 1e-4f + 1e-5f;
 
 // ------------------------------------------------------------------ PTX wrappers
@@ -149,6 +166,19 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr)
     return d;
 }
 
+// The same for the 32-byte-swizzled extension tiles: 8-row atoms of 32 B
+// stacked every 256 B, swizzle mode 6 (32 B).
+__device__ __forceinline__ uint64_t sdesc32(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)(16u >> 4) << 16;
+    d |= (uint64_t)(256u >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)6 << 61;
+    return d;
+}
+
 // Instruction descriptor, kind::f16: D = FP32, A = B = BF16, both K-major,
 // N = 128, M = 128.
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTileN >> 3) << 17) | ((128u >> 4) << 24);
@@ -206,9 +236,10 @@ struct TcParams {
     int nrp;               // number of 256-row blocks
     int S;                 // column splits
     long long cps;         // columns per split (multiple of kTileN)
-    const float* nb16;     // |b~_j|^2 (+inf when invalid), length NB
-    float4* pv;            // [S][NA][2] the kTopK smallest values
-    int4* pj;              // [S][NA][2] their columns (-1 = none)
+    float2* pm;            // pass 1 output [S][NA]: the split's two smallest chunk minima
+    const float* thr;      // pass 2 input [NA]: candidate threshold per row (-inf: none)
+    int32_t* cand;         // pass 2 output [NA][kCandCapacity]: candidate columns (unordered)
+    int32_t* ncand;        // [NA]: candidates found (may exceed the capacity)
     int32_t* status;
 };
 
@@ -226,43 +257,37 @@ __device__ __forceinline__ void unit_range(const TcParams& p, int u, int& rp, in
     ntiles = c1 > c0 ? (int)((c1 - c0 + kTileN - 1) / kTileN) : 0;
 }
 
-// Sorted top-k (ascending) in registers; every index is a compile-time
-// constant after unrolling.
-struct TopK {
-    float v[kTopK];
-    int j[kTopK];
-};
-
-__device__ __forceinline__ void topk_insert(TopK& t, float x, int jx)
+__device__ __forceinline__ float max3f(float a, float b, float c)
 {
-    bool c[kTopK];
-#pragma unroll
-    for (int i = 0; i < kTopK; ++i) c[i] = x < t.v[i];
-#pragma unroll
-    for (int i = kTopK - 1; i > 0; --i) {
-        t.v[i] = c[i - 1] ? t.v[i - 1] : (c[i] ? x : t.v[i]);
-        t.j[i] = c[i - 1] ? t.j[i - 1] : (c[i] ? jx : t.j[i]);
-    }
-    t.v[0] = c[0] ? x : t.v[0];
-    t.j[0] = c[0] ? jx : t.j[0];
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
 }
 
-// v with its 5 low mantissa bits replaced by the column's position i in the
-// chunk: the chunk minimum then also names its column.
-__device__ __forceinline__ float tag(float v, int i)
+// Append up to 4 register-held candidate columns to the row's list.
+__device__ __noinline__ void flush_cands(int32_t* ncand, int32_t* cand, long long row, int nc, int c0, int c1, int c2,
+                                         int c3)
 {
-    return __uint_as_float((__float_as_uint(v) & ~31u) | (uint32_t)i);
+    const int b0 = atomicAdd(ncand + row, nc);
+    int32_t* dst = cand + row * kCandCapacity;
+    if (b0 + 0 < kCandCapacity) dst[b0 + 0] = c0;
+    if (nc > 1 && b0 + 1 < kCandCapacity) dst[b0 + 1] = c1;
+    if (nc > 2 && b0 + 2 < kCandCapacity) dst[b0 + 2] = c2;
+    if (nc > 3 && b0 + 3 < kCandCapacity) dst[b0 + 3] = c3;
 }
 
+template <int kPass>
 __global__ void __launch_bounds__(kThreadsTC, 1)
-k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcParams p)
+k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+           const __grid_constant__ CUtensorMap tmAx, const __grid_constant__ CUtensorMap tmBx, const TcParams p)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t* sA = smem;
     uint8_t* sB = smem + kABytes;
-    float* snb = reinterpret_cast<float*>(smem + kABytes + kStages * kBBytes);   // [kEpiWarps][kTileN]
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kABytes + kStages * kBBytes + kNbBytes);
+    uint8_t* sAx = smem + kABytes + kStages * kBBytes;   // A extension, 2 x 128 rows
+    uint8_t* sBx = sAx + kAExtBytes;                     // B extension per stage
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sBx + kStages * kBExtBytes);
     // barrier slots
     uint64_t* full = bars;                 // [kStages]
     uint64_t* empty = bars + kStages;      // [kStages]
@@ -296,6 +321,8 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         tma_prefetch_desc(&tmA);
         tma_prefetch_desc(&tmB);
+        tma_prefetch_desc(&tmAx);
+        tma_prefetch_desc(&tmBx);
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tmem_slot))
@@ -325,9 +352,10 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
                 if (rp != prev_rp) {
                     ok = mbar_wait(smem_u32(aempty), (v & 1) ^ 1, abort_flag, p.status);
                     if (!ok) break;
-                    mbar_expect_tx(smem_u32(afull), kABytes);
+                    mbar_expect_tx(smem_u32(afull), kABytes + (v == 0 ? kAExtBytes : 0u));
                     tma_load_2d(smem_u32(sA), &tmA, 0, rp * kRowsPerUnit, smem_u32(afull));
                     tma_load_2d(smem_u32(sA + kABytes / 2), &tmA, 64, rp * kRowsPerUnit, smem_u32(afull));
+                    if (v == 0) tma_load_2d(smem_u32(sAx), &tmAx, 0, 0, smem_u32(afull));   // constant rows
                     a_armed = v;
                     ++v;
                     prev_rp = rp;
@@ -339,9 +367,10 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
                     if (!ok) break;
                     uint8_t* dst = sB + s * kBBytes;
                     const int y = (int)(c0 + (long long)t * kTileN);
-                    mbar_expect_tx(smem_u32(&full[s]), kBBytes);
+                    mbar_expect_tx(smem_u32(&full[s]), kBBytes + kBExtBytes);
                     tma_load_2d(smem_u32(dst), &tmB, 0, y, smem_u32(&full[s]));
                     tma_load_2d(smem_u32(dst + kBBytes / 2), &tmB, 64, y, smem_u32(&full[s]));
+                    tma_load_2d(smem_u32(sBx + s * kBExtBytes), &tmBx, 0, y, smem_u32(&full[s]));
                     armed[s] = (int)k;
                 }
             }
@@ -405,6 +434,8 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
                                 const uint64_t bd = sdesc(bbase + h * (kBBytes / 2) + kk * 32);
                                 mma_bf16(d, ad, bd, (h | kk) ? 1u : 0u);
                             }
+                        mma_bf16(d, sdesc32(smem_u32(sAx) + rb * 128 * kExtRowBytes),
+                                 sdesc32(smem_u32(sBx) + s * kBExtBytes), 1u);
                     }
                     mma_commit(smem_u32(&empty[s]));
                     mma_commit(smem_u32(&tfull[b]));
@@ -418,49 +449,31 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
         }
     } else {
         // ---------------------------------------------------------- epilogue
+        // The accumulator holds D = -v / 2: smaller v is larger D.
+        // Pass 1: per (split, row) the two largest chunk maxima of D (a chunk =
+        //   32 columns), which name two different columns; written as v.
+        // Pass 2: every column with v <= T (D >= -T / 2) is a candidate; a
+        //   lane holds up to 4 in registers and appends them to the row's list
+        //   (one atomic slot reservation per flush).
         const int q = warp & 3;                 // TMEM lane quarter this warp may access
         const int rb = (warp - 2) >> 2;         // row block 0 (warps 2-5) or 1 (warps 6-9)
         const int row_in_unit = rb * 128 + q * 32 + lane;
         long long n = 0;
         bool ok = true;
-        int prev_rp = -1;
-        float warm = INFINITY;
         for (int u = u_begin; u < u_end && ok; ++u) {
             int rp, split, ntiles;
             long long c0;
             unit_range(p, u, rp, split, c0, ntiles);
             long long c1 = c0 + p.cps;
             if (c1 > p.NB) c1 = p.NB;
-            // a split of the same row block starts from the previous split's
-            // k-th best: placeholders (column -1) at that value.  Columns never
-            // stored are then still >= the list's last value, the bound the
-            // re-rank uses.
-            const float t0 = (rp == prev_rp && ntiles > 0) ? warm : INFINITY;
-            TopK tk;
-#pragma unroll
-            for (int i = 0; i < kTopK; ++i) { tk.v[i] = t0; tk.j[i] = -1; }
-            float* wnb = snb + (warp - 2) * kTileN;
-            // |b~|^2 of tile t, lane l holding columns 4l .. 4l+3 (+inf past the split)
-            auto load_nb = [&](int t) {
-                const long long j = c0 + (long long)t * kTileN + 4 * lane;
-                if (j + 4 <= c1) return __ldg(reinterpret_cast<const float4*>(p.nb16 + j));
-                float4 w;
-                w.x = j + 0 < c1 ? __ldg(p.nb16 + j + 0) : kNoColumn;
-                w.y = j + 1 < c1 ? __ldg(p.nb16 + j + 1) : kNoColumn;
-                w.z = j + 2 < c1 ? __ldg(p.nb16 + j + 2) : kNoColumn;
-                w.w = j + 3 < c1 ? __ldg(p.nb16 + j + 3) : kNoColumn;
-                return w;
-            };
-            float4 nb_next = ntiles > 0 ? load_nb(0) : make_float4(0.f, 0.f, 0.f, 0.f);
+            const long long row = (long long)rp * kRowsPerUnit + row_in_unit;
+            const bool live = row < p.NA;
+            float d1 = -INFINITY, d2 = -INFINITY;                                    // pass 1
+            const float TD = (kPass == 2 && live) ? -0.5f * p.thr[row] : INFINITY;  // pass 2
+            int nc = 0, cj0 = 0, cj1 = 0, cj2 = 0, cj3 = 0;
             for (int t = 0; t < ntiles; ++t, ++n) {
                 const int b = (int)(n & 1);
                 const uint32_t kb = (uint32_t)(n >> 1);
-                // stage this tile's norms, start fetching the next tile's
-                __syncwarp();
-                const float4 nb_cur = nb_next;
-                reinterpret_cast<float4*>(wnb)[lane] = nb_cur;
-                if (t + 1 < ntiles) nb_next = load_nb(t + 1);
-                __syncwarp();
                 ok = mbar_wait(smem_u32(&tfull[b]), kb & 1, abort_flag, p.status);
                 if (!ok) break;
                 tc_fence_after();
@@ -474,36 +487,45 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
                     uint32_t (&cur)[32] = (ch & 1) ? rb2 : ra;
                     uint32_t (&nxt)[32] = (ch & 1) ? ra : rb2;
                     if (ch + 1 < kTileN / 32) tmem_ld32(tbase + (uint32_t)((ch + 1) * 32), nxt);
-                    // tagged v_j = |b~_j|^2 - 2 s_j and the chunk minimum
-                    float kv[32];
-                    const float4* nb4 = reinterpret_cast<const float4*>(wnb + ch * 32);
+                    float dv[32];
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        const float4 w = nb4[i];
-                        kv[4 * i + 0] = tag(fmaf(-2.f, __uint_as_float(cur[4 * i + 0]), w.x), 4 * i + 0);
-                        kv[4 * i + 1] = tag(fmaf(-2.f, __uint_as_float(cur[4 * i + 1]), w.y), 4 * i + 1);
-                        kv[4 * i + 2] = tag(fmaf(-2.f, __uint_as_float(cur[4 * i + 2]), w.z), 4 * i + 2);
-                        kv[4 * i + 3] = tag(fmaf(-2.f, __uint_as_float(cur[4 * i + 3]), w.w), 4 * i + 3);
+                    for (int i = 0; i < 32; ++i) dv[i] = __uint_as_float(cur[i]);
+                    const long long j0 = cbase + ch * 32;
+                    if (j0 + 32 > c1) {   // columns past the split or past NB (zero-filled rows)
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) dv[i] = j0 + i < c1 ? dv[i] : -INFINITY;
                     }
-                    float m16[16];
+                    float gx[4];
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) m16[i] = fminf(kv[i], kv[i + 16]);
+                    for (int g = 0; g < 4; ++g)
+                        gx[g] = max3f(max3f(dv[8 * g + 0], dv[8 * g + 1], dv[8 * g + 2]),
+                                      max3f(dv[8 * g + 3], dv[8 * g + 4], dv[8 * g + 5]),
+                                      fmaxf(dv[8 * g + 6], dv[8 * g + 7]));
+                    const float cmax = max3f(gx[0], gx[1], fmaxf(gx[2], gx[3]));
+                    if (kPass == 1) {
+                        const float lo = fminf(d1, cmax);
+                        d1 = fmaxf(d1, cmax);
+                        d2 = fmaxf(d2, lo);
+                    } else {
+                        const bool trig = cmax >= TD;
+                        if (__any_sync(0xFFFFFFFFu, trig)) {
+                            // bit i: column j0 + i qualifies; then one short loop over the bits
+                            uint32_t m = 0;
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) m16[i] = fminf(m16[i], m16[i + 8]);
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) m16[i] = fminf(m16[i], m16[i + 4]);
-                    float cand = fminf(fminf(m16[0], m16[2]), fminf(m16[1], m16[3]));
-                    // insert this row's qualifying columns, smallest first; the
-                    // loop runs only while some row of the warp still qualifies
-                    bool act = cand < tk.v[kTopK - 1];
-                    const int j0 = (int)(cbase + ch * 32);
-                    while (__any_sync(0xFFFFFFFFu, act)) {
-                        if (act) topk_insert(tk, cand, j0 + (int)(__float_as_uint(cand) & 31u));
-                        float nx = INFINITY;
-#pragma unroll
-                        for (int i = 0; i < 32; ++i) nx = fminf(nx, kv[i] > cand ? kv[i] : INFINITY);
-                        cand = nx;
-                        act = act && cand < tk.v[kTopK - 1];
+                            for (int i = 0; i < 32; ++i) m |= (dv[i] >= TD ? 1u : 0u) << i;
+                            while (m) {
+                                const int j = (int)j0 + __ffs(m) - 1;
+                                m &= m - 1;
+                                cj0 = nc == 0 ? j : cj0;
+                                cj1 = nc == 1 ? j : cj1;
+                                cj2 = nc == 2 ? j : cj2;
+                                cj3 = nc == 3 ? j : cj3;
+                                if (++nc == 4) {
+                                    flush_cands(p.ncand, p.cand, row, 4, cj0, cj1, cj2, cj3);
+                                    nc = 0;
+                                }
+                            }
+                        }
                     }
                     if (ch + 1 < kTileN / 32) tmem_wait(nxt);
                 }
@@ -512,19 +534,8 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
                 if (lane == 0) mbar_arrive(smem_u32(&tempty[b]));
             }
             if (!ok) break;
-            const long long row = (long long)rp * kRowsPerUnit + row_in_unit;
-            if (row < p.NA) {
-                float4* pv = p.pv + ((long long)split * p.NA + row) * 2;
-                int4* pj = p.pj + ((long long)split * p.NA + row) * 2;
-                pv[0] = make_float4(tk.v[0], tk.v[1], tk.v[2], tk.v[3]);
-                pv[1] = make_float4(tk.v[4], tk.v[5], tk.v[6], tk.v[7]);
-                pj[0] = make_int4(tk.j[0], tk.j[1], tk.j[2], tk.j[3]);
-                pj[1] = make_int4(tk.j[4], tk.j[5], tk.j[6], tk.j[7]);
-            }
-            if (ntiles > 0) {
-                prev_rp = rp;
-                warm = tk.v[kTopK - 1];
-            }
+            if (kPass == 1 && live) p.pm[(long long)split * p.NA + row] = make_float2(-2.f * d1, -2.f * d2);
+            if (kPass == 2 && nc > 0) flush_cands(p.ncand, p.cand, row, nc, cj0, cj1, cj2, cj3);
         }
     }
     tc_fence_before();
@@ -533,20 +544,35 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
     if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
 }
 
-// |b~|^2 of the bf16 rows in FP32 (+inf when invalid).
-__global__ void k_row_norms_bf16(const __nv_bfloat16* d, const uint8_t* v, long long n, float* out)
+// B extension rows: (-h1, -h2, -h3, 0 x 13) with h1 + h2 + h3 = |b~|^2 / 2 to
+// within 2^-24 relative (|b~|^2 in FP32 from the BF16 row; kNoColumn / 2 for
+// an invalid row), and the constant A extension rows (1, 1, 1, 0 x 13).
+__global__ void k_ext_rows(const __nv_bfloat16* d, const uint8_t* v, long long n, __nv_bfloat16* bext,
+                           __nv_bfloat16* aext)
 {
     const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
+    if (blockIdx.x == 0 && threadIdx.x < kRowsPerUnit) {
+        __nv_bfloat16* r = aext + threadIdx.x * 16;
+        for (int k = 0; k < 16; ++k) r[k] = __float2bfloat16_rn(k < 3 ? 1.f : 0.f);
+    }
     if (w >= n) return;
     const uint2 raw = reinterpret_cast<const uint2*>(d + w * 128)[lane];
     const __nv_bfloat162 lo = *reinterpret_cast<const __nv_bfloat162*>(&raw.x);
     const __nv_bfloat162 hi = *reinterpret_cast<const __nv_bfloat162*>(&raw.y);
     const float2 a = __bfloat1622float2(lo), b = __bfloat1622float2(hi);
-    float s = a.x * a.x + a.y * a.y + b.x * b.x + b.y * b.y;
+    float sq = a.x * a.x + a.y * a.y + b.x * b.x + b.y * b.y;
 #pragma unroll
-    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
-    if (lane == 0) out[w] = v[w] ? s : kNoColumn;
+    for (int o = 16; o; o >>= 1) sq += __shfl_xor_sync(0xFFFFFFFFu, sq, o);
+    if (lane < 16) {
+        const float x = -0.5f * (v[w] ? sq : kNoColumn);
+        const float h1 = __bfloat162float(__float2bfloat16_rn(x));
+        const float r1 = x - h1;
+        const float h2 = __bfloat162float(__float2bfloat16_rn(r1));
+        const float h3 = r1 - h2;
+        const float e = lane == 0 ? h1 : lane == 1 ? h2 : lane == 2 ? h3 : 0.f;
+        bext[w * 16 + lane] = __float2bfloat16_rn(e);
+    }
 }
 
 // ------------------------------------------------------------------ re-rank
@@ -568,7 +594,6 @@ __device__ __forceinline__ float fp32_form_value(const float* a, const float* b,
 }
 
 constexpr int kRerankWarps = 8;
-constexpr int kMaxCand = 32 * kTopK;   // S <= 32 splits of kTopK candidates
 
 __device__ __forceinline__ void top2_lex(float& b1, int& j1, float& b2, int& j2, float x, int j)
 {
@@ -591,15 +616,38 @@ __device__ __forceinline__ void warp_top2(float& b1, int& j1, float& b2, int& j2
     }
 }
 
-// One warp per row.  The candidates of all splits whose BF16 value lies in the
-// window are pooled in shared memory and re-scored one per lane, so the row
-// costs about one FP32-form evaluation whatever the split they came from.
+// Candidate threshold per row from the pass-1 pairs: m2 = the second-smallest
+// of all splits' chunk minima names a column other than the row's BF16
+// minimum, so m2 >= B, the row's second-smallest BF16 value.  The threshold
+// is m2 + delta + kMargin (capped below the invalid-column marker), -inf for
+// an invalid query row; the row's candidate counter is cleared.
+__global__ void k_row_threshold(const float2* pm, int S, long long NA, const uint8_t* vA, float delta, float* thr,
+                                int32_t* ncand)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= NA) return;
+    float m1 = INFINITY, m2 = INFINITY;
+    for (int s = 0; s < S; ++s) {
+        const float2 q = pm[(long long)s * NA + i];
+        const float lo = fminf(q.x, q.y), hi = fmaxf(q.x, q.y);
+        m2 = fminf(fminf(m2, hi), fmaxf(m1, lo));
+        m1 = fminf(m1, lo);
+    }
+    thr[i] = vA[i] ? fminf(m2 + delta + kMargin, kCandCap) : -INFINITY;
+    ncand[i] = 0;
+}
+
+// One warp per row, one candidate per lane: exact FP32-form values (the FP32
+// form's own arithmetic), the top 2 by (value, column).  Every column outside
+// the list has a BF16 value > T and so an FP32-form value > T - delta: the
+// row is certified when its exact second-best is < T - delta.  Rows with an
+// overflowed list or without that margin are queued for the FP32 re-scan.
 __global__ void __launch_bounds__(kRerankWarps * 32)
-k_rerank(const float* A, const uint8_t* vA, const float* B, const float* nb32, const float4* pv, const int4* pj, int S,
-         long long NA, float delta, float4* out_part, int32_t* rescan_rows, int32_t* rescan_count)
+k_rerank(const float* A, const uint8_t* vA, const float* B, const float* nb32, const int32_t* cand,
+         const int32_t* ncand, const float* thr, long long NA, float delta, float4* out_part, int32_t* rescan_rows,
+         int32_t* rescan_count)
 {
     __shared__ __align__(16) float qa[kRerankWarps][128];
-    __shared__ int pool[kRerankWarps][kMaxCand];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long i = (long long)blockIdx.x * kRerankWarps + warp;
     if (i >= NA) return;
@@ -607,76 +655,26 @@ k_rerank(const float* A, const uint8_t* vA, const float* B, const float* nb32, c
         if (lane == 0) out_part[i] = make_float4(INFINITY, INFINITY, __int_as_float(-1), __int_as_float(-1));
         return;
     }
-    reinterpret_cast<float4*>(qa[warp])[lane] = reinterpret_cast<const float4*>(A + i * 128)[lane];
-    // lane c holds the kTopK candidates of split c (S <= 32)
-    float cv[kTopK];
-    int cj[kTopK];
-    float t4 = INFINITY;   // smallest k-th best value over the splits
-    if (lane < S) {
-        const float4* v = pv + ((long long)lane * NA + i) * 2;
-        const int4* j = pj + ((long long)lane * NA + i) * 2;
-        const float4 v0 = v[0], v1 = v[1];
-        const int4 j0 = j[0], j1 = j[1];
-        cv[0] = v0.x; cv[1] = v0.y; cv[2] = v0.z; cv[3] = v0.w;
-        cv[4] = v1.x; cv[5] = v1.y; cv[6] = v1.z; cv[7] = v1.w;
-        cj[0] = j0.x; cj[1] = j0.y; cj[2] = j0.z; cj[3] = j0.w;
-        cj[4] = j1.x; cj[5] = j1.y; cj[6] = j1.z; cj[7] = j1.w;
-#pragma unroll
-        for (int k = 0; k < kTopK; ++k)
-            if (cv[k] >= 1.0e38f) { cv[k] = INFINITY; cj[k] = -1; }
-        t4 = cv[kTopK - 1];
-    } else {
-#pragma unroll
-        for (int k = 0; k < kTopK; ++k) { cv[k] = INFINITY; cj[k] = -1; }
-    }
-#pragma unroll
-    for (int o = 16; o; o >>= 1) t4 = fminf(t4, __shfl_xor_sync(0xFFFFFFFFu, t4, o));
-    // second-smallest BF16 value over all candidates
-    float m1 = cv[0], m2 = cv[1];
-#pragma unroll
-    for (int o = 16; o; o >>= 1) {
-        const float o1 = __shfl_xor_sync(0xFFFFFFFFu, m1, o);
-        const float o2 = __shfl_xor_sync(0xFFFFFFFFu, m2, o);
-        const float n1 = fminf(m1, o1);
-        const float n2 = fminf(fmaxf(m1, o1), fminf(m2, o2));
-        m1 = n1;
-        m2 = n2;
-    }
-    const float window = m2 + 2.f * delta;
-    // pool the window's candidates (lane order, then list order)
-    int mine = 0;
-#pragma unroll
-    for (int k = 0; k < kTopK; ++k) mine += (cj[k] >= 0 && cv[k] <= window);
-    int off = mine;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int v = __shfl_up_sync(0xFFFFFFFFu, off, o);
-        if (lane >= o) off += v;
-    }
-    const int n = __shfl_sync(0xFFFFFFFFu, off, 31);
-    off -= mine;
-#pragma unroll
-    for (int k = 0; k < kTopK; ++k)
-        if (cj[k] >= 0 && cv[k] <= window) pool[warp][off++] = cj[k];
-    __syncwarp();
-    // exact FP32-form values, one candidate per lane
+    const int n = ncand[i];
+    const float T = thr[i];
+    bool ok = n <= kCandCapacity;
     float b1 = INFINITY, b2 = INFINITY;
     int j1 = -1, j2 = -1;
-    for (int c = lane; c < n; c += 32) {
-        const int j = pool[warp][c];
-        top2_lex(b1, j1, b2, j2, fp32_form_value(qa[warp], B + (long long)j * 128, __ldg(nb32 + j)), j);
+    if (ok) {
+        reinterpret_cast<float4*>(qa[warp])[lane] = reinterpret_cast<const float4*>(A + i * 128)[lane];
+        __syncwarp();
+        if (lane < n) {
+            const int j = cand[i * kCandCapacity + lane];
+            top2_lex(b1, j1, b2, j2, fp32_form_value(qa[warp], B + (long long)j * 128, __ldg(nb32 + j)), j);
+        }
+        warp_top2(b1, j1, b2, j2);
+        ok = b2 < T - delta;
     }
-    warp_top2(b1, j1, b2, j2);
     if (lane == 0) {
-        // every column outside the candidates has an FP32-form value >= t4 - delta
-        // t4 = inf: no split saw more than kTopK valid columns, so every
-        // column was a candidate
-        const bool certified = isinf(t4) || b2 < t4 - delta;
-        if (certified) {
+        if (ok) {
             out_part[i] = make_float4(b1, b2, __int_as_float(j1), __int_as_float(j2));
         } else {
-            const int slot = atomicAdd(rescan_count, 1);
-            rescan_rows[slot] = (int32_t)i;
+            rescan_rows[atomicAdd(rescan_count, 1)] = (int32_t)i;
         }
     }
 }
@@ -818,6 +816,19 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
     return fn;
 }
 
+bool make_map_ext(CUtensorMap* m, const void* base, long long rows, uint32_t box_rows)
+{
+    auto fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {16, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {32};
+    cuuint32_t box[2] = {16, box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 bool make_map(CUtensorMap* m, const void* base, long long rows, uint32_t box_rows)
 {
     auto fn = encode_fn();
@@ -849,7 +860,8 @@ int pick_tc_splits(int nrp, long long NB, int sms)
 
 struct TcLayout {
     int S;
-    size_t off_nb16, off_na, off_nb32, off_pv, off_pj, off_part1, off_rows, off_cnt, off_part_r, total;
+    size_t off_bext, off_aext, off_na, off_nb32, off_pm, off_thr, off_cand, off_ncand, off_part1, off_rows, off_cnt, off_part_r,
+        total;
 };
 
 TcLayout tc_layout(long long NA, long long NB, int sms)
@@ -859,11 +871,14 @@ TcLayout tc_layout(long long NA, long long NB, int sms)
     L.S = pick_tc_splits(nrp, NB, sms);
     size_t o = 0;
     auto take = [&](size_t bytes) { size_t r = o; o += (bytes + 255) & ~size_t(255); return r; };
-    L.off_nb16 = take(sizeof(float) * (size_t)NB + 64);
+    L.off_bext = take(kExtRowBytes * (size_t)NB + 64);
+    L.off_aext = take(kAExtBytes);
     L.off_na = take(sizeof(float) * (size_t)NA);
     L.off_nb32 = take(sizeof(float) * (size_t)NB);
-    L.off_pv = take(sizeof(float4) * 2 * (size_t)L.S * NA);
-    L.off_pj = take(sizeof(int4) * 2 * (size_t)L.S * NA);
+    L.off_pm = take(sizeof(float2) * (size_t)L.S * NA);
+    L.off_thr = take(sizeof(float) * (size_t)NA);
+    L.off_cand = take(sizeof(int32_t) * kCandCapacity * (size_t)NA);
+    L.off_ncand = take(sizeof(int32_t) * (size_t)NA);
     L.off_part1 = take(sizeof(float4) * (size_t)NA);
     L.off_rows = take(sizeof(int32_t) * (size_t)NA);
     L.off_cnt = take(64);
@@ -893,11 +908,14 @@ cudaError_t launch_match_bf16(const MatchArgs& a, void* ws, size_t ws_bytes, int
     const TcLayout L = tc_layout(a.NA, a.NB, num_sms);
     if (ws_bytes < L.total) return cudaErrorInvalidValue;
     uint8_t* w = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(ws) + 255) & ~uintptr_t(255));
-    float* nb16 = reinterpret_cast<float*>(w + L.off_nb16);
+    __nv_bfloat16* bext = reinterpret_cast<__nv_bfloat16*>(w + L.off_bext);
+    __nv_bfloat16* aext = reinterpret_cast<__nv_bfloat16*>(w + L.off_aext);
     float* na = reinterpret_cast<float*>(w + L.off_na);
     float* nb32 = reinterpret_cast<float*>(w + L.off_nb32);
-    float4* pv = reinterpret_cast<float4*>(w + L.off_pv);
-    int4* pj = reinterpret_cast<int4*>(w + L.off_pj);
+    float2* pm = reinterpret_cast<float2*>(w + L.off_pm);
+    float* thr = reinterpret_cast<float*>(w + L.off_thr);
+    int32_t* cand = reinterpret_cast<int32_t*>(w + L.off_cand);
+    int32_t* ncand = reinterpret_cast<int32_t*>(w + L.off_ncand);
     float4* part1 = reinterpret_cast<float4*>(w + L.off_part1);
     int32_t* rows = reinterpret_cast<int32_t*>(w + L.off_rows);
     int32_t* cnt = reinterpret_cast<int32_t*>(w + L.off_cnt);
@@ -907,10 +925,11 @@ cudaError_t launch_match_bf16(const MatchArgs& a, void* ws, size_t ws_bytes, int
     k_row_norms<<<(unsigned)((a.NA * 32 + 255) / 256), 256, 0, s>>>(a.dA, a.vA, a.NA, na, 0.f);
     if (a.NB > 0) {
         k_row_norms<<<(unsigned)((a.NB * 32 + 255) / 256), 256, 0, s>>>(a.dB, a.vB, a.NB, nb32, INFINITY);
-        k_row_norms_bf16<<<(unsigned)((a.NB * 32 + 255) / 256), 256, 0, s>>>(
-            reinterpret_cast<const __nv_bfloat16*>(a.dB16), a.vB, a.NB, nb16);
-        CUtensorMap tA, tB;
-        if (!make_map(&tA, a.dA16, a.NA, kRowsPerUnit) || !make_map(&tB, a.dB16, a.NB, kTileN))
+        k_ext_rows<<<(unsigned)((a.NB * 32 + 255) / 256), 256, 0, s>>>(
+            reinterpret_cast<const __nv_bfloat16*>(a.dB16), a.vB, a.NB, bext, aext);
+        CUtensorMap tA, tB, tAx, tBx;
+        if (!make_map(&tA, a.dA16, a.NA, kRowsPerUnit) || !make_map(&tB, a.dB16, a.NB, kTileN) ||
+            !make_map_ext(&tAx, aext, kRowsPerUnit, kRowsPerUnit) || !make_map_ext(&tBx, bext, a.NB, kTileN))
             return cudaErrorInvalidValue;
         TcParams p;
         p.NA = a.NA;
@@ -919,21 +938,26 @@ cudaError_t launch_match_bf16(const MatchArgs& a, void* ws, size_t ws_bytes, int
         p.S = L.S;
         const long long tiles = (a.NB + kTileN - 1) / kTileN;
         p.cps = ((tiles + L.S - 1) / L.S) * kTileN;
-        p.nb16 = nb16;
-        p.pv = pv;
-        p.pj = pj;
+        p.pm = pm;
+        p.thr = thr;
+        p.cand = cand;
+        p.ncand = ncand;
         p.status = a.status;
         const int U = p.nrp * p.S;
         const int grid = U < num_sms ? U : num_sms;
-        if ((e = cudaFuncSetAttribute(k_match_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTC)) !=
-            cudaSuccess)
+        if ((e = cudaFuncSetAttribute(k_match_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTC)) !=
+                cudaSuccess ||
+            (e = cudaFuncSetAttribute(k_match_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTC)) !=
+                cudaSuccess)
             return e;
         if (a.ev0) cudaEventRecord(a.ev0, s);
-        k_match_tc<<<grid, kThreadsTC, kSmemTC, s>>>(tA, tB, p);
+        k_match_tc<1><<<grid, kThreadsTC, kSmemTC, s>>>(tA, tB, tAx, tBx, p);
+        k_row_threshold<<<(unsigned)((a.NA + 255) / 256), 256, 0, s>>>(pm, L.S, a.NA, a.vA, kDelta, thr, ncand);
+        k_match_tc<2><<<grid, kThreadsTC, kSmemTC, s>>>(tA, tB, tAx, tBx, p);
         if (a.ev1) cudaEventRecord(a.ev1, s);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         k_rerank<<<(unsigned)((a.NA + kRerankWarps - 1) / kRerankWarps), kRerankWarps * 32, 0, s>>>(
-            a.dA, a.vA, a.dB, nb32, pv, pj, L.S, a.NA, kDelta, part1, rows, cnt);
+            a.dA, a.vA, a.dB, nb32, cand, ncand, thr, a.NA, kDelta, part1, rows, cnt);
         if ((e = cudaFuncSetAttribute(k_rescan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRescanSmem)) !=
             cudaSuccess)
             return e;
