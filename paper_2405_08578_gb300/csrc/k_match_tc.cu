@@ -479,14 +479,22 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
                 tc_fence_after();
                 const long long cbase = c0 + (long long)t * kTileN;
                 const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)((b * 2 + rb) * kTileN);
-                uint32_t ra[32], rb2[32];
-                tmem_ld32(tbase, ra);
-                tmem_wait(ra);
+                // the whole tile row in registers, then the buffer goes back to the MMA
+                uint32_t r0[32], r1[32], r2[32], r3[32];
+                tmem_ld32(tbase, r0);
+                tmem_ld32(tbase + 32, r1);
+                tmem_ld32(tbase + 64, r2);
+                tmem_ld32(tbase + 96, r3);
+                tmem_wait(r0);
+                tmem_wait(r1);
+                tmem_wait(r2);
+                tmem_wait(r3);
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&tempty[b]));
 #pragma unroll
                 for (int ch = 0; ch < kTileN / 32; ++ch) {
-                    uint32_t (&cur)[32] = (ch & 1) ? rb2 : ra;
-                    uint32_t (&nxt)[32] = (ch & 1) ? ra : rb2;
-                    if (ch + 1 < kTileN / 32) tmem_ld32(tbase + (uint32_t)((ch + 1) * 32), nxt);
+                    const uint32_t (&cur)[32] = ch == 0 ? r0 : ch == 1 ? r1 : ch == 2 ? r2 : r3;
                     float dv[32];
 #pragma unroll
                     for (int i = 0; i < 32; ++i) dv[i] = __uint_as_float(cur[i]);
@@ -527,11 +535,7 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
                             }
                         }
                     }
-                    if (ch + 1 < kTileN / 32) tmem_wait(nxt);
                 }
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(smem_u32(&tempty[b]));
             }
             if (!ok) break;
             if (kPass == 1 && live) p.pm[(long long)split * p.NA + row] = make_float2(-2.f * d1, -2.f * d2);
