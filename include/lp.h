@@ -231,6 +231,14 @@ typedef struct lp_image {
 LP_API int lp_stitch_pairs(lp_ctx* ctx, const lp_image* imgs, int N, const int32_t* pairs, int P, double* HM,
                            int32_t* n_in, uint8_t* valid, int32_t* M_out, void* stream);
 
+/* lp_stitch_pairs with explicit RANSAC pair ids (host uint32[P]; the Philox
+ * key of pair q uses pair_ids[q] instead of q), so that a subset of a pair
+ * list run on another GPU reproduces the full list's entries exactly.
+ * `pairs` must not be NULL here. */
+LP_API int lp_stitch_pairs_ids(lp_ctx* ctx, const lp_image* imgs, int N, const int32_t* pairs,
+                               const uint32_t* pair_ids, int P, double* HM, int32_t* n_in, uint8_t* valid,
+                               int32_t* M_out, void* stream);
+
 /* ---- learned RANSAC proposal (not in the paper) ----
  * A small network scores each matched pair's chance of being an inlier;
  * RANSAC can then draw its samples in proportion to the score.  Scoring of the

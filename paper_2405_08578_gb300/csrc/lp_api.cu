@@ -494,7 +494,14 @@ struct ImgBufs {
 int lp_stitch_pairs(lp_ctx* c, const lp_image* imgs, int N, const int32_t* pairs, int P, double* HM, int32_t* n_in,
                     uint8_t* valid, int32_t* M_out, void* stream)
 {
+    return lp_stitch_pairs_ids(c, imgs, N, pairs, nullptr, P, HM, n_in, valid, M_out, stream);
+}
+
+int lp_stitch_pairs_ids(lp_ctx* c, const lp_image* imgs, int N, const int32_t* pairs, const uint32_t* pair_ids, int P,
+                        double* HM, int32_t* n_in, uint8_t* valid, int32_t* M_out, void* stream)
+{
     if (!c) return LP_ERR_ARG;
+    if (pair_ids && !pairs) return fail(c, LP_ERR_ARG, "pair_ids need an explicit pair list");
     if (!imgs || N < 2) return fail(c, LP_ERR_ARG, "need at least two images");
     if (!HM || !n_in || !valid) return fail(c, LP_ERR_ARG, "null output");
     const int ch = imgs[0].channels;
@@ -569,6 +576,9 @@ int lp_stitch_pairs(lp_ctx* c, const lp_image* imgs, int N, const int32_t* pairs
         key.push_back(imgs[i].H); key.push_back(imgs[i].W); key.push_back(imgs[i].pitch);
     }
     key.insert(key.end(), pl.begin(), pl.end());
+    std::vector<uint32_t> pid((size_t)P);
+    for (int q = 0; q < P; ++q) pid[q] = pair_ids ? pair_ids[q] : (uint32_t)q;
+    key.insert(key.end(), pid.begin(), pid.end());
     c->last = s;
     if (s && c->graph_exec && key == c->graph_key) {
         LP_CUDA(c, cudaGraphLaunch(c->graph_exec, s));
@@ -610,10 +620,10 @@ int lp_stitch_pairs(lp_ctx* c, const lp_image* imgs, int N, const int32_t* pairs
                                  (const uint32_t*)(base + B.kp), base + B.ori, imgs[b].H, imgs[b].W,
                                  (const int32_t*)(base + o_match), (const float*)(base + o_d1),
                                  (const float*)(base + o_d2), (int32_t*)(base + o_rows), (float*)(base + o_feat),
-                                 (float*)(base + o_prob), (const float*)(base + o_pts), A.K, Mbuf + q, (uint32_t)q,
+                                 (float*)(base + o_prob), (const float*)(base + o_pts), A.K, Mbuf + q, pid[q],
                                  HM + 9 * (size_t)q, base + o_inl, n_in + q, stream);
             else
-                rr = lp_ransac(c, (const float*)(base + o_pts), A.K, Mbuf + q, (uint32_t)q, HM + 9 * (size_t)q,
+                rr = lp_ransac(c, (const float*)(base + o_pts), A.K, Mbuf + q, pid[q], HM + 9 * (size_t)q,
                                base + o_inl, n_in + q, nullptr, stream);
             if (rr) return rr;
         }

@@ -42,7 +42,7 @@ class lp_config(C.Structure):
 
 _lib = None
 SYMBOLS = ["lp_config_default", "lp_create", "lp_destroy", "lp_num_keypoints", "lp_detect", "lp_describe",
-           "lp_match", "lp_compact", "lp_ransac", "lp_ransac_static", "lp_stitch_pair", "lp_stitch_pair_host", "lp_stitch_pairs", "lp_sync_status",
+           "lp_match", "lp_compact", "lp_ransac", "lp_ransac_static", "lp_stitch_pair", "lp_stitch_pair_host", "lp_stitch_pairs", "lp_stitch_pairs_ids", "lp_sync_status",
            "lp_last_error", "lp_diag_last_rescans", "lp_diag_orient_bins", "lp_diag_orient_weights", "lp_diag_philox", "lp_diag_gray",
            "lp_mlp_create", "lp_mlp_destroy", "lp_mlp_set_params", "lp_mlp_get_params", "lp_mlp_get_state", "lp_mlp_save",
            "lp_mlp_load", "lp_mlp_features", "lp_mlp_forward", "lp_mlp_train_step", "lp_ransac_prior",
@@ -79,6 +79,7 @@ def load(build_if_missing: bool = True):
         "lp_stitch_pair": (i32, [P, P, i32, i32, i32, P, i32, i32, i32, i32, u32, P, P, P, P]),
         "lp_stitch_pair_host": (i32, [P, P, i32, i32, i32, P, i32, i32, i32, i32, u32, P, P, P, P]),
         "lp_stitch_pairs": (i32, [P, P, i32, P, i32, P, P, P, P, P]),
+        "lp_stitch_pairs_ids": (i32, [P, P, i32, P, P, i32, P, P, P, P, P]),
         "lp_sync_status": (i32, [P]),
         "lp_last_error": (C.c_char_p, [P]),
         "lp_diag_last_rescans": (i32, [P, C.POINTER(C.c_int64)]),
@@ -209,16 +210,24 @@ class Context:
                                                _stream(stream)), "lp_stitch_pair_host")
         return [list(Hh[0:3]), list(Hh[3:6]), list(Hh[6:9])], n.value, m.value
 
-    def lp_stitch_pairs(self, images, HM, n_in, valid, pairs=None, M_out=None, stream=None):
-        """images: list of (device uint8 tensor, H, W, pitch, channels)."""
+    def lp_stitch_pairs(self, images, HM, n_in, valid, pairs=None, M_out=None, stream=None, pair_ids=None):
+        """images: list of (device uint8 tensor, H, W, pitch, channels).  With
+        pair_ids (one per pair) the call is lp_stitch_pairs_ids."""
         arr = (lp_image * len(images))(*[lp_image(_ptr(t), H, W, p, ch) for (t, H, W, p, ch) in images])
         if pairs is None:
             pp, P = None, 0
         else:
             flat = (C.c_int32 * (2 * len(pairs)))(*[int(v) for pr in pairs for v in pr])
             pp, P = C.cast(flat, C.c_void_p), len(pairs)
-        self._chk(self.lib.lp_stitch_pairs(self.h, C.cast(arr, C.c_void_p), len(images), pp, P, _ptr(HM), _ptr(n_in),
-                                           _ptr(valid), _ptr(M_out), _stream(stream)), "lp_stitch_pairs")
+        if pair_ids is None:
+            self._chk(self.lib.lp_stitch_pairs(self.h, C.cast(arr, C.c_void_p), len(images), pp, P, _ptr(HM),
+                                               _ptr(n_in), _ptr(valid), _ptr(M_out), _stream(stream)),
+                      "lp_stitch_pairs")
+        else:
+            ids = (C.c_uint32 * len(pair_ids))(*[int(v) for v in pair_ids])
+            self._chk(self.lib.lp_stitch_pairs_ids(self.h, C.cast(arr, C.c_void_p), len(images), pp,
+                                                   C.cast(ids, C.c_void_p), P, _ptr(HM), _ptr(n_in), _ptr(valid),
+                                                   _ptr(M_out), _stream(stream)), "lp_stitch_pairs_ids")
 
     def lp_mlp_features(self, kpA, oriA, HA, WA, kpB, oriB, HB, WB, match, d1, d2, rows, d_M, M_cap, feat,
                         stream=None):

@@ -102,3 +102,29 @@ def test_stitch_pairs_3x3_tiles():
                 found += 1
             q += 1
     assert found == 12
+
+
+def test_pair_ids_let_a_shard_reproduce_the_full_list():
+    """The pair subset a rank would run (shard.shard) with lp_stitch_pairs_ids
+    gives exactly the full list's entries for those pairs."""
+    from paper_2405_08578_gb300 import shard
+    h, w = 240, 320
+    s1 = synth.small_pair(h, w, seed=31, theta_deg=2.0, shift=0.25)
+    s2 = synth.small_pair(h, w, seed=32, theta_deg=-3.0, shift=0.3)
+    imgs = [s1.A, s1.B, s2.A, s2.B, s1.B]
+    bufs = [lp.pitched_device(im) for im in imgs]
+    images = [(b, h, w, p, 1) for (b, p) in bufs]
+    ctx = lp.Context(Ls=(8, 16, 32), precision=lp.PREC_BF16, seed=9)
+    pl = shard.all_pairs(len(imgs))
+    P = len(pl)
+    HM, n_in, valid, M = _outputs(P)
+    ctx.lp_stitch_pairs(images, HM, n_in, valid, M_out=M)
+    torch.cuda.synchronize()
+    for world in (2, 3):
+        for rank in range(world):
+            mine = shard.shard(P, world, rank)
+            h2, n2, v2, m2 = _outputs(len(mine))
+            ctx.lp_stitch_pairs(images, h2, n2, v2, pairs=[pl[q] for q in mine], M_out=m2, pair_ids=mine)
+            torch.cuda.synchronize()
+            idx = torch.tensor(mine, device="cuda")
+            assert torch.equal(h2, HM[idx]) and torch.equal(n2, n_in[idx]) and torch.equal(m2, M[idx])
