@@ -693,12 +693,21 @@ k_rerank(const float* A, const uint8_t* vA, const float* B, const float* nb32, c
 constexpr int kRescanThreads = 128;
 constexpr int kRescanRows = 8;
 constexpr int kRescanPitch = 132;
-constexpr int kRescanGroups = 64;   // column ranges per queued row (partials per row)
+constexpr int kRescanGroups = 64;   // partial slots per row of A in the workspace
+
+// Column ranges per queued row: as many as the workspace holds for R queued
+// rows (R * G <= NA * kRescanGroups), at most one 128-column chunk each.
+__device__ __forceinline__ int rescan_groups(int R, long long NA, long long nchunks)
+{
+    long long g = R > 0 ? (NA * kRescanGroups) / R : 1;
+    if (g > nchunks) g = nchunks;
+    return (int)(g < 1 ? 1 : g);
+}
 constexpr size_t kRescanSmem = sizeof(float) * (kRescanThreads * kRescanPitch + 2 * kRescanRows * 128);
 
 __global__ void __launch_bounds__(kRescanThreads)
-k_rescan(const float* A, const float* B, const float* nb32, long long NB, const int32_t* rows, const int32_t* count,
-         float4* part_r)
+k_rescan(const float* A, const float* B, const float* nb32, long long NA, long long NB, const int32_t* rows,
+         const int32_t* count, float4* part_r)
 {
     extern __shared__ __align__(16) float rsm[];
     float* tb = rsm;                                   // [128 columns][kRescanPitch]
@@ -707,14 +716,15 @@ k_rescan(const float* A, const float* B, const float* nb32, long long NB, const 
     __shared__ float4 run[kRescanRows];   // running (b1, b2, j1, j2) per row
     const int R = *count;
     const int groups = (R + kRescanRows - 1) / kRescanRows;
-    const long long items = (long long)groups * kRescanGroups;
     const long long nchunks = (NB + kRescanThreads - 1) / kRescanThreads;
-    const long long cpg = (nchunks + kRescanGroups - 1) / kRescanGroups;
+    const int G = rescan_groups(R, NA, nchunks);
+    const long long items = (long long)groups * G;
+    const long long cpg = (nchunks + G - 1) / G;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const float4* B4 = reinterpret_cast<const float4*>(B);
     for (long long it = blockIdx.x; it < items; it += gridDim.x) {
-        const int g = (int)(it / kRescanGroups);
-        const int cg = (int)(it - (long long)g * kRescanGroups);
+        const int g = (int)(it / G);
+        const int cg = (int)(it - (long long)g * G);
         const int r0 = g * kRescanRows, nr = min(kRescanRows, R - r0);
         __syncthreads();
         for (int e = tid; e < kRescanRows * 32; e += kRescanThreads) {
@@ -783,17 +793,19 @@ k_rescan(const float* A, const float* B, const float* nb32, long long NB, const 
             }
         }
         __syncthreads();
-        if (tid < nr) part_r[(long long)(r0 + tid) * kRescanGroups + cg] = run[tid];
+        if (tid < nr) part_r[(long long)(r0 + tid) * G + cg] = run[tid];
     }
 }
 
 // Merge the re-scan partials of queued row r into the row's single partial.
-__global__ void k_rescan_merge(const float4* part_r, int nchunks, const int32_t* rows, const int32_t* count,
-                               float4* out_part)
+__global__ void k_rescan_merge(const float4* part_r, long long NA, long long NB, const int32_t* rows,
+                               const int32_t* count, float4* out_part)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long r = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
-    if (r >= *count) return;
+    const int R = *count;
+    if (r >= R) return;
+    const int nchunks = rescan_groups(R, NA, (NB + kRescanThreads - 1) / kRescanThreads);
     float b1 = INFINITY, b2 = INFINITY;
     int j1 = -1, j2 = -1;
     for (int c = lane; c < nchunks; c += 32) {
@@ -965,9 +977,9 @@ cudaError_t launch_match_bf16(const MatchArgs& a, void* ws, size_t ws_bytes, int
         if ((e = cudaFuncSetAttribute(k_rescan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRescanSmem)) !=
             cudaSuccess)
             return e;
-        k_rescan<<<(unsigned)(4 * num_sms), kRescanThreads, kRescanSmem, s>>>(a.dA, a.dB, nb32, a.NB, rows, cnt,
-                                                                               part_r);
-        k_rescan_merge<<<(unsigned)((a.NA + 7) / 8), 256, 0, s>>>(part_r, kRescanGroups, rows, cnt, part1);
+        k_rescan<<<(unsigned)(4 * num_sms), kRescanThreads, kRescanSmem, s>>>(a.dA, a.dB, nb32, a.NA, a.NB, rows,
+                                                                               cnt, part_r);
+        k_rescan_merge<<<(unsigned)((a.NA + 7) / 8), 256, 0, s>>>(part_r, a.NA, a.NB, rows, cnt, part1);
         k_match_finish<<<(unsigned)((a.NA + 255) / 256), 256, 0, s>>>(part1, 1, a.NA, na, a.vA, a.ratio2, a.delta_s2,
                                                                       a.match, a.d1, a.d2);
     } else {

@@ -749,7 +749,7 @@ k_refit_solve(const double* Hs, const int32_t* best_in, RefitWS ws, double* Hout
 #pragma unroll
             for (int o = 16; o; o >>= 1) diff = fmax(diff, __shfl_xor_sync(0xFFFFFFFFu, diff, o));
             x = xn;
-            if (it >= 2 && diff < 1e-15) break;
+            if (it >= 2 && diff < 1e-12) break;
         }
     }
     double h[9];
