@@ -66,13 +66,23 @@ constexpr uint32_t kAExtBytes = kRowsPerUnit * kExtRowBytes;   // 8 KB, loaded o
 constexpr uint32_t kBExtBytes = kTileN * kExtRowBytes;         // 4 KB per stage
 constexpr uint32_t kSmemTC =
     kABytes + kStages * kBBytes + kAExtBytes + kStages * kBExtBytes + 1024 /*barriers*/ + 1024 /*align slack*/;
-constexpr int kCandCapacity = 32;                      // pass-2 candidates kept per row
+#ifndef LP_CAND_CAPACITY
+#define LP_CAND_CAPACITY 64
+#endif
+constexpr int kCandCapacity = LP_CAND_CAPACITY;        // pass-2 candidates kept per row
 // largest value a candidate may have: invalid columns (kNoColumn) never qualify
 constexpr float kCandCap = 1.0e38f;
 // margin of the candidate window above m2 + delta (about five standard
 // deviations of the BF16 rounding error of a value); a row whose exact
 // second-best exceeds m2 + kMargin is not certified and is re-scanned
 constexpr float kMargin = 4.0e-3f;
+// Pass 1 visits every kPass1Stride-th column tile: its m2 is then the second
+// smallest chunk minimum of a spread subset, still the value of a second
+// column, so still >= B; the candidate window widens a little.
+#ifndef LP_PASS1_STRIDE
+#define LP_PASS1_STRIDE 3
+#endif
+constexpr int kPass1Stride = LP_PASS1_STRIDE;
 // |b~|^2 of an invalid or masked column: finite (so that the column tag below
 // never turns it into a NaN) and far above any real value; treated as +inf by
 // the re-rank.
@@ -147,6 +157,30 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
         : "memory");
 }
 
+// The same load delivered to the same shared-memory offset (data and
+// complete_tx on the mbarrier at the same offset) in every CTA of `mask`.
+__device__ __forceinline__ void tma_load_2d_mc(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar,
+                                               uint16_t mask)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster "
+        "[%0], [%1, {%2, %3}], [%4], %5;"
+        ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar), "h"(mask)
+        : "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_ctarank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ void cluster_sync()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 __device__ __forceinline__ void tma_prefetch_desc(const CUtensorMap* map)
 {
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
@@ -198,6 +232,15 @@ __device__ __forceinline__ void mma_commit(uint32_t bar)
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
 
+// Arrive (when this thread's MMAs complete) on the mbarrier at offset `bar`
+// of every CTA in `mask`.
+__device__ __forceinline__ void mma_commit_mc(uint32_t bar, uint16_t mask)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;"
+                 ::"r"(bar), "h"(mask)
+                 : "memory");
+}
+
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -233,28 +276,33 @@ __device__ __forceinline__ void tmem_wait(uint32_t (&r)[32])
 // ------------------------------------------------------------------ work split
 struct TcParams {
     long long NA, NB;
-    int nrp;               // number of 256-row blocks
+    int nrp;               // number of pairs of 256-row blocks (one pair per CTA cluster)
     int S;                 // column splits
     long long cps;         // columns per split (multiple of kTileN)
     float2* pm;            // pass 1 output [S][NA]: the split's two smallest chunk minima
     const float* thr;      // pass 2 input [NA]: candidate threshold per row (-inf: none)
     int32_t* cand;         // pass 2 output [NA][kCandCapacity]: candidate columns (unordered)
     int32_t* ncand;        // [NA]: candidates found (may exceed the capacity)
+    int tstride;           // tiles visited: every tstride-th 128-column tile of a split
     int32_t* status;
 };
 
-// Unit u = (256-row block rp, column split): consecutive units share a row
-// block, and each CTA takes a contiguous run of units, so the A block is
-// usually reused and each split's list can start from the previous split's
-// k-th best.
-__device__ __forceinline__ void unit_range(const TcParams& p, int u, int& rp, int& split, long long& c0, int& ntiles)
+// Unit u = (pair of 256-row blocks, column split), processed by one cluster of
+// two CTAs: CTA rank r takes row block rp = 2 * pair + r, and both stream the
+// same B tiles, each loading one K-half of every tile for both (multicast).
+// Consecutive units share a row block and each cluster takes a contiguous run
+// of units, so the A blocks are usually reused.
+__device__ __forceinline__ void unit_range(const TcParams& p, int u, uint32_t crank, int& rp, int& split,
+                                           long long& c0, int& ntiles)
 {
-    rp = u / p.S;
-    split = u - rp * p.S;
+    const int pair = u / p.S;
+    split = u - pair * p.S;
+    rp = 2 * pair + (int)crank;
     c0 = (long long)split * p.cps;
     long long c1 = c0 + p.cps;
     if (c1 > p.NB) c1 = p.NB;
-    ntiles = c1 > c0 ? (int)((c1 - c0 + kTileN - 1) / kTileN) : 0;
+    const int all = c1 > c0 ? (int)((c1 - c0 + kTileN - 1) / kTileN) : 0;
+    ntiles = (all + p.tstride - 1) / p.tstride;
 }
 
 __device__ __forceinline__ float max3f(float a, float b, float c)
@@ -300,15 +348,17 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t crank = cluster_ctarank();
+    const int cid = (int)blockIdx.x >> 1, ncl = (int)gridDim.x >> 1;
     const int U = p.nrp * p.S;
-    const int per = U / (int)gridDim.x, rem = U % (int)gridDim.x;
-    const int u_begin = (int)blockIdx.x * per + min((int)blockIdx.x, rem);
-    const int u_end = u_begin + per + ((int)blockIdx.x < rem ? 1 : 0);
+    const int per = U / ncl, rem = U % ncl;
+    const int u_begin = cid * per + min(cid, rem);
+    const int u_end = u_begin + per + (cid < rem ? 1 : 0);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
             mbar_init(smem_u32(&full[s]), 1);
-            mbar_init(smem_u32(&empty[s]), 1);
+            mbar_init(smem_u32(&empty[s]), 2);   // both CTAs' MMAs release a stage
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(smem_u32(&tfull[b]), 1);
@@ -331,6 +381,7 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
     }
     tc_fence_before();
     __syncthreads();
+    cluster_sync();   // the peer's barriers exist before any multicast reaches them
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
@@ -347,7 +398,7 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
             for (int u = u_begin; u < u_end && ok; ++u) {
                 int rp, split, ntiles;
                 long long c0;
-                unit_range(p, u, rp, split, c0, ntiles);
+                unit_range(p, u, crank, rp, split, c0, ntiles);
                 if (ntiles == 0) continue;
                 if (rp != prev_rp) {
                     ok = mbar_wait(smem_u32(aempty), (v & 1) ^ 1, abort_flag, p.status);
@@ -366,11 +417,14 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
                     ok = mbar_wait(smem_u32(&empty[s]), (k & 1) ^ 1, abort_flag, p.status);
                     if (!ok) break;
                     uint8_t* dst = sB + s * kBBytes;
-                    const int y = (int)(c0 + (long long)t * kTileN);
+                    const int y = (int)(c0 + (long long)t * p.tstride * kTileN);
                     mbar_expect_tx(smem_u32(&full[s]), kBBytes + kBExtBytes);
-                    tma_load_2d(smem_u32(dst), &tmB, 0, y, smem_u32(&full[s]));
-                    tma_load_2d(smem_u32(dst + kBBytes / 2), &tmB, 64, y, smem_u32(&full[s]));
-                    tma_load_2d(smem_u32(sBx + s * kBExtBytes), &tmBx, 0, y, smem_u32(&full[s]));
+                    if (crank == 0) {
+                        tma_load_2d_mc(smem_u32(dst), &tmB, 0, y, smem_u32(&full[s]), 3);
+                        tma_load_2d_mc(smem_u32(sBx + s * kBExtBytes), &tmBx, 0, y, smem_u32(&full[s]), 3);
+                    } else {
+                        tma_load_2d_mc(smem_u32(dst + kBBytes / 2), &tmB, 64, y, smem_u32(&full[s]), 3);
+                    }
                     armed[s] = (int)k;
                 }
             }
@@ -392,6 +446,11 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
     } else if (warp == 1) {
         // ---------------------------------------------------------- MMA issuer
         if (lane == 0) {
+            // descriptors of the fixed buffers; an operand at byte offset o from
+            // a base is the base descriptor + (o >> 4) (the 14-bit start field
+            // never carries: shared addresses stay below 256 KB)
+            const uint64_t dA0 = sdesc(smem_u32(sA)), dB0 = sdesc(smem_u32(sB));
+            const uint64_t dAx0 = sdesc32(smem_u32(sAx)), dBx0 = sdesc32(smem_u32(sBx));
             long long n = 0;
             int v = 0;
             bool ok = true;
@@ -399,7 +458,7 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
             for (int u = u_begin; u < u_end && ok; ++u) {
                 int rp, split, ntiles;
                 long long c0;
-                unit_range(p, u, rp, split, c0, ntiles);
+                unit_range(p, u, crank, rp, split, c0, ntiles);
                 if (ntiles == 0) continue;
                 if (rp != prev_rp) {
                     // release the previous A block once its MMAs are done, then
@@ -421,23 +480,22 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
                     ok = mbar_wait(smem_u32(&full[s]), k & 1, abort_flag, p.status);
                     if (!ok) break;
                     tc_fence_after();
-                    const uint32_t bbase = smem_u32(sB + s * kBBytes);
+                    const uint64_t dB = dB0 + (uint64_t)((s * kBBytes) >> 4);
+                    const uint64_t dBx = dBx0 + (uint64_t)((s * kBExtBytes) >> 4);
 #pragma unroll
                     for (int rb = 0; rb < 2; ++rb) {
                         const uint32_t d = tmem + (uint32_t)((b * 2 + rb) * kTileN);
-                        const uint32_t abase = smem_u32(sA) + rb * (128 * 128);
 #pragma unroll
                         for (int h = 0; h < 2; ++h)
 #pragma unroll
                             for (int kk = 0; kk < 4; ++kk) {
-                                const uint64_t ad = sdesc(abase + h * (kABytes / 2) + kk * 32);
-                                const uint64_t bd = sdesc(bbase + h * (kBBytes / 2) + kk * 32);
+                                const uint64_t ad = dA0 + (uint64_t)((rb * (128 * 128) + h * (kABytes / 2) + kk * 32) >> 4);
+                                const uint64_t bd = dB + (uint64_t)((h * (kBBytes / 2) + kk * 32) >> 4);
                                 mma_bf16(d, ad, bd, (h | kk) ? 1u : 0u);
                             }
-                        mma_bf16(d, sdesc32(smem_u32(sAx) + rb * 128 * kExtRowBytes),
-                                 sdesc32(smem_u32(sBx) + s * kBExtBytes), 1u);
+                        mma_bf16(d, dAx0 + (uint64_t)((rb * 128 * kExtRowBytes) >> 4), dBx, 1u);
                     }
-                    mma_commit(smem_u32(&empty[s]));
+                    mma_commit_mc(smem_u32(&empty[s]), 3);
                     mma_commit(smem_u32(&tfull[b]));
                 }
             }
@@ -463,7 +521,7 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
         for (int u = u_begin; u < u_end && ok; ++u) {
             int rp, split, ntiles;
             long long c0;
-            unit_range(p, u, rp, split, c0, ntiles);
+            unit_range(p, u, crank, rp, split, c0, ntiles);
             long long c1 = c0 + p.cps;
             if (c1 > p.NB) c1 = p.NB;
             const long long row = (long long)rp * kRowsPerUnit + row_in_unit;
@@ -477,7 +535,7 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
                 ok = mbar_wait(smem_u32(&tfull[b]), kb & 1, abort_flag, p.status);
                 if (!ok) break;
                 tc_fence_after();
-                const long long cbase = c0 + (long long)t * kTileN;
+                const long long cbase = c0 + (long long)t * p.tstride * kTileN;
                 const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)((b * 2 + rb) * kTileN);
                 // the whole tile row in registers, then the buffer goes back to the MMA
                 uint32_t r0[32], r1[32], r2[32], r3[32];
@@ -544,6 +602,7 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
     }
     tc_fence_before();
     __syncthreads();
+    cluster_sync();   // no multicast copy or remote arrival still targets this CTA
     tc_fence_after();
     if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
 }
@@ -667,8 +726,8 @@ k_rerank(const float* A, const uint8_t* vA, const float* B, const float* nb32, c
     if (ok) {
         reinterpret_cast<float4*>(qa[warp])[lane] = reinterpret_cast<const float4*>(A + i * 128)[lane];
         __syncwarp();
-        if (lane < n) {
-            const int j = cand[i * kCandCapacity + lane];
+        for (int c = lane; c < n; c += 32) {
+            const int j = cand[i * kCandCapacity + c];
             top2_lex(b1, j1, b2, j2, fp32_form_value(qa[warp], B + (long long)j * 128, __ldg(nb32 + j)), j);
         }
         warp_top2(b1, j1, b2, j2);
@@ -883,8 +942,8 @@ struct TcLayout {
 TcLayout tc_layout(long long NA, long long NB, int sms)
 {
     TcLayout L;
-    const int nrp = (int)((NA + kRowsPerUnit - 1) / kRowsPerUnit);
-    L.S = pick_tc_splits(nrp, NB, sms);
+    const int nrp = (int)((NA + 2 * kRowsPerUnit - 1) / (2 * kRowsPerUnit));
+    L.S = pick_tc_splits(nrp, NB, std::max(1, sms / 2));
     size_t o = 0;
     auto take = [&](size_t bytes) { size_t r = o; o += (bytes + 255) & ~size_t(255); return r; };
     L.off_bext = take(kExtRowBytes * (size_t)NB + 64);
@@ -950,7 +1009,7 @@ cudaError_t launch_match_bf16(const MatchArgs& a, void* ws, size_t ws_bytes, int
         TcParams p;
         p.NA = a.NA;
         p.NB = a.NB;
-        p.nrp = (int)((a.NA + kRowsPerUnit - 1) / kRowsPerUnit);
+        p.nrp = (int)((a.NA + 2 * kRowsPerUnit - 1) / (2 * kRowsPerUnit));
         p.S = L.S;
         const long long tiles = (a.NB + kTileN - 1) / kTileN;
         p.cps = ((tiles + L.S - 1) / L.S) * kTileN;
@@ -958,18 +1017,36 @@ cudaError_t launch_match_bf16(const MatchArgs& a, void* ws, size_t ws_bytes, int
         p.thr = thr;
         p.cand = cand;
         p.ncand = ncand;
+        p.tstride = 1;
         p.status = a.status;
         const int U = p.nrp * p.S;
-        const int grid = U < num_sms ? U : num_sms;
         if ((e = cudaFuncSetAttribute(k_match_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTC)) !=
                 cudaSuccess ||
             (e = cudaFuncSetAttribute(k_match_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTC)) !=
                 cudaSuccess)
             return e;
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = 2;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.blockDim = dim3(kThreadsTC);
+        cfg.dynamicSmemBytes = kSmemTC;
+        cfg.stream = s;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        cfg.gridDim = dim3(2 * (unsigned)std::max(1, num_sms / 2));
+        int clusters = 0;
+        if ((e = cudaOccupancyMaxActiveClusters(&clusters, k_match_tc<1>, &cfg)) != cudaSuccess) return e;
+        if (clusters < 1) return cudaErrorInvalidConfiguration;
+        cfg.gridDim = dim3(2 * (unsigned)std::min(U, clusters));
         if (a.ev0) cudaEventRecord(a.ev0, s);
-        k_match_tc<1><<<grid, kThreadsTC, kSmemTC, s>>>(tA, tB, tAx, tBx, p);
+        TcParams p1 = p;
+        p1.tstride = kPass1Stride;
+        if ((e = cudaLaunchKernelEx(&cfg, k_match_tc<1>, tA, tB, tAx, tBx, p1)) != cudaSuccess) return e;
         k_row_threshold<<<(unsigned)((a.NA + 255) / 256), 256, 0, s>>>(pm, L.S, a.NA, a.vA, kDelta, thr, ncand);
-        k_match_tc<2><<<grid, kThreadsTC, kSmemTC, s>>>(tA, tB, tAx, tBx, p);
+        if ((e = cudaLaunchKernelEx(&cfg, k_match_tc<2>, tA, tB, tAx, tBx, p)) != cudaSuccess) return e;
         if (a.ev1) cudaEventRecord(a.ev1, s);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         k_rerank<<<(unsigned)((a.NA + kRerankWarps - 1) / kRerankWarps), kRerankWarps * 32, 0, s>>>(
