@@ -49,6 +49,7 @@ struct DescParams {
     float cs[36][2];        // cos, sin of (k + 0.5) * 10 degrees
     int upright;
     int warp_bytes, patch_bytes, mid_bytes;
+    int word_ok;           // gray base 4-byte aligned and pitch % 4 == 0: interior patches load 32-bit words
     const uint8_t* lut_bin;
     const uint32_t* lut_w;
     uint8_t* ori;
@@ -127,6 +128,10 @@ __device__ __forceinline__ void grad_polar(float a, float b, float x2, float& m,
     if (o >= 8.f) o -= 8.f;
 }
 
+// Shared-memory row stride of an S-wide patch: room for the up-to-3-byte shift
+// of word-aligned rows.
+__host__ __device__ __forceinline__ int patch_stride(int S) { return 4 * ((S + 6) / 4); }
+
 // Bilinear intensity at (row, col) offsets relative to the patch centre;
 // nested linear interpolation, exact on flat neighbourhoods.
 __device__ __forceinline__ float bilinear(const uint8_t* patch, int S, int P, float r, float c)
@@ -172,17 +177,27 @@ __global__ void __launch_bounds__(kWarps * 32) k_describe_all(const DescParams p
     uint32_t* hlo = reinterpret_cast<uint32_t*>(base + p.patch_bytes + p.mid_bytes);   // [36]
     uint32_t* hhi = hlo + 36;                                                          // [36]
     float* acc = reinterpret_cast<float*>(base + p.patch_bytes + p.mid_bytes + 2 * 36 * 4);
-    const int ws = p.wsl[l], R = 2 * ws, P = p.Pl[l], S = 2 * P + 1;
+    const int ws = p.wsl[l], R = 2 * ws, P = p.Pl[l], S = 2 * P + 1, SP = patch_stride(S);
     const uint32_t id = __ldg(p.kp + k);
     const int y = (int)(id / (uint32_t)p.W), x = (int)(id - (uint32_t)y * (uint32_t)p.W);
 
-    // clamped neighbourhood
-    {
+    // neighbourhood: aligned 32-bit words for interior points (row r of the
+    // patch starts `off` bytes into shared row r), clamped bytes near the edge
+    if (p.word_ok && y >= P && y + P < p.H && x >= P && x + P + 3 < p.W) {
+        const int off = (x - P) & 3, nw = (off + S + 3) >> 2;
+        const uint8_t* src = p.gray + (size_t)(y - P) * p.pitch + (x - P - off);
+        Walk2D w(lane, nw);
+#pragma unroll 2
+        for (; w.r < S; w.next())
+            reinterpret_cast<uint32_t*>(base + w.r * SP)[w.c] =
+                __ldg(reinterpret_cast<const uint32_t*>(src + (size_t)w.r * p.pitch) + w.c);
+        patch = base + off;
+    } else {
         Walk2D w(lane, S);
 #pragma unroll 4
         for (; w.r < S; w.next()) {
             const int yy = min(max(y - P + w.r, 0), p.H - 1), xx = min(max(x - P + w.c, 0), p.W - 1);
-            patch[w.r * S + w.c] = __ldg(p.gray + (size_t)yy * p.pitch + xx);
+            patch[w.r * SP + w.c] = __ldg(p.gray + (size_t)yy * p.pitch + xx);
         }
     }
     if (lane < 36) { hlo[lane] = 0u; hhi[lane] = 0u; }
@@ -195,11 +210,11 @@ __global__ void __launch_bounds__(kWarps * 32) k_describe_all(const DescParams p
     int best = 0;
     if (!p.upright) {
         const int n = 2 * R + 1;
-        const uint8_t* c0 = patch + (P - R) * S + (P - R);
+        const uint8_t* c0 = patch + (P - R) * SP + (P - R);
         Walk2D w(lane, n);
         for (; w.r < n; w.next()) {
-            const uint8_t* q = c0 + w.r * S + w.c;
-            const int a = (int)q[S] - (int)q[-S];
+            const uint8_t* q = c0 + w.r * SP + w.c;
+            const int a = (int)q[SP] - (int)q[-SP];
             const int b = (int)q[1] - (int)q[-1];
             if (a | b) {
                 const int bin = __ldg(p.lut_bin + (a + 255) * 511 + (b + 255));
@@ -232,7 +247,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_describe_all(const DescParams p
         Walk2D w(lane, G);
         for (; w.r < G; w.next()) {
             const float fu = (float)(w.r - R - 1), fv = (float)(w.c - R - 1);
-            grid[w.r * G + w.c] = bilinear(patch, S, P, fu * c - fv * s, fu * s + fv * c);
+            grid[w.r * G + w.c] = bilinear(patch, SP, P, fu * c - fv * s, fu * s + fv * c);
         }
     }
     float* mine = acc + lane * kAccStride;
@@ -315,26 +330,36 @@ __global__ void __launch_bounds__(kCtaThreads) k_describe_cta(const DescParams p
     __shared__ int best_s;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const long long k = p.k0 + p.n - 1 - blockIdx.x;   // heaviest first
-    const int ws = p.ws, R = 2 * ws, P = p.P, S = 2 * P + 1, G = 2 * R + 2;
+    const int ws = p.ws, R = 2 * ws, P = p.P, S = 2 * P + 1, G = 2 * R + 2, SP = patch_stride(S);
     uint8_t* patch = sm;
     float* grid = reinterpret_cast<float*>(sm + p.patch_bytes);
     const uint32_t id = __ldg(p.kp + k);
     const int y = (int)(id / (uint32_t)p.W), x = (int)(id - (uint32_t)y * (uint32_t)p.W);
-    for (int e = tid; e < S * S; e += kCtaThreads) {
-        const int r = e / S, c = e - (e / S) * S;
-        const int yy = min(max(y - P + r, 0), p.H - 1), xx = min(max(x - P + c, 0), p.W - 1);
-        patch[e] = __ldg(p.gray + (size_t)yy * p.pitch + xx);
+    if (p.word_ok && y >= P && y + P < p.H && x >= P && x + P + 3 < p.W) {
+        const int off = (x - P) & 3, nw = (off + S + 3) >> 2;
+        const uint8_t* src = p.gray + (size_t)(y - P) * p.pitch + (x - P - off);
+        for (int e = tid; e < S * nw; e += kCtaThreads) {
+            const int r = e / nw, c = e - (e / nw) * nw;
+            reinterpret_cast<uint32_t*>(sm + r * SP)[c] = __ldg(reinterpret_cast<const uint32_t*>(src + (size_t)r * p.pitch) + c);
+        }
+        patch = sm + off;
+    } else {
+        for (int e = tid; e < S * S; e += kCtaThreads) {
+            const int r = e / S, c = e - (e / S) * S;
+            const int yy = min(max(y - P + r, 0), p.H - 1), xx = min(max(x - P + c, 0), p.W - 1);
+            patch[r * SP + c] = __ldg(p.gray + (size_t)yy * p.pitch + xx);
+        }
     }
     if (tid < 36) { hlo[tid] = 0u; hhi[tid] = 0u; }
     __syncthreads();
     int best = 0;
     if (!p.upright) {
         const int n = 2 * R + 1;
-        const uint8_t* c0 = patch + (P - R) * S + (P - R);
+        const uint8_t* c0 = patch + (P - R) * SP + (P - R);
         for (int e = tid; e < n * n; e += kCtaThreads) {
             const int r = e / n, c = e - (e / n) * n;
-            const uint8_t* q = c0 + r * S + c;
-            const int a = (int)q[S] - (int)q[-S];
+            const uint8_t* q = c0 + r * SP + c;
+            const int a = (int)q[SP] - (int)q[-SP];
             const int b = (int)q[1] - (int)q[-1];
             if (a | b) {
                 const int bin = __ldg(p.lut_bin + (a + 255) * 511 + (b + 255));
@@ -367,7 +392,7 @@ __global__ void __launch_bounds__(kCtaThreads) k_describe_cta(const DescParams p
     for (int e = tid; e < G * G; e += kCtaThreads) {
         const int iu = e / G, iv = e - (e / G) * G;
         const float fu = (float)(iu - R - 1), fv = (float)(iv - R - 1);
-        grid[e] = bilinear(patch, S, P, fu * c - fv * s, fu * s + fv * c);
+        grid[e] = bilinear(patch, SP, P, fu * c - fv * s, fu * s + fv * c);
     }
     __syncthreads();
     const int cell = tid >> 3, sub = tid & 7, cr = cell >> 2, cc = cell & 3;
@@ -553,6 +578,7 @@ cudaError_t launch_describe(const uint8_t* gray, int H, int W, int pitch, const 
         p.cs[k][1] = (float)sin(th);
     }
     p.upright = upright;
+    p.word_ok = ((reinterpret_cast<uintptr_t>(gray) & 3u) == 0 && (pitch & 3) == 0) ? 1 : 0;
     p.lut_w = reinterpret_cast<const uint32_t*>(luts);
     p.lut_bin = reinterpret_cast<const uint8_t*>(luts) + (((size_t)kLutWeights * 4 + 255) & ~size_t(255));
     p.ori = ori; p.desc = desc; p.desc16 = reinterpret_cast<__nv_bfloat16*>(desc_bf16); p.valid = valid;
@@ -564,7 +590,7 @@ cudaError_t launch_describe(const uint8_t* gray, int H, int W, int pitch, const 
     while (m < st.nL && st.ws[m] <= 15) ++m;
     auto warp_bytes = [&](int l) {
         const int S = 2 * st.pr[l] + 1, G = 4 * st.ws[l] + 2;
-        return ((S * S + 15) / 16) * 16 + ((G * G * 4 + 15) / 16) * 16 + 2 * 36 * 4 + kAccBytes;
+        return ((S * patch_stride(S) + 15) / 16) * 16 + ((G * G * 4 + 15) / 16) * 16 + 2 * 36 * 4 + kAccBytes;
     };
     constexpr int kSmallWarpBytes = 7680;
     int first_big = 0;
@@ -582,7 +608,7 @@ cudaError_t launch_describe(const uint8_t* gray, int H, int W, int pitch, const 
         p.n = st.off[l1] - st.off[l0];
         if (p.n == 0) return cudaSuccess;
         const int S = 2 * Pmax + 1;
-        p.patch_bytes = ((S * S + 15) / 16) * 16;
+        p.patch_bytes = ((S * patch_stride(S) + 15) / 16) * 16;
         p.mid_bytes = ((Gmax * Gmax * 4) + 15) / 16 * 16;
         p.warp_bytes = p.patch_bytes + p.mid_bytes + 2 * 36 * 4 + kAccBytes;
         const size_t smem = (size_t)kWarps * p.warp_bytes;
@@ -600,7 +626,7 @@ cudaError_t launch_describe(const uint8_t* gray, int H, int W, int pitch, const 
         p.ws = st.ws[l];
         p.P = st.pr[l];
         const int S = 2 * p.P + 1, G = 4 * p.ws + 2;
-        p.patch_bytes = ((S * S + 15) / 16) * 16;
+        p.patch_bytes = ((S * patch_stride(S) + 15) / 16) * 16;
         const size_t smem = (size_t)p.patch_bytes + (size_t)G * G * 4;
         if (smem > 48 * 1024) {
             cudaError_t e = cudaFuncSetAttribute(k_describe_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
