@@ -67,6 +67,8 @@ def lib():
             "or_ransac_sample_guided": (i32, [i64, P, C.c_uint64, u32, i32, P]),
             "or_ransac_prior": (i32, [P, i64, P, i32, i32, f64, C.c_uint64, u32, P, P, P, P, P, P]),
             "or_guided_stop": (i32, [C.c_uint64, C.c_uint64, i32]),
+            "or_mosaic_plan": (i32, [i32, P, i32, P, P, P, P, P, P, P, P, P]),
+            "or_mosaic_render": (i32, [i32, P, P, P, P, i32, P, P, i32, i32, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -373,3 +375,39 @@ def ransac_prior(pts, prob, Tg=64, T=1000, thresh=3.0, seed=0, pair_id=0, want_c
 
 def guided_stop(s_in, total, Tg) -> bool:
     return bool(lib().or_guided_stop(int(s_in), int(total), int(Tg)))
+
+
+def mosaic_plan(n_images, pairs, HM, valid, sizes):
+    """Sec. 4 rounds.  pairs [(a, b)], HM [P, 3, 3] (x_b ~ H x_a), valid [P],
+    sizes [(H, W)].  Returns dict(G [N, 3, 3] image -> canvas, round [N],
+    ref [N], canvas (h, w))."""
+    pr = _c(np.asarray(pairs, np.int32).reshape(-1, 2), np.int32)
+    H = _c(np.asarray(HM, np.float64).reshape(-1, 9), np.float64)
+    v = _c(np.asarray(valid, np.uint8), np.uint8)
+    Hs = _c([s[0] for s in sizes], np.int32)
+    Ws = _c([s[1] for s in sizes], np.int32)
+    G = np.zeros((n_images, 9), np.float64)
+    rnd = np.zeros(n_images, np.int32)
+    ref = np.zeros(n_images, np.int32)
+    cw, ch = C.c_int(), C.c_int()
+    assert lib().or_mosaic_plan(n_images, _p(pr), len(pr), _p(H), _p(v), _p(Hs), _p(Ws), _p(G), _p(rnd), _p(ref),
+                                C.byref(cw), C.byref(ch)) == 0
+    return dict(G=G.reshape(-1, 3, 3), round=rnd, ref=ref, canvas=(ch.value, cw.value))
+
+
+def mosaic_render(images, G, rounds, canvas_hw):
+    """images: list of uint8 (H, W) or (H, W, 3); G [N, 3, 3]; -> (canvas, cover)."""
+    C_ = 3 if images[0].ndim == 3 else 1
+    ims = [np.ascontiguousarray(im, np.uint8) for im in images]
+    ptrs = (C.c_void_p * len(ims))(*[im.ctypes.data for im in ims])
+    Hs = _c([im.shape[0] for im in ims], np.int32)
+    Ws = _c([im.shape[1] for im in ims], np.int32)
+    pitch = _c([im.shape[1] * C_ for im in ims], np.int32)
+    h, w = canvas_hw
+    canvas = np.zeros((h, w, C_) if C_ == 3 else (h, w), np.uint8)
+    cover = np.zeros((h, w), np.uint8)
+    Gd = _c(np.asarray(G, np.float64).reshape(-1, 9), np.float64)
+    r = _c(rounds, np.int32)
+    assert lib().or_mosaic_render(len(ims), C.cast(ptrs, C.c_void_p), _p(Hs), _p(Ws), _p(pitch), C_, _p(Gd), _p(r),
+                                  w, h, _p(canvas), _p(cover)) == 0
+    return canvas, cover

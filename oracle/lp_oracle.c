@@ -898,3 +898,150 @@ int or_ransac_prior(const double* pts, int64_t M, const float* prob, int Tg, int
     memcpy(H, Hf, sizeof Hf);
     return 0;
 }
+
+/* ------------------------------------------------------------------ */
+/* Sec. 4 mosaic: rounds of reference selection over H_M, then every placed
+ * image warped onto one canvas.
+ * Readings:
+ *  - the degree of an image is its number of valid H_M entries;
+ *  - round 1: the reference is the image of largest degree (lowest index on
+ *    ties); it is placed with the identity, every image matched with it is
+ *    placed through their H_M entry;
+ *  - round k > 1: among unmatched images with a valid entry to a placed image,
+ *    the one of largest degree (lowest index on ties) is the reference; it is
+ *    placed through its valid entry to the placed image of lowest index, then
+ *    its unmatched neighbours through it;
+ *  - images that never connect stay unplaced (round -1).
+ * H_M entry q of pair (a, b) maps image a pixels to image b pixels
+ * (x_b ~ H x_a, Eq. 7); the placement G_i maps image i pixels to the
+ * reference frame of round 1.  The canvas is the integer bounding box of the
+ * placed images' corner pixels; G is returned with the canvas shift applied. */
+
+static int inv3(const double* M, double* R)
+{
+    const double c00 = M[4] * M[8] - M[5] * M[7], c01 = M[5] * M[6] - M[3] * M[8], c02 = M[3] * M[7] - M[4] * M[6];
+    const double det = M[0] * c00 + M[1] * c01 + M[2] * c02;
+    if (!(fabs(det) > 0)) return 1;
+    R[0] = c00 / det; R[1] = (M[2] * M[7] - M[1] * M[8]) / det; R[2] = (M[1] * M[5] - M[2] * M[4]) / det;
+    R[3] = c01 / det; R[4] = (M[0] * M[8] - M[2] * M[6]) / det; R[5] = (M[2] * M[3] - M[0] * M[5]) / det;
+    R[6] = c02 / det; R[7] = (M[1] * M[6] - M[0] * M[7]) / det; R[8] = (M[0] * M[4] - M[1] * M[3]) / det;
+    return 0;
+}
+
+/* map of image `from` into image `to` (x_to ~ M x_from) from entry q */
+static int pair_map(const int32_t* pairs, const double* HM, int q, int from, double* M)
+{
+    if (pairs[2 * q] == from) { memcpy(M, HM + 9 * q, sizeof(double) * 9); return 0; }
+    return inv3(HM + 9 * q, M);
+}
+
+int or_mosaic_plan(int N, const int32_t* pairs, int P, const double* HM, const uint8_t* valid, const int* Hs,
+                   const int* Ws, double* G, int32_t* round_of, int32_t* ref_of, int* canvas_w, int* canvas_h)
+{
+    if (N < 1 || P < 0) return -1;
+    int* deg = (int*)calloc((size_t)N, sizeof(int));
+    for (int q = 0; q < P; ++q)
+        if (valid[q]) { deg[pairs[2 * q]]++; deg[pairs[2 * q + 1]]++; }
+    for (int i = 0; i < N; ++i) { round_of[i] = -1; ref_of[i] = -1; }
+    double* Gr = (double*)calloc((size_t)N * 9, sizeof(double));
+    int placed = 0;
+    for (int rnd = 0; placed < N; ++rnd) {
+        int ref = -1, via = -1;
+        for (int i = 0; i < N; ++i) {
+            if (round_of[i] >= 0) continue;
+            int link = -1;
+            if (rnd > 0)
+                for (int q = 0; q < P; ++q) {
+                    if (!valid[q]) continue;
+                    int o = pairs[2 * q] == i ? pairs[2 * q + 1] : (pairs[2 * q + 1] == i ? pairs[2 * q] : -1);
+                    if (o >= 0 && round_of[o] >= 0 && (link < 0 || o < pairs[2 * link] + pairs[2 * link + 1] - i))
+                        link = q;
+                }
+            if (rnd > 0 && link < 0) continue;
+            if (ref < 0 || deg[i] > deg[ref]) { ref = i; via = link; }
+        }
+        if (ref < 0) break;
+        if (rnd == 0) {
+            for (int k = 0; k < 9; ++k) Gr[9 * ref + k] = (k % 4 == 0) ? 1.0 : 0.0;
+        } else {
+            const int o = pairs[2 * via] == ref ? pairs[2 * via + 1] : pairs[2 * via];
+            double M[9];
+            if (pair_map(pairs, HM, via, ref, M)) break;          /* ref -> o */
+            mat3_mul(Gr + 9 * o, M, Gr + 9 * ref);
+        }
+        round_of[ref] = rnd; ref_of[ref] = ref; ++placed;
+        for (int q = 0; q < P; ++q) {
+            if (!valid[q]) continue;
+            int j = pairs[2 * q] == ref ? pairs[2 * q + 1] : (pairs[2 * q + 1] == ref ? pairs[2 * q] : -1);
+            if (j < 0 || round_of[j] >= 0) continue;
+            double M[9];
+            if (pair_map(pairs, HM, q, j, M)) continue;            /* j -> ref */
+            mat3_mul(Gr + 9 * ref, M, Gr + 9 * j);
+            round_of[j] = rnd; ref_of[j] = ref; ++placed;
+        }
+    }
+    double x0 = INFINITY, y0 = INFINITY, x1 = -INFINITY, y1 = -INFINITY;
+    for (int i = 0; i < N; ++i) {
+        if (round_of[i] < 0) continue;
+        const double cx[4] = {0, Ws[i] - 1.0, 0, Ws[i] - 1.0}, cy[4] = {0, 0, Hs[i] - 1.0, Hs[i] - 1.0};
+        for (int c = 0; c < 4; ++c) {
+            const double* g = Gr + 9 * i;
+            const double w = g[6] * cx[c] + g[7] * cy[c] + g[8];
+            const double x = (g[0] * cx[c] + g[1] * cy[c] + g[2]) / w, y = (g[3] * cx[c] + g[4] * cy[c] + g[5]) / w;
+            x0 = fmin(x0, x); x1 = fmax(x1, x); y0 = fmin(y0, y); y1 = fmax(y1, y);
+        }
+    }
+    const double fx = floor(x0), fy = floor(y0);
+    *canvas_w = placed ? (int)(ceil(x1) - fx) + 1 : 0;
+    *canvas_h = placed ? (int)(ceil(y1) - fy) + 1 : 0;
+    const double T[9] = {1, 0, -fx, 0, 1, -fy, 0, 0, 1};
+    for (int i = 0; i < N; ++i) {
+        if (round_of[i] < 0) { memset(G + 9 * i, 0, sizeof(double) * 9); continue; }
+        mat3_mul(T, Gr + 9 * i, G + 9 * i);
+    }
+    free(deg);
+    free(Gr);
+    return 0;
+}
+
+/* Canvas pixel (x, y): every placed image i whose inverse placement maps the
+ * pixel inside [0, W-1] x [0, H-1] (w > 0) contributes its bilinear sample;
+ * the canvas value is the mean, rounded half up, and 0 where nothing covers;
+ * cover[] counts the contributions. */
+int or_mosaic_render(int N, const uint8_t* const* imgs, const int* Hs, const int* Ws, const int* pitches, int C,
+                     const double* G, const int32_t* round_of, int cw, int ch, uint8_t* canvas, uint8_t* cover)
+{
+    double* Gi = (double*)malloc(sizeof(double) * 9 * (size_t)(N > 0 ? N : 1));
+    for (int i = 0; i < N; ++i)
+        if (round_of[i] >= 0 && inv3(G + 9 * i, Gi + 9 * i)) { free(Gi); return -1; }
+    for (int y = 0; y < ch; ++y)
+        for (int x = 0; x < cw; ++x) {
+            double sum[4] = {0, 0, 0, 0};
+            int n = 0;
+            for (int i = 0; i < N; ++i) {
+                if (round_of[i] < 0) continue;
+                const double* m = Gi + 9 * i;
+                const double w = m[6] * x + m[7] * y + m[8];
+                if (!(w > 0)) continue;
+                const double u = (m[0] * x + m[1] * y + m[2]) / w, v = (m[3] * x + m[4] * y + m[5]) / w;
+                if (!(u >= 0 && v >= 0 && u <= Ws[i] - 1 && v <= Hs[i] - 1)) continue;
+                const int u0 = (int)floor(u), v0 = (int)floor(v);
+                const int u1 = u0 + 1 < Ws[i] ? u0 + 1 : u0, v1 = v0 + 1 < Hs[i] ? v0 + 1 : v0;
+                const double fu = u - u0, fv = v - v0;
+                for (int c = 0; c < C; ++c) {
+                    const uint8_t* I = imgs[i];
+                    const double p00 = I[(size_t)v0 * pitches[i] + (size_t)u0 * C + c];
+                    const double p01 = I[(size_t)v0 * pitches[i] + (size_t)u1 * C + c];
+                    const double p10 = I[(size_t)v1 * pitches[i] + (size_t)u0 * C + c];
+                    const double p11 = I[(size_t)v1 * pitches[i] + (size_t)u1 * C + c];
+                    const double top = p00 + fu * (p01 - p00), bot = p10 + fu * (p11 - p10);
+                    sum[c] += top + fv * (bot - top);
+                }
+                ++n;
+            }
+            for (int c = 0; c < C; ++c) canvas[((size_t)y * cw + x) * C + c] = n ? (uint8_t)floor(sum[c] / n + 0.5) : 0;
+            if (cover) cover[(size_t)y * cw + x] = (uint8_t)n;
+        }
+    free(Gi);
+    return 0;
+}

@@ -118,6 +118,16 @@ int or_guided_stop(uint64_t s_in, uint64_t total, int Tg);
 int or_ransac_prior(const double* pts, int64_t M, const float* prob, int Tg, int T, double thresh, uint64_t seed,
                     uint32_t pair_id, double* H, uint8_t* inl, int32_t* n_in, int32_t* best_t, int32_t* iters,
                     int32_t* counts);
+/* Sec. 4 mosaic (readings in lp_oracle.c): rounds of reference selection over
+ * H_M (pairs host int32[P*2], HM double[P*9], valid uint8[P]) and placements G
+ * (double[N*9], image pixel -> canvas pixel) on a canvas_w x canvas_h canvas. */
+int or_mosaic_plan(int N, const int32_t* pairs, int P, const double* HM, const uint8_t* valid, const int* Hs,
+                   const int* Ws, double* G, int32_t* round_of, int32_t* ref_of, int* canvas_w, int* canvas_h);
+/* Mean of the bilinear samples of every placed image covering each canvas
+ * pixel (rounded half up, 0 where none); cover (or NULL) counts them. */
+int or_mosaic_render(int N, const uint8_t* const* imgs, const int* Hs, const int* Ws, const int* pitches, int C,
+                     const double* G, const int32_t* round_of, int cw, int ch, uint8_t* canvas, uint8_t* cover);
+
 #ifdef __cplusplus
 }
 #endif
