@@ -239,6 +239,39 @@ LP_API int lp_stitch_pairs_ids(lp_ctx* ctx, const lp_image* imgs, int N, const i
                                const uint32_t* pair_ids, int P, double* HM, int32_t* n_in, uint8_t* valid,
                                int32_t* M_out, void* stream);
 
+/* Sec. 4 mosaic rounds (host only, synchronous).  The image of largest degree
+ * (number of valid H_M entries; lowest index on ties) is the first reference;
+ * it and every image matched with it are placed in its frame through their H_M
+ * entries.  Each later round takes, among unmatched images with a valid entry
+ * to a placed image, the one of largest degree, places it through that entry
+ * (to the placed image of lowest index) and then its unmatched neighbours
+ * through it.  Images that never connect stay unplaced.
+ *  pairs, HM, valid  host: the P pairs (a, b), their H (x_b ~ H x_a, double[9]
+ *                    each) and validity, as lp_stitch_pairs returns them
+ *  Hs, Ws            host int32[N] image sizes
+ *  G                 host double[N*9] out: image pixel -> canvas pixel (zero
+ *                    for an unplaced image)
+ *  round_of, ref_of  host int32[N] out: round of each image (-1 unplaced) and
+ *                    the reference it was placed through
+ *  canvas_w/h        out: the integer bounding box of the placed corner pixels
+ * Errors: LP_ERR_ARG (N outside 1..64, bad pair index or size),
+ * LP_ERR_UNSUPPORTED (canvas side above 32768). */
+LP_API int lp_mosaic_plan(int N, const int32_t* pairs, int P, const double* HM, const uint8_t* valid,
+                          const int32_t* Hs, const int32_t* Ws, double* G, int32_t* round_of, int32_t* ref_of,
+                          int32_t* canvas_w, int32_t* canvas_h);
+
+/* Warp every placed image onto the canvas: each canvas pixel is the mean of
+ * the bilinear samples of the placed images whose inverse placement maps it
+ * inside the image (rounded half up; 0 where none does).
+ *  imgs      host array of N image descriptors (device pixels, same channels)
+ *  G, round_of  lp_mosaic_plan's host outputs
+ *  canvas    device uint8, canvas_h rows of canvas_pitch bytes (>= w * channels)
+ *  cover     device uint8[canvas_w * canvas_h] images per pixel, or NULL
+ * Errors: LP_ERR_ARG, LP_ERR_ALIGN, LP_ERR_CUDA. */
+LP_API int lp_mosaic_render(lp_ctx* ctx, const lp_image* imgs, int N, const double* G, const int32_t* round_of,
+                            uint8_t* canvas, int canvas_w, int canvas_h, int canvas_pitch, uint8_t* cover,
+                            void* stream);
+
 /* ---- learned RANSAC proposal (not in the paper) ----
  * A small network scores each matched pair's chance of being an inlier;
  * RANSAC can then draw its samples in proportion to the score.  Scoring of the

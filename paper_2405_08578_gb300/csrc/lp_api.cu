@@ -703,6 +703,28 @@ int lp_mlp_features(lp_ctx* c, const uint32_t* kpA, const uint8_t* oriA, int HA,
     return LP_OK;
 }
 
+int lp_mosaic_render(lp_ctx* c, const lp_image* imgs, int N, const double* G, const int32_t* round_of,
+                     uint8_t* canvas, int canvas_w, int canvas_h, int canvas_pitch, uint8_t* cover, void* stream)
+{
+    if (!c) return LP_ERR_ARG;
+    if (!imgs || N < 1 || !G || !round_of || canvas_w < 0 || canvas_h < 0) return fail(c, LP_ERR_ARG, "bad arguments");
+    const int ch = imgs[0].channels;
+    for (int i = 0; i < N; ++i) {
+        if (round_of[i] < 0) continue;
+        int r = check_image(c, imgs[i].data, imgs[i].H, imgs[i].W, imgs[i].pitch, imgs[i].channels);
+        if (r) return r;
+        if (imgs[i].channels != ch) return fail(c, LP_ERR_ARG, "images differ in channel count");
+    }
+    if (canvas_w > 0 && canvas_h > 0 && (!canvas || canvas_pitch < canvas_w * ch))
+        return fail(c, LP_ERR_ARG, "canvas pointer or pitch");
+    c->last = S(stream);
+    int bad = 0;
+    LP_CUDA(c, lp::launch_mosaic_render(imgs, N, G, round_of, canvas, canvas_w, canvas_h, canvas_pitch, cover,
+                                        S(stream), &bad));
+    if (bad) return fail(c, LP_ERR_ARG, "more than 64 images or a singular placement");
+    return LP_OK;
+}
+
 int lp_set_profiling(lp_ctx* c, int on)
 {
     if (!c) return LP_ERR_ARG;

@@ -77,6 +77,10 @@ cudaError_t launch_ransac_prior(const float* pts, int64_t M_cap, const int32_t* 
                                 size_t ws_bytes, cudaStream_t s);
 cudaError_t ransac_counts(void* ws, int Ttot, int32_t* host_counts, cudaStream_t s);
 
+// k_mosaic.cu (Sec. 4 canvas); *bad = 1: more than 64 images or a singular placement
+cudaError_t launch_mosaic_render(const lp_image* imgs, int N, const double* G, const int32_t* round_of, uint8_t* canvas,
+                                 int cw, int ch, int pitch, uint8_t* cover, cudaStream_t s, int* bad);
+
 // k_mlp.cu (learned proposal)
 constexpr int kMlpParams = 4801;
 struct MlpScales {

@@ -46,7 +46,8 @@ SYMBOLS = ["lp_config_default", "lp_create", "lp_destroy", "lp_num_keypoints", "
            "lp_last_error", "lp_diag_last_rescans", "lp_diag_orient_bins", "lp_diag_orient_weights", "lp_diag_philox", "lp_diag_gray",
            "lp_mlp_create", "lp_mlp_destroy", "lp_mlp_set_params", "lp_mlp_get_params", "lp_mlp_get_state", "lp_mlp_save",
            "lp_mlp_load", "lp_mlp_features", "lp_mlp_forward", "lp_mlp_train_step", "lp_ransac_prior",
-           "lp_diag_last_ransac_counts", "lp_set_proposal", "lp_set_profiling", "lp_diag_last_match_kernel_ms"]
+           "lp_diag_last_ransac_counts", "lp_set_proposal", "lp_set_profiling", "lp_diag_last_match_kernel_ms",
+           "lp_mosaic_plan", "lp_mosaic_render"]
 MLP_PARAMS = 4801
 
 
@@ -101,6 +102,8 @@ def load(build_if_missing: bool = True):
         "lp_diag_last_ransac_counts": (i32, [P, P, i32]),
         "lp_set_proposal": (i32, [P, P, i32]),
         "lp_set_profiling": (i32, [P, i32]),
+        "lp_mosaic_plan": (i32, [i32, P, i32, P, P, P, P, P, P, P, P, P]),
+        "lp_mosaic_render": (i32, [P, P, i32, P, P, P, i32, i32, i32, P, P]),
         "lp_diag_last_match_kernel_ms": (i32, [P, C.POINTER(C.c_float)]),
     }
     for name, (res, args) in sig.items():
@@ -262,6 +265,17 @@ class Context:
         self._chk(self.lib.lp_diag_last_match_kernel_ms(self.h, C.byref(v)), "lp_diag_last_match_kernel_ms")
         return v.value
 
+    def lp_mosaic_render(self, images, G, round_of, canvas, canvas_w, canvas_h, canvas_pitch, cover=None,
+                         stream=None):
+        """images: list of (device uint8 tensor, H, W, pitch, channels); G, round_of: lp_mosaic_plan's."""
+        arr = (lp_image * len(images))(*[lp_image(_ptr(t), H, W, p, ch) for (t, H, W, p, ch) in images])
+        Gh = np.ascontiguousarray(G, np.float64).reshape(-1)
+        r = np.ascontiguousarray(round_of, np.int32)
+        self._chk(self.lib.lp_mosaic_render(self.h, C.cast(arr, C.c_void_p), len(images),
+                                            Gh.ctypes.data_as(C.c_void_p), r.ctypes.data_as(C.c_void_p), _ptr(canvas),
+                                            int(canvas_w), int(canvas_h), int(canvas_pitch), _ptr(cover),
+                                            _stream(stream)), "lp_mosaic_render")
+
     def lp_sync_status(self):
         return self.lib.lp_sync_status(self.h)
 
@@ -327,6 +341,27 @@ class Mlp:
     def lp_mlp_train_step(self, feat, label, B, lr, loss=None, stream=None):
         self._chk(self.lib.lp_mlp_train_step(self.h, _ptr(feat), _ptr(label), B, float(lr), _ptr(loss),
                                              _stream(stream)), "lp_mlp_train_step")
+
+
+def lp_mosaic_plan(n_images, pairs, HM, valid, sizes):
+    """Sec. 4 rounds on the host.  pairs [(a, b)], HM [P, 9] or [P, 3, 3] (host
+    arrays), valid [P], sizes [(H, W)].  Returns dict(G [N, 3, 3], round [N],
+    ref [N], canvas (h, w))."""
+    pr = np.ascontiguousarray(np.asarray(pairs, np.int32).reshape(-1, 2))
+    Hm = np.ascontiguousarray(np.asarray(HM, np.float64).reshape(-1, 9))
+    v = np.ascontiguousarray(np.asarray(valid, np.uint8))
+    Hs = np.ascontiguousarray([s[0] for s in sizes], np.int32)
+    Ws = np.ascontiguousarray([s[1] for s in sizes], np.int32)
+    G = np.zeros((n_images, 9), np.float64)
+    rnd = np.zeros(n_images, np.int32)
+    ref = np.zeros(n_images, np.int32)
+    cw, ch = C.c_int32(), C.c_int32()
+    vp = lambda a: a.ctypes.data_as(C.c_void_p)  # noqa: E731
+    r = load().lp_mosaic_plan(int(n_images), vp(pr), len(pr), vp(Hm), vp(v), vp(Hs), vp(Ws), vp(G), vp(rnd), vp(ref),
+                              C.byref(cw), C.byref(ch))
+    if r != LP_OK:
+        raise LpError(r, "lp_mosaic_plan")
+    return dict(G=G.reshape(-1, 3, 3), round=rnd, ref=ref, canvas=(ch.value, cw.value))
 
 
 def lp_num_keypoints(H, W, Ls) -> int:
