@@ -312,9 +312,58 @@ def fp32_form_and_batch(args, rank):
         t += a.elapsed_time(b) / 1e3
     out["batch_3x3"] = {"images": 9, "pairs": 36, "pairs_per_s": 36 * k / t, "ms_per_batch": 1e3 * t / k,
                         "valid_pairs": int(va.sum().item()), "graph": True}
+    out["mosaic_3x3"] = mosaic(bt, images, ctx, HM, va, flush, k)
     if args.train_pairs > 0:
         out["learned_proposal"] = learned_proposal(args, bt, images, ctx, HM, ni, va, flush, k)
     return out
+
+
+def mosaic(bt, images, ctx, HM, va, flush, k):
+    """Sec. 4 on the nine-tile batch: the reference rounds over H_M (host) and
+    the canvas warp (device), timed after the batch's H_M."""
+    import torch
+
+    from paper_2405_08578_gb300 import lp, shard
+    pairs = shard.all_pairs(9)
+    HMh, vh = HM.cpu().numpy(), va.cpu().numpy()
+    t0 = time.perf_counter()
+    plan = lp.lp_mosaic_plan(9, pairs, HMh, vh, [(H_IMG, W_IMG)] * 9)
+    plan_ms = 1e3 * (time.perf_counter() - t0)
+    ch, cw = plan["canvas"]
+    pitch = (cw * 3 + 15) // 16 * 16
+    canvas = torch.empty((ch, pitch), dtype=torch.uint8, device="cuda")
+    s = torch.cuda.current_stream()
+    for _ in range(2):
+        ctx.lp_mosaic_render(images, plan["G"], plan["round"], canvas, cw, ch, pitch)
+    torch.cuda.synchronize()
+    t = 0.0
+    for _ in range(k):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        ctx.lp_mosaic_render(images, plan["G"], plan["round"], canvas, cw, ch, pitch)
+        e1.record(s)
+        torch.cuda.synchronize()
+        t += e0.elapsed_time(e1) / 1e3
+    placed = int((plan["round"] >= 0).sum())
+    # each tile against the reference it was placed through, on their true overlap
+    gy, gx = np.mgrid[0:H_IMG:64, 0:W_IMG:64]
+    grid = np.c_[gx.ravel(), gy.ravel(), np.ones(gx.size)]
+    err = 0.0
+    for j, r in enumerate(plan["ref"]):
+        if r < 0 or r == j:
+            continue
+        q = grid @ bt.H[(j, r)].T
+        q = q[:, :2] / q[:, 2:]
+        inside = (q[:, 0] >= 0) & (q[:, 0] <= W_IMG - 1) & (q[:, 1] >= 0) & (q[:, 1] <= H_IMG - 1)
+        a = grid[inside] @ plan["G"][j].T
+        b = np.c_[q[inside], np.ones(inside.sum())] @ plan["G"][r].T
+        if len(a):
+            err = max(err, float(np.abs(a[:, :2] / a[:, 2:] - b[:, :2] / b[:, 2:]).max()))
+    bytes_alg = ch * cw * 3 + placed * H_IMG * W_IMG * 3
+    return {"placed": placed, "rounds": int(plan["round"].max()) + 1, "canvas": [ch, cw], "plan_ms": round(plan_ms, 3),
+            "placement_err_px": round(err, 2),
+            "render_ms": 1e3 * t / k, "render_GBps_algorithmic": bytes_alg / (t / k) / 1e9}
 
 
 def learned_proposal(args, bt, images, ctx, HM, ni, va, flush, k):
@@ -458,6 +507,7 @@ def main():
         line["config"]["speedup_vs_fp32_form"] = value / world / extra["fp32_form_pairs_per_s"]
         line["config"]["fp32_form_inliers"] = extra["fp32_form_inliers"]
         line["config"]["batch_3x3"] = extra["batch_3x3"]
+        line["config"]["mosaic_3x3"] = extra["mosaic_3x3"]
         if "learned_proposal" in extra:
             line["config"]["learned_proposal"] = extra["learned_proposal"]
     if world == 1 and not args.no_cpu_baseline:
