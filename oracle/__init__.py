@@ -59,6 +59,10 @@ def lib():
             "or_eig_sym": (i32, [i32, P, P, P]),
             "or_score": (i64, [P, P, i64, f64, P]),
             "or_ransac": (i32, [P, i64, i32, f64, C.c_uint64, u32, P, P, P, P, P, P]),
+            "or_ransac_model": (i32, [P, i64, i32, i32, f64, C.c_uint64, u32, P, P, P, P, P, P]),
+            "or_ransac_sample_k": (i32, [i64, C.c_uint64, u32, i32, i32, P]),
+            "or_rigid_fit": (i32, [P, P, i64, P]),
+            "or_model_sample_size": (i32, [i32]),
             "or_mlp_features": (i32, [i64, P, P, P, i32, P, P, P, i32, i32, i32, i32, P]),
             "or_mlp_forward": (i32, [P, P, i64, P, P]),
             "or_mlp_loss_grad": (i32, [P, P, P, i64, P, P]),
@@ -66,7 +70,10 @@ def lib():
             "or_guided_weights": (i32, [P, i64, P]),
             "or_ransac_sample_guided": (i32, [i64, P, C.c_uint64, u32, i32, P]),
             "or_ransac_prior": (i32, [P, i64, P, i32, i32, f64, C.c_uint64, u32, P, P, P, P, P, P]),
+            "or_ransac_prior_model": (i32, [P, i64, i32, P, i32, i32, f64, C.c_uint64, u32, P, P, P, P, P, P]),
             "or_guided_stop": (i32, [C.c_uint64, C.c_uint64, i32]),
+            "or_guided_stop_k": (i32, [C.c_uint64, C.c_uint64, i32, i32]),
+            "or_ransac_sample_guided_k": (i32, [i64, P, C.c_uint64, u32, i32, i32, P]),
             "or_mosaic_plan": (i32, [i32, P, i32, P, P, P, P, P, P, P, P, P]),
             "or_mosaic_render": (i32, [i32, P, P, P, P, i32, P, P, i32, i32, P, P]),
         }
@@ -193,10 +200,24 @@ def philox4x32_10(ctr, key) -> np.ndarray:
     return out
 
 
-def ransac_sample(M: int, seed: int, pair_id: int, t: int):
-    s = np.empty(4, np.int32)
-    r = lib().or_ransac_sample(M, seed, pair_id, t, _p(s))
+def ransac_sample(M: int, seed: int, pair_id: int, t: int, k: int = 4):
+    s = np.empty(k, np.int32)
+    r = lib().or_ransac_sample_k(M, seed, pair_id, t, k, _p(s))
     return None if r else s
+
+
+# Sec. 2.5 models: Eq. 7 homography (4-match samples), Eq. 8 rigid (2-match samples)
+MODEL_HOMOGRAPHY = 0
+MODEL_RIGID = 1
+
+
+def rigid_fit(pts, mask=None):
+    """Least-squares Eq. 8 (rotation + translation) of the masked rows of pts."""
+    p = _c(pts, np.float64).reshape(-1, 4)
+    m = _c(np.ones(len(p), np.uint8) if mask is None else mask, np.uint8)
+    H = np.empty(9, np.float64)
+    r = lib().or_rigid_fit(_p(p), _p(m), len(p), _p(H))
+    return None if r else H.reshape(3, 3)
 
 
 def dlt4(src, dst):
@@ -232,7 +253,8 @@ def score(H, pts, thresh: float = 3.0):
     return int(n), m
 
 
-def ransac(pts, T: int = 1000, thresh: float = 3.0, seed: int = 0, pair_id: int = 0, want_all: bool = False):
+def ransac(pts, T: int = 1000, thresh: float = 3.0, seed: int = 0, pair_id: int = 0, want_all: bool = False,
+           model: int = MODEL_HOMOGRAPHY):
     """Returns dict(H, inliers, n_in, best_t[, counts, Hs])."""
     p = _c(pts, np.float64).reshape(-1, 4)
     M = len(p)
@@ -242,8 +264,8 @@ def ransac(pts, T: int = 1000, thresh: float = 3.0, seed: int = 0, pair_id: int 
     bt = C.c_int32()
     counts = np.empty(T, np.int32) if want_all else None
     Hs = np.empty((T, 9), np.float64) if want_all else None
-    lib().or_ransac(_p(p), M, T, float(thresh), seed, pair_id, _p(H), _p(inl), C.byref(n_in),
-                    C.byref(bt), _p(counts), _p(Hs))
+    lib().or_ransac_model(_p(p), M, int(model), T, float(thresh), seed, pair_id, _p(H), _p(inl), C.byref(n_in),
+                          C.byref(bt), _p(counts), _p(Hs))
     out = dict(H=H.reshape(3, 3), inliers=inl, n_in=int(n_in.value), best_t=int(bt.value))
     if want_all:
         out["counts"] = counts
@@ -276,13 +298,13 @@ def features(img: np.ndarray, Ls, beta0: float = 0.0, upright: bool = False):
 
 
 def stitch_pair(imgA, imgB, Ls, ratio=0.8, T=1000, thresh=3.0, seed=0, pair_id=0, upright=False,
-                delta_s=float("inf")):
+                delta_s=float("inf"), model=MODEL_HOMOGRAPHY):
     """Sec. 2 end to end for one pair (Fig. 2): H from A to B and its inliers."""
     fa = features(imgA, Ls, upright=upright)
     fb = features(imgB, Ls, upright=upright)
     m, d1, d2, _, _ = match(fa["desc"], fa["valid"], fb["desc"], fb["valid"], ratio, delta_s)
     pts, rows = match_points(fa["idx"], fb["idx"], m, fa["gray"].shape[1], fb["gray"].shape[1])
-    r = ransac(pts, T, thresh, seed, pair_id)
+    r = ransac(pts, T, thresh, seed, pair_id, model=model)
     r.update(fa=fa, fb=fb, match=m, d1=d1, d2=d2, pts=pts, rows=rows)
     return r
 
@@ -347,14 +369,15 @@ def guided_weights(prob):
     return out
 
 
-def ransac_sample_guided(prefix, seed, pair_id, t):
+def ransac_sample_guided(prefix, seed, pair_id, t, k=4):
     pf = _c(prefix, np.uint64)
-    s = np.empty(4, np.int32)
-    r = lib().or_ransac_sample_guided(len(pf), _p(pf), seed, pair_id, t, _p(s))
+    s = np.empty(k, np.int32)
+    r = lib().or_ransac_sample_guided_k(len(pf), _p(pf), seed, pair_id, t, k, _p(s))
     return None if r else s
 
 
-def ransac_prior(pts, prob, Tg=64, T=1000, thresh=3.0, seed=0, pair_id=0, want_counts=False):
+def ransac_prior(pts, prob, Tg=64, T=1000, thresh=3.0, seed=0, pair_id=0, want_counts=False,
+                 model=MODEL_HOMOGRAPHY):
     """Guided phase of Tg hypotheses, then uniform fallback of T (see lp_oracle.h)."""
     p = _c(pts, np.float64).reshape(-1, 4)
     pr = _c(prob, np.float32)
@@ -365,16 +388,16 @@ def ransac_prior(pts, prob, Tg=64, T=1000, thresh=3.0, seed=0, pair_id=0, want_c
     bt = C.c_int32()
     it = C.c_int32()
     counts = np.empty(Tg + T, np.int32) if want_counts else None
-    lib().or_ransac_prior(_p(p), M, _p(pr), int(Tg), int(T), float(thresh), seed, pair_id, _p(H), _p(inl),
-                          C.byref(n_in), C.byref(bt), C.byref(it), _p(counts))
+    lib().or_ransac_prior_model(_p(p), M, int(model), _p(pr), int(Tg), int(T), float(thresh), seed, pair_id, _p(H),
+                                _p(inl), C.byref(n_in), C.byref(bt), C.byref(it), _p(counts))
     out = dict(H=H.reshape(3, 3), inliers=inl[:M], n_in=int(n_in.value), best_t=int(bt.value), iters=int(it.value))
     if want_counts:
         out["counts"] = counts
     return out
 
 
-def guided_stop(s_in, total, Tg) -> bool:
-    return bool(lib().or_guided_stop(int(s_in), int(total), int(Tg)))
+def guided_stop(s_in, total, Tg, k=4) -> bool:
+    return bool(lib().or_guided_stop_k(int(s_in), int(total), int(Tg), int(k)))
 
 
 def mosaic_plan(n_images, pairs, HM, valid, sizes):

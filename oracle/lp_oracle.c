@@ -357,22 +357,27 @@ void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out
  * with counter (t, block, 0, 0); word j of the stream is word j%4 of block
  * j/4; index = floor(word * M / 2^32); repeated indices are redrawn, at most
  * 64 words per iteration, after which the iteration is skipped. */
-int or_ransac_sample(int64_t M, uint64_t seed, uint32_t pair_id, int t, int32_t* idx4)
+int or_ransac_sample_k(int64_t M, uint64_t seed, uint32_t pair_id, int t, int k, int32_t* idx)
 {
     uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32) ^ pair_id};
     uint32_t blk[4];
     int n = 0;
-    for (int j = 0; j < 64 && n < 4; ++j) {
+    for (int j = 0; j < 64 && n < k; ++j) {
         if (j % 4 == 0) {
             uint32_t ctr[4] = {(uint32_t)t, (uint32_t)(j / 4), 0u, 0u};
             or_philox4x32_10(ctr, key, blk);
         }
         int32_t i = (int32_t)(((uint64_t)blk[j % 4] * (uint64_t)M) >> 32);
         int dup = 0;
-        for (int q = 0; q < n; ++q) dup |= idx4[q] == i;
-        if (!dup) idx4[n++] = i;
+        for (int q = 0; q < n; ++q) dup |= idx[q] == i;
+        if (!dup) idx[n++] = i;
     }
-    return n == 4 ? 0 : 1;
+    return n == k ? 0 : 1;
+}
+
+int or_ransac_sample(int64_t M, uint64_t seed, uint32_t pair_id, int t, int32_t* idx4)
+{
+    return or_ransac_sample_k(M, seed, pair_id, t, 4, idx4);
 }
 
 /* Hartley normalisation: centroid to 0, mean distance to sqrt(2). */
@@ -581,15 +586,87 @@ static int collinear(const double* p, const double* q, const double* r)
     return fabs(cr) <= 1e-9 * (ux * ux + uy * uy + vx * vx + vy * vy);
 }
 
+/* Eq. 8 by least squares: the rotation theta and translation (t_x, t_y) that
+ * minimise sum |R(theta) p_A + t - p_B|^2 over the masked correspondences.
+ * With a and b the coordinates minus their centroids, the sum equals a
+ * constant minus 2 (cos(theta) C + sin(theta) S), C = sum a.b and
+ * S = sum (a_x b_y - a_y b_x), so (cos, sin) = (C, S) / sqrt(C^2 + S^2), and
+ * t = centroid_B - R centroid_A.  Two correspondences give the minimal sample
+ * of the rigid model.  Returns 0, or 1 for fewer than two correspondences or
+ * C = S = 0 (all points of one image on one spot). */
+int or_rigid_fit(const double* pts, const uint8_t* mask, int64_t M, double* H)
+{
+    int64_t n = 0;
+    double sxa = 0, sya = 0, sxb = 0, syb = 0;
+    for (int64_t i = 0; i < M; ++i)
+        if (mask[i]) {
+            ++n;
+            sxa += pts[4 * i]; sya += pts[4 * i + 1]; sxb += pts[4 * i + 2]; syb += pts[4 * i + 3];
+        }
+    if (n < 2) return 1;
+    const double cxa = sxa / n, cya = sya / n, cxb = sxb / n, cyb = syb / n;
+    double Cs = 0, Ss = 0;
+    for (int64_t i = 0; i < M; ++i)
+        if (mask[i]) {
+            const double ax = pts[4 * i] - cxa, ay = pts[4 * i + 1] - cya;
+            const double bx = pts[4 * i + 2] - cxb, by = pts[4 * i + 3] - cyb;
+            Cs += ax * bx + ay * by;
+            Ss += ax * by - ay * bx;
+        }
+    const double r = sqrt(Cs * Cs + Ss * Ss);
+    if (!(r > 0)) return 1;
+    const double c = Cs / r, sn = Ss / r;
+    H[0] = c;  H[1] = -sn; H[2] = cxb - (c * cxa - sn * cya);
+    H[3] = sn; H[4] = c;   H[5] = cyb - (sn * cxa + c * cya);
+    H[6] = 0;  H[7] = 0;   H[8] = 1;
+    return 0;
+}
+
+int or_model_sample_size(int model) { return model == OR_MODEL_RIGID ? 2 : 4; }
+
+/* The hypothesis of one minimal sample s[] (Sec. 2.5).  Eq. 7: four
+ * correspondences by the DLT, skipped when three of them are collinear in
+ * either image.  Eq. 8: two correspondences by or_rigid_fit.  Returns 0, or 1
+ * when the sample is degenerate. */
+static int hypothesis(int model, const double* pts, const int32_t* s, double* Ht)
+{
+    if (model == OR_MODEL_RIGID) {
+        double sub[8];
+        const uint8_t both[2] = {1, 1};
+        for (int j = 0; j < 2; ++j) memcpy(sub + 4 * j, pts + 4 * (size_t)s[j], sizeof(double) * 4);
+        return or_rigid_fit(sub, both, 2, Ht);
+    }
+    double src[8], dst[8];
+    for (int j = 0; j < 4; ++j) {
+        src[2 * j] = pts[4 * s[j]]; src[2 * j + 1] = pts[4 * s[j] + 1];
+        dst[2 * j] = pts[4 * s[j] + 2]; dst[2 * j + 1] = pts[4 * s[j] + 3];
+    }
+    for (int a = 0; a < 4; ++a) {
+        int i0 = (a + 1) % 4, i1 = (a + 2) % 4, i2 = (a + 3) % 4;
+        if (collinear(src + 2 * i0, src + 2 * i1, src + 2 * i2) || collinear(dst + 2 * i0, dst + 2 * i1, dst + 2 * i2))
+            return 1;
+    }
+    return or_dlt4(src, dst, Ht);
+}
+
+/* Least-squares fit of the model to the masked correspondences. */
+static int refit_model(int model, const double* pts, const uint8_t* mask, int64_t M, double* H)
+{
+    return model == OR_MODEL_RIGID ? or_rigid_fit(pts, mask, M, H) : or_refit(pts, mask, M, H);
+}
+
 /* Sec. 2.5: RANSAC over the matched pairs with the homography of Eq. 7.
  * Readings: a full 8-DOF homography (Eq. 8's rigid form is a special case);
  * T iterations (no adaptive stop); a sample with three collinear points in
  * either image, or a singular system, is skipped; the hypothesis with the most
  * inliers wins, the earliest on ties; the winner's inliers are refitted once
- * by least squares, and the final inlier set is taken from the refitted H. */
-int or_ransac(const double* pts, int64_t M, int T, double thresh, uint64_t seed, uint32_t pair_id,
-              double* H, uint8_t* inl, int32_t* n_in, int32_t* best_t, int32_t* counts, double* Hs)
+ * by least squares, and the final inlier set is taken from the refitted H.
+ * or_ransac_model runs the same loop with Eq. 8's rigid model, drawing two
+ * matches per iteration (the first two distinct indices of the same stream). */
+int or_ransac_model(const double* pts, int64_t M, int model, int T, double thresh, uint64_t seed, uint32_t pair_id,
+                    double* H, uint8_t* inl, int32_t* n_in, int32_t* best_t, int32_t* counts, double* Hs)
 {
+    const int k = or_model_sample_size(model);
     memset(H, 0, sizeof(double) * 9);
     *n_in = 0;
     *best_t = -1;
@@ -597,26 +674,14 @@ int or_ransac(const double* pts, int64_t M, int T, double thresh, uint64_t seed,
     if (counts)
         for (int t = 0; t < T; ++t) counts[t] = -1;
     if (Hs) memset(Hs, 0, sizeof(double) * 9 * (size_t)T);
-    if (M < 4) return 1;
+    if (M < k) return 1;
     int64_t bestc = -1;
     double Hb[9];
     for (int t = 0; t < T; ++t) {
         int32_t s[4];
-        if (or_ransac_sample(M, seed, pair_id, t, s)) continue;
-        double src[8], dst[8];
-        for (int j = 0; j < 4; ++j) {
-            src[2 * j] = pts[4 * s[j]]; src[2 * j + 1] = pts[4 * s[j] + 1];
-            dst[2 * j] = pts[4 * s[j] + 2]; dst[2 * j + 1] = pts[4 * s[j] + 3];
-        }
-        int deg = 0;
-        for (int a = 0; a < 4; ++a) {
-            int i0 = (a + 1) % 4, i1 = (a + 2) % 4, i2 = (a + 3) % 4;
-            deg |= collinear(src + 2 * i0, src + 2 * i1, src + 2 * i2);
-            deg |= collinear(dst + 2 * i0, dst + 2 * i1, dst + 2 * i2);
-        }
-        if (deg) continue;
+        if (or_ransac_sample_k(M, seed, pair_id, t, k, s)) continue;
         double Ht[9];
-        if (or_dlt4(src, dst, Ht)) continue;
+        if (hypothesis(model, pts, s, Ht)) continue;
         int64_t c = or_score(Ht, pts, M, thresh, NULL);
         if (counts) counts[t] = (int32_t)c;
         if (Hs) memcpy(Hs + 9 * t, Ht, sizeof Ht);
@@ -630,12 +695,18 @@ int or_ransac(const double* pts, int64_t M, int T, double thresh, uint64_t seed,
     uint8_t* m = (uint8_t*)malloc((size_t)M);
     or_score(Hb, pts, M, thresh, m);
     double Hf[9];
-    if (or_refit(pts, m, M, Hf)) memcpy(Hf, Hb, sizeof Hf);
+    if (refit_model(model, pts, m, M, Hf)) memcpy(Hf, Hb, sizeof Hf);
     *n_in = (int32_t)or_score(Hf, pts, M, thresh, m);
     if (inl) memcpy(inl, m, (size_t)M);
     free(m);
     memcpy(H, Hf, sizeof Hf);
     return 0;
+}
+
+int or_ransac(const double* pts, int64_t M, int T, double thresh, uint64_t seed, uint32_t pair_id,
+              double* H, uint8_t* inl, int32_t* n_in, int32_t* best_t, int32_t* counts, double* Hs)
+{
+    return or_ransac_model(pts, M, OR_MODEL_HOMOGRAPHY, T, thresh, seed, pair_id, H, inl, n_in, best_t, counts, Hs);
 }
 
 /* ------------------------------------------------------------------ */
@@ -779,13 +850,14 @@ int or_guided_weights(const float* prob, int64_t M, uint64_t* prefix)
  * match whose prefix interval contains floor(word * total / 2^32): probability
  * proportional to q_i.  Repeated indices are redrawn (sampling without
  * replacement), at most 64 words. */
-int or_ransac_sample_guided(int64_t M, const uint64_t* prefix, uint64_t seed, uint32_t pair_id, int t, int32_t* idx4)
+int or_ransac_sample_guided_k(int64_t M, const uint64_t* prefix, uint64_t seed, uint32_t pair_id, int t, int k,
+                               int32_t* idx)
 {
     uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32) ^ pair_id};
     uint32_t blk[4];
     const uint64_t total = prefix[M - 1];
     int n = 0;
-    for (int j = 0; j < 64 && n < 4; ++j) {
+    for (int j = 0; j < 64 && n < k; ++j) {
         if (j % 4 == 0) {
             uint32_t ctr[4] = {(uint32_t)t, (uint32_t)(j / 4), 0u, 0u};
             or_philox4x32_10(ctr, key, blk);
@@ -798,24 +870,30 @@ int or_ransac_sample_guided(int64_t M, const uint64_t* prefix, uint64_t seed, ui
         }
         int32_t i = (int32_t)lo;
         int dup = 0;
-        for (int q = 0; q < n; ++q) dup |= idx4[q] == i;
-        if (!dup) idx4[n++] = i;
+        for (int q = 0; q < n; ++q) dup |= idx[q] == i;
+        if (!dup) idx[n++] = i;
     }
-    return n == 4 ? 0 : 1;
+    return n == k ? 0 : 1;
+}
+
+int or_ransac_sample_guided(int64_t M, const uint64_t* prefix, uint64_t seed, uint32_t pair_id, int t, int32_t* idx4)
+{
+    return or_ransac_sample_guided_k(M, prefix, seed, pair_id, t, 4, idx4);
 }
 
 /* Stop test of the guided phase: the standard RANSAC bound T >= log(0.01) /
- * log(1 - w^4), rewritten as (1 - w^4)^T <= 0.01 (the chance that T samples
- * all contained an outlier), with w the prior-weighted inlier fraction
- * s_in / total of the guided winner: the probability that one guided draw
- * lands on an inlier.  Powers by binary exponentiation. */
-int or_guided_stop(uint64_t s_in, uint64_t total, int Tg)
+ * log(1 - w^k), rewritten as (1 - w^k)^T <= 0.01 (the chance that T samples
+ * of k matches all contained an outlier), with w the prior-weighted inlier
+ * fraction s_in / total of the guided winner: the probability that one guided
+ * draw lands on an inlier.  k = 4 for Eq. 7, 2 for Eq. 8.  Powers by binary
+ * exponentiation. */
+int or_guided_stop_k(uint64_t s_in, uint64_t total, int Tg, int k)
 {
-    if (total == 0 || Tg <= 0) return 0;
+    if (total == 0 || Tg <= 0 || (k != 2 && k != 4)) return 0;
     const double w = (double)s_in / (double)total;
     const double w2 = w * w;
-    const double w4 = w2 * w2;
-    double b = 1.0 - w4, r = 1.0;
+    const double wk = k == 2 ? w2 : w2 * w2;
+    double b = 1.0 - wk, r = 1.0;
     for (int e = Tg; e; e >>= 1) {
         if (e & 1) r = r * b;
         b = b * b;
@@ -823,14 +901,17 @@ int or_guided_stop(uint64_t s_in, uint64_t total, int Tg)
     return r <= 0.01;
 }
 
+int or_guided_stop(uint64_t s_in, uint64_t total, int Tg) { return or_guided_stop_k(s_in, total, Tg, 4); }
+
 /* Learned-proposal RANSAC: Tg hypotheses from guided samples are scored by all
  * matches; when the stop test holds for the guided winner, it is refitted as in
  * or_ransac; otherwise the call falls back to uniform RANSAC with T iterations
  * (or_ransac itself, whose best_t is reported offset by Tg). */
-int or_ransac_prior(const double* pts, int64_t M, const float* prob, int Tg, int T, double thresh, uint64_t seed,
-                    uint32_t pair_id, double* H, uint8_t* inl, int32_t* n_in, int32_t* best_t, int32_t* iters,
-                    int32_t* counts /* Tg + T or NULL */)
+int or_ransac_prior_model(const double* pts, int64_t M, int model, const float* prob, int Tg, int T, double thresh,
+                          uint64_t seed, uint32_t pair_id, double* H, uint8_t* inl, int32_t* n_in, int32_t* best_t,
+                          int32_t* iters, int32_t* counts /* Tg + T or NULL */)
 {
+    const int k = or_model_sample_size(model);
     memset(H, 0, sizeof(double) * 9);
     *n_in = 0;
     *best_t = -1;
@@ -842,26 +923,14 @@ int or_ransac_prior(const double* pts, int64_t M, const float* prob, int Tg, int
     double Hb[9];
     int tg = -1;
     uint64_t* prefix = NULL;
-    if (M >= 4) {
+    if (M >= k) {
         prefix = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)M);
         or_guided_weights(prob, M, prefix);
         for (int t = 0; t < Tg; ++t) {
             int32_t s[4];
-            if (or_ransac_sample_guided(M, prefix, seed, pair_id, t, s)) continue;
-            double src[8], dst[8];
-            for (int j = 0; j < 4; ++j) {
-                src[2 * j] = pts[4 * s[j]]; src[2 * j + 1] = pts[4 * s[j] + 1];
-                dst[2 * j] = pts[4 * s[j] + 2]; dst[2 * j + 1] = pts[4 * s[j] + 3];
-            }
-            int deg = 0;
-            for (int a = 0; a < 4; ++a) {
-                int i0 = (a + 1) % 4, i1 = (a + 2) % 4, i2 = (a + 3) % 4;
-                deg |= collinear(src + 2 * i0, src + 2 * i1, src + 2 * i2);
-                deg |= collinear(dst + 2 * i0, dst + 2 * i1, dst + 2 * i2);
-            }
-            if (deg) continue;
+            if (or_ransac_sample_guided_k(M, prefix, seed, pair_id, t, k, s)) continue;
             double Ht[9];
-            if (or_dlt4(src, dst, Ht)) continue;
+            if (hypothesis(model, pts, s, Ht)) continue;
             int64_t c = or_score(Ht, pts, M, thresh, NULL);
             if (counts) counts[t] = (int32_t)c;
             if (c > bestc) {
@@ -878,25 +947,34 @@ int or_ransac_prior(const double* pts, int64_t M, const float* prob, int Tg, int
         uint64_t s_in = 0;
         for (int64_t i = 0; i < M; ++i)
             if (m[i]) s_in += prefix[i] - (i ? prefix[i - 1] : 0);
-        stop = or_guided_stop(s_in, prefix[M - 1], Tg);
+        stop = or_guided_stop_k(s_in, prefix[M - 1], Tg, k);
     }
     free(prefix);
     if (!stop) {
         free(m);
         int32_t bt;
-        int r = or_ransac(pts, M, T, thresh, seed, pair_id, H, inl, n_in, &bt, counts ? counts + Tg : NULL, NULL);
+        int r = or_ransac_model(pts, M, model, T, thresh, seed, pair_id, H, inl, n_in, &bt, counts ? counts + Tg : NULL,
+                                NULL);
         *best_t = bt >= 0 ? Tg + bt : -1;
         return r;
     }
     *iters = Tg;
     *best_t = tg;
     double Hf[9];
-    if (or_refit(pts, m, M, Hf)) memcpy(Hf, Hb, sizeof Hf);
+    if (refit_model(model, pts, m, M, Hf)) memcpy(Hf, Hb, sizeof Hf);
     *n_in = (int32_t)or_score(Hf, pts, M, thresh, m);
     if (inl) memcpy(inl, m, (size_t)M);
     free(m);
     memcpy(H, Hf, sizeof Hf);
     return 0;
+}
+
+int or_ransac_prior(const double* pts, int64_t M, const float* prob, int Tg, int T, double thresh, uint64_t seed,
+                    uint32_t pair_id, double* H, uint8_t* inl, int32_t* n_in, int32_t* best_t, int32_t* iters,
+                    int32_t* counts)
+{
+    return or_ransac_prior_model(pts, M, OR_MODEL_HOMOGRAPHY, prob, Tg, T, thresh, seed, pair_id, H, inl, n_in,
+                                 best_t, iters, counts);
 }
 
 /* ------------------------------------------------------------------ */

@@ -60,6 +60,18 @@ void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out
 
 /* The four sample indices of RANSAC iteration t; returns 0, or 1 if skipped. */
 int or_ransac_sample(int64_t M, uint64_t seed, uint32_t pair_id, int t, int32_t* idx4);
+/* The same stream's first k (2 or 4) distinct indices. */
+int or_ransac_sample_k(int64_t M, uint64_t seed, uint32_t pair_id, int t, int k, int32_t* idx);
+
+/* Models of Sec. 2.5: the homography of Eq. 7 (8 DOF, four matches per sample)
+ * or the rigid transform of Eq. 8 (rotation + translation, two matches). */
+#define OR_MODEL_HOMOGRAPHY 0
+#define OR_MODEL_RIGID 1
+int or_model_sample_size(int model);
+
+/* Least-squares Eq. 8 (rotation + translation) over the masked correspondences;
+ * returns 0, or 1 for fewer than two of them or a degenerate set. */
+int or_rigid_fit(const double* pts /*M x 4*/, const uint8_t* mask, int64_t M, double* H /*9*/);
 
 /* 4-point DLT (h33 = 1) with Hartley normalisation; returns 0, or 1 if singular. */
 int or_dlt4(const double* src /*4x2 (x,y)*/, const double* dst /*4x2*/, double* H /*9*/);
@@ -78,6 +90,9 @@ int64_t or_score(const double* H, const double* pts, int64_t M, double thresh, u
  * model was found (H = 0, n_in = 0).  counts (T) and Hs (T*9) are optional. */
 int or_ransac(const double* pts, int64_t M, int T, double thresh, uint64_t seed, uint32_t pair_id,
               double* H, uint8_t* inl, int32_t* n_in, int32_t* best_t, int32_t* counts, double* Hs);
+/* The same with a model of Sec. 2.5 (OR_MODEL_*). */
+int or_ransac_model(const double* pts, int64_t M, int model, int T, double thresh, uint64_t seed, uint32_t pair_id,
+                    double* H, uint8_t* inl, int32_t* n_in, int32_t* best_t, int32_t* counts, double* Hs);
 
 
 /* ---- learned RANSAC proposal (not in the paper) -- TEST INFRASTRUCTURE ---- */
@@ -104,11 +119,15 @@ int or_mlp_adam(double* params, double* m, double* v, const double* grad, int n,
 /* Guided draw of four distinct matches from integer weights (see lp_oracle.c). */
 int or_ransac_sample_guided(int64_t M, const uint64_t* prefix /* inclusive prefix sums of q */, uint64_t seed,
                             uint32_t pair_id, int t, int32_t* idx4);
+int or_ransac_sample_guided_k(int64_t M, const uint64_t* prefix, uint64_t seed, uint32_t pair_id, int t, int k,
+                              int32_t* idx);
 int or_guided_weights(const float* prob, int64_t M, uint64_t* prefix);
 
 /* Stop test of the guided phase: (1 - w^4)^Tg <= 0.01 with w = s_in / total
  * (the standard bound T >= log(0.01) / log(1 - w^4)). */
 int or_guided_stop(uint64_t s_in, uint64_t total, int Tg);
+/* The same bound for samples of k matches: (1 - w^k)^Tg <= 0.01, k = 2 or 4. */
+int or_guided_stop_k(uint64_t s_in, uint64_t total, int Tg, int k);
 
 /* Tg guided hypotheses (samples drawn with probability proportional to the
  * prior), scored by all matches; the guided winner is refitted when
@@ -118,6 +137,10 @@ int or_guided_stop(uint64_t s_in, uint64_t total, int Tg);
 int or_ransac_prior(const double* pts, int64_t M, const float* prob, int Tg, int T, double thresh, uint64_t seed,
                     uint32_t pair_id, double* H, uint8_t* inl, int32_t* n_in, int32_t* best_t, int32_t* iters,
                     int32_t* counts);
+/* The same with a model of Sec. 2.5 (OR_MODEL_*). */
+int or_ransac_prior_model(const double* pts, int64_t M, int model, const float* prob, int Tg, int T, double thresh,
+                          uint64_t seed, uint32_t pair_id, double* H, uint8_t* inl, int32_t* n_in, int32_t* best_t,
+                          int32_t* iters, int32_t* counts);
 /* Sec. 4 mosaic (readings in lp_oracle.c): rounds of reference selection over
  * H_M (pairs host int32[P*2], HM double[P*9], valid uint8[P]) and placements G
  * (double[N*9], image pixel -> canvas pixel) on a canvas_w x canvas_h canvas. */
