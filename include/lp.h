@@ -56,6 +56,17 @@ typedef enum lp_precision {
     LP_PREC_BF16 = 1         /* BF16 tcgen05 distances, top-k, FP32 re-rank */
 } lp_precision;
 
+/* Transform models of Sec. 2.5.  Eq. 7 maps points through a 3x3 homography
+ * H; Eq. 8 prints H in rigid form (rotation theta and translation t_x, t_y).
+ * LP_MODEL_HOMOGRAPHY estimates all eight degrees of freedom from samples of
+ * four matches; LP_MODEL_RIGID estimates Eq. 8's three from samples of two
+ * (the least-squares rotation and translation of the two) and refits them by
+ * least squares.  Both report H as a row-major double[9] with h33 = 1. */
+typedef enum lp_model {
+    LP_MODEL_HOMOGRAPHY = 0,
+    LP_MODEL_RIGID = 1
+} lp_model;
+
 #define LP_MAX_SCALES 8
 
 /* Parameters of the method.  lp_config_default() fills the values used by the
@@ -72,6 +83,7 @@ typedef struct lp_config {
     int32_t  min_inliers;         /* an H_M entry is non-zero iff n_in >= this */
     int32_t  precision;           /* lp_precision */
     int32_t  upright;             /* 1: every orientation is 0 (no rotation) */
+    int32_t  model;               /* lp_model of lp_ransac and the stitch calls */
 } lp_config;
 
 typedef struct lp_ctx lp_ctx;
@@ -157,6 +169,10 @@ LP_API int lp_compact(lp_ctx* ctx, const uint32_t* kpA, int WA, const uint32_t* 
  * most inliers win (earliest t on ties), decided in FP64 for every hypothesis
  * whose FP32 count could reach the maximum.  The winner's inliers are refitted
  * by least squares (FP64) and the final mask is taken from the refitted H.
+ * With cfg.model = LP_MODEL_RIGID (Eq. 8) iteration t takes the first 2
+ * distinct matches of the same stream, the hypothesis is their least-squares
+ * rotation and translation, and the refit is the least-squares rotation and
+ * translation of the winner's inliers.
  * Errors: LP_ERR_ARG, LP_ERR_NOMEM, LP_ERR_CUDA. */
 LP_API int lp_ransac(lp_ctx* ctx, const float* pts, int64_t M_cap, const int32_t* d_M, uint32_t pair_id,
               double* H, uint8_t* inlier, int32_t* n_inliers, int32_t* best_t, void* stream);
@@ -175,8 +191,9 @@ LP_API int lp_ransac(lp_ctx* ctx, const float* pts, int64_t M_cap, const int32_t
  *
  * Arguments are those of lp_ransac, with the configuration values passed
  * directly: iters = T (1..LP_RANSAC_STATIC_MAX_ITERS; more returns
- * LP_ERR_ARG), thresh_px, seed and pair_id.  The results equal lp_ransac's for
- * the same inputs and configuration.
+ * LP_ERR_ARG), thresh_px, seed and pair_id.  The model is the homography
+ * (Eq. 7).  The results equal lp_ransac's for the same inputs and
+ * configuration.
  *
  * The first call on each device looks up the array's device address (once per
  * device, with that device current); make that first call before any stream
@@ -336,9 +353,9 @@ LP_API int lp_mlp_train_step(lp_mlp* mlp, const float* feat, const uint8_t* labe
  * repeated indices are redrawn.  Every hypothesis is scored by all matches, as
  * in lp_ransac.  Stop test: with w = (sum of q over the guided winner's
  * inliers) / sum(q), the chance that a guided draw is an inlier, the phase
- * stops when (1 - w^4)^guided_iters <= 0.01 -- the standard bound
- * T >= log(0.01) / log(1 - w^4).  Then the guided winner is refitted as in
- * lp_ransac.  Otherwise the uniform phase runs: exactly lp_ransac with the
+ * stops when (1 - w^k)^guided_iters <= 0.01 -- the standard bound
+ * T >= log(0.01) / log(1 - w^k), k = 4 matches per sample (2 for
+ * LP_MODEL_RIGID).  Then the guided winner is refitted as in lp_ransac.  Otherwise the uniform phase runs: exactly lp_ransac with the
  * context's T (the test and the skipped work are decided on the device, so
  * the call never waits for the host).
  *  prior         device float[M_cap] (e.g. lp_mlp_forward's prob)

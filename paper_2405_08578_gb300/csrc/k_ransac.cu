@@ -193,6 +193,47 @@ __device__ bool denorm(const Norm2D& na, const Norm2D& nb, const double* hn, dou
 // Slots of the per-call flags word array (int32).
 constexpr int kFlagBest = 0, kFlagCount = 1, kFlagStop = 2, kFlagIters = 3, kFlagCmax = 4, kFlagWords = 8;
 
+// The first K distinct match indices of iteration t's Philox stream: word j is
+// word j % 4 of block j / 4 (counter (t, j / 4, 0, 0)); prefix == nullptr
+// draws uniformly (index = floor(w * M / 2^32)), otherwise word w picks the
+// match whose interval of the inclusive prefix sums of integer weights
+// contains floor(w * total / 2^32).  Repeats are redrawn, at most 64 words.
+// Returns how many indices were drawn (K, or fewer when the words ran out).
+template <int K>
+__device__ __forceinline__ int draw_sample(int t, uint32_t k0, uint32_t k1, long long M,
+                                           const unsigned long long* prefix, int* idx)
+{
+    int n = 0;
+    uint4 blk = make_uint4(0, 0, 0, 0);
+    for (int j = 0; j < 64 && n < K; ++j) {
+        if ((j & 3) == 0) blk = philox(make_uint4((uint32_t)t, (uint32_t)(j >> 2), 0u, 0u), k0, k1);
+        const uint32_t w = (j & 3) == 0 ? blk.x : (j & 3) == 1 ? blk.y : (j & 3) == 2 ? blk.z : blk.w;
+        int i;
+        if (!prefix) {
+            i = (int)(((unsigned long long)w * (unsigned long long)M) >> 32);
+        } else {
+            const unsigned long long total = prefix[M - 1];
+            const unsigned long long target = __umul64hi((unsigned long long)w << 32, total);
+            long long lo = 0, hi = M - 1;
+            while (lo < hi) {
+                const long long mid = (lo + hi) >> 1;
+                if (prefix[mid] > target) hi = mid; else lo = mid + 1;
+            }
+            i = (int)lo;
+        }
+        bool dup = false;
+#pragma unroll
+        for (int q = 0; q < K - 1; ++q) dup |= q < n && idx[q] == i;
+        if (!dup) {
+#pragma unroll
+            for (int q = 0; q < K; ++q)
+                if (q == n) idx[q] = i;
+            ++n;
+        }
+    }
+    return n;
+}
+
 // Eight lanes per hypothesis, lane r owning row r of the normalised 8x9 DLT
 // system (two rows per correspondence).
 constexpr int kHypThreads = 64;
@@ -217,31 +258,7 @@ k_ransac_hyp(const float4* pts, long long M_cap, const int32_t* dM, int T, uint3
     if (M < 4) return;
     // every lane of the group draws the same four indices
     int idx[4] = {0, 0, 0, 0};
-    int n = 0;
-    uint4 blk = make_uint4(0, 0, 0, 0);
-    for (int j = 0; j < 64 && n < 4; ++j) {
-        if ((j & 3) == 0) blk = philox(make_uint4((uint32_t)t, (uint32_t)(j >> 2), 0u, 0u), k0, k1);
-        const uint32_t w = (j & 3) == 0 ? blk.x : (j & 3) == 1 ? blk.y : (j & 3) == 2 ? blk.z : blk.w;
-        int i;
-        if (!prefix) {
-            i = (int)(((unsigned long long)w * (unsigned long long)M) >> 32);
-        } else {
-            const unsigned long long total = prefix[M - 1];
-            const unsigned long long target = __umul64hi((unsigned long long)w << 32, total);
-            long long lo = 0, hi = M - 1;
-            while (lo < hi) {
-                const long long mid = (lo + hi) >> 1;
-                if (prefix[mid] > target) hi = mid; else lo = mid + 1;
-            }
-            i = (int)lo;
-        }
-        const bool dup = (n > 0 && idx[0] == i) || (n > 1 && idx[1] == i) || (n > 2 && idx[2] == i);
-        if (!dup) {
-            if (n == 0) idx[0] = i; else if (n == 1) idx[1] = i; else if (n == 2) idx[2] = i; else idx[3] = i;
-            ++n;
-        }
-    }
-    if (n < 4) return;
+    if (draw_sample<4>(t, k0, k1, M, prefix, idx) < 4) return;
     double xa[4], ya[4], xb[4], yb[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -313,6 +330,57 @@ k_ransac_hyp(const float4* pts, long long M_cap, const int32_t* dM, int T, uint3
     if (r != 0) return;
     double H[9];
     if (!denorm(na, nb, h, H)) return;
+    for (int i = 0; i < 9; ++i) Hs[9ll * t + i] = H[i];
+    hok[t] = 1;
+}
+
+// Eq. 8 (rotation + translation): one thread per hypothesis.  The minimal
+// sample is the first two distinct indices of the same stream; the model is
+// their least-squares rigid fit: centroids, C = a.b and S = a x b of the
+// centred coordinates, (cos, sin) = (C, S) / sqrt(C^2 + S^2), t = centroid_B -
+// R centroid_A.  Every operation is one IEEE rounding in the order of the
+// definition (no contraction), so the hypothesis is the same double on any
+// conforming machine.  C = S = 0 (coincident points in one image) is skipped.
+constexpr int kRigidThreads = 128;
+
+__device__ bool rigid_fit2(const float4& p, const float4& q, double* H)
+{
+    const double cxa = __ddiv_rn(__dadd_rn(p.x, q.x), 2.0), cya = __ddiv_rn(__dadd_rn(p.y, q.y), 2.0);
+    const double cxb = __ddiv_rn(__dadd_rn(p.z, q.z), 2.0), cyb = __ddiv_rn(__dadd_rn(p.w, q.w), 2.0);
+    double Cs = 0.0, Ss = 0.0;
+    const float4 r[2] = {p, q};
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const double ax = __dsub_rn(r[i].x, cxa), ay = __dsub_rn(r[i].y, cya);
+        const double bx = __dsub_rn(r[i].z, cxb), by = __dsub_rn(r[i].w, cyb);
+        Cs = __dadd_rn(Cs, __dadd_rn(__dmul_rn(ax, bx), __dmul_rn(ay, by)));
+        Ss = __dadd_rn(Ss, __dsub_rn(__dmul_rn(ax, by), __dmul_rn(ay, bx)));
+    }
+    const double rr = __dsqrt_rn(__dadd_rn(__dmul_rn(Cs, Cs), __dmul_rn(Ss, Ss)));
+    if (!(rr > 0.0)) return false;
+    const double c = __ddiv_rn(Cs, rr), s = __ddiv_rn(Ss, rr);
+    H[0] = c; H[1] = -s; H[2] = __dsub_rn(cxb, __dsub_rn(__dmul_rn(c, cxa), __dmul_rn(s, cya)));
+    H[3] = s; H[4] = c;  H[5] = __dsub_rn(cyb, __dadd_rn(__dmul_rn(s, cxa), __dmul_rn(c, cya)));
+    H[6] = 0.0; H[7] = 0.0; H[8] = 1.0;
+    return true;
+}
+
+__global__ void __launch_bounds__(kRigidThreads)
+k_ransac_hyp_rigid(const float4* pts, long long M_cap, const int32_t* dM, int T, uint32_t k0, uint32_t k1,
+                   const unsigned long long* prefix, const int32_t* skip, double* Hs, int8_t* hok, int32_t* flags)
+{
+    const int t = blockIdx.x * kRigidThreads + threadIdx.x;
+    if (skip && *skip) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) flags[kFlagCmax] = -1;
+    if (t >= T) return;
+    hok[t] = 0;
+    const long long M = m_count(dM, M_cap);
+    if (M < 2) return;
+    int idx[2] = {0, 0};
+    if (draw_sample<2>(t, k0, k1, M, prefix, idx) < 2) return;
+    double H[9];
+    if (!rigid_fit2(pts[idx[0]], pts[idx[1]], H)) return;
+#pragma unroll
     for (int i = 0; i < 9; ++i) Hs[9ll * t + i] = H[i];
     hok[t] = 1;
 }
@@ -461,12 +529,12 @@ k_ransac_argmax(const int32_t* exact, int T, const int32_t* skip, int t_off, int
 // flags[kFlagStop] = stop, flags[kFlagIters] = iterations used.
 __global__ void __launch_bounds__(kSelThreads)
 k_guided_decide(const float4* pts, long long M_cap, const int32_t* dM, const double* Hs,
-                const unsigned long long* prefix, int Tg, int T, double t2, int32_t* flags)
+                const unsigned long long* prefix, int Tg, int T, int k, double t2, int32_t* flags)
 {
     __shared__ unsigned long long part[kSelThreads / 32];
     const int tb = flags[kFlagBest];
     const long long M = m_count(dM, M_cap);
-    if (tb < 0 || M < 4) {
+    if (tb < 0 || M < k) {
         if (threadIdx.x == 0) { flags[kFlagStop] = 0; flags[kFlagIters] = Tg + T; }
         return;
     }
@@ -485,7 +553,8 @@ k_guided_decide(const float4* pts, long long M_cap, const int32_t* dM, const dou
     for (int w = 0; w < kSelThreads / 32; ++w) s_in += part[w];
     const double w = __ddiv_rn((double)s_in, (double)prefix[M - 1]);
     const double w2 = __dmul_rn(w, w);
-    double b = __dsub_rn(1.0, __dmul_rn(w2, w2)), r = 1.0;
+    const double wk = k == 2 ? w2 : __dmul_rn(w2, w2);
+    double b = __dsub_rn(1.0, wk), r = 1.0;
     for (int e = Tg; e; e >>= 1) {
         if (e & 1) r = __dmul_rn(r, b);
         b = __dmul_rn(b, b);
@@ -767,6 +836,69 @@ k_refit_solve(const double* Hs, const int32_t* best_in, RefitWS ws, double* Hout
     }
 }
 
+// Eq. 8 refit, pass 2 (after k_refit_p1's mask, count and coordinate sums):
+// C = sum a.b and S = sum a x b of the inliers' coordinates minus their
+// centroids, into columns 5 and 6.
+__global__ void __launch_bounds__(kRefitThreads)
+k_rigid_p2(const float4* pts, long long M_cap, const int32_t* dM, const int32_t* best_in, const uint8_t* inl,
+           RefitWS ws)
+{
+    __shared__ double part[kRefitWarps][2];
+    __shared__ double tot[2];
+    __shared__ double c5[5];
+    if (*best_in < 0) return;
+    const long long M = m_count(dM, M_cap);
+    if (threadIdx.x < 5) c5[threadIdx.x] = sum_col(ws.part, threadIdx.x);
+    __syncthreads();
+    const double n = c5[0];
+    const double cxa = c5[1] / n, cya = c5[2] / n, cxb = c5[3] / n, cyb = c5[4] / n;
+    long long b, e;
+    cta_range(M, b, e);
+    double v2[2] = {0, 0};
+    for (long long i = b + threadIdx.x; i < e; i += kRefitThreads) {
+        if (!inl[i]) continue;
+        const float4 p = pts[i];
+        const double ax = p.x - cxa, ay = p.y - cya, bx = p.z - cxb, by = p.w - cyb;
+        v2[0] += ax * bx + ay * by;
+        v2[1] += ax * by - ay * bx;
+    }
+    block_sum_n<2>(v2, part, tot);
+    if (threadIdx.x < 2) ws.part[blockIdx.x * kPartStride + 5 + threadIdx.x] = tot[threadIdx.x];
+}
+
+// Eq. 8 refit, solve: (cos, sin) = (C, S) / sqrt(C^2 + S^2), t = centroid_B -
+// R centroid_A; fewer than two inliers or C = S = 0 keeps the hypothesis.
+__global__ void __launch_bounds__(32)
+k_rigid_solve(const double* Hs, const int32_t* best_in, RefitWS ws, double* Hout, int32_t* n_in, int32_t* best_t)
+{
+    if (threadIdx.x != 0) return;
+    const int best = *best_in;
+    if (best_t) *best_t = best;
+    *n_in = 0;
+    if (best < 0) {
+        for (int i = 0; i < 9; ++i) { Hout[i] = 0.0; ws.Hf[i] = 0.0; }
+        return;
+    }
+    double c7[7];
+    for (int q = 0; q < 7; ++q) c7[q] = sum_col(ws.part, q);
+    const double n = c7[0];
+    const double cxa = c7[1] / n, cya = c7[2] / n, cxb = c7[3] / n, cyb = c7[4] / n;
+    const double r = sqrt(c7[5] * c7[5] + c7[6] * c7[6]);
+    const bool ok = n >= 2 && r > 0;
+    double H[9];
+    if (ok) {
+        const double c = c7[5] / r, s = c7[6] / r;
+        H[0] = c; H[1] = -s; H[2] = cxb - (c * cxa - s * cya);
+        H[3] = s; H[4] = c;  H[5] = cyb - (s * cxa + c * cya);
+        H[6] = 0.0; H[7] = 0.0; H[8] = 1.0;
+    }
+    for (int i = 0; i < 9; ++i) {
+        const double v = ok ? H[i] : Hs[9ll * best + i];
+        ws.Hf[i] = v;
+        Hout[i] = v;
+    }
+}
+
 // final inlier set of the refitted H
 __global__ void __launch_bounds__(kRefitThreads)
 k_refit_final(const float4* pts, long long M_cap, const int32_t* dM, RefitWS ws, double t2, uint8_t* inl,
@@ -836,26 +968,37 @@ RansacWS carve(void* ws, int Ttot)
     return r;
 }
 
-void refit_launch(const float4* p4, int64_t M_cap, const int32_t* d_M, double t2, const RansacWS& w, double* H,
-                  uint8_t* inlier, int32_t* n_in, int32_t* best_t, cudaStream_t s)
+void refit_launch(int model, const float4* p4, int64_t M_cap, const int32_t* d_M, double t2, const RansacWS& w,
+                  double* H, uint8_t* inlier, int32_t* n_in, int32_t* best_t, cudaStream_t s)
 {
     k_refit_p1<<<kRefitCTAs, kRefitThreads, 0, s>>>(p4, M_cap, d_M, w.Hs, w.flags, t2, inlier, w.rw);
-    k_refit_p2<<<kRefitCTAs, kRefitThreads, 0, s>>>(p4, M_cap, d_M, w.flags, inlier, w.rw);
-    k_refit_p3<<<kRefitCTAs, kRefitThreads, 0, s>>>(p4, M_cap, d_M, w.flags, inlier, w.rw);
-    k_refit_solve<<<1, kSolveThreads, 0, s>>>(w.Hs, w.flags, w.rw, H, n_in, best_t);
+    if (model == LP_MODEL_RIGID) {
+        k_rigid_p2<<<kRefitCTAs, kRefitThreads, 0, s>>>(p4, M_cap, d_M, w.flags, inlier, w.rw);
+        k_rigid_solve<<<1, 32, 0, s>>>(w.Hs, w.flags, w.rw, H, n_in, best_t);
+    } else {
+        k_refit_p2<<<kRefitCTAs, kRefitThreads, 0, s>>>(p4, M_cap, d_M, w.flags, inlier, w.rw);
+        k_refit_p3<<<kRefitCTAs, kRefitThreads, 0, s>>>(p4, M_cap, d_M, w.flags, inlier, w.rw);
+        k_refit_solve<<<1, kSolveThreads, 0, s>>>(w.Hs, w.flags, w.rw, H, n_in, best_t);
+    }
     const unsigned gfin = (unsigned)std::max<long long>(1, std::min<long long>(kRefitCTAs, (M_cap + 1023) / 1024));
     k_refit_final<<<gfin, kRefitThreads, 0, s>>>(p4, M_cap, d_M, w.rw, t2, inlier, n_in);
 }
 
 // One batch of T hypotheses at rows [t_off, t_off + T) of the workspace,
 // Philox counters 0..T-1; skipped entirely while *skip is non-zero.
-void hyp_batch(const float4* p4, int64_t M_cap, const int32_t* d_M, const unsigned long long* prefix, int T,
-               int t_off, uint32_t k0, uint32_t k1, float t2f, float eps, double t2, const int32_t* skip,
+void hyp_batch(int model, const float4* p4, int64_t M_cap, const int32_t* d_M, const unsigned long long* prefix,
+               int T, int t_off, uint32_t k0, uint32_t k1, float t2f, float eps, double t2, const int32_t* skip,
                const RansacWS& w, cudaStream_t s)
 {
-    const unsigned gh = (unsigned)((8ll * T + kHypThreads - 1) / kHypThreads);
-    k_ransac_hyp<<<gh, kHypThreads, 0, s>>>(p4, M_cap, d_M, T, k0, k1, prefix, skip, w.Hs + 9ll * t_off,
-                                            w.hok + t_off, w.flags);
+    if (model == LP_MODEL_RIGID) {
+        const unsigned gh = (unsigned)((T + kRigidThreads - 1) / kRigidThreads);
+        k_ransac_hyp_rigid<<<gh, kRigidThreads, 0, s>>>(p4, M_cap, d_M, T, k0, k1, prefix, skip, w.Hs + 9ll * t_off,
+                                                        w.hok + t_off, w.flags);
+    } else {
+        const unsigned gh = (unsigned)((8ll * T + kHypThreads - 1) / kHypThreads);
+        k_ransac_hyp<<<gh, kHypThreads, 0, s>>>(p4, M_cap, d_M, T, k0, k1, prefix, skip, w.Hs + 9ll * t_off,
+                                                w.hok + t_off, w.flags);
+    }
     k_ransac_score<<<T, kScoreThreads, 0, s>>>(p4, M_cap, d_M, w.Hs + 9ll * t_off, w.hok + t_off, t2f, eps, skip,
                                                w.lo + t_off, w.hi + t_off, w.flags);
     k_ransac_recount<<<T, kRecountThreads, 0, s>>>(p4, M_cap, d_M, w.Hs + 9ll * t_off, w.lo + t_off, w.hi + t_off,
@@ -873,11 +1016,10 @@ size_t ransac_workspace(int64_t M_cap, int Ttot)
            sizeof(double) * (kRefitCTAs * kPartStride + 16) + 256;
 }
 
-cudaError_t launch_ransac(const float* pts, int64_t M_cap, const int32_t* d_M, int T, float thresh,
+cudaError_t launch_ransac(const float* pts, int64_t M_cap, const int32_t* d_M, int T, int model, float thresh,
                           uint64_t seed, uint32_t pair_id, double* H, uint8_t* inlier, int32_t* n_in,
-                          int32_t* best_t, void* ws, size_t ws_bytes, int32_t* status, cudaStream_t s)
+                          int32_t* best_t, void* ws, size_t ws_bytes, cudaStream_t s)
 {
-    (void)status;
     if (ws_bytes < ransac_workspace(M_cap, T)) return cudaErrorInvalidValue;
     const RansacWS w = carve(ws, T);
     const float4* p4 = reinterpret_cast<const float4*>(pts);
@@ -885,8 +1027,8 @@ cudaError_t launch_ransac(const float* pts, int64_t M_cap, const int32_t* d_M, i
     const double t2 = (double)thresh * (double)thresh;
     const float t2f = (float)t2;
     const float eps = fmaxf(0.05f, 0.01f * t2f);
-    hyp_batch(p4, M_cap, d_M, nullptr, T, 0, k0, k1, t2f, eps, t2, nullptr, w, s);
-    refit_launch(p4, M_cap, d_M, t2, w, H, inlier, n_in, best_t, s);
+    hyp_batch(model, p4, M_cap, d_M, nullptr, T, 0, k0, k1, t2f, eps, t2, nullptr, w, s);
+    refit_launch(model, p4, M_cap, d_M, t2, w, H, inlier, n_in, best_t, s);
     return cudaGetLastError();
 }
 
@@ -895,7 +1037,7 @@ cudaError_t launch_ransac(const float* pts, int64_t M_cap, const int32_t* d_M, i
 // the device when the guided phase stopped.  Hypothesis rows: guided [0, Tg),
 // uniform [Tg, Tg + T).
 cudaError_t launch_ransac_prior(const float* pts, int64_t M_cap, const int32_t* d_M, const unsigned long long* prefix,
-                                int Tg, int T, float thresh, uint64_t seed, uint32_t pair_id, double* H,
+                                int Tg, int T, int model, float thresh, uint64_t seed, uint32_t pair_id, double* H,
                                 uint8_t* inlier, int32_t* n_in, int32_t* best_t, int32_t* iters, void* ws,
                                 size_t ws_bytes, cudaStream_t s)
 {
@@ -906,10 +1048,11 @@ cudaError_t launch_ransac_prior(const float* pts, int64_t M_cap, const int32_t* 
     const double t2 = (double)thresh * (double)thresh;
     const float t2f = (float)t2;
     const float eps = fmaxf(0.05f, 0.01f * t2f);
-    hyp_batch(p4, M_cap, d_M, prefix, Tg, 0, k0, k1, t2f, eps, t2, nullptr, w, s);
-    k_guided_decide<<<1, kSelThreads, 0, s>>>(p4, M_cap, d_M, w.Hs, prefix, Tg, T, t2, w.flags);
-    hyp_batch(p4, M_cap, d_M, nullptr, T, Tg, k0, k1, t2f, eps, t2, w.flags + kFlagStop, w, s);
-    refit_launch(p4, M_cap, d_M, t2, w, H, inlier, n_in, best_t, s);
+    const int k = model == LP_MODEL_RIGID ? 2 : 4;
+    hyp_batch(model, p4, M_cap, d_M, prefix, Tg, 0, k0, k1, t2f, eps, t2, nullptr, w, s);
+    k_guided_decide<<<1, kSelThreads, 0, s>>>(p4, M_cap, d_M, w.Hs, prefix, Tg, T, k, t2, w.flags);
+    hyp_batch(model, p4, M_cap, d_M, nullptr, T, Tg, k0, k1, t2f, eps, t2, w.flags + kFlagStop, w, s);
+    refit_launch(model, p4, M_cap, d_M, t2, w, H, inlier, n_in, best_t, s);
     if (iters) {
         cudaError_t e = cudaMemcpyAsync(iters, w.flags + kFlagIters, sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
         if (e != cudaSuccess) return e;

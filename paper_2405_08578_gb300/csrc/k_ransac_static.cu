@@ -68,8 +68,8 @@ extern "C" LP_API int lp_ransac_static(const float* pts, int64_t M_cap, const in
     void* scratch = nullptr;
     const int r = scratch_address(&scratch);
     if (r != LP_OK) return r;
-    const cudaError_t e = lp::launch_ransac(pts, M_cap, d_M, iters, thresh_px, seed, pair_id, H, inlier, n_inliers,
-                                            best_t, scratch, kScratchBytes, nullptr,
+    const cudaError_t e = lp::launch_ransac(pts, M_cap, d_M, iters, LP_MODEL_HOMOGRAPHY, thresh_px, seed, pair_id, H,
+                                            inlier, n_inliers, best_t, scratch, kScratchBytes,
                                             static_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? LP_OK : LP_ERR_CUDA;
 }

@@ -123,6 +123,8 @@ int check_cfg(lp_ctx* c, const lp_config* cfg)
     if (!(cfg->thresh_px > 0.f)) return fail(c, LP_ERR_ARG, "thresh_px must be > 0");
     if (cfg->precision != LP_PREC_FP32 && cfg->precision != LP_PREC_BF16)
         return fail(c, LP_ERR_ARG, "unknown precision %d", cfg->precision);
+    if (cfg->model != LP_MODEL_HOMOGRAPHY && cfg->model != LP_MODEL_RIGID)
+        return fail(c, LP_ERR_ARG, "unknown model %d", cfg->model);
     return LP_OK;
 }
 
@@ -201,6 +203,7 @@ int lp_config_default(lp_config* cfg)
     cfg->min_inliers = 8;
     cfg->precision = LP_PREC_FP32;
     cfg->upright = 0;
+    cfg->model = LP_MODEL_HOMOGRAPHY;
     return LP_OK;
 }
 
@@ -361,8 +364,8 @@ int lp_ransac(lp_ctx* c, const float* pts, int64_t M_cap, const int32_t* d_M, ui
     if (r) return r;
     c->last = S(stream);
     c->last_ransac_hyps = T;
-    LP_CUDA(c, lp::launch_ransac(pts, M_cap, d_M, T, c->cfg.thresh_px, c->cfg.seed, pair_id, H, inlier, n_inliers,
-                                 best_t, c->buf[B_RANSAC_WS].p, c->buf[B_RANSAC_WS].n, c->d_status, S(stream)));
+    LP_CUDA(c, lp::launch_ransac(pts, M_cap, d_M, T, c->cfg.model, c->cfg.thresh_px, c->cfg.seed, pair_id, H, inlier,
+                                 n_inliers, best_t, c->buf[B_RANSAC_WS].p, c->buf[B_RANSAC_WS].n, S(stream)));
     return LP_OK;
 }
 
@@ -669,8 +672,9 @@ int lp_ransac_prior(lp_ctx* c, const float* pts, int64_t M_cap, const int32_t* d
     c->last_ransac_hyps = Ttot;
     auto* pre = static_cast<unsigned long long*>(c->buf[B_PREFIX].p);
     LP_CUDA(c, lp::launch_guided_prefix(prior, M_cap, d_M, pre, S(stream)));
-    LP_CUDA(c, lp::launch_ransac_prior(pts, M_cap, d_M, pre, guided_iters, T, c->cfg.thresh_px, c->cfg.seed, pair_id,
-                                       H, inlier, n_inliers, best_t, iters_used, c->buf[B_RANSAC_WS].p,
+    LP_CUDA(c, lp::launch_ransac_prior(pts, M_cap, d_M, pre, guided_iters, T, c->cfg.model, c->cfg.thresh_px,
+                                       c->cfg.seed, pair_id, H, inlier, n_inliers, best_t, iters_used,
+                                       c->buf[B_RANSAC_WS].p,
                                        c->buf[B_RANSAC_WS].n, S(stream)));
     return LP_OK;
 }

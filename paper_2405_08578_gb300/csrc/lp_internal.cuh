@@ -64,15 +64,16 @@ size_t compact_workspace(int64_t NA);
 cudaError_t launch_compact(const uint32_t* kpA, int WA, const uint32_t* kpB, int WB, const int32_t* match,
                            int64_t NA, float* pts, int32_t* rows, int32_t* d_M, int32_t* tile_cnt, cudaStream_t s);
 size_t ransac_workspace(int64_t M_cap, int Ttot);
-cudaError_t launch_ransac(const float* pts, int64_t M_cap, const int32_t* d_M, int T, float thresh,
+// model: LP_MODEL_HOMOGRAPHY (Eq. 7) or LP_MODEL_RIGID (Eq. 8)
+cudaError_t launch_ransac(const float* pts, int64_t M_cap, const int32_t* d_M, int T, int model, float thresh,
                           uint64_t seed, uint32_t pair_id, double* H, uint8_t* inlier, int32_t* n_in,
-                          int32_t* best_t, void* ws, size_t ws_bytes, int32_t* status, cudaStream_t s);
+                          int32_t* best_t, void* ws, size_t ws_bytes, cudaStream_t s);
 cudaError_t launch_diag_philox(const uint32_t* ctr, int64_t n, uint32_t k0, uint32_t k1, uint32_t* out,
                                cudaStream_t s);
 
 // k_ransac.cu (guided phase, stop test, uniform fallback); Ttot = Tg + T
 cudaError_t launch_ransac_prior(const float* pts, int64_t M_cap, const int32_t* d_M, const unsigned long long* prefix,
-                                int Tg, int T, float thresh, uint64_t seed, uint32_t pair_id, double* H,
+                                int Tg, int T, int model, float thresh, uint64_t seed, uint32_t pair_id, double* H,
                                 uint8_t* inlier, int32_t* n_in, int32_t* best_t, int32_t* iters, void* ws,
                                 size_t ws_bytes, cudaStream_t s);
 cudaError_t ransac_counts(void* ws, int Ttot, int32_t* host_counts, cudaStream_t s);
