@@ -313,6 +313,7 @@ def fp32_form_and_batch(args, rank):
     out["batch_3x3"] = {"images": 9, "pairs": 36, "pairs_per_s": 36 * k / t, "ms_per_batch": 1e3 * t / k,
                         "valid_pairs": int(va.sum().item()), "graph": True}
     out["mosaic_3x3"] = mosaic(bt, images, ctx, HM, va, flush, k)
+    out["table2"] = table2(flush)
     if args.train_pairs > 0:
         out["learned_proposal"] = learned_proposal(args, bt, images, ctx, HM, ni, va, flush, k)
     return out
@@ -364,6 +365,51 @@ def mosaic(bt, images, ctx, HM, va, flush, k):
     return {"placed": placed, "rounds": int(plan["round"].max()) + 1, "canvas": [ch, cw], "plan_ms": round(plan_ms, 3),
             "placement_err_px": round(err, 2),
             "render_ms": 1e3 * t / k, "render_GBps_algorithmic": bytes_alg / (t / k) / 1e9}
+
+
+# Table 2 stitching times of LP-SIFT (MATLAB on an i9-12900 CPU, detection to
+# stitching), for context beside the per-pair device times below
+TABLE2_PAPER_S = {"mountain": 1.16, "street_view": 2.05, "terrain": 4.47, "building": 2.03,
+                  "campus_translation": 4.49, "campus_rotation": 4.58}
+
+
+def table2(flush, k=10):
+    """Per-pair device time of lp_stitch_pair (BF16) on stand-ins for Table 2's
+    LP-SIFT rows: the printed sizes and window-size sets."""
+    import torch
+
+    from paper_2405_08578_gb300 import lp, synth
+    out = {}
+    s = torch.cuda.current_stream()
+    for name in sorted(synth.TABLE2):
+        p, Ls = synth.table2_pair(name)
+        h, w = p.A.shape
+        bA, pA = lp.pitched_device(p.A)
+        bB, pB = lp.pitched_device(p.B)
+        H = torch.zeros(9, dtype=torch.float64, device="cuda")
+        n = torch.zeros(1, dtype=torch.int32, device="cuda")
+        M = torch.zeros(1, dtype=torch.int32, device="cuda")
+        row = {"W": w, "H": h, "Ls": list(Ls), "K_per_image": lp.lp_num_keypoints(h, w, Ls),
+               "paper_matlab_s": TABLE2_PAPER_S[name]}
+        for model, tag in ((lp.MODEL_HOMOGRAPHY, ""), (lp.MODEL_RIGID, "_rigid")):
+            ctx = lp.Context(Ls=Ls, precision=lp.PREC_BF16, model=model)
+            for _ in range(3):
+                ctx.lp_stitch_pair(bA, h, w, pA, bB, h, w, pB, 1, 0, H, n, M)
+            torch.cuda.synchronize()
+            t = 0.0
+            for _ in range(k):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(s)
+                ctx.lp_stitch_pair(bA, h, w, pA, bB, h, w, pB, 1, 0, H, n, M)
+                e1.record(s)
+                torch.cuda.synchronize()
+                t += e0.elapsed_time(e1)
+            row["ms_per_pair" + tag] = round(t / k, 4)
+            row["inliers" + tag] = int(n.item())
+            row["matches"] = int(M.item())
+        out[name] = row
+    return out
 
 
 def learned_proposal(args, bt, images, ctx, HM, ni, va, flush, k):
@@ -508,6 +554,7 @@ def main():
         line["config"]["fp32_form_inliers"] = extra["fp32_form_inliers"]
         line["config"]["batch_3x3"] = extra["batch_3x3"]
         line["config"]["mosaic_3x3"] = extra["mosaic_3x3"]
+        line["config"]["table2"] = extra["table2"]
         if "learned_proposal" in extra:
             line["config"]["learned_proposal"] = extra["learned_proposal"]
     if world == 1 and not args.no_cpu_baseline:

@@ -554,6 +554,213 @@ __global__ void __launch_bounds__(kWarps * 32) k_describe_global(const DescParam
     }
 }
 
+// ---------------------------------------------------------------- split path
+// Scales with w_s > 15 have few points and long per-point loops, so one point's
+// work is spread over many CTAs:
+//   k_orient_split   CTA (point, band of rows of the upright (4 w_s + 1)^2
+//                    window): Eq. 5 gradient weights summed per bin in shared
+//                    memory (low 16 and high 9 bits, as k_describe_cta), then
+//                    added to the point's 64-bit bins in global memory.  The
+//                    sums are integers, so their order does not matter.
+//   k_orient_pick    one thread per point: argmax, the lowest bin on ties.
+//   k_desc_cell      CTA (point, cell): the cell's turned (w_s + 2)^2 grid is
+//                    interpolated once from the neighbourhood staged in shared
+//                    memory; Eq. 5 differences; soft 8-bin histogram summed in
+//                    a fixed order; the cell's 8 raw values are written.
+//   k_desc_finalize  one warp per point: L2 norm, clamp at 0.2, L2 norm.
+// The 36 bins of a point live in its own descriptor row (288 of its 512
+// bytes) until k_desc_cell overwrites the row.
+constexpr int kSplitThreads = 256;
+constexpr int kOrientBandSamples = 4096;
+
+__global__ void __launch_bounds__(kSplitThreads) k_orient_split(const DescParams p, int rows_per_band, int nbands)
+{
+    __shared__ uint32_t hlo[36], hhi[36];
+    const long long idx = blockIdx.x / nbands;
+    const int band = (int)(blockIdx.x - idx * nbands);
+    const long long k = p.k0 + idx;
+    const int R = 2 * p.ws, n = 2 * R + 1;
+    const uint32_t id = __ldg(p.kp + k);
+    const int y = (int)(id / (uint32_t)p.W), x = (int)(id - (uint32_t)y * (uint32_t)p.W);
+    auto px = [&](int yy, int xx) -> int {
+        yy = min(max(yy, 0), p.H - 1);
+        xx = min(max(xx, 0), p.W - 1);
+        return __ldg(p.gray + (size_t)yy * p.pitch + xx);
+    };
+    if (threadIdx.x < 36) { hlo[threadIdx.x] = 0u; hhi[threadIdx.x] = 0u; }
+    __syncthreads();
+    const int u0 = band * rows_per_band, u1 = min(n, u0 + rows_per_band);
+    const int cnt = (u1 - u0) * n;
+    for (int e = threadIdx.x; e < cnt; e += kSplitThreads) {
+        const int r = u0 + e / n, c = e - (e / n) * n;
+        const int yy = y + r - R, xx = x + c - R;
+        const int a = px(yy + 1, xx) - px(yy - 1, xx);
+        const int b = px(yy, xx + 1) - px(yy, xx - 1);
+        if (a | b) {
+            const int bin = __ldg(p.lut_bin + (a + 255) * 511 + (b + 255));
+            const uint32_t wt = __ldg(p.lut_w + a * a + b * b);
+            atomicAdd(&hlo[bin], wt & 0xFFFFu);
+            atomicAdd(&hhi[bin], wt >> 16);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 36) {
+        const unsigned long long v = ((unsigned long long)hhi[threadIdx.x] << 16) + hlo[threadIdx.x];
+        if (v) atomicAdd(reinterpret_cast<unsigned long long*>(p.desc + k * 128) + threadIdx.x, v);
+    }
+}
+
+__global__ void __launch_bounds__(128) k_orient_pick(const DescParams p)
+{
+    const long long idx = (long long)blockIdx.x * 128 + threadIdx.x;
+    if (idx >= p.n) return;
+    const long long k = p.k0 + idx;
+    const unsigned long long* h = reinterpret_cast<const unsigned long long*>(p.desc + k * 128);
+    unsigned long long bv = h[0];
+    int bb = 0;
+    for (int b = 1; b < 36; ++b)
+        if (h[b] > bv) { bv = h[b]; bb = b; }
+    p.ori[k] = (uint8_t)bb;
+}
+
+// Shared memory of k_desc_cell for cell grids of side Gc = w_s + 2: the staged
+// neighbourhood (side at most ceil((Gc - 1) sqrt 2) + 6, rows padded to 4
+// bytes) and the FP32 grid.
+__host__ __device__ __forceinline__ int cell_box_side(int Gc) { return (int)((Gc - 1) * 1.41422f) + 7; }
+__host__ __device__ __forceinline__ int cell_box_bytes(int Gc)
+{
+    const int b = cell_box_side(Gc);
+    return ((b * ((b + 3) & ~3)) + 15) / 16 * 16;
+}
+
+__global__ void __launch_bounds__(kSplitThreads) k_desc_cell(const DescParams p)
+{
+    extern __shared__ __align__(16) uint8_t sm[];
+    __shared__ float red[kSplitThreads / 32][8];
+    const long long idx = blockIdx.x >> 4;
+    const int cell = blockIdx.x & 15, cr = cell >> 2, cq = cell & 3;
+    const long long k = p.k0 + idx;
+    const int ws = p.ws, R = 2 * ws, Gc = ws + 2;
+    const int bmax = cell_box_side(Gc);
+    const uint32_t id = __ldg(p.kp + k);
+    const int y = (int)(id / (uint32_t)p.W), x = (int)(id - (uint32_t)y * (uint32_t)p.W);
+    const int best = p.upright ? 0 : p.ori[k];
+    const float c = p.upright ? 1.f : p.cs[best][0];
+    const float s = p.upright ? 0.f : p.cs[best][1];
+    // frame points (fu, fv) = (fu0 + iu, fv0 + iv), iu, iv in [0, Gc): image
+    // offsets (dy, dx) = (fu c - fv s, fu s + fv c) from the point
+    const int fu0 = -R + cr * ws - 1, fv0 = -R + cq * ws - 1;
+    float ymin = 3.4e38f, ymax = -3.4e38f, xmin = 3.4e38f, xmax = -3.4e38f;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float fu = (float)(fu0 + ((q & 1) ? Gc - 1 : 0)), fv = (float)(fv0 + ((q & 2) ? Gc - 1 : 0));
+        const float dy = fu * c - fv * s, dx = fu * s + fv * c;
+        ymin = fminf(ymin, dy); ymax = fmaxf(ymax, dy); xmin = fminf(xmin, dx); xmax = fmaxf(xmax, dx);
+    }
+    // one spare row and column on each side; the taps below are clamped to the box
+    const int r0 = (int)floorf(ymin) - 1, c0 = (int)floorf(xmin) - 1;
+    const int nr = min(bmax, (int)floorf(ymax) + 3 - r0), nc = min(bmax, (int)floorf(xmax) + 3 - c0);
+    const int SPc = (bmax + 3) & ~3;
+    uint8_t* box = sm;
+    float* grid = reinterpret_cast<float*>(sm + cell_box_bytes(Gc));
+    for (int e = threadIdx.x; e < nr * nc; e += kSplitThreads) {
+        const int r = e / nc, q = e - (e / nc) * nc;
+        const int yy = min(max(y + r0 + r, 0), p.H - 1), xx = min(max(x + c0 + q, 0), p.W - 1);
+        box[r * SPc + q] = __ldg(p.gray + (size_t)yy * p.pitch + xx);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < Gc * Gc; e += kSplitThreads) {
+        const int iu = e / Gc, iv = e - (e / Gc) * Gc;
+        const float fu = (float)(fu0 + iu), fv = (float)(fv0 + iv);
+        const float rr = fu * c - fv * s - (float)r0, cc = fu * s + fv * c - (float)c0;
+        const float rf = floorf(rr), cf = floorf(cc);
+        const int ri = min(max((int)rf, 0), nr - 2), ci = min(max((int)cf, 0), nc - 2);
+        const float fr = rr - rf, fc = cc - cf;
+        const uint8_t* b0 = box + ri * SPc + ci;
+        const float v00 = b0[0], v01 = b0[1], v10 = b0[SPc], v11 = b0[SPc + 1];
+        const float top = v00 + fc * (v01 - v00);
+        const float bot = v10 + fc * (v11 - v10);
+        grid[e] = top + fr * (bot - top);
+    }
+    __syncthreads();
+    float h[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) h[q] = 0.f;
+    for (int i = threadIdx.x; i < ws * ws; i += kSplitThreads) {
+        const int iu = i / ws, iv = i - (i / ws) * ws;
+        const float* g = grid + (iu + 1) * Gc + iv + 1;
+        const float a = g[Gc] - g[-Gc];
+        const float b = g[1] - g[-1];
+        const float x2 = a * a + b * b;
+        if (x2 > 0.f) {
+            float m, o;
+            grad_polar(a, b, x2, m, o);
+            const int b0 = (int)o;
+            const float t = o - (float)b0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                h[q] += (q == b0) ? m * (1.f - t) : 0.f;
+                h[q] += (q == ((b0 + 1) & 7)) ? m * t : 0.f;
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) h[q] += __shfl_xor_sync(0xFFFFFFFFu, h[q], o);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) red[warp][q] = h[q];
+    __syncthreads();
+    if (threadIdx.x < 8) {
+        float v = 0.f;
+        for (int w = 0; w < kSplitThreads / 32; ++w) v += red[w][threadIdx.x];
+        p.desc[k * 128 + cell * 8 + threadIdx.x] = v;
+    }
+}
+
+__global__ void __launch_bounds__(128) k_desc_finalize(const DescParams p)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long idx = (long long)blockIdx.x * 4 + warp;
+    if (idx >= p.n) return;
+    const long long k = p.k0 + idx;
+    const float4 r = reinterpret_cast<const float4*>(p.desc + k * 128)[lane];
+    float v[4] = {r.x, r.y, r.z, r.w};
+    float ss = 0.f;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) ss += v[q] * v[q];
+#pragma unroll
+    for (int o = 16; o; o >>= 1) ss += __shfl_xor_sync(0xFFFFFFFFu, ss, o);
+    const float nrm = sqrtf(ss);
+    const bool ok = nrm > 0.f;
+    float ss2 = 0.f;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        v[q] = ok ? fminf(v[q] / nrm, 0.2f) : 0.f;
+        ss2 += v[q] * v[q];
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) ss2 += __shfl_xor_sync(0xFFFFFFFFu, ss2, o);
+    const float n2 = sqrtf(ss2);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[q] = ok ? v[q] / n2 : 0.f;
+    reinterpret_cast<float4*>(p.desc + k * 128)[lane] = make_float4(v[0], v[1], v[2], v[3]);
+    if (p.desc16) {
+        __nv_bfloat162 lo = __floats2bfloat162_rn(v[0], v[1]);
+        __nv_bfloat162 hi = __floats2bfloat162_rn(v[2], v[3]);
+        uint2 w;
+        w.x = *reinterpret_cast<uint32_t*>(&lo);
+        w.y = *reinterpret_cast<uint32_t*>(&hi);
+        reinterpret_cast<uint2*>(p.desc16 + k * 128)[lane] = w;
+    }
+    if (lane == 0) {
+        if (p.upright) p.ori[k] = 0;
+        p.valid[k] = ok ? 1 : 0;
+    }
+}
+
 }  // namespace
 
 size_t describe_lut_bytes() { return (size_t)kLutWeights * 4 + 256 + (size_t)kLutBins + 256; }
@@ -585,7 +792,8 @@ cudaError_t launch_describe(const uint8_t* gray, int H, int W, int pitch, const 
     // Scales with w_s <= 15 run in launches of consecutive scales whose
     // per-warp shared memory fits kSmallWarpBytes (high occupancy), every larger
     // footprint in a launch of its own; larger footprints are launched first.
-    // Scales with w_s > 15 take the global-memory kernel.
+    // Scales with w_s > 15 take the split path (many CTAs per point), or the
+    // global-memory kernel when a cell's grid does not fit shared memory.
     int m = 0;
     while (m < st.nL && st.ws[m] <= 15) ++m;
     auto warp_bytes = [&](int l) {
@@ -646,8 +854,28 @@ cudaError_t launch_describe(const uint8_t* gray, int H, int W, int pitch, const 
         if (p.n == 0) continue;
         p.ws = st.ws[l];
         p.P = st.pr[l];
-        const unsigned grid = (unsigned)((p.n + kWarps - 1) / kWarps);
-        k_describe_global<<<grid, kWarps * 32, (size_t)kWarps * (2 * kHistBytes + kAccBytes), s>>>(p);
+        const int Gc = p.ws + 2;
+        const size_t csm = (size_t)cell_box_bytes(Gc) + (size_t)Gc * Gc * 4;
+        if (csm > 200 * 1024) {
+            const unsigned grid = (unsigned)((p.n + kWarps - 1) / kWarps);
+            k_describe_global<<<grid, kWarps * 32, (size_t)kWarps * (2 * kHistBytes + kAccBytes), s>>>(p);
+            continue;
+        }
+        if (!upright) {
+            cudaError_t e = cudaMemsetAsync(desc + p.k0 * 128, 0, sizeof(float) * 128 * (size_t)p.n, s);
+            if (e != cudaSuccess) return e;
+            const int n = 4 * p.ws + 1;
+            const int rows = kOrientBandSamples / n > 1 ? kOrientBandSamples / n : 1;
+            const int nb = (n + rows - 1) / rows;
+            k_orient_split<<<(unsigned)(p.n * nb), kSplitThreads, 0, s>>>(p, rows, nb);
+            k_orient_pick<<<(unsigned)((p.n + 127) / 128), 128, 0, s>>>(p);
+        }
+        if (csm > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(k_desc_cell, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm);
+            if (e != cudaSuccess) return e;
+        }
+        k_desc_cell<<<(unsigned)(p.n * 16), kSplitThreads, csm, s>>>(p);
+        k_desc_finalize<<<(unsigned)((p.n + 3) / 4), 128, 0, s>>>(p);
     }
     return cudaGetLastError();
 }

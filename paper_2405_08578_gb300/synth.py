@@ -185,6 +185,30 @@ def pair_2688x1600(seed: int = 0, rgb: bool = True) -> Pair:
     return make_pair(h, w, H, seed, rgb=rgb)
 
 
+# Table 2's LP-SIFT rows: image size (width x height, as printed) and the
+# window-size set [a, b], read as the two scales {a, b}.
+TABLE2 = {
+    "mountain": (602, 400, (32, 40)),
+    "street_view": (653, 490, (32, 40)),
+    "terrain": (1024, 768, (32, 64)),
+    "building": (1080, 1920, (100, 128)),
+    "campus_translation": (3072, 4096, (256, 512)),
+    "campus_rotation": (3072, 4096, (256, 512)),
+}
+
+
+def table2_pair(name: str, seed: int = 0) -> tuple[Pair, tuple[int, ...]]:
+    """Gray stand-in for a Table 2 pair: the printed size and L set, B = A
+    through a seeded rigid motion about the centre (rotation U[-5, 5] deg, or
+    U[8, 12] deg for the rotation pair; x shift 0.5 w; y shift U[-0.05, 0.05]
+    h), about half the frame overlapping."""
+    w, h, Ls = TABLE2[name]
+    rng = np.random.default_rng(30_000 + seed + 97 * sorted(TABLE2).index(name))
+    th = rng.uniform(8.0, 12.0) if name == "campus_rotation" else rng.uniform(-5.0, 5.0)
+    H = similarity(th, 1.0, 0.5 * w, rng.uniform(-0.05, 0.05) * h, w / 2.0, h / 2.0)
+    return make_pair(h, w, H, seed), Ls
+
+
 def small_pair(h: int, w: int, seed: int, theta_deg: float = 4.0, scale: float = 1.03,
                shift: float = 0.3, rgb: bool = False) -> Pair:
     """Small pair for parity tests: similarity about the centre, x shift = shift * w."""

@@ -135,7 +135,8 @@ def _describe_parity(gray, Ls, sample=None, upright=False):
 
 
 @pytest.mark.parametrize("shape,Ls", [((64, 80), (8, 16)), ((75, 93), (8, 16, 32)), ((120, 200), (16, 32, 64)),
-                                      ((128, 160), (32, 40)), ((200, 300), (100, 128))])
+                                      ((128, 160), (32, 40)), ((200, 300), (100, 128)),
+                                      ((500, 700), (64, 160)), ((700, 900), (256, 512))])
 def test_describe_small(shape, Ls):
     p = synth.small_pair(shape[0], shape[1], seed=shape[0] + shape[1])
     _describe_parity(p.A, Ls)
@@ -157,12 +158,13 @@ def test_describe_2688x1600_sampled():
     _describe_parity(g, Ls, sample=sample)
 
 
-def test_describe_flat_image_invalid():
-    ctx = ctx_for((8, 16))
-    g = np.full((48, 64), 100, np.uint8)
-    kp = oracle.detect(g, (8, 16))
+@pytest.mark.parametrize("shape,Ls", [((48, 64), (8, 16)), ((260, 300), (100, 128))])
+def test_describe_flat_image_invalid(shape, Ls):
+    ctx = ctx_for(Ls)
+    g = np.full(shape, 100, np.uint8)
+    kp = oracle.detect(g, Ls)
     ori, desc, valid = G.describe(ctx, g, kp)
-    assert not valid.any() and not desc.any() and not ori.any()
+    assert len(kp) and not valid.any() and not desc.any() and not ori.any()
 
 
 # ------------------------------------------------------------------ matching
