@@ -2,40 +2,45 @@
 // (tcgen05) for sm_103a, re-ranked in FP32 so that every decision equals the
 // plain FP32 form's.
 //
-// Stage 1, k_match_tc (persistent, one CTA per SM, 10 warps):
-//   warp 0    TMA producer: per work unit a 256-row A block (2 x 32 KB boxes,
-//             128-byte swizzle), then 128-row B tiles (2 x 16 KB boxes) into a
-//             3-stage ring.
-//   warp 1    allocates all 512 TMEM columns; one lane issues
-//             tcgen05.mma.cta_group::1.kind::f16 (M = 128, N = 128, K = 16,
-//             BF16 x BF16 -> FP32): 2 row blocks x 8 K-steps per B tile, into
-//             one of two TMEM accumulator buffers; tcgen05.commit releases the
-//             B stage and hands the buffer to the epilogue.
-//   warps 2-9 epilogue: each thread owns one A row, reads its 128 FP32 dot
-//             products per tile with tcgen05.ld (32x32b.x32) and forms
-//             v = |b~|^2 - 2 a~.b~.  Per 32-column chunk it takes the minimum
-//             (three-input min tree) and keeps the row's two smallest chunk
-//             minima m1 <= m2; columns with v <= m2 + 2 delta go into the row's
-//             candidate buffer in shared memory.  No distance matrix is
-//             written; a split's output is its candidates (at most 8) and its
-//             own two smallest chunk minima.
-//   A work unit is (256-row block of A, one of S column splits of B); units
-//   are dealt round-robin to the persistent CTAs.  Every mbarrier wait is
-//   bounded by a 2 s clock limit; on expiry the CTA records LP_ERR_TIMEOUT,
-//   drains, frees its TMEM and returns.
+// Distances: the accumulator of one MMA holds D = a~.b~ - |b~|^2 / 2 = -v / 2
+// (v = |b~|^2 - 2 a~.b~, the squared distance up to the row constant |a~|^2):
+// eight K-steps of the BF16 descriptors plus a ninth in which A carries
+// (1, 1, 1, 0, ...) and B carries (-h1, -h2, -h3, 0, ...), a three-term BF16
+// split of |b~|^2 / 2 (invalid B rows get a huge value instead).
 //
-// Stage 2, k_rerank (one warp per row): candidates within 2*delta of m2 (the
-//   second-smallest chunk minimum over all splits) are re-scored with exactly
-//   the FP32 form's arithmetic (sequential FMA over k, then
-//   fma(-2, dot, |b|^2)), so their values are bit-identical to the FP32 form's.
-//   With unit, non-negative descriptors and BF16 unit roundoff u = 2^-8,
-//   |v~_j - v_j| <= 3u + 3u^2 + 1.1e-4 = delta for every column j.  m2 is at
-//   least the row's second-smallest BF16 value B, and every column with
-//   v~ <= B + 2 delta is a candidate, so every other column has v > B + delta,
-//   which is at least the exact second-best: the exact top 2 are found among
-//   the candidates.  A row whose candidate buffer overflowed in some split is
-//   queued.
-// Stage 3: queued rows are re-scanned with the FP32 form's arithmetic.
+// k_match_tc<pass> (persistent, one CTA per SM, clusters of two, 10 warps):
+//   warp 0    TMA producer: per work unit a 128-row A block (2 x 16 KB boxes,
+//             128-byte swizzle), then 256-row B tiles into a 2-stage ring;
+//             each CTA of the cluster loads one K-half (32 KB) of every tile
+//             and multicasts it to both CTAs (one L2 read per cluster).
+//   warp 1    allocates all 512 TMEM columns; one lane issues
+//             tcgen05.mma.cta_group::1.kind::f16 (M = 128, N = 256, K = 16,
+//             BF16 x BF16 -> FP32), 9 per B tile, into one of two 256-column
+//             TMEM accumulator buffers; tcgen05.commit releases the B stage
+//             (in both CTAs) and hands the buffer to the epilogue.
+//   warps 2-9 epilogue: each thread owns one A row and one 128-column half of
+//             every tile; it loads the half row from TMEM (tcgen05.ld
+//             32x32b.x32), returns the buffer, then works on registers.
+//             Pass 1 (every third tile): the two largest 32-column chunk
+//             maxima of D per (split, half, row), written as v.  Pass 2 (all
+//             tiles): every column with v <= T (a three-input max tree per
+//             chunk finds the rare chunks that hold one) is appended to the
+//             row's candidate list (capacity 64, one atomic per 4 columns).
+//   A work unit is (pair of 128-row blocks, one of S column splits of B); a
+//   cluster takes a contiguous run of units.  Every mbarrier wait is bounded
+//   by a 2 s clock limit; on expiry the CTA records LP_ERR_TIMEOUT, drains its
+//   copies, frees its TMEM and returns.
+//
+// k_row_threshold: T = m2 + delta + margin per row, m2 the second smallest of
+//   the pass-1 values.  With unit, non-negative descriptors and BF16 unit
+//   roundoff u = 2^-8, |v~_j - v_j| <= 3u + 3u^2 + 1.1e-4 = delta for every
+//   column, so every column outside the candidate list has an exact value
+//   above T - delta >= the exact second-best.
+// k_rerank (one warp per row): the candidates are re-scored with exactly the
+//   FP32 form's arithmetic (sequential FMA over k, then fma(-2, dot, |b|^2)),
+//   so their values are bit-identical to the FP32 form's; a row is certified
+//   when its exact second-best is < T - delta.  Rows with an overflowed list
+//   or without that margin are re-scanned in FP32 (k_rescan, k_rescan_merge).
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -50,20 +55,21 @@ __global__ void k_match_finish(const float4* part, int S, long long NA, const fl
 
 namespace {
 
-constexpr int kRowsPerUnit = 256;       // two M = 128 row blocks
-constexpr int kTileN = 128;             // B rows per tile (MMA N)
-constexpr int kStages = 4;              // B ring depth
+constexpr int kRowsPerUnit = 128;       // one M = 128 row block per CTA
+constexpr int kTileN = 256;             // B rows per tile (MMA N)
+constexpr int kTmemBufs = 2;            // accumulator buffers of kTileN columns (512 TMEM columns)
+constexpr int kStages = 2;              // B ring depth
 constexpr int kThreadsTC = 320;         // 10 warps
 constexpr int kEpiWarps = 8;
-constexpr uint32_t kABytes = kRowsPerUnit * 128 * 2;   // 64 KB
-constexpr uint32_t kBBytes = kTileN * 128 * 2;         // 32 KB per stage
+constexpr uint32_t kABytes = kRowsPerUnit * 128 * 2;   // 32 KB
+constexpr uint32_t kBBytes = kTileN * 128 * 2;         // 64 KB per stage
 // Ninth K-step: A rows extended by (1, 1, 1, 0, ..., 0), B rows by
 // (-h1, -h2, -h3, 0, ..., 0) with h1 + h2 + h3 = |b~|^2 / 2 (three BF16 terms),
 // so the accumulator holds D = a~.b~ - |b~|^2 / 2 = -v / 2.  16 BF16 per
 // extension row, 32-byte swizzle.
 constexpr uint32_t kExtRowBytes = 32;
-constexpr uint32_t kAExtBytes = kRowsPerUnit * kExtRowBytes;   // 8 KB, loaded once
-constexpr uint32_t kBExtBytes = kTileN * kExtRowBytes;         // 4 KB per stage
+constexpr uint32_t kAExtBytes = kRowsPerUnit * kExtRowBytes;   // 4 KB, loaded once
+constexpr uint32_t kBExtBytes = kTileN * kExtRowBytes;         // 8 KB per stage
 constexpr uint32_t kSmemTC =
     kABytes + kStages * kBBytes + kAExtBytes + kStages * kBExtBytes + 1024 /*barriers*/ + 1024 /*align slack*/;
 #ifndef LP_CAND_CAPACITY
@@ -276,10 +282,10 @@ __device__ __forceinline__ void tmem_wait(uint32_t (&r)[32])
 // ------------------------------------------------------------------ work split
 struct TcParams {
     long long NA, NB;
-    int nrp;               // number of pairs of 256-row blocks (one pair per CTA cluster)
+    int nrp;               // number of pairs of 128-row blocks (one pair per CTA cluster)
     int S;                 // column splits
     long long cps;         // columns per split (multiple of kTileN)
-    float2* pm;            // pass 1 output [S][NA]: the split's two smallest chunk minima
+    float2* pm;            // pass 1 output [2S][NA]: per split and column half, the two smallest chunk minima
     const float* thr;      // pass 2 input [NA]: candidate threshold per row (-inf: none)
     int32_t* cand;         // pass 2 output [NA][kCandCapacity]: candidate columns (unordered)
     int32_t* ncand;        // [NA]: candidates found (may exceed the capacity)
@@ -339,9 +345,9 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
     // barrier slots
     uint64_t* full = bars;                 // [kStages]
     uint64_t* empty = bars + kStages;      // [kStages]
-    uint64_t* tfull = bars + 2 * kStages;  // [2]
-    uint64_t* tempty = tfull + 2;          // [2]
-    uint64_t* afull = tempty + 2;          // [1]
+    uint64_t* tfull = bars + 2 * kStages;  // [kTmemBufs]
+    uint64_t* tempty = tfull + kTmemBufs;  // [kTmemBufs]
+    uint64_t* afull = tempty + kTmemBufs;  // [1]
     uint64_t* aempty = afull + 1;          // [1]
     uint64_t* drain = aempty + 1;          // [1]
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
@@ -360,7 +366,7 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
             mbar_init(smem_u32(&full[s]), 1);
             mbar_init(smem_u32(&empty[s]), 2);   // both CTAs' MMAs release a stage
         }
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < kTmemBufs; ++b) {
             mbar_init(smem_u32(&tfull[b]), 1);
             mbar_init(smem_u32(&tempty[b]), kEpiWarps);
         }
@@ -473,8 +479,8 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
                 for (int t = 0; t < ntiles; ++t, ++n) {
                     const int s = (int)(n % kStages);
                     const uint32_t k = (uint32_t)(n / kStages);
-                    const int b = (int)(n & 1);
-                    const uint32_t kb = (uint32_t)(n >> 1);
+                    const int b = (int)(n % kTmemBufs);
+                    const uint32_t kb = (uint32_t)(n / kTmemBufs);
                     ok = mbar_wait(smem_u32(&tempty[b]), (kb & 1) ^ 1, abort_flag, p.status);
                     if (!ok) break;
                     ok = mbar_wait(smem_u32(&full[s]), k & 1, abort_flag, p.status);
@@ -482,19 +488,16 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
                     tc_fence_after();
                     const uint64_t dB = dB0 + (uint64_t)((s * kBBytes) >> 4);
                     const uint64_t dBx = dBx0 + (uint64_t)((s * kBExtBytes) >> 4);
+                    const uint32_t d = tmem + (uint32_t)(b * kTileN);
 #pragma unroll
-                    for (int rb = 0; rb < 2; ++rb) {
-                        const uint32_t d = tmem + (uint32_t)((b * 2 + rb) * kTileN);
+                    for (int h = 0; h < 2; ++h)
 #pragma unroll
-                        for (int h = 0; h < 2; ++h)
-#pragma unroll
-                            for (int kk = 0; kk < 4; ++kk) {
-                                const uint64_t ad = dA0 + (uint64_t)((rb * (128 * 128) + h * (kABytes / 2) + kk * 32) >> 4);
-                                const uint64_t bd = dB + (uint64_t)((h * (kBBytes / 2) + kk * 32) >> 4);
-                                mma_bf16(d, ad, bd, (h | kk) ? 1u : 0u);
-                            }
-                        mma_bf16(d, dAx0 + (uint64_t)((rb * 128 * kExtRowBytes) >> 4), dBx, 1u);
-                    }
+                        for (int kk = 0; kk < 4; ++kk) {
+                            const uint64_t ad = dA0 + (uint64_t)((h * (kABytes / 2) + kk * 32) >> 4);
+                            const uint64_t bd = dB + (uint64_t)((h * (kBBytes / 2) + kk * 32) >> 4);
+                            mma_bf16(d, ad, bd, (h | kk) ? 1u : 0u);
+                        }
+                    mma_bf16(d, dAx0, dBx, 1u);
                     mma_commit_mc(smem_u32(&empty[s]), 3);
                     mma_commit(smem_u32(&tfull[b]));
                 }
@@ -514,8 +517,8 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
         //   lane holds up to 4 in registers and appends them to the row's list
         //   (one atomic slot reservation per flush).
         const int q = warp & 3;                 // TMEM lane quarter this warp may access
-        const int rb = (warp - 2) >> 2;         // row block 0 (warps 2-5) or 1 (warps 6-9)
-        const int row_in_unit = rb * 128 + q * 32 + lane;
+        const int half = (warp - 2) >> 2;       // columns [0, 128) (warps 2-5) or [128, 256) (warps 6-9) of a tile
+        const int row_in_unit = q * 32 + lane;
         long long n = 0;
         bool ok = true;
         for (int u = u_begin; u < u_end && ok; ++u) {
@@ -530,13 +533,13 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
             const float TD = (kPass == 2 && live) ? -0.5f * p.thr[row] : INFINITY;  // pass 2
             int nc = 0, cj0 = 0, cj1 = 0, cj2 = 0, cj3 = 0;
             for (int t = 0; t < ntiles; ++t, ++n) {
-                const int b = (int)(n & 1);
-                const uint32_t kb = (uint32_t)(n >> 1);
+                const int b = (int)(n % kTmemBufs);
+                const uint32_t kb = (uint32_t)(n / kTmemBufs);
                 ok = mbar_wait(smem_u32(&tfull[b]), kb & 1, abort_flag, p.status);
                 if (!ok) break;
                 tc_fence_after();
-                const long long cbase = c0 + (long long)t * p.tstride * kTileN;
-                const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)((b * 2 + rb) * kTileN);
+                const long long cbase = c0 + (long long)t * p.tstride * kTileN + half * 128;
+                const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * kTileN + half * 128);
                 // the whole tile row in registers, then the buffer goes back to the MMA
                 uint32_t r0[32], r1[32], r2[32], r3[32];
                 tmem_ld32(tbase, r0);
@@ -551,7 +554,7 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
                 __syncwarp();
                 if (lane == 0) mbar_arrive(smem_u32(&tempty[b]));
 #pragma unroll
-                for (int ch = 0; ch < kTileN / 32; ++ch) {
+                for (int ch = 0; ch < 4; ++ch) {
                     const uint32_t (&cur)[32] = ch == 0 ? r0 : ch == 1 ? r1 : ch == 2 ? r2 : r3;
                     float dv[32];
 #pragma unroll
@@ -596,7 +599,7 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
                 }
             }
             if (!ok) break;
-            if (kPass == 1 && live) p.pm[(long long)split * p.NA + row] = make_float2(-2.f * d1, -2.f * d2);
+            if (kPass == 1 && live) p.pm[((long long)split * 2 + half) * p.NA + row] = make_float2(-2.f * d1, -2.f * d2);
             if (kPass == 2 && nc > 0) flush_cands(p.ncand, p.cand, row, nc, cj0, cj1, cj2, cj3);
         }
     }
@@ -927,7 +930,7 @@ int pick_tc_splits(int nrp, long long NB, int sms)
     for (int S = 1; S <= 32 && S <= tiles; ++S) {
         const long long U = (long long)nrp * S;
         const double rounds = (double)((U + sms - 1) / sms);
-        const double cost = rounds * (double)((tiles + S - 1) / S + 2);
+        const double cost = rounds * (double)((tiles + S - 1) / S + 256 / kTileN);
         if (cost < best_cost - 1e-9) { best_cost = cost; best = S; }
     }
     return best;
@@ -950,7 +953,7 @@ TcLayout tc_layout(long long NA, long long NB, int sms)
     L.off_aext = take(kAExtBytes);
     L.off_na = take(sizeof(float) * (size_t)NA);
     L.off_nb32 = take(sizeof(float) * (size_t)NB);
-    L.off_pm = take(sizeof(float2) * (size_t)L.S * NA);
+    L.off_pm = take(sizeof(float2) * 2 * (size_t)L.S * NA);
     L.off_thr = take(sizeof(float) * (size_t)NA);
     L.off_cand = take(sizeof(int32_t) * kCandCapacity * (size_t)NA);
     L.off_ncand = take(sizeof(int32_t) * (size_t)NA);
@@ -1045,7 +1048,7 @@ cudaError_t launch_match_bf16(const MatchArgs& a, void* ws, size_t ws_bytes, int
         TcParams p1 = p;
         p1.tstride = kPass1Stride;
         if ((e = cudaLaunchKernelEx(&cfg, k_match_tc<1>, tA, tB, tAx, tBx, p1)) != cudaSuccess) return e;
-        k_row_threshold<<<(unsigned)((a.NA + 255) / 256), 256, 0, s>>>(pm, L.S, a.NA, a.vA, kDelta, thr, ncand);
+        k_row_threshold<<<(unsigned)((a.NA + 255) / 256), 256, 0, s>>>(pm, 2 * L.S, a.NA, a.vA, kDelta, thr, ncand);
         if ((e = cudaLaunchKernelEx(&cfg, k_match_tc<2>, tA, tB, tAx, tBx, p)) != cudaSuccess) return e;
         if (a.ev1) cudaEventRecord(a.ev1, s);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
