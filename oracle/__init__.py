@@ -75,6 +75,7 @@ def lib():
             "or_guided_stop_k": (i32, [C.c_uint64, C.c_uint64, i32, i32]),
             "or_ransac_sample_guided_k": (i32, [i64, P, C.c_uint64, u32, i32, i32, P]),
             "or_mosaic_plan": (i32, [i32, P, i32, P, P, P, P, P, P, P, P, P]),
+            "or_border_valid": (i32, [P, P, i64, i32, i32, P]),
             "or_mosaic_render": (i32, [i32, P, P, P, P, i32, P, P, i32, i32, P, P]),
         }
         for name, (res, args) in sig.items():
@@ -160,7 +161,7 @@ def orient(g: np.ndarray, idx: np.ndarray, ws: np.ndarray, want_hist: bool = Fal
     return (ori, hist) if want_hist else ori
 
 
-def describe(g: np.ndarray, idx: np.ndarray, ws: np.ndarray, ori: np.ndarray | None):
+def describe(g: np.ndarray, idx: np.ndarray, ws: np.ndarray, ori: np.ndarray | None, border: bool = False):
     g = _c(g, np.uint8)
     H, W = g.shape
     idx = _c(idx, np.uint32)
@@ -170,6 +171,8 @@ def describe(g: np.ndarray, idx: np.ndarray, ws: np.ndarray, ori: np.ndarray | N
     desc = np.empty((K, 128), np.float64)
     valid = np.empty(K, np.uint8)
     assert lib().or_describe(_p(g), H, W, W, _p(idx), _p(ws), _p(o), K, _p(desc), _p(valid)) == 0
+    if border:
+        assert lib().or_border_valid(_p(idx), _p(ws), K, H, W, _p(valid)) == 0
     return desc, valid
 
 
@@ -286,22 +289,23 @@ def match_points(idxA, idxB, m, WA: int, WB: int) -> tuple[np.ndarray, np.ndarra
     return np.concatenate([pa, pb], axis=1), rows
 
 
-def features(img: np.ndarray, Ls, beta0: float = 0.0, upright: bool = False):
+def features(img: np.ndarray, Ls, beta0: float = 0.0, upright: bool = False, alpha: float = 0.0,
+             border: bool = False):
     """Sec. 2.1-2.3 for one image: gray, peaks, orientation, descriptors."""
     g = gray(img)
     H, W = g.shape
-    idx = detect(g, Ls)
+    idx = detect(g, Ls, alpha)
     _, ws = keypoint_scales(H, W, Ls, beta0)
     ori = None if upright else orient(g, idx, ws)
-    desc, valid = describe(g, idx, ws, ori)
+    desc, valid = describe(g, idx, ws, ori, border)
     return dict(gray=g, idx=idx, ws=ws, ori=ori, desc=desc, valid=valid)
 
 
 def stitch_pair(imgA, imgB, Ls, ratio=0.8, T=1000, thresh=3.0, seed=0, pair_id=0, upright=False,
-                delta_s=float("inf"), model=MODEL_HOMOGRAPHY):
+                delta_s=float("inf"), model=MODEL_HOMOGRAPHY, alpha=0.0, border=False):
     """Sec. 2 end to end for one pair (Fig. 2): H from A to B and its inliers."""
-    fa = features(imgA, Ls, upright=upright)
-    fb = features(imgB, Ls, upright=upright)
+    fa = features(imgA, Ls, upright=upright, alpha=alpha, border=border)
+    fb = features(imgB, Ls, upright=upright, alpha=alpha, border=border)
     m, d1, d2, _, _ = match(fa["desc"], fa["valid"], fb["desc"], fb["valid"], ratio, delta_s)
     pts, rows = match_points(fa["idx"], fb["idx"], m, fa["gray"].shape[1], fb["gray"].shape[1])
     r = ransac(pts, T, thresh, seed, pair_id, model=model)

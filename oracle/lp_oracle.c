@@ -279,12 +279,31 @@ int or_describe(const uint8_t* gray, int H, int W, int pitch, const uint32_t* id
     return 0;
 }
 
+/* Border rejection (a paper-literal variant of Sec. 2.3; the default reading
+ * clamps to the edge): a point of region side w_s is invalid when the pixels
+ * within P = ceil(2 sqrt(2) w_s + 1.5) + 1 of it do not all lie inside the
+ * image.  P bounds every pixel that the orientation window (|u|, |v| <= 2 w_s,
+ * plus one-pixel gradient taps) and the turned descriptor grid (radius
+ * sqrt(2) (2 w_s + 1), plus bilinear taps) can read. */
+int or_border_valid(const uint32_t* idx, const int* ws, int64_t K, int H, int W, uint8_t* valid)
+{
+    if ((K > 0 && (!idx || !ws || !valid)) || H <= 0 || W <= 0) return -1;
+    for (int64_t k = 0; k < K; ++k) {
+        const int P = (int)ceil(2.0 * sqrt(2.0) * ws[k] + 1.5) + 1;
+        const int y = (int)(idx[k] / (uint32_t)W), x = (int)(idx[k] % (uint32_t)W);
+        if (x - P < 0 || y - P < 0 || x + P > W - 1 || y + P > H - 1) valid[k] = 0;
+    }
+    return 0;
+}
+
 /* ------------------------------------------------------------------ */
 /* Sec. 2.4, Eq. 6: Delta = |d_f1 - d_f2|.  Readings: every valid point of the
  * reference image queries all valid points of the registered image; the
  * nearest one (lowest index on ties) is kept when it passes the ratio test
  * Delta_1 < ratio * Delta_2 (Delta_2 = the next nearest) and, when set,
- * Delta_1 < Delta_s. */
+ * Delta_1 < Delta_s.  ratio = 0 drops the ratio test: the paper's own rule
+ * keeps a nearest neighbour on Delta_1 < Delta_s alone (any valid candidate
+ * when Delta_s is off). */
 int or_match(const double* dA, const uint8_t* vA, int64_t NA, const double* dB, const uint8_t* vB,
              int64_t NB, double ratio, double delta_s, const int64_t* rows, int64_t nrows,
              int32_t* match, double* d1, double* d2, int32_t* j1o, int32_t* j2o)
@@ -322,7 +341,7 @@ int or_match(const double* dA, const uint8_t* vA, int64_t NA, const double* dB, 
         d2[q] = sqrt(b2);
         if (j1o) j1o[q] = (int32_t)j1;
         if (j2o) j2o[q] = (int32_t)j2;
-        int ok = nbv >= 2 && b1 < ratio * ratio * b2;
+        int ok = ratio > 0 ? (nbv >= 2 && b1 < ratio * ratio * b2) : nbv >= 1;
         if (delta_s > 0 && isfinite(delta_s)) ok = ok && sqrt(b1) < delta_s;
         if (ok) match[q] = (int32_t)j1;
     }

@@ -79,6 +79,10 @@ int or_dlt4(const double* src /*4x2 (x,y)*/, const double* dst /*4x2*/, double* 
 /* Least-squares DLT over the masked correspondences; returns 0, or 1 on failure. */
 int or_refit(const double* pts /*M x 4: xA yA xB yB*/, const uint8_t* mask, int64_t M, double* H);
 
+/* Border rejection (paper-literal variant): clears valid[k] when the pixels
+ * within ceil(2 sqrt(2) ws[k] + 1.5) + 1 of point k leave the image. */
+int or_border_valid(const uint32_t* idx, const int* ws, int64_t K, int H, int W, uint8_t* valid);
+
 /* Symmetric eigen-decomposition (cyclic Jacobi), ascending eigenvalues,
  * eigenvectors in the columns of evecs (row-major n x n). */
 int or_eig_sym(int n, const double* A, double* evals, double* evecs);
