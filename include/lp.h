@@ -75,7 +75,8 @@ typedef struct lp_config {
     int32_t  nL;                  /* number of window sizes, 1..LP_MAX_SCALES */
     int32_t  Ls[LP_MAX_SCALES];   /* interrogation window sizes L (Eq. 2), >= 2 */
     double   beta0;               /* Eq. 3 beta0; <= 0 selects (1/d) sqrt(Lmin/Lmax) */
-    float    ratio;               /* ratio test: accept Delta1 < ratio * Delta2 */
+    float    ratio;               /* ratio test: accept Delta1 < ratio * Delta2; 0 = no ratio
+                                     test (Sec. 2.4 literally: Delta1 < Delta_s alone) */
     float    delta_s;             /* Delta_s of Sec. 2.4; <= 0 or inf disables it */
     int32_t  ransac_iters;        /* RANSAC iterations T, 1..65536 */
     float    thresh_px;           /* inlier threshold on reprojection error (px) */
@@ -84,6 +85,12 @@ typedef struct lp_config {
     int32_t  precision;           /* lp_precision */
     int32_t  upright;             /* 1: every orientation is 0 (no rotation) */
     int32_t  model;               /* lp_model of lp_ransac and the stitch calls */
+    /* Paper-literal variants (off by default). */
+    double   alpha;               /* Eq. 1 ramp coefficient: 0 = the limit alpha -> 0+ (exact
+                                     integer keys); > 0 = M + alpha * (raster index + 1) in
+                                     FP64, ties to the earlier raster position */
+    int32_t  border;              /* 1: a point whose describe neighbourhood (radius
+                                     ceil(2 sqrt(2) w_s + 1.5) + 1) leaves the image is invalid */
 } lp_config;
 
 typedef struct lp_ctx lp_ctx;

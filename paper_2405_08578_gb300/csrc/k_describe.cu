@@ -773,10 +773,44 @@ cudaError_t launch_build_luts(void* luts, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_describe(const uint8_t* gray, int H, int W, int pitch, const uint32_t* kp,
-                            const ScaleTable& st, int upright, const void* luts, uint8_t* ori, float* desc,
-                            uint16_t* desc_bf16, uint8_t* valid, cudaStream_t s)
+// Border rejection (a paper-literal variant; off by default): a point whose
+// neighbourhood of radius P = ceil(2 sqrt(2) w_s + 1.5) + 1 -- every pixel its
+// orientation window, turned grid and their taps can read -- does not lie
+// inside the image is marked invalid, so no kept description depends on the
+// clamp-to-edge reading.
+struct BorderParams {
+    long long off[LP_MAX_SCALES + 1];
+    int pr[LP_MAX_SCALES];
+    int nL;
+};
+
+__global__ void k_border_reject(const uint32_t* kp, int H, int W, const BorderParams b, uint8_t* valid)
 {
+    const long long k = (long long)blockIdx.x * 256 + threadIdx.x;
+    if (k >= b.off[b.nL]) return;
+    int l = 0;
+    while (l + 1 < b.nL && k >= b.off[l + 1]) ++l;
+    const int P = b.pr[l];
+    const uint32_t id = kp[k];
+    const int y = (int)(id / (uint32_t)W), x = (int)(id - (uint32_t)y * (uint32_t)W);
+    if (x < P || y < P || x + P > W - 1 || y + P > H - 1) valid[k] = 0;
+}
+
+cudaError_t launch_describe(const uint8_t* gray, int H, int W, int pitch, const uint32_t* kp,
+                            const ScaleTable& st, int upright, int border, const void* luts, uint8_t* ori,
+                            float* desc, uint16_t* desc_bf16, uint8_t* valid, cudaStream_t s)
+{
+    if (border) {
+        cudaError_t e = launch_describe(gray, H, W, pitch, kp, st, upright, 0, luts, ori, desc, desc_bf16, valid, s);
+        if (e != cudaSuccess) return e;
+        BorderParams b;
+        b.nL = st.nL;
+        for (int l = 0; l <= st.nL; ++l) b.off[l] = st.off[l];
+        for (int l = 0; l < st.nL; ++l) b.pr[l] = st.pr[l];
+        const long long K = st.off[st.nL];
+        if (K > 0) k_border_reject<<<(unsigned)((K + 255) / 256), 256, 0, s>>>(kp, H, W, b, valid);
+        return cudaGetLastError();
+    }
     DescParams p;
     p.gray = gray; p.H = H; p.W = W; p.pitch = pitch; p.kp = kp;
     for (int k = 0; k < 36; ++k) {

@@ -211,6 +211,55 @@ __global__ void __launch_bounds__(kDetectThreads) k_detect_window(const uint8_t*
     (void)H;
 }
 
+// Eq. 1 with a finite alpha: M_n = g + alpha * (raster index + 1) in FP64, one
+// rounding for the product and one for the sum (no contraction); the maximum
+// and minimum of each window, equal values going to the earlier raster
+// position (the first in the window's row-major scan).
+template <int CH>
+__global__ void __launch_bounds__(kDetectThreads) k_detect_window_ramp(const uint8_t* img, int W, int pitch, int L,
+                                                                        int nwx, long long off, double alpha,
+                                                                        uint32_t* kp)
+{
+    const int w = blockIdx.x;
+    const int wy = w / nwx, wx = w - wy * nwx;
+    double vmax = -INFINITY, vmin = INFINITY;
+    uint32_t imax = 0xFFFFFFFFu, imin = 0xFFFFFFFFu;
+    const int n = L * L;
+    for (int i = threadIdx.x; i < n; i += kDetectThreads) {
+        const int r = i / L, c = i - r * L;
+        const int y = wy * L + r, x = wx * L + c;
+        const uint8_t* px = img + (size_t)y * pitch + (size_t)CH * x;
+        const uint32_t g = CH == 1 ? px[0] : rgb2gray(px[0], px[1], px[2]);
+        const uint32_t id = (uint32_t)y * (uint32_t)W + (uint32_t)x;
+        const double v = __dadd_rn((double)g, __dmul_rn(alpha, (double)id + 1.0));
+        if (v > vmax || (v == vmax && id < imax)) { vmax = v; imax = id; }
+        if (v < vmin || (v == vmin && id < imin)) { vmin = v; imin = id; }
+    }
+    for (int o = 16; o; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xFFFFFFFFu, vmax, o);
+        const uint32_t oi = __shfl_xor_sync(0xFFFFFFFFu, imax, o);
+        if (ov > vmax || (ov == vmax && oi < imax)) { vmax = ov; imax = oi; }
+        const double nv = __shfl_xor_sync(0xFFFFFFFFu, vmin, o);
+        const uint32_t ni = __shfl_xor_sync(0xFFFFFFFFu, imin, o);
+        if (nv < vmin || (nv == vmin && ni < imin)) { vmin = nv; imin = ni; }
+    }
+    __shared__ double rv[2][kDetectThreads / 32];
+    __shared__ uint32_t ri[2][kDetectThreads / 32];
+    if ((threadIdx.x & 31) == 0) {
+        rv[0][threadIdx.x >> 5] = vmax; ri[0][threadIdx.x >> 5] = imax;
+        rv[1][threadIdx.x >> 5] = vmin; ri[1][threadIdx.x >> 5] = imin;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int q = 1; q < kDetectThreads / 32; ++q) {
+            if (rv[0][q] > vmax || (rv[0][q] == vmax && ri[0][q] < imax)) { vmax = rv[0][q]; imax = ri[0][q]; }
+            if (rv[1][q] < vmin || (rv[1][q] == vmin && ri[1][q] < imin)) { vmin = rv[1][q]; imin = ri[1][q]; }
+        }
+        kp[off + 2ll * w] = imax;
+        kp[off + 2ll * w + 1] = imin;
+    }
+}
+
 __global__ void k_rgb_to_gray(const uint8_t* img, int H, int W, int pitch, uint8_t* gray)
 {
     const long long n = (long long)H * W;
@@ -229,9 +278,23 @@ __global__ void k_diag_gray(const uint8_t* rgb, long long n, uint8_t* gray)
 
 }  // namespace
 
-cudaError_t launch_detect(const uint8_t* img, int H, int W, int pitch, int ch, const ScaleTable& st,
+cudaError_t launch_detect(const uint8_t* img, int H, int W, int pitch, int ch, const ScaleTable& st, double alpha,
                           uint32_t* kp, uint8_t* gray, cudaStream_t s)
 {
+    if (alpha > 0.0) {
+        if (ch == 3) k_rgb_to_gray<<<1216, 256, 0, s>>>(img, H, W, pitch, gray);
+        for (int l = 0; l < st.nL; ++l) {
+            const int nw = st.nwx[l] * st.nwy[l];
+            if (nw == 0) continue;
+            if (ch == 1)
+                k_detect_window_ramp<1><<<nw, kDetectThreads, 0, s>>>(img, W, pitch, st.L[l], st.nwx[l], st.off[l],
+                                                                      alpha, kp);
+            else
+                k_detect_window_ramp<3><<<nw, kDetectThreads, 0, s>>>(img, W, pitch, st.L[l], st.nwx[l], st.off[l],
+                                                                      alpha, kp);
+        }
+        return cudaGetLastError();
+    }
     bool nested = st.L[st.nL - 1] <= 128;
     for (int l = 1; l < st.nL && nested; ++l) nested = st.L[l] % st.L[l - 1] == 0;
     int TS = st.L[st.nL - 1];

@@ -199,7 +199,8 @@ __global__ void k_row_norms(const float* d, const uint8_t* v, long long n, float
 }
 
 // Merge S partial top-2 lists (split order = column order), then Eq. 6 and the
-// ratio test.  part rows hold (b1, b2, j1, j2) with b = |b|^2 - 2 a.b.
+// ratio test (ratio2 = 0: no ratio test, any valid nearest neighbour passes to
+// the Delta_s test).  part rows hold (b1, b2, j1, j2) with b = |b|^2 - 2 a.b.
 __global__ void k_match_finish(const float4* part, int S, long long NA, const float* na, const uint8_t* vA,
                                float ratio2, float delta_s2, int32_t* match, float* d1, float* d2)
 {
@@ -213,7 +214,8 @@ __global__ void k_match_finish(const float4* part, int S, long long NA, const fl
     }
     const float a2 = na[i];
     const float e1 = fmaxf(a2 + t.b1, 0.f), e2 = fmaxf(a2 + t.b2, 0.f);
-    const bool ok = vA[i] && t.j2 >= 0 && isfinite(t.b2) && e1 < ratio2 * e2 && e1 < delta_s2;
+    const bool ratio_ok = ratio2 > 0.f ? (t.j2 >= 0 && isfinite(t.b2) && e1 < ratio2 * e2) : (t.j1 >= 0 && isfinite(t.b1));
+    const bool ok = vA[i] && ratio_ok && e1 < delta_s2;
     match[i] = ok ? t.j1 : -1;
     d1[i] = (vA[i] && t.j1 >= 0) ? sqrtf(e1) : INFINITY;
     d2[i] = (vA[i] && t.j2 >= 0) ? sqrtf(e2) : INFINITY;

@@ -118,7 +118,9 @@ int check_cfg(lp_ctx* c, const lp_config* cfg)
         for (int m = 0; m < l; ++m)
             if (cfg->Ls[m] == cfg->Ls[l]) return fail(c, LP_ERR_ARG, "window size %d repeated", cfg->Ls[l]);
     }
-    if (!(cfg->ratio > 0.f && cfg->ratio <= 1.f)) return fail(c, LP_ERR_ARG, "ratio must be in (0, 1]");
+    if (!(cfg->ratio >= 0.f && cfg->ratio <= 1.f)) return fail(c, LP_ERR_ARG, "ratio must be in [0, 1]");
+    if (!(cfg->alpha >= 0.0 && cfg->alpha < 1e300)) return fail(c, LP_ERR_ARG, "alpha must be finite and >= 0");
+    if (cfg->border != 0 && cfg->border != 1) return fail(c, LP_ERR_ARG, "border must be 0 or 1");
     if (cfg->ransac_iters < 1 || cfg->ransac_iters > 65536) return fail(c, LP_ERR_ARG, "ransac_iters outside 1..65536");
     if (!(cfg->thresh_px > 0.f)) return fail(c, LP_ERR_ARG, "thresh_px must be > 0");
     if (cfg->precision != LP_PREC_FP32 && cfg->precision != LP_PREC_BF16)
@@ -204,6 +206,8 @@ int lp_config_default(lp_config* cfg)
     cfg->precision = LP_PREC_FP32;
     cfg->upright = 0;
     cfg->model = LP_MODEL_HOMOGRAPHY;
+    cfg->alpha = 0.0;
+    cfg->border = 0;
     return LP_OK;
 }
 
@@ -269,7 +273,7 @@ int lp_detect(lp_ctx* c, const uint8_t* img, int H, int W, int pitch, int channe
     lp::ScaleTable st;
     lp::make_scale_table(c->cfg.Ls, c->cfg.nL, c->cfg.beta0, H, W, &st);
     c->last = S(stream);
-    LP_CUDA(c, lp::launch_detect(img, H, W, pitch, channels, st, kp_idx, gray, S(stream)));
+    LP_CUDA(c, lp::launch_detect(img, H, W, pitch, channels, st, c->cfg.alpha, kp_idx, gray, S(stream)));
     return LP_OK;
 }
 
@@ -291,8 +295,8 @@ int lp_describe(lp_ctx* c, const uint8_t* gray, int H, int W, int gray_pitch, co
         int r = build_luts(c, S(stream));
         if (r) return r;
     }
-    LP_CUDA(c, lp::launch_describe(gray, H, W, gray_pitch, kp_idx, st, c->cfg.upright, c->buf[B_LUTS].p, ori, desc,
-                                   desc_bf16, valid, S(stream)));
+    LP_CUDA(c, lp::launch_describe(gray, H, W, gray_pitch, kp_idx, st, c->cfg.upright, c->cfg.border,
+                                   c->buf[B_LUTS].p, ori, desc, desc_bf16, valid, S(stream)));
     return LP_OK;
 }
 

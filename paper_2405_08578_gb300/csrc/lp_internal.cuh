@@ -31,16 +31,18 @@ int make_scale_table(const int* Ls, int nL, double beta0, int H, int W, ScaleTab
 
 // ---- kernel launchers (each .cu file owns its kernels) ----
 // k_detect.cu
-cudaError_t launch_detect(const uint8_t* img, int H, int W, int pitch, int ch, const ScaleTable& st,
+// alpha > 0: Eq. 1's literal FP64 ramp (one launch per scale); 0: integer keys
+cudaError_t launch_detect(const uint8_t* img, int H, int W, int pitch, int ch, const ScaleTable& st, double alpha,
                           uint32_t* kp, uint8_t* gray, cudaStream_t s);
 cudaError_t launch_diag_gray(const uint8_t* rgb, int64_t n, uint8_t* gray, cudaStream_t s);
 
 // k_describe.cu
 size_t describe_lut_bytes();
 cudaError_t launch_build_luts(void* luts, cudaStream_t s);
+// border = 1: points whose neighbourhood (radius st.pr) leaves the image are marked invalid
 cudaError_t launch_describe(const uint8_t* gray, int H, int W, int pitch, const uint32_t* kp,
-                            const ScaleTable& st, int upright, const void* luts, uint8_t* ori, float* desc,
-                            uint16_t* desc_bf16, uint8_t* valid, cudaStream_t s);
+                            const ScaleTable& st, int upright, int border, const void* luts, uint8_t* ori,
+                            float* desc, uint16_t* desc_bf16, uint8_t* valid, cudaStream_t s);
 cudaError_t launch_diag_orient(int32_t* bins, uint32_t* weights, cudaStream_t s);
 
 // k_match.cu

@@ -1,0 +1,104 @@
+"""Paper-literal variants through the C ABI against the oracle: Eq. 1's finite
+alpha ramp, border rejection, and Sec. 2.4's match rule without a ratio test."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2405_08578_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a GPU", allow_module_level=True)
+
+from paper_2405_08578_gb300 import lp  # noqa: E402
+import gpu_util as G  # noqa: E402
+
+DESC_TOL = 1e-4
+NEAR_TIE = 1e-5
+
+
+@pytest.mark.parametrize("alpha", [1e-9, 1e-5, 0.01, 0.7, 50.0])
+@pytest.mark.parametrize("shape,Ls,ch", [((96, 130), (8, 16), 1), ((75, 101), (5, 7, 12), 3),
+                                         ((480, 640), (8, 16, 32), 1), ((300, 410), (32, 40), 3)])
+def test_detect_finite_alpha_bitexact(alpha, shape, Ls, ch):
+    rng = np.random.default_rng(shape[0] + int(1e3 * alpha) % 97)
+    for levels in (256, 3):
+        img = rng.integers(0, levels, size=shape + ((3,) if ch == 3 else ())).astype(np.uint8)
+        ctx = lp.Context(Ls=Ls, alpha=alpha)
+        kp, g = G.detect(ctx, img)
+        og = oracle.gray(img)
+        assert np.array_equal(kp, oracle.detect(og, Ls, alpha))
+        if ch == 3:
+            assert np.array_equal(g, og)
+
+
+@pytest.mark.parametrize("upright", [False, True])
+@pytest.mark.parametrize("shape,Ls", [((150, 190), (8, 16, 32)), ((240, 320), (16, 32, 64)),
+                                      ((260, 330), (100, 128))])
+def test_border_rejection_valid_flags(shape, Ls, upright):
+    p = synth.small_pair(shape[0], shape[1], seed=shape[1])
+    g = p.A
+    H, W = g.shape
+    ctx = lp.Context(Ls=Ls, border=True, upright=upright)
+    kp = oracle.detect(g, Ls)
+    ori, desc, valid = G.describe(ctx, g, kp)
+    _, ws = oracle.keypoint_scales(H, W, Ls)
+    o_ori = None if upright else oracle.orient(g, kp, ws)
+    o_desc, o_valid = oracle.describe(g, kp, ws, o_ori, border=True)
+    assert np.array_equal(valid, o_valid)
+    keep = o_valid.astype(bool)
+    if not upright:
+        assert np.array_equal(ori, o_ori)
+    if keep.any():
+        assert np.abs(desc[keep] - o_desc[keep]).max() <= DESC_TOL
+    # the flag only removes points: without it the same points are described
+    _, _, valid_all = G.describe(lp.Context(Ls=Ls, upright=upright), g, kp)
+    assert not (valid.astype(bool) & ~valid_all.astype(bool)).any()
+
+
+def _unit(rng, n):
+    d = np.abs(rng.standard_normal((n, 128))).astype(np.float32)
+    return d / np.linalg.norm(d, axis=1, keepdims=True)
+
+
+@pytest.mark.parametrize("precision", [lp.PREC_FP32, lp.PREC_BF16])
+@pytest.mark.parametrize("NA,NB,delta_s", [(300, 517, None), (1000, 777, 0.9), (2049, 4099, 1.0), (64, 1, None)])
+def test_match_without_ratio_test(NA, NB, delta_s, precision):
+    rng = np.random.default_rng(NA + 7 * NB)
+    A = _unit(rng, NA)
+    B = _unit(rng, NB)
+    k = min(NA, NB) // 2
+    B[:k] = A[:k] + 0.03 * rng.standard_normal((k, 128)).astype(np.float32)
+    B[:k] = np.abs(B[:k]) / np.linalg.norm(B[:k], axis=1, keepdims=True)
+    vA = (rng.uniform(size=NA) > 0.05).astype(np.uint8)
+    vB = np.ones(NB, np.uint8) if NB == 1 else (rng.uniform(size=NB) > 0.05).astype(np.uint8)
+    ds = float("inf") if delta_s is None else delta_s
+    ctx = lp.Context(Ls=(16,), precision=precision, ratio=0.0, delta_s=ds)
+    m, d1, _ = G.match(ctx, A, vA, B, vB)
+    om, od1, od2, _, _ = oracle.match(A.astype(np.float64), vA, B.astype(np.float64), vB, ratio=0.0,
+                                      delta_s=float(np.float32(ds)) if np.isfinite(ds) else ds)
+    near = (np.isfinite(od2) & (od2 - od1 <= NEAR_TIE)) | (np.abs(od1 - ds) <= NEAR_TIE)
+    assert np.array_equal(m[~near], om[~near])
+    assert (om >= 0).sum() > 0.3 * NA
+    fin = ~near & np.isfinite(od1)
+    assert np.abs(d1[fin] - od1[fin]).max(initial=0) < 1e-5
+
+
+def test_literal_pair_640x480_vs_oracle():
+    p = synth.pair_640x480(0)
+    Ls = synth.PAIR_640x480_LS
+    kw = dict(ratio=0.0, delta_s=0.25, alpha=1e-5, border=True)
+    ctx = lp.Context(Ls=Ls, precision=lp.PREC_BF16, **kw)
+    Hg, n_in, M = G.stitch(ctx, p.A, p.B)
+    o = oracle.stitch_pair(p.A, p.B, Ls, **kw)
+    ys, xs = np.mgrid[0:480:40, 0:640:40]
+    q = np.c_[xs.ravel(), ys.ravel()].astype(np.float64)
+    pb = G.proj(p.H, q)
+    q = q[(pb[:, 0] >= 0) & (pb[:, 0] < 640) & (pb[:, 1] >= 0) & (pb[:, 1] < 480)]
+    assert abs(M - (o["match"] >= 0).sum()) <= 2 and abs(n_in - o["n_in"]) <= 2
+    assert n_in >= 50
+    assert np.abs(G.proj(Hg, q) - G.proj(o["H"], q)).max() < 0.5
+    assert np.abs(G.proj(Hg, q) - G.proj(p.H, q)).max() < 2.0
