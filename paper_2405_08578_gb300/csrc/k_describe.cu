@@ -798,10 +798,11 @@ __global__ void k_border_reject(const uint32_t* kp, int H, int W, const BorderPa
 
 cudaError_t launch_describe(const uint8_t* gray, int H, int W, int pitch, const uint32_t* kp,
                             const ScaleTable& st, int upright, int border, const void* luts, uint8_t* ori,
-                            float* desc, uint16_t* desc_bf16, uint8_t* valid, cudaStream_t s)
+                            float* desc, uint16_t* desc_bf16, uint8_t* valid, const Fork* fork, cudaStream_t s)
 {
     if (border) {
-        cudaError_t e = launch_describe(gray, H, W, pitch, kp, st, upright, 0, luts, ori, desc, desc_bf16, valid, s);
+        cudaError_t e = launch_describe(gray, H, W, pitch, kp, st, upright, 0, luts, ori, desc, desc_bf16, valid,
+                                        fork, s);
         if (e != cudaSuccess) return e;
         BorderParams b;
         b.nL = st.nL;
@@ -837,6 +838,18 @@ cudaError_t launch_describe(const uint8_t* gray, int H, int W, int pitch, const 
     constexpr int kSmallWarpBytes = 7680;
     int first_big = 0;
     while (first_big < m && warp_bytes(first_big) <= kSmallWarpBytes) ++first_big;
+    // Three independent groups of launches (the per-point CTA scales, the
+    // warp-per-point group, the split scales): with a fork they run
+    // concurrently, which fills the tail waves of the smaller launches.
+    const int ngroups = (first_big < m ? 1 : 0) + (first_big > 0 ? 1 : 0) + (m < st.nL ? 1 : 0);
+    const bool forked = fork && ngroups > 1;
+    const cudaStream_t s_cta = forked ? fork->aux[0] : s, s_big = forked ? fork->aux[1] : s;
+    if (forked) {
+        cudaError_t e = cudaEventRecord(fork->fork_ev, s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(fork->aux[0], fork->fork_ev, 0);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(fork->aux[1], fork->fork_ev, 0);
+        if (e != cudaSuccess) return e;
+    }
     auto launch_group = [&](int l0, int l1) -> cudaError_t {
         int Pmax = 0, Gmax = 0;
         for (int l = l0; l < l1; ++l) {
@@ -874,7 +887,7 @@ cudaError_t launch_describe(const uint8_t* gray, int H, int W, int pitch, const 
             cudaError_t e = cudaFuncSetAttribute(k_describe_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
         }
-        k_describe_cta<<<(unsigned)p.n, kCtaThreads, smem, s>>>(p);
+        k_describe_cta<<<(unsigned)p.n, kCtaThreads, smem, s_cta>>>(p);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -892,26 +905,34 @@ cudaError_t launch_describe(const uint8_t* gray, int H, int W, int pitch, const 
         const size_t csm = (size_t)cell_box_bytes(Gc) + (size_t)Gc * Gc * 4;
         if (csm > 200 * 1024) {
             const unsigned grid = (unsigned)((p.n + kWarps - 1) / kWarps);
-            k_describe_global<<<grid, kWarps * 32, (size_t)kWarps * (2 * kHistBytes + kAccBytes), s>>>(p);
+            k_describe_global<<<grid, kWarps * 32, (size_t)kWarps * (2 * kHistBytes + kAccBytes), s_big>>>(p);
             continue;
         }
         if (!upright) {
-            cudaError_t e = cudaMemsetAsync(desc + p.k0 * 128, 0, sizeof(float) * 128 * (size_t)p.n, s);
+            cudaError_t e = cudaMemsetAsync(desc + p.k0 * 128, 0, sizeof(float) * 128 * (size_t)p.n, s_big);
             if (e != cudaSuccess) return e;
             const int n = 4 * p.ws + 1;
             const int rows = kOrientBandSamples / n > 1 ? kOrientBandSamples / n : 1;
             const int nb = (n + rows - 1) / rows;
-            k_orient_split<<<(unsigned)(p.n * nb), kSplitThreads, 0, s>>>(p, rows, nb);
-            k_orient_pick<<<(unsigned)((p.n + 127) / 128), 128, 0, s>>>(p);
+            k_orient_split<<<(unsigned)(p.n * nb), kSplitThreads, 0, s_big>>>(p, rows, nb);
+            k_orient_pick<<<(unsigned)((p.n + 127) / 128), 128, 0, s_big>>>(p);
         }
         if (csm > 48 * 1024) {
             cudaError_t e = cudaFuncSetAttribute(k_desc_cell, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm);
             if (e != cudaSuccess) return e;
         }
-        k_desc_cell<<<(unsigned)(p.n * 16), kSplitThreads, csm, s>>>(p);
-        k_desc_finalize<<<(unsigned)((p.n + 3) / 4), 128, 0, s>>>(p);
+        k_desc_cell<<<(unsigned)(p.n * 16), kSplitThreads, csm, s_big>>>(p);
+        k_desc_finalize<<<(unsigned)((p.n + 3) / 4), 128, 0, s_big>>>(p);
     }
-    return cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    if (forked) {
+        cudaError_t j = cudaEventRecord(fork->join_ev[0], fork->aux[0]);
+        if (j == cudaSuccess) j = cudaEventRecord(fork->join_ev[1], fork->aux[1]);
+        if (j == cudaSuccess) j = cudaStreamWaitEvent(s, fork->join_ev[0], 0);
+        if (j == cudaSuccess) j = cudaStreamWaitEvent(s, fork->join_ev[1], 0);
+        if (e == cudaSuccess) e = j;
+    }
+    return e;
 }
 
 cudaError_t launch_diag_orient(int32_t* bins, uint32_t* weights, cudaStream_t s)

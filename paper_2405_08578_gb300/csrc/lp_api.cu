@@ -55,6 +55,8 @@ struct lp_ctx {
     cudaEvent_t prof_ev[2] = {nullptr, nullptr};   // lp_set_profiling: around the last distance kernel
     bool prof_recorded = false;
     int32_t guided_iters = 0;
+    lp::Fork fork{};                    // auxiliary streams of lp_describe (created on first use)
+    bool fork_ready = false;
     DBuf buf[B_COUNT];
     char err[512];
 };
@@ -244,6 +246,11 @@ int lp_destroy(lp_ctx* c)
     if (c->d_status) cudaFree(c->d_status);
     for (auto& e : c->prof_ev)
         if (e) cudaEventDestroy(e);
+    if (c->fork_ready) {
+        for (auto& a : c->fork.aux) cudaStreamDestroy(a);
+        cudaEventDestroy(c->fork.fork_ev);
+        for (auto& e : c->fork.join_ev) cudaEventDestroy(e);
+    }
     delete c;
     return LP_OK;
 }
@@ -295,8 +302,20 @@ int lp_describe(lp_ctx* c, const uint8_t* gray, int H, int W, int gray_pitch, co
         int r = build_luts(c, S(stream));
         if (r) return r;
     }
+    if (!c->fork_ready) {
+        cudaError_t e = cudaStreamCreateWithFlags(&c->fork.aux[0], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->fork.aux[1], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->fork.fork_ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->fork.join_ev[0], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->fork.join_ev[1], cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, LP_ERR_CUDA, "auxiliary streams: %s", cudaGetErrorString(e));
+        }
+        c->fork_ready = true;
+    }
     LP_CUDA(c, lp::launch_describe(gray, H, W, gray_pitch, kp_idx, st, c->cfg.upright, c->cfg.border,
-                                   c->buf[B_LUTS].p, ori, desc, desc_bf16, valid, S(stream)));
+                                   c->buf[B_LUTS].p, ori, desc, desc_bf16, valid, &c->fork, S(stream)));
     return LP_OK;
 }
 

@@ -39,10 +39,18 @@ cudaError_t launch_diag_gray(const uint8_t* rgb, int64_t n, uint8_t* gray, cudaS
 // k_describe.cu
 size_t describe_lut_bytes();
 cudaError_t launch_build_luts(void* luts, cudaStream_t s);
-// border = 1: points whose neighbourhood (radius st.pr) leaves the image are marked invalid
+// Two auxiliary streams a launcher may fork independent launches onto; it
+// joins them back to its own stream before returning (graph capture follows).
+struct Fork {
+    cudaStream_t aux[2];
+    cudaEvent_t fork_ev, join_ev[2];
+};
+
+// border = 1: points whose neighbourhood (radius st.pr) leaves the image are marked invalid.
+// fork (or nullptr): the scale groups run concurrently on s and the two auxiliary streams.
 cudaError_t launch_describe(const uint8_t* gray, int H, int W, int pitch, const uint32_t* kp,
                             const ScaleTable& st, int upright, int border, const void* luts, uint8_t* ori,
-                            float* desc, uint16_t* desc_bf16, uint8_t* valid, cudaStream_t s);
+                            float* desc, uint16_t* desc_bf16, uint8_t* valid, const Fork* fork, cudaStream_t s);
 cudaError_t launch_diag_orient(int32_t* bins, uint32_t* weights, cudaStream_t s);
 
 // k_match.cu
