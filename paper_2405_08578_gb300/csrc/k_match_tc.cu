@@ -1000,9 +1000,22 @@ cudaError_t launch_match_bf16(const MatchArgs& a, void* ws, size_t ws_bytes, int
     float4* part_r = reinterpret_cast<float4*>(w + L.off_part_r);
     cudaError_t e;
     if ((e = cudaMemsetAsync(cnt, 0, sizeof(int32_t), s)) != cudaSuccess) return e;
-    k_row_norms<<<(unsigned)((a.NA * 32 + 255) / 256), 256, 0, s>>>(a.dA, a.vA, a.NA, na, 0.f);
+    // the FP32 norms are needed only by the re-rank (B) and the finish (A): with
+    // a fork they run on the auxiliary streams beside the tensor-core passes
+    const bool forked = a.fork != nullptr && a.NB > 0;
+    if (forked) {
+        if ((e = cudaEventRecord(a.fork->fork_ev, s)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(a.fork->aux[0], a.fork->fork_ev, 0)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(a.fork->aux[1], a.fork->fork_ev, 0)) != cudaSuccess)
+            return e;
+    }
+    k_row_norms<<<(unsigned)((a.NA * 32 + 255) / 256), 256, 0, forked ? a.fork->aux[0] : s>>>(a.dA, a.vA, a.NA, na,
+                                                                                             0.f);
+    if (forked && (e = cudaEventRecord(a.fork->join_ev[0], a.fork->aux[0])) != cudaSuccess) return e;
     if (a.NB > 0) {
-        k_row_norms<<<(unsigned)((a.NB * 32 + 255) / 256), 256, 0, s>>>(a.dB, a.vB, a.NB, nb32, INFINITY);
+        k_row_norms<<<(unsigned)((a.NB * 32 + 255) / 256), 256, 0, forked ? a.fork->aux[1] : s>>>(a.dB, a.vB, a.NB,
+                                                                                                 nb32, INFINITY);
+        if (forked && (e = cudaEventRecord(a.fork->join_ev[1], a.fork->aux[1])) != cudaSuccess) return e;
         k_ext_rows<<<(unsigned)((a.NB * 32 + 255) / 256), 256, 0, s>>>(
             reinterpret_cast<const __nv_bfloat16*>(a.dB16), a.vB, a.NB, bext, aext);
         CUtensorMap tA, tB, tAx, tBx;
@@ -1052,6 +1065,9 @@ cudaError_t launch_match_bf16(const MatchArgs& a, void* ws, size_t ws_bytes, int
         if ((e = cudaLaunchKernelEx(&cfg, k_match_tc<2>, tA, tB, tAx, tBx, p)) != cudaSuccess) return e;
         if (a.ev1) cudaEventRecord(a.ev1, s);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if (forked && ((e = cudaStreamWaitEvent(s, a.fork->join_ev[1], 0)) != cudaSuccess ||
+                       (e = cudaStreamWaitEvent(s, a.fork->join_ev[0], 0)) != cudaSuccess))
+            return e;
         k_rerank<<<(unsigned)((a.NA + kRerankWarps - 1) / kRerankWarps), kRerankWarps * 32, 0, s>>>(
             a.dA, a.vA, a.dB, nb32, cand, ncand, thr, a.NA, kDelta, part1, rows, cnt);
         if ((e = cudaFuncSetAttribute(k_rescan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRescanSmem)) !=

@@ -63,6 +63,25 @@ struct lp_ctx {
 
 namespace {
 
+int fail(lp_ctx* c, int code, const char* fmt, ...);
+
+// The context's auxiliary streams and events, created on first use.
+int ensure_fork(lp_ctx* c)
+{
+    if (c->fork_ready) return LP_OK;
+    cudaError_t e = cudaStreamCreateWithFlags(&c->fork.aux[0], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->fork.aux[1], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->fork.fork_ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->fork.join_ev[0], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->fork.join_ev[1], cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, LP_ERR_CUDA, "auxiliary streams: %s", cudaGetErrorString(e));
+    }
+    c->fork_ready = true;
+    return LP_OK;
+}
+
 int fail(lp_ctx* c, int code, const char* fmt, ...)
 {
     if (c) {
@@ -302,18 +321,7 @@ int lp_describe(lp_ctx* c, const uint8_t* gray, int H, int W, int gray_pitch, co
         int r = build_luts(c, S(stream));
         if (r) return r;
     }
-    if (!c->fork_ready) {
-        cudaError_t e = cudaStreamCreateWithFlags(&c->fork.aux[0], cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->fork.aux[1], cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->fork.fork_ev, cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->fork.join_ev[0], cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->fork.join_ev[1], cudaEventDisableTiming);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            return fail(c, LP_ERR_CUDA, "auxiliary streams: %s", cudaGetErrorString(e));
-        }
-        c->fork_ready = true;
-    }
+    if (int r = ensure_fork(c)) return r;
     LP_CUDA(c, lp::launch_describe(gray, H, W, gray_pitch, kp_idx, st, c->cfg.upright, c->cfg.border,
                                    c->buf[B_LUTS].p, ori, desc, desc_bf16, valid, &c->fork, S(stream)));
     return LP_OK;
@@ -351,6 +359,8 @@ int lp_match(lp_ctx* c, const float* dA, const uint16_t* dA_bf16, const uint8_t*
         if (r) return r;
         c->last_NA = NA;
         c->last_NB = NB;
+        if ((r = ensure_fork(c))) return r;
+        a.fork = &c->fork;
         LP_CUDA(c, lp::launch_match_bf16(a, c->buf[B_MATCH_WS].p, c->buf[B_MATCH_WS].n, c->num_sms, S(stream)));
         return LP_OK;
     }

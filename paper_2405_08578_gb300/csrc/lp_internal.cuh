@@ -30,6 +30,13 @@ struct ScaleTable {
 int make_scale_table(const int* Ls, int nL, double beta0, int H, int W, ScaleTable* st);
 
 // ---- kernel launchers (each .cu file owns its kernels) ----
+// Two auxiliary streams a launcher may fork independent launches onto; it
+// joins them back to its own stream before returning (graph capture follows).
+struct Fork {
+    cudaStream_t aux[2];
+    cudaEvent_t fork_ev, join_ev[2];
+};
+
 // k_detect.cu
 // alpha > 0: Eq. 1's literal FP64 ramp (one launch per scale); 0: integer keys
 cudaError_t launch_detect(const uint8_t* img, int H, int W, int pitch, int ch, const ScaleTable& st, double alpha,
@@ -39,12 +46,6 @@ cudaError_t launch_diag_gray(const uint8_t* rgb, int64_t n, uint8_t* gray, cudaS
 // k_describe.cu
 size_t describe_lut_bytes();
 cudaError_t launch_build_luts(void* luts, cudaStream_t s);
-// Two auxiliary streams a launcher may fork independent launches onto; it
-// joins them back to its own stream before returning (graph capture follows).
-struct Fork {
-    cudaStream_t aux[2];
-    cudaEvent_t fork_ev, join_ev[2];
-};
 
 // border = 1: points whose neighbourhood (radius st.pr) leaves the image are marked invalid.
 // fork (or nullptr): the scale groups run concurrently on s and the two auxiliary streams.
@@ -54,6 +55,7 @@ cudaError_t launch_describe(const uint8_t* gray, int H, int W, int pitch, const 
 cudaError_t launch_diag_orient(int32_t* bins, uint32_t* weights, cudaStream_t s);
 
 // k_match.cu
+
 struct MatchArgs {
     const float* dA; const uint16_t* dA16; const uint8_t* vA; int64_t NA;
     const float* dB; const uint16_t* dB16; const uint8_t* vB; int64_t NB;
@@ -62,6 +64,7 @@ struct MatchArgs {
     int32_t* match; float* d1; float* d2;
     int32_t* status;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;   // recorded around the distance kernel when set
+    const Fork* fork = nullptr;                 // BF16 form: row norms run on the auxiliary streams
 };
 size_t match_fp32_workspace(int64_t NA, int64_t NB, int num_sms);
 cudaError_t launch_match_fp32(const MatchArgs& a, void* ws, size_t ws_bytes, int num_sms, cudaStream_t s);
