@@ -570,6 +570,11 @@ k_guided_decide(const float4* pts, long long M_cap, const int32_t* dM, const dou
 // a fixed order, so results do not depend on scheduling.
 constexpr int kRefitThreads = 256;
 constexpr int kRefitWarps = kRefitThreads / 32;
+// The summing passes are FP64 reductions, and FP64 issue is scarce: a CTA has
+// ~M / 32 points, so two warps per CTA keep the per-point work and halve
+// nothing but the reduction.
+constexpr int kSumThreads = 64;
+constexpr int kSumWarps = kSumThreads / 32;
 constexpr int kRefitCTAs = 32;
 constexpr int kPartStride = 64;   // doubles per CTA partial row
 
@@ -593,9 +598,9 @@ __device__ void block_sum_n(double* v, double (*part)[N], double* tot)
 #pragma unroll
         for (int q = 0; q < N; ++q) part[warp][q] = v[q];
     __syncthreads();
-    for (int q = threadIdx.x; q < N; q += kRefitThreads) {
+    for (int q = threadIdx.x; q < N; q += kSumThreads) {
         double s = 0;
-        for (int w = 0; w < kRefitWarps; ++w) s += part[w][q];
+        for (int w = 0; w < kSumWarps; ++w) s += part[w][q];
         tot[q] = s;
     }
     __syncthreads();
@@ -618,11 +623,11 @@ __device__ __forceinline__ double sum_col(const double* part, int q)
 }
 
 // pass 1: inlier mask of the winning hypothesis, count and coordinate sums
-__global__ void __launch_bounds__(kRefitThreads)
+__global__ void __launch_bounds__(kSumThreads)
 k_refit_p1(const float4* pts, long long M_cap, const int32_t* dM, const double* Hs, const int32_t* best_in,
            double t2, uint8_t* inl, RefitWS ws)
 {
-    __shared__ double part[kRefitWarps][5];
+    __shared__ double part[kSumWarps][5];
     __shared__ double tot[5];
     const int best = *best_in;
     if (best < 0) return;
@@ -633,7 +638,7 @@ k_refit_p1(const float4* pts, long long M_cap, const int32_t* dM, const double* 
 #pragma unroll
     for (int i = 0; i < 9; ++i) Hb[i] = Hs[9ll * best + i];
     double v5[5] = {0, 0, 0, 0, 0};
-    for (long long i = b + threadIdx.x; i < e; i += kRefitThreads) {
+    for (long long i = b + threadIdx.x; i < e; i += kSumThreads) {
         const float4 p = pts[i];
         const bool in = inlier64(Hb, p, t2);
         inl[i] = in;
@@ -644,11 +649,11 @@ k_refit_p1(const float4* pts, long long M_cap, const int32_t* dM, const double* 
 }
 
 // pass 2: mean distances to the centroids (Hartley normalisation)
-__global__ void __launch_bounds__(kRefitThreads)
+__global__ void __launch_bounds__(kSumThreads)
 k_refit_p2(const float4* pts, long long M_cap, const int32_t* dM, const int32_t* best_in, const uint8_t* inl,
            RefitWS ws)
 {
-    __shared__ double part[kRefitWarps][2];
+    __shared__ double part[kSumWarps][2];
     __shared__ double tot[2];
     __shared__ double c5[5];
     if (*best_in < 0) return;
@@ -660,7 +665,7 @@ k_refit_p2(const float4* pts, long long M_cap, const int32_t* dM, const int32_t*
     long long b, e;
     cta_range(M, b, e);
     double v2[2] = {0, 0};
-    for (long long i = b + threadIdx.x; i < e; i += kRefitThreads) {
+    for (long long i = b + threadIdx.x; i < e; i += kSumThreads) {
         if (!inl[i]) continue;
         const float4 p = pts[i];
         v2[0] += sqrt((p.x - cxa) * (p.x - cxa) + (p.y - cya) * (p.y - cya));
@@ -682,13 +687,17 @@ __device__ void norms_from_sums(const double* c7, Norm2D& na, Norm2D& nb, double
     good = n >= 4 && da > 0 && db > 0;
 }
 
-// pass 3: upper triangle of A^T A (45 entries) in normalised coordinates
-__global__ void __launch_bounds__(kRefitThreads)
+// pass 3: A^T A in normalised coordinates.  With a = (x, y, 1) of the A point
+// and (u, v) of the B point, the two rows of a correspondence are (-a, 0, u a)
+// and (0, -a, v a), so A^T A has the blocks sum a a^T (twice), -sum u a a^T,
+// -sum v a a^T and sum (u^2 + v^2) a a^T: 4 x 6 distinct sums (columns 8..31:
+// for each of 1, u, v, u^2 + v^2 the products xx, xy, x, yy, y, 1).
+__global__ void __launch_bounds__(kSumThreads)
 k_refit_p3(const float4* pts, long long M_cap, const int32_t* dM, const int32_t* best_in, const uint8_t* inl,
            RefitWS ws)
 {
-    __shared__ double part[kRefitWarps][45];
-    __shared__ double tot[45];
+    __shared__ double part[kSumWarps][24];
+    __shared__ double tot[24];
     __shared__ double nrm[6];
     __shared__ double c7[7];
     __shared__ int good_s;
@@ -708,30 +717,29 @@ k_refit_p3(const float4* pts, long long M_cap, const int32_t* dM, const int32_t*
     const Norm2D na{nrm[0], nrm[1], nrm[2]}, nb{nrm[3], nrm[4], nrm[5]};
     long long b, e;
     cta_range(M, b, e);
-    double acc[45];
+    double acc[24];
 #pragma unroll
-    for (int q = 0; q < 45; ++q) acc[q] = 0;
+    for (int q = 0; q < 24; ++q) acc[q] = 0;
     if (good_s) {
-        for (long long i = b + threadIdx.x; i < e; i += kRefitThreads) {
+        for (long long i = b + threadIdx.x; i < e; i += kSumThreads) {
             if (!inl[i]) continue;
             const float4 p = pts[i];
             const double x = na.s * (p.x - na.cx), y = na.s * (p.y - na.cy);
             const double u = nb.s * (p.z - nb.cx), v = nb.s * (p.w - nb.cy);
-            const double r0[9] = {-x, -y, -1, 0, 0, 0, x * u, y * u, u};
-            const double r1[9] = {0, 0, 0, -x, -y, -1, x * v, y * v, v};
-            int q = 0;
+            const double m[6] = {x * x, x * y, x, y * y, y, 1.0};
+            const double f[4] = {1.0, u, v, u * u + v * v};
 #pragma unroll
-            for (int j = 0; j < 9; ++j)
+            for (int g = 0; g < 4; ++g)
 #pragma unroll
-                for (int k = j; k < 9; ++k) acc[q++] += r0[j] * r0[k] + r1[j] * r1[k];
+                for (int q = 0; q < 6; ++q) acc[6 * g + q] += f[g] * m[q];
         }
     }
-    block_sum_n<45>(acc, part, tot);
-    if (threadIdx.x < 45) ws.part[blockIdx.x * kPartStride + 8 + threadIdx.x] = tot[threadIdx.x];
+    block_sum_n<24>(acc, part, tot);
+    if (threadIdx.x < 24) ws.part[blockIdx.x * kPartStride + 8 + threadIdx.x] = tot[threadIdx.x];
 }
 
 // Smallest eigenvector of the symmetric positive semi-definite 9x9 normal
-// matrix S (upper triangle in the summed columns 8..52) by shifted inverse
+// matrix S (assembled from the summed columns 8..31) by shifted inverse
 // iteration: Cholesky of S + mu I (mu = 1e-12 trace S), then repeated pairs of
 // triangular solves.  The shift keeps the factorisation positive definite for
 // exact data and leaves the eigenvectors unchanged.  One warp; lane i owns row
@@ -741,7 +749,8 @@ constexpr int kSolveThreads = 64;
 __global__ void __launch_bounds__(kSolveThreads)
 k_refit_solve(const double* Hs, const int32_t* best_in, RefitWS ws, double* Hout, int32_t* n_in, int32_t* best_t)
 {
-    __shared__ double col[56];
+    __shared__ double col[32];
+    __shared__ double Sm[9][9];
     __shared__ double L[9][10];
     __shared__ double invd[9];
     const int tid = threadIdx.x, lane = tid & 31;
@@ -754,19 +763,28 @@ k_refit_solve(const double* Hs, const int32_t* best_in, RefitWS ws, double* Hout
         if (tid < 9) { Hout[tid] = 0.0; ws.Hf[tid] = 0.0; }
         return;
     }
-    if (tid < 7) col[tid] = sum_col(ws.part, tid);
-    if (tid >= 8 && tid < 53) col[tid] = sum_col(ws.part, tid);
+    if (tid < 7 || (tid >= 8 && tid < 32)) col[tid] = sum_col(ws.part, tid);
+    __syncthreads();
+    // S from the blocks: [[M1, 0, -Mu], [0, M1, -Mv], [-Mu, -Mv, Mw]], each M
+    // the symmetric 3x3 of its six sums (xx, xy, x, yy, y, 1)
+    for (int e = tid; e < 81; e += kSolveThreads) {
+        const int r = e / 9, c = e % 9, br = r / 3, bc = c / 3, i = r % 3, j = c % 3;
+        const int lo = i < j ? i : j, hi = i < j ? j : i;
+        const int q = lo == 0 ? hi : (lo == 1 ? 2 + hi : 5);   // (0,0..2) -> 0..2, (1,1..2) -> 3..4, (2,2) -> 5
+        double v = 0.0;
+        if (br == bc && br < 2) v = col[8 + q];
+        else if ((br == 0 && bc == 2) || (br == 2 && bc == 0)) v = -col[8 + 6 + q];
+        else if ((br == 1 && bc == 2) || (br == 2 && bc == 1)) v = -col[8 + 12 + q];
+        else if (br == 2 && bc == 2) v = col[8 + 18 + q];
+        Sm[r][c] = v;
+    }
     __syncthreads();
     if (tid >= 32) return;
     Norm2D na, nb;
     double n;
     bool good;
     norms_from_sums(col, na, nb, n, good);
-    // S[j][k] for k >= j sits in column 8 + (upper-triangle position of (j, k))
-    auto S = [&](int j, int k) {
-        if (k < j) { const int x = j; j = k; k = x; }
-        return col[8 + j * 9 - (j * (j - 1)) / 2 + (k - j)];
-    };
+    auto S = [&](int j, int k) { return Sm[j][k]; };
     bool ok = good;
     double tr = 0;
     for (int i = 0; i < 9; ++i) tr += S(i, i);
@@ -839,11 +857,11 @@ k_refit_solve(const double* Hs, const int32_t* best_in, RefitWS ws, double* Hout
 // Eq. 8 refit, pass 2 (after k_refit_p1's mask, count and coordinate sums):
 // C = sum a.b and S = sum a x b of the inliers' coordinates minus their
 // centroids, into columns 5 and 6.
-__global__ void __launch_bounds__(kRefitThreads)
+__global__ void __launch_bounds__(kSumThreads)
 k_rigid_p2(const float4* pts, long long M_cap, const int32_t* dM, const int32_t* best_in, const uint8_t* inl,
            RefitWS ws)
 {
-    __shared__ double part[kRefitWarps][2];
+    __shared__ double part[kSumWarps][2];
     __shared__ double tot[2];
     __shared__ double c5[5];
     if (*best_in < 0) return;
@@ -855,7 +873,7 @@ k_rigid_p2(const float4* pts, long long M_cap, const int32_t* dM, const int32_t*
     long long b, e;
     cta_range(M, b, e);
     double v2[2] = {0, 0};
-    for (long long i = b + threadIdx.x; i < e; i += kRefitThreads) {
+    for (long long i = b + threadIdx.x; i < e; i += kSumThreads) {
         if (!inl[i]) continue;
         const float4 p = pts[i];
         const double ax = p.x - cxa, ay = p.y - cya, bx = p.z - cxb, by = p.w - cyb;
@@ -971,13 +989,13 @@ RansacWS carve(void* ws, int Ttot)
 void refit_launch(int model, const float4* p4, int64_t M_cap, const int32_t* d_M, double t2, const RansacWS& w,
                   double* H, uint8_t* inlier, int32_t* n_in, int32_t* best_t, cudaStream_t s)
 {
-    k_refit_p1<<<kRefitCTAs, kRefitThreads, 0, s>>>(p4, M_cap, d_M, w.Hs, w.flags, t2, inlier, w.rw);
+    k_refit_p1<<<kRefitCTAs, kSumThreads, 0, s>>>(p4, M_cap, d_M, w.Hs, w.flags, t2, inlier, w.rw);
     if (model == LP_MODEL_RIGID) {
-        k_rigid_p2<<<kRefitCTAs, kRefitThreads, 0, s>>>(p4, M_cap, d_M, w.flags, inlier, w.rw);
+        k_rigid_p2<<<kRefitCTAs, kSumThreads, 0, s>>>(p4, M_cap, d_M, w.flags, inlier, w.rw);
         k_rigid_solve<<<1, 32, 0, s>>>(w.Hs, w.flags, w.rw, H, n_in, best_t);
     } else {
-        k_refit_p2<<<kRefitCTAs, kRefitThreads, 0, s>>>(p4, M_cap, d_M, w.flags, inlier, w.rw);
-        k_refit_p3<<<kRefitCTAs, kRefitThreads, 0, s>>>(p4, M_cap, d_M, w.flags, inlier, w.rw);
+        k_refit_p2<<<kRefitCTAs, kSumThreads, 0, s>>>(p4, M_cap, d_M, w.flags, inlier, w.rw);
+        k_refit_p3<<<kRefitCTAs, kSumThreads, 0, s>>>(p4, M_cap, d_M, w.flags, inlier, w.rw);
         k_refit_solve<<<1, kSolveThreads, 0, s>>>(w.Hs, w.flags, w.rw, H, n_in, best_t);
     }
     const unsigned gfin = (unsigned)std::max<long long>(1, std::min<long long>(kRefitCTAs, (M_cap + 1023) / 1024));
