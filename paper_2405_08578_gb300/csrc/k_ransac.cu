@@ -739,21 +739,31 @@ k_refit_p3(const float4* pts, long long M_cap, const int32_t* dM, const int32_t*
 }
 
 // Smallest eigenvector of the symmetric positive semi-definite 9x9 normal
-// matrix S (assembled from the summed columns 8..31) by shifted inverse
-// iteration: Cholesky of S + mu I (mu = 1e-12 trace S), then repeated pairs of
-// triangular solves.  The shift keeps the factorisation positive definite for
-// exact data and leaves the eigenvectors unchanged.  One warp; lane i owns row
-// i of L and component i of the iterate.
-constexpr int kSolveThreads = 64;
+// matrix S (assembled from the summed columns 8..31), as the dominant
+// eigenvector of (S + mu I)^-1 (mu = 1e-12 trace S keeps the matrix positive
+// definite for exact data and leaves the eigenvectors unchanged):
+//   Gauss-Jordan inversion of [S + mu I | I] (9 pivot steps over the whole
+//   block in parallel; positive pivots, as S + mu I is positive definite);
+//   eight squarings of the inverse, each rescaled by a power of two (exact) so
+//   its largest diagonal entry is in [1, 2): the result is (S + mu I)^-256 up
+//   to scale, numerically rank one;
+//   its column of largest diagonal entry, then two products with the inverse.
+// FP64 issue is scarce, so the work is spread over few, wide steps instead of
+// long serial chains.
+constexpr int kSolveThreads = 192;
 
 __global__ void __launch_bounds__(kSolveThreads)
 k_refit_solve(const double* Hs, const int32_t* best_in, RefitWS ws, double* Hout, int32_t* n_in, int32_t* best_t)
 {
     __shared__ double col[32];
     __shared__ double Sm[9][9];
-    __shared__ double L[9][10];
-    __shared__ double invd[9];
-    const int tid = threadIdx.x, lane = tid & 31;
+    __shared__ double Ab[9][18];
+    __shared__ double X[9][9];
+    __shared__ double Y[9][9];
+    __shared__ double vv[9];
+    __shared__ double ipiv;
+    __shared__ int ok_s;
+    const int tid = threadIdx.x;
     const int best = *best_in;
     if (best < 0) {
         if (tid == 0) {
@@ -779,76 +789,87 @@ k_refit_solve(const double* Hs, const int32_t* best_in, RefitWS ws, double* Hout
         Sm[r][c] = v;
     }
     __syncthreads();
-    if (tid >= 32) return;
     Norm2D na, nb;
     double n;
     bool good;
     norms_from_sums(col, na, nb, n, good);
-    auto S = [&](int j, int k) { return Sm[j][k]; };
-    bool ok = good;
     double tr = 0;
-    for (int i = 0; i < 9; ++i) tr += S(i, i);
+    for (int i = 0; i < 9; ++i) tr += Sm[i][i];
     const double mu = 1e-12 * tr;
-    for (int j = 0; j < 9 && ok; ++j) {
-        if (lane == j) {
-            double d = S(j, j) + mu;
-            for (int k = 0; k < j; ++k) d -= L[j][k] * L[j][k];
-            L[j][j] = d > 0 ? sqrt(d) : 0.0;
-            invd[j] = d > 0 ? 1.0 / L[j][j] : 0.0;
+    const int r = tid / 18, c = tid - (tid / 18) * 18;   // this thread's entry of the 9 x 18 block
+    const bool mine = tid < 162;
+    if (mine) Ab[r][c] = c < 9 ? Sm[r][c] + (r == c ? mu : 0.0) : (c - 9 == r ? 1.0 : 0.0);
+    if (tid == 0) ok_s = good ? 1 : 0;
+    __syncthreads();
+    for (int k = 0; k < 9; ++k) {
+        if (tid == 0) {
+            const double pv = Ab[k][k];
+            if (!(pv > 0.0)) ok_s = 0;
+            ipiv = pv > 0.0 ? 1.0 / pv : 0.0;
         }
-        __syncwarp();
-        ok = invd[j] != 0.0;
-        if (ok && lane > j && lane < 9) {
-            double sum = S(lane, j);
-            for (int k = 0; k < j; ++k) sum -= L[lane][k] * L[j][k];
-            L[lane][j] = sum * invd[j];
+        __syncthreads();
+        double nv = 0.0;
+        if (mine) {
+            const double akc = Ab[k][c] * ipiv;
+            nv = r == k ? akc : Ab[r][c] - Ab[r][k] * akc;
         }
-        __syncwarp();
+        __syncthreads();
+        if (mine) Ab[r][c] = nv;
+        __syncthreads();
     }
-    double x = 1.0;   // lane i < 9: component i of the iterate
+    const bool ok = ok_s != 0;
+    const int e = tid, er = e / 9, ec = e - (e / 9) * 9;   // this thread's entry of a 9 x 9 matrix
     if (ok) {
-        for (int it = 0; it < 24; ++it) {
-            double rr = x;   // L y = x, columns in order
-            double y = 0.0;
-            for (int k = 0; k < 9; ++k) {
-                const double yk = __shfl_sync(0xFFFFFFFFu, rr * (lane < 9 ? invd[lane < 9 ? lane : 0] : 0.0), k);
-                if (lane == k) y = yk;
-                if (lane > k && lane < 9) rr -= L[lane][k] * yk;
-            }
-            double r2 = y;   // L^T z = y, columns from the last
+        // X = (S + mu I)^-1, then X <- X^2 eight times, each scaled by a power of two
+        if (e < 81) X[er][ec] = Ab[er][9 + ec];
+        __syncthreads();
+        for (int it = 0; it < 8; ++it) {
+            double acc = 0.0;
+            if (e < 81)
+                for (int k = 0; k < 9; ++k) acc += X[er][k] * X[k][ec];
+            if (e < 81) Y[er][ec] = acc;
+            __syncthreads();
+            double dmax = 0.0;
+            for (int i = 0; i < 9; ++i) dmax = fmax(dmax, Y[i][i]);
+            if (e < 81) X[er][ec] = dmax > 0.0 ? scalbn(Y[er][ec], -ilogb(dmax)) : Y[er][ec];
+            __syncthreads();
+        }
+        // the column of largest diagonal entry, normalised
+        if (tid == 0) {
+            int cb = 0;
+            for (int i = 1; i < 9; ++i)
+                if (X[i][i] > X[cb][cb]) cb = i;
+            double nrm = 0.0;
+            for (int i = 0; i < 9; ++i) nrm += X[i][cb] * X[i][cb];
+            const double sc = nrm > 0.0 ? 1.0 / sqrt(nrm) : 0.0;
+            for (int i = 0; i < 9; ++i) vv[i] = X[i][cb] * sc;
+        }
+        __syncthreads();
+        // two inverse-iteration products: v <- (S + mu I)^-1 v, normalised
+        for (int it = 0; it < 2; ++it) {
             double z = 0.0;
-            for (int k = 8; k >= 0; --k) {
-                const double zk = __shfl_sync(0xFFFFFFFFu, r2 * (lane < 9 ? invd[lane < 9 ? lane : 0] : 0.0), k);
-                if (lane == k) z = zk;
-                if (lane < k) r2 -= L[k][lane] * zk;
+            if (tid < 9)
+                for (int k = 0; k < 9; ++k) z += Ab[tid][9 + k] * vv[k];
+            __syncthreads();
+            if (tid < 9) Y[0][tid] = z;
+            __syncthreads();
+            if (tid == 0) {
+                double nrm = 0.0;
+                for (int i = 0; i < 9; ++i) nrm += Y[0][i] * Y[0][i];
+                const double sc = nrm > 0.0 ? 1.0 / sqrt(nrm) : 0.0;
+                for (int i = 0; i < 9; ++i) vv[i] = Y[0][i] * sc;
             }
-            if (lane >= 9) z = 0.0;
-            double nz = z * z, dot = z * x;
-#pragma unroll
-            for (int o = 16; o; o >>= 1) {
-                nz += __shfl_xor_sync(0xFFFFFFFFu, nz, o);
-                dot += __shfl_xor_sync(0xFFFFFFFFu, dot, o);
-            }
-            // align the sign with the previous iterate before comparing
-            const double sg = (dot < 0 ? -1.0 : 1.0) / sqrt(nz);
-            const double xn = lane < 9 ? z * sg : 1.0;
-            double diff = fabs(xn - x);
-#pragma unroll
-            for (int o = 16; o; o >>= 1) diff = fmax(diff, __shfl_xor_sync(0xFFFFFFFFu, diff, o));
-            x = xn;
-            if (it >= 2 && diff < 1e-12) break;
+            __syncthreads();
         }
     }
-    double h[9];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) h[i] = __shfl_sync(0xFFFFFFFFu, x, i);
-    if (lane != 0) return;
+    if (tid != 0) return;
     if (best_t) *best_t = best;
     *n_in = 0;
-    double H[9];
-    ok = ok && denorm(na, nb, h, H);
+    double h[9], H[9];
+    for (int i = 0; i < 9; ++i) h[i] = vv[i];
+    const bool fit = ok && denorm(na, nb, h, H);
     for (int i = 0; i < 9; ++i) {
-        const double v = ok ? H[i] : Hs[9ll * best + i];
+        const double v = fit ? H[i] : Hs[9ll * best + i];
         ws.Hf[i] = v;
         Hout[i] = v;
     }
