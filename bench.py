@@ -533,8 +533,11 @@ def main():
     roof["traffic"] = profiled_traffic("k_match_tc.cu" if r["bf"] else "k_match_fp32.cu")
     roof["peak_source"] = f"{pk_kind}" if r["bf"] else "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"
     value = world * args.steps / r["t_steps"]
-    # our kernels per step (BF16 form): detect 2, describe 6, match 8, compact 1,
-    # RANSAC 8; FP32 form: detect 2, describe 6, match 4, compact 1, RANSAC 8
+    # our kernels per step (BF16 form): detect 2, describe 6, match 10 (two row
+    # norms, extension rows, pass 1, threshold, pass 2, re-rank, re-scan,
+    # re-scan merge, finish), compact 2, RANSAC 9 (hypotheses, score, recount,
+    # argmax, three refit sums, solve, final); FP32 form: match 4 (two row
+    # norms, main, finish) and the rest as BF16
     launches_per_step = 29 if r["bf"] else 23
     line = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * r["t_steps"] / args.steps, "higher_is_better": True,
