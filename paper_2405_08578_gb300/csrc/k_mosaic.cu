@@ -13,7 +13,9 @@
 //  k_mosaic_render   one thread per canvas pixel: every placed image whose
 //                    inverse placement maps the pixel inside the image adds
 //                    its bilinear sample; the pixel is the mean (rounded half
-//                    up), 0 where no image covers it; `cover` counts them.
+//                    up), 0 where no image covers it; `cover` counts them.  A
+//                    CTA skips the images whose canvas bounding box (from the
+//                    placed corners, with a margin) misses its 32 x 8 tile.
 #include <math.h>
 #include <string.h>
 
@@ -29,6 +31,7 @@ struct MosaicImage {
     const uint8_t* data;
     int H, W, pitch;
     float m[9];   // canvas pixel -> image pixel
+    int bx0, by0, bx1, by1;   // canvas pixels the image can cover (inclusive)
 };
 
 struct MosaicParams {
@@ -40,14 +43,16 @@ struct MosaicParams {
 
 __global__ void __launch_bounds__(256) k_mosaic_render(const __grid_constant__ MosaicParams p)
 {
-    const int x = blockIdx.x * 32 + (threadIdx.x & 31);
-    const int y = blockIdx.y * 8 + (threadIdx.x >> 5);
+    const int tx0 = blockIdx.x * 32, ty0 = blockIdx.y * 8;
+    const int x = tx0 + (threadIdx.x & 31);
+    const int y = ty0 + (threadIdx.x >> 5);
     if (x >= p.cw || y >= p.ch) return;
     const float fx = (float)x, fy = (float)y;
     float sum[3] = {0.f, 0.f, 0.f};
     int n = 0;
     for (int i = 0; i < p.n; ++i) {
         const MosaicImage& I = p.im[i];
+        if (I.bx1 < tx0 || I.bx0 > tx0 + 31 || I.by1 < ty0 || I.by0 > ty0 + 7) continue;   // CTA-uniform
         const float w = fmaf(I.m[6], fx, fmaf(I.m[7], fy, I.m[8]));
         if (!(w > 0.f)) continue;
         const float u = fmaf(I.m[0], fx, fmaf(I.m[1], fy, I.m[2])) / w;
@@ -207,6 +212,26 @@ cudaError_t launch_mosaic_render(const lp_image* imgs, int N, const double* G, c
         m.W = imgs[i].W;
         m.pitch = imgs[i].pitch;
         for (int k = 0; k < 9; ++k) m.m[k] = (float)inv[k];
+        // canvas footprint: with w > 0 at the four corners (w is affine over
+        // the image, so positive everywhere) the image maps onto the convex
+        // quad of its corners; otherwise no culling
+        const double* g = G + 9 * (size_t)i;
+        double x0 = INFINITY, y0 = INFINITY, x1 = -INFINITY, y1 = -INFINITY;
+        bool bounded = true;
+        for (int q = 0; q < 4; ++q) {
+            const double cx = (q & 1) ? imgs[i].W - 1.0 : 0.0, cy = (q & 2) ? imgs[i].H - 1.0 : 0.0;
+            const double w = g[6] * cx + g[7] * cy + g[8];
+            if (!(w > 0)) { bounded = false; break; }
+            const double u = (g[0] * cx + g[1] * cy + g[2]) / w, v = (g[3] * cx + g[4] * cy + g[5]) / w;
+            x0 = fmin(x0, u); x1 = fmax(x1, u); y0 = fmin(y0, v); y1 = fmax(y1, v);
+        }
+        if (bounded && x1 - x0 < 1e9 && y1 - y0 < 1e9) {
+            m.bx0 = (int)floor(x0) - 2; m.by0 = (int)floor(y0) - 2;
+            m.bx1 = (int)ceil(x1) + 2;  m.by1 = (int)ceil(y1) + 2;
+        } else {
+            m.bx0 = m.by0 = -(1 << 30);
+            m.bx1 = m.by1 = 1 << 30;
+        }
     }
     if (cw <= 0 || ch <= 0) return cudaSuccess;
     const dim3 grid((unsigned)((cw + 31) / 32), (unsigned)((ch + 7) / 8));
