@@ -57,6 +57,8 @@ struct lp_ctx {
     int32_t guided_iters = 0;
     lp::Fork fork{};                    // auxiliary streams of lp_describe (created on first use)
     bool fork_ready = false;
+    cudaStream_t img_stream = nullptr;  // lp_stitch_pair: image B's detect and describe
+    cudaEvent_t img_ev[2] = {nullptr, nullptr};
     DBuf buf[B_COUNT];
     char err[512];
 };
@@ -74,6 +76,13 @@ int ensure_fork(lp_ctx* c)
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->fork.fork_ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->fork.join_ev[0], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->fork.join_ev[1], cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, LP_ERR_CUDA, "auxiliary streams: %s", cudaGetErrorString(e));
+    }
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->img_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->img_ev[0], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->img_ev[1], cudaEventDisableTiming);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(c, LP_ERR_CUDA, "auxiliary streams: %s", cudaGetErrorString(e));
@@ -269,6 +278,8 @@ int lp_destroy(lp_ctx* c)
         for (auto& a : c->fork.aux) cudaStreamDestroy(a);
         cudaEventDestroy(c->fork.fork_ev);
         for (auto& e : c->fork.join_ev) cudaEventDestroy(e);
+        cudaStreamDestroy(c->img_stream);
+        for (auto& e : c->img_ev) cudaEventDestroy(e);
     }
     delete c;
     return LP_OK;
@@ -428,8 +439,13 @@ int lp_set_proposal(lp_ctx* c, lp_mlp* mlp, int32_t guided_iters)
     return LP_OK;
 }
 
-int lp_stitch_pair(lp_ctx* c, const uint8_t* imgA, int HA, int WA, int pitchA, const uint8_t* imgB, int HB, int WB,
-                   int pitchB, int channels, uint32_t pair_id, double* H, int32_t* n_in, int32_t* M_out, void* stream)
+namespace {
+
+// b_queued: image B's upload is already queued on the context's image stream,
+// which is ordered after the caller's earlier work (lp_stitch_pair_host)
+int stitch_pair_impl(lp_ctx* c, const uint8_t* imgA, int HA, int WA, int pitchA, const uint8_t* imgB, int HB, int WB,
+                     int pitchB, int channels, uint32_t pair_id, double* H, int32_t* n_in, int32_t* M_out,
+                     void* stream, bool b_queued)
 {
     if (!c) return LP_ERR_ARG;
     int r = check_image(c, imgA, HA, WA, pitchA, channels);
@@ -454,14 +470,24 @@ int lp_stitch_pair(lp_ctx* c, const uint8_t* imgA, int HA, int WA, int pitchA, c
     const uint8_t* gA = channels == 3 ? (const uint8_t*)P(B_GRAY_A) : imgA;
     const uint8_t* gB = channels == 3 ? (const uint8_t*)P(B_GRAY_B) : imgB;
     const int gpA = channels == 3 ? WA : pitchA, gpB = channels == 3 ? WB : pitchB;
+    // image B on the context's image stream, beside image A on the caller's
+    // stream; joined back before matching
+    if ((r = ensure_fork(c))) return r;
+    void* sB = c->img_stream;
+    if (!b_queued) {
+        LP_CUDA(c, cudaEventRecord(c->img_ev[0], S(stream)));
+        LP_CUDA(c, cudaStreamWaitEvent(c->img_stream, c->img_ev[0], 0));
+    }
     if ((r = lp_detect(c, imgA, HA, WA, pitchA, channels, (uint32_t*)P(B_KP_A), (uint8_t*)P(B_GRAY_A), stream))) return r;
-    if ((r = lp_detect(c, imgB, HB, WB, pitchB, channels, (uint32_t*)P(B_KP_B), (uint8_t*)P(B_GRAY_B), stream))) return r;
+    if ((r = lp_detect(c, imgB, HB, WB, pitchB, channels, (uint32_t*)P(B_KP_B), (uint8_t*)P(B_GRAY_B), sB))) return r;
     if ((r = lp_describe(c, gA, HA, WA, gpA, (const uint32_t*)P(B_KP_A), KA, (uint8_t*)P(B_ORI_A), (float*)P(B_DESC_A),
                          bf ? (uint16_t*)P(B_D16_A) : nullptr, (uint8_t*)P(B_VAL_A), stream)))
         return r;
     if ((r = lp_describe(c, gB, HB, WB, gpB, (const uint32_t*)P(B_KP_B), KB, (uint8_t*)P(B_ORI_B), (float*)P(B_DESC_B),
-                         bf ? (uint16_t*)P(B_D16_B) : nullptr, (uint8_t*)P(B_VAL_B), stream)))
+                         bf ? (uint16_t*)P(B_D16_B) : nullptr, (uint8_t*)P(B_VAL_B), sB)))
         return r;
+    LP_CUDA(c, cudaEventRecord(c->img_ev[1], c->img_stream));
+    LP_CUDA(c, cudaStreamWaitEvent(S(stream), c->img_ev[1], 0));
     if ((r = lp_match(c, (const float*)P(B_DESC_A), (const uint16_t*)P(B_D16_A), (const uint8_t*)P(B_VAL_A), KA,
                       (const float*)P(B_DESC_B), (const uint16_t*)P(B_D16_B), (const uint8_t*)P(B_VAL_B), KB,
                       (int32_t*)P(B_MATCH), (float*)P(B_D1), (float*)P(B_D2), stream)))
@@ -482,6 +508,15 @@ int lp_stitch_pair(lp_ctx* c, const uint8_t* imgA, int HA, int WA, int pitchA, c
     return lp_ransac(c, (const float*)P(B_PTS), KA, dM, pair_id, H, (uint8_t*)P(B_INL), n_in, nullptr, stream);
 }
 
+}  // namespace
+
+int lp_stitch_pair(lp_ctx* c, const uint8_t* imgA, int HA, int WA, int pitchA, const uint8_t* imgB, int HB, int WB,
+                   int pitchB, int channels, uint32_t pair_id, double* H, int32_t* n_in, int32_t* M_out, void* stream)
+{
+    return stitch_pair_impl(c, imgA, HA, WA, pitchA, imgB, HB, WB, pitchB, channels, pair_id, H, n_in, M_out, stream,
+                            false);
+}
+
 int lp_stitch_pair_host(lp_ctx* c, const uint8_t* hA, int HA, int WA, int pitchA, const uint8_t* hB, int HB, int WB,
                         int pitchB, int channels, uint32_t pair_id, double* H_host, int32_t* n_in_host,
                         int32_t* M_host, void* stream)
@@ -494,14 +529,19 @@ int lp_stitch_pair_host(lp_ctx* c, const uint8_t* hA, int HA, int WA, int pitchA
     if ((r = ensure(c, B_IMG_A, nA)) || (r = ensure(c, B_IMG_B, nB)) || (r = ensure(c, B_H, 128)) ||
         (r = ensure(c, B_NIN, 64)))
         return r;
+    if ((r = ensure_fork(c))) return r;
     cudaStream_t s = S(stream);
     c->last = s;
+    // A uploads on the caller's stream, B on the image stream (after the
+    // caller's earlier work): the two copies and image A's detection overlap
+    LP_CUDA(c, cudaEventRecord(c->img_ev[0], s));
+    LP_CUDA(c, cudaStreamWaitEvent(c->img_stream, c->img_ev[0], 0));
     LP_CUDA(c, cudaMemcpyAsync(c->buf[B_IMG_A].p, hA, nA, cudaMemcpyHostToDevice, s));
-    LP_CUDA(c, cudaMemcpyAsync(c->buf[B_IMG_B].p, hB, nB, cudaMemcpyHostToDevice, s));
+    LP_CUDA(c, cudaMemcpyAsync(c->buf[B_IMG_B].p, hB, nB, cudaMemcpyHostToDevice, c->img_stream));
     double* dH = (double*)c->buf[B_H].p;
     int32_t* dn = (int32_t*)c->buf[B_NIN].p;
-    if ((r = lp_stitch_pair(c, (const uint8_t*)c->buf[B_IMG_A].p, HA, WA, pitchA, (const uint8_t*)c->buf[B_IMG_B].p,
-                            HB, WB, pitchB, channels, pair_id, dH, dn, dn + 1, stream)))
+    if ((r = stitch_pair_impl(c, (const uint8_t*)c->buf[B_IMG_A].p, HA, WA, pitchA, (const uint8_t*)c->buf[B_IMG_B].p,
+                              HB, WB, pitchB, channels, pair_id, dH, dn, dn + 1, stream, true)))
         return r;
     int32_t tmp[2];
     LP_CUDA(c, cudaMemcpyAsync(H_host, dH, 9 * sizeof(double), cudaMemcpyDeviceToHost, s));

@@ -128,3 +128,26 @@ def test_pair_ids_let_a_shard_reproduce_the_full_list():
             torch.cuda.synchronize()
             idx = torch.tensor(mine, device="cuda")
             assert torch.equal(h2, HM[idx]) and torch.equal(n2, n_in[idx]) and torch.equal(m2, M[idx])
+
+
+@pytest.mark.parametrize("rgb", [False, True])
+def test_host_buffer_pair_equals_device_pair(rgb):
+    """lp_stitch_pair_host (host images, uploads on two streams) returns the
+    device call's H, inlier count and match count exactly, on repeated calls
+    that alternate between two pairs (its upload buffers are reused)."""
+    pairs = [synth.small_pair(240, 320, s, theta_deg=3.0 * s, shift=0.3, rgb=rgb) for s in (1, 2)]
+    ctx = lp.Context(Ls=(8, 16, 32), precision=lp.PREC_BF16)
+    ch = 3 if rgb else 1
+    want = []
+    for k, p in enumerate(pairs):
+        H, n, M = G.stitch(ctx, p.A, p.B, pair_id=k)
+        want.append((H, n, M))
+    hosts = []
+    for p in pairs:
+        a, pa = lp.pitched_device(p.A)
+        b, pb = lp.pitched_device(p.B)
+        hosts.append((a.cpu().pin_memory(), pa, b.cpu().pin_memory(), pb))
+    for rep in range(3):
+        for k, (a, pa, b, pb) in enumerate(hosts):
+            H, n, M = ctx.lp_stitch_pair_host(a, 240, 320, pa, b, 240, 320, pb, ch, k)
+            assert np.array_equal(np.array(H), want[k][0]) and n == want[k][1] and M == want[k][2], (rep, k)
