@@ -142,7 +142,7 @@ def oracle_pair_seconds(pair, rows_sample=1500, desc_sample=15000, seed=0, M=300
 # workload, from one ncu capture, valid only for the kernel source it was taken
 # on (file SHA-1).
 PROFILED_TRAFFIC = {
-    "k_match_tc.cu": ("7b95b9eeac1d6fc61d953c25003b44ae4c291655", 40.4877e6),
+    "k_match_tc.cu": ("c040957f97ed413feaff23dac1b68f938f30f874", 40.4910e6),
 }
 
 

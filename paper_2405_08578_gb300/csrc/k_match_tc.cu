@@ -859,24 +859,25 @@ k_rescan(const float* A, const float* B, const float* nb32, long long NA, long l
     }
 }
 
-// Merge the re-scan partials of queued row r into the row's single partial.
+// Merge the re-scan partials of queued row r into the row's single partial
+// (one warp per queued row, grid-stride: the queue is usually short).
 __global__ void k_rescan_merge(const float4* part_r, long long NA, long long NB, const int32_t* rows,
                                const int32_t* count, float4* out_part)
 {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const long long r = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     const int R = *count;
-    if (r >= R) return;
     const int nchunks = rescan_groups(R, NA, (NB + kRescanThreads - 1) / kRescanThreads);
-    float b1 = INFINITY, b2 = INFINITY;
-    int j1 = -1, j2 = -1;
-    for (int c = lane; c < nchunks; c += 32) {
-        const float4 q = part_r[r * nchunks + c];
-        top2_lex(b1, j1, b2, j2, q.x, __float_as_int(q.z));
-        top2_lex(b1, j1, b2, j2, q.y, __float_as_int(q.w));
+    for (long long r = (long long)blockIdx.x * nw + warp; r < R; r += (long long)gridDim.x * nw) {
+        float b1 = INFINITY, b2 = INFINITY;
+        int j1 = -1, j2 = -1;
+        for (int c = lane; c < nchunks; c += 32) {
+            const float4 q = part_r[r * nchunks + c];
+            top2_lex(b1, j1, b2, j2, q.x, __float_as_int(q.z));
+            top2_lex(b1, j1, b2, j2, q.y, __float_as_int(q.w));
+        }
+        warp_top2(b1, j1, b2, j2);
+        if (lane == 0) out_part[rows[r]] = make_float4(b1, b2, __int_as_float(j1), __int_as_float(j2));
     }
-    warp_top2(b1, j1, b2, j2);
-    if (lane == 0) out_part[rows[r]] = make_float4(b1, b2, __int_as_float(j1), __int_as_float(j2));
 }
 
 // ------------------------------------------------------------------ host side
@@ -1075,7 +1076,8 @@ cudaError_t launch_match_bf16(const MatchArgs& a, void* ws, size_t ws_bytes, int
             return e;
         k_rescan<<<(unsigned)(4 * num_sms), kRescanThreads, kRescanSmem, s>>>(a.dA, a.dB, nb32, a.NA, a.NB, rows,
                                                                                cnt, part_r);
-        k_rescan_merge<<<(unsigned)((a.NA + 7) / 8), 256, 0, s>>>(part_r, a.NA, a.NB, rows, cnt, part1);
+        k_rescan_merge<<<(unsigned)std::min<long long>((a.NA + 7) / 8, 2ll * num_sms), 256, 0, s>>>(
+            part_r, a.NA, a.NB, rows, cnt, part1);
         k_match_finish<<<(unsigned)((a.NA + 255) / 256), 256, 0, s>>>(part1, 1, a.NA, na, a.vA, a.ratio2, a.delta_s2,
                                                                       a.match, a.d1, a.d2);
     } else {
