@@ -100,7 +100,12 @@ typedef struct lp_ctx lp_ctx;
 LP_API int lp_config_default(lp_config* cfg);
 
 /* Create a context on the current CUDA device.  The context owns a copy of the
- * configuration, a device status word and a grow-only device workspace.
+ * configuration, a device status word and a grow-only device workspace, and
+ * (created on first use) three streams of its own: lp_describe, lp_match and
+ * lp_stitch_pair fork independent launches onto them and join them back to
+ * the caller's stream with events before returning, so every call is ordered
+ * on the caller's stream as if all its work ran there (also under graph
+ * capture).  A context is not thread-safe: use one per host thread.
  * Errors: LP_ERR_ARG (bad config), LP_ERR_CUDA, LP_ERR_NOMEM. */
 LP_API int lp_create(lp_ctx** ctx, const lp_config* cfg);
 

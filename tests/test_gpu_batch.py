@@ -151,3 +151,36 @@ def test_host_buffer_pair_equals_device_pair(rgb):
         for k, (a, pa, b, pb) in enumerate(hosts):
             H, n, M = ctx.lp_stitch_pair_host(a, 240, 320, pa, b, 240, 320, pb, ch, k)
             assert np.array_equal(np.array(H), want[k][0]) and n == want[k][1] and M == want[k][2], (rep, k)
+
+
+@pytest.mark.parametrize("rgb", [False, True])
+def test_stitch_pairs_uneven_sizes_equal_single_pairs(rgb):
+    """Images of different sizes in one batch (unequal point counts per pair):
+    every H_M entry, inlier and match count equals the single-pair call's."""
+    s1 = synth.small_pair(240, 320, seed=31, theta_deg=2.0, shift=0.25, rgb=rgb)
+    s2 = synth.small_pair(300, 420, seed=32, theta_deg=-3.0, shift=0.3, rgb=rgb)
+    imgs = [s1.A, s2.A, s1.B, s2.B]
+    ch = 3 if rgb else 1
+    bufs = [lp.pitched_device(im) for im in imgs]
+    ctx = lp.Context(Ls=(8, 16, 32), precision=lp.PREC_BF16, seed=3)
+    images = [(b, im.shape[0], im.shape[1], p, ch) for (b, p), im in zip(bufs, imgs)]
+    P = 6
+    HM, n_in, valid, M = _outputs(P)
+    for rep in range(2):                       # eager, then graph replay
+        for t in (HM, n_in, valid, M):
+            t.zero_()
+        ctx.lp_stitch_pairs(images, HM, n_in, valid, M_out=M)
+        torch.cuda.synchronize()
+        q = 0
+        for i in range(4):
+            for j in range(i + 1, 4):
+                (bi, pi), (bj, pj) = bufs[i], bufs[j]
+                H1 = torch.zeros(9, dtype=torch.float64, device="cuda")
+                n1 = torch.zeros(1, dtype=torch.int32, device="cuda")
+                M1 = torch.zeros(1, dtype=torch.int32, device="cuda")
+                ctx.lp_stitch_pair(bi, imgs[i].shape[0], imgs[i].shape[1], pi, bj, imgs[j].shape[0],
+                                   imgs[j].shape[1], pj, ch, q, H1, n1, M1)
+                torch.cuda.synchronize()
+                assert torch.equal(HM[q], H1) and int(n_in[q]) == int(n1) and int(M[q]) == int(M1), (rep, i, j)
+                q += 1
+        assert int(valid[1]) == 1 and int(valid[4]) == 1   # (s1.A, s1.B) and (s2.A, s2.B)
