@@ -5,8 +5,11 @@
  * fast and random image stitching": multiscale local-peak detection (Sec. 2.1-
  * 2.2, Eq. 1-2), SIFT-style orientation and 128-d description (Sec. 2.3,
  * Eq. 3-5), nearest-neighbour matching with Eq. 6 distances (Sec. 2.4) and
- * RANSAC homography estimation (Sec. 2.5, Eq. 7), plus the all-pairs
- * homography matrix H_M of Sec. 4.
+ * RANSAC estimation of the homography of Eq. 7 or the rigid transform of
+ * Eq. 8 (Sec. 2.5), plus the all-pairs homography matrix H_M and the mosaic of
+ * Sec. 4.  Paper-literal variants (finite alpha in Eq. 1, border rejection,
+ * Delta_s-only matching) are configuration options.  A learned RANSAC
+ * proposal, not in the paper, is an addition.
  *
  * Conventions shared by every entry point
  *  - Pointers named d_* or documented as "device" are device pointers that the
@@ -96,7 +99,9 @@ typedef struct lp_config {
 typedef struct lp_ctx lp_ctx;
 
 /* Fill *cfg with L = {16, 32, 64, 128}, beta0 auto, ratio 0.8, Delta_s off,
- * T = 1000, 3 px, seed 0, min_inliers 8, BF16, rotated descriptors. */
+ * T = 1000, 3 px, seed 0, min_inliers 8, LP_PREC_FP32 (select LP_PREC_BF16
+ * for the tensor-core form), rotated descriptors, the homography model, and
+ * the paper-literal variants off (alpha 0, border 0). */
 LP_API int lp_config_default(lp_config* cfg);
 
 /* Create a context on the current CUDA device.  The context owns a copy of the
@@ -137,7 +142,8 @@ LP_API int lp_detect(lp_ctx* ctx, const uint8_t* img, int H, int W, int pitch, i
  *  ori        device, uint8[K]: orientation bin k (theta = (k + 0.5) * 10 deg)
  *  desc       device, float[K*128], row-major, unit L2 norm (zeros if invalid)
  *  desc_bf16  device, uint16[K*128] bfloat16 copy of desc, or NULL
- *  valid      device, uint8[K]: 0 when the gradient histogram is all zero
+ *  valid      device, uint8[K]: 0 when the gradient histogram is all zero, or
+ *             (cfg.border = 1) when the point's neighbourhood leaves the image
  * Errors: LP_ERR_ARG, LP_ERR_ALIGN, LP_ERR_CUDA. */
 LP_API int lp_describe(lp_ctx* ctx, const uint8_t* gray, int H, int W, int gray_pitch, const uint32_t* kp_idx,
                 int64_t K, uint8_t* ori, float* desc, uint16_t* desc_bf16, uint8_t* valid, void* stream);
