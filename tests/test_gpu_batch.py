@@ -184,3 +184,31 @@ def test_stitch_pairs_uneven_sizes_equal_single_pairs(rgb):
                 assert torch.equal(HM[q], H1) and int(n_in[q]) == int(n1) and int(M[q]) == int(M1), (rep, i, j)
                 q += 1
         assert int(valid[1]) == 1 and int(valid[4]) == 1   # (s1.A, s1.B) and (s2.A, s2.B)
+
+
+def test_degenerate_pairs_report_no_model():
+    """Edge cases of the whole path: an image smaller than every window (no
+    feature points), a flat image (no valid descriptor), and both in a batch:
+    the calls succeed, report no model (H = 0, n_in = 0) and leave the context
+    usable."""
+    ctx = lp.Context(Ls=(16, 32), precision=lp.PREC_BF16)
+    tiny = np.full((12, 12), 90, np.uint8)
+    flat = np.full((64, 96), 90, np.uint8)
+    real = synth.small_pair(128, 160, seed=41, shift=0.2)
+    for A, B in ((tiny, real.A), (real.A, tiny), (tiny, tiny), (flat, real.B), (real.A, flat)):
+        H, n, M = G.stitch(ctx, A, B)
+        assert n == 0 and M == 0 and not H.any(), (A.shape, B.shape)
+        assert ctx.lp_sync_status() == 0
+    H, n, M = G.stitch(ctx, real.A, real.B, pair_id=4)   # the batch's pair (1, 3) has pair id 4
+    assert n >= 8
+    imgs = [tiny, real.A, flat, real.B]
+    bufs = [lp.pitched_device(im) for im in imgs]
+    images = [(b, im.shape[0], im.shape[1], p, 1) for (b, p), im in zip(bufs, imgs)]
+    HM, n_in, valid, Mo = _outputs(6)
+    ctx.lp_stitch_pairs(images, HM, n_in, valid, M_out=Mo)
+    torch.cuda.synchronize()
+    assert ctx.lp_sync_status() == 0
+    # only (real.A, real.B) = pair (1, 3), index 4, has a model
+    v = valid.cpu().numpy()
+    assert v[4] == 1 and v.sum() == 1 and int(n_in[4]) == n
+    assert not HM[[0, 1, 2, 3, 5]].any()
