@@ -57,8 +57,10 @@ struct lp_ctx {
     int32_t guided_iters = 0;
     lp::Fork fork{};                    // auxiliary streams of lp_describe (created on first use)
     bool fork_ready = false;
-    cudaStream_t img_stream = nullptr;  // lp_stitch_pair: image B's detect and describe
+    cudaStream_t img_stream = nullptr;  // lp_stitch_pair: image B's detect and describe;
+                                        // lp_stitch_pairs: the pairs' RANSAC
     cudaEvent_t img_ev[2] = {nullptr, nullptr};
+    cudaEvent_t pair_ev[3] = {nullptr, nullptr, nullptr};   // lp_stitch_pairs: compacted, slot 0 / 1 free
     DBuf buf[B_COUNT];
     char err[512];
 };
@@ -83,6 +85,7 @@ int ensure_fork(lp_ctx* c)
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->img_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->img_ev[0], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->img_ev[1], cudaEventDisableTiming);
+    for (int q = 0; q < 3 && e == cudaSuccess; ++q) e = cudaEventCreateWithFlags(&c->pair_ev[q], cudaEventDisableTiming);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(c, LP_ERR_CUDA, "auxiliary streams: %s", cudaGetErrorString(e));
@@ -280,6 +283,7 @@ int lp_destroy(lp_ctx* c)
         for (auto& e : c->fork.join_ev) cudaEventDestroy(e);
         cudaStreamDestroy(c->img_stream);
         for (auto& e : c->img_ev) cudaEventDestroy(e);
+        for (auto& e : c->pair_ev) cudaEventDestroy(e);
     }
     delete c;
     return LP_OK;
@@ -616,8 +620,11 @@ int lp_stitch_pairs_ids(lp_ctx* c, const lp_image* imgs, int N, const int32_t* p
     const size_t o_match = o; o += al256(4 * (size_t)Kmax + 8);
     const size_t o_d1 = o; o += al256(4 * (size_t)Kmax + 8);
     const size_t o_d2 = o; o += al256(4 * (size_t)Kmax + 8);
-    const size_t o_pts = o; o += al256(16 * (size_t)Kmax + 16);
-    const size_t o_inl = o; o += al256((size_t)Kmax + 8);
+    // two slots of compacted points and inlier masks: pair q's RANSAC (on the
+    // context's second stream) overlaps the next pair's matching
+    const size_t o_pts = o; o += 2 * al256(16 * (size_t)Kmax + 16);
+    const size_t o_inl = o; o += 2 * al256((size_t)Kmax + 8);
+    const size_t pts_slot = al256(16 * (size_t)Kmax + 16), inl_slot = al256((size_t)Kmax + 8);
     const size_t o_M = o; o += al256(4 * (size_t)P + 8);
     const bool guided = c->proposal != nullptr;
     const size_t o_rows = o; o += guided ? al256(4 * (size_t)Kmax + 8) : 0;
@@ -625,6 +632,7 @@ int lp_stitch_pairs_ids(lp_ctx* c, const lp_image* imgs, int N, const int32_t* p
     const size_t o_prob = o; o += guided ? al256(4 * (size_t)Kmax + 8) : 0;
     int r = ensure(c, B_BATCH, o + 256);
     if (r) return r;
+    if ((r = ensure_fork(c))) return r;
     size_t mws = 0;
     for (int q = 0; q < P; ++q) {
         const int64_t KA = ib[pl[2 * q]].K, KB = ib[pl[2 * q + 1]].K;
@@ -675,9 +683,23 @@ int lp_stitch_pairs_ids(lp_ctx* c, const lp_image* imgs, int N, const int32_t* p
                                   bf ? (uint16_t*)(base + ib[i].d16) : nullptr, base + ib[i].val, stream)))
                 return rr;
         }
+        // unguided: RANSAC of pair q on the second stream, beside pair q + 1's
+        // matching; the guided tail reads the match buffers, so it stays in order
+        const bool overlap = !guided;
+        cudaStream_t sr = overlap ? c->img_stream : s;
+        if (overlap) {
+            LP_CUDA(c, cudaEventRecord(c->pair_ev[1], s));
+            LP_CUDA(c, cudaStreamWaitEvent(sr, c->pair_ev[1], 0));
+            LP_CUDA(c, cudaEventRecord(c->pair_ev[2], s));
+        }
         for (int q = 0; q < P; ++q) {
             const int a = pl[2 * q], b = pl[2 * q + 1];
             const ImgBufs &A = ib[a], &B = ib[b];
+            const int slot = overlap ? (q & 1) : 0;
+            float* pts = (float*)(base + o_pts + slot * pts_slot);
+            uint8_t* inl = base + o_inl + slot * inl_slot;
+            // the slot's previous RANSAC (pair q - 2) has finished reading it
+            if (overlap) LP_CUDA(c, cudaStreamWaitEvent(s, c->pair_ev[1 + slot], 0));
             if (A.K == 0) {
                 LP_CUDA(c, cudaMemsetAsync(Mbuf + q, 0, sizeof(int32_t), s));
             } else {
@@ -687,22 +709,31 @@ int lp_stitch_pairs_ids(lp_ctx* c, const lp_image* imgs, int N, const int32_t* p
                                    (int32_t*)(base + o_match), (float*)(base + o_d1), (float*)(base + o_d2), stream)))
                     return rr;
                 if ((rr = lp_compact(c, (const uint32_t*)(base + A.kp), imgs[a].W, (const uint32_t*)(base + B.kp),
-                                     imgs[b].W, (const int32_t*)(base + o_match), A.K, (float*)(base + o_pts),
+                                     imgs[b].W, (const int32_t*)(base + o_match), A.K, pts,
                                      guided ? (int32_t*)(base + o_rows) : nullptr, Mbuf + q, stream)))
                     return rr;
+            }
+            if (overlap) {
+                LP_CUDA(c, cudaEventRecord(c->pair_ev[0], s));
+                LP_CUDA(c, cudaStreamWaitEvent(sr, c->pair_ev[0], 0));
             }
             if (guided && A.K > 0)
                 rr = guided_tail(c, (const uint32_t*)(base + A.kp), base + A.ori, imgs[a].H, imgs[a].W,
                                  (const uint32_t*)(base + B.kp), base + B.ori, imgs[b].H, imgs[b].W,
                                  (const int32_t*)(base + o_match), (const float*)(base + o_d1),
                                  (const float*)(base + o_d2), (int32_t*)(base + o_rows), (float*)(base + o_feat),
-                                 (float*)(base + o_prob), (const float*)(base + o_pts), A.K, Mbuf + q, pid[q],
-                                 HM + 9 * (size_t)q, base + o_inl, n_in + q, stream);
+                                 (float*)(base + o_prob), pts, A.K, Mbuf + q, pid[q],
+                                 HM + 9 * (size_t)q, inl, n_in + q, stream);
             else
-                rr = lp_ransac(c, (const float*)(base + o_pts), A.K, Mbuf + q, pid[q], HM + 9 * (size_t)q,
-                               base + o_inl, n_in + q, nullptr, stream);
+                rr = lp_ransac(c, pts, A.K, Mbuf + q, pid[q], HM + 9 * (size_t)q, inl, n_in + q, nullptr, sr);
             if (rr) return rr;
+            if (overlap) LP_CUDA(c, cudaEventRecord(c->pair_ev[1 + slot], sr));
         }
+        if (overlap) {
+            LP_CUDA(c, cudaEventRecord(c->pair_ev[0], sr));
+            LP_CUDA(c, cudaStreamWaitEvent(s, c->pair_ev[0], 0));
+        }
+        c->last = s;
         k_pair_valid<<<(P + 127) / 128, 128, 0, s>>>(n_in, P, c->cfg.min_inliers, valid);
         LP_CUDA(c, cudaGetLastError());
         return LP_OK;
