@@ -628,7 +628,8 @@ int lp_stitch_pairs_ids(lp_ctx* c, const lp_image* imgs, int N, const int32_t* p
     const size_t o_M = o; o += al256(4 * (size_t)P + 8);
     const bool guided = c->proposal != nullptr;
     const size_t o_rows = o; o += guided ? al256(4 * (size_t)Kmax + 8) : 0;
-    const size_t o_feat = o; o += guided ? al256(32 * (size_t)Kmax + 32) : 0;
+    const size_t feat_slot = guided ? al256(32 * (size_t)Kmax + 32) : 0;
+    const size_t o_feat = o; o += 2 * feat_slot;
     const size_t o_prob = o; o += guided ? al256(4 * (size_t)Kmax + 8) : 0;
     int r = ensure(c, B_BATCH, o + 256);
     if (r) return r;
@@ -683,9 +684,10 @@ int lp_stitch_pairs_ids(lp_ctx* c, const lp_image* imgs, int N, const int32_t* p
                                   bf ? (uint16_t*)(base + ib[i].d16) : nullptr, base + ib[i].val, stream)))
                 return rr;
         }
-        // unguided: RANSAC of pair q on the second stream, beside pair q + 1's
-        // matching; the guided tail reads the match buffers, so it stays in order
-        const bool overlap = !guided;
+        // RANSAC of pair q (with the learned proposal: its forward pass and the
+        // guided RANSAC) on the second stream, beside pair q + 1's matching; the
+        // proposal's features read the match buffers, so they run in order
+        const bool overlap = true;
         cudaStream_t sr = overlap ? c->img_stream : s;
         if (overlap) {
             LP_CUDA(c, cudaEventRecord(c->pair_ev[1], s));
@@ -698,6 +700,7 @@ int lp_stitch_pairs_ids(lp_ctx* c, const lp_image* imgs, int N, const int32_t* p
             const int slot = overlap ? (q & 1) : 0;
             float* pts = (float*)(base + o_pts + slot * pts_slot);
             uint8_t* inl = base + o_inl + slot * inl_slot;
+            float* feat = (float*)(base + o_feat + slot * feat_slot);
             // the slot's previous RANSAC (pair q - 2) has finished reading it
             if (overlap) LP_CUDA(c, cudaStreamWaitEvent(s, c->pair_ev[1 + slot], 0));
             if (A.K == 0) {
@@ -713,18 +716,24 @@ int lp_stitch_pairs_ids(lp_ctx* c, const lp_image* imgs, int N, const int32_t* p
                                      guided ? (int32_t*)(base + o_rows) : nullptr, Mbuf + q, stream)))
                     return rr;
             }
+            if (guided && A.K > 0 &&
+                (rr = lp_mlp_features(c, (const uint32_t*)(base + A.kp), base + A.ori, imgs[a].H, imgs[a].W,
+                                      (const uint32_t*)(base + B.kp), base + B.ori, imgs[b].H, imgs[b].W,
+                                      (const int32_t*)(base + o_match), (const float*)(base + o_d1),
+                                      (const float*)(base + o_d2), (const int32_t*)(base + o_rows), Mbuf + q, A.K,
+                                      feat, stream)))
+                return rr;
             if (overlap) {
                 LP_CUDA(c, cudaEventRecord(c->pair_ev[0], s));
                 LP_CUDA(c, cudaStreamWaitEvent(sr, c->pair_ev[0], 0));
             }
-            if (guided && A.K > 0)
-                rr = guided_tail(c, (const uint32_t*)(base + A.kp), base + A.ori, imgs[a].H, imgs[a].W,
-                                 (const uint32_t*)(base + B.kp), base + B.ori, imgs[b].H, imgs[b].W,
-                                 (const int32_t*)(base + o_match), (const float*)(base + o_d1),
-                                 (const float*)(base + o_d2), (int32_t*)(base + o_rows), (float*)(base + o_feat),
-                                 (float*)(base + o_prob), pts, A.K, Mbuf + q, pid[q],
-                                 HM + 9 * (size_t)q, inl, n_in + q, stream);
-            else
+            if (guided && A.K > 0) {
+                float* prob = (float*)(base + o_prob);
+                if ((rr = lp_mlp_forward(c->proposal, feat, A.K, Mbuf + q, prob, nullptr, sr)))
+                    return fail(c, rr, "lp_mlp_forward failed");
+                rr = lp_ransac_prior(c, pts, A.K, Mbuf + q, prob, c->guided_iters, pid[q], HM + 9 * (size_t)q, inl,
+                                     n_in + q, nullptr, nullptr, sr);
+            } else
                 rr = lp_ransac(c, pts, A.K, Mbuf + q, pid[q], HM + 9 * (size_t)q, inl, n_in + q, nullptr, sr);
             if (rr) return rr;
             if (overlap) LP_CUDA(c, cudaEventRecord(c->pair_ev[1 + slot], sr));
