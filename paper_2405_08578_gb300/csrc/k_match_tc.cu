@@ -2,20 +2,21 @@
 // (tcgen05) for sm_103a, re-ranked in FP32 so that every decision equals the
 // plain FP32 form's.
 //
-// Distances: the accumulator of one MMA holds D = a~.b~ - |b~|^2 / 2 = -v / 2
-// (v = |b~|^2 - 2 a~.b~, the squared distance up to the row constant |a~|^2):
-// eight K-steps of the BF16 descriptors plus a ninth in which A carries
-// (1, 1, 1, 0, ...) and B carries (-h1, -h2, -h3, 0, ...), a three-term BF16
-// split of |b~|^2 / 2 (invalid B rows get a huge value instead).
+// Distances: the accumulator of one MMA holds D = a~.b~ over the eight K-steps
+// of the BF16 descriptors.  Valid descriptors have unit norm, so the squared
+// distance up to the row constant |a|^2 is v = |b|^2 - 2 a.b, estimated by
+// v~ = 1 - 2 D.  An invalid B row is all zero: v~ = 1, outside the candidate
+// window of every row whose second-best value is below 1 - delta - margin (its
+// exact value is +inf, so it can never be ranked).
 //
 // k_match_tc<pass> (persistent, one CTA per SM, clusters of two, 10 warps):
 //   warp 0    TMA producer: per work unit a 128-row A block (2 x 16 KB boxes,
-//             128-byte swizzle), then 256-row B tiles into a 2-stage ring;
+//             128-byte swizzle), then 256-row B tiles into a 3-stage ring;
 //             each CTA of the cluster loads one K-half (32 KB) of every tile
 //             and multicasts it to both CTAs (one L2 read per cluster).
 //   warp 1    allocates all 512 TMEM columns; one lane issues
 //             tcgen05.mma.cta_group::1.kind::f16 (M = 128, N = 256, K = 16,
-//             BF16 x BF16 -> FP32), 9 per B tile, into one of two 256-column
+//             BF16 x BF16 -> FP32), 8 per B tile, into one of two 256-column
 //             TMEM accumulator buffers; tcgen05.commit releases the B stage
 //             (in both CTAs) and hands the buffer to the epilogue.
 //   warps 2-9 epilogue: each thread owns one A row and one 128-column half of
@@ -33,9 +34,11 @@
 //
 // k_row_threshold: T = m2 + delta + margin per row, m2 the second smallest of
 //   the pass-1 values.  With unit, non-negative descriptors and BF16 unit
-//   roundoff u = 2^-8, |v~_j - v_j| <= 3u + 3u^2 + 1.1e-4 = delta for every
-//   column, so every column outside the candidate list has an exact value
-//   above T - delta >= the exact second-best.
+//   roundoff u = 2^-8, a~_k b~_k = a_k b_k (1 + e), |e| <= 2u + u^2, so
+//   |v~_j - v_j| <= |1 - |b_j|^2| + 2 (2u + u^2) a.b_j + accumulation
+//   <= 4u + 2u^2 + 1.5e-4 = delta for every valid column; every column outside
+//   the candidate list has an exact value above T - delta >= the exact
+//   second-best (invalid columns have the exact value +inf).
 // k_rerank (one warp per row): the candidates are re-scored with exactly the
 //   FP32 form's arithmetic (sequential FMA over k, then fma(-2, dot, |b|^2)),
 //   so their values are bit-identical to the FP32 form's; a row is certified
@@ -58,25 +61,18 @@ namespace {
 constexpr int kRowsPerUnit = 128;       // one M = 128 row block per CTA
 constexpr int kTileN = 256;             // B rows per tile (MMA N)
 constexpr int kTmemBufs = 2;            // accumulator buffers of kTileN columns (512 TMEM columns)
-constexpr int kStages = 2;              // B ring depth
+constexpr int kStages = 3;              // B ring depth
 constexpr int kThreadsTC = 320;         // 10 warps
 constexpr int kEpiWarps = 8;
 constexpr uint32_t kABytes = kRowsPerUnit * 128 * 2;   // 32 KB
 constexpr uint32_t kBBytes = kTileN * 128 * 2;         // 64 KB per stage
-// Ninth K-step: A rows extended by (1, 1, 1, 0, ..., 0), B rows by
-// (-h1, -h2, -h3, 0, ..., 0) with h1 + h2 + h3 = |b~|^2 / 2 (three BF16 terms),
-// so the accumulator holds D = a~.b~ - |b~|^2 / 2 = -v / 2.  16 BF16 per
-// extension row, 32-byte swizzle.
-constexpr uint32_t kExtRowBytes = 32;
-constexpr uint32_t kAExtBytes = kRowsPerUnit * kExtRowBytes;   // 4 KB, loaded once
-constexpr uint32_t kBExtBytes = kTileN * kExtRowBytes;         // 8 KB per stage
-constexpr uint32_t kSmemTC =
-    kABytes + kStages * kBBytes + kAExtBytes + kStages * kBExtBytes + 1024 /*barriers*/ + 1024 /*align slack*/;
+// 32 KB + 3 x 64 KB + 2 KB = 231,424 bytes of the 232,448 a CTA may opt into
+constexpr uint32_t kSmemTC = kABytes + kStages * kBBytes + 1024 /*barriers*/ + 1024 /*align slack*/;
 #ifndef LP_CAND_CAPACITY
 #define LP_CAND_CAPACITY 64
 #endif
 constexpr int kCandCapacity = LP_CAND_CAPACITY;        // pass-2 candidates kept per row
-// largest value a candidate may have: invalid columns (kNoColumn) never qualify
+// largest threshold a row may get (rows with fewer than two sampled columns)
 constexpr float kCandCap = 1.0e38f;
 // margin of the candidate window above m2 + delta (about five standard
 // deviations of the BF16 rounding error of a value); a row whose exact
@@ -89,12 +85,13 @@ constexpr float kMargin = 4.0e-3f;
 #define LP_PASS1_STRIDE 3
 #endif
 constexpr int kPass1Stride = LP_PASS1_STRIDE;
-// |b~|^2 of an invalid or masked column: finite (so that the column tag below
-// never turns it into a NaN) and far above any real value; treated as +inf by
-// the re-rank.
-constexpr float kNoColumn = 3.0e38f;
-// 3u + 3u^2 (BF16 rounding) + FP32 accumulation allowance (+ 1e-5 margin)
-constexpr float kDelta = 3.0f / 256.0f + 3.0f / 65536.0f + 1e-4f + 1e-5f;
+// |v~ - v| <= delta for every valid column, v~ = 1 - 2 a~.b~ (the tensor-core
+// value) and v = |b|^2 - 2 a.b (the FP32 form's): 4u + 2u^2 for the BF16
+// rounding of both operands (u = 2^-8; non-negative entries, a.b <= 1),
+// |1 - |b|^2| <= 5e-5 for FP32 unit descriptors (their rounding and the FP32
+// form's own norm accumulation), and an FP32 accumulation allowance of 1e-4
+// for both sides.
+constexpr float kDelta = 4.0f / 256.0f + 2.0f / 65536.0f + 1e-4f + 5e-5f;
 
 // ------------------------------------------------------------------ PTX wrappers
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
@@ -203,19 +200,6 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr)
     d |= (uint64_t)(1024u >> 4) << 32;
     d |= (uint64_t)1 << 46;
     d |= (uint64_t)2 << 61;
-    return d;
-}
-
-// The same for the 32-byte-swizzled extension tiles: 8-row atoms of 32 B
-// stacked every 256 B, swizzle mode 6 (32 B).
-__device__ __forceinline__ uint64_t sdesc32(uint32_t saddr)
-{
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)(16u >> 4) << 16;
-    d |= (uint64_t)(256u >> 4) << 32;
-    d |= (uint64_t)1 << 46;
-    d |= (uint64_t)6 << 61;
     return d;
 }
 
@@ -332,16 +316,13 @@ __device__ __noinline__ void flush_cands(int32_t* ncand, int32_t* cand, long lon
 
 template <int kPass>
 __global__ void __launch_bounds__(kThreadsTC, 1)
-k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-           const __grid_constant__ CUtensorMap tmAx, const __grid_constant__ CUtensorMap tmBx, const TcParams p)
+k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcParams p)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t* sA = smem;
     uint8_t* sB = smem + kABytes;
-    uint8_t* sAx = smem + kABytes + kStages * kBBytes;   // A extension, 2 x 128 rows
-    uint8_t* sBx = sAx + kAExtBytes;                     // B extension per stage
-    uint64_t* bars = reinterpret_cast<uint64_t*>(sBx + kStages * kBExtBytes);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sB + kStages * kBBytes);
     // barrier slots
     uint64_t* full = bars;                 // [kStages]
     uint64_t* empty = bars + kStages;      // [kStages]
@@ -377,8 +358,6 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         tma_prefetch_desc(&tmA);
         tma_prefetch_desc(&tmB);
-        tma_prefetch_desc(&tmAx);
-        tma_prefetch_desc(&tmBx);
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tmem_slot))
@@ -409,10 +388,9 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
                 if (rp != prev_rp) {
                     ok = mbar_wait(smem_u32(aempty), (v & 1) ^ 1, abort_flag, p.status);
                     if (!ok) break;
-                    mbar_expect_tx(smem_u32(afull), kABytes + (v == 0 ? kAExtBytes : 0u));
+                    mbar_expect_tx(smem_u32(afull), kABytes);
                     tma_load_2d(smem_u32(sA), &tmA, 0, rp * kRowsPerUnit, smem_u32(afull));
                     tma_load_2d(smem_u32(sA + kABytes / 2), &tmA, 64, rp * kRowsPerUnit, smem_u32(afull));
-                    if (v == 0) tma_load_2d(smem_u32(sAx), &tmAx, 0, 0, smem_u32(afull));   // constant rows
                     a_armed = v;
                     ++v;
                     prev_rp = rp;
@@ -424,13 +402,11 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
                     if (!ok) break;
                     uint8_t* dst = sB + s * kBBytes;
                     const int y = (int)(c0 + (long long)t * p.tstride * kTileN);
-                    mbar_expect_tx(smem_u32(&full[s]), kBBytes + kBExtBytes);
-                    if (crank == 0) {
+                    mbar_expect_tx(smem_u32(&full[s]), kBBytes);
+                    if (crank == 0)
                         tma_load_2d_mc(smem_u32(dst), &tmB, 0, y, smem_u32(&full[s]), 3);
-                        tma_load_2d_mc(smem_u32(sBx + s * kBExtBytes), &tmBx, 0, y, smem_u32(&full[s]), 3);
-                    } else {
+                    else
                         tma_load_2d_mc(smem_u32(dst + kBBytes / 2), &tmB, 64, y, smem_u32(&full[s]), 3);
-                    }
                     armed[s] = (int)k;
                 }
             }
@@ -456,7 +432,6 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
             // a base is the base descriptor + (o >> 4) (the 14-bit start field
             // never carries: shared addresses stay below 256 KB)
             const uint64_t dA0 = sdesc(smem_u32(sA)), dB0 = sdesc(smem_u32(sB));
-            const uint64_t dAx0 = sdesc32(smem_u32(sAx)), dBx0 = sdesc32(smem_u32(sBx));
             long long n = 0;
             int v = 0;
             bool ok = true;
@@ -487,7 +462,6 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
                     if (!ok) break;
                     tc_fence_after();
                     const uint64_t dB = dB0 + (uint64_t)((s * kBBytes) >> 4);
-                    const uint64_t dBx = dBx0 + (uint64_t)((s * kBExtBytes) >> 4);
                     const uint32_t d = tmem + (uint32_t)(b * kTileN);
 #pragma unroll
                     for (int h = 0; h < 2; ++h)
@@ -497,7 +471,6 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
                             const uint64_t bd = dB + (uint64_t)((h * (kBBytes / 2) + kk * 32) >> 4);
                             mma_bf16(d, ad, bd, (h | kk) ? 1u : 0u);
                         }
-                    mma_bf16(d, dAx0, dBx, 1u);
                     mma_commit_mc(smem_u32(&empty[s]), 3);
                     mma_commit(smem_u32(&tfull[b]));
                 }
@@ -530,7 +503,8 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
             const long long row = (long long)rp * kRowsPerUnit + row_in_unit;
             const bool live = row < p.NA;
             float d1 = -INFINITY, d2 = -INFINITY;                                    // pass 1
-            const float TD = (kPass == 2 && live) ? -0.5f * p.thr[row] : INFINITY;  // pass 2
+            // pass 2: v~ = 1 - 2 D <= T  <=>  D >= (1 - T) / 2 (1e-6 lower: rounding of TD)
+            const float TD = (kPass == 2 && live) ? 0.5f * (1.f - p.thr[row]) - 1e-6f : INFINITY;
             int nc = 0, cj0 = 0, cj1 = 0, cj2 = 0, cj3 = 0;
             for (int t = 0; t < ntiles; ++t, ++n) {
                 const int b = (int)(n % kTmemBufs);
@@ -599,7 +573,8 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
                 }
             }
             if (!ok) break;
-            if (kPass == 1 && live) p.pm[((long long)split * 2 + half) * p.NA + row] = make_float2(-2.f * d1, -2.f * d2);
+            if (kPass == 1 && live)
+                p.pm[((long long)split * 2 + half) * p.NA + row] = make_float2(1.f - 2.f * d1, 1.f - 2.f * d2);
             if (kPass == 2 && nc > 0) flush_cands(p.ncand, p.cand, row, nc, cj0, cj1, cj2, cj3);
         }
     }
@@ -608,37 +583,6 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
     cluster_sync();   // no multicast copy or remote arrival still targets this CTA
     tc_fence_after();
     if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
-}
-
-// B extension rows: (-h1, -h2, -h3, 0 x 13) with h1 + h2 + h3 = |b~|^2 / 2 to
-// within 2^-24 relative (|b~|^2 in FP32 from the BF16 row; kNoColumn / 2 for
-// an invalid row), and the constant A extension rows (1, 1, 1, 0 x 13).
-__global__ void k_ext_rows(const __nv_bfloat16* d, const uint8_t* v, long long n, __nv_bfloat16* bext,
-                           __nv_bfloat16* aext)
-{
-    const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (blockIdx.x == 0 && threadIdx.x < kRowsPerUnit) {
-        __nv_bfloat16* r = aext + threadIdx.x * 16;
-        for (int k = 0; k < 16; ++k) r[k] = __float2bfloat16_rn(k < 3 ? 1.f : 0.f);
-    }
-    if (w >= n) return;
-    const uint2 raw = reinterpret_cast<const uint2*>(d + w * 128)[lane];
-    const __nv_bfloat162 lo = *reinterpret_cast<const __nv_bfloat162*>(&raw.x);
-    const __nv_bfloat162 hi = *reinterpret_cast<const __nv_bfloat162*>(&raw.y);
-    const float2 a = __bfloat1622float2(lo), b = __bfloat1622float2(hi);
-    float sq = a.x * a.x + a.y * a.y + b.x * b.x + b.y * b.y;
-#pragma unroll
-    for (int o = 16; o; o >>= 1) sq += __shfl_xor_sync(0xFFFFFFFFu, sq, o);
-    if (lane < 16) {
-        const float x = -0.5f * (v[w] ? sq : kNoColumn);
-        const float h1 = __bfloat162float(__float2bfloat16_rn(x));
-        const float r1 = x - h1;
-        const float h2 = __bfloat162float(__float2bfloat16_rn(r1));
-        const float h3 = r1 - h2;
-        const float e = lane == 0 ? h1 : lane == 1 ? h2 : lane == 2 ? h3 : 0.f;
-        bext[w * 16 + lane] = __float2bfloat16_rn(e);
-    }
 }
 
 // ------------------------------------------------------------------ re-rank
@@ -895,19 +839,6 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
     return fn;
 }
 
-bool make_map_ext(CUtensorMap* m, const void* base, long long rows, uint32_t box_rows)
-{
-    auto fn = encode_fn();
-    if (!fn) return false;
-    cuuint64_t dims[2] = {16, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {32};
-    cuuint32_t box[2] = {16, box_rows};
-    cuuint32_t estr[2] = {1, 1};
-    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
-              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
 bool make_map(CUtensorMap* m, const void* base, long long rows, uint32_t box_rows)
 {
     auto fn = encode_fn();
@@ -939,7 +870,7 @@ int pick_tc_splits(int nrp, long long NB, int sms)
 
 struct TcLayout {
     int S;
-    size_t off_bext, off_aext, off_na, off_nb32, off_pm, off_thr, off_cand, off_ncand, off_part1, off_rows, off_cnt, off_part_r,
+    size_t off_na, off_nb32, off_pm, off_thr, off_cand, off_ncand, off_part1, off_rows, off_cnt, off_part_r,
         total;
 };
 
@@ -950,8 +881,6 @@ TcLayout tc_layout(long long NA, long long NB, int sms)
     L.S = pick_tc_splits(nrp, NB, std::max(1, sms / 2));
     size_t o = 0;
     auto take = [&](size_t bytes) { size_t r = o; o += (bytes + 255) & ~size_t(255); return r; };
-    L.off_bext = take(kExtRowBytes * (size_t)NB + 64);
-    L.off_aext = take(kAExtBytes);
     L.off_na = take(sizeof(float) * (size_t)NA);
     L.off_nb32 = take(sizeof(float) * (size_t)NB);
     L.off_pm = take(sizeof(float2) * 2 * (size_t)L.S * NA);
@@ -987,8 +916,6 @@ cudaError_t launch_match_bf16(const MatchArgs& a, void* ws, size_t ws_bytes, int
     const TcLayout L = tc_layout(a.NA, a.NB, num_sms);
     if (ws_bytes < L.total) return cudaErrorInvalidValue;
     uint8_t* w = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(ws) + 255) & ~uintptr_t(255));
-    __nv_bfloat16* bext = reinterpret_cast<__nv_bfloat16*>(w + L.off_bext);
-    __nv_bfloat16* aext = reinterpret_cast<__nv_bfloat16*>(w + L.off_aext);
     float* na = reinterpret_cast<float*>(w + L.off_na);
     float* nb32 = reinterpret_cast<float*>(w + L.off_nb32);
     float2* pm = reinterpret_cast<float2*>(w + L.off_pm);
@@ -1017,11 +944,8 @@ cudaError_t launch_match_bf16(const MatchArgs& a, void* ws, size_t ws_bytes, int
         k_row_norms<<<(unsigned)((a.NB * 32 + 255) / 256), 256, 0, forked ? a.fork->aux[1] : s>>>(a.dB, a.vB, a.NB,
                                                                                                  nb32, INFINITY);
         if (forked && (e = cudaEventRecord(a.fork->join_ev[1], a.fork->aux[1])) != cudaSuccess) return e;
-        k_ext_rows<<<(unsigned)((a.NB * 32 + 255) / 256), 256, 0, s>>>(
-            reinterpret_cast<const __nv_bfloat16*>(a.dB16), a.vB, a.NB, bext, aext);
-        CUtensorMap tA, tB, tAx, tBx;
-        if (!make_map(&tA, a.dA16, a.NA, kRowsPerUnit) || !make_map(&tB, a.dB16, a.NB, kTileN) ||
-            !make_map_ext(&tAx, aext, kRowsPerUnit, kRowsPerUnit) || !make_map_ext(&tBx, bext, a.NB, kTileN))
+        CUtensorMap tA, tB;
+        if (!make_map(&tA, a.dA16, a.NA, kRowsPerUnit) || !make_map(&tB, a.dB16, a.NB, kTileN))
             return cudaErrorInvalidValue;
         TcParams p;
         p.NA = a.NA;
@@ -1061,9 +985,9 @@ cudaError_t launch_match_bf16(const MatchArgs& a, void* ws, size_t ws_bytes, int
         if (a.ev0) cudaEventRecord(a.ev0, s);
         TcParams p1 = p;
         p1.tstride = kPass1Stride;
-        if ((e = cudaLaunchKernelEx(&cfg, k_match_tc<1>, tA, tB, tAx, tBx, p1)) != cudaSuccess) return e;
+        if ((e = cudaLaunchKernelEx(&cfg, k_match_tc<1>, tA, tB, p1)) != cudaSuccess) return e;
         k_row_threshold<<<(unsigned)((a.NA + 255) / 256), 256, 0, s>>>(pm, 2 * L.S, a.NA, a.vA, kDelta, thr, ncand);
-        if ((e = cudaLaunchKernelEx(&cfg, k_match_tc<2>, tA, tB, tAx, tBx, p)) != cudaSuccess) return e;
+        if ((e = cudaLaunchKernelEx(&cfg, k_match_tc<2>, tA, tB, p)) != cudaSuccess) return e;
         if (a.ev1) cudaEventRecord(a.ev1, s);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if (forked && ((e = cudaStreamWaitEvent(s, a.fork->join_ev[1], 0)) != cudaSuccess ||
