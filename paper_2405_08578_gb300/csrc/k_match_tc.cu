@@ -26,7 +26,7 @@
 //             maxima of D per (split, half, row), written as v.  Pass 2 (all
 //             tiles): every column with v <= T (a three-input max tree per
 //             chunk finds the rare chunks that hold one) is appended to the
-//             row's candidate list (capacity 64, one atomic per 4 columns).
+//             row's candidate list (capacity 96, one atomic per 4 columns).
 //   A work unit is (pair of 128-row blocks, one of S column splits of B); a
 //   cluster takes a contiguous run of units.  Every mbarrier wait is bounded
 //   by a 2 s clock limit; on expiry the CTA records LP_ERR_TIMEOUT, drains its
@@ -69,7 +69,7 @@ constexpr uint32_t kBBytes = kTileN * 128 * 2;         // 64 KB per stage
 // 32 KB + 3 x 64 KB + 2 KB = 231,424 bytes of the 232,448 a CTA may opt into
 constexpr uint32_t kSmemTC = kABytes + kStages * kBBytes + 1024 /*barriers*/ + 1024 /*align slack*/;
 #ifndef LP_CAND_CAPACITY
-#define LP_CAND_CAPACITY 64
+#define LP_CAND_CAPACITY 96
 #endif
 constexpr int kCandCapacity = LP_CAND_CAPACITY;        // pass-2 candidates kept per row
 // largest threshold a row may get (rows with fewer than two sampled columns)
@@ -77,7 +77,10 @@ constexpr float kCandCap = 1.0e38f;
 // margin of the candidate window above m2 + delta (about five standard
 // deviations of the BF16 rounding error of a value); a row whose exact
 // second-best exceeds m2 + kMargin is not certified and is re-scanned
-constexpr float kMargin = 4.0e-3f;
+#ifndef LP_CAND_MARGIN
+#define LP_CAND_MARGIN 4.0e-3f
+#endif
+constexpr float kMargin = LP_CAND_MARGIN;
 // Pass 1 visits every kPass1Stride-th column tile: its m2 is then the second
 // smallest chunk minimum of a spread subset, still the value of a second
 // column, so still >= B; the candidate window widens a little.
