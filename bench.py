@@ -142,7 +142,7 @@ def oracle_pair_seconds(pair, rows_sample=1500, desc_sample=15000, seed=0, M=300
 # workload, from one ncu capture, valid only for the kernel source it was taken
 # on (file SHA-1).
 PROFILED_TRAFFIC = {
-    "k_match_tc.cu": ("c040957f97ed413feaff23dac1b68f938f30f874", 40.4910e6),
+    "k_match_tc.cu": ("b66d5fbc152f9503dc29fe685a13b1f301b2590a", 38.6358e6),
 }
 
 
@@ -557,12 +557,12 @@ def main():
     roof["traffic"] = profiled_traffic("k_match_tc.cu" if r["bf"] else "k_match_fp32.cu")
     roof["peak_source"] = f"{pk_kind}" if r["bf"] else "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"
     value = world * args.steps / r["t_steps"]
-    # our kernels per step (BF16 form): detect 2, describe 6, match 10 (two row
-    # norms, extension rows, pass 1, threshold, pass 2, re-rank, re-scan,
-    # re-scan merge, finish), compact 2, RANSAC 9 (hypotheses, score, recount,
-    # argmax, three refit sums, solve, final); FP32 form: match 4 (two row
-    # norms, main, finish) and the rest as BF16
-    launches_per_step = 29 if r["bf"] else 23
+    # our kernels per step (BF16 form): detect 2, describe 6, match 9 (two row
+    # norms, pass 1, threshold, pass 2, re-rank, re-scan, re-scan merge,
+    # finish), compact 2, RANSAC 9 (hypotheses, score, recount, argmax, three
+    # refit sums, solve, final); FP32 form: match 4 (two row norms, main,
+    # finish) and the rest as BF16
+    launches_per_step = 28 if r["bf"] else 23
     line = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * r["t_steps"] / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if r["bf"] else "f32", "data": "synthetic",
