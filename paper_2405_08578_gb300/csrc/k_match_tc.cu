@@ -6,8 +6,8 @@
 // of the BF16 descriptors.  Valid descriptors have unit norm, so the squared
 // distance up to the row constant |a|^2 is v = |b|^2 - 2 a.b, estimated by
 // v~ = 1 - 2 D.  An invalid B row is all zero: v~ = 1, outside the candidate
-// window of every row whose second-best value is below 1 - delta - margin (its
-// exact value is +inf, so it can never be ranked).
+// window of every row whose second-best value is well below 1 (its exact value
+// is +inf, so it can never be ranked).
 //
 // k_match_tc<pass> (persistent, one CTA per SM, clusters of two, 10 warps):
 //   warp 0    TMA producer: per work unit a 128-row A block (2 x 16 KB boxes,
@@ -32,17 +32,18 @@
 //   by a 2 s clock limit; on expiry the CTA records LP_ERR_TIMEOUT, drains its
 //   copies, frees its TMEM and returns.
 //
-// k_row_threshold: T = m2 + delta + margin per row, m2 the second smallest of
-//   the pass-1 values.  With unit, non-negative descriptors and BF16 unit
-//   roundoff u = 2^-8, a~_k b~_k = a_k b_k (1 + e), |e| <= 2u + u^2, so
-//   |v~_j - v_j| <= |1 - |b_j|^2| + 2 (2u + u^2) a.b_j + accumulation
-//   <= 4u + 2u^2 + 1.5e-4 = delta for every valid column; every column outside
-//   the candidate list has an exact value above T - delta >= the exact
-//   second-best (invalid columns have the exact value +inf).
+// k_row_threshold: the certification point x = m2 + margin per row, m2 the
+//   second smallest of the pass-1 values.  With unit, non-negative
+//   descriptors and BF16 unit roundoff u = 2^-8, a~_k b~_k = a_k b_k (1 + e),
+//   |e| <= 2u + u^2, and 2 a.b_j = |b_j|^2 - v_j <= 1 + eps - v_j, so
+//   |v~_j - v_j| <= delta(v_j) = c + k (1 + eps - v_j), k = 2u + u^2, c the
+//   norm and accumulation allowance.  Pass 2 lists every column with
+//   v~ <= T = x + delta(x).  v + delta(v) increases with v, so a column outside
+//   the list (v~ > T) has an exact value above x (invalid columns: +inf).
 // k_rerank (one warp per row): the candidates are re-scored with exactly the
 //   FP32 form's arithmetic (sequential FMA over k, then fma(-2, dot, |b|^2)),
 //   so their values are bit-identical to the FP32 form's; a row is certified
-//   when its exact second-best is < T - delta.  Rows with an overflowed list
+//   when its exact second-best is < x.  Rows with an overflowed list
 //   or without that margin are re-scanned in FP32 (k_rescan, k_rescan_merge).
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -74,9 +75,9 @@ constexpr uint32_t kSmemTC = kABytes + kStages * kBBytes + 1024 /*barriers*/ + 1
 constexpr int kCandCapacity = LP_CAND_CAPACITY;        // pass-2 candidates kept per row
 // largest threshold a row may get (rows with fewer than two sampled columns)
 constexpr float kCandCap = 1.0e38f;
-// margin of the candidate window above m2 + delta (about five standard
-// deviations of the BF16 rounding error of a value); a row whose exact
-// second-best exceeds m2 + kMargin is not certified and is re-scanned
+// margin of the certification point above m2 (about five standard deviations
+// of the BF16 rounding error of a value); a row whose exact second-best
+// exceeds m2 + kMargin is not certified and is re-scanned
 #ifndef LP_CAND_MARGIN
 #define LP_CAND_MARGIN 4.0e-3f
 #endif
@@ -88,13 +89,22 @@ constexpr float kMargin = LP_CAND_MARGIN;
 #define LP_PASS1_STRIDE 3
 #endif
 constexpr int kPass1Stride = LP_PASS1_STRIDE;
-// |v~ - v| <= delta for every valid column, v~ = 1 - 2 a~.b~ (the tensor-core
-// value) and v = |b|^2 - 2 a.b (the FP32 form's): 4u + 2u^2 for the BF16
-// rounding of both operands (u = 2^-8; non-negative entries, a.b <= 1),
-// |1 - |b|^2| <= 5e-5 for FP32 unit descriptors (their rounding and the FP32
-// form's own norm accumulation), and an FP32 accumulation allowance of 1e-4
-// for both sides.
-constexpr float kDelta = 4.0f / 256.0f + 2.0f / 65536.0f + 1e-4f + 5e-5f;
+// |v~ - v| <= delta(v) = kDeltaC + kDeltaK (1 + kNormEps - v) for every valid
+// column, v~ = 1 - 2 a~.b~ (the tensor-core value) and v = |b|^2 - 2 a.b (the
+// FP32 form's): (2u + u^2) 2 a.b for the BF16 rounding of both operands
+// (u = 2^-8, non-negative entries), |1 - |b|^2| <= kNormEps = 5e-5 for FP32
+// unit descriptors (their rounding and the FP32 form's own norm
+// accumulation), and 1.5e-4 of FP32 accumulation on both sides.
+constexpr float kNormEps = 5e-5f;
+constexpr float kDeltaK = 2.0f / 256.0f + 1.0f / 65536.0f;
+constexpr float kDeltaC = kNormEps + 1.5e-4f;
+
+// Top of the candidate window of a row certified at x: T = x + delta(x).
+__host__ __device__ __forceinline__ float window_top(float x)
+{
+    const float r = 1.f + kNormEps - x;
+    return x + kDeltaC + kDeltaK * (r > 0.f ? r : 0.f);
+}
 
 // ------------------------------------------------------------------ PTX wrappers
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
@@ -507,7 +517,7 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
             const bool live = row < p.NA;
             float d1 = -INFINITY, d2 = -INFINITY;                                    // pass 1
             // pass 2: v~ = 1 - 2 D <= T  <=>  D >= (1 - T) / 2 (1e-6 lower: rounding of TD)
-            const float TD = (kPass == 2 && live) ? 0.5f * (1.f - p.thr[row]) - 1e-6f : INFINITY;
+            const float TD = (kPass == 2 && live) ? 0.5f * (1.f - window_top(p.thr[row])) - 1e-6f : INFINITY;
             int nc = 0, cj0 = 0, cj1 = 0, cj2 = 0, cj3 = 0;
             for (int t = 0; t < ntiles; ++t, ++n) {
                 const int b = (int)(n % kTmemBufs);
@@ -629,13 +639,10 @@ __device__ __forceinline__ void warp_top2(float& b1, int& j1, float& b2, int& j2
     }
 }
 
-// Candidate threshold per row from the pass-1 pairs: m2 = the second-smallest
-// of all splits' chunk minima names a column other than the row's BF16
-// minimum, so m2 >= B, the row's second-smallest BF16 value.  The threshold
-// is m2 + delta + kMargin (capped below the invalid-column marker), -inf for
+// Per row, the certification point x = m2 + kMargin (m2 the second smallest
+// pass-1 value; capped for rows with fewer than two sampled columns), -inf for
 // an invalid query row; the row's candidate counter is cleared.
-__global__ void k_row_threshold(const float2* pm, int S, long long NA, const uint8_t* vA, float delta, float* thr,
-                                int32_t* ncand)
+__global__ void k_row_threshold(const float2* pm, int S, long long NA, const uint8_t* vA, float* thr, int32_t* ncand)
 {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= NA) return;
@@ -646,18 +653,18 @@ __global__ void k_row_threshold(const float2* pm, int S, long long NA, const uin
         m2 = fminf(fminf(m2, hi), fmaxf(m1, lo));
         m1 = fminf(m1, lo);
     }
-    thr[i] = vA[i] ? fminf(m2 + delta + kMargin, kCandCap) : -INFINITY;
+    thr[i] = vA[i] ? fminf(m2 + kMargin, kCandCap) : -INFINITY;
     ncand[i] = 0;
 }
 
 // One warp per row, one candidate per lane: exact FP32-form values (the FP32
 // form's own arithmetic), the top 2 by (value, column).  Every column outside
-// the list has a BF16 value > T and so an FP32-form value > T - delta: the
-// row is certified when its exact second-best is < T - delta.  Rows with an
-// overflowed list or without that margin are queued for the FP32 re-scan.
+// the list has a BF16 value > window_top(x) and so an FP32-form value > x: the
+// row is certified when its exact second-best is < x.  Rows with an overflowed
+// list or without that margin are queued for the FP32 re-scan.
 __global__ void __launch_bounds__(kRerankWarps * 32)
 k_rerank(const float* A, const uint8_t* vA, const float* B, const float* nb32, const int32_t* cand,
-         const int32_t* ncand, const float* thr, long long NA, float delta, float4* out_part, int32_t* rescan_rows,
+         const int32_t* ncand, const float* thr, long long NA, float4* out_part, int32_t* rescan_rows,
          int32_t* rescan_count)
 {
     __shared__ __align__(16) float qa[kRerankWarps][128];
@@ -681,7 +688,7 @@ k_rerank(const float* A, const uint8_t* vA, const float* B, const float* nb32, c
             top2_lex(b1, j1, b2, j2, fp32_form_value(qa[warp], B + (long long)j * 128, __ldg(nb32 + j)), j);
         }
         warp_top2(b1, j1, b2, j2);
-        ok = b2 < T - delta;
+        ok = b2 < T;   // T = x, the row's certification point
     }
     if (lane == 0) {
         if (ok) {
@@ -989,7 +996,7 @@ cudaError_t launch_match_bf16(const MatchArgs& a, void* ws, size_t ws_bytes, int
         TcParams p1 = p;
         p1.tstride = kPass1Stride;
         if ((e = cudaLaunchKernelEx(&cfg, k_match_tc<1>, tA, tB, p1)) != cudaSuccess) return e;
-        k_row_threshold<<<(unsigned)((a.NA + 255) / 256), 256, 0, s>>>(pm, 2 * L.S, a.NA, a.vA, kDelta, thr, ncand);
+        k_row_threshold<<<(unsigned)((a.NA + 255) / 256), 256, 0, s>>>(pm, 2 * L.S, a.NA, a.vA, thr, ncand);
         if ((e = cudaLaunchKernelEx(&cfg, k_match_tc<2>, tA, tB, p)) != cudaSuccess) return e;
         if (a.ev1) cudaEventRecord(a.ev1, s);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -997,7 +1004,7 @@ cudaError_t launch_match_bf16(const MatchArgs& a, void* ws, size_t ws_bytes, int
                        (e = cudaStreamWaitEvent(s, a.fork->join_ev[0], 0)) != cudaSuccess))
             return e;
         k_rerank<<<(unsigned)((a.NA + kRerankWarps - 1) / kRerankWarps), kRerankWarps * 32, 0, s>>>(
-            a.dA, a.vA, a.dB, nb32, cand, ncand, thr, a.NA, kDelta, part1, rows, cnt);
+            a.dA, a.vA, a.dB, nb32, cand, ncand, thr, a.NA, part1, rows, cnt);
         if ((e = cudaFuncSetAttribute(k_rescan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRescanSmem)) !=
             cudaSuccess)
             return e;
