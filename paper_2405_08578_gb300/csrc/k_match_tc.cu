@@ -79,7 +79,7 @@ constexpr float kCandCap = 1.0e38f;
 // of the BF16 rounding error of a value); a row whose exact second-best
 // exceeds m2 + kMargin is not certified and is re-scanned
 #ifndef LP_CAND_MARGIN
-#define LP_CAND_MARGIN 4.0e-3f
+#define LP_CAND_MARGIN 5.0e-3f
 #endif
 constexpr float kMargin = LP_CAND_MARGIN;
 // Pass 1 visits every kPass1Stride-th column tile: its m2 is then the second
