@@ -547,7 +547,7 @@ def main():
                 "unit": "TFLOP/s", "kernel": "k_match_tc pass 1 + k_row_threshold + k_match_tc pass 2",
                 "launch_ms": 1e3 * r["t_kern"], "stage_tflops": flops / r["t_match"] / 1e12,
                 "note": "achieved counts the useful 2*NA*NB*128 flops; the tensor pipe also runs pass 1 on a "
-                        "third of the tiles and a ninth K-step"}
+                        "third of the tiles; traffic is the DRAM bytes of both passes from one ncu capture"}
     else:
         sm_max = pk.get("sm_max_mhz", 2070.0)
         fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12
