@@ -143,6 +143,14 @@ def test_describe_small(shape, Ls):
     _describe_parity(p.A, Ls, upright=True)
 
 
+def test_describe_huge_scale_global_path():
+    # w_s = 256 (L = 1024): each cell's grid exceeds the shared-memory budget of
+    # the split path, so these points take the global-memory kernel
+    p = synth.small_pair(2048, 2048, seed=9)
+    _describe_parity(p.A, (1024,))
+    _describe_parity(p.A, (1024,), upright=True)
+
+
 def test_describe_640x480():
     p = synth.pair_640x480(0)
     _describe_parity(p.A, synth.PAIR_640x480_LS)
