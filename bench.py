@@ -337,6 +337,7 @@ def fp32_form_and_batch(args, rank):
     out["batch_3x3"] = {"images": 9, "pairs": 36, "pairs_per_s": 36 * k / t, "ms_per_batch": 1e3 * t / k,
                         "valid_pairs": int(va.sum().item()), "graph": True}
     out["mosaic_3x3"] = mosaic(bt, images, ctx, HM, va, flush, k)
+    out["detect_3x3"] = detect_batch(ctx, images, flush, k)
     out["table2"] = table2(flush)
     if args.train_pairs > 0:
         out["learned_proposal"] = learned_proposal(args, bt, images, ctx, HM, ni, va, flush, k)
@@ -389,6 +390,42 @@ def mosaic(bt, images, ctx, HM, va, flush, k):
     return {"placed": placed, "rounds": int(plan["round"].max()) + 1, "canvas": [ch, cw], "plan_ms": round(plan_ms, 3),
             "placement_err_px": round(err, 2),
             "render_ms": 1e3 * t / k, "render_GBps_algorithmic": bytes_alg / (t / k) / 1e9}
+
+
+def detect_batch(ctx, images, flush, k):
+    """Sec. 2.1-2.2 on the nine RGB tiles: one lp_detect_batch against nine
+    lp_detect calls; algorithmic bytes = RGB read + intensity written + keys
+    written, per image."""
+    import torch
+
+    from paper_2405_08578_gb300 import lp
+    s = torch.cuda.current_stream()
+    K = lp.lp_num_keypoints(H_IMG, W_IMG, LS)
+    kps = [torch.empty(K, dtype=torch.int32, device="cuda") for _ in images]
+    grays = [torch.empty(H_IMG * W_IMG + 16, dtype=torch.uint8, device="cuda") for _ in images]
+    nbytes = len(images) * (H_IMG * W_IMG * 3 + H_IMG * W_IMG + 4 * K)
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        t = 0.0
+        for _ in range(k):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            fn()
+            e1.record(s)
+            torch.cuda.synchronize()
+            t += e0.elapsed_time(e1) / 1e3
+        return t / k
+
+    tb = timed(lambda: ctx.lp_detect_batch(images, kps, grays))
+    ts = timed(lambda: [ctx.lp_detect(t, h, w, p, ch, kp, g) for (t, h, w, p, ch), kp, g in zip(images, kps, grays)])
+    pk = peaks()[0]
+    return {"images": len(images), "algorithmic_MB": nbytes / 1e6, "batch_ms": 1e3 * tb, "batch_GBps": nbytes / tb / 1e9,
+            "batch_frac_hbm": nbytes / tb / 1e9 / pk["hbm_gbs"], "one_by_one_ms": 1e3 * ts,
+            "one_by_one_GBps": nbytes / ts / 1e9}
 
 
 # Table 2 stitching times of LP-SIFT (MATLAB on an i9-12900 CPU, detection to
@@ -584,6 +621,7 @@ def main():
         line["config"]["batch_3x3"] = extra["batch_3x3"]
         line["config"]["mosaic_3x3"] = extra["mosaic_3x3"]
         line["config"]["table2"] = extra["table2"]
+        line["config"]["detect_3x3"] = extra["detect_3x3"]
         if "learned_proposal" in extra:
             line["config"]["learned_proposal"] = extra["learned_proposal"]
     if world == 1 and not args.no_cpu_baseline:

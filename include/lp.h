@@ -247,6 +247,18 @@ typedef struct lp_image {
     int32_t H, W, pitch, channels;
 } lp_image;
 
+/* lp_detect for N images at once (same configuration, same channel count):
+ * on the fast path (nested window sizes, the largest <= 128, alpha = 0) the
+ * images share launches of up to 12, so a batch fills the GPU that one image
+ * cannot; otherwise the images are detected one by one.  Results are those of
+ * lp_detect, bit for bit.
+ *  imgs     host array of N images (device data pointers)
+ *  kp_idx   host array of N device pointers, uint32[K_i] each
+ *  gray     host array of N device pointers (uint8[H_i*W_i], required for RGB)
+ * Errors: LP_ERR_ARG, LP_ERR_ALIGN, LP_ERR_CUDA. */
+LP_API int lp_detect_batch(lp_ctx* ctx, const lp_image* imgs, int N, uint32_t* const* kp_idx, uint8_t* const* gray,
+                           void* stream);
+
 /* Sec. 4: the homography matrix H_M of a set of images, one entry per pair.
  *  imgs     host array of N image descriptors (device pixel pointers); every
  *           image uses the same channel count

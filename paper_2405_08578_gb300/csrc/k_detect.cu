@@ -59,8 +59,9 @@ __device__ __forceinline__ uint4 gray16(const uint4& c0, const uint4& c1, const 
     return make_uint4(o[0], o[1], o[2], o[3]);
 }
 
+// One TS x TS tile (tile column bx, tile row by) of one image.
 template <int CH>
-__global__ void __launch_bounds__(kDetectThreads) k_detect_nested(DetectParams p)
+__device__ __forceinline__ void detect_tile(const DetectParams& p, int bx, int by)
 {
     extern __shared__ __align__(16) uint8_t sm[];
     const int TS = p.TS;
@@ -73,7 +74,7 @@ __global__ void __launch_bounds__(kDetectThreads) k_detect_nested(DetectParams p
     uint32_t* wmx = smn + nseg;
     uint32_t* wmn = wmx + p.lvl_off[p.nL];
 
-    const int tx0 = blockIdx.x * TS, ty0 = blockIdx.y * TS;
+    const int tx0 = bx * TS, ty0 = by * TS;
     const int rows = min(TS, p.H - ty0), cols = min(TS, p.W - tx0);
 
     // ---- stream the tile once: 16 pixels per 16-byte (gray) or 48-byte (RGB) load
@@ -170,6 +171,34 @@ __global__ void __launch_bounds__(kDetectThreads) k_detect_nested(DetectParams p
             }
         }
     }
+}
+
+template <int CH>
+__global__ void __launch_bounds__(kDetectThreads) k_detect_nested(const __grid_constant__ DetectParams p)
+{
+    detect_tile<CH>(p, blockIdx.x, blockIdx.y);
+}
+
+// Several images (same scales and channel count) in one launch: a flat CTA
+// index runs over every image's tiles, so a batch fills the GPU that one
+// image cannot.
+constexpr int kDetectBatch = 12;   // keeps the parameter block under 4 KB
+struct DetectBatch {
+    DetectParams im[kDetectBatch];   // the shared fields (TS, nL, L, lvl_off) are equal in all
+    int tiles_x[kDetectBatch];
+    int tile0[kDetectBatch + 1];     // prefix sums of the images' tile counts
+    int n;
+};
+
+template <int CH>
+__global__ void __launch_bounds__(kDetectThreads) k_detect_nested_batch(const __grid_constant__ DetectBatch b)
+{
+    const int t = blockIdx.x;
+    int i = 0;
+    while (i + 1 < b.n && t >= b.tile0[i + 1]) ++i;
+    const int lt = t - b.tile0[i];
+    const int by = lt / b.tiles_x[i], bx = lt - by * b.tiles_x[i];
+    detect_tile<CH>(b.im[i], bx, by);
 }
 
 // General path: one CTA per full window of one scale.
@@ -278,6 +307,81 @@ __global__ void k_diag_gray(const uint8_t* rgb, long long n, uint8_t* gray)
 
 }  // namespace
 
+namespace {
+
+// The fast path's tile side: nested scales with Lmax <= 128; TS holds whole
+// 16-byte loads and at most 4096 finest-scale segments.  false: general path.
+bool nested_tile(const ScaleTable& st, int* TS_out)
+{
+    bool nested = st.L[st.nL - 1] <= 128;
+    for (int l = 1; l < st.nL && nested; ++l) nested = st.L[l] % st.L[l - 1] == 0;
+    int TS = st.L[st.nL - 1];
+    if (nested && TS % 16 != 0) {
+        nested = (16 % TS == 0);
+        TS = 16;
+    }
+    if (nested && (long long)TS * TS / st.L[0] > 4096) nested = false;
+    *TS_out = TS;
+    return nested;
+}
+
+// Parameters of one image on the fast path; returns the dynamic shared memory.
+size_t fill_nested(DetectParams& p, const uint8_t* img, int H, int W, int pitch, const ScaleTable& st, int TS,
+                   uint32_t* kp, uint8_t* gray)
+{
+    p.img = img; p.gray = gray; p.kp = kp; p.H = H; p.W = W; p.pitch = pitch; p.TS = TS; p.nL = st.nL;
+    int acc = 0;
+    for (int l = 0; l < st.nL; ++l) {
+        p.L[l] = st.L[l]; p.nwx[l] = st.nwx[l]; p.nwy[l] = st.nwy[l]; p.off[l] = st.off[l];
+        p.lvl_off[l] = acc;
+        acc += (TS / st.L[l]) * (TS / st.L[l]);
+    }
+    for (int l = st.nL; l <= LP_MAX_SCALES; ++l) p.lvl_off[l] = acc;
+    const int nseg = TS * TS / st.L[0];
+    return (size_t)TS * TS + 8u * nseg + 8u * acc;
+}
+
+}  // namespace
+
+cudaError_t launch_detect_batch(const uint8_t* const* imgs, const int* Hs, const int* Ws, const int* pitches, int N,
+                                int ch, const ScaleTable* sts, uint32_t* const* kps, uint8_t* const* grays,
+                                cudaStream_t s, bool* done)
+{
+    *done = false;
+    int TS = 0;
+    if (N < 1 || !nested_tile(sts[0], &TS)) return cudaSuccess;   // the caller detects image by image
+    for (int i0 = 0; i0 < N; i0 += kDetectBatch) {
+        DetectBatch b;
+        b.n = N - i0 < kDetectBatch ? N - i0 : kDetectBatch;
+        b.tile0[0] = 0;
+        size_t smem = 0;
+        for (int k = 0; k < b.n; ++k) {
+            const int i = i0 + k;
+            smem = fill_nested(b.im[k], imgs[i], Hs[i], Ws[i], pitches[i], sts[i], TS, kps[i], grays[i]);
+            b.tiles_x[k] = (Ws[i] + TS - 1) / TS;
+            b.tile0[k + 1] = b.tile0[k] + b.tiles_x[k] * ((Hs[i] + TS - 1) / TS);
+        }
+        if (b.tile0[b.n] == 0) continue;
+        cudaError_t e;
+        if (ch == 1) {
+            if (smem > 48 * 1024 &&
+                (e = cudaFuncSetAttribute(k_detect_nested_batch<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem)) != cudaSuccess)
+                return e;
+            k_detect_nested_batch<1><<<(unsigned)b.tile0[b.n], kDetectThreads, smem, s>>>(b);
+        } else {
+            if (smem > 48 * 1024 &&
+                (e = cudaFuncSetAttribute(k_detect_nested_batch<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem)) != cudaSuccess)
+                return e;
+            k_detect_nested_batch<3><<<(unsigned)b.tile0[b.n], kDetectThreads, smem, s>>>(b);
+        }
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    *done = true;
+    return cudaSuccess;
+}
+
 cudaError_t launch_detect(const uint8_t* img, int H, int W, int pitch, int ch, const ScaleTable& st, double alpha,
                           uint32_t* kp, uint8_t* gray, cudaStream_t s)
 {
@@ -295,27 +399,11 @@ cudaError_t launch_detect(const uint8_t* img, int H, int W, int pitch, int ch, c
         }
         return cudaGetLastError();
     }
-    bool nested = st.L[st.nL - 1] <= 128;
-    for (int l = 1; l < st.nL && nested; ++l) nested = st.L[l] % st.L[l - 1] == 0;
-    int TS = st.L[st.nL - 1];
-    if (nested && TS % 16 != 0) {
-        // a tile must hold whole 16-byte loads: use 16 when every L divides it
-        nested = (16 % TS == 0);
-        TS = 16;
-    }
-    if (nested && (long long)TS * TS / st.L[0] > 4096) nested = false;
+    int TS = 0;
+    const bool nested = nested_tile(st, &TS);
     if (nested) {
         DetectParams p;
-        p.img = img; p.gray = gray; p.kp = kp; p.H = H; p.W = W; p.pitch = pitch; p.TS = TS; p.nL = st.nL;
-        int acc = 0;
-        for (int l = 0; l < st.nL; ++l) {
-            p.L[l] = st.L[l]; p.nwx[l] = st.nwx[l]; p.nwy[l] = st.nwy[l]; p.off[l] = st.off[l];
-            p.lvl_off[l] = acc;
-            acc += (TS / st.L[l]) * (TS / st.L[l]);
-        }
-        for (int l = st.nL; l <= LP_MAX_SCALES; ++l) p.lvl_off[l] = acc;
-        const int nseg = TS * TS / st.L[0];
-        const size_t smem = (size_t)TS * TS + 8u * nseg + 8u * acc;
+        const size_t smem = fill_nested(p, img, H, W, pitch, st, TS, kp, gray);
         dim3 grid((W + TS - 1) / TS, (H + TS - 1) / TS);
         if (ch == 1) {
             if (smem > 48 * 1024) cudaFuncSetAttribute(k_detect_nested<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

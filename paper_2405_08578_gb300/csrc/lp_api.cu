@@ -318,6 +318,43 @@ int lp_detect(lp_ctx* c, const uint8_t* img, int H, int W, int pitch, int channe
     return LP_OK;
 }
 
+int lp_detect_batch(lp_ctx* c, const lp_image* imgs, int N, uint32_t* const* kp_idx, uint8_t* const* gray,
+                    void* stream)
+{
+    if (!c) return LP_ERR_ARG;
+    if (N < 1 || !imgs || !kp_idx || !gray) return fail(c, LP_ERR_ARG, "need N >= 1 images and their outputs");
+    const int ch = imgs[0].channels;
+    for (int i = 0; i < N; ++i) {
+        int r = check_image(c, imgs[i].data, imgs[i].H, imgs[i].W, imgs[i].pitch, imgs[i].channels);
+        if (r) return r;
+        if (imgs[i].channels != ch) return fail(c, LP_ERR_ARG, "images differ in channel count");
+        const int64_t K = lp_num_keypoints(imgs[i].H, imgs[i].W, c->cfg.Ls, c->cfg.nL);
+        if (K > 0 && !kp_idx[i]) return fail(c, LP_ERR_ARG, "null kp_idx[%d]", i);
+        if (kp_idx[i] && !aligned(kp_idx[i], 8)) return fail(c, LP_ERR_ALIGN, "kp_idx[%d] must be 8-byte aligned", i);
+        if (ch == 3 && !gray[i]) return fail(c, LP_ERR_ARG, "RGB input needs gray[%d]", i);
+        if (ch == 3 && (imgs[i].W % 16 == 0) && !aligned(gray[i], 16))
+            return fail(c, LP_ERR_ALIGN, "gray[%d] must be 16-byte aligned", i);
+    }
+    c->last = S(stream);
+    bool done = false;
+    if (c->cfg.alpha == 0.0) {
+        std::vector<lp::ScaleTable> st((size_t)N);
+        std::vector<const uint8_t*> src((size_t)N);
+        std::vector<int> Hs((size_t)N), Ws((size_t)N), ps((size_t)N);
+        for (int i = 0; i < N; ++i) {
+            lp::make_scale_table(c->cfg.Ls, c->cfg.nL, c->cfg.beta0, imgs[i].H, imgs[i].W, &st[i]);
+            src[i] = imgs[i].data; Hs[i] = imgs[i].H; Ws[i] = imgs[i].W; ps[i] = imgs[i].pitch;
+        }
+        LP_CUDA(c, lp::launch_detect_batch(src.data(), Hs.data(), Ws.data(), ps.data(), N, ch, st.data(), kp_idx,
+                                           gray, S(stream), &done));
+    }
+    for (int i = 0; i < N && !done; ++i) {
+        int r = lp_detect(c, imgs[i].data, imgs[i].H, imgs[i].W, imgs[i].pitch, ch, kp_idx[i], gray[i], stream);
+        if (r) return r;
+    }
+    return LP_OK;
+}
+
 int lp_describe(lp_ctx* c, const uint8_t* gray, int H, int W, int gray_pitch, const uint32_t* kp_idx, int64_t K,
                 uint8_t* ori, float* desc, uint16_t* desc_bf16, uint8_t* valid, void* stream)
 {
@@ -672,11 +709,17 @@ int lp_stitch_pairs_ids(lp_ctx* c, const lp_image* imgs, int N, const int32_t* p
 
     auto enqueue = [&]() -> int {
         int rr;
+        {
+            std::vector<uint32_t*> kps((size_t)N);
+            std::vector<uint8_t*> grays((size_t)N);
+            for (int i = 0; i < N; ++i) {
+                kps[i] = (uint32_t*)(base + ib[i].kp);
+                grays[i] = ch == 3 ? base + ib[i].gray : nullptr;
+            }
+            if ((rr = lp_detect_batch(c, imgs, N, kps.data(), grays.data(), stream))) return rr;
+        }
         for (int i = 0; i < N; ++i) {
             uint8_t* g = ch == 3 ? base + ib[i].gray : nullptr;
-            if ((rr = lp_detect(c, imgs[i].data, imgs[i].H, imgs[i].W, imgs[i].pitch, ch, (uint32_t*)(base + ib[i].kp), g,
-                                stream)))
-                return rr;
             const uint8_t* gsrc = ch == 3 ? g : imgs[i].data;
             const int gp = ch == 3 ? imgs[i].W : imgs[i].pitch;
             if ((rr = lp_describe(c, gsrc, imgs[i].H, imgs[i].W, gp, (const uint32_t*)(base + ib[i].kp), ib[i].K,

@@ -42,6 +42,12 @@ struct Fork {
 cudaError_t launch_detect(const uint8_t* img, int H, int W, int pitch, int ch, const ScaleTable& st, double alpha,
                           uint32_t* kp, uint8_t* gray, cudaStream_t s);
 cudaError_t launch_diag_gray(const uint8_t* rgb, int64_t n, uint8_t* gray, cudaStream_t s);
+// N images with the same scales and channels in launches of up to 12 on the
+// fast path; *done = false (nothing launched) when the scales need the general
+// path, which the caller then runs image by image
+cudaError_t launch_detect_batch(const uint8_t* const* imgs, const int* Hs, const int* Ws, const int* pitches, int N,
+                                int ch, const ScaleTable* sts, uint32_t* const* kps, uint8_t* const* grays,
+                                cudaStream_t s, bool* done);
 
 // k_describe.cu
 size_t describe_lut_bytes();

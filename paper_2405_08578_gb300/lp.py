@@ -42,7 +42,8 @@ class lp_config(C.Structure):
 
 
 _lib = None
-SYMBOLS = ["lp_config_default", "lp_create", "lp_destroy", "lp_num_keypoints", "lp_detect", "lp_describe",
+SYMBOLS = ["lp_config_default", "lp_create", "lp_destroy", "lp_num_keypoints", "lp_detect", "lp_detect_batch",
+           "lp_describe",
            "lp_match", "lp_compact", "lp_ransac", "lp_ransac_static", "lp_stitch_pair", "lp_stitch_pair_host", "lp_stitch_pairs", "lp_stitch_pairs_ids", "lp_sync_status",
            "lp_last_error", "lp_diag_last_rescans", "lp_diag_orient_bins", "lp_diag_orient_weights", "lp_diag_philox", "lp_diag_gray",
            "lp_mlp_create", "lp_mlp_destroy", "lp_mlp_set_params", "lp_mlp_get_params", "lp_mlp_get_state", "lp_mlp_save",
@@ -73,6 +74,7 @@ def load(build_if_missing: bool = True):
         "lp_destroy": (i32, [P]),
         "lp_num_keypoints": (i64, [i32, i32, P, i32]),
         "lp_detect": (i32, [P, P, i32, i32, i32, i32, P, P, P]),
+        "lp_detect_batch": (i32, [P, P, i32, P, P, P]),
         "lp_describe": (i32, [P, P, i32, i32, i32, P, i64, P, P, P, P, P]),
         "lp_match": (i32, [P, P, P, P, i64, P, P, P, i64, P, P, P, P]),
         "lp_compact": (i32, [P, P, i32, P, i32, P, i64, P, P, P, P]),
@@ -184,6 +186,15 @@ class Context:
     def lp_detect(self, img, H, W, pitch, channels, kp_idx, gray=None, stream=None):
         self._chk(self.lib.lp_detect(self.h, _ptr(img), H, W, pitch, channels, _ptr(kp_idx), _ptr(gray),
                                      _stream(stream)), "lp_detect")
+
+    def lp_detect_batch(self, images, kps, grays=None, stream=None):
+        """images: list of (device uint8 tensor, H, W, pitch, channels); kps: int32
+        device tensors, one per image; grays: uint8 device tensors (RGB) or None."""
+        n = len(images)
+        arr = (lp_image * n)(*[lp_image(_ptr(t), H, W, p, ch) for (t, H, W, p, ch) in images])
+        kp_arr = (C.c_void_p * n)(*[_ptr(k) for k in kps])
+        g_arr = (C.c_void_p * n)(*[_ptr(g) if g is not None else None for g in (grays or [None] * n)])
+        self._chk(self.lib.lp_detect_batch(self.h, arr, n, kp_arr, g_arr, _stream(stream)), "lp_detect_batch")
 
     def lp_describe(self, gray, H, W, gray_pitch, kp_idx, K, ori, desc, desc_bf16, valid, stream=None):
         self._chk(self.lib.lp_describe(self.h, _ptr(gray), H, W, gray_pitch, _ptr(kp_idx), K, _ptr(ori), _ptr(desc),

@@ -212,3 +212,38 @@ def test_degenerate_pairs_report_no_model():
     v = valid.cpu().numpy()
     assert v[4] == 1 and v.sum() == 1 and int(n_in[4]) == n
     assert not HM[[0, 1, 2, 3, 5]].any()
+
+
+@pytest.mark.parametrize("case", ["gray14", "rgb5", "nonnested", "alpha"])
+def test_detect_batch_equals_single_images(case):
+    """lp_detect_batch (images sharing launches) gives every image exactly the
+    peaks and intensity of lp_detect: more images than one launch takes, mixed
+    sizes, RGB widths that are not multiples of 16, and the configurations that
+    detect image by image."""
+    rng = np.random.default_rng(len(case))
+    Ls, alpha, ch, n = (16, 32, 64), 0.0, 1, 5
+    if case == "gray14":
+        n = 14
+    elif case == "rgb5":
+        ch = 3
+    elif case == "nonnested":
+        Ls = (12, 20)
+    else:
+        alpha = 1e-4
+    shapes = [(int(rng.integers(70, 400)), int(rng.integers(70, 500))) for _ in range(n)]
+    imgs = [rng.integers(0, 256, size=s + ((3,) if ch == 3 else ())).astype(np.uint8) for s in shapes]
+    ctx = lp.Context(Ls=Ls, alpha=alpha)
+    bufs = [lp.pitched_device(im) for im in imgs]
+    images = [(b, im.shape[0], im.shape[1], p, ch) for (b, p), im in zip(bufs, imgs)]
+    Ks = [lp.lp_num_keypoints(im.shape[0], im.shape[1], Ls) for im in imgs]
+    kps = [torch.full((max(K, 1),), -1, dtype=torch.int32, device="cuda") for K in Ks]
+    grays = [torch.zeros(im.shape[0] * im.shape[1] + 16, dtype=torch.uint8, device="cuda") for im in imgs] \
+        if ch == 3 else None
+    ctx.lp_detect_batch(images, kps, grays)
+    torch.cuda.synchronize()
+    assert ctx.lp_sync_status() == 0
+    for i, im in enumerate(imgs):
+        kp1, g1 = G.detect(ctx, im)
+        assert np.array_equal(G.host(kps[i])[:Ks[i]].astype(np.uint32), kp1), (case, i, im.shape)
+        if ch == 3:
+            assert np.array_equal(G.host(grays[i])[:im.shape[0] * im.shape[1]].reshape(im.shape[:2]), g1)
