@@ -44,17 +44,21 @@ __device__ __forceinline__ uint8_t byte_of(const uint4& v, int i)
     return (uint8_t)(w >> (8 * (i & 3)));
 }
 
-// 16 interleaved RGB pixels (48 bytes) -> 16 intensities.
+// 16 interleaved RGB pixels (48 bytes) -> 16 intensities.  Pixel p's bytes
+// are gathered into one word (R, G, B, x) and 299 R + 587 G + 114 B + 500 is
+// formed exactly with two byte dot products: 299 = 256 + 43, 587 = 512 + 75,
+// so the sum is dp(43, 75, 114, 0) + 500 + 256 dp(1, 2, 0, 0).
 __device__ __forceinline__ uint4 gray16(const uint4& c0, const uint4& c1, const uint4& c2)
 {
+    const uint32_t w[12] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w, c2.x, c2.y, c2.z, c2.w};
     uint32_t o[4] = {0, 0, 0, 0};
 #pragma unroll
     for (int p = 0; p < 16; ++p) {
-        int b = 3 * p;
-        uint8_t r = b < 16 ? byte_of(c0, b) : b < 32 ? byte_of(c1, b - 16) : byte_of(c2, b - 32);
-        uint8_t g = b + 1 < 16 ? byte_of(c0, b + 1) : b + 1 < 32 ? byte_of(c1, b + 1 - 16) : byte_of(c2, b + 1 - 32);
-        uint8_t bl = b + 2 < 16 ? byte_of(c0, b + 2) : b + 2 < 32 ? byte_of(c1, b + 2 - 16) : byte_of(c2, b + 2 - 32);
-        o[p >> 2] |= (uint32_t)rgb2gray(r, g, bl) << (8 * (p & 3));
+        const int i = (3 * p) >> 2, j = (3 * p) & 3;
+        const uint32_t rgb = __byte_perm(w[i], i + 1 < 12 ? w[i + 1] : w[i],
+                                         (uint32_t)(j | ((j + 1) << 4) | ((j + 2) << 8) | ((j + 3) << 12)));
+        const uint32_t s = __dp4a(rgb, 0x00724B2Bu, 500u) + (__dp4a(rgb, 0x00000201u, 0u) << 8);
+        o[p >> 2] |= (s / 1000u) << (8 * (p & 3));
     }
     return make_uint4(o[0], o[1], o[2], o[3]);
 }
