@@ -8,9 +8,11 @@
 //
 // Fast path (nested scales, Lmax <= 128): one CTA per Lmax x Lmax tile.  The
 // tile is streamed from HBM once with 16-byte loads (RGB converted to
-// intensity on the fly and written back as the dense intensity image), staged
-// in shared memory, reduced to per-row segment extrema of the finest window,
-// then to finest-window extrema, then each coarser level combines its children.
+// intensity on the fly and written back as the dense intensity image).  When
+// the finest side is a multiple of 16, each thread reduces its 16 pixels to
+// their extreme keys in registers; otherwise the tile is staged in shared
+// memory and reduced per row segment of the finest window.  Finest-window
+// extrema follow, then each coarser level combines its children.
 // General path: one CTA per window per scale (any L set, any Lmax).
 #include "lp_internal.cuh"
 
@@ -63,6 +65,40 @@ __device__ __forceinline__ uint4 gray16(const uint4& c0, const uint4& c1, const 
     return make_uint4(o[0], o[1], o[2], o[3]);
 }
 
+__device__ __forceinline__ uint32_t max_u16x2(uint32_t a, uint32_t b)
+{
+    uint32_t d;
+    asm("max.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+
+__device__ __forceinline__ uint32_t min_u16x2(uint32_t a, uint32_t b)
+{
+    uint32_t d;
+    asm("min.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+
+// Extreme keys of 16 consecutive pixels of one row (raster index of the first:
+// base).  Within the group, (intensity << 4) | position orders pixels exactly
+// as the key does, and two such 12-bit values share a word, so the maximum
+// and minimum run as packed 16-bit pairs.
+__device__ __forceinline__ void group_keys(const uint4& v, uint32_t base, uint32_t& kmax, uint32_t& kmin)
+{
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+    uint32_t mx = 0u, mn = 0xFFFFFFFFu;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const uint32_t lo = __byte_perm(w[k], 0u, 0x4140u) * 16u + ((4u * k) | ((4u * k + 1u) << 16));
+        const uint32_t hi = __byte_perm(w[k], 0u, 0x4342u) * 16u + ((4u * k + 2u) | ((4u * k + 3u) << 16));
+        mx = max_u16x2(mx, max_u16x2(lo, hi));
+        mn = min_u16x2(mn, min_u16x2(lo, hi));
+    }
+    const uint32_t M = max(mx & 0xFFFFu, mx >> 16), m = min(mn & 0xFFFFu, mn >> 16);
+    kmax = ((M >> 4) << 24) | (base + (M & 15u));
+    kmin = ((m >> 4) << 24) | (base + (m & 15u));
+}
+
 // One TS x TS tile (tile column bx, tile row by) of one image.
 template <int CH>
 __device__ __forceinline__ void detect_tile(const DetectParams& p, int bx, int by)
@@ -70,16 +106,19 @@ __device__ __forceinline__ void detect_tile(const DetectParams& p, int bx, int b
     extern __shared__ __align__(16) uint8_t sm[];
     const int TS = p.TS;
     const int L0 = p.L[0];
-    const int spr = TS / L0;                 // segments per tile row
+    const bool fused = (L0 & 15) == 0;       // 16-pixel groups reduced in registers
+    const int spr = fused ? TS / 16 : TS / L0;   // segments per tile row
+    const int gpw = fused ? L0 / 16 : 1;         // segments per finest-window row
     const int nseg = TS * spr;
     uint8_t* tile = sm;
-    uint32_t* smx = reinterpret_cast<uint32_t*>(sm + TS * TS);
+    uint32_t* smx = reinterpret_cast<uint32_t*>(sm + (fused ? 0 : TS * TS));
     uint32_t* smn = smx + nseg;
     uint32_t* wmx = smn + nseg;
     uint32_t* wmn = wmx + p.lvl_off[p.nL];
 
     const int tx0 = bx * TS, ty0 = by * TS;
     const int rows = min(TS, p.H - ty0), cols = min(TS, p.W - tx0);
+    const int Hf = (p.H / L0) * L0 - ty0, Wf = (p.W / L0) * L0 - tx0;   // full finest windows
 
     // ---- stream the tile once: 16 pixels per 16-byte (gray) or 48-byte (RGB) load
     const int gpr = TS / 16;
@@ -108,13 +147,20 @@ __device__ __forceinline__ void detect_tile(const DetectParams& p, int bx, int b
                 }
             }
         }
-        *reinterpret_cast<uint4*>(tile + r * TS + c) = v;
+        if (fused) {
+            uint32_t kmax = 0u, kmin = 0xFFFFFFFFu;
+            if (r < Hf && c < Wf)
+                group_keys(v, (uint32_t)(ty0 + r) * (uint32_t)p.W + (uint32_t)(tx0 + c), kmax, kmin);
+            smx[g] = kmax;
+            smn[g] = kmin;
+        } else {
+            *reinterpret_cast<uint4*>(tile + r * TS + c) = v;
+        }
     }
     __syncthreads();
 
     // ---- finest scale: extrema of every L0-pixel row segment of a full window
-    const int Hf = (p.H / L0) * L0 - ty0, Wf = (p.W / L0) * L0 - tx0;
-    for (int s = threadIdx.x; s < nseg; s += kDetectThreads) {
+    for (int s = threadIdx.x; s < (fused ? 0 : nseg); s += kDetectThreads) {
         const int r = s / spr, c0 = (s - r * spr) * L0;
         uint32_t kmax = 0u, kmin = 0xFFFFFFFFu;
         if (r < Hf && c0 < Wf) {
@@ -137,11 +183,12 @@ __device__ __forceinline__ void detect_tile(const DetectParams& p, int bx, int b
         for (int w = threadIdx.x; w < n0 * n0; w += kDetectThreads) {
             const int wr = w / n0, wc = w - wr * n0;
             uint32_t kmax = 0u, kmin = 0xFFFFFFFFu;
-            for (int i = 0; i < L0; ++i) {
-                const int s = (wr * L0 + i) * spr + wc;
-                kmax = max(kmax, smx[s]);
-                kmin = min(kmin, smn[s]);
-            }
+            for (int i = 0; i < L0; ++i)
+                for (int j = 0; j < gpw; ++j) {
+                    const int s = (wr * L0 + i) * spr + wc * gpw + j;
+                    kmax = max(kmax, smx[s]);
+                    kmin = min(kmin, smn[s]);
+                }
             wmx[w] = kmax;
             wmn[w] = kmin;
             const int gy = ty0 / L0 + wr, gx = tx0 / L0 + wc;
@@ -341,6 +388,7 @@ size_t fill_nested(DetectParams& p, const uint8_t* img, int H, int W, int pitch,
         acc += (TS / st.L[l]) * (TS / st.L[l]);
     }
     for (int l = st.nL; l <= LP_MAX_SCALES; ++l) p.lvl_off[l] = acc;
+    if (st.L[0] % 16 == 0) return 8u * (size_t)(TS * TS / 16) + 8u * acc;   // no staged tile
     const int nseg = TS * TS / st.L[0];
     return (size_t)TS * TS + 8u * nseg + 8u * acc;
 }

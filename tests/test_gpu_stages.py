@@ -70,6 +70,7 @@ DETECT_CASES = [
     ((40, 56), (8, 16), 1), ((37, 61), (4, 8, 16), 1), ((100, 130), (16, 32), 3), ((96, 112), (5, 7), 1),
     ((33, 45), (2, 4, 8), 3), ((240, 320), (16, 32, 64, 128), 1), ((150, 300), (128, 256), 1),
     ((480, 640), (8, 16, 32), 1), ((12, 12), (16,), 1), ((31, 17), (16,), 3),
+    ((200, 330), (32, 64), 3), ((130, 270), (48, 96), 1), ((97, 161), (16, 48), 3),
 ]
 
 
