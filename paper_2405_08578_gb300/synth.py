@@ -209,6 +209,24 @@ def table2_pair(name: str, seed: int = 0) -> tuple[Pair, tuple[int, ...]]:
     return make_pair(h, w, H, seed), Ls
 
 
+def uneven_pairs(n: int = 64, seed: int = 2, long_lo: int = 480, long_hi: int = 4096, rgb: bool = False) -> list[Pair]:
+    """Independent pairs of uneven sizes: long side U[long_lo, long_hi] (integer),
+    aspect U[4/3, 16/9] (landscape), and B through a similarity drawn like the
+    2688x1600 pair's (rotation U[-10, 10] deg, scale U[0.9, 1.1], x shift 0.6 w
+    of either sign, y shift U[-0.05, 0.05] h: about 40% overlap)."""
+    rng = np.random.default_rng(40_000 + seed)
+    out = []
+    for q in range(n):
+        w = int(rng.integers(long_lo, long_hi + 1))
+        h = max(16, int(round(w / rng.uniform(4.0 / 3.0, 16.0 / 9.0))))
+        th = rng.uniform(-10.0, 10.0)
+        sc = rng.uniform(0.9, 1.1)
+        tx = 0.6 * w * (1 if rng.uniform() < 0.5 else -1)
+        ty = rng.uniform(-0.05, 0.05) * h
+        out.append(make_pair(h, w, similarity(th, sc, tx, ty, w / 2.0, h / 2.0), 1000 * seed + q, rgb=rgb))
+    return out
+
+
 def small_pair(h: int, w: int, seed: int, theta_deg: float = 4.0, scale: float = 1.03,
                shift: float = 0.3, rgb: bool = False) -> Pair:
     """Small pair for parity tests: similarity about the centre, x shift = shift * w."""

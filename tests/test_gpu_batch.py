@@ -186,6 +186,46 @@ def test_stitch_pairs_uneven_sizes_equal_single_pairs(rgb):
         assert int(valid[1]) == 1 and int(valid[4]) == 1   # (s1.A, s1.B) and (s2.A, s2.B)
 
 
+def test_uneven_pairs_batch_equals_single_pairs_and_truth():
+    """Independent pairs of uneven sizes and aspect ratios in one explicit pair
+    list (the 64-pair uneven workload's shape, here at long sides 480..1024):
+    every entry equals lp_stitch_pair with the same pair id, every pair is
+    registered within 1 px of its true homography, and two of them agree with
+    the oracle's H within 0.5 px."""
+    import oracle
+    ps = synth.uneven_pairs(12, seed=2, long_hi=1024)
+    Ls = synth.PAIR_2688x1600_LS
+    imgs = [im for p in ps for im in (p.A, p.B)]
+    bufs = [lp.pitched_device(im) for im in imgs]
+    images = [(b, im.shape[0], im.shape[1], pt, 1) for (b, pt), im in zip(bufs, imgs)]
+    ctx = lp.Context(Ls=Ls, precision=lp.PREC_BF16, seed=0)
+    P = len(ps)
+    HM, n_in, valid, M = _outputs(P)
+    ctx.lp_stitch_pairs(images, HM, n_in, valid, pairs=[(2 * q, 2 * q + 1) for q in range(P)], M_out=M,
+                        pair_ids=list(range(P)))
+    torch.cuda.synchronize()
+    assert int(valid.sum()) == P
+    HMh = HM.cpu().numpy().reshape(P, 3, 3)
+    for q, p in enumerate(ps):
+        h, w = p.A.shape
+        (ba, pa), (bb, pb_) = bufs[2 * q], bufs[2 * q + 1]
+        H1 = torch.zeros(9, dtype=torch.float64, device="cuda")
+        n1 = torch.zeros(1, dtype=torch.int32, device="cuda")
+        M1 = torch.zeros(1, dtype=torch.int32, device="cuda")
+        ctx.lp_stitch_pair(ba, h, w, pa, bb, h, w, pb_, 1, q, H1, n1, M1)
+        torch.cuda.synchronize()
+        assert torch.equal(HM[q], H1) and int(n_in[q]) == int(n1) and int(M[q]) == int(M1), q
+        ys, xs = np.mgrid[0:h:max(1, h // 12), 0:w:max(1, w // 12)]
+        pts = np.c_[xs.ravel(), ys.ravel()].astype(np.float64)
+        tb = G.proj(p.H, pts)
+        ov = (tb[:, 0] >= 0) & (tb[:, 0] < w) & (tb[:, 1] >= 0) & (tb[:, 1] < h)
+        assert np.abs(G.proj(HMh[q], pts[ov]) - tb[ov]).max() < 1.0, q
+        if q in (2, 10):
+            o = oracle.stitch_pair(p.A, p.B, Ls)
+            assert abs(int(n_in[q]) - o["n_in"]) <= 3, q
+            assert np.abs(G.proj(HMh[q], pts[ov]) - G.proj(o["H"], pts[ov])).max() < 0.5, q
+
+
 def test_degenerate_pairs_report_no_model():
     """Edge cases of the whole path: an image smaller than every window (no
     feature points), a flat image (no valid descriptor), and both in a batch:
