@@ -20,6 +20,18 @@
  *   or_philox4x32_10   pinned (published known-answer vectors)
  *   or_dlt4 / or_refit pinned (known homographies, numpy SVD)
  *   or_ransac          pinned (synthetic inliers + outliers)
+ *   or_border_valid    pinned (closed-form radius, padding invariance)
+ *   or_rigid_fit / or_ransac_model (Eq. 8)
+ *                      pinned (exact rotations, independent least squares,
+ *                      special case of the homography model)
+ *   or_mlp_*           pinned (finite differences, closed-form networks,
+ *                      Adam first step, hand-computed features)
+ *   or_guided_* / or_ransac_prior*
+ *                      pinned (exact integer weights, chi-square of draws,
+ *                      closed-form stop bound, uniform fallback)
+ *   or_mosaic_plan / or_mosaic_render
+ *                      pinned (star and chain graphs, identity and shifted
+ *                      renders)
  */
 #include "lp_oracle.h"
 
