@@ -47,3 +47,19 @@ def test_binding_refuses_host_tensors():
     from paper_2405_08578_gb300 import lp
     with pytest.raises(ValueError):
         lp._ptr(torch.zeros(4))
+
+
+def test_num_keypoints_equals_oracle_over_a_sweep():
+    # the library's host scale table against the oracle's count: every full
+    # window of every scale contributes its maximum and its minimum
+    import numpy as np
+    import oracle
+    from paper_2405_08578_gb300 import lp
+    rng = np.random.default_rng(11)
+    sets = [(8, 16, 32), (16, 32, 64, 128), (32, 40), (100, 128), (256, 512), (5, 7, 12), (3,), (64, 160)]
+    for _ in range(60):
+        H, W = (int(v) for v in rng.integers(1, 3000, size=2))
+        Ls = sets[int(rng.integers(len(sets)))]
+        want = oracle.num_keypoints(H, W, Ls)
+        got = lp.lp_num_keypoints(H, W, list(Ls))
+        assert got == want, (H, W, Ls)
