@@ -120,41 +120,64 @@ __device__ __forceinline__ void detect_tile(const DetectParams& p, int bx, int b
     const int rows = min(TS, p.H - ty0), cols = min(TS, p.W - tx0);
     const int Hf = (p.H / L0) * L0 - ty0, Wf = (p.W / L0) * L0 - tx0;   // full finest windows
 
-    // ---- stream the tile once: 16 pixels per 16-byte (gray) or 48-byte (RGB) load
-    const int gpr = TS / 16;
-    for (int g = threadIdx.x; g < TS * gpr; g += kDetectThreads) {
-        const int r = g / gpr, c = (g - r * gpr) * 16;
-        uint4 v = make_uint4(0, 0, 0, 0);
-        if (r < rows && c < cols) {
-            const uint8_t* row = p.img + (size_t)(ty0 + r) * p.pitch;
-            const int x = tx0 + c;
-            if (CH == 1) {
-                v = __ldg(reinterpret_cast<const uint4*>(row + x));
-            } else {
-                // chunk q holds bytes [3x + 16q, 3x + 16q + 16); it lies inside the
-                // pitch whenever its first byte is a pixel byte of this row
-                const uint4* src = reinterpret_cast<const uint4*>(row + 3 * (size_t)x);
-                uint4 c0 = __ldg(src);
-                uint4 c1 = (3 * x + 16 < 3 * p.W) ? __ldg(src + 1) : make_uint4(0, 0, 0, 0);
-                uint4 c2 = (3 * x + 32 < 3 * p.W) ? __ldg(src + 2) : make_uint4(0, 0, 0, 0);
-                v = gray16(c0, c1, c2);
-                uint8_t* gout = p.gray + (size_t)(ty0 + r) * p.W + x;
-                if ((p.W & 15) == 0) {
-                    *reinterpret_cast<uint4*>(gout) = v;
+    // ---- stream the tile once: 16 pixels per 16-byte (gray) or 48-byte (RGB)
+    // load.  Each pass issues the loads of a thread's next kGroups 16-pixel
+    // groups before it uses the first, so two DRAM round trips overlap.
+    constexpr int kGroups = 2;
+    const int gpr = TS / 16, ng = TS * gpr;
+    for (int g0 = 0; g0 < ng; g0 += kGroups * kDetectThreads) {
+        uint4 raw[kGroups][CH];
+#pragma unroll
+        for (int u = 0; u < kGroups; ++u) {
+            const int g = g0 + threadIdx.x + u * kDetectThreads;
+            const int r = g / gpr, c = (g - r * gpr) * 16;
+#pragma unroll
+            for (int q = 0; q < CH; ++q) raw[u][q] = make_uint4(0, 0, 0, 0);
+            if (g < ng && r < rows && c < cols) {
+                const uint8_t* row = p.img + (size_t)(ty0 + r) * p.pitch;
+                const int x = tx0 + c;
+                if (CH == 1) {
+                    raw[u][0] = __ldg(reinterpret_cast<const uint4*>(row + x));
                 } else {
-                    const int n = min(16, p.W - x);
-                    for (int i = 0; i < n; ++i) gout[i] = byte_of(v, i);
+                    // chunk q holds bytes [3x + 16q, 3x + 16q + 16); it lies inside the
+                    // pitch whenever its first byte is a pixel byte of this row
+                    const uint4* src = reinterpret_cast<const uint4*>(row + 3 * (size_t)x);
+                    raw[u][0] = __ldg(src);
+                    if (3 * x + 16 < 3 * p.W) raw[u][CH > 1 ? 1 : 0] = __ldg(src + 1);
+                    if (3 * x + 32 < 3 * p.W) raw[u][CH > 2 ? 2 : 0] = __ldg(src + 2);
                 }
             }
         }
-        if (fused) {
-            uint32_t kmax = 0u, kmin = 0xFFFFFFFFu;
-            if (r < Hf && c < Wf)
-                group_keys(v, (uint32_t)(ty0 + r) * (uint32_t)p.W + (uint32_t)(tx0 + c), kmax, kmin);
-            smx[g] = kmax;
-            smn[g] = kmin;
-        } else {
-            *reinterpret_cast<uint4*>(tile + r * TS + c) = v;
+#pragma unroll
+        for (int u = 0; u < kGroups; ++u) {
+            const int g = g0 + threadIdx.x + u * kDetectThreads;
+            if (g >= ng) break;
+            const int r = g / gpr, c = (g - r * gpr) * 16;
+            uint4 v = make_uint4(0, 0, 0, 0);
+            if (r < rows && c < cols) {
+                if (CH == 1) {
+                    v = raw[u][0];
+                } else {
+                    const int x = tx0 + c;
+                    v = gray16(raw[u][0], raw[u][CH > 1 ? 1 : 0], raw[u][CH > 2 ? 2 : 0]);
+                    uint8_t* gout = p.gray + (size_t)(ty0 + r) * p.W + x;
+                    if ((p.W & 15) == 0) {
+                        *reinterpret_cast<uint4*>(gout) = v;
+                    } else {
+                        const int n = min(16, p.W - x);
+                        for (int i = 0; i < n; ++i) gout[i] = byte_of(v, i);
+                    }
+                }
+            }
+            if (fused) {
+                uint32_t kmax = 0u, kmin = 0xFFFFFFFFu;
+                if (r < Hf && c < Wf)
+                    group_keys(v, (uint32_t)(ty0 + r) * (uint32_t)p.W + (uint32_t)(tx0 + c), kmax, kmin);
+                smx[g] = kmax;
+                smn[g] = kmin;
+            } else {
+                *reinterpret_cast<uint4*>(tile + r * TS + c) = v;
+            }
         }
     }
     __syncthreads();
