@@ -180,3 +180,24 @@ def test_describe_upright_equals_integer_eq5():
     h = np.minimum(h, 0.2)
     h /= np.linalg.norm(h)
     assert np.abs(d[0] - h).max() < 1e-12
+
+
+def test_describe_offset_and_gain_invariance():
+    # Eq. 5 takes intensity differences only: a constant offset leaves every
+    # gradient, the orientation histogram and the descriptor unchanged.  A gain
+    # of 2 doubles every gradient (exactly, bilinear taps included), and the L2
+    # normalisation removes it.
+    rng = np.random.default_rng(12)
+    g = rng.integers(0, 100, size=(70, 80)).astype(np.uint8)
+    idx = (rng.integers(20, 50, 40) * 80 + rng.integers(20, 60, 40)).astype(np.uint32)
+    ws = rng.integers(1, 5, 40).astype(np.int32)
+    ori = oracle.orient(g, idx, ws)
+    assert np.array_equal(oracle.orient(g + 37, idx, ws), ori)
+    d, v = oracle.describe(g, idx, ws, ori)
+    d1, v1 = oracle.describe(g + 37, idx, ws, ori)
+    d2, v2 = oracle.describe(g * 2, idx, ws, ori)
+    assert v.all() and np.array_equal(v, v1) and np.array_equal(v, v2)
+    assert np.abs(d1 - d).max() < 1e-12 and np.abs(d2 - d).max() < 1e-12
+    # the invariance is not vacuous: another orientation changes the descriptors
+    d3, _ = oracle.describe(g, idx, ws, ((ori.astype(int) + 5) % 36).astype(np.uint8))
+    assert np.abs(d3 - d).max(axis=1).min() > 1e-3

@@ -115,3 +115,17 @@ def test_region_ws_closed_form():
         # more than the rounding of w_s
         for L, w in zip(Ls, ws):
             assert 4 * w <= L + 2
+
+
+def test_detect_invariant_under_strictly_increasing_intensity_maps():
+    # Eq. 1-2 peaks (alpha -> 0+) depend on the order of the intensities and on
+    # raster position only, so a strictly increasing map keeps every peak; a map
+    # that merges two levels creates new ties and moves some peaks
+    rng = np.random.default_rng(13)
+    g = rng.integers(0, 128, size=(45, 70)).astype(np.uint8)
+    lut = np.concatenate([[0], np.cumsum(rng.integers(1, 3, 127))]).astype(np.uint8)
+    assert (np.diff(lut.astype(int)) > 0).all()
+    for Ls in ((4, 8), (5, 7, 12), (3,)):
+        assert np.array_equal(oracle.detect(lut[g], Ls), oracle.detect(g, Ls))
+    merged = (g // 2).astype(np.uint8)
+    assert not np.array_equal(oracle.detect(merged, (4, 8)), oracle.detect(g, (4, 8)))
