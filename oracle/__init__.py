@@ -10,6 +10,7 @@ all-pairs homography matrix H_M); each C function cites its passage.
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes as C
 import os
 import subprocess
@@ -38,52 +39,78 @@ def build(force: bool = False) -> str:
 def lib():
     global _lib
     if _lib is None:
-        build()
-        L = C.CDLL(_LIB)
-        P = C.c_void_p
-        i32, i64, u32, f64 = C.c_int, C.c_int64, C.c_uint32, C.c_double
-        sig = {
-            "or_gray_from_rgb": (i32, [P, i32, i32, i32, P]),
-            "or_num_keypoints": (i64, [i32, i32, P, i32]),
-            "or_detect": (i32, [P, i32, i32, i32, P, i32, f64, P]),
-            "or_region_ws": (i32, [P, i32, f64, i32, P]),
-            "or_orient_bin": (i32, [i32, i32]),
-            "or_orient_weight": (u32, [i32]),
-            "or_orient": (i32, [P, i32, i32, i32, P, P, i64, P, P]),
-            "or_describe": (i32, [P, i32, i32, i32, P, P, P, i64, P, P]),
-            "or_match": (i32, [P, P, i64, P, P, i64, f64, f64, P, i64, P, P, P, P, P]),
-            "or_philox4x32_10": (None, [P, P, P]),
-            "or_ransac_sample": (i32, [i64, C.c_uint64, u32, i32, P]),
-            "or_dlt4": (i32, [P, P, P]),
-            "or_refit": (i32, [P, P, i64, P]),
-            "or_eig_sym": (i32, [i32, P, P, P]),
-            "or_score": (i64, [P, P, i64, f64, P]),
-            "or_ransac": (i32, [P, i64, i32, f64, C.c_uint64, u32, P, P, P, P, P, P]),
-            "or_ransac_model": (i32, [P, i64, i32, i32, f64, C.c_uint64, u32, P, P, P, P, P, P]),
-            "or_ransac_sample_k": (i32, [i64, C.c_uint64, u32, i32, i32, P]),
-            "or_rigid_fit": (i32, [P, P, i64, P]),
-            "or_model_sample_size": (i32, [i32]),
-            "or_mlp_features": (i32, [i64, P, P, P, i32, P, P, P, i32, i32, i32, i32, P]),
-            "or_mlp_forward": (i32, [P, P, i64, P, P]),
-            "or_mlp_loss_grad": (i32, [P, P, P, i64, P, P]),
-            "or_mlp_adam": (i32, [P, P, P, P, i32, i32, f64, f64, f64, f64]),
-            "or_guided_weights": (i32, [P, i64, P]),
-            "or_ransac_sample_guided": (i32, [i64, P, C.c_uint64, u32, i32, P]),
-            "or_ransac_prior": (i32, [P, i64, P, i32, i32, f64, C.c_uint64, u32, P, P, P, P, P, P]),
-            "or_ransac_prior_model": (i32, [P, i64, i32, P, i32, i32, f64, C.c_uint64, u32, P, P, P, P, P, P]),
-            "or_guided_stop": (i32, [C.c_uint64, C.c_uint64, i32]),
-            "or_guided_stop_k": (i32, [C.c_uint64, C.c_uint64, i32, i32]),
-            "or_ransac_sample_guided_k": (i32, [i64, P, C.c_uint64, u32, i32, i32, P]),
-            "or_mosaic_plan": (i32, [i32, P, i32, P, P, P, P, P, P, P, P, P]),
-            "or_border_valid": (i32, [P, P, i64, i32, i32, P]),
-            "or_mosaic_render": (i32, [i32, P, P, P, P, i32, P, P, i32, i32, P, P]),
-        }
-        for name, (res, args) in sig.items():
-            f = getattr(L, name)
-            f.restype = res
-            f.argtypes = args
-        _lib = L
+        _lib = _load(build())
     return _lib
+
+
+@contextlib.contextmanager
+def use_library(path: str):
+    """Run every oracle function against another build of the C source (the
+    mutation tests compile copies of lp_oracle.c with one planted mistake)."""
+    global _lib
+    saved = lib()
+    _lib = _load(path)
+    try:
+        yield
+    finally:
+        _lib = saved
+
+
+def compile_variant(src_text: str, out_path: str) -> str:
+    """Compile C source text (a copy of lp_oracle.c) with the oracle's flags."""
+    c_path = out_path + ".c"
+    with open(c_path, "w") as f:
+        f.write(src_text)
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fno-fast-math", "-ffp-contract=off",
+                           "-I", _HERE, "-o", out_path, c_path, "-lm"])
+    return out_path
+
+
+def _load(path: str):
+    L = C.CDLL(path)
+    P = C.c_void_p
+    i32, i64, u32, f64 = C.c_int, C.c_int64, C.c_uint32, C.c_double
+    sig = {
+        "or_gray_from_rgb": (i32, [P, i32, i32, i32, P]),
+        "or_num_keypoints": (i64, [i32, i32, P, i32]),
+        "or_detect": (i32, [P, i32, i32, i32, P, i32, f64, P]),
+        "or_region_ws": (i32, [P, i32, f64, i32, P]),
+        "or_orient_bin": (i32, [i32, i32]),
+        "or_orient_weight": (u32, [i32]),
+        "or_orient": (i32, [P, i32, i32, i32, P, P, i64, P, P]),
+        "or_describe": (i32, [P, i32, i32, i32, P, P, P, i64, P, P]),
+        "or_match": (i32, [P, P, i64, P, P, i64, f64, f64, P, i64, P, P, P, P, P]),
+        "or_philox4x32_10": (None, [P, P, P]),
+        "or_ransac_sample": (i32, [i64, C.c_uint64, u32, i32, P]),
+        "or_dlt4": (i32, [P, P, P]),
+        "or_refit": (i32, [P, P, i64, P]),
+        "or_eig_sym": (i32, [i32, P, P, P]),
+        "or_score": (i64, [P, P, i64, f64, P]),
+        "or_ransac": (i32, [P, i64, i32, f64, C.c_uint64, u32, P, P, P, P, P, P]),
+        "or_ransac_model": (i32, [P, i64, i32, i32, f64, C.c_uint64, u32, P, P, P, P, P, P]),
+        "or_ransac_sample_k": (i32, [i64, C.c_uint64, u32, i32, i32, P]),
+        "or_rigid_fit": (i32, [P, P, i64, P]),
+        "or_model_sample_size": (i32, [i32]),
+        "or_mlp_features": (i32, [i64, P, P, P, i32, P, P, P, i32, i32, i32, i32, P]),
+        "or_mlp_forward": (i32, [P, P, i64, P, P]),
+        "or_mlp_loss_grad": (i32, [P, P, P, i64, P, P]),
+        "or_mlp_adam": (i32, [P, P, P, P, i32, i32, f64, f64, f64, f64]),
+        "or_guided_weights": (i32, [P, i64, P]),
+        "or_ransac_sample_guided": (i32, [i64, P, C.c_uint64, u32, i32, P]),
+        "or_ransac_prior": (i32, [P, i64, P, i32, i32, f64, C.c_uint64, u32, P, P, P, P, P, P]),
+        "or_ransac_prior_model": (i32, [P, i64, i32, P, i32, i32, f64, C.c_uint64, u32, P, P, P, P, P, P]),
+        "or_guided_stop": (i32, [C.c_uint64, C.c_uint64, i32]),
+        "or_guided_stop_k": (i32, [C.c_uint64, C.c_uint64, i32, i32]),
+        "or_ransac_sample_guided_k": (i32, [i64, P, C.c_uint64, u32, i32, i32, P]),
+        "or_mosaic_plan": (i32, [i32, P, i32, P, P, P, P, P, P, P, P, P]),
+        "or_border_valid": (i32, [P, P, i64, i32, i32, P]),
+        "or_mosaic_render": (i32, [i32, P, P, P, P, i32, P, P, i32, i32, P, P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    return L
 
 
 def _p(a: np.ndarray | None):

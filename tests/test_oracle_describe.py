@@ -201,3 +201,17 @@ def test_describe_offset_and_gain_invariance():
     # the invariance is not vacuous: another orientation changes the descriptors
     d3, _ = oracle.describe(g, idx, ws, ((ori.astype(int) + 5) % 36).astype(np.uint8))
     assert np.abs(d3 - d).max(axis=1).min() > 1e-3
+
+
+def test_orient_exact_tie_lowest_bin_wins():
+    # I = 3 max(r - y0, c - x0): above the diagonal every gradient is (6, 0)
+    # (bin 0), below it (0, 6) (bin 9), on it (3, 3) (bin 4).  The window is
+    # symmetric about the diagonal, so bins 0 and 9 tie exactly and the lower
+    # bin must win.
+    H = W = 40
+    yy, xx = np.mgrid[0:H, 0:W]
+    g = (100 + 3 * np.maximum(yy - 20, xx - 20)).astype(np.uint8)
+    ori, hist = oracle.orient(g, _kp(H, W, 20, 20), np.array([3], np.int32), want_hist=True)
+    h = hist[0]
+    assert h[0] == h[9] > h[4] > 0 and h.sum() == h[0] + h[9] + h[4]
+    assert ori[0] == 0

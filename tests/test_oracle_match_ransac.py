@@ -52,6 +52,21 @@ def test_match_permutation_and_rows_subset():
     del inv
 
 
+def test_match_exact_tie_takes_the_lowest_index():
+    # duplicated candidates are equally near: the lowest index is the nearest
+    # neighbour (ratio test off), and the ratio test rejects the tie
+    rng = np.random.default_rng(6)
+    A = _unit(rng, 12)
+    B = _unit(rng, 30)
+    B[7] = A[4] + 0.02 * rng.standard_normal(128)
+    B[19] = B[7]
+    v = np.ones(30, np.uint8)
+    m, d1, d2, j1, j2 = oracle.match(A, np.ones(12, np.uint8), B, v, ratio=0.0)
+    assert m[4] == 7 and j1[4] == 7 and j2[4] == 19 and d1[4] == d2[4]
+    m, *_ = oracle.match(A, np.ones(12, np.uint8), B, v, ratio=0.8)
+    assert m[4] == -1
+
+
 def test_match_delta_s_and_too_few_valid():
     rng = np.random.default_rng(2)
     A = _unit(rng, 10)
@@ -170,6 +185,12 @@ def test_score_counts_and_w_nonpositive():
     pts = np.array([[0.0, 0, 5, 0], [0, 0, 9, 0], [-150, 0, 0, 0], [10, 0, 15 / 1.1, 0]])
     n, m = oracle.score(H, pts, 3.0)
     assert m.tolist() == [1, 0, 0, 1] and n == 2       # x = -150 gives w = -0.5 -> outlier
+    # an error of exactly the threshold is not an inlier (e < thresh)
+    n, m = oracle.score(H, np.array([[0.0, 0, 8, 0], [0, 0, 7.999, 0]]), 3.0)
+    assert m.tolist() == [0, 1] and n == 1
+    # x = -200 gives w = -1 and projects exactly onto (195, 0): still not an inlier
+    n, m = oracle.score(H, np.array([[-200.0, 0, 195, 0]]), 3.0)
+    assert m.tolist() == [0] and n == 0
 
 
 def test_ransac_recovers_known_h_with_outliers():

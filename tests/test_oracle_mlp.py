@@ -64,6 +64,9 @@ def test_features_by_hand():
     assert np.allclose(f[0], [0.4, 0.2, 4 / 7, 20 / 180, 10 / 640, 20 / 480, 300 / 640, 40 / 480])
     # 0 - 35 bins = -350 deg -> wraps to +10 deg
     assert np.allclose(f[1], [0.5, 0.3, 1.0, 10 / 180, 639 / 640, 479 / 480, 0, 0])
+    # a half turn lands on the closed end of [-180, 180): -180 deg
+    f = oracle.mlp_features([0.2], [0.5], [32], 128, [0], [18], pts[:1], 640, 480, 640, 480)
+    assert np.allclose(f[0, :4], [0.4, 0.2, 5 / 7, -1.0])
 
 
 def test_guided_weights_are_exact_integers():

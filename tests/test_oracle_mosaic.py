@@ -47,6 +47,17 @@ def test_chain_graph_rounds_and_references():
         assert np.allclose(np.linalg.inv(plan["G"][2]) @ plan["G"][k], np.linalg.inv(place[2]) @ place[k], atol=1e-9)
 
 
+def test_degree_tie_takes_the_lowest_index():
+    # a 4-cycle: every image has degree 2, so image 0 is the first reference and
+    # places 1 and 3; image 2 follows in round 1 as its own reference
+    n = 4
+    place = [T(9 * k, 4 * k) for k in range(n)]
+    pairs, HM, valid = _hm_for(n, place, {(0, 1), (1, 2), (2, 3), (0, 3)})
+    plan = oracle.mosaic_plan(n, pairs, HM, valid, [(30, 30)] * n)
+    assert plan["round"].tolist() == [0, 0, 1, 0]
+    assert plan["ref"].tolist() == [0, 0, 2, 0]
+
+
 def test_disconnected_image_stays_unplaced_and_canvas_box():
     n = 3
     place = [T(0, 0), T(25, 10), T(500, 500)]
