@@ -168,6 +168,52 @@ MUTANTS = [
     ("feature_angle_wrap",
      "if (dth >= 180.0) dth -= 360.0;", "if (dth > 180.0) dth -= 360.0;",
      [ML.test_features_by_hand]),
+    ("orient_window_one_sided",
+     "for (int u = -R; u <= R; ++u)", "for (int u = -R; u < R; ++u)",
+     [DS.test_orient_rotation_90_histogram_roll, DS.test_orient_exact_tie_lowest_bin_wins]),
+    ("bilinear_wrong_fraction",
+     "double top = v00 + fc * (v01 - v00);", "double top = v00 + fr * (v01 - v00);",
+     [DS.test_describe_ramp_closed_forms, DS.test_describe_rotation_90_invariant]),
+    ("describe_second_normalisation_dropped",
+     "for (int j = 0; j < 128; ++j) out[j] /= n2;", "for (int j = 0; j < 128; ++j) out[j] /= 1.0;",
+     [DS.test_describe_unit_norm_and_invalid, DS.test_describe_ramp_closed_forms]),
+    ("match_distance_not_rooted",
+     "d1[q] = sqrt(b1);", "d1[q] = b1;",
+     [MR.test_match_vs_numpy_bruteforce]),
+    ("sample_duplicates_kept",
+     "(uint64_t)M) >> 32);\n        int dup = 0;\n        for (int q = 0; q < n; ++q) dup |= idx[q] == i;",
+     "(uint64_t)M) >> 32);\n        int dup = 0;\n        for (int q = 0; q < n; ++q) dup |= 0;",
+     [MR.test_ransac_sample_distinct_uniform]),
+    ("jacobi_rotation_sign",
+     "a[k][p] = c * akp - s * akq;", "a[k][p] = c * akp + s * akq;",
+     [MR.test_eig_sym_vs_numpy, MR.test_refit_equals_numpy_svd]),
+    ("rigid_centroid_variable",
+     "cxb = sxb / n, cyb = syb / n;", "cxb = sxa / n, cyb = syb / n;",
+     [_rigid_exact]),
+    ("mlp_first_bias_dropped",
+     "double s = b1[i];", "double s = 0;",
+     [ML.test_closed_form_networks, ML.test_loss_gradient_matches_central_differences]),
+    ("mlp_distance_ratio_inverted",
+     "f[0] = d2[i] > 0 ? d1[i] / d2[i] : 1.0;", "f[0] = d1[i] > 0 ? d2[i] / d1[i] : 1.0;",
+     [ML.test_features_by_hand]),
+    ("adam_second_moment_not_squared",
+     "v[i] = b2 * v[i] + (1 - b2) * grad[i] * grad[i];", "v[i] = b2 * v[i] + (1 - b2) * fabs(grad[i]);",
+     [ML.test_adam_first_step_closed_form]),
+    ("guided_weight_truncated",
+     "acc += (uint64_t)floor(65536.0 * p + 0.5);", "acc += (uint64_t)floor(65536.0 * p);",
+     [ML.test_guided_weights_are_exact_integers]),
+    ("border_right_edge_loose",
+     "x + P > W - 1 || y + P > H - 1", "x + P > W || y + P > H - 1",
+     [_border]),
+    ("region_default_beta_inverted",
+     "beta0 = sqrt((double)Lmin / (double)Lmax) / (double)d;", "beta0 = sqrt((double)Lmax / (double)Lmin) / (double)d;",
+     [D.test_region_ws_closed_form]),
+    ("render_mean_truncated",
+     "(uint8_t)floor(sum[c] / n + 0.5) : 0;", "(uint8_t)floor(sum[c] / n) : 0;",
+     [MO.test_render_half_pixel_shift_is_the_mean_of_neighbours, MO.test_render_identity_and_integer_overlap]),
+    ("render_vertical_fraction",
+     "sum[c] += top + fv * (bot - top);", "sum[c] += top + fu * (bot - top);",
+     [MO.test_render_half_pixel_shift_is_the_mean_of_neighbours, MO.test_render_identity_and_integer_overlap]),
     ("mosaic_reference_tie_takes_last",
      "if (ref < 0 || deg[i] > deg[ref]) { ref = i; via = link; }",
      "if (ref < 0 || deg[i] >= deg[ref]) { ref = i; via = link; }",
