@@ -9,19 +9,24 @@
 // window of every row whose second-best value is well below 1 (its exact value
 // is +inf, so it can never be ranked).
 //
-// k_match_tc<pass> (persistent, one CTA per SM, clusters of two, 10 warps):
-//   warp 0    TMA producer: per work unit a 128-row A block (2 x 16 KB boxes,
-//             128-byte swizzle), then 256-row B tiles into a 3-stage ring;
-//             each CTA of the cluster loads one K-half (32 KB) of every tile
-//             and multicasts it to both CTAs (one L2 read per cluster).
-//   warp 1    allocates all 512 TMEM columns; one lane issues
-//             tcgen05.mma.cta_group::1.kind::f16 (M = 128, N = 256, K = 16,
-//             BF16 x BF16 -> FP32), 8 per B tile, into one of two 256-column
-//             TMEM accumulator buffers; tcgen05.commit releases the B stage
-//             (in both CTAs) and hands the buffer to the epilogue.
+// k_match_tc<pass> (persistent, one CTA per SM, clusters of two CTAs that
+// run one pair MMA, 10 warps):
+//   warp 0    TMA producer in each CTA: per work unit its own 128-row A block
+//             (2 x 16 KB boxes, 128-byte swizzle), then its own 128-row half
+//             of every 256-row B tile (2 x 16 KB) into a 6-stage ring.  The
+//             copies of both CTAs complete on the even CTA's barriers (plain
+//             per-CTA loads, nothing shared between the CTAs' copies).
+//   warp 1    both CTAs allocate all 512 TMEM columns as a pair; in the even
+//             CTA one lane issues tcgen05.mma.cta_group::2.kind::f16
+//             (M = 256: 128 rows from each CTA, N = 256: 128 B rows from
+//             each CTA, K = 16, BF16 x BF16 -> FP32), 8 per B tile, into one
+//             of two 256-column TMEM accumulator buffers of each CTA;
+//             tcgen05.commit releases the B stage and hands the buffer to
+//             the epilogue, once into each CTA's barrier.
 //   warps 2-9 epilogue: each thread owns one A row and one 128-column half of
-//             every tile; it loads the half row from TMEM (tcgen05.ld
-//             32x32b.x32), returns the buffer, then works on registers.
+//             every tile; it loads the half row from its CTA's TMEM
+//             (tcgen05.ld 32x32b.x32), returns the buffer (an arrival on the
+//             even CTA's barrier), then works on registers.
 //             Pass 1 (every third tile): the two largest 32-column chunk
 //             maxima of D per (split, half, row), written as v.  Pass 2 (all
 //             tiles): every column with v <= T (a three-input max tree per
@@ -60,14 +65,26 @@ __global__ void k_match_finish(const float4* part, int S, long long NA, const fl
 namespace {
 
 constexpr int kRowsPerUnit = 128;       // one M = 128 row block per CTA
-constexpr int kTileN = 256;             // B rows per tile (MMA N)
-constexpr int kTmemBufs = 2;            // accumulator buffers of kTileN columns (512 TMEM columns)
-constexpr int kStages = 3;              // B ring depth
+constexpr int kTileN = 256;             // B rows per tile (128 staged by each CTA of the pair)
+#ifndef LP_TC_MMA_N
+#define LP_TC_MMA_N 256
+#endif
+constexpr int kMmaN = LP_TC_MMA_N;      // MMA N: kMmaN / 2 B rows from each CTA per instruction
+constexpr int kSub = kTileN / kMmaN;    // MMA groups (accumulator buffers) per tile
+constexpr int kTmemBufs = 512 / kMmaN;  // accumulator buffers of kMmaN columns (512 TMEM columns)
+constexpr int kChunks = kMmaN / 64;     // 32-column chunks per epilogue thread and buffer
+static_assert(kMmaN == 128 || kMmaN == 256, "MMA N");
+#ifndef LP_TC_STAGES
+#define LP_TC_STAGES 6
+#endif
+constexpr int kStages = LP_TC_STAGES;   // B ring depth (half tiles)
 constexpr int kThreadsTC = 320;         // 10 warps
 constexpr int kEpiWarps = 8;
 constexpr uint32_t kABytes = kRowsPerUnit * 128 * 2;   // 32 KB
-constexpr uint32_t kBBytes = kTileN * 128 * 2;         // 64 KB per stage
-// 32 KB + 3 x 64 KB + 2 KB = 231,424 bytes of the 232,448 a CTA may opt into
+constexpr int kHalfN = kTileN / 2;      // B rows a CTA stages per tile
+constexpr uint32_t kBBytes = kHalfN * 128 * 2;         // 32 KB per stage (this CTA's half tile)
+// 32 KB + 6 x 32 KB + 2 KB = 231,424 bytes of the 232,448 a CTA may opt into
+static_assert(kABytes + kStages * kBBytes + 2048 <= 232448, "shared memory");
 constexpr uint32_t kSmemTC = kABytes + kStages * kBBytes + 1024 /*barriers*/ + 1024 /*align slack*/;
 #ifndef LP_CAND_CAPACITY
 #define LP_CAND_CAPACITY 96
@@ -122,22 +139,43 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
 
-__device__ __forceinline__ void mbar_arrive(uint32_t bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-
 __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
 {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
+#if LP_TC_WAIT_CLUSTER
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+#else
         "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+#endif
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
         : "r"(bar), "r"(parity)
         : "memory");
     return ok != 0;
+}
+
+// Shared::cluster address of the object at shared::cta address `a` in the
+// cluster's CTA `rank`.
+__device__ __forceinline__ uint32_t cluster_addr(uint32_t a, uint32_t rank)
+{
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    return r;
+}
+
+// Arrive on an mbarrier of any CTA of the cluster.  The default (CTA-scope)
+// release: what the arrival publishes is the completion of this warp's TMEM
+// loads, which tcgen05.fence::before_thread_sync orders before it; a
+// cluster-scope release would also wait for the thread's global writes.
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cbar)
+{
+#if LP_TC_ARRIVE_REL_CLUSTER
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cbar) : "memory");
+#else
+    asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(cbar) : "memory");
+#endif
 }
 
 __device__ __forceinline__ uint64_t globaltimer()
@@ -165,23 +203,15 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
     }
 }
 
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar)
+// 2-D tile load into this CTA's shared memory; its complete_tx goes to the
+// mbarrier at shared::cluster address `cbar`, which may be the even CTA's of
+// the pair (.cta_group::2).
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t cbar)
 {
     asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
-        ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
-        : "memory");
-}
-
-// The same load delivered to the same shared-memory offset (data and
-// complete_tx on the mbarrier at the same offset) in every CTA of `mask`.
-__device__ __forceinline__ void tma_load_2d_mc(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar,
-                                               uint16_t mask)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster "
-        "[%0], [%1, {%2, %3}], [%4], %5;"
-        ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar), "h"(mask)
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.cta_group::2 "
+        "[%0], [%1, {%2, %3}], [%4];"
+        ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(cbar)
         : "memory");
 }
 
@@ -217,31 +247,25 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr)
 }
 
 // Instruction descriptor, kind::f16: D = FP32, A = B = BF16, both K-major,
-// N = 128, M = 128.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTileN >> 3) << 17) | ((128u >> 4) << 24);
+// N = kMmaN, M = 256 (the CTA pair's 2 x 128 rows).
+constexpr uint32_t kIdesc =
+    (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kMmaN >> 3) << 17) | ((uint32_t)(2 * kRowsPerUnit >> 4) << 24);
 
 __device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t accumulate)
 {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.u32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}"
         ::"r"(dtmem), "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate)
         : "memory");
 }
 
-__device__ __forceinline__ void mma_commit(uint32_t bar)
+// Arrive (when this thread's MMAs complete) on the mbarrier at shared::cluster
+// address `cbar` (either CTA of the pair).
+__device__ __forceinline__ void mma_commit(uint32_t cbar)
 {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
-}
-
-// Arrive (when this thread's MMAs complete) on the mbarrier at offset `bar`
-// of every CTA in `mask`.
-__device__ __forceinline__ void mma_commit_mc(uint32_t bar, uint16_t mask)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;"
-                 ::"r"(bar), "h"(mask)
-                 : "memory");
+    asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(cbar) : "memory");
 }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -290,11 +314,11 @@ struct TcParams {
     int32_t* status;
 };
 
-// Unit u = (pair of 256-row blocks, column split), processed by one cluster of
-// two CTAs: CTA rank r takes row block rp = 2 * pair + r, and both stream the
-// same B tiles, each loading one K-half of every tile for both (multicast).
-// Consecutive units share a row block and each cluster takes a contiguous run
-// of units, so the A blocks are usually reused.
+// Unit u = (pair of 128-row blocks, column split), processed by one cluster
+// of two CTAs: CTA rank r holds row block rp = 2 * pair + r and rows
+// [128 r, 128 r + 128) of every 256-row B tile of the split.  Consecutive
+// units share a row block and each cluster takes a contiguous run of units,
+// so the A blocks are usually reused.
 __device__ __forceinline__ void unit_range(const TcParams& p, int u, uint32_t crank, int& rp, int& split,
                                            long long& c0, int& ntiles)
 {
@@ -336,19 +360,20 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
     uint8_t* sA = smem;
     uint8_t* sB = smem + kABytes;
     uint64_t* bars = reinterpret_cast<uint64_t*>(sB + kStages * kBBytes);
-    // barrier slots
-    uint64_t* full = bars;                 // [kStages]
-    uint64_t* empty = bars + kStages;      // [kStages]
-    uint64_t* tfull = bars + 2 * kStages;  // [kTmemBufs]
-    uint64_t* tempty = tfull + kTmemBufs;  // [kTmemBufs]
-    uint64_t* afull = tempty + kTmemBufs;  // [1]
-    uint64_t* aempty = afull + 1;          // [1]
-    uint64_t* drain = aempty + 1;          // [1]
+    // barrier slots (the same offsets in both CTAs of the pair)
+    uint64_t* full = bars;                 // [kStages]  even CTA: both halves of stage s landed
+    uint64_t* empty = bars + kStages;      // [kStages]  this CTA's half of stage s is free
+    uint64_t* tfull = bars + 2 * kStages;  // [kTmemBufs] this CTA's accumulator buffer b is ready
+    uint64_t* tempty = tfull + kTmemBufs;  // [kTmemBufs] even CTA: both CTAs' epilogues drained buffer b
+    uint64_t* afull = tempty + kTmemBufs;  // [1] even CTA: both A blocks landed
+    uint64_t* aempty = afull + 1;          // [1] this CTA's A block is free
+    uint64_t* drain = aempty + 1;          // [1] even CTA: every issued MMA completed
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t crank = cluster_ctarank();
+    const bool leader = crank == 0;
     const int cid = (int)blockIdx.x >> 1, ncl = (int)gridDim.x >> 1;
     const int U = p.nrp * p.S;
     const int per = U / ncl, rem = U % ncl;
@@ -357,12 +382,12 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
-            mbar_init(smem_u32(&full[s]), 1);
-            mbar_init(smem_u32(&empty[s]), 2);   // both CTAs' MMAs release a stage
+            mbar_init(smem_u32(&full[s]), 1);    // the even CTA's expect_tx arrival
+            mbar_init(smem_u32(&empty[s]), 1);   // one MMA commit
         }
         for (int b = 0; b < kTmemBufs; ++b) {
             mbar_init(smem_u32(&tfull[b]), 1);
-            mbar_init(smem_u32(&tempty[b]), kEpiWarps);
+            mbar_init(smem_u32(&tempty[b]), 2 * kEpiWarps);   // the epilogue warps of both CTAs
         }
         mbar_init(smem_u32(afull), 1);
         mbar_init(smem_u32(aempty), 1);
@@ -373,13 +398,14 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
         tma_prefetch_desc(&tmB);
     }
     if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tmem_slot))
+        // one warp of each CTA of the pair allocates, collectively
+        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tmem_slot))
                      : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
     }
     tc_fence_before();
     __syncthreads();
-    cluster_sync();   // the peer's barriers exist before any multicast reaches them
+    cluster_sync();   // both CTAs' barriers exist before any copy, commit or arrival reaches them
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
@@ -391,8 +417,9 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
             int armed[kStages];
             int a_armed = -1;
             for (int s = 0; s < kStages; ++s) armed[s] = -1;
-            bool ok = true;
+            bool ok = true, issued = false;
             int prev_rp = -1;
+            const uint32_t c_afull = cluster_addr(smem_u32(afull), 0);
             for (int u = u_begin; u < u_end && ok; ++u) {
                 int rp, split, ntiles;
                 long long c0;
@@ -401,10 +428,11 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
                 if (rp != prev_rp) {
                     ok = mbar_wait(smem_u32(aempty), (v & 1) ^ 1, abort_flag, p.status);
                     if (!ok) break;
-                    mbar_expect_tx(smem_u32(afull), kABytes);
-                    tma_load_2d(smem_u32(sA), &tmA, 0, rp * kRowsPerUnit, smem_u32(afull));
-                    tma_load_2d(smem_u32(sA + kABytes / 2), &tmA, 64, rp * kRowsPerUnit, smem_u32(afull));
+                    if (leader) mbar_expect_tx(smem_u32(afull), 2 * kABytes);
+                    tma_load_2d(smem_u32(sA), &tmA, 0, rp * kRowsPerUnit, c_afull);
+                    tma_load_2d(smem_u32(sA + kABytes / 2), &tmA, 64, rp * kRowsPerUnit, c_afull);
                     a_armed = v;
+                    issued = true;
                     ++v;
                     prev_rp = rp;
                 }
@@ -414,36 +442,46 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
                     ok = mbar_wait(smem_u32(&empty[s]), (k & 1) ^ 1, abort_flag, p.status);
                     if (!ok) break;
                     uint8_t* dst = sB + s * kBBytes;
-                    const int y = (int)(c0 + (long long)t * p.tstride * kTileN);
-                    mbar_expect_tx(smem_u32(&full[s]), kBBytes);
-                    if (crank == 0)
-                        tma_load_2d_mc(smem_u32(dst), &tmB, 0, y, smem_u32(&full[s]), 3);
-                    else
-                        tma_load_2d_mc(smem_u32(dst + kBBytes / 2), &tmB, 64, y, smem_u32(&full[s]), 3);
+                    const int y = (int)(c0 + (long long)t * p.tstride * kTileN) + (int)crank * kHalfN;
+                    if (leader) mbar_expect_tx(smem_u32(&full[s]), 2 * kBBytes);
+                    const uint32_t c_full = cluster_addr(smem_u32(&full[s]), 0);
+                    tma_load_2d(smem_u32(dst), &tmB, 0, y, c_full);
+                    tma_load_2d(smem_u32(dst + kBBytes / 2), &tmB, 64, y, c_full);
                     armed[s] = (int)k;
+                    issued = true;
                 }
             }
             if (!ok) {
-                // drain: wait (bounded) for the copies this thread issued to land
-                for (int s = 0; s < kStages; ++s) {
-                    if (armed[s] < 0) continue;
-                    const uint64_t t0 = globaltimer();
-                    while (!mbar_try(smem_u32(&full[s]), (uint32_t)armed[s] & 1u) && globaltimer() - t0 < 200000000ull) {
+                if (leader) {
+                    // drain: wait (bounded) for the stages this CTA armed to land
+                    for (int s = 0; s < kStages; ++s) {
+                        if (armed[s] < 0) continue;
+                        const uint64_t t0 = globaltimer();
+                        while (!mbar_try(smem_u32(&full[s]), (uint32_t)armed[s] & 1u) &&
+                               globaltimer() - t0 < 200000000ull) {
+                        }
                     }
-                }
-                if (a_armed >= 0) {
+                    if (a_armed >= 0) {
+                        const uint64_t t0 = globaltimer();
+                        while (!mbar_try(smem_u32(afull), (uint32_t)a_armed & 1u) && globaltimer() - t0 < 200000000ull) {
+                        }
+                    }
+                } else if (issued) {
+                    // this CTA's copies complete on the even CTA's barriers: give
+                    // the ones in flight a fixed 2 ms to land
                     const uint64_t t0 = globaltimer();
-                    while (!mbar_try(smem_u32(afull), (uint32_t)a_armed & 1u) && globaltimer() - t0 < 200000000ull) {
+                    while (globaltimer() - t0 < 2000000ull) {
                     }
                 }
             }
         }
     } else if (warp == 1) {
-        // ---------------------------------------------------------- MMA issuer
-        if (lane == 0) {
+        // ---------------------------------------------------------- MMA issuer (even CTA)
+        if (lane == 0 && leader) {
             // descriptors of the fixed buffers; an operand at byte offset o from
             // a base is the base descriptor + (o >> 4) (the 14-bit start field
-            // never carries: shared addresses stay below 256 KB)
+            // never carries: shared addresses stay below 256 KB).  The same
+            // offsets address the odd CTA's rows and B half.
             const uint64_t dA0 = sdesc(smem_u32(sA)), dB0 = sdesc(smem_u32(sB));
             long long n = 0;
             int v = 0;
@@ -455,41 +493,53 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
                 unit_range(p, u, crank, rp, split, c0, ntiles);
                 if (ntiles == 0) continue;
                 if (rp != prev_rp) {
-                    // release the previous A block once its MMAs are done, then
-                    // wait for the new one
-                    if (v > 0) mma_commit(smem_u32(aempty));
+                    // release the previous A blocks once their MMAs are done, then
+                    // wait for the new ones
+                    if (v > 0) {
+                        mma_commit(cluster_addr(smem_u32(aempty), 0));
+                        mma_commit(cluster_addr(smem_u32(aempty), 1));
+                    }
                     ok = mbar_wait(smem_u32(afull), v & 1, abort_flag, p.status);
                     ++v;
                     prev_rp = rp;
                     if (!ok) break;
                     tc_fence_after();
                 }
-                for (int t = 0; t < ntiles; ++t, ++n) {
+                for (int t = 0; t < ntiles && ok; ++t, ++n) {
                     const int s = (int)(n % kStages);
                     const uint32_t k = (uint32_t)(n / kStages);
-                    const int b = (int)(n % kTmemBufs);
-                    const uint32_t kb = (uint32_t)(n / kTmemBufs);
-                    ok = mbar_wait(smem_u32(&tempty[b]), (kb & 1) ^ 1, abort_flag, p.status);
-                    if (!ok) break;
                     ok = mbar_wait(smem_u32(&full[s]), k & 1, abort_flag, p.status);
                     if (!ok) break;
-                    tc_fence_after();
                     const uint64_t dB = dB0 + (uint64_t)((s * kBBytes) >> 4);
-                    const uint32_t d = tmem + (uint32_t)(b * kTileN);
+                    // sub-tile st: B rows [st N/2, st N/2 + N/2) of each CTA's half tile
 #pragma unroll
-                    for (int h = 0; h < 2; ++h)
+                    for (int st = 0; st < kSub; ++st) {
+                        const long long nn = n * kSub + st;
+                        const int b = (int)(nn % kTmemBufs);
+                        const uint32_t kb = (uint32_t)(nn / kTmemBufs);
+                        ok = mbar_wait(smem_u32(&tempty[b]), (kb & 1) ^ 1, abort_flag, p.status);
+                        if (!ok) break;
+                        tc_fence_after();
+                        const uint32_t d = tmem + (uint32_t)(b * kMmaN);
 #pragma unroll
-                        for (int kk = 0; kk < 4; ++kk) {
-                            const uint64_t ad = dA0 + (uint64_t)((h * (kABytes / 2) + kk * 32) >> 4);
-                            const uint64_t bd = dB + (uint64_t)((h * (kBBytes / 2) + kk * 32) >> 4);
-                            mma_bf16(d, ad, bd, (h | kk) ? 1u : 0u);
-                        }
-                    mma_commit_mc(smem_u32(&empty[s]), 3);
-                    mma_commit(smem_u32(&tfull[b]));
+                        for (int h = 0; h < 2; ++h)
+#pragma unroll
+                            for (int kk = 0; kk < 4; ++kk) {
+                                const uint64_t ad = dA0 + (uint64_t)((h * (kABytes / 2) + kk * 32) >> 4);
+                                const uint64_t bd =
+                                    dB + (uint64_t)((h * (kBBytes / 2) + st * (kMmaN / 2) * 128 + kk * 32) >> 4);
+                                mma_bf16(d, ad, bd, (h | kk) ? 1u : 0u);
+                            }
+                        mma_commit(cluster_addr(smem_u32(&tfull[b]), 0));
+                        mma_commit(cluster_addr(smem_u32(&tfull[b]), 1));
+                    }
+                    if (!ok) break;
+                    mma_commit(cluster_addr(smem_u32(&empty[s]), 0));
+                    mma_commit(cluster_addr(smem_u32(&empty[s]), 1));
                 }
             }
             // wait (bounded) for every MMA this thread issued before TMEM is freed
-            mma_commit(smem_u32(drain));
+            mma_commit(cluster_addr(smem_u32(drain), 0));
             const uint64_t t0 = globaltimer();
             while (!mbar_try(smem_u32(drain), 0) && globaltimer() - t0 < 2000000000ull) {
             }
@@ -519,66 +569,69 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
             // pass 2: v~ = 1 - 2 D <= T  <=>  D >= (1 - T) / 2 (1e-6 lower: rounding of TD)
             const float TD = (kPass == 2 && live) ? 0.5f * (1.f - window_top(p.thr[row])) - 1e-6f : INFINITY;
             int nc = 0, cj0 = 0, cj1 = 0, cj2 = 0, cj3 = 0;
-            for (int t = 0; t < ntiles; ++t, ++n) {
-                const int b = (int)(n % kTmemBufs);
-                const uint32_t kb = (uint32_t)(n / kTmemBufs);
-                ok = mbar_wait(smem_u32(&tfull[b]), kb & 1, abort_flag, p.status);
-                if (!ok) break;
-                tc_fence_after();
-                const long long cbase = c0 + (long long)t * p.tstride * kTileN + half * 128;
-                const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * kTileN + half * 128);
-                // the whole tile row in registers, then the buffer goes back to the MMA
-                uint32_t r0[32], r1[32], r2[32], r3[32];
-                tmem_ld32(tbase, r0);
-                tmem_ld32(tbase + 32, r1);
-                tmem_ld32(tbase + 64, r2);
-                tmem_ld32(tbase + 96, r3);
-                tmem_wait(r0);
-                tmem_wait(r1);
-                tmem_wait(r2);
-                tmem_wait(r3);
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(smem_u32(&tempty[b]));
+            for (int t = 0; t < ntiles && ok; ++t, ++n) {
+#pragma unroll 1
+                for (int st = 0; st < kSub; ++st) {
+                    const long long nn = n * kSub + st;
+                    const int b = (int)(nn % kTmemBufs);
+                    const uint32_t kb = (uint32_t)(nn / kTmemBufs);
+                    ok = mbar_wait(smem_u32(&tfull[b]), kb & 1, abort_flag, p.status);
+                    if (!ok) break;
+                    tc_fence_after();
+                    // accumulator columns [half N/2, half N/2 + N/2) hold B rows
+                    // st N/2 + [0, N/2) of CTA `half`'s half tile: tile columns
+                    // 128 half + st N/2 + [0, N/2)
+                    const long long cbase = c0 + (long long)t * p.tstride * kTileN + half * 128 + st * (kMmaN / 2);
+                    const uint32_t tbase =
+                        tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * kMmaN + half * (kMmaN / 2));
+                    // the thread's accumulator row in registers, then the buffer goes back to the MMA
+                    uint32_t r[kChunks][32];
 #pragma unroll
-                for (int ch = 0; ch < 4; ++ch) {
-                    const uint32_t (&cur)[32] = ch == 0 ? r0 : ch == 1 ? r1 : ch == 2 ? r2 : r3;
-                    float dv[32];
+                    for (int ch = 0; ch < kChunks; ++ch) tmem_ld32(tbase + 32 * ch, r[ch]);
 #pragma unroll
-                    for (int i = 0; i < 32; ++i) dv[i] = __uint_as_float(cur[i]);
-                    const long long j0 = cbase + ch * 32;
-                    if (j0 + 32 > c1) {   // columns past the split or past NB (zero-filled rows)
+                    for (int ch = 0; ch < kChunks; ++ch) tmem_wait(r[ch]);
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive_cluster(cluster_addr(smem_u32(&tempty[b]), 0));
 #pragma unroll
-                        for (int i = 0; i < 32; ++i) dv[i] = j0 + i < c1 ? dv[i] : -INFINITY;
-                    }
-                    float gx[4];
+                    for (int ch = 0; ch < kChunks; ++ch) {
+                        float dv[32];
 #pragma unroll
-                    for (int g = 0; g < 4; ++g)
-                        gx[g] = max3f(max3f(dv[8 * g + 0], dv[8 * g + 1], dv[8 * g + 2]),
-                                      max3f(dv[8 * g + 3], dv[8 * g + 4], dv[8 * g + 5]),
-                                      fmaxf(dv[8 * g + 6], dv[8 * g + 7]));
-                    const float cmax = max3f(gx[0], gx[1], fmaxf(gx[2], gx[3]));
-                    if (kPass == 1) {
-                        const float lo = fminf(d1, cmax);
-                        d1 = fmaxf(d1, cmax);
-                        d2 = fmaxf(d2, lo);
-                    } else {
-                        const bool trig = cmax >= TD;
-                        if (__any_sync(0xFFFFFFFFu, trig)) {
-                            // bit i: column j0 + i qualifies; then one short loop over the bits
-                            uint32_t m = 0;
+                        for (int i = 0; i < 32; ++i) dv[i] = __uint_as_float(r[ch][i]);
+                        const long long j0 = cbase + ch * 32;
+                        if (j0 + 32 > c1) {   // columns past the split or past NB (zero-filled rows)
 #pragma unroll
-                            for (int i = 0; i < 32; ++i) m |= (dv[i] >= TD ? 1u : 0u) << i;
-                            while (m) {
-                                const int j = (int)j0 + __ffs(m) - 1;
-                                m &= m - 1;
-                                cj0 = nc == 0 ? j : cj0;
-                                cj1 = nc == 1 ? j : cj1;
-                                cj2 = nc == 2 ? j : cj2;
-                                cj3 = nc == 3 ? j : cj3;
-                                if (++nc == 4) {
-                                    flush_cands(p.ncand, p.cand, row, 4, cj0, cj1, cj2, cj3);
-                                    nc = 0;
+                            for (int i = 0; i < 32; ++i) dv[i] = j0 + i < c1 ? dv[i] : -INFINITY;
+                        }
+                        float gx[4];
+#pragma unroll
+                        for (int g = 0; g < 4; ++g)
+                            gx[g] = max3f(max3f(dv[8 * g + 0], dv[8 * g + 1], dv[8 * g + 2]),
+                                          max3f(dv[8 * g + 3], dv[8 * g + 4], dv[8 * g + 5]),
+                                          fmaxf(dv[8 * g + 6], dv[8 * g + 7]));
+                        const float cmax = max3f(gx[0], gx[1], fmaxf(gx[2], gx[3]));
+                        if (kPass == 1) {
+                            const float lo = fminf(d1, cmax);
+                            d1 = fmaxf(d1, cmax);
+                            d2 = fmaxf(d2, lo);
+                        } else {
+                            const bool trig = cmax >= TD;
+                            if (__any_sync(0xFFFFFFFFu, trig)) {
+                                // bit i: column j0 + i qualifies; then one short loop over the bits
+                                uint32_t m = 0;
+#pragma unroll
+                                for (int i = 0; i < 32; ++i) m |= (dv[i] >= TD ? 1u : 0u) << i;
+                                while (m) {
+                                    const int j = (int)j0 + __ffs(m) - 1;
+                                    m &= m - 1;
+                                    cj0 = nc == 0 ? j : cj0;
+                                    cj1 = nc == 1 ? j : cj1;
+                                    cj2 = nc == 2 ? j : cj2;
+                                    cj3 = nc == 3 ? j : cj3;
+                                    if (++nc == 4) {
+                                        flush_cands(p.ncand, p.cand, row, 4, cj0, cj1, cj2, cj3);
+                                        nc = 0;
+                                    }
                                 }
                             }
                         }
@@ -593,9 +646,9 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
     }
     tc_fence_before();
     __syncthreads();
-    cluster_sync();   // no multicast copy or remote arrival still targets this CTA
+    cluster_sync();   // no copy, commit or arrival of either CTA still targets the other
     tc_fence_after();
-    if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+    if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
 }
 
 // ------------------------------------------------------------------ re-rank
@@ -955,7 +1008,7 @@ cudaError_t launch_match_bf16(const MatchArgs& a, void* ws, size_t ws_bytes, int
                                                                                                  nb32, INFINITY);
         if (forked && (e = cudaEventRecord(a.fork->join_ev[1], a.fork->aux[1])) != cudaSuccess) return e;
         CUtensorMap tA, tB;
-        if (!make_map(&tA, a.dA16, a.NA, kRowsPerUnit) || !make_map(&tB, a.dB16, a.NB, kTileN))
+        if (!make_map(&tA, a.dA16, a.NA, kRowsPerUnit) || !make_map(&tB, a.dB16, a.NB, kHalfN))
             return cudaErrorInvalidValue;
         TcParams p;
         p.NA = a.NA;
