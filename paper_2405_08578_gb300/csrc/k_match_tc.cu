@@ -9,33 +9,29 @@
 // window of every row whose second-best value is well below 1 (its exact value
 // is +inf, so it can never be ranked).
 //
-// k_match_tc<pass> (persistent, one CTA per SM, clusters of two CTAs that
-// run one pair MMA, 10 warps):
-//   warp 0    TMA producer in each CTA: per work unit its own 128-row A block
-//             (2 x 16 KB boxes, 128-byte swizzle), then its own 128-row half
-//             of every 256-row B tile (2 x 16 KB) into a 6-stage ring.  The
-//             copies of both CTAs complete on the even CTA's barriers (plain
-//             per-CTA loads, nothing shared between the CTAs' copies).
-//   warp 1    both CTAs allocate all 512 TMEM columns as a pair; in the even
-//             CTA one lane issues tcgen05.mma.cta_group::2.kind::f16
-//             (M = 256: 128 rows from each CTA, N = 256: 128 B rows from
-//             each CTA, K = 16, BF16 x BF16 -> FP32), 8 per B tile, into one
-//             of two 256-column TMEM accumulator buffers of each CTA;
-//             tcgen05.commit releases the B stage and hands the buffer to
-//             the epilogue, once into each CTA's barrier.
+// k_match_tc<pass> (persistent, one CTA per SM, 10 warps, no clusters):
+//   warp 0    TMA producer: per work unit a 128-row A block (2 x 16 KB boxes,
+//             128-byte swizzle), then 256-row B tiles (2 x 32 KB boxes) into
+//             a 3-stage ring; plain per-CTA loads.
+//   warp 1    allocates all 512 TMEM columns; one lane issues
+//             tcgen05.mma.cta_group::1.kind::f16 (M = 128, N = 256, K = 16,
+//             BF16 x BF16 -> FP32), 8 per B tile, into one of two 256-column
+//             TMEM accumulator buffers; tcgen05.commit releases the B stage
+//             and hands the buffer to the epilogue.
 //   warps 2-9 epilogue: each thread owns one A row and one 128-column half of
-//             every tile; it loads the half row from its CTA's TMEM
-//             (tcgen05.ld 32x32b.x32), returns the buffer (an arrival on the
-//             even CTA's barrier), then works on registers.
+//             every tile; it loads the half row from TMEM (tcgen05.ld
+//             32x32b.x32), returns the buffer, then works on registers.
 //             Pass 1 (every third tile): the two largest 32-column chunk
 //             maxima of D per (split, half, row), written as v.  Pass 2 (all
 //             tiles): every column with v <= T (a three-input max tree per
-//             chunk finds the rare chunks that hold one) is appended to the
-//             row's candidate list (capacity 96, one atomic per 4 columns).
-//   A work unit is (pair of 128-row blocks, one of S column splits of B); a
-//   cluster takes a contiguous run of units.  Every mbarrier wait is bounded
-//   by a 2 s clock limit; on expiry the CTA records LP_ERR_TIMEOUT, drains its
-//   copies, frees its TMEM and returns.
+//             chunk finds the rare chunks that hold one) is stored in the
+//             candidate sub-list of (row, split, half).  Exactly one thread
+//             owns a sub-list, so it keeps its count in a register: no
+//             atomics, and no store waits for anything.
+//   A work unit is (128-row block, one of S column splits of B); a CTA takes
+//   a contiguous run of units, so consecutive units usually reuse the A block.
+//   Every mbarrier wait is bounded by a 2 s clock limit; on expiry the CTA
+//   records LP_ERR_TIMEOUT, drains its copies, frees its TMEM and returns.
 //
 // k_row_threshold: the certification point x = m2 + margin per row, m2 the
 //   second smallest of the pass-1 values.  With unit, non-negative
@@ -48,7 +44,7 @@
 // k_rerank (one warp per row): the candidates are re-scored with exactly the
 //   FP32 form's arithmetic (sequential FMA over k, then fma(-2, dot, |b|^2)),
 //   so their values are bit-identical to the FP32 form's; a row is certified
-//   when its exact second-best is < x.  Rows with an overflowed list
+//   when its exact second-best is < x.  Rows with an overflowed sub-list
 //   or without that margin are re-scanned in FP32 (k_rescan, k_rescan_merge).
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -65,31 +61,23 @@ __global__ void k_match_finish(const float4* part, int S, long long NA, const fl
 namespace {
 
 constexpr int kRowsPerUnit = 128;       // one M = 128 row block per CTA
-constexpr int kTileN = 256;             // B rows per tile (128 staged by each CTA of the pair)
-#ifndef LP_TC_MMA_N
-#define LP_TC_MMA_N 256
-#endif
-constexpr int kMmaN = LP_TC_MMA_N;      // MMA N: kMmaN / 2 B rows from each CTA per instruction
-constexpr int kSub = kTileN / kMmaN;    // MMA groups (accumulator buffers) per tile
-constexpr int kTmemBufs = 512 / kMmaN;  // accumulator buffers of kMmaN columns (512 TMEM columns)
-constexpr int kChunks = kMmaN / 64;     // 32-column chunks per epilogue thread and buffer
-static_assert(kMmaN == 128 || kMmaN == 256, "MMA N");
-#ifndef LP_TC_STAGES
-#define LP_TC_STAGES 6
-#endif
-constexpr int kStages = LP_TC_STAGES;   // B ring depth (half tiles)
+constexpr int kTileN = 256;             // B rows per tile (MMA N)
+constexpr int kTmemBufs = 2;            // accumulator buffers of kTileN columns (512 TMEM columns)
+constexpr int kStages = 3;              // B ring depth
 constexpr int kThreadsTC = 320;         // 10 warps
 constexpr int kEpiWarps = 8;
 constexpr uint32_t kABytes = kRowsPerUnit * 128 * 2;   // 32 KB
-constexpr int kHalfN = kTileN / 2;      // B rows a CTA stages per tile
-constexpr uint32_t kBBytes = kHalfN * 128 * 2;         // 32 KB per stage (this CTA's half tile)
-// 32 KB + 6 x 32 KB + 2 KB = 231,424 bytes of the 232,448 a CTA may opt into
+constexpr uint32_t kBBytes = kTileN * 128 * 2;         // 64 KB per stage
+// 32 KB + 3 x 64 KB + 2 KB = 231,424 bytes of the 232,448 a CTA may opt into
 static_assert(kABytes + kStages * kBBytes + 2048 <= 232448, "shared memory");
 constexpr uint32_t kSmemTC = kABytes + kStages * kBBytes + 1024 /*barriers*/ + 1024 /*align slack*/;
-#ifndef LP_CAND_CAPACITY
-#define LP_CAND_CAPACITY 96
+// pass-2 candidates kept per (row, column split, tile half); a row with a
+// longer sub-list is re-scanned
+#ifndef LP_CAND_SUBCAP
+#define LP_CAND_SUBCAP 32
 #endif
-constexpr int kCandCapacity = LP_CAND_CAPACITY;        // pass-2 candidates kept per row
+constexpr int kSubCap = LP_CAND_SUBCAP;
+constexpr int kMaxSplits = 16;          // column splits S (2 S sub-lists per row)
 // largest threshold a row may get (rows with fewer than two sampled columns)
 constexpr float kCandCap = 1.0e38f;
 // margin of the certification point above m2 (about five standard deviations
@@ -144,11 +132,7 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-#if LP_TC_WAIT_CLUSTER
-        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
-#else
         "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-#endif
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
         : "r"(bar), "r"(parity)
@@ -156,26 +140,9 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
     return ok != 0;
 }
 
-// Shared::cluster address of the object at shared::cta address `a` in the
-// cluster's CTA `rank`.
-__device__ __forceinline__ uint32_t cluster_addr(uint32_t a, uint32_t rank)
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
 {
-    uint32_t r;
-    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
-    return r;
-}
-
-// Arrive on an mbarrier of any CTA of the cluster.  The default (CTA-scope)
-// release: what the arrival publishes is the completion of this warp's TMEM
-// loads, which tcgen05.fence::before_thread_sync orders before it; a
-// cluster-scope release would also wait for the thread's global writes.
-__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cbar)
-{
-#if LP_TC_ARRIVE_REL_CLUSTER
-    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cbar) : "memory");
-#else
-    asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(cbar) : "memory");
-#endif
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
 __device__ __forceinline__ uint64_t globaltimer()
@@ -203,28 +170,12 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
     }
 }
 
-// 2-D tile load into this CTA's shared memory; its complete_tx goes to the
-// mbarrier at shared::cluster address `cbar`, which may be the even CTA's of
-// the pair (.cta_group::2).
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t cbar)
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar)
 {
     asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.cta_group::2 "
-        "[%0], [%1, {%2, %3}], [%4];"
-        ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(cbar)
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
         : "memory");
-}
-
-__device__ __forceinline__ uint32_t cluster_ctarank()
-{
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-    return r;
-}
-
-__device__ __forceinline__ void cluster_sync()
-{
-    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
 __device__ __forceinline__ void tma_prefetch_desc(const CUtensorMap* map)
@@ -247,25 +198,24 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr)
 }
 
 // Instruction descriptor, kind::f16: D = FP32, A = B = BF16, both K-major,
-// N = kMmaN, M = 256 (the CTA pair's 2 x 128 rows).
+// N = kTileN = 256, M = 128.
 constexpr uint32_t kIdesc =
-    (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kMmaN >> 3) << 17) | ((uint32_t)(2 * kRowsPerUnit >> 4) << 24);
+    (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTileN >> 3) << 17) | ((uint32_t)(kRowsPerUnit >> 4) << 24);
 
 __device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t accumulate)
 {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.u32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
         ::"r"(dtmem), "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate)
         : "memory");
 }
 
-// Arrive (when this thread's MMAs complete) on the mbarrier at shared::cluster
-// address `cbar` (either CTA of the pair).
-__device__ __forceinline__ void mma_commit(uint32_t cbar)
+// Arrive on the mbarrier at `bar` when this thread's MMAs complete.
+__device__ __forceinline__ void mma_commit(uint32_t bar)
 {
-    asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(cbar) : "memory");
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -303,28 +253,24 @@ __device__ __forceinline__ void tmem_wait(uint32_t (&r)[32])
 // ------------------------------------------------------------------ work split
 struct TcParams {
     long long NA, NB;
-    int nrp;               // number of pairs of 128-row blocks (one pair per CTA cluster)
-    int S;                 // column splits
+    int nrb;               // number of 128-row blocks
+    int S;                 // column splits (<= kMaxSplits)
     long long cps;         // columns per split (multiple of kTileN)
     float2* pm;            // pass 1 output [2S][NA]: per split and column half, the two smallest chunk minima
     const float* thr;      // pass 2 input [NA]: candidate threshold per row (-inf: none)
-    int32_t* cand;         // pass 2 output [NA][kCandCapacity]: candidate columns (unordered)
-    int32_t* ncand;        // [NA]: candidates found (may exceed the capacity)
-    int tstride;           // tiles visited: every tstride-th 128-column tile of a split
+    int32_t* cand;         // pass 2 output [NA][2S][kSubCap]: candidate columns per (row, split, half)
+    int32_t* ncand;        // pass 2 output [NA][2S]: candidates found per sub-list (may exceed kSubCap)
+    int tstride;           // tiles visited: every tstride-th 256-column tile of a split
     int32_t* status;
 };
 
-// Unit u = (pair of 128-row blocks, column split), processed by one cluster
-// of two CTAs: CTA rank r holds row block rp = 2 * pair + r and rows
-// [128 r, 128 r + 128) of every 256-row B tile of the split.  Consecutive
-// units share a row block and each cluster takes a contiguous run of units,
-// so the A blocks are usually reused.
-__device__ __forceinline__ void unit_range(const TcParams& p, int u, uint32_t crank, int& rp, int& split,
-                                           long long& c0, int& ntiles)
+// Unit u = (128-row block rb, column split).  Consecutive units share a row
+// block and each CTA takes a contiguous run of units, so the A block is
+// usually reused.
+__device__ __forceinline__ void unit_range(const TcParams& p, int u, int& rb, int& split, long long& c0, int& ntiles)
 {
-    const int pair = u / p.S;
-    split = u - pair * p.S;
-    rp = 2 * pair + (int)crank;
+    rb = u / p.S;
+    split = u - rb * p.S;
     c0 = (long long)split * p.cps;
     long long c1 = c0 + p.cps;
     if (c1 > p.NB) c1 = p.NB;
@@ -339,18 +285,6 @@ __device__ __forceinline__ float max3f(float a, float b, float c)
     return r;
 }
 
-// Append up to 4 register-held candidate columns to the row's list.
-__device__ __noinline__ void flush_cands(int32_t* ncand, int32_t* cand, long long row, int nc, int c0, int c1, int c2,
-                                         int c3)
-{
-    const int b0 = atomicAdd(ncand + row, nc);
-    int32_t* dst = cand + row * kCandCapacity;
-    if (b0 + 0 < kCandCapacity) dst[b0 + 0] = c0;
-    if (nc > 1 && b0 + 1 < kCandCapacity) dst[b0 + 1] = c1;
-    if (nc > 2 && b0 + 2 < kCandCapacity) dst[b0 + 2] = c2;
-    if (nc > 3 && b0 + 3 < kCandCapacity) dst[b0 + 3] = c3;
-}
-
 template <int kPass>
 __global__ void __launch_bounds__(kThreadsTC, 1)
 k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcParams p)
@@ -360,34 +294,32 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
     uint8_t* sA = smem;
     uint8_t* sB = smem + kABytes;
     uint64_t* bars = reinterpret_cast<uint64_t*>(sB + kStages * kBBytes);
-    // barrier slots (the same offsets in both CTAs of the pair)
-    uint64_t* full = bars;                 // [kStages]  even CTA: both halves of stage s landed
-    uint64_t* empty = bars + kStages;      // [kStages]  this CTA's half of stage s is free
-    uint64_t* tfull = bars + 2 * kStages;  // [kTmemBufs] this CTA's accumulator buffer b is ready
-    uint64_t* tempty = tfull + kTmemBufs;  // [kTmemBufs] even CTA: both CTAs' epilogues drained buffer b
-    uint64_t* afull = tempty + kTmemBufs;  // [1] even CTA: both A blocks landed
-    uint64_t* aempty = afull + 1;          // [1] this CTA's A block is free
-    uint64_t* drain = aempty + 1;          // [1] even CTA: every issued MMA completed
+    // barrier slots
+    uint64_t* full = bars;                 // [kStages]
+    uint64_t* empty = bars + kStages;      // [kStages]
+    uint64_t* tfull = bars + 2 * kStages;  // [kTmemBufs]
+    uint64_t* tempty = tfull + kTmemBufs;  // [kTmemBufs]
+    uint64_t* afull = tempty + kTmemBufs;  // [1]
+    uint64_t* aempty = afull + 1;          // [1]
+    uint64_t* drain = aempty + 1;          // [1]
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t crank = cluster_ctarank();
-    const bool leader = crank == 0;
-    const int cid = (int)blockIdx.x >> 1, ncl = (int)gridDim.x >> 1;
-    const int U = p.nrp * p.S;
-    const int per = U / ncl, rem = U % ncl;
-    const int u_begin = cid * per + min(cid, rem);
-    const int u_end = u_begin + per + (cid < rem ? 1 : 0);
+    const int U = p.nrb * p.S;
+    const int nct = (int)gridDim.x, cta = (int)blockIdx.x;
+    const int per = U / nct, rem = U % nct;
+    const int u_begin = cta * per + min(cta, rem);
+    const int u_end = u_begin + per + (cta < rem ? 1 : 0);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
-            mbar_init(smem_u32(&full[s]), 1);    // the even CTA's expect_tx arrival
-            mbar_init(smem_u32(&empty[s]), 1);   // one MMA commit
+            mbar_init(smem_u32(&full[s]), 1);
+            mbar_init(smem_u32(&empty[s]), 1);
         }
         for (int b = 0; b < kTmemBufs; ++b) {
             mbar_init(smem_u32(&tfull[b]), 1);
-            mbar_init(smem_u32(&tempty[b]), 2 * kEpiWarps);   // the epilogue warps of both CTAs
+            mbar_init(smem_u32(&tempty[b]), kEpiWarps);
         }
         mbar_init(smem_u32(afull), 1);
         mbar_init(smem_u32(aempty), 1);
@@ -398,14 +330,12 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
         tma_prefetch_desc(&tmB);
     }
     if (warp == 1) {
-        // one warp of each CTA of the pair allocates, collectively
-        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tmem_slot))
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tmem_slot))
                      : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     tc_fence_before();
     __syncthreads();
-    cluster_sync();   // both CTAs' barriers exist before any copy, commit or arrival reaches them
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
@@ -413,28 +343,26 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
         // ---------------------------------------------------------- TMA producer
         if (lane == 0) {
             long long n = 0;   // tile counter of this CTA (non-empty units only)
-            int v = 0;         // non-empty unit counter of this CTA
+            int v = 0;         // A block counter of this CTA
             int armed[kStages];
             int a_armed = -1;
             for (int s = 0; s < kStages; ++s) armed[s] = -1;
-            bool ok = true, issued = false;
-            int prev_rp = -1;
-            const uint32_t c_afull = cluster_addr(smem_u32(afull), 0);
+            bool ok = true;
+            int prev_rb = -1;
             for (int u = u_begin; u < u_end && ok; ++u) {
-                int rp, split, ntiles;
+                int rb, split, ntiles;
                 long long c0;
-                unit_range(p, u, crank, rp, split, c0, ntiles);
+                unit_range(p, u, rb, split, c0, ntiles);
                 if (ntiles == 0) continue;
-                if (rp != prev_rp) {
+                if (rb != prev_rb) {
                     ok = mbar_wait(smem_u32(aempty), (v & 1) ^ 1, abort_flag, p.status);
                     if (!ok) break;
-                    if (leader) mbar_expect_tx(smem_u32(afull), 2 * kABytes);
-                    tma_load_2d(smem_u32(sA), &tmA, 0, rp * kRowsPerUnit, c_afull);
-                    tma_load_2d(smem_u32(sA + kABytes / 2), &tmA, 64, rp * kRowsPerUnit, c_afull);
+                    mbar_expect_tx(smem_u32(afull), kABytes);
+                    tma_load_2d(smem_u32(sA), &tmA, 0, rb * kRowsPerUnit, smem_u32(afull));
+                    tma_load_2d(smem_u32(sA + kABytes / 2), &tmA, 64, rb * kRowsPerUnit, smem_u32(afull));
                     a_armed = v;
-                    issued = true;
                     ++v;
-                    prev_rp = rp;
+                    prev_rb = rb;
                 }
                 for (int t = 0; t < ntiles; ++t, ++n) {
                     const int s = (int)(n % kStages);
@@ -442,104 +370,80 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
                     ok = mbar_wait(smem_u32(&empty[s]), (k & 1) ^ 1, abort_flag, p.status);
                     if (!ok) break;
                     uint8_t* dst = sB + s * kBBytes;
-                    const int y = (int)(c0 + (long long)t * p.tstride * kTileN) + (int)crank * kHalfN;
-                    if (leader) mbar_expect_tx(smem_u32(&full[s]), 2 * kBBytes);
-                    const uint32_t c_full = cluster_addr(smem_u32(&full[s]), 0);
-                    tma_load_2d(smem_u32(dst), &tmB, 0, y, c_full);
-                    tma_load_2d(smem_u32(dst + kBBytes / 2), &tmB, 64, y, c_full);
+                    const int y = (int)(c0 + (long long)t * p.tstride * kTileN);
+                    mbar_expect_tx(smem_u32(&full[s]), kBBytes);
+                    tma_load_2d(smem_u32(dst), &tmB, 0, y, smem_u32(&full[s]));
+                    tma_load_2d(smem_u32(dst + kBBytes / 2), &tmB, 64, y, smem_u32(&full[s]));
                     armed[s] = (int)k;
-                    issued = true;
                 }
             }
             if (!ok) {
-                if (leader) {
-                    // drain: wait (bounded) for the stages this CTA armed to land
-                    for (int s = 0; s < kStages; ++s) {
-                        if (armed[s] < 0) continue;
-                        const uint64_t t0 = globaltimer();
-                        while (!mbar_try(smem_u32(&full[s]), (uint32_t)armed[s] & 1u) &&
-                               globaltimer() - t0 < 200000000ull) {
-                        }
-                    }
-                    if (a_armed >= 0) {
-                        const uint64_t t0 = globaltimer();
-                        while (!mbar_try(smem_u32(afull), (uint32_t)a_armed & 1u) && globaltimer() - t0 < 200000000ull) {
-                        }
-                    }
-                } else if (issued) {
-                    // this CTA's copies complete on the even CTA's barriers: give
-                    // the ones in flight a fixed 2 ms to land
+                // drain: wait (bounded) for the copies this thread issued to land
+                for (int s = 0; s < kStages; ++s) {
+                    if (armed[s] < 0) continue;
                     const uint64_t t0 = globaltimer();
-                    while (globaltimer() - t0 < 2000000ull) {
+                    while (!mbar_try(smem_u32(&full[s]), (uint32_t)armed[s] & 1u) && globaltimer() - t0 < 200000000ull) {
+                    }
+                }
+                if (a_armed >= 0) {
+                    const uint64_t t0 = globaltimer();
+                    while (!mbar_try(smem_u32(afull), (uint32_t)a_armed & 1u) && globaltimer() - t0 < 200000000ull) {
                     }
                 }
             }
         }
     } else if (warp == 1) {
-        // ---------------------------------------------------------- MMA issuer (even CTA)
-        if (lane == 0 && leader) {
+        // ---------------------------------------------------------- MMA issuer
+        if (lane == 0) {
             // descriptors of the fixed buffers; an operand at byte offset o from
             // a base is the base descriptor + (o >> 4) (the 14-bit start field
-            // never carries: shared addresses stay below 256 KB).  The same
-            // offsets address the odd CTA's rows and B half.
+            // never carries: shared addresses stay below 256 KB)
             const uint64_t dA0 = sdesc(smem_u32(sA)), dB0 = sdesc(smem_u32(sB));
             long long n = 0;
             int v = 0;
             bool ok = true;
-            int prev_rp = -1;
+            int prev_rb = -1;
             for (int u = u_begin; u < u_end && ok; ++u) {
-                int rp, split, ntiles;
+                int rb, split, ntiles;
                 long long c0;
-                unit_range(p, u, crank, rp, split, c0, ntiles);
+                unit_range(p, u, rb, split, c0, ntiles);
                 if (ntiles == 0) continue;
-                if (rp != prev_rp) {
-                    // release the previous A blocks once their MMAs are done, then
-                    // wait for the new ones
-                    if (v > 0) {
-                        mma_commit(cluster_addr(smem_u32(aempty), 0));
-                        mma_commit(cluster_addr(smem_u32(aempty), 1));
-                    }
+                if (rb != prev_rb) {
+                    // release the previous A block once its MMAs are done, then
+                    // wait for the new one
+                    if (v > 0) mma_commit(smem_u32(aempty));
                     ok = mbar_wait(smem_u32(afull), v & 1, abort_flag, p.status);
                     ++v;
-                    prev_rp = rp;
+                    prev_rb = rb;
                     if (!ok) break;
                     tc_fence_after();
                 }
-                for (int t = 0; t < ntiles && ok; ++t, ++n) {
+                for (int t = 0; t < ntiles; ++t, ++n) {
                     const int s = (int)(n % kStages);
                     const uint32_t k = (uint32_t)(n / kStages);
+                    const int b = (int)(n % kTmemBufs);
+                    const uint32_t kb = (uint32_t)(n / kTmemBufs);
+                    ok = mbar_wait(smem_u32(&tempty[b]), (kb & 1) ^ 1, abort_flag, p.status);
+                    if (!ok) break;
                     ok = mbar_wait(smem_u32(&full[s]), k & 1, abort_flag, p.status);
                     if (!ok) break;
+                    tc_fence_after();
                     const uint64_t dB = dB0 + (uint64_t)((s * kBBytes) >> 4);
-                    // sub-tile st: B rows [st N/2, st N/2 + N/2) of each CTA's half tile
+                    const uint32_t d = tmem + (uint32_t)(b * kTileN);
 #pragma unroll
-                    for (int st = 0; st < kSub; ++st) {
-                        const long long nn = n * kSub + st;
-                        const int b = (int)(nn % kTmemBufs);
-                        const uint32_t kb = (uint32_t)(nn / kTmemBufs);
-                        ok = mbar_wait(smem_u32(&tempty[b]), (kb & 1) ^ 1, abort_flag, p.status);
-                        if (!ok) break;
-                        tc_fence_after();
-                        const uint32_t d = tmem + (uint32_t)(b * kMmaN);
+                    for (int h = 0; h < 2; ++h)
 #pragma unroll
-                        for (int h = 0; h < 2; ++h)
-#pragma unroll
-                            for (int kk = 0; kk < 4; ++kk) {
-                                const uint64_t ad = dA0 + (uint64_t)((h * (kABytes / 2) + kk * 32) >> 4);
-                                const uint64_t bd =
-                                    dB + (uint64_t)((h * (kBBytes / 2) + st * (kMmaN / 2) * 128 + kk * 32) >> 4);
-                                mma_bf16(d, ad, bd, (h | kk) ? 1u : 0u);
-                            }
-                        mma_commit(cluster_addr(smem_u32(&tfull[b]), 0));
-                        mma_commit(cluster_addr(smem_u32(&tfull[b]), 1));
-                    }
-                    if (!ok) break;
-                    mma_commit(cluster_addr(smem_u32(&empty[s]), 0));
-                    mma_commit(cluster_addr(smem_u32(&empty[s]), 1));
+                        for (int kk = 0; kk < 4; ++kk) {
+                            const uint64_t ad = dA0 + (uint64_t)((h * (kABytes / 2) + kk * 32) >> 4);
+                            const uint64_t bd = dB + (uint64_t)((h * (kBBytes / 2) + kk * 32) >> 4);
+                            mma_bf16(d, ad, bd, (h | kk) ? 1u : 0u);
+                        }
+                    mma_commit(smem_u32(&empty[s]));
+                    mma_commit(smem_u32(&tfull[b]));
                 }
             }
             // wait (bounded) for every MMA this thread issued before TMEM is freed
-            mma_commit(cluster_addr(smem_u32(drain), 0));
+            mma_commit(smem_u32(drain));
             const uint64_t t0 = globaltimer();
             while (!mbar_try(smem_u32(drain), 0) && globaltimer() - t0 < 2000000000ull) {
             }
@@ -549,91 +453,75 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
         // The accumulator holds D = -v / 2: smaller v is larger D.
         // Pass 1: per (split, row) the two largest chunk maxima of D (a chunk =
         //   32 columns), which name two different columns; written as v.
-        // Pass 2: every column with v <= T (D >= -T / 2) is a candidate; a
-        //   lane holds up to 4 in registers and appends them to the row's list
-        //   (one atomic slot reservation per flush).
+        // Pass 2: every column with v <= T (D >= -T / 2) is a candidate, stored
+        //   in this thread's own sub-list of the row.
         const int q = warp & 3;                 // TMEM lane quarter this warp may access
         const int half = (warp - 2) >> 2;       // columns [0, 128) (warps 2-5) or [128, 256) (warps 6-9) of a tile
         const int row_in_unit = q * 32 + lane;
         long long n = 0;
         bool ok = true;
         for (int u = u_begin; u < u_end && ok; ++u) {
-            int rp, split, ntiles;
+            int rb, split, ntiles;
             long long c0;
-            unit_range(p, u, crank, rp, split, c0, ntiles);
+            unit_range(p, u, rb, split, c0, ntiles);
             long long c1 = c0 + p.cps;
             if (c1 > p.NB) c1 = p.NB;
-            const long long row = (long long)rp * kRowsPerUnit + row_in_unit;
+            const long long row = (long long)rb * kRowsPerUnit + row_in_unit;
             const bool live = row < p.NA;
+            const long long sub = (live ? row : 0) * (2 * p.S) + split * 2 + half;
+            int32_t* const dst = p.cand + sub * kSubCap;
             float d1 = -INFINITY, d2 = -INFINITY;                                    // pass 1
             // pass 2: v~ = 1 - 2 D <= T  <=>  D >= (1 - T) / 2 (1e-6 lower: rounding of TD)
             const float TD = (kPass == 2 && live) ? 0.5f * (1.f - window_top(p.thr[row])) - 1e-6f : INFINITY;
-            int nc = 0, cj0 = 0, cj1 = 0, cj2 = 0, cj3 = 0;
-            for (int t = 0; t < ntiles && ok; ++t, ++n) {
-#pragma unroll 1
-                for (int st = 0; st < kSub; ++st) {
-                    const long long nn = n * kSub + st;
-                    const int b = (int)(nn % kTmemBufs);
-                    const uint32_t kb = (uint32_t)(nn / kTmemBufs);
-                    ok = mbar_wait(smem_u32(&tfull[b]), kb & 1, abort_flag, p.status);
-                    if (!ok) break;
-                    tc_fence_after();
-                    // accumulator columns [half N/2, half N/2 + N/2) hold B rows
-                    // st N/2 + [0, N/2) of CTA `half`'s half tile: tile columns
-                    // 128 half + st N/2 + [0, N/2)
-                    const long long cbase = c0 + (long long)t * p.tstride * kTileN + half * 128 + st * (kMmaN / 2);
-                    const uint32_t tbase =
-                        tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * kMmaN + half * (kMmaN / 2));
-                    // the thread's accumulator row in registers, then the buffer goes back to the MMA
-                    uint32_t r[kChunks][32];
+            int nc = 0;
+            for (int t = 0; t < ntiles; ++t, ++n) {
+                const int b = (int)(n % kTmemBufs);
+                const uint32_t kb = (uint32_t)(n / kTmemBufs);
+                ok = mbar_wait(smem_u32(&tfull[b]), kb & 1, abort_flag, p.status);
+                if (!ok) break;
+                tc_fence_after();
+                const long long cbase = c0 + (long long)t * p.tstride * kTileN + half * 128;
+                const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * kTileN + half * 128);
+                // the whole tile row in registers, then the buffer goes back to the MMA
+                uint32_t r[4][32];
 #pragma unroll
-                    for (int ch = 0; ch < kChunks; ++ch) tmem_ld32(tbase + 32 * ch, r[ch]);
+                for (int ch = 0; ch < 4; ++ch) tmem_ld32(tbase + 32 * ch, r[ch]);
 #pragma unroll
-                    for (int ch = 0; ch < kChunks; ++ch) tmem_wait(r[ch]);
-                    tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive_cluster(cluster_addr(smem_u32(&tempty[b]), 0));
+                for (int ch = 0; ch < 4; ++ch) tmem_wait(r[ch]);
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&tempty[b]));
 #pragma unroll
-                    for (int ch = 0; ch < kChunks; ++ch) {
-                        float dv[32];
+                for (int ch = 0; ch < 4; ++ch) {
+                    float dv[32];
 #pragma unroll
-                        for (int i = 0; i < 32; ++i) dv[i] = __uint_as_float(r[ch][i]);
-                        const long long j0 = cbase + ch * 32;
-                        if (j0 + 32 > c1) {   // columns past the split or past NB (zero-filled rows)
+                    for (int i = 0; i < 32; ++i) dv[i] = __uint_as_float(r[ch][i]);
+                    const long long j0 = cbase + ch * 32;
+                    if (j0 + 32 > c1) {   // columns past the split or past NB (zero-filled rows)
 #pragma unroll
-                            for (int i = 0; i < 32; ++i) dv[i] = j0 + i < c1 ? dv[i] : -INFINITY;
-                        }
-                        float gx[4];
+                        for (int i = 0; i < 32; ++i) dv[i] = j0 + i < c1 ? dv[i] : -INFINITY;
+                    }
+                    float gx[4];
 #pragma unroll
-                        for (int g = 0; g < 4; ++g)
-                            gx[g] = max3f(max3f(dv[8 * g + 0], dv[8 * g + 1], dv[8 * g + 2]),
-                                          max3f(dv[8 * g + 3], dv[8 * g + 4], dv[8 * g + 5]),
-                                          fmaxf(dv[8 * g + 6], dv[8 * g + 7]));
-                        const float cmax = max3f(gx[0], gx[1], fmaxf(gx[2], gx[3]));
-                        if (kPass == 1) {
-                            const float lo = fminf(d1, cmax);
-                            d1 = fmaxf(d1, cmax);
-                            d2 = fmaxf(d2, lo);
-                        } else {
-                            const bool trig = cmax >= TD;
-                            if (__any_sync(0xFFFFFFFFu, trig)) {
-                                // bit i: column j0 + i qualifies; then one short loop over the bits
-                                uint32_t m = 0;
+                    for (int g = 0; g < 4; ++g)
+                        gx[g] = max3f(max3f(dv[8 * g + 0], dv[8 * g + 1], dv[8 * g + 2]),
+                                      max3f(dv[8 * g + 3], dv[8 * g + 4], dv[8 * g + 5]),
+                                      fmaxf(dv[8 * g + 6], dv[8 * g + 7]));
+                    const float cmax = max3f(gx[0], gx[1], fmaxf(gx[2], gx[3]));
+                    if (kPass == 1) {
+                        const float lo = fminf(d1, cmax);
+                        d1 = fmaxf(d1, cmax);
+                        d2 = fmaxf(d2, lo);
+                    } else if (cmax >= TD) {
+                        // bit i: column j0 + i qualifies; one store per candidate
+                        uint32_t m = 0;
 #pragma unroll
-                                for (int i = 0; i < 32; ++i) m |= (dv[i] >= TD ? 1u : 0u) << i;
-                                while (m) {
-                                    const int j = (int)j0 + __ffs(m) - 1;
-                                    m &= m - 1;
-                                    cj0 = nc == 0 ? j : cj0;
-                                    cj1 = nc == 1 ? j : cj1;
-                                    cj2 = nc == 2 ? j : cj2;
-                                    cj3 = nc == 3 ? j : cj3;
-                                    if (++nc == 4) {
-                                        flush_cands(p.ncand, p.cand, row, 4, cj0, cj1, cj2, cj3);
-                                        nc = 0;
-                                    }
-                                }
-                            }
+                        for (int i = 0; i < 32; ++i) m |= (dv[i] >= TD ? 1u : 0u) << i;
+                        while (m) {
+                            const int j = (int)j0 + __ffs(m) - 1;
+                            m &= m - 1;
+                            if (nc < kSubCap) dst[nc] = j;
+                            ++nc;
                         }
                     }
                 }
@@ -641,14 +529,13 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
             if (!ok) break;
             if (kPass == 1 && live)
                 p.pm[((long long)split * 2 + half) * p.NA + row] = make_float2(1.f - 2.f * d1, 1.f - 2.f * d2);
-            if (kPass == 2 && nc > 0) flush_cands(p.ncand, p.cand, row, nc, cj0, cj1, cj2, cj3);
+            if (kPass == 2 && live) p.ncand[sub] = nc;
         }
     }
     tc_fence_before();
     __syncthreads();
-    cluster_sync();   // no copy, commit or arrival of either CTA still targets the other
     tc_fence_after();
-    if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+    if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
 }
 
 // ------------------------------------------------------------------ re-rank
@@ -694,8 +581,8 @@ __device__ __forceinline__ void warp_top2(float& b1, int& j1, float& b2, int& j2
 
 // Per row, the certification point x = m2 + kMargin (m2 the second smallest
 // pass-1 value; capped for rows with fewer than two sampled columns), -inf for
-// an invalid query row; the row's candidate counter is cleared.
-__global__ void k_row_threshold(const float2* pm, int S, long long NA, const uint8_t* vA, float* thr, int32_t* ncand)
+// an invalid query row.
+__global__ void k_row_threshold(const float2* pm, int S, long long NA, const uint8_t* vA, float* thr)
 {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= NA) return;
@@ -707,17 +594,17 @@ __global__ void k_row_threshold(const float2* pm, int S, long long NA, const uin
         m1 = fminf(m1, lo);
     }
     thr[i] = vA[i] ? fminf(m2 + kMargin, kCandCap) : -INFINITY;
-    ncand[i] = 0;
 }
 
-// One warp per row, one candidate per lane: exact FP32-form values (the FP32
-// form's own arithmetic), the top 2 by (value, column).  Every column outside
-// the list has a BF16 value > window_top(x) and so an FP32-form value > x: the
-// row is certified when its exact second-best is < x.  Rows with an overflowed
-// list or without that margin are queued for the FP32 re-scan.
+// One warp per row: every candidate of the row's 2S sub-lists is re-scored
+// with exactly the FP32 form's arithmetic, and the top 2 kept by (value,
+// column).  Every column outside the lists has a BF16 value > window_top(x)
+// and so an FP32-form value > x: the row is certified when its exact
+// second-best is < x.  Rows with an overflowed sub-list or without that margin
+// are queued for the FP32 re-scan.
 __global__ void __launch_bounds__(kRerankWarps * 32)
 k_rerank(const float* A, const uint8_t* vA, const float* B, const float* nb32, const int32_t* cand,
-         const int32_t* ncand, const float* thr, long long NA, float4* out_part, int32_t* rescan_rows,
+         const int32_t* ncand, int nsub, const float* thr, long long NA, float4* out_part, int32_t* rescan_rows,
          int32_t* rescan_count)
 {
     __shared__ __align__(16) float qa[kRerankWarps][128];
@@ -728,16 +615,20 @@ k_rerank(const float* A, const uint8_t* vA, const float* B, const float* nb32, c
         if (lane == 0) out_part[i] = make_float4(INFINITY, INFINITY, __int_as_float(-1), __int_as_float(-1));
         return;
     }
-    const int n = ncand[i];
+    const int32_t* cnt = ncand + i * nsub;
+    const int32_t* lst = cand + i * (long long)nsub * kSubCap;
     const float T = thr[i];
-    bool ok = n <= kCandCapacity;
+    bool over = false;
+    for (int q = lane; q < nsub; q += 32) over |= (unsigned)cnt[q] > (unsigned)kSubCap;
+    bool ok = !__any_sync(0xFFFFFFFFu, over);
     float b1 = INFINITY, b2 = INFINITY;
     int j1 = -1, j2 = -1;
     if (ok) {
         reinterpret_cast<float4*>(qa[warp])[lane] = reinterpret_cast<const float4*>(A + i * 128)[lane];
         __syncwarp();
-        for (int c = lane; c < n; c += 32) {
-            const int j = cand[i * kCandCapacity + c];
+        for (int e = lane; e < nsub * kSubCap; e += 32) {
+            if (e % kSubCap >= cnt[e / kSubCap]) continue;
+            const int j = lst[e];
             top2_lex(b1, j1, b2, j2, fp32_form_value(qa[warp], B + (long long)j * 128, __ldg(nb32 + j)), j);
         }
         warp_top2(b1, j1, b2, j2);
@@ -915,17 +806,17 @@ bool make_map(CUtensorMap* m, const void* base, long long rows, uint32_t box_row
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// Column splits S: minimise (rounds of units per CTA) x (tiles per unit + ~2
-// tiles of per-unit A reload and pipeline refill).
-int pick_tc_splits(int nrp, long long NB, int sms)
+// Column splits S: minimise (rounds of units per CTA) x (tiles per unit + ~1
+// tile of per-unit A reload and pipeline refill).
+int pick_tc_splits(int nrb, long long NB, int ctas)
 {
     const long long tiles = (NB + kTileN - 1) / kTileN;
     int best = 1;
     double best_cost = 1e300;
-    for (int S = 1; S <= 32 && S <= tiles; ++S) {
-        const long long U = (long long)nrp * S;
-        const double rounds = (double)((U + sms - 1) / sms);
-        const double cost = rounds * (double)((tiles + S - 1) / S + 256 / kTileN);
+    for (int S = 1; S <= kMaxSplits && S <= tiles; ++S) {
+        const long long U = (long long)nrb * S;
+        const double rounds = (double)((U + ctas - 1) / ctas);
+        const double cost = rounds * (double)((tiles + S - 1) / S + 1);
         if (cost < best_cost - 1e-9) { best_cost = cost; best = S; }
     }
     return best;
@@ -940,16 +831,16 @@ struct TcLayout {
 TcLayout tc_layout(long long NA, long long NB, int sms)
 {
     TcLayout L;
-    const int nrp = (int)((NA + 2 * kRowsPerUnit - 1) / (2 * kRowsPerUnit));
-    L.S = pick_tc_splits(nrp, NB, std::max(1, sms / 2));
+    const int nrb = (int)((NA + kRowsPerUnit - 1) / kRowsPerUnit);
+    L.S = pick_tc_splits(nrb, NB, std::max(1, sms));
     size_t o = 0;
     auto take = [&](size_t bytes) { size_t r = o; o += (bytes + 255) & ~size_t(255); return r; };
     L.off_na = take(sizeof(float) * (size_t)NA);
     L.off_nb32 = take(sizeof(float) * (size_t)NB);
     L.off_pm = take(sizeof(float2) * 2 * (size_t)L.S * NA);
     L.off_thr = take(sizeof(float) * (size_t)NA);
-    L.off_cand = take(sizeof(int32_t) * kCandCapacity * (size_t)NA);
-    L.off_ncand = take(sizeof(int32_t) * (size_t)NA);
+    L.off_cand = take(sizeof(int32_t) * kSubCap * 2 * (size_t)L.S * NA);
+    L.off_ncand = take(sizeof(int32_t) * 2 * (size_t)L.S * NA);
     L.off_part1 = take(sizeof(float4) * (size_t)NA);
     L.off_rows = take(sizeof(int32_t) * (size_t)NA);
     L.off_cnt = take(64);
@@ -1008,12 +899,12 @@ cudaError_t launch_match_bf16(const MatchArgs& a, void* ws, size_t ws_bytes, int
                                                                                                  nb32, INFINITY);
         if (forked && (e = cudaEventRecord(a.fork->join_ev[1], a.fork->aux[1])) != cudaSuccess) return e;
         CUtensorMap tA, tB;
-        if (!make_map(&tA, a.dA16, a.NA, kRowsPerUnit) || !make_map(&tB, a.dB16, a.NB, kHalfN))
+        if (!make_map(&tA, a.dA16, a.NA, kRowsPerUnit) || !make_map(&tB, a.dB16, a.NB, kTileN))
             return cudaErrorInvalidValue;
         TcParams p;
         p.NA = a.NA;
         p.NB = a.NB;
-        p.nrp = (int)((a.NA + 2 * kRowsPerUnit - 1) / (2 * kRowsPerUnit));
+        p.nrb = (int)((a.NA + kRowsPerUnit - 1) / kRowsPerUnit);
         p.S = L.S;
         const long long tiles = (a.NB + kTileN - 1) / kTileN;
         p.cps = ((tiles + L.S - 1) / L.S) * kTileN;
@@ -1023,41 +914,31 @@ cudaError_t launch_match_bf16(const MatchArgs& a, void* ws, size_t ws_bytes, int
         p.ncand = ncand;
         p.tstride = 1;
         p.status = a.status;
-        const int U = p.nrp * p.S;
+        const int U = p.nrb * p.S;
         if ((e = cudaFuncSetAttribute(k_match_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTC)) !=
                 cudaSuccess ||
             (e = cudaFuncSetAttribute(k_match_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTC)) !=
                 cudaSuccess)
             return e;
-        cudaLaunchConfig_t cfg = {};
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = 2;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.blockDim = dim3(kThreadsTC);
-        cfg.dynamicSmemBytes = kSmemTC;
-        cfg.stream = s;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        cfg.gridDim = dim3(2 * (unsigned)std::max(1, num_sms / 2));
-        int clusters = 0;
-        if ((e = cudaOccupancyMaxActiveClusters(&clusters, k_match_tc<1>, &cfg)) != cudaSuccess) return e;
-        if (clusters < 1) return cudaErrorInvalidConfiguration;
-        cfg.gridDim = dim3(2 * (unsigned)std::min(U, clusters));
+        int per_sm = 0;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_match_tc<1>, kThreadsTC, kSmemTC)) !=
+            cudaSuccess)
+            return e;
+        if (per_sm < 1) return cudaErrorInvalidConfiguration;
+        const dim3 grid((unsigned)std::min(U, per_sm * num_sms));
         if (a.ev0) cudaEventRecord(a.ev0, s);
         TcParams p1 = p;
         p1.tstride = kPass1Stride;
-        if ((e = cudaLaunchKernelEx(&cfg, k_match_tc<1>, tA, tB, p1)) != cudaSuccess) return e;
-        k_row_threshold<<<(unsigned)((a.NA + 255) / 256), 256, 0, s>>>(pm, 2 * L.S, a.NA, a.vA, thr, ncand);
-        if ((e = cudaLaunchKernelEx(&cfg, k_match_tc<2>, tA, tB, p)) != cudaSuccess) return e;
+        k_match_tc<1><<<grid, kThreadsTC, kSmemTC, s>>>(tA, tB, p1);
+        k_row_threshold<<<(unsigned)((a.NA + 255) / 256), 256, 0, s>>>(pm, 2 * L.S, a.NA, a.vA, thr);
+        k_match_tc<2><<<grid, kThreadsTC, kSmemTC, s>>>(tA, tB, p);
         if (a.ev1) cudaEventRecord(a.ev1, s);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if (forked && ((e = cudaStreamWaitEvent(s, a.fork->join_ev[1], 0)) != cudaSuccess ||
                        (e = cudaStreamWaitEvent(s, a.fork->join_ev[0], 0)) != cudaSuccess))
             return e;
         k_rerank<<<(unsigned)((a.NA + kRerankWarps - 1) / kRerankWarps), kRerankWarps * 32, 0, s>>>(
-            a.dA, a.vA, a.dB, nb32, cand, ncand, thr, a.NA, part1, rows, cnt);
+            a.dA, a.vA, a.dB, nb32, cand, ncand, 2 * L.S, thr, a.NA, part1, rows, cnt);
         if ((e = cudaFuncSetAttribute(k_rescan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRescanSmem)) !=
             cudaSuccess)
             return e;
