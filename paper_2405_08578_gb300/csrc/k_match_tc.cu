@@ -18,14 +18,15 @@
 //             BF16 x BF16 -> FP32), 8 per B tile, into one of two 256-column
 //             TMEM accumulator buffers; tcgen05.commit releases the B stage
 //             and hands the buffer to the epilogue.
-//   warps 2-9 epilogue: each thread owns one A row and one 128-column half of
-//             every tile; it loads the half row from TMEM (tcgen05.ld
-//             32x32b.x32), returns the buffer, then works on registers.
+//   warps 2-9 epilogue: each thread owns one A row and one 128-column range
+//             of every tile (LP_TC_EPI_RANGES = 4: 16 warps, 64-column ranges);
+//             it loads its part of the row from TMEM (tcgen05.ld 32x32b.x32),
+//             returns the buffer, then works on registers.
 //             Pass 1 (every third tile): the two largest 32-column chunk
-//             maxima of D per (split, half, row), written as v.  Pass 2 (all
+//             maxima of D per (split, range, row), written as v.  Pass 2 (all
 //             tiles): every column with v <= T (a three-input max tree per
 //             chunk finds the rare chunks that hold one) is stored in the
-//             candidate sub-list of (row, split, half).  Exactly one thread
+//             candidate sub-list of (row, split, range).  Exactly one thread
 //             owns a sub-list, so it keeps its count in a register: no
 //             atomics, and no store waits for anything.
 //   A work unit is (128-row block, one of S column splits of B); a CTA takes
@@ -64,20 +65,27 @@ constexpr int kRowsPerUnit = 128;       // one M = 128 row block per CTA
 constexpr int kTileN = 256;             // B rows per tile (MMA N)
 constexpr int kTmemBufs = 2;            // accumulator buffers of kTileN columns (512 TMEM columns)
 constexpr int kStages = 3;              // B ring depth
-constexpr int kThreadsTC = 320;         // 10 warps
-constexpr int kEpiWarps = 8;
+#ifndef LP_TC_EPI_RANGES
+#define LP_TC_EPI_RANGES 2
+#endif
+constexpr int kRanges = LP_TC_EPI_RANGES;       // column ranges of a tile, one epilogue warp per (range, lane quarter)
+constexpr int kEpiWarps = 4 * kRanges;
+constexpr int kThreadsTC = 64 + 32 * kEpiWarps; // producer warp, MMA warp, epilogue warps
+constexpr int kRangeCols = kTileN / kRanges;    // columns of a tile one epilogue thread scans
+constexpr int kChunks = kRangeCols / 32;
+static_assert(kRanges == 2 || kRanges == 4, "epilogue column ranges");
 constexpr uint32_t kABytes = kRowsPerUnit * 128 * 2;   // 32 KB
 constexpr uint32_t kBBytes = kTileN * 128 * 2;         // 64 KB per stage
 // 32 KB + 3 x 64 KB + 2 KB = 231,424 bytes of the 232,448 a CTA may opt into
 static_assert(kABytes + kStages * kBBytes + 2048 <= 232448, "shared memory");
 constexpr uint32_t kSmemTC = kABytes + kStages * kBBytes + 1024 /*barriers*/ + 1024 /*align slack*/;
-// pass-2 candidates kept per (row, column split, tile half); a row with a
+// pass-2 candidates kept per (row, column split, column range); a row with a
 // longer sub-list is re-scanned
 #ifndef LP_CAND_SUBCAP
 #define LP_CAND_SUBCAP 32
 #endif
 constexpr int kSubCap = LP_CAND_SUBCAP;
-constexpr int kMaxSplits = 16;          // column splits S (2 S sub-lists per row)
+constexpr int kMaxSplits = 16;          // column splits S (kRanges S sub-lists per row)
 // largest threshold a row may get (rows with fewer than two sampled columns)
 constexpr float kCandCap = 1.0e38f;
 // margin of the certification point above m2 (about five standard deviations
@@ -256,10 +264,10 @@ struct TcParams {
     int nrb;               // number of 128-row blocks
     int S;                 // column splits (<= kMaxSplits)
     long long cps;         // columns per split (multiple of kTileN)
-    float2* pm;            // pass 1 output [2S][NA]: per split and column half, the two smallest chunk minima
+    float2* pm;            // pass 1 output [kRanges S][NA]: per split and column range, the two smallest chunk minima
     const float* thr;      // pass 2 input [NA]: candidate threshold per row (-inf: none)
-    int32_t* cand;         // pass 2 output [NA][2S][kSubCap]: candidate columns per (row, split, half)
-    int32_t* ncand;        // pass 2 output [NA][2S]: candidates found per sub-list (may exceed kSubCap)
+    int32_t* cand;         // pass 2 output [NA][kRanges S][kSubCap]: candidate columns per (row, split, range)
+    int32_t* ncand;        // pass 2 output [NA][kRanges S]: candidates found per sub-list (may exceed kSubCap)
     int tstride;           // tiles visited: every tstride-th 256-column tile of a split
     int32_t* status;
 };
@@ -451,12 +459,12 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
     } else {
         // ---------------------------------------------------------- epilogue
         // The accumulator holds D = -v / 2: smaller v is larger D.
-        // Pass 1: per (split, row) the two largest chunk maxima of D (a chunk =
-        //   32 columns), which name two different columns; written as v.
+        // Pass 1: per (split, range, row) the two largest chunk maxima of D (a
+        //   chunk = 32 columns), which name two different columns; written as v.
         // Pass 2: every column with v <= T (D >= -T / 2) is a candidate, stored
         //   in this thread's own sub-list of the row.
         const int q = warp & 3;                 // TMEM lane quarter this warp may access
-        const int half = (warp - 2) >> 2;       // columns [0, 128) (warps 2-5) or [128, 256) (warps 6-9) of a tile
+        const int rg = (warp - 2) >> 2;         // columns [rg kRangeCols, (rg + 1) kRangeCols) of a tile
         const int row_in_unit = q * 32 + lane;
         long long n = 0;
         bool ok = true;
@@ -468,7 +476,7 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
             if (c1 > p.NB) c1 = p.NB;
             const long long row = (long long)rb * kRowsPerUnit + row_in_unit;
             const bool live = row < p.NA;
-            const long long sub = (live ? row : 0) * (2 * p.S) + split * 2 + half;
+            const long long sub = (live ? row : 0) * (kRanges * p.S) + split * kRanges + rg;
             int32_t* const dst = p.cand + sub * kSubCap;
             float d1 = -INFINITY, d2 = -INFINITY;                                    // pass 1
             // pass 2: v~ = 1 - 2 D <= T  <=>  D >= (1 - T) / 2 (1e-6 lower: rounding of TD)
@@ -480,19 +488,19 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
                 ok = mbar_wait(smem_u32(&tfull[b]), kb & 1, abort_flag, p.status);
                 if (!ok) break;
                 tc_fence_after();
-                const long long cbase = c0 + (long long)t * p.tstride * kTileN + half * 128;
-                const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * kTileN + half * 128);
-                // the whole tile row in registers, then the buffer goes back to the MMA
-                uint32_t r[4][32];
+                const long long cbase = c0 + (long long)t * p.tstride * kTileN + rg * kRangeCols;
+                const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * kTileN + rg * kRangeCols);
+                // the thread's columns of the tile row in registers, then the buffer goes back to the MMA
+                uint32_t r[kChunks][32];
 #pragma unroll
-                for (int ch = 0; ch < 4; ++ch) tmem_ld32(tbase + 32 * ch, r[ch]);
+                for (int ch = 0; ch < kChunks; ++ch) tmem_ld32(tbase + 32 * ch, r[ch]);
 #pragma unroll
-                for (int ch = 0; ch < 4; ++ch) tmem_wait(r[ch]);
+                for (int ch = 0; ch < kChunks; ++ch) tmem_wait(r[ch]);
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(smem_u32(&tempty[b]));
 #pragma unroll
-                for (int ch = 0; ch < 4; ++ch) {
+                for (int ch = 0; ch < kChunks; ++ch) {
                     float dv[32];
 #pragma unroll
                     for (int i = 0; i < 32; ++i) dv[i] = __uint_as_float(r[ch][i]);
@@ -528,7 +536,7 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
             }
             if (!ok) break;
             if (kPass == 1 && live)
-                p.pm[((long long)split * 2 + half) * p.NA + row] = make_float2(1.f - 2.f * d1, 1.f - 2.f * d2);
+                p.pm[((long long)split * kRanges + rg) * p.NA + row] = make_float2(1.f - 2.f * d1, 1.f - 2.f * d2);
             if (kPass == 2 && live) p.ncand[sub] = nc;
         }
     }
@@ -596,7 +604,7 @@ __global__ void k_row_threshold(const float2* pm, int S, long long NA, const uin
     thr[i] = vA[i] ? fminf(m2 + kMargin, kCandCap) : -INFINITY;
 }
 
-// One warp per row: every candidate of the row's 2S sub-lists is re-scored
+// One warp per row: every candidate of the row's kRanges S sub-lists is re-scored
 // with exactly the FP32 form's arithmetic, and the top 2 kept by (value,
 // column).  Every column outside the lists has a BF16 value > window_top(x)
 // and so an FP32-form value > x: the row is certified when its exact
@@ -837,10 +845,10 @@ TcLayout tc_layout(long long NA, long long NB, int sms)
     auto take = [&](size_t bytes) { size_t r = o; o += (bytes + 255) & ~size_t(255); return r; };
     L.off_na = take(sizeof(float) * (size_t)NA);
     L.off_nb32 = take(sizeof(float) * (size_t)NB);
-    L.off_pm = take(sizeof(float2) * 2 * (size_t)L.S * NA);
+    L.off_pm = take(sizeof(float2) * kRanges * (size_t)L.S * NA);
     L.off_thr = take(sizeof(float) * (size_t)NA);
-    L.off_cand = take(sizeof(int32_t) * kSubCap * 2 * (size_t)L.S * NA);
-    L.off_ncand = take(sizeof(int32_t) * 2 * (size_t)L.S * NA);
+    L.off_cand = take(sizeof(int32_t) * kSubCap * kRanges * (size_t)L.S * NA);
+    L.off_ncand = take(sizeof(int32_t) * kRanges * (size_t)L.S * NA);
     L.off_part1 = take(sizeof(float4) * (size_t)NA);
     L.off_rows = take(sizeof(int32_t) * (size_t)NA);
     L.off_cnt = take(64);
@@ -930,7 +938,7 @@ cudaError_t launch_match_bf16(const MatchArgs& a, void* ws, size_t ws_bytes, int
         TcParams p1 = p;
         p1.tstride = kPass1Stride;
         k_match_tc<1><<<grid, kThreadsTC, kSmemTC, s>>>(tA, tB, p1);
-        k_row_threshold<<<(unsigned)((a.NA + 255) / 256), 256, 0, s>>>(pm, 2 * L.S, a.NA, a.vA, thr);
+        k_row_threshold<<<(unsigned)((a.NA + 255) / 256), 256, 0, s>>>(pm, kRanges * L.S, a.NA, a.vA, thr);
         k_match_tc<2><<<grid, kThreadsTC, kSmemTC, s>>>(tA, tB, p);
         if (a.ev1) cudaEventRecord(a.ev1, s);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -938,7 +946,7 @@ cudaError_t launch_match_bf16(const MatchArgs& a, void* ws, size_t ws_bytes, int
                        (e = cudaStreamWaitEvent(s, a.fork->join_ev[0], 0)) != cudaSuccess))
             return e;
         k_rerank<<<(unsigned)((a.NA + kRerankWarps - 1) / kRerankWarps), kRerankWarps * 32, 0, s>>>(
-            a.dA, a.vA, a.dB, nb32, cand, ncand, 2 * L.S, thr, a.NA, part1, rows, cnt);
+            a.dA, a.vA, a.dB, nb32, cand, ncand, kRanges * L.S, thr, a.NA, part1, rows, cnt);
         if ((e = cudaFuncSetAttribute(k_rescan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRescanSmem)) !=
             cudaSuccess)
             return e;
