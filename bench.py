@@ -562,7 +562,10 @@ def main():
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(secs) / len(secs),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                 "data": "synthetic", "config": {"workload": WORKLOAD, "H": H_IMG, "W": W_IMG, "Ls": list(LS),
-                                                "flush": "n/a (CPU)"},
+                                                "flush": "n/a (CPU)",
+                                                "timing": "sample-scaled: each step times a bounded sample of "
+                                                          "the pair and scales it to the whole pair (see "
+                                                          "cpu_baseline.sample); not a full-pair measurement"},
                 "cpu_baseline": {"value": v, "unit": "pairs/s", "cores": 1, "kind": "oracle", "sample": sample},
                 "e2e": {"value": v, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line))

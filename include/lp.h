@@ -209,9 +209,9 @@ LP_API int lp_ransac(lp_ctx* ctx, const float* pts, int64_t M_cap, const int32_t
  *
  * Arguments are those of lp_ransac, with the configuration values passed
  * directly: iters = T (1..LP_RANSAC_STATIC_MAX_ITERS; more returns
- * LP_ERR_ARG), thresh_px, seed and pair_id.  The model is the homography
- * (Eq. 7).  The results equal lp_ransac's for the same inputs and
- * configuration.
+ * LP_ERR_ARG), thresh_px, seed and pair_id.  The model is the full
+ * 8-parameter homography.  The results equal lp_ransac's for the same inputs
+ * and configuration.
  *
  * The first call on each device looks up the array's device address (once per
  * device, with that device current); make that first call before any stream
