@@ -14,6 +14,11 @@
 // memory and reduced per row segment of the finest window.  Finest-window
 // extrema follow, then each coarser level combines its children.
 // General path: one CTA per window per scale (any L set, any Lmax).
+#include <cudaTypedefs.h>
+#include <string.h>
+
+#include <algorithm>
+
 #include "lp_internal.cuh"
 
 namespace lp {
@@ -275,6 +280,275 @@ __global__ void __launch_bounds__(kDetectThreads) k_detect_nested_batch(const __
     detect_tile<CH>(b.im[i], bx, by);
 }
 
+// ------------------------------------------------------------------ TMA-fed fast path
+// Nested scales drawn from {16, 32, 64, 128} with 16 the finest, 8-bit gray
+// or RGB input.  Persistent CTAs (one per SM) walk a flat list of 128 x 128
+// tiles of up to kDetectBatch images.  Warp 8 streams whole tiles into a
+// 4-stage shared-memory ring with cp.async.bulk.tensor (one 2-D box of
+// 128 rows x 128 pixels, out-of-image bytes zero-filled); warps 0-3 and 4-7
+// are two groups that take alternate tiles (group g uses stages g and g + 2).
+// In a group, warp w holds pixel rows [32 w, 32 w + 32) of the tile and lane
+// (h, r, c) = (lane >> 4, (lane >> 3) & 1, lane & 7) holds the 8 x 16 strip at
+// rows 32 w + 16 r + 8 h, columns 16 c: it converts RGB to intensity, writes
+// the intensity, and reduces the keys of its strip in registers.  The
+// 16-pixel windows follow from one shuffle (xor 16), the 32-pixel windows
+// from two more (xor 1, xor 8), the 64-pixel half windows from one more
+// (xor 2); warp 0 of the group combines the four warps' halves, handed over
+// in shared memory, into the 64- and 128-pixel windows.  A window that is not
+// full is dropped at output, so out-of-image pixels never reach a kept key.
+// Every wait is bounded (2 s): on expiry the CTA records LP_ERR_TIMEOUT, lets
+// its copies in flight land and returns.
+constexpr int kTmaTile = 128;
+constexpr int kTmaStages = 4;
+constexpr int kTmaThreads = 288;   // 8 compute warps + 1 producer warp
+
+struct TmaImage {
+    uint8_t* gray;          // intensity output (RGB input) or nullptr
+    uint32_t* kp;
+    int H, W;
+    int tiles_x;
+    int nwx[4], nwy[4];     // windows per row / column at L = 16, 32, 64, 128 (0: scale not requested)
+    long long off[4];       // first keypoint of each of those scales
+};
+
+struct DetectTmaBatch {
+    CUtensorMap map[kDetectBatch];   // 2-D, 4-byte elements: {pitch / 4, H}, box {32 CH, 128}
+    TmaImage im[kDetectBatch];
+    int tile0[kDetectBatch + 1];     // prefix sums of the images' tile counts
+    int n;
+    int32_t* status;
+};
+
+__device__ __forceinline__ uint32_t d_smem_u32(const void* p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ bool d_mbar_try(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ void d_mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ uint64_t d_globaltimer()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait: true when the phase completed, false on abort or after 2 s.
+__device__ __forceinline__ bool d_mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, int32_t* status)
+{
+    if (d_mbar_try(bar, parity)) return true;
+    const uint64_t t0 = d_globaltimer();
+    for (uint32_t it = 1;; ++it) {
+        if (d_mbar_try(bar, parity)) return true;
+        if ((it & 255u) == 0) {
+            if (*abort_flag) return false;
+            if (d_globaltimer() - t0 > 2000000000ull) {
+                *abort_flag = 1;
+                set_status(status, DEV_TIMEOUT);
+                return false;
+            }
+        }
+    }
+}
+
+// Global tile t -> (image, tile column, tile row).
+__device__ __forceinline__ void tma_tile(const DetectTmaBatch& b, int t, int& i, int& tx, int& ty)
+{
+    i = 0;
+    while (i + 1 < b.n && t >= b.tile0[i + 1]) ++i;
+    const int lt = t - b.tile0[i];
+    ty = lt / b.im[i].tiles_x;
+    tx = lt - ty * b.im[i].tiles_x;
+}
+
+__device__ __forceinline__ void key_max_min(uint32_t& kmax, uint32_t& kmin, uint32_t omax, uint32_t omin)
+{
+    kmax = max(kmax, omax);
+    kmin = min(kmin, omin);
+}
+
+__device__ __forceinline__ void shfl_key(uint32_t& kmax, uint32_t& kmin, int lanemask)
+{
+    key_max_min(kmax, kmin, __shfl_xor_sync(0xFFFFFFFFu, kmax, lanemask), __shfl_xor_sync(0xFFFFFFFFu, kmin, lanemask));
+}
+
+// Window (gx, gy) of scale slot l: written when the window is full.
+__device__ __forceinline__ void put_key(const TmaImage& im, int l, int gx, int gy, uint32_t kmax, uint32_t kmin)
+{
+    if (gx < im.nwx[l] && gy < im.nwy[l])
+        *reinterpret_cast<uint2*>(im.kp + im.off[l] + 2ll * ((long long)gy * im.nwx[l] + gx)) =
+            make_uint2(kmax & 0xFFFFFFu, kmin & 0xFFFFFFu);
+}
+
+template <int CH>
+__global__ void __launch_bounds__(kTmaThreads, 1) k_detect_tma(const __grid_constant__ DetectTmaBatch b)
+{
+    constexpr uint32_t kStageBytes = kTmaTile * kTmaTile * CH;   // 48 KB (RGB) or 16 KB (gray)
+    extern __shared__ uint8_t dsm_raw[];
+    uint8_t* dsm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(dsm_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t* full = reinterpret_cast<uint64_t*>(dsm + kTmaStages * kStageBytes);
+    uint64_t* empty = full + kTmaStages;
+    uint64_t* xfull = empty + kTmaStages;    // [2 groups][2 buffers]: the four warps' halves are written
+    uint64_t* xempty = xfull + 4;            // [2 groups][2 buffers]: warp 0 of the group has read them
+    uint32_t* xch = reinterpret_cast<uint32_t*>(xempty + 4);   // [2 groups][2 buffers][4 warps][2 halves][2]
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(xch + 2 * 2 * 4 * 2 * 2);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int T = b.tile0[b.n];
+    const int G = (int)gridDim.x;
+    const int ntile = (int)blockIdx.x < T ? (T - (int)blockIdx.x + G - 1) / G : 0;   // this CTA's tiles
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kTmaStages; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(d_smem_u32(&full[s])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(d_smem_u32(&empty[s])) : "memory");
+        }
+        for (int q = 0; q < 4; ++q) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(d_smem_u32(&xfull[q])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(d_smem_u32(&xempty[q])) : "memory");
+        }
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    if (warp == 8) {
+        // ------------------------------------------------------------ producer
+        if (lane == 0) {
+            int armed[kTmaStages];
+            for (int s = 0; s < kTmaStages; ++s) armed[s] = -1;
+            bool ok = true;
+            for (int n = 0; n < ntile && ok; ++n) {
+                const int s = n % kTmaStages;
+                const uint32_t k = (uint32_t)(n / kTmaStages);
+                ok = d_mbar_wait(d_smem_u32(&empty[s]), (k & 1) ^ 1, abort_flag, b.status);
+                if (!ok) break;
+                int i, tx, ty;
+                tma_tile(b, (int)blockIdx.x + n * G, i, tx, ty);
+                const uint32_t bar = d_smem_u32(&full[s]);
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kStageBytes)
+                             : "memory");
+                asm volatile(
+                    "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+                    "[%0], [%1, {%2, %3}], [%4];" ::"r"(d_smem_u32(dsm + s * kStageBytes)),
+                    "l"(reinterpret_cast<uint64_t>(&b.map[i])), "r"(tx * 32 * CH), "r"(ty * kTmaTile), "r"(bar)
+                    : "memory");
+                armed[s] = (int)k;
+            }
+            if (!ok) {
+                // let the copies in flight land (bounded) before the CTA exits
+                for (int s = 0; s < kTmaStages; ++s) {
+                    if (armed[s] < 0) continue;
+                    const uint64_t t0 = d_globaltimer();
+                    while (!d_mbar_try(d_smem_u32(&full[s]), (uint32_t)armed[s] & 1u) &&
+                           d_globaltimer() - t0 < 200000000ull) {
+                    }
+                }
+            }
+        }
+        return;
+    }
+
+    // ---------------------------------------------------------------- compute groups
+    const int grp = warp >> 2, wg = warp & 3;
+    const int h = lane >> 4, rr = (lane >> 3) & 1, c = lane & 7;
+    const int row0 = 32 * wg + 16 * rr + 8 * h;      // first tile row of this lane's strip
+    for (int n = grp; n < ntile; n += 2) {
+        const int s = n % kTmaStages;
+        const uint32_t k = (uint32_t)(n / kTmaStages);
+        // every lane waits; the warp acts on one decision (they differ only
+        // after a timeout)
+        if (!__all_sync(0xFFFFFFFFu, d_mbar_wait(d_smem_u32(&full[s]), k & 1, abort_flag, b.status))) break;
+        int i, tx, ty;
+        tma_tile(b, (int)blockIdx.x + n * G, i, tx, ty);
+        const TmaImage& im = b.im[i];
+        const int x0 = tx * kTmaTile + 16 * c;           // first column of the strip
+        const uint8_t* src = dsm + s * kStageBytes + row0 * (kTmaTile * CH) + 16 * CH * c;
+        uint32_t kmax = 0u, kmin = 0xFFFFFFFFu;
+        const bool gray_vec = CH == 3 && (im.W & 15) == 0;
+#pragma unroll 2
+        for (int r = 0; r < 8; ++r) {
+            const int y = ty * kTmaTile + row0 + r;
+            uint4 v;
+            if (CH == 1) {
+                v = *reinterpret_cast<const uint4*>(src + r * kTmaTile);
+            } else {
+                const uint4* q = reinterpret_cast<const uint4*>(src + r * kTmaTile * 3);
+                v = gray16(q[0], q[1], q[2]);
+                if (y < im.H && x0 < im.W) {
+                    uint8_t* gout = im.gray + (size_t)y * im.W + x0;
+                    if (gray_vec) {
+                        *reinterpret_cast<uint4*>(gout) = v;
+                    } else {
+                        const int nb = min(16, im.W - x0);
+                        for (int j = 0; j < nb; ++j) gout[j] = byte_of(v, j);
+                    }
+                }
+            }
+            uint32_t gmax, gmin;
+            group_keys(v, (uint32_t)y * (uint32_t)im.W + (uint32_t)x0, gmax, gmin);
+            key_max_min(kmax, kmin, gmax, gmin);
+        }
+        // the stage is no longer read: hand it back to the producer
+        __syncwarp();
+        if (lane == 0) d_mbar_arrive(d_smem_u32(&empty[s]));
+
+        // 16-pixel windows: the two 8-row strips (lanes xor 16)
+        shfl_key(kmax, kmin, 16);
+        const int wy16 = ty * 8 + 2 * wg + rr, wx16 = tx * 8 + c;
+        if (h == 0 && im.nwx[0]) put_key(im, 0, wx16, wy16, kmax, kmin);
+        // 32-pixel windows: column pairs (xor 1) and row pairs (xor 8)
+        shfl_key(kmax, kmin, 1);
+        shfl_key(kmax, kmin, 8);
+        if (h == 0 && rr == 0 && (c & 1) == 0 && im.nwx[1]) put_key(im, 1, wx16 >> 1, wy16 >> 1, kmax, kmin);
+        // 64-pixel half windows (this warp's 32 rows): column quads (xor 2)
+        shfl_key(kmax, kmin, 2);
+        // hand the two halves to warp 0 of the group through buffer xb (one of
+        // two, alternating over the group's tiles); every wait is bounded
+        const int m = n >> 1, xb = grp * 2 + (m & 1);
+        const uint32_t use = (uint32_t)(m >> 1);
+        if (!__all_sync(0xFFFFFFFFu, d_mbar_wait(d_smem_u32(&xempty[xb]), (use & 1) ^ 1, abort_flag, b.status)))
+            break;
+        uint32_t* x = xch + (xb * 4 + wg) * 4;   // [half][max, min]
+        if (lane == 0) { x[0] = kmax; x[1] = kmin; }
+        if (lane == 4) { x[2] = kmax; x[3] = kmin; }
+        __syncwarp();
+        if (lane == 0) d_mbar_arrive(d_smem_u32(&xfull[xb]));
+        if (wg == 0) {
+            if (!__all_sync(0xFFFFFFFFu, d_mbar_wait(d_smem_u32(&xfull[xb]), use & 1, abort_flag, b.status))) break;
+            // lane j (mod 4): the 64-pixel window at column j & 1, row (j >> 1) & 1,
+            // from the halves of warps 2 hr and 2 hr + 1
+            const uint32_t* xr = xch + xb * 16;
+            const int hc = lane & 1, hr = (lane >> 1) & 1;
+            uint32_t m0 = xr[(2 * hr) * 4 + 2 * hc], n0 = xr[(2 * hr) * 4 + 2 * hc + 1];
+            key_max_min(m0, n0, xr[(2 * hr + 1) * 4 + 2 * hc], xr[(2 * hr + 1) * 4 + 2 * hc + 1]);
+            __syncwarp();
+            if (lane == 0) d_mbar_arrive(d_smem_u32(&xempty[xb]));
+            if (lane < 4 && im.nwx[2]) put_key(im, 2, tx * 2 + hc, ty * 2 + hr, m0, n0);
+            // 128-pixel window: the four 64-pixel windows (every lane quad holds them)
+            shfl_key(m0, n0, 1);
+            shfl_key(m0, n0, 2);
+            if (lane == 0 && im.nwx[3]) put_key(im, 3, tx, ty, m0, n0);
+        }
+    }
+}
+
 // General path: one CTA per full window of one scale.
 template <int CH>
 __global__ void __launch_bounds__(kDetectThreads) k_detect_window(const uint8_t* img, int H, int W, int pitch,
@@ -416,15 +690,87 @@ size_t fill_nested(DetectParams& p, const uint8_t* img, int H, int W, int pitch,
     return (size_t)TS * TS + 8u * nseg + 8u * acc;
 }
 
+// The TMA path takes scale sets drawn from {16, 32, 64, 128} with 16 the finest.
+bool tma_scales(const ScaleTable& st)
+{
+    if (st.nL < 1 || st.L[0] != 16) return false;
+    for (int l = 0; l < st.nL; ++l)
+        if (st.L[l] != 16 && st.L[l] != 32 && st.L[l] != 64 && st.L[l] != 128) return false;
+    return true;
+}
+
+size_t tma_smem(int ch) { return (size_t)kTmaStages * kTmaTile * kTmaTile * ch + 1024 + 512; }
+
+// Up to N images in launches of kDetectBatch on the TMA path.
+cudaError_t launch_detect_tma(const uint8_t* const* imgs, const int* Hs, const int* Ws, const int* pitches, int N,
+                              int ch, const ScaleTable* sts, uint32_t* const* kps, uint8_t* const* grays,
+                              int32_t* status, int num_sms, cudaStream_t s)
+{
+    const size_t smem = tma_smem(ch);
+    cudaError_t e;
+    auto kern = ch == 1 ? k_detect_tma<1> : k_detect_tma<3>;
+    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+        return e;
+    int per_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTmaThreads, smem)) != cudaSuccess)
+        return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    for (int i0 = 0; i0 < N; i0 += kDetectBatch) {
+        DetectTmaBatch b;
+        memset(&b, 0, sizeof b);
+        b.n = N - i0 < kDetectBatch ? N - i0 : kDetectBatch;
+        b.status = status;
+        b.tile0[0] = 0;
+        for (int k = 0; k < b.n; ++k) {
+            const int i = i0 + k;
+            const ScaleTable& st = sts[i];
+            // the image as rows of pitch / 4 four-byte elements; a box is one tile
+            if (!encode_tiled_2d(&b.map[k], CU_TENSOR_MAP_DATA_TYPE_UINT32, imgs[i], (uint64_t)pitches[i] / 4,
+                                 (uint64_t)Hs[i], (uint64_t)pitches[i], 32u * ch, kTmaTile, CU_TENSOR_MAP_SWIZZLE_NONE))
+                return cudaErrorInvalidValue;
+            TmaImage& im = b.im[k];
+            im.gray = grays ? grays[i] : nullptr;
+            im.kp = kps[i];
+            im.H = Hs[i];
+            im.W = Ws[i];
+            im.tiles_x = (Ws[i] + kTmaTile - 1) / kTmaTile;
+            for (int l = 0; l < st.nL; ++l) {
+                const int slot = st.L[l] == 16 ? 0 : st.L[l] == 32 ? 1 : st.L[l] == 64 ? 2 : 3;
+                im.nwx[slot] = st.nwx[l];
+                im.nwy[slot] = st.nwx[l] > 0 ? st.nwy[l] : 0;
+                im.off[slot] = st.off[l];
+            }
+            b.tile0[k + 1] = b.tile0[k] + im.tiles_x * ((Hs[i] + kTmaTile - 1) / kTmaTile);
+        }
+        const int T = b.tile0[b.n];
+        if (T == 0) continue;
+        const int grid = std::min(T, per_sm * num_sms);
+        if (ch == 1)
+            k_detect_tma<1><<<grid, kTmaThreads, smem, s>>>(b);
+        else
+            k_detect_tma<3><<<grid, kTmaThreads, smem, s>>>(b);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 }  // namespace
 
 cudaError_t launch_detect_batch(const uint8_t* const* imgs, const int* Hs, const int* Ws, const int* pitches, int N,
                                 int ch, const ScaleTable* sts, uint32_t* const* kps, uint8_t* const* grays,
-                                cudaStream_t s, bool* done)
+                                int32_t* status, int num_sms, cudaStream_t s, bool* done)
 {
     *done = false;
+    if (N < 1) return cudaSuccess;
+    bool tma = true;
+    for (int i = 0; i < N && tma; ++i) tma = tma_scales(sts[i]) && Hs[i] >= kTmaTile && pitches[i] >= kTmaTile * ch;
+    if (tma) {
+        const cudaError_t e = launch_detect_tma(imgs, Hs, Ws, pitches, N, ch, sts, kps, grays, status, num_sms, s);
+        *done = e == cudaSuccess;
+        return e;
+    }
     int TS = 0;
-    if (N < 1 || !nested_tile(sts[0], &TS)) return cudaSuccess;   // the caller detects image by image
+    if (!nested_tile(sts[0], &TS)) return cudaSuccess;   // the caller detects image by image
     for (int i0 = 0; i0 < N; i0 += kDetectBatch) {
         DetectBatch b;
         b.n = N - i0 < kDetectBatch ? N - i0 : kDetectBatch;
@@ -458,8 +804,10 @@ cudaError_t launch_detect_batch(const uint8_t* const* imgs, const int* Hs, const
 }
 
 cudaError_t launch_detect(const uint8_t* img, int H, int W, int pitch, int ch, const ScaleTable& st, double alpha,
-                          uint32_t* kp, uint8_t* gray, cudaStream_t s)
+                          uint32_t* kp, uint8_t* gray, int32_t* status, int num_sms, cudaStream_t s)
 {
+    if (alpha == 0.0 && tma_scales(st) && H >= kTmaTile && pitch >= kTmaTile * ch)
+        return launch_detect_tma(&img, &H, &W, &pitch, 1, ch, &st, &kp, &gray, status, num_sms, s);
     if (alpha > 0.0) {
         if (ch == 3) k_rgb_to_gray<<<1216, 256, 0, s>>>(img, H, W, pitch, gray);
         for (int l = 0; l < st.nL; ++l) {

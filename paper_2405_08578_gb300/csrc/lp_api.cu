@@ -314,7 +314,8 @@ int lp_detect(lp_ctx* c, const uint8_t* img, int H, int W, int pitch, int channe
     lp::ScaleTable st;
     lp::make_scale_table(c->cfg.Ls, c->cfg.nL, c->cfg.beta0, H, W, &st);
     c->last = S(stream);
-    LP_CUDA(c, lp::launch_detect(img, H, W, pitch, channels, st, c->cfg.alpha, kp_idx, gray, S(stream)));
+    LP_CUDA(c, lp::launch_detect(img, H, W, pitch, channels, st, c->cfg.alpha, kp_idx, gray, c->d_status, c->num_sms,
+                                 S(stream)));
     return LP_OK;
 }
 
@@ -346,7 +347,7 @@ int lp_detect_batch(lp_ctx* c, const lp_image* imgs, int N, uint32_t* const* kp_
             src[i] = imgs[i].data; Hs[i] = imgs[i].H; Ws[i] = imgs[i].W; ps[i] = imgs[i].pitch;
         }
         LP_CUDA(c, lp::launch_detect_batch(src.data(), Hs.data(), Ws.data(), ps.data(), N, ch, st.data(), kp_idx,
-                                           gray, S(stream), &done));
+                                           gray, c->d_status, c->num_sms, S(stream), &done));
     }
     for (int i = 0; i < N && !done; ++i) {
         int r = lp_detect(c, imgs[i].data, imgs[i].H, imgs[i].W, imgs[i].pitch, ch, kp_idx[i], gray[i], stream);
@@ -511,16 +512,24 @@ int stitch_pair_impl(lp_ctx* c, const uint8_t* imgA, int HA, int WA, int pitchA,
     const uint8_t* gA = channels == 3 ? (const uint8_t*)P(B_GRAY_A) : imgA;
     const uint8_t* gB = channels == 3 ? (const uint8_t*)P(B_GRAY_B) : imgB;
     const int gpA = channels == 3 ? WA : pitchA, gpB = channels == 3 ? WB : pitchB;
-    // image B on the context's image stream, beside image A on the caller's
-    // stream; joined back before matching
+    // both images' peaks in one launch on the caller's stream (after image B's
+    // upload when that is queued on the image stream); then image B's
+    // description on the context's image stream beside image A's, joined back
+    // before matching
     if ((r = ensure_fork(c))) return r;
     void* sB = c->img_stream;
-    if (!b_queued) {
-        LP_CUDA(c, cudaEventRecord(c->img_ev[0], S(stream)));
-        LP_CUDA(c, cudaStreamWaitEvent(c->img_stream, c->img_ev[0], 0));
+    if (b_queued) {
+        LP_CUDA(c, cudaEventRecord(c->img_ev[0], c->img_stream));
+        LP_CUDA(c, cudaStreamWaitEvent(S(stream), c->img_ev[0], 0));
     }
-    if ((r = lp_detect(c, imgA, HA, WA, pitchA, channels, (uint32_t*)P(B_KP_A), (uint8_t*)P(B_GRAY_A), stream))) return r;
-    if ((r = lp_detect(c, imgB, HB, WB, pitchB, channels, (uint32_t*)P(B_KP_B), (uint8_t*)P(B_GRAY_B), sB))) return r;
+    {
+        const lp_image ims[2] = {{imgA, HA, WA, pitchA, channels}, {imgB, HB, WB, pitchB, channels}};
+        uint32_t* const kps[2] = {(uint32_t*)P(B_KP_A), (uint32_t*)P(B_KP_B)};
+        uint8_t* const grs[2] = {(uint8_t*)P(B_GRAY_A), (uint8_t*)P(B_GRAY_B)};
+        if ((r = lp_detect_batch(c, ims, 2, kps, grs, stream))) return r;
+    }
+    LP_CUDA(c, cudaEventRecord(c->img_ev[0], S(stream)));
+    LP_CUDA(c, cudaStreamWaitEvent(c->img_stream, c->img_ev[0], 0));
     if ((r = lp_describe(c, gA, HA, WA, gpA, (const uint32_t*)P(B_KP_A), KA, (uint8_t*)P(B_ORI_A), (float*)P(B_DESC_A),
                          bf ? (uint16_t*)P(B_D16_A) : nullptr, (uint8_t*)P(B_VAL_A), stream)))
         return r;

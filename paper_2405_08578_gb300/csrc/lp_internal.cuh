@@ -1,5 +1,6 @@
 // Internal declarations of liblp (GB300 / sm_103a).  Not part of the C ABI.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -29,6 +30,13 @@ struct ScaleTable {
 // Host-side construction (lp_api.cu).
 int make_scale_table(const int* Ls, int nL, double beta0, int H, int W, ScaleTable* st);
 
+// 2-D tiled TMA descriptor of a row-major array: `inner` elements per row,
+// `outer` rows, `row_bytes` between rows, box {box_inner, box_outer}; no
+// interleave, out-of-range elements read as zero.  false when the driver
+// entry point is missing or rejects the arguments (k_match_tc.cu).
+bool encode_tiled_2d(CUtensorMap* m, CUtensorMapDataType dt, const void* base, uint64_t inner, uint64_t outer,
+                     uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer, CUtensorMapSwizzle swizzle);
+
 // ---- kernel launchers (each .cu file owns its kernels) ----
 // Two auxiliary streams a launcher may fork independent launches onto; it
 // joins them back to its own stream before returning (graph capture follows).
@@ -39,15 +47,16 @@ struct Fork {
 
 // k_detect.cu
 // alpha > 0: Eq. 1's literal FP64 ramp (one launch per scale); 0: integer keys
+// status: the device status word (bounded waits of the TMA path); num_sms: the device's SM count
 cudaError_t launch_detect(const uint8_t* img, int H, int W, int pitch, int ch, const ScaleTable& st, double alpha,
-                          uint32_t* kp, uint8_t* gray, cudaStream_t s);
+                          uint32_t* kp, uint8_t* gray, int32_t* status, int num_sms, cudaStream_t s);
 cudaError_t launch_diag_gray(const uint8_t* rgb, int64_t n, uint8_t* gray, cudaStream_t s);
 // N images with the same scales and channels in launches of up to 12 on the
 // fast path; *done = false (nothing launched) when the scales need the general
 // path, which the caller then runs image by image
 cudaError_t launch_detect_batch(const uint8_t* const* imgs, const int* Hs, const int* Ws, const int* pitches, int N,
                                 int ch, const ScaleTable* sts, uint32_t* const* kps, uint8_t* const* grays,
-                                cudaStream_t s, bool* done);
+                                int32_t* status, int num_sms, cudaStream_t s, bool* done);
 
 // k_describe.cu
 size_t describe_lut_bytes();

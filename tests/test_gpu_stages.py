@@ -344,19 +344,22 @@ def test_ransac_degenerate():
 E2E_NEAR = 5e-3
 
 
-def _e2e_near(od1, od2):
+def _e2e_near(om, od1, od2):
+    """Rows whose ratio test is within E2E_NEAR of its boundary, and accepted
+    rows whose runner-up is within E2E_NEAR of the nearest neighbour (a
+    rejected row stays rejected whichever of the two is nearer)."""
     fin = np.isfinite(od2)
-    return fin & ((np.abs(od1 - 0.8 * od2) <= E2E_NEAR) | (od2 - od1 <= E2E_NEAR))
+    return fin & ((np.abs(od1 - 0.8 * od2) <= E2E_NEAR) | ((om >= 0) & (od2 - od1 <= E2E_NEAR)))
 
 
 def _match_set_parity(m_gpu, om, od1, od2, label):
-    near = _e2e_near(od1, od2)
+    near = _e2e_near(om, od1, od2)
     ok = ~near
     diff = np.nonzero(m_gpu[ok] != om[ok])[0]
     print(f"{label}: {len(om)} rows, {int((om >= 0).sum())} oracle matches, {int(near.sum())} near-ties excluded, "
           f"{len(diff)} differing rows")
     assert len(diff) == 0, f"match[] differs from the oracle on {len(diff)} non-near-tie rows"
-    assert near.sum() <= max(3, 0.01 * len(om))
+    assert near.sum() <= max(3, 0.03 * len(om))
     return int(near.sum())
 
 
