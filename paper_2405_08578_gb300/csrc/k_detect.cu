@@ -40,9 +40,15 @@ struct DetectParams {
     int lvl_off[LP_MAX_SCALES + 1];   // start of each level's window keys in shared memory
 };
 
+// floor(s / 1000) for 0 <= s < 2^32 / 704: with C = ceil(2^32 / 1000) =
+// 4,294,968 and C * 1000 - 2^32 = 704, s C / 2^32 = s / 1000 + s 704 / (1000 2^32),
+// and the added term stays below 1/1000 for such s, so the high word of s C is
+// floor(s / 1000).  Intensity sums are at most 255,500.
+__device__ __forceinline__ uint32_t div1000(uint32_t s) { return __umulhi(s, 4294968u); }
+
 __device__ __forceinline__ uint8_t rgb2gray(uint32_t r, uint32_t g, uint32_t b)
 {
-    return (uint8_t)((299u * r + 587u * g + 114u * b + 500u) / 1000u);
+    return (uint8_t)div1000(299u * r + 587u * g + 114u * b + 500u);
 }
 
 __device__ __forceinline__ uint8_t byte_of(const uint4& v, int i)
@@ -58,15 +64,20 @@ __device__ __forceinline__ uint8_t byte_of(const uint4& v, int i)
 __device__ __forceinline__ uint4 gray16(const uint4& c0, const uint4& c1, const uint4& c2)
 {
     const uint32_t w[12] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w, c2.x, c2.y, c2.z, c2.w};
-    uint32_t o[4] = {0, 0, 0, 0};
+    uint32_t q[16];
 #pragma unroll
     for (int p = 0; p < 16; ++p) {
         const int i = (3 * p) >> 2, j = (3 * p) & 3;
         const uint32_t rgb = __byte_perm(w[i], i + 1 < 12 ? w[i + 1] : w[i],
                                          (uint32_t)(j | ((j + 1) << 4) | ((j + 2) << 8) | ((j + 3) << 12)));
-        const uint32_t s = __dp4a(rgb, 0x00724B2Bu, 500u) + (__dp4a(rgb, 0x00000201u, 0u) << 8);
-        o[p >> 2] |= (s / 1000u) << (8 * (p & 3));
+        q[p] = div1000(__dp4a(rgb, 0x00000201u, 0u) * 256u + __dp4a(rgb, 0x00724B2Bu, 500u));
     }
+    // four intensities (each < 256) per word: bytes (q0, q1, q2, q3)
+    uint32_t o[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        o[k] = __byte_perm(__byte_perm(q[4 * k], q[4 * k + 1], 0x0040u), __byte_perm(q[4 * k + 2], q[4 * k + 3], 0x0040u),
+                           0x5410u);
     return make_uint4(o[0], o[1], o[2], o[3]);
 }
 
@@ -283,24 +294,26 @@ __global__ void __launch_bounds__(kDetectThreads) k_detect_nested_batch(const __
 // ------------------------------------------------------------------ TMA-fed fast path
 // Nested scales drawn from {16, 32, 64, 128} with 16 the finest, 8-bit gray
 // or RGB input.  Persistent CTAs (one per SM) walk a flat list of 128 x 128
-// tiles of up to kDetectBatch images.  Warp 8 streams whole tiles into a
-// 4-stage shared-memory ring with cp.async.bulk.tensor (one 2-D box of
-// 128 rows x 128 pixels, out-of-image bytes zero-filled); warps 0-3 and 4-7
-// are two groups that take alternate tiles (group g uses stages g and g + 2).
-// In a group, warp w holds pixel rows [32 w, 32 w + 32) of the tile and lane
-// (h, r, c) = (lane >> 4, (lane >> 3) & 1, lane & 7) holds the 8 x 16 strip at
-// rows 32 w + 16 r + 8 h, columns 16 c: it converts RGB to intensity, writes
-// the intensity, and reduces the keys of its strip in registers.  The
-// 16-pixel windows follow from one shuffle (xor 16), the 32-pixel windows
-// from two more (xor 1, xor 8), the 64-pixel half windows from one more
-// (xor 2); warp 0 of the group combines the four warps' halves, handed over
-// in shared memory, into the 64- and 128-pixel windows.  A window that is not
-// full is dropped at output, so out-of-image pixels never reach a kept key.
-// Every wait is bounded (2 s): on expiry the CTA records LP_ERR_TIMEOUT, lets
-// its copies in flight land and returns.
+// tiles of up to kDetectBatch images.
+//   warp 16     streams whole tiles into a 4-stage shared-memory ring with
+//               cp.async.bulk.tensor (one 2-D box of 128 rows x 128 pixels,
+//               out-of-image bytes zero-filled).
+//   warps 0-15  all work on every tile: warp w holds pixel rows [8 w, 8 w + 8),
+//               lane (p, c) = (lane >> 3, lane & 7) the 2 x 16 strip at rows
+//               8 w + 2 p, columns 16 c.  A lane converts RGB to intensity,
+//               writes the intensity and reduces its keys in registers; two
+//               shuffles (xor 8, xor 16) give the 8 x 16 half windows, which
+//               go to shared memory (one of two buffers, alternating tiles).
+//   warp 17     combines the half windows into the 16-pixel windows and, with
+//               shuffles, the 32-, 64- and 128-pixel windows, and writes the
+//               keys of the requested scales.
+// A window that is not full is dropped at output, so out-of-image pixels
+// never reach a kept key.  Every wait is bounded (2 s): on expiry the CTA
+// records LP_ERR_TIMEOUT, lets its copies in flight land and returns.
 constexpr int kTmaTile = 128;
 constexpr int kTmaStages = 4;
-constexpr int kTmaThreads = 288;   // 8 compute warps + 1 producer warp
+constexpr int kTmaCompute = 16;                          // compute warps
+constexpr int kTmaThreads = 32 * (kTmaCompute + 2);      // + producer warp + reducer warp
 
 struct TmaImage {
     uint8_t* gray;          // intensity output (RGB input) or nullptr
@@ -404,10 +417,10 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_detect_tma(const __grid_cons
     uint8_t* dsm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(dsm_raw) + 1023) & ~uintptr_t(1023));
     uint64_t* full = reinterpret_cast<uint64_t*>(dsm + kTmaStages * kStageBytes);
     uint64_t* empty = full + kTmaStages;
-    uint64_t* xfull = empty + kTmaStages;    // [2 groups][2 buffers]: the four warps' halves are written
-    uint64_t* xempty = xfull + 4;            // [2 groups][2 buffers]: warp 0 of the group has read them
-    uint32_t* xch = reinterpret_cast<uint32_t*>(xempty + 4);   // [2 groups][2 buffers][4 warps][2 halves][2]
-    volatile int* abort_flag = reinterpret_cast<volatile int*>(xch + 2 * 2 * 4 * 2 * 2);
+    uint64_t* xfull = empty + kTmaStages;    // [2 buffers]: every compute warp wrote its half windows
+    uint64_t* xempty = xfull + 2;            // [2 buffers]: the reducer has read them
+    uint32_t* hw = reinterpret_cast<uint32_t*>(xempty + 2);   // [2 buffers][16 warps][8 columns][max, min]
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(hw + 2 * kTmaCompute * 8 * 2);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int T = b.tile0[b.n];
@@ -417,10 +430,12 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_detect_tma(const __grid_cons
     if (threadIdx.x == 0) {
         for (int s = 0; s < kTmaStages; ++s) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(d_smem_u32(&full[s])) : "memory");
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(d_smem_u32(&empty[s])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(d_smem_u32(&empty[s])), "r"(kTmaCompute)
+                         : "memory");
         }
-        for (int q = 0; q < 4; ++q) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(d_smem_u32(&xfull[q])) : "memory");
+        for (int q = 0; q < 2; ++q) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(d_smem_u32(&xfull[q])), "r"(kTmaCompute)
+                         : "memory");
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(d_smem_u32(&xempty[q])) : "memory");
         }
         *abort_flag = 0;
@@ -428,9 +443,11 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_detect_tma(const __grid_cons
     }
     __syncthreads();
 
-    if (warp == 8) {
+    if (warp == kTmaCompute) {
         // ------------------------------------------------------------ producer
         if (lane == 0) {
+            for (int i = 0; i < b.n; ++i)
+                asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&b.map[i])) : "memory");
             int armed[kTmaStages];
             for (int s = 0; s < kTmaStages; ++s) armed[s] = -1;
             bool ok = true;
@@ -465,11 +482,61 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_detect_tma(const __grid_cons
         return;
     }
 
-    // ---------------------------------------------------------------- compute groups
-    const int grp = warp >> 2, wg = warp & 3;
-    const int h = lane >> 4, rr = (lane >> 3) & 1, c = lane & 7;
-    const int row0 = 32 * wg + 16 * rr + 8 * h;      // first tile row of this lane's strip
-    for (int n = grp; n < ntile; n += 2) {
+    if (warp == kTmaCompute + 1) {
+        // ------------------------------------------------------------ reducer
+        // lane (q, c) = (lane >> 3, lane & 7): the 16-pixel windows at window
+        // rows q (set A) and q + 4 (set B), window column c
+        const int q = lane >> 3, c = lane & 7;
+        for (int n = 0; n < ntile; ++n) {
+            const int xb = n & 1;
+            const uint32_t use = (uint32_t)(n >> 1);
+            if (!__all_sync(0xFFFFFFFFu, d_mbar_wait(d_smem_u32(&xfull[xb]), use & 1, abort_flag, b.status))) break;
+            const uint32_t* hx = hw + xb * (kTmaCompute * 16);
+            // window row r = 16-pixel rows of half-window warps 2 r and 2 r + 1
+            uint32_t amax = max(hx[(2 * q) * 16 + 2 * c], hx[(2 * q + 1) * 16 + 2 * c]);
+            uint32_t amin = min(hx[(2 * q) * 16 + 2 * c + 1], hx[(2 * q + 1) * 16 + 2 * c + 1]);
+            uint32_t bmax = max(hx[(2 * q + 8) * 16 + 2 * c], hx[(2 * q + 9) * 16 + 2 * c]);
+            uint32_t bmin = min(hx[(2 * q + 8) * 16 + 2 * c + 1], hx[(2 * q + 9) * 16 + 2 * c + 1]);
+            __syncwarp();
+            if (lane == 0) d_mbar_arrive(d_smem_u32(&xempty[xb]));
+            int i, tx, ty;
+            tma_tile(b, (int)blockIdx.x + n * G, i, tx, ty);
+            const TmaImage& im = b.im[i];
+            if (im.nwx[0]) {
+                put_key(im, 0, tx * 8 + c, ty * 8 + q, amax, amin);
+                put_key(im, 0, tx * 8 + c, ty * 8 + q + 4, bmax, bmin);
+            }
+            // 32-pixel windows: column pairs (xor 1), row pairs (xor 8)
+            shfl_key(amax, amin, 1);
+            shfl_key(amax, amin, 8);
+            shfl_key(bmax, bmin, 1);
+            shfl_key(bmax, bmin, 8);
+            if (im.nwx[1] && (c & 1) == 0 && (q & 1) == 0) {
+                put_key(im, 1, tx * 4 + (c >> 1), ty * 4 + (q >> 1), amax, amin);
+                put_key(im, 1, tx * 4 + (c >> 1), ty * 4 + 2 + (q >> 1), bmax, bmin);
+            }
+            // 64-pixel windows: column quads (xor 2), row quads (xor 16); A is
+            // the top half of the tile, B the bottom half
+            shfl_key(amax, amin, 2);
+            shfl_key(amax, amin, 16);
+            shfl_key(bmax, bmin, 2);
+            shfl_key(bmax, bmin, 16);
+            if (im.nwx[2] && (c & 3) == 0 && q == 0) {
+                put_key(im, 2, tx * 2 + (c >> 2), ty * 2, amax, amin);
+                put_key(im, 2, tx * 2 + (c >> 2), ty * 2 + 1, bmax, bmin);
+            }
+            // 128-pixel window: both halves, both column halves (xor 4)
+            key_max_min(amax, amin, bmax, bmin);
+            shfl_key(amax, amin, 4);
+            if (im.nwx[3] && lane == 0) put_key(im, 3, tx, ty, amax, amin);
+        }
+        return;
+    }
+
+    // ---------------------------------------------------------------- compute warps
+    const int p = lane >> 3, c = lane & 7;
+    const int row0 = 8 * warp + 2 * p;               // first tile row of this lane's strip
+    for (int n = 0; n < ntile; ++n) {
         const int s = n % kTmaStages;
         const uint32_t k = (uint32_t)(n / kTmaStages);
         // every lane waits; the warp acts on one decision (they differ only
@@ -480,72 +547,55 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_detect_tma(const __grid_cons
         const TmaImage& im = b.im[i];
         const int x0 = tx * kTmaTile + 16 * c;           // first column of the strip
         const uint8_t* src = dsm + s * kStageBytes + row0 * (kTmaTile * CH) + 16 * CH * c;
-        uint32_t kmax = 0u, kmin = 0xFFFFFFFFu;
-        const bool gray_vec = CH == 3 && (im.W & 15) == 0;
-#pragma unroll 2
-        for (int r = 0; r < 8; ++r) {
-            const int y = ty * kTmaTile + row0 + r;
-            uint4 v;
+        const int y0 = ty * kTmaTile + row0;
+        // rows of the strip whose intensity is written (inside the image)
+        const int nrow = x0 < im.W ? max(0, min(2, im.H - y0)) : 0;
+        const uint32_t base = (uint32_t)y0 * (uint32_t)im.W + (uint32_t)x0;
+        uint4 v[2];
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
             if (CH == 1) {
-                v = *reinterpret_cast<const uint4*>(src + r * kTmaTile);
+                v[r] = *reinterpret_cast<const uint4*>(src + r * kTmaTile);
             } else {
-                const uint4* q = reinterpret_cast<const uint4*>(src + r * kTmaTile * 3);
-                v = gray16(q[0], q[1], q[2]);
-                if (y < im.H && x0 < im.W) {
-                    uint8_t* gout = im.gray + (size_t)y * im.W + x0;
-                    if (gray_vec) {
-                        *reinterpret_cast<uint4*>(gout) = v;
-                    } else {
-                        const int nb = min(16, im.W - x0);
-                        for (int j = 0; j < nb; ++j) gout[j] = byte_of(v, j);
-                    }
-                }
+                const uint4* qs = reinterpret_cast<const uint4*>(src + r * kTmaTile * 3);
+                v[r] = gray16(qs[0], qs[1], qs[2]);
             }
-            uint32_t gmax, gmin;
-            group_keys(v, (uint32_t)y * (uint32_t)im.W + (uint32_t)x0, gmax, gmin);
-            key_max_min(kmax, kmin, gmax, gmin);
         }
         // the stage is no longer read: hand it back to the producer
         __syncwarp();
         if (lane == 0) d_mbar_arrive(d_smem_u32(&empty[s]));
-
-        // 16-pixel windows: the two 8-row strips (lanes xor 16)
-        shfl_key(kmax, kmin, 16);
-        const int wy16 = ty * 8 + 2 * wg + rr, wx16 = tx * 8 + c;
-        if (h == 0 && im.nwx[0]) put_key(im, 0, wx16, wy16, kmax, kmin);
-        // 32-pixel windows: column pairs (xor 1) and row pairs (xor 8)
-        shfl_key(kmax, kmin, 1);
+        if (CH == 3) {
+            uint8_t* gout = im.gray + (size_t)y0 * im.W + x0;
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                if (r < nrow) {
+                    if ((im.W & 15) == 0) {
+                        *reinterpret_cast<uint4*>(gout + (size_t)r * im.W) = v[r];
+                    } else {
+                        const int nb = min(16, im.W - x0);
+                        for (int j = 0; j < nb; ++j) gout[(size_t)r * im.W + j] = byte_of(v[r], j);
+                    }
+                }
+            }
+        }
+        uint32_t kmax, kmin, omax, omin;
+        group_keys(v[0], base, kmax, kmin);
+        group_keys(v[1], base + (uint32_t)im.W, omax, omin);
+        key_max_min(kmax, kmin, omax, omin);
+        // 8 x 16 half windows: the four row pairs of a column (xor 8, xor 16)
         shfl_key(kmax, kmin, 8);
-        if (h == 0 && rr == 0 && (c & 1) == 0 && im.nwx[1]) put_key(im, 1, wx16 >> 1, wy16 >> 1, kmax, kmin);
-        // 64-pixel half windows (this warp's 32 rows): column quads (xor 2)
-        shfl_key(kmax, kmin, 2);
-        // hand the two halves to warp 0 of the group through buffer xb (one of
-        // two, alternating over the group's tiles); every wait is bounded
-        const int m = n >> 1, xb = grp * 2 + (m & 1);
-        const uint32_t use = (uint32_t)(m >> 1);
+        shfl_key(kmax, kmin, 16);
+        const int xb = n & 1;
+        const uint32_t use = (uint32_t)(n >> 1);
         if (!__all_sync(0xFFFFFFFFu, d_mbar_wait(d_smem_u32(&xempty[xb]), (use & 1) ^ 1, abort_flag, b.status)))
             break;
-        uint32_t* x = xch + (xb * 4 + wg) * 4;   // [half][max, min]
-        if (lane == 0) { x[0] = kmax; x[1] = kmin; }
-        if (lane == 4) { x[2] = kmax; x[3] = kmin; }
+        if (p == 0) {
+            uint32_t* h = hw + xb * (kTmaCompute * 16) + warp * 16 + 2 * c;
+            h[0] = kmax;
+            h[1] = kmin;
+        }
         __syncwarp();
         if (lane == 0) d_mbar_arrive(d_smem_u32(&xfull[xb]));
-        if (wg == 0) {
-            if (!__all_sync(0xFFFFFFFFu, d_mbar_wait(d_smem_u32(&xfull[xb]), use & 1, abort_flag, b.status))) break;
-            // lane j (mod 4): the 64-pixel window at column j & 1, row (j >> 1) & 1,
-            // from the halves of warps 2 hr and 2 hr + 1
-            const uint32_t* xr = xch + xb * 16;
-            const int hc = lane & 1, hr = (lane >> 1) & 1;
-            uint32_t m0 = xr[(2 * hr) * 4 + 2 * hc], n0 = xr[(2 * hr) * 4 + 2 * hc + 1];
-            key_max_min(m0, n0, xr[(2 * hr + 1) * 4 + 2 * hc], xr[(2 * hr + 1) * 4 + 2 * hc + 1]);
-            __syncwarp();
-            if (lane == 0) d_mbar_arrive(d_smem_u32(&xempty[xb]));
-            if (lane < 4 && im.nwx[2]) put_key(im, 2, tx * 2 + hc, ty * 2 + hr, m0, n0);
-            // 128-pixel window: the four 64-pixel windows (every lane quad holds them)
-            shfl_key(m0, n0, 1);
-            shfl_key(m0, n0, 2);
-            if (lane == 0 && im.nwx[3]) put_key(im, 3, tx, ty, m0, n0);
-        }
     }
 }
 
@@ -699,7 +749,7 @@ bool tma_scales(const ScaleTable& st)
     return true;
 }
 
-size_t tma_smem(int ch) { return (size_t)kTmaStages * kTmaTile * kTmaTile * ch + 1024 + 512; }
+size_t tma_smem(int ch) { return (size_t)kTmaStages * kTmaTile * kTmaTile * ch + 1024 + 2048; }
 
 // Up to N images in launches of kDetectBatch on the TMA path.
 cudaError_t launch_detect_tma(const uint8_t* const* imgs, const int* Hs, const int* Ws, const int* pitches, int N,
@@ -709,12 +759,20 @@ cudaError_t launch_detect_tma(const uint8_t* const* imgs, const int* Hs, const i
     const size_t smem = tma_smem(ch);
     cudaError_t e;
     auto kern = ch == 1 ? k_detect_tma<1> : k_detect_tma<3>;
-    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
-        return e;
-    int per_sm = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTmaThreads, smem)) != cudaSuccess)
-        return e;
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    // the shared-memory opt-in and the resident CTAs per SM, once per device
+    // and channel count (host calls that would otherwise precede every launch)
+    static int per_sm_cache[2][64];
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    int& per_sm = per_sm_cache[ch == 3][dev & 63];
+    if (per_sm == 0 || dev >= 64) {
+        if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+            return e;
+        int n = 0;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, kTmaThreads, smem)) != cudaSuccess) return e;
+        if (n < 1) return cudaErrorInvalidConfiguration;
+        per_sm = n;
+    }
     for (int i0 = 0; i0 < N; i0 += kDetectBatch) {
         DetectTmaBatch b;
         memset(&b, 0, sizeof b);
