@@ -337,15 +337,22 @@ __device__ __forceinline__ uint32_t d_smem_u32(const void* p)
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
+// One try of a phase wait.  The thread may be suspended for up to
+// kSuspendNs (it resumes as soon as the phase completes), so a waiting warp
+// takes few issue slots from the working ones.
+#ifndef LP_DETECT_SUSPEND_NS
+#define LP_DETECT_SUSPEND_NS 10000
+#endif
+constexpr uint32_t kSuspendNs = LP_DETECT_SUSPEND_NS;
 __device__ __forceinline__ bool d_mbar_try(uint32_t bar, uint32_t parity)
 {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(bar), "r"(parity)
+        : "r"(bar), "r"(parity), "r"(kSuspendNs)
         : "memory");
     return ok != 0;
 }
@@ -369,7 +376,7 @@ __device__ __forceinline__ bool d_mbar_wait(uint32_t bar, uint32_t parity, volat
     const uint64_t t0 = d_globaltimer();
     for (uint32_t it = 1;; ++it) {
         if (d_mbar_try(bar, parity)) return true;
-        if ((it & 255u) == 0) {
+        if ((it & 15u) == 0) {
             if (*abort_flag) return false;
             if (d_globaltimer() - t0 > 2000000000ull) {
                 *abort_flag = 1;
@@ -420,7 +427,9 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_detect_tma(const __grid_cons
     uint64_t* xfull = empty + kTmaStages;    // [2 buffers]: every compute warp wrote its half windows
     uint64_t* xempty = xfull + 2;            // [2 buffers]: the reducer has read them
     uint32_t* hw = reinterpret_cast<uint32_t*>(xempty + 2);   // [2 buffers][16 warps][8 columns][max, min]
-    volatile int* abort_flag = reinterpret_cast<volatile int*>(hw + 2 * kTmaCompute * 8 * 2);
+    int* hmeta = reinterpret_cast<int*>(hw + 2 * kTmaCompute * 8 * 2);   // [2 buffers][image, tile x, tile y]
+    int* tinfo = hmeta + 2 * 4;                                          // [stage][image, tile x, tile y]
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tinfo + kTmaStages * 4);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int T = b.tile0[b.n];
@@ -458,6 +467,10 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_detect_tma(const __grid_cons
                 if (!ok) break;
                 int i, tx, ty;
                 tma_tile(b, (int)blockIdx.x + n * G, i, tx, ty);
+                // the tile's place, for the compute warps (published by the arrival below)
+                tinfo[4 * s] = i;
+                tinfo[4 * s + 1] = tx;
+                tinfo[4 * s + 2] = ty;
                 const uint32_t bar = d_smem_u32(&full[s]);
                 asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kStageBytes)
                              : "memory");
@@ -497,10 +510,9 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_detect_tma(const __grid_cons
             uint32_t amin = min(hx[(2 * q) * 16 + 2 * c + 1], hx[(2 * q + 1) * 16 + 2 * c + 1]);
             uint32_t bmax = max(hx[(2 * q + 8) * 16 + 2 * c], hx[(2 * q + 9) * 16 + 2 * c]);
             uint32_t bmin = min(hx[(2 * q + 8) * 16 + 2 * c + 1], hx[(2 * q + 9) * 16 + 2 * c + 1]);
+            const int i = hmeta[4 * xb], tx = hmeta[4 * xb + 1], ty = hmeta[4 * xb + 2];
             __syncwarp();
             if (lane == 0) d_mbar_arrive(d_smem_u32(&xempty[xb]));
-            int i, tx, ty;
-            tma_tile(b, (int)blockIdx.x + n * G, i, tx, ty);
             const TmaImage& im = b.im[i];
             if (im.nwx[0]) {
                 put_key(im, 0, tx * 8 + c, ty * 8 + q, amax, amin);
@@ -542,8 +554,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_detect_tma(const __grid_cons
         // every lane waits; the warp acts on one decision (they differ only
         // after a timeout)
         if (!__all_sync(0xFFFFFFFFu, d_mbar_wait(d_smem_u32(&full[s]), k & 1, abort_flag, b.status))) break;
-        int i, tx, ty;
-        tma_tile(b, (int)blockIdx.x + n * G, i, tx, ty);
+        const int i = tinfo[4 * s], tx = tinfo[4 * s + 1], ty = tinfo[4 * s + 2];
         const TmaImage& im = b.im[i];
         const int x0 = tx * kTmaTile + 16 * c;           // first column of the strip
         const uint8_t* src = dsm + s * kStageBytes + row0 * (kTmaTile * CH) + 16 * CH * c;
@@ -593,6 +604,11 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_detect_tma(const __grid_cons
             uint32_t* h = hw + xb * (kTmaCompute * 16) + warp * 16 + 2 * c;
             h[0] = kmax;
             h[1] = kmin;
+        }
+        if (warp == 0 && lane == 0) {   // the tile's place, for the reducer
+            hmeta[4 * xb] = i;
+            hmeta[4 * xb + 1] = tx;
+            hmeta[4 * xb + 2] = ty;
         }
         __syncwarp();
         if (lane == 0) d_mbar_arrive(d_smem_u32(&xfull[xb]));
@@ -749,7 +765,9 @@ bool tma_scales(const ScaleTable& st)
     return true;
 }
 
-size_t tma_smem(int ch) { return (size_t)kTmaStages * kTmaTile * kTmaTile * ch + 1024 + 2048; }
+// the ring, up to 1 KB of alignment slack, then barriers (96 B), the half
+// windows (2 KB), the tile slots (96 B) and the abort flag: 4 KB reserved
+size_t tma_smem(int ch) { return (size_t)kTmaStages * kTmaTile * kTmaTile * ch + 1024 + 4096; }
 
 // Up to N images in launches of kDetectBatch on the TMA path.
 cudaError_t launch_detect_tma(const uint8_t* const* imgs, const int* Hs, const int* Ws, const int* pitches, int N,
