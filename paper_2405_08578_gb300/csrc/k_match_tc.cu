@@ -135,15 +135,22 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
 
+// One try of a phase wait; the thread may be suspended for up to kSuspendNs
+// (it resumes as soon as the phase completes), so waiting warps take few
+// issue slots from the epilogue.
+#ifndef LP_TC_SUSPEND_NS
+#define LP_TC_SUSPEND_NS 10000
+#endif
+constexpr uint32_t kSuspendNs = LP_TC_SUSPEND_NS;
 __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
 {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(bar), "r"(parity)
+        : "r"(bar), "r"(parity), "r"(kSuspendNs)
         : "memory");
     return ok != 0;
 }
@@ -167,7 +174,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
     const uint64_t t0 = globaltimer();
     for (uint32_t it = 1;; ++it) {
         if (mbar_try(bar, parity)) return true;
-        if ((it & 255u) == 0) {
+        if ((it & 15u) == 0) {
             if (*abort_flag) return false;
             if (globaltimer() - t0 > 2000000000ull) {   // 2 s
                 *abort_flag = 1;
