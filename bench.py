@@ -353,11 +353,36 @@ def fp32_form_and_batch(args, rank):
         t += a.elapsed_time(b) / 1e3
     out["batch_3x3"] = {"images": 9, "pairs": 36, "pairs_per_s": 36 * k / t, "ms_per_batch": 1e3 * t / k,
                         "valid_pairs": int(va.sum().item()), "graph": True}
+    # the same batch through the plain FP32 form (FP32 SIMT distances): the
+    # comparison the metric names, on identical work
+    ctx32 = lp.Context(Ls=LS, precision=lp.PREC_FP32)
+    HM32 = torch.zeros((36, 9), dtype=torch.float64, device="cuda")
+    ni32 = torch.zeros(36, dtype=torch.int32, device="cuda")
+    va32 = torch.zeros(36, dtype=torch.uint8, device="cuda")
+    for _ in range(2):
+        ctx32.lp_stitch_pairs(images, HM32, ni32, va32)
+    torch.cuda.synchronize()
+    k32 = max(3, k // 2)
+    t32 = 0.0
+    for _ in range(k32):
+        flush()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        ctx32.lp_stitch_pairs(images, HM32, ni32, va32)
+        b.record(s)
+        torch.cuda.synchronize()
+        t32 += a.elapsed_time(b) / 1e3
+    ref = {"pairs_per_s": 36 * k32 / t32, "bf16_pairs_per_s": 36 * k / t,
+           "HM": HM32.cpu().numpy().reshape(36, 3, 3), "n_in": ni32.cpu().numpy()}
+    out["batch_3x3_fp32"] = {"pairs_per_s": ref["pairs_per_s"], "ms_per_batch": 1e3 * t32 / k32,
+                             "valid_pairs": int(va32.sum().item()),
+                             "bf16_equals_fp32": bool(torch.equal(HM, HM32) and torch.equal(ni, ni32))}
+    del ctx32
     out["mosaic_3x3"] = mosaic(bt, images, ctx, HM, va, flush, k)
     out["detect_3x3"] = detect_batch(ctx, images, flush, k)
     out["table2"] = table2(flush)
     if args.train_pairs > 0:
-        out["learned_proposal"] = learned_proposal(args, bt, images, ctx, HM, ni, va, flush, k)
+        out["learned_proposal"] = learned_proposal(args, bt, images, ctx, HM, ni, va, flush, k, ref)
     return out
 
 
@@ -496,7 +521,26 @@ def table2(flush, k=10):
     return out
 
 
-def learned_proposal(args, bt, images, ctx, HM, ni, va, flush, k):
+def _training_pair(seed: int):
+    """One seeded 640x480 training pair (runs in a spawned worker process)."""
+    from paper_2405_08578_gb300 import synth
+    p = synth.pair_640x480_random(seed)
+    return p.A, p.B
+
+
+def training_pairs(seeds):
+    """The training pairs in seed order, generated on the host's cores by a
+    spawned process pool (no CUDA state is inherited) and streamed to the
+    caller as they are ready."""
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    seeds = list(seeds)
+    workers = max(1, min(16, (os.cpu_count() or 2) - 1))
+    with ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        yield from ex.map(_training_pair, seeds, chunksize=8)
+
+
+def learned_proposal(args, bt, images, ctx, HM, ni, va, flush, k, ref=None):
     """Train the inlier-probability network on seeded 640x480 pairs labelled by
     plain RANSAC, then run the nine-tile batch with it guiding RANSAC: the
     iterations each pair needs to reach plain RANSAC's best count, whether the
@@ -507,31 +551,76 @@ def learned_proposal(args, bt, images, ctx, HM, ni, va, flush, k):
     t0 = time.time()
     ctx_t = lp.Context(Ls=synth.PAIR_640x480_LS)
     seeds = range(1000, 1000 + args.train_pairs)
-    feat, label = proposal.collect(ctx_t, ((p.A, p.B) for p in map(synth.pair_640x480_random, seeds)))
+    feat, label = proposal.collect(ctx_t, training_pairs(seeds))
+    collect_s = time.time() - t0
     net = lp.Mlp(seed=0)
-    losses = proposal.train(net, feat, label, epochs=20, batch=4096, lr=3e-3)
-    train_s = time.time() - t0
+    # about 100 passes over 4096-match minibatches per 100k matches, at least 4 epochs
+    epochs = max(4, min(20, int(2.0e6 / max(1, feat.shape[0]))))
+    t1 = time.time()
+    losses = proposal.train(net, feat, label, epochs=epochs, batch=4096, lr=3e-3)
+    torch.cuda.synchronize()
+    train_s = time.time() - t1
     Tg, T = 64, ctx.cfg.ransac_iters
     feats = [lp.features(ctx, im) for im in bt.images]
     reach_u, reach_g, stopped, same, nvalid, q = [], [], 0, 0, 0, 0
+    inl_pts = {}          # pair -> plain RANSAC's inlier points (xA, yA)
+    dev_inl = 0.0         # guided vs plain H on plain's inliers, px
+    pms = []
     for a in range(9):
         for b in range(a + 1, 9):
             pm = proposal.pair_matches(ctx, feats[a], feats[b])
-            _, inl_u, n_u, _ = lp.ransac(ctx, pm.pts, q, pm.d_M)
+            pms.append(pm)
+            H_u, inl_u, n_u, _ = lp.ransac(ctx, pm.pts, q, pm.d_M)
             cu = ctx.lp_diag_last_ransac_counts(T)
             g = proposal.guided_ransac(ctx, net, pm, Tg, q, want_counts=True)
             q += 1
             if int(n_u.item()) < ctx.cfg.min_inliers:
                 continue
             nvalid += 1
+            sel = inl_u[:pm.M].cpu().numpy().astype(bool)
+            pa = pm.pts[:pm.M, :2].cpu().numpy().astype(np.float64)[sel]
+            inl_pts[q - 1] = pa
+            hu = H_u.cpu().numpy().reshape(3, 3)
+            x = np.c_[pa, np.ones(len(pa))]
+            pu, pg = x @ hu.T, x @ g.H.T
+            dev_inl = max(dev_inl, float(np.abs(pu[:, :2] / pu[:, 2:] - pg[:, :2] / pg[:, 2:]).max(initial=0.0)))
             target = max(cu)
             reach_u.append(proposal.iterations_to_reach(cu, target))
             reach_g.append(proposal.iterations_to_reach(g.counts[:Tg], target) if g.iters == Tg
                            else Tg + proposal.iterations_to_reach(g.counts[Tg:], target))
             stopped += g.iters == Tg
             same += bool(np.array_equal(g.inliers, inl_u[:pm.M].cpu().numpy()))
-    ctx.lp_set_proposal(net, Tg)
+    # the RANSAC stage alone, pair after pair (no matching beside it): plain
+    # lp_ransac against the proposal's forward pass + guided RANSAC
     s = torch.cuda.current_stream()
+
+    def stage(fn):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for qq, pm in enumerate(pms):
+            fn(qq, pm)
+        e1.record(s)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    Hs_ = torch.zeros(9, dtype=torch.float64, device="cuda")
+    ns_ = torch.zeros(1, dtype=torch.int32, device="cuda")
+    inl_ = torch.zeros(max(pm.M_cap for pm in pms), dtype=torch.uint8, device="cuda")
+    prob_ = torch.zeros(max(pm.M_cap for pm in pms), dtype=torch.float32, device="cuda")
+
+    def plain(qq, pm):
+        ctx.lp_ransac(pm.pts, pm.M_cap, pm.d_M, qq, Hs_, inl_, ns_, None)
+
+    def guided(qq, pm):
+        net.lp_mlp_forward(pm.feat, pm.M_cap, pm.d_M, prob_, None)
+        ctx.lp_ransac_prior(pm.pts, pm.M_cap, pm.d_M, prob_, Tg, qq, Hs_, inl_, ns_, None, None)
+
+    for fn in (plain, guided):
+        stage(fn)
+    ms_plain = min(stage(plain) for _ in range(3))
+    ms_guided = min(stage(guided) for _ in range(3))
+    ctx.lp_set_proposal(net, Tg)
     for _ in range(3):
         ctx.lp_stitch_pairs(images, HM, ni, va)
     torch.cuda.synchronize()
@@ -545,13 +634,39 @@ def learned_proposal(args, bt, images, ctx, HM, ni, va, flush, k):
         torch.cuda.synchronize()
         t += e0.elapsed_time(e1) / 1e3
     ctx.lp_set_proposal(None)
-    return {"train_pairs": args.train_pairs, "train_matches": int(feat.shape[0]),
-            "inlier_label_frac": float(label.float().mean().item()), "loss_first": losses[0], "loss_last": losses[-1],
-            "train_s": round(train_s, 1), "guided_iters": Tg, "valid_pairs": nvalid,
-            "mean_iters_to_plain_best": {"uniform": float(np.mean(reach_u)) if reach_u else None,
-                                         "guided": float(np.mean(reach_g)) if reach_g else None},
-            "guided_stopped": stopped, "identical_inlier_sets": same,
-            "batch_pairs_per_s": 36 * k / t, "batch_valid_pairs": int(va.sum().item())}
+    pps = 36 * k / t
+    out = {"train_pairs": args.train_pairs, "train_matches": int(feat.shape[0]),
+           "inlier_label_frac": float(label.float().mean().item()), "loss_first": losses[0], "loss_last": losses[-1],
+           "epochs": epochs, "collect_s": round(collect_s, 1), "train_s": round(train_s, 1), "guided_iters": Tg,
+           "valid_pairs": nvalid,
+           "mean_iters_to_plain_best": {"uniform": float(np.mean(reach_u)) if reach_u else None,
+                                        "guided": float(np.mean(reach_g)) if reach_g else None},
+           "guided_stopped": stopped, "identical_inlier_sets": same,
+           "max_reprojection_px_on_plain_inliers": dev_inl,
+           "ransac_stage_ms_36_pairs": {"plain": ms_plain, "learned": ms_guided,
+                                        "note": "pair after pair, nothing beside it; learned = forward pass + "
+                                                "guided RANSAC with uniform fallback"},
+           "batch_pairs_per_s": pps, "batch_valid_pairs": int(va.sum().item())}
+    if ref is not None:
+        # the same 36 pairs through the plain FP32 form: the metric's comparison
+        hm = HM.cpu().numpy().reshape(36, 3, 3)
+        n_l = ni.cpu().numpy()
+        same_n = int((n_l == ref["n_in"]).sum())
+        # both homographies on the FP32 form's valid pairs, at plain RANSAC's inlier points
+        dev = 0.0
+        for p_, pa in inl_pts.items():
+            x = np.c_[pa, np.ones(len(pa))]
+            a, b_ = x @ ref["HM"][p_].T, x @ hm[p_].T
+            dev = max(dev, float(np.abs(b_[:, :2] / b_[:, 2:] - a[:, :2] / a[:, 2:]).max(initial=0.0)))
+        out["vs_fp32_batch"] = {"fp32_batch_pairs_per_s": ref["pairs_per_s"],
+                                "bf16_batch_pairs_per_s": ref["bf16_pairs_per_s"],
+                                "bf16_learned_batch_pairs_per_s": pps,
+                                "speedup_bf16_learned_vs_fp32": pps / ref["pairs_per_s"],
+                                "speedup_bf16_vs_fp32": ref["bf16_pairs_per_s"] / ref["pairs_per_s"],
+                                "learned_vs_plain_bf16": pps / ref["bf16_pairs_per_s"],
+                                "pairs_with_equal_inlier_count": same_n,
+                                "max_reprojection_px_on_inliers": dev}
+    return out
 
 
 def main():
@@ -562,7 +677,7 @@ def main():
     ap.add_argument("--impl", default="lp", choices=["lp", "reference"])
     ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16"])
     ap.add_argument("--no-extras", action="store_true", help="skip the FP32-form and 3x3-batch side measurements")
-    ap.add_argument("--train-pairs", type=int, default=64,
+    ap.add_argument("--train-pairs", type=int, default=2000,
                     help="640x480 pairs that train the learned RANSAC proposal (0 skips it)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -645,6 +760,7 @@ def main():
         line["config"]["speedup_vs_fp32_form"] = value / world / extra["fp32_form_pairs_per_s"]
         line["config"]["fp32_form_inliers"] = extra["fp32_form_inliers"]
         line["config"]["batch_3x3"] = extra["batch_3x3"]
+        line["config"]["batch_3x3_fp32"] = extra["batch_3x3_fp32"]
         line["config"]["mosaic_3x3"] = extra["mosaic_3x3"]
         line["config"]["table2"] = extra["table2"]
         line["config"]["detect_3x3"] = extra["detect_3x3"]

@@ -385,7 +385,10 @@ LP_API int lp_mlp_train_step(lp_mlp* mlp, const float* feat, const uint8_t* labe
  * inliers) / sum(q), the chance that a guided draw is an inlier, the phase
  * stops when (1 - w^k)^guided_iters <= 0.01 -- the standard bound
  * T >= log(0.01) / log(1 - w^k), k = 4 matches per sample (2 for
- * LP_MODEL_RIGID).  Then the guided winner is refitted as in lp_ransac.  Otherwise the uniform phase runs: exactly lp_ransac with the
+ * LP_MODEL_RIGID) -- and the guided winner has at least the configuration's
+ * min_inliers inliers (a prior concentrated on a few matches, any four of
+ * which fit a homography, cannot end the search).  Then the guided winner is
+ * refitted as in lp_ransac.  Otherwise the uniform phase runs: exactly lp_ransac with the
  * context's T (the test and the skipped work are decided on the device, so
  * the call never waits for the host).
  *  prior         device float[M_cap] (e.g. lp_mlp_forward's prob)

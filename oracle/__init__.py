@@ -97,8 +97,8 @@ def _load(path: str):
         "or_mlp_adam": (i32, [P, P, P, P, i32, i32, f64, f64, f64, f64]),
         "or_guided_weights": (i32, [P, i64, P]),
         "or_ransac_sample_guided": (i32, [i64, P, C.c_uint64, u32, i32, P]),
-        "or_ransac_prior": (i32, [P, i64, P, i32, i32, f64, C.c_uint64, u32, P, P, P, P, P, P]),
-        "or_ransac_prior_model": (i32, [P, i64, i32, P, i32, i32, f64, C.c_uint64, u32, P, P, P, P, P, P]),
+        "or_ransac_prior": (i32, [P, i64, P, i32, i32, f64, C.c_uint64, u32, i32, P, P, P, P, P, P]),
+        "or_ransac_prior_model": (i32, [P, i64, i32, P, i32, i32, f64, C.c_uint64, u32, i32, P, P, P, P, P, P]),
         "or_guided_stop": (i32, [C.c_uint64, C.c_uint64, i32]),
         "or_guided_stop_k": (i32, [C.c_uint64, C.c_uint64, i32, i32]),
         "or_ransac_sample_guided_k": (i32, [i64, P, C.c_uint64, u32, i32, i32, P]),
@@ -408,8 +408,9 @@ def ransac_sample_guided(prefix, seed, pair_id, t, k=4):
 
 
 def ransac_prior(pts, prob, Tg=64, T=1000, thresh=3.0, seed=0, pair_id=0, want_counts=False,
-                 model=MODEL_HOMOGRAPHY):
-    """Guided phase of Tg hypotheses, then uniform fallback of T (see lp_oracle.h)."""
+                 model=MODEL_HOMOGRAPHY, min_support=8):
+    """Guided phase of Tg hypotheses, then uniform fallback of T (see lp_oracle.h);
+    the guided phase may end the search only with at least min_support inliers."""
     p = _c(pts, np.float64).reshape(-1, 4)
     pr = _c(prob, np.float32)
     M = len(p)
@@ -419,8 +420,9 @@ def ransac_prior(pts, prob, Tg=64, T=1000, thresh=3.0, seed=0, pair_id=0, want_c
     bt = C.c_int32()
     it = C.c_int32()
     counts = np.empty(Tg + T, np.int32) if want_counts else None
-    lib().or_ransac_prior_model(_p(p), M, int(model), _p(pr), int(Tg), int(T), float(thresh), seed, pair_id, _p(H),
-                                _p(inl), C.byref(n_in), C.byref(bt), C.byref(it), _p(counts))
+    lib().or_ransac_prior_model(_p(p), M, int(model), _p(pr), int(Tg), int(T), float(thresh), seed, pair_id,
+                                int(min_support), _p(H), _p(inl), C.byref(n_in), C.byref(bt), C.byref(it),
+                                _p(counts))
     out = dict(H=H.reshape(3, 3), inliers=inl[:M], n_in=int(n_in.value), best_t=int(bt.value), iters=int(it.value))
     if want_counts:
         out["counts"] = counts

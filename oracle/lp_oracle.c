@@ -935,12 +935,16 @@ int or_guided_stop_k(uint64_t s_in, uint64_t total, int Tg, int k)
 int or_guided_stop(uint64_t s_in, uint64_t total, int Tg) { return or_guided_stop_k(s_in, total, Tg, 4); }
 
 /* Learned-proposal RANSAC: Tg hypotheses from guided samples are scored by all
- * matches; when the stop test holds for the guided winner, it is refitted as in
- * or_ransac; otherwise the call falls back to uniform RANSAC with T iterations
- * (or_ransac itself, whose best_t is reported offset by Tg). */
+ * matches; when the stop test holds for the guided winner and the winner has at
+ * least min_support inliers and an unweighted inlier fraction for which the
+ * same bound holds, it is refitted as in or_ransac; otherwise the call
+ * falls back to uniform RANSAC with T iterations (or_ransac itself, whose
+ * best_t is reported offset by Tg).  The support floor keeps a prior that
+ * concentrates on a handful of matches (any four of which fit a homography
+ * exactly) from ending the search on them. */
 int or_ransac_prior_model(const double* pts, int64_t M, int model, const float* prob, int Tg, int T, double thresh,
-                          uint64_t seed, uint32_t pair_id, double* H, uint8_t* inl, int32_t* n_in, int32_t* best_t,
-                          int32_t* iters, int32_t* counts /* Tg + T or NULL */)
+                          uint64_t seed, uint32_t pair_id, int min_support, double* H, uint8_t* inl, int32_t* n_in,
+                          int32_t* best_t, int32_t* iters, int32_t* counts /* Tg + T or NULL */)
 {
     const int k = or_model_sample_size(model);
     memset(H, 0, sizeof(double) * 9);
@@ -978,7 +982,8 @@ int or_ransac_prior_model(const double* pts, int64_t M, int model, const float* 
         uint64_t s_in = 0;
         for (int64_t i = 0; i < M; ++i)
             if (m[i]) s_in += prefix[i] - (i ? prefix[i - 1] : 0);
-        stop = or_guided_stop_k(s_in, prefix[M - 1], Tg, k);
+        stop = or_guided_stop_k(s_in, prefix[M - 1], Tg, k) && bestc >= (int64_t)min_support &&
+               or_guided_stop_k((uint64_t)bestc, (uint64_t)M, Tg, k);
     }
     free(prefix);
     if (!stop) {
@@ -1001,11 +1006,11 @@ int or_ransac_prior_model(const double* pts, int64_t M, int model, const float* 
 }
 
 int or_ransac_prior(const double* pts, int64_t M, const float* prob, int Tg, int T, double thresh, uint64_t seed,
-                    uint32_t pair_id, double* H, uint8_t* inl, int32_t* n_in, int32_t* best_t, int32_t* iters,
-                    int32_t* counts)
+                    uint32_t pair_id, int min_support, double* H, uint8_t* inl, int32_t* n_in, int32_t* best_t,
+                    int32_t* iters, int32_t* counts)
 {
-    return or_ransac_prior_model(pts, M, OR_MODEL_HOMOGRAPHY, prob, Tg, T, thresh, seed, pair_id, H, inl, n_in,
-                                 best_t, iters, counts);
+    return or_ransac_prior_model(pts, M, OR_MODEL_HOMOGRAPHY, prob, Tg, T, thresh, seed, pair_id, min_support, H, inl,
+                                 n_in, best_t, iters, counts);
 }
 
 /* ------------------------------------------------------------------ */

@@ -135,16 +135,18 @@ int or_guided_stop_k(uint64_t s_in, uint64_t total, int Tg, int k);
 
 /* Tg guided hypotheses (samples drawn with probability proportional to the
  * prior), scored by all matches; the guided winner is refitted when
- * or_guided_stop holds for its prior-weighted inlier fraction, otherwise the
- * result is uniform or_ransac with T iterations (best_t offset by Tg).
- * iters = Tg or Tg + T; counts (Tg + T, optional) as or_ransac's. */
+ * or_guided_stop holds for its prior-weighted inlier fraction and for its
+ * plain inlier fraction (inliers / M), and it has at least min_support
+ * inliers; otherwise the result is uniform or_ransac with T
+ * iterations (best_t offset by Tg).  iters = Tg or Tg + T; counts (Tg + T,
+ * optional) as or_ransac's. */
 int or_ransac_prior(const double* pts, int64_t M, const float* prob, int Tg, int T, double thresh, uint64_t seed,
-                    uint32_t pair_id, double* H, uint8_t* inl, int32_t* n_in, int32_t* best_t, int32_t* iters,
-                    int32_t* counts);
+                    uint32_t pair_id, int min_support, double* H, uint8_t* inl, int32_t* n_in, int32_t* best_t,
+                    int32_t* iters, int32_t* counts);
 /* The same with a model of Sec. 2.5 (OR_MODEL_*). */
 int or_ransac_prior_model(const double* pts, int64_t M, int model, const float* prob, int Tg, int T, double thresh,
-                          uint64_t seed, uint32_t pair_id, double* H, uint8_t* inl, int32_t* n_in, int32_t* best_t,
-                          int32_t* iters, int32_t* counts);
+                          uint64_t seed, uint32_t pair_id, int min_support, double* H, uint8_t* inl, int32_t* n_in,
+                          int32_t* best_t, int32_t* iters, int32_t* counts);
 /* Sec. 4 mosaic (readings in lp_oracle.c): rounds of reference selection over
  * H_M (pairs host int32[P*2], HM double[P*9], valid uint8[P]) and placements G
  * (double[N*9], image pixel -> canvas pixel) on a canvas_w x canvas_h canvas. */

@@ -527,11 +527,28 @@ k_ransac_argmax(const int32_t* exact, int T, const int32_t* skip, int t_off, int
 // T >= log(0.01) / log(1 - w^4) without logarithms.  Every operation is a
 // single IEEE-rounded one (no contraction), powers by binary exponentiation.
 // flags[kFlagStop] = stop, flags[kFlagIters] = iterations used.
+// (1 - w^k)^Tg <= 0.01 for w = num / den: the standard stop bound
+// T >= log(0.01) / log(1 - w^k), each operation one IEEE rounding in the
+// order the CPU reference takes them, powers by binary exponentiation.
+__device__ __forceinline__ bool guided_bound(double num, double den, int Tg, int k)
+{
+    const double w = __ddiv_rn(num, den);
+    const double w2 = __dmul_rn(w, w);
+    const double wk = k == 2 ? w2 : __dmul_rn(w2, w2);
+    double b = __dsub_rn(1.0, wk), r = 1.0;
+    for (int e = Tg; e; e >>= 1) {
+        if (e & 1) r = __dmul_rn(r, b);
+        b = __dmul_rn(b, b);
+    }
+    return r <= 0.01;
+}
+
 __global__ void __launch_bounds__(kSelThreads)
 k_guided_decide(const float4* pts, long long M_cap, const int32_t* dM, const double* Hs,
-                const unsigned long long* prefix, int Tg, int T, int k, double t2, int32_t* flags)
+                const unsigned long long* prefix, int Tg, int T, int k, double t2, int min_support, int32_t* flags)
 {
     __shared__ unsigned long long part[kSelThreads / 32];
+    __shared__ long long cpart[kSelThreads / 32];
     const int tb = flags[kFlagBest];
     const long long M = m_count(dM, M_cap);
     if (tb < 0 || M < k) {
@@ -541,25 +558,35 @@ k_guided_decide(const float4* pts, long long M_cap, const int32_t* dM, const dou
     double H[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) H[i] = Hs[9ll * tb + i];
+    // prior mass and number of the guided winner's inliers
     unsigned long long sw = 0;
+    long long cnt = 0;
     for (long long i = threadIdx.x; i < M; i += kSelThreads)
-        if (inlier64(H, pts[i], t2)) sw += prefix[i] - (i ? prefix[i - 1] : 0ull);
+        if (inlier64(H, pts[i], t2)) {
+            sw += prefix[i] - (i ? prefix[i - 1] : 0ull);
+            ++cnt;
+        }
 #pragma unroll
-    for (int o = 16; o; o >>= 1) sw += __shfl_xor_sync(0xFFFFFFFFu, sw, o);
-    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = sw;
+    for (int o = 16; o; o >>= 1) {
+        sw += __shfl_xor_sync(0xFFFFFFFFu, sw, o);
+        cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        part[threadIdx.x >> 5] = sw;
+        cpart[threadIdx.x >> 5] = cnt;
+    }
     __syncthreads();
     if (threadIdx.x != 0) return;
     unsigned long long s_in = 0;
-    for (int w = 0; w < kSelThreads / 32; ++w) s_in += part[w];
-    const double w = __ddiv_rn((double)s_in, (double)prefix[M - 1]);
-    const double w2 = __dmul_rn(w, w);
-    const double wk = k == 2 ? w2 : __dmul_rn(w2, w2);
-    double b = __dsub_rn(1.0, wk), r = 1.0;
-    for (int e = Tg; e; e >>= 1) {
-        if (e & 1) r = __dmul_rn(r, b);
-        b = __dmul_rn(b, b);
+    long long n_win = 0;
+    for (int w = 0; w < kSelThreads / 32; ++w) {
+        s_in += part[w];
+        n_win += cpart[w];
     }
-    const int stop = r <= 0.01;
+    // the search ends on the guided winner only when the bound holds for its
+    // prior-weighted and its plain inlier fraction, with enough support
+    const int stop = guided_bound((double)s_in, (double)prefix[M - 1], Tg, k) && n_win >= (long long)min_support &&
+                     guided_bound((double)n_win, (double)M, Tg, k);
     flags[kFlagStop] = stop;
     flags[kFlagIters] = stop ? Tg : Tg + T;
 }
@@ -1076,7 +1103,8 @@ cudaError_t launch_ransac(const float* pts, int64_t M_cap, const int32_t* d_M, i
 // the device when the guided phase stopped.  Hypothesis rows: guided [0, Tg),
 // uniform [Tg, Tg + T).
 cudaError_t launch_ransac_prior(const float* pts, int64_t M_cap, const int32_t* d_M, const unsigned long long* prefix,
-                                int Tg, int T, int model, float thresh, uint64_t seed, uint32_t pair_id, double* H,
+                                int Tg, int T, int model, float thresh, uint64_t seed, uint32_t pair_id,
+                                int min_support, double* H,
                                 uint8_t* inlier, int32_t* n_in, int32_t* best_t, int32_t* iters, void* ws,
                                 size_t ws_bytes, cudaStream_t s)
 {
@@ -1089,7 +1117,7 @@ cudaError_t launch_ransac_prior(const float* pts, int64_t M_cap, const int32_t* 
     const float eps = fmaxf(0.05f, 0.01f * t2f);
     const int k = model == LP_MODEL_RIGID ? 2 : 4;
     hyp_batch(model, p4, M_cap, d_M, prefix, Tg, 0, k0, k1, t2f, eps, t2, nullptr, w, s);
-    k_guided_decide<<<1, kSelThreads, 0, s>>>(p4, M_cap, d_M, w.Hs, prefix, Tg, T, k, t2, w.flags);
+    k_guided_decide<<<1, kSelThreads, 0, s>>>(p4, M_cap, d_M, w.Hs, prefix, Tg, T, k, t2, min_support, w.flags);
     hyp_batch(model, p4, M_cap, d_M, nullptr, T, Tg, k0, k1, t2f, eps, t2, w.flags + kFlagStop, w, s);
     refit_launch(model, p4, M_cap, d_M, t2, w, H, inlier, n_in, best_t, s);
     if (iters) {

@@ -663,17 +663,19 @@ int lp_stitch_pairs_ids(lp_ctx* c, const lp_image* imgs, int N, const int32_t* p
         ib[i].d16 = o; o += bf ? al256(256 * (size_t)K + 16) : 0;
         ib[i].val = o; o += al256((size_t)K + 8);
     }
-    const size_t o_match = o; o += al256(4 * (size_t)Kmax + 8);
-    const size_t o_d1 = o; o += al256(4 * (size_t)Kmax + 8);
-    const size_t o_d2 = o; o += al256(4 * (size_t)Kmax + 8);
-    // two slots of compacted points and inlier masks: pair q's RANSAC (on the
-    // context's second stream) overlaps the next pair's matching
+    // two slots of match outputs, compacted points and inlier masks: pair q's
+    // RANSAC (and, with the learned proposal, its features and forward pass)
+    // run on the context's second stream beside the next pair's matching
+    const size_t row_slot = al256(4 * (size_t)Kmax + 8);
+    const size_t o_match = o; o += 2 * row_slot;
+    const size_t o_d1 = o; o += 2 * row_slot;
+    const size_t o_d2 = o; o += 2 * row_slot;
     const size_t o_pts = o; o += 2 * al256(16 * (size_t)Kmax + 16);
     const size_t o_inl = o; o += 2 * al256((size_t)Kmax + 8);
     const size_t pts_slot = al256(16 * (size_t)Kmax + 16), inl_slot = al256((size_t)Kmax + 8);
     const size_t o_M = o; o += al256(4 * (size_t)P + 8);
     const bool guided = c->proposal != nullptr;
-    const size_t o_rows = o; o += guided ? al256(4 * (size_t)Kmax + 8) : 0;
+    const size_t o_rows = o; o += guided ? 2 * row_slot : 0;
     const size_t feat_slot = guided ? al256(32 * (size_t)Kmax + 32) : 0;
     const size_t o_feat = o; o += 2 * feat_slot;
     const size_t o_prob = o; o += guided ? al256(4 * (size_t)Kmax + 8) : 0;
@@ -736,9 +738,9 @@ int lp_stitch_pairs_ids(lp_ctx* c, const lp_image* imgs, int N, const int32_t* p
                                   bf ? (uint16_t*)(base + ib[i].d16) : nullptr, base + ib[i].val, stream)))
                 return rr;
         }
-        // RANSAC of pair q (with the learned proposal: its forward pass and the
-        // guided RANSAC) on the second stream, beside pair q + 1's matching; the
-        // proposal's features read the match buffers, so they run in order
+        // RANSAC of pair q (with the learned proposal: its features, forward
+        // pass and guided RANSAC) on the second stream, beside pair q + 1's
+        // matching; every buffer they read has two slots
         const bool overlap = true;
         cudaStream_t sr = overlap ? c->img_stream : s;
         if (overlap) {
@@ -753,6 +755,10 @@ int lp_stitch_pairs_ids(lp_ctx* c, const lp_image* imgs, int N, const int32_t* p
             float* pts = (float*)(base + o_pts + slot * pts_slot);
             uint8_t* inl = base + o_inl + slot * inl_slot;
             float* feat = (float*)(base + o_feat + slot * feat_slot);
+            int32_t* mt = (int32_t*)(base + o_match + slot * row_slot);
+            float* d1 = (float*)(base + o_d1 + slot * row_slot);
+            float* d2 = (float*)(base + o_d2 + slot * row_slot);
+            int32_t* rows = guided ? (int32_t*)(base + o_rows + slot * row_slot) : nullptr;
             // the slot's previous RANSAC (pair q - 2) has finished reading it
             if (overlap) LP_CUDA(c, cudaStreamWaitEvent(s, c->pair_ev[1 + slot], 0));
             if (A.K == 0) {
@@ -760,25 +766,22 @@ int lp_stitch_pairs_ids(lp_ctx* c, const lp_image* imgs, int N, const int32_t* p
             } else {
                 if ((rr = lp_match(c, (const float*)(base + A.desc), bf ? (const uint16_t*)(base + A.d16) : nullptr,
                                    base + A.val, A.K, (const float*)(base + B.desc),
-                                   bf ? (const uint16_t*)(base + B.d16) : nullptr, base + B.val, B.K,
-                                   (int32_t*)(base + o_match), (float*)(base + o_d1), (float*)(base + o_d2), stream)))
+                                   bf ? (const uint16_t*)(base + B.d16) : nullptr, base + B.val, B.K, mt, d1, d2,
+                                   stream)))
                     return rr;
                 if ((rr = lp_compact(c, (const uint32_t*)(base + A.kp), imgs[a].W, (const uint32_t*)(base + B.kp),
-                                     imgs[b].W, (const int32_t*)(base + o_match), A.K, pts,
-                                     guided ? (int32_t*)(base + o_rows) : nullptr, Mbuf + q, stream)))
+                                     imgs[b].W, mt, A.K, pts, rows, Mbuf + q, stream)))
                     return rr;
             }
-            if (guided && A.K > 0 &&
-                (rr = lp_mlp_features(c, (const uint32_t*)(base + A.kp), base + A.ori, imgs[a].H, imgs[a].W,
-                                      (const uint32_t*)(base + B.kp), base + B.ori, imgs[b].H, imgs[b].W,
-                                      (const int32_t*)(base + o_match), (const float*)(base + o_d1),
-                                      (const float*)(base + o_d2), (const int32_t*)(base + o_rows), Mbuf + q, A.K,
-                                      feat, stream)))
-                return rr;
             if (overlap) {
                 LP_CUDA(c, cudaEventRecord(c->pair_ev[0], s));
                 LP_CUDA(c, cudaStreamWaitEvent(sr, c->pair_ev[0], 0));
             }
+            if (guided && A.K > 0 &&
+                (rr = lp_mlp_features(c, (const uint32_t*)(base + A.kp), base + A.ori, imgs[a].H, imgs[a].W,
+                                      (const uint32_t*)(base + B.kp), base + B.ori, imgs[b].H, imgs[b].W, mt, d1, d2,
+                                      rows, Mbuf + q, A.K, feat, sr)))
+                return rr;
             if (guided && A.K > 0) {
                 float* prob = (float*)(base + o_prob);
                 if ((rr = lp_mlp_forward(c->proposal, feat, A.K, Mbuf + q, prob, nullptr, sr)))
@@ -838,7 +841,8 @@ int lp_ransac_prior(lp_ctx* c, const float* pts, int64_t M_cap, const int32_t* d
     auto* pre = static_cast<unsigned long long*>(c->buf[B_PREFIX].p);
     LP_CUDA(c, lp::launch_guided_prefix(prior, M_cap, d_M, pre, S(stream)));
     LP_CUDA(c, lp::launch_ransac_prior(pts, M_cap, d_M, pre, guided_iters, T, c->cfg.model, c->cfg.thresh_px,
-                                       c->cfg.seed, pair_id, H, inlier, n_inliers, best_t, iters_used,
+                                       c->cfg.seed, pair_id, c->cfg.min_inliers, H, inlier, n_inliers, best_t,
+                                       iters_used,
                                        c->buf[B_RANSAC_WS].p,
                                        c->buf[B_RANSAC_WS].n, S(stream)));
     return LP_OK;

@@ -99,9 +99,11 @@ cudaError_t launch_ransac(const float* pts, int64_t M_cap, const int32_t* d_M, i
 cudaError_t launch_diag_philox(const uint32_t* ctr, int64_t n, uint32_t k0, uint32_t k1, uint32_t* out,
                                cudaStream_t s);
 
-// k_ransac.cu (guided phase, stop test, uniform fallback); Ttot = Tg + T
+// k_ransac.cu (guided phase, stop test, uniform fallback); Ttot = Tg + T; the
+// guided winner ends the search only with at least min_support inliers
 cudaError_t launch_ransac_prior(const float* pts, int64_t M_cap, const int32_t* d_M, const unsigned long long* prefix,
-                                int Tg, int T, int model, float thresh, uint64_t seed, uint32_t pair_id, double* H,
+                                int Tg, int T, int model, float thresh, uint64_t seed, uint32_t pair_id,
+                                int min_support, double* H,
                                 uint8_t* inlier, int32_t* n_in, int32_t* best_t, int32_t* iters, void* ws,
                                 size_t ws_bytes, cudaStream_t s);
 cudaError_t ransac_counts(void* ws, int Ttot, int32_t* host_counts, cudaStream_t s);

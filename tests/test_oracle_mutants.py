@@ -199,6 +199,14 @@ MUTANTS = [
     ("adam_second_moment_not_squared",
      "v[i] = b2 * v[i] + (1 - b2) * grad[i] * grad[i];", "v[i] = b2 * v[i] + (1 - b2) * fabs(grad[i]);",
      [ML.test_adam_first_step_closed_form]),
+    ("guided_support_floor_dropped",
+     "stop = or_guided_stop_k(s_in, prefix[M - 1], Tg, k) && bestc >= (int64_t)min_support &&",
+     "stop = or_guided_stop_k(s_in, prefix[M - 1], Tg, k) &&",
+     [ML.test_ransac_prior_support_floor]),
+    ("guided_plain_fraction_bound_dropped",
+     "(int64_t)min_support &&\n               or_guided_stop_k((uint64_t)bestc, (uint64_t)M, Tg, k);",
+     "(int64_t)min_support;",
+     [ML.test_ransac_prior_support_floor]),
     ("guided_weight_truncated",
      "acc += (uint64_t)floor(65536.0 * p + 0.5);", "acc += (uint64_t)floor(65536.0 * p);",
      [ML.test_guided_weights_are_exact_integers]),

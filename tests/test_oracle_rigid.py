@@ -176,7 +176,7 @@ def test_rigid_prior_falls_back_to_uniform():
 
 def test_rigid_prior_stops_on_a_good_prior():
     rng = np.random.default_rng(9)
-    pts, Ht, inl = _case(rng, 300, 0.3, -0.9, (5.0, 60.0))
+    pts, Ht, inl = _case(rng, 300, 0.7, -0.9, (5.0, 60.0))
     prior = np.where(inl, 0.99, 0.001).astype(np.float32)
     g = oracle.ransac_prior(pts, prior, Tg=16, T=500, seed=3, model=RIGID)
     assert g["iters"] == 16 and 0 <= g["best_t"] < 16
