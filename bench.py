@@ -381,6 +381,7 @@ def fp32_form_and_batch(args, rank):
     out["mosaic_3x3"] = mosaic(bt, images, ctx, HM, va, flush, k)
     out["detect_3x3"] = detect_batch(ctx, images, flush, k)
     out["table2"] = table2(flush)
+    out["uneven_64"] = uneven_64(flush, max(3, k // 2))
     if args.train_pairs > 0:
         out["learned_proposal"] = learned_proposal(args, bt, images, ctx, HM, ni, va, flush, k, ref)
     return out
@@ -538,6 +539,99 @@ def training_pairs(seeds):
     workers = max(1, min(16, (os.cpu_count() or 2) - 1))
     with ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
         yield from ex.map(_training_pair, seeds, chunksize=8)
+
+
+def _uneven_pair(spec):
+    """One pair of the uneven workload (runs in a spawned worker process)."""
+    from paper_2405_08578_gb300 import synth
+    p = synth.make_pair(*spec)
+    return p.A, p.B, p.H
+
+
+def _grid_dev(Ha, Hb, h, w, Href=None, step=32):
+    """Largest distance (px) between Ha and Hb images of a grid of A's pixels
+    that Href (default Ha) maps inside a w x h image B."""
+    ys, xs = np.mgrid[0:h:step, 0:w:step]
+    x = np.c_[xs.ravel(), ys.ravel(), np.ones(xs.size)]
+    r = x @ np.asarray(Ha if Href is None else Href).T
+    r = r[:, :2] / r[:, 2:]
+    inside = (r[:, 0] >= 0) & (r[:, 0] < w) & (r[:, 1] >= 0) & (r[:, 1] < h)
+    a = x[inside] @ np.asarray(Ha).T
+    b = x[inside] @ np.asarray(Hb).T
+    return float(np.abs(a[:, :2] / a[:, 2:] - b[:, :2] / b[:, 2:]).max(initial=0.0)), int(inside.sum())
+
+
+def uneven_64(flush, k, oracle_pairs=3):
+    """The 64-pair uneven workload (long sides U[480, 4096], aspect U[4/3,
+    16/9], gray, L = {16, 32, 64, 128}) as one lp_stitch_pairs call with an
+    explicit pair list, BF16 with and without the matcher's autotuner: pairs/s
+    of each, the tuning table, error against each pair's true homography and,
+    on the smallest pairs, against the oracle's."""
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+
+    import torch
+
+    import oracle
+    from paper_2405_08578_gb300 import lp, synth
+    specs = synth.uneven_pair_specs(64, seed=2)
+    t0 = time.time()
+    workers = max(1, min(16, (os.cpu_count() or 2) - 1))
+    with ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        pairs = list(ex.map(_uneven_pair, specs))
+    gen_s = time.time() - t0
+    images, plist = [], []
+    for q, (A, B, _) in enumerate(pairs):
+        for im in (A, B):
+            buf, pitch = lp.pitched_device(im)
+            images.append((buf, im.shape[0], im.shape[1], pitch, 1))
+        plist.append((2 * q, 2 * q + 1))
+    s = torch.cuda.current_stream()
+    res = {}
+    for tuned in (False, True):
+        ctx = lp.Context(Ls=LS, precision=lp.PREC_BF16)
+        ctx.lp_set_autotune(tuned)
+        HM = torch.zeros((64, 9), dtype=torch.float64, device="cuda")
+        ni = torch.zeros(64, dtype=torch.int32, device="cuda")
+        va = torch.zeros(64, dtype=torch.uint8, device="cuda")
+        for _ in range(3):
+            ctx.lp_stitch_pairs(images, HM, ni, va, pairs=plist)
+        torch.cuda.synchronize()
+        t = 0.0
+        for _ in range(k):
+            flush()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            ctx.lp_stitch_pairs(images, HM, ni, va, pairs=plist)
+            e1.record(s)
+            torch.cuda.synchronize()
+            t += e0.elapsed_time(e1) / 1e3
+        assert ctx.lp_sync_status() == 0
+        res[tuned] = dict(pps=64 * k / t, HM=HM.cpu().numpy().reshape(64, 3, 3), ni=ni.cpu().numpy(),
+                          va=va.cpu().numpy(), table=ctx.lp_autotune_table() if tuned else [])
+        del ctx
+    out = {"pairs": 64, "images": 128, "long_side_px": [min(sp[1] for sp in specs), max(sp[1] for sp in specs)],
+           "generate_s": round(gen_s, 1), "pairs_per_s_builtin_tiles": res[False]["pps"],
+           "pairs_per_s_autotuned": res[True]["pps"], "autotune_table": res[True]["table"],
+           "tuned_equals_builtin": bool(np.array_equal(res[True]["HM"], res[False]["HM"]) and
+                                        np.array_equal(res[True]["ni"], res[False]["ni"])),
+           "valid_pairs": int(res[True]["va"].sum())}
+    # error against each pair's true homography over the true overlap
+    dev_t = [_grid_dev(res[True]["HM"][q], pairs[q][2], pairs[q][0].shape[0], pairs[q][0].shape[1])[0]
+             for q in range(64) if res[True]["va"][q]]
+    out["truth_error_px"] = {"median": float(np.median(dev_t)) if dev_t else None,
+                             "max": float(np.max(dev_t)) if dev_t else None}
+    # the smallest pairs end to end through the oracle
+    order = sorted(range(64), key=lambda q: pairs[q][0].size)[:oracle_pairs]
+    rows = []
+    for q in order:
+        A, B, Ht = pairs[q]
+        o = oracle.stitch_pair(A, B, LS, pair_id=q)
+        d, n = _grid_dev(res[True]["HM"][q], o["H"], A.shape[0], A.shape[1], Href=Ht)
+        rows.append({"pair": q, "size": [int(A.shape[1]), int(A.shape[0])], "n_in_gpu": int(res[True]["ni"][q]),
+                     "n_in_oracle": o["n_in"], "H_vs_oracle_px": d, "overlap_points": n})
+    out["vs_oracle_smallest_pairs"] = rows
+    return out
 
 
 def learned_proposal(args, bt, images, ctx, HM, ni, va, flush, k, ref=None):
@@ -761,6 +855,7 @@ def main():
         line["config"]["fp32_form_inliers"] = extra["fp32_form_inliers"]
         line["config"]["batch_3x3"] = extra["batch_3x3"]
         line["config"]["batch_3x3_fp32"] = extra["batch_3x3_fp32"]
+        line["config"]["uneven_64"] = extra["uneven_64"]
         line["config"]["mosaic_3x3"] = extra["mosaic_3x3"]
         line["config"]["table2"] = extra["table2"]
         line["config"]["detect_3x3"] = extra["detect_3x3"]

@@ -374,6 +374,25 @@ LP_API int lp_mlp_forward(lp_mlp* mlp, const float* feat, int64_t M_cap, const i
 LP_API int lp_mlp_train_step(lp_mlp* mlp, const float* feat, const uint8_t* label, int64_t B, float lr, float* loss,
                              void* stream);
 
+/* Tile autotuning of the BF16 matcher (BASELINE's uneven-batch workload; the
+ * paper has no counterpart).  on = 1: the first lp_match (or stitch call) of a
+ * size class -- (ceil(log2 NA), ceil(log2 NB)) -- that runs outside stream
+ * capture times a few choices of the column-split count S and the pass-1 tile
+ * stride around the built-in ones on the caller's own inputs (each once,
+ * after a warm-up run; the call synchronises the stream for it), keeps the
+ * fastest for the class in the context and uses it from then on.  Every
+ * choice is certified against the FP32 form, so outputs do not change.  Under
+ * capture, classes not yet tuned run the built-in choice.  on = 0: the
+ * built-in choice everywhere (the table is kept).
+ * Errors: LP_ERR_ARG. */
+LP_API int lp_set_autotune(lp_ctx* ctx, int32_t on);
+
+/* The tuning table: *n = number of tuned classes; rows (host int32[cap * 6],
+ * or NULL with cap = 0) receives up to cap rows (ceil(log2 NA), ceil(log2 NB),
+ * S, pass-1 stride, tuned time in us, built-in choice's time in us).
+ * Errors: LP_ERR_ARG. */
+LP_API int lp_autotune_table(lp_ctx* ctx, int32_t* rows, int32_t cap, int32_t* n);
+
 /* RANSAC guided by a prior, with uniform RANSAC as fallback and judge.
  * Guided phase: guided_iters hypotheses whose samples are drawn in proportion
  * to the prior -- match i gets the integer weight

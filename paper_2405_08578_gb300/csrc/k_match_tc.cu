@@ -822,11 +822,14 @@ struct TcLayout {
         total;
 };
 
-TcLayout tc_layout(long long NA, long long NB, int sms)
+// S_force > 0: that many column splits (at most kMaxSplits and the tile count)
+TcLayout tc_layout(long long NA, long long NB, int sms, int S_force = 0)
 {
     TcLayout L;
     const int nrb = (int)((NA + kRowsPerUnit - 1) / kRowsPerUnit);
-    L.S = pick_tc_splits(nrb, NB, std::max(1, sms));
+    const long long tiles = std::max<long long>(1, (NB + kTileN - 1) / kTileN);
+    L.S = S_force > 0 ? (int)std::min<long long>(std::min(S_force, kMaxSplits), tiles)
+                      : pick_tc_splits(nrb, NB, std::max(1, sms));
     size_t o = 0;
     auto take = [&](size_t bytes) { size_t r = o; o += (bytes + 255) & ~size_t(255); return r; };
     L.off_na = take(sizeof(float) * (size_t)NA);
@@ -866,12 +869,14 @@ bool encode_tiled_2d(CUtensorMap* m, CUtensorMapDataType dt, const void* base, u
               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-size_t match_bf16_workspace(int64_t NA, int64_t NB, int num_sms) { return tc_layout(NA, NB, num_sms).total; }
+size_t match_bf16_workspace(int64_t NA, int64_t NB, int num_sms, int S) { return tc_layout(NA, NB, num_sms, S).total; }
+
+int match_bf16_default_splits(int64_t NA, int64_t NB, int num_sms) { return tc_layout(NA, NB, num_sms).S; }
 
 // Number of rows the last BF16 match re-scanned in FP32 (synchronous read).
-int64_t match_bf16_rescans(const void* ws, int64_t NA, int64_t NB, int num_sms, cudaStream_t s)
+int64_t match_bf16_rescans(const void* ws, int64_t NA, int64_t NB, int num_sms, int S, cudaStream_t s)
 {
-    const TcLayout L = tc_layout(NA, NB, num_sms);
+    const TcLayout L = tc_layout(NA, NB, num_sms, S);
     const uint8_t* w = reinterpret_cast<const uint8_t*>((reinterpret_cast<uintptr_t>(ws) + 255) & ~uintptr_t(255));
     int32_t c = -1;
     if (cudaMemcpyAsync(&c, w + L.off_cnt, sizeof c, cudaMemcpyDeviceToHost, s) != cudaSuccess) return -1;
@@ -882,7 +887,7 @@ int64_t match_bf16_rescans(const void* ws, int64_t NA, int64_t NB, int num_sms, 
 cudaError_t launch_match_bf16(const MatchArgs& a, void* ws, size_t ws_bytes, int num_sms, cudaStream_t s)
 {
     if (a.NA == 0) return cudaSuccess;
-    const TcLayout L = tc_layout(a.NA, a.NB, num_sms);
+    const TcLayout L = tc_layout(a.NA, a.NB, num_sms, a.splits);
     if (ws_bytes < L.total) return cudaErrorInvalidValue;
     uint8_t* w = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(ws) + 255) & ~uintptr_t(255));
     float* na = reinterpret_cast<float*>(w + L.off_na);
@@ -943,7 +948,7 @@ cudaError_t launch_match_bf16(const MatchArgs& a, void* ws, size_t ws_bytes, int
         const dim3 grid((unsigned)std::min(U, per_sm * num_sms));
         if (a.ev0) cudaEventRecord(a.ev0, s);
         TcParams p1 = p;
-        p1.tstride = kPass1Stride;
+        p1.tstride = a.pass1_stride > 0 ? a.pass1_stride : kPass1Stride;
         k_match_tc<1><<<grid, kThreadsTC, kSmemTC, s>>>(tA, tB, p1);
         k_row_threshold<<<(unsigned)((a.NA + 255) / 256), 256, 0, s>>>(pm, kRanges * L.S, a.NA, a.vA, thr);
         k_match_tc<2><<<grid, kThreadsTC, kSmemTC, s>>>(tA, tB, p);

@@ -55,6 +55,15 @@ struct lp_ctx {
     cudaEvent_t prof_ev[2] = {nullptr, nullptr};   // lp_set_profiling: around the last distance kernel
     bool prof_recorded = false;
     int32_t guided_iters = 0;
+    // lp_set_autotune: (S, pass-1 stride) of the BF16 matcher per size class
+    // (ceil(log2 NA), ceil(log2 NB)), timed on the class's first eager call
+    bool autotune = false;
+    struct TuneEntry {
+        int ba, bb, S, stride;
+        float us, us_builtin;
+    };
+    std::vector<TuneEntry> tune;
+    int last_S = 0;                     // column splits of the last BF16 match
     lp::Fork fork{};                    // auxiliary streams of lp_describe (created on first use)
     bool fork_ready = false;
     cudaStream_t img_stream = nullptr;  // lp_stitch_pair: image B's detect and describe;
@@ -380,6 +389,76 @@ int lp_describe(lp_ctx* c, const uint8_t* gray, int H, int W, int gray_pitch, co
     return LP_OK;
 }
 
+namespace {
+
+int log2_bucket(int64_t n)
+{
+    int b = 0;
+    while (b < 62 && (int64_t(1) << b) < n) ++b;
+    return b;
+}
+
+// The BF16 matcher's (column splits, pass-1 stride) for a's size class: the
+// cached choice, or -- on the class's first call outside stream capture --
+// the fastest of a few candidates around the built-in choice, each timed once
+// after a warm-up run on the caller's own inputs.  Every candidate gives the
+// same outputs (each is certified against the FP32 form), so tuning on live
+// data changes nothing but the time.  Under capture the built-in choice runs.
+int tune_match(lp_ctx* c, lp::MatchArgs& a, cudaStream_t s)
+{
+    const int ba = log2_bucket(a.NA), bb = log2_bucket(a.NB);
+    for (const auto& e : c->tune)
+        if (e.ba == ba && e.bb == bb) {
+            a.splits = e.S;
+            a.pass1_stride = e.stride;
+            return LP_OK;
+        }
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return LP_OK;
+    const int S0 = lp::match_bf16_default_splits(a.NA, a.NB, c->num_sms);
+    std::vector<std::pair<int, int>> cand = {{S0, 3}, {S0, 2}, {S0, 4}, {std::max(1, S0 / 2), 3},
+                                             {std::min(16, 2 * S0), 3}, {std::min(16, S0 + 1), 3}};
+    std::sort(cand.begin() + 1, cand.end());
+    cand.erase(std::unique(cand.begin() + 1, cand.end()), cand.end());
+    size_t ws = 0;
+    for (const auto& q : cand) ws = std::max(ws, lp::match_bf16_workspace(a.NA, a.NB, c->num_sms, q.first));
+    int r = ensure(c, B_MATCH_WS, ws);
+    if (r) return r;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    LP_CUDA(c, cudaEventCreate(&e0));
+    cudaError_t ce = cudaEventCreate(&e1);
+    if (ce != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cuda_fail(c, ce, "cudaEventCreate");
+    }
+    lp::MatchArgs t = a;
+    t.ev0 = t.ev1 = nullptr;
+    float best = INFINITY, builtin = INFINITY;
+    int bS = S0, bst = 3;
+    for (size_t k = 0; k < cand.size() && ce == cudaSuccess; ++k) {
+        t.splits = cand[k].first;
+        t.pass1_stride = cand[k].second;
+        float ms = 0.f;
+        if ((ce = lp::launch_match_bf16(t, c->buf[B_MATCH_WS].p, c->buf[B_MATCH_WS].n, c->num_sms, s)) != cudaSuccess ||
+            (ce = cudaEventRecord(e0, s)) != cudaSuccess ||
+            (ce = lp::launch_match_bf16(t, c->buf[B_MATCH_WS].p, c->buf[B_MATCH_WS].n, c->num_sms, s)) != cudaSuccess ||
+            (ce = cudaEventRecord(e1, s)) != cudaSuccess || (ce = cudaEventSynchronize(e1)) != cudaSuccess ||
+            (ce = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess)
+            break;
+        if (k == 0) builtin = ms;
+        if (ms < best) { best = ms; bS = cand[k].first; bst = cand[k].second; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (ce != cudaSuccess) return cuda_fail(c, ce, "autotune");
+    c->tune.push_back({ba, bb, bS, bst, 1e3f * best, 1e3f * builtin});
+    a.splits = bS;
+    a.pass1_stride = bst;
+    return LP_OK;
+}
+
+}  // namespace
+
 int lp_match(lp_ctx* c, const float* dA, const uint16_t* dA_bf16, const uint8_t* vA, int64_t NA, const float* dB,
              const uint16_t* dB_bf16, const uint8_t* vB, int64_t NB, int32_t* match, float* d1, float* d2,
              void* stream)
@@ -408,12 +487,15 @@ int lp_match(lp_ctx* c, const float* dA, const uint16_t* dA_bf16, const uint8_t*
     if (c->cfg.precision == LP_PREC_BF16) {
         if (!dA_bf16 || (NB > 0 && !dB_bf16)) return fail(c, LP_ERR_ARG, "BF16 matching needs the bf16 descriptors");
         if (!aligned(dA_bf16, 16) || (dB_bf16 && !aligned(dB_bf16, 16))) return fail(c, LP_ERR_ALIGN, "bf16 alignment");
-        int r = ensure(c, B_MATCH_WS, lp::match_bf16_workspace(NA, NB, c->num_sms));
-        if (r) return r;
-        c->last_NA = NA;
-        c->last_NB = NB;
+        int r;
         if ((r = ensure_fork(c))) return r;
         a.fork = &c->fork;
+        if (c->autotune && NB > 0 && (r = tune_match(c, a, S(stream)))) return r;
+        r = ensure(c, B_MATCH_WS, lp::match_bf16_workspace(NA, NB, c->num_sms, a.splits));
+        if (r) return r;
+        c->last_S = a.splits;
+        c->last_NA = NA;
+        c->last_NB = NB;
         LP_CUDA(c, lp::launch_match_bf16(a, c->buf[B_MATCH_WS].p, c->buf[B_MATCH_WS].n, c->num_sms, S(stream)));
         return LP_OK;
     }
@@ -898,6 +980,27 @@ int lp_mosaic_render(lp_ctx* c, const lp_image* imgs, int N, const double* G, co
     return LP_OK;
 }
 
+int lp_set_autotune(lp_ctx* c, int32_t on)
+{
+    if (!c) return LP_ERR_ARG;
+    c->autotune = on != 0;
+    return LP_OK;
+}
+
+int lp_autotune_table(lp_ctx* c, int32_t* rows, int32_t cap, int32_t* n)
+{
+    if (!c) return LP_ERR_ARG;
+    if (!n || cap < 0 || (cap > 0 && !rows)) return fail(c, LP_ERR_ARG, "null argument");
+    *n = (int32_t)c->tune.size();
+    for (int32_t k = 0; k < cap && k < *n; ++k) {
+        const auto& e = c->tune[(size_t)k];
+        int32_t* r = rows + 6 * (size_t)k;
+        r[0] = e.ba; r[1] = e.bb; r[2] = e.S; r[3] = e.stride;
+        r[4] = (int32_t)lrintf(e.us); r[5] = (int32_t)lrintf(e.us_builtin);
+    }
+    return LP_OK;
+}
+
 int lp_set_profiling(lp_ctx* c, int on)
 {
     if (!c) return LP_ERR_ARG;
@@ -943,7 +1046,7 @@ int lp_diag_last_rescans(lp_ctx* c, int64_t* out)
     if (!c || !out) return LP_ERR_ARG;
     *out = 0;
     if (c->cfg.precision != LP_PREC_BF16 || !c->buf[B_MATCH_WS].p || c->last_NA == 0) return LP_OK;
-    *out = lp::match_bf16_rescans(c->buf[B_MATCH_WS].p, c->last_NA, c->last_NB, c->num_sms, c->last);
+    *out = lp::match_bf16_rescans(c->buf[B_MATCH_WS].p, c->last_NA, c->last_NB, c->num_sms, c->last_S, c->last);
     return *out < 0 ? LP_ERR_CUDA : LP_OK;
 }
 

@@ -80,12 +80,16 @@ struct MatchArgs {
     int32_t* status;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;   // recorded around the distance kernel when set
     const Fork* fork = nullptr;                 // BF16 form: row norms run on the auxiliary streams
+    int splits = 0;                             // BF16 form: column splits (0: the built-in choice)
+    int pass1_stride = 0;                       // BF16 form: pass-1 tile stride (0: the built-in 3)
 };
 size_t match_fp32_workspace(int64_t NA, int64_t NB, int num_sms);
 cudaError_t launch_match_fp32(const MatchArgs& a, void* ws, size_t ws_bytes, int num_sms, cudaStream_t s);
-size_t match_bf16_workspace(int64_t NA, int64_t NB, int num_sms);
+// S: column splits (0: the built-in choice, match_bf16_default_splits)
+size_t match_bf16_workspace(int64_t NA, int64_t NB, int num_sms, int S = 0);
+int match_bf16_default_splits(int64_t NA, int64_t NB, int num_sms);
 cudaError_t launch_match_bf16(const MatchArgs& a, void* ws, size_t ws_bytes, int num_sms, cudaStream_t s);
-int64_t match_bf16_rescans(const void* ws, int64_t NA, int64_t NB, int num_sms, cudaStream_t s);
+int64_t match_bf16_rescans(const void* ws, int64_t NA, int64_t NB, int num_sms, int S, cudaStream_t s);
 
 // k_ransac.cu
 size_t compact_workspace(int64_t NA);

@@ -49,6 +49,7 @@ SYMBOLS = ["lp_config_default", "lp_create", "lp_destroy", "lp_num_keypoints", "
            "lp_mlp_create", "lp_mlp_destroy", "lp_mlp_set_params", "lp_mlp_get_params", "lp_mlp_get_state", "lp_mlp_save",
            "lp_mlp_load", "lp_mlp_features", "lp_mlp_forward", "lp_mlp_train_step", "lp_ransac_prior",
            "lp_diag_last_ransac_counts", "lp_set_proposal", "lp_set_profiling", "lp_diag_last_match_kernel_ms",
+           "lp_set_autotune", "lp_autotune_table",
            "lp_mosaic_plan", "lp_mosaic_render"]
 MLP_PARAMS = 4801
 
@@ -108,6 +109,8 @@ def load(build_if_missing: bool = True):
         "lp_mosaic_plan": (i32, [i32, P, i32, P, P, P, P, P, P, P, P, P]),
         "lp_mosaic_render": (i32, [P, P, i32, P, P, P, i32, i32, i32, P, P]),
         "lp_diag_last_match_kernel_ms": (i32, [P, C.POINTER(C.c_float)]),
+        "lp_set_autotune": (i32, [P, i32]),
+        "lp_autotune_table": (i32, [P, P, i32, C.POINTER(C.c_int32)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -274,6 +277,18 @@ class Context:
 
     def lp_set_profiling(self, on: bool = True):
         self._chk(self.lib.lp_set_profiling(self.h, int(bool(on))), "lp_set_profiling")
+
+    def lp_set_autotune(self, on: bool = True):
+        self._chk(self.lib.lp_set_autotune(self.h, int(bool(on))), "lp_set_autotune")
+
+    def lp_autotune_table(self) -> list[dict]:
+        """Tuned classes: log2 buckets of NA and NB, S, pass-1 stride, tuned and built-in times (us)."""
+        n = C.c_int32()
+        self._chk(self.lib.lp_autotune_table(self.h, None, 0, C.byref(n)), "lp_autotune_table")
+        rows = (C.c_int32 * (6 * max(n.value, 1)))()
+        self._chk(self.lib.lp_autotune_table(self.h, rows, n.value, C.byref(n)), "lp_autotune_table")
+        keys = ("log2_NA", "log2_NB", "splits", "pass1_stride", "tuned_us", "builtin_us")
+        return [dict(zip(keys, rows[6 * k:6 * k + 6])) for k in range(n.value)]
 
     def lp_diag_last_match_kernel_ms(self) -> float:
         v = C.c_float()

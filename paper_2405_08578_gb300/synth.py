@@ -214,6 +214,12 @@ def uneven_pairs(n: int = 64, seed: int = 2, long_lo: int = 480, long_hi: int = 
     aspect U[4/3, 16/9] (landscape), and B through a similarity drawn like the
     2688x1600 pair's (rotation U[-10, 10] deg, scale U[0.9, 1.1], x shift 0.6 w
     of either sign, y shift U[-0.05, 0.05] h: about 40% overlap)."""
+    return [make_pair(*spec, rgb=rgb) for spec in uneven_pair_specs(n, seed, long_lo, long_hi)]
+
+
+def uneven_pair_specs(n: int = 64, seed: int = 2, long_lo: int = 480, long_hi: int = 4096) -> list[tuple]:
+    """The (h, w, H, canvas seed) of each pair of uneven_pairs, in order; each
+    make_pair(*spec) can then be built independently."""
     rng = np.random.default_rng(40_000 + seed)
     out = []
     for q in range(n):
@@ -223,7 +229,7 @@ def uneven_pairs(n: int = 64, seed: int = 2, long_lo: int = 480, long_hi: int = 
         sc = rng.uniform(0.9, 1.1)
         tx = 0.6 * w * (1 if rng.uniform() < 0.5 else -1)
         ty = rng.uniform(-0.05, 0.05) * h
-        out.append(make_pair(h, w, similarity(th, sc, tx, ty, w / 2.0, h / 2.0), 1000 * seed + q, rgb=rgb))
+        out.append((h, w, similarity(th, sc, tx, ty, w / 2.0, h / 2.0), 1000 * seed + q))
     return out
 
 

@@ -287,3 +287,29 @@ def test_detect_batch_equals_single_images(case):
         assert np.array_equal(G.host(kps[i])[:Ks[i]].astype(np.uint32), kp1), (case, i, im.shape)
         if ch == 3:
             assert np.array_equal(G.host(grays[i])[:im.shape[0] * im.shape[1]].reshape(im.shape[:2]), g1)
+
+
+def test_autotuned_matcher_equals_builtin_and_caches():
+    """lp_set_autotune: the tuned (splits, pass-1 stride) give the built-in
+    choice's outputs bit for bit, one table row per size class, reused on the
+    class's later calls."""
+    Ls = (16, 32, 64, 128)
+    base = lp.Context(Ls=Ls, precision=lp.PREC_BF16)
+    tun = lp.Context(Ls=Ls, precision=lp.PREC_BF16)
+    tun.lp_set_autotune(True)
+    pairs = synth.uneven_pairs(3, seed=5, long_lo=480, long_hi=900)
+    for rep in range(2):
+        for p in pairs:
+            fa, fb = lp.features(base, p.A), lp.features(base, p.B)
+            want = [G.host(t) for t in lp.match(base, fa, fb)]
+            got = [G.host(t) for t in lp.match(tun, fa, fb)]
+            for x, y in zip(want, got):
+                assert np.array_equal(x, y, equal_nan=True)
+        table = tun.lp_autotune_table()
+        if rep == 0:
+            first = table
+        assert table == first and 1 <= len(table) <= 3
+    for row in table:
+        assert 1 <= row["splits"] <= 16 and row["pass1_stride"] in (2, 3, 4)
+        assert 0 < row["tuned_us"] <= row["builtin_us"]
+    assert tun.lp_sync_status() == 0
