@@ -382,6 +382,7 @@ def fp32_form_and_batch(args, rank):
     out["detect_3x3"] = detect_batch(ctx, images, flush, k)
     out["table2"] = table2(flush)
     out["uneven_64"] = uneven_64(flush, max(3, k // 2))
+    out["fp8_census"] = fp8_census()
     if args.train_pairs > 0:
         out["learned_proposal"] = learned_proposal(args, bt, images, ctx, HM, ni, va, flush, k, ref)
     return out
@@ -539,6 +540,56 @@ def training_pairs(seeds):
     workers = max(1, min(16, (os.cpu_count() or 2) - 1))
     with ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
         yield from ex.map(_training_pair, seeds, chunksize=8)
+
+
+def fp8_census(chunk=4096, margin=5e-3, capacity=192):
+    """How many columns per row a certified low-precision filter must keep on
+    the 2688x1600 pair, for BF16 (the built matcher's operands) and for E4M3
+    with per-descriptor scaling (max entry -> 448).  For unit descriptors the
+    estimate v~ = 1 - 2 a~.b~ of v = |b|^2 - 2 a.b is within
+    delta(v) = c + k (1 + eps - v), k = 2u + u^2 (u = 2^-8 for BF16, 2^-4 for
+    E4M3).  The window of a row is every column with v~ <= x + delta(x), x its
+    exact second-best plus the certification margin (the smallest x any first
+    pass could give).  Analysis only: plain torch matmuls, TF32 off."""
+    import torch
+
+    from paper_2405_08578_gb300 import lp, synth
+    pair = synth.pair_2688x1600(seed=0)
+    ctx = lp.Context(Ls=LS, precision=lp.PREC_BF16)
+    fa, fb = lp.features(ctx, pair.A), lp.features(ctx, pair.B)
+    A = fa.desc[fa.valid.bool()].float()
+    B = fb.desc[fb.valid.bool()].float()
+    tf32 = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    nb = (B * B).sum(1)
+
+    def e4m3(X):
+        s = 448.0 / X.abs().amax(1, keepdim=True).clamp_min(1e-30)
+        return (X * s).to(torch.float8_e4m3fn).float(), s
+
+    A8, sa = e4m3(A)
+    B8, sb = e4m3(B)
+    A16, B16 = A.bfloat16().float(), B.bfloat16().float()
+    eps, c = 5e-5, 2e-4
+    counts = {"bf16": [], "e4m3": []}
+    for r0 in range(0, A.shape[0], chunk):
+        a = A[r0:r0 + chunk]
+        v = nb[None, :] - 2.0 * (a @ B.T)
+        x = v.topk(2, dim=1, largest=False).values[:, 1:2] + margin
+        for name, u, vt in (("bf16", 2.0 ** -8, 1.0 - 2.0 * (A16[r0:r0 + chunk] @ B16.T)),
+                            ("e4m3", 2.0 ** -4, 1.0 - 2.0 * ((A8[r0:r0 + chunk] @ B8.T) / (sa[r0:r0 + chunk] * sb.T)))):
+            k = 2 * u + u * u
+            top = x + c + k * (1.0 + eps - x).clamp_min(0.0)
+            counts[name].append((vt <= top).sum(1))
+        del v
+    torch.backends.cuda.matmul.allow_tf32 = tf32
+    out = {"rows": int(A.shape[0]), "columns": int(B.shape[0]), "margin": margin, "list_capacity": capacity}
+    for name, cs in counts.items():
+        cs = torch.cat(cs).float()
+        out[name] = {"mean": float(cs.mean()), "median": float(cs.median()),
+                     "p99": float(cs.quantile(0.99)), "max": float(cs.max()),
+                     "rows_over_capacity": int((cs > capacity).sum())}
+    return out
 
 
 def _uneven_pair(spec):
@@ -856,6 +907,7 @@ def main():
         line["config"]["batch_3x3"] = extra["batch_3x3"]
         line["config"]["batch_3x3_fp32"] = extra["batch_3x3_fp32"]
         line["config"]["uneven_64"] = extra["uneven_64"]
+        line["config"]["fp8_census"] = extra["fp8_census"]
         line["config"]["mosaic_3x3"] = extra["mosaic_3x3"]
         line["config"]["table2"] = extra["table2"]
         line["config"]["detect_3x3"] = extra["detect_3x3"]
