@@ -641,10 +641,32 @@ k_rerank(const float* A, const uint8_t* vA, const float* B, const float* nb32, c
     if (ok) {
         reinterpret_cast<float4*>(qa[warp])[lane] = reinterpret_cast<const float4*>(A + i * 128)[lane];
         __syncwarp();
-        for (int e = lane; e < nsub * kSubCap; e += 32) {
-            if (e % kSubCap >= cnt[e / kSubCap]) continue;
-            const int j = lst[e];
-            top2_lex(b1, j1, b2, j2, fp32_form_value(qa[warp], B + (long long)j * 128, __ldg(nb32 + j)), j);
+        // the row's candidates, 32 sub-lists at a time: lane l holds sub-list
+        // l's count; an exclusive warp scan gives where each starts, and the
+        // lane scoring candidate c finds its sub-list by binary search
+        for (int s0 = 0; s0 < nsub; s0 += 32) {
+            const int n_l = s0 + lane < nsub ? cnt[s0 + lane] : 0;
+            int incl = n_l;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+                if (lane >= o) incl += v;
+            }
+            const int excl = incl - n_l, total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+            for (int c0 = 0; c0 < total; c0 += 32) {
+                const int c = c0 + lane;
+                int lo = 0;
+#pragma unroll
+                for (int st = 16; st; st >>= 1) {
+                    const int e = __shfl_sync(0xFFFFFFFFu, excl, lo + st);
+                    if (e <= c) lo += st;
+                }
+                const int base = __shfl_sync(0xFFFFFFFFu, excl, lo);
+                if (c < total) {
+                    const int j = lst[(s0 + lo) * kSubCap + (c - base)];
+                    top2_lex(b1, j1, b2, j2, fp32_form_value(qa[warp], B + (long long)j * 128, __ldg(nb32 + j)), j);
+                }
+            }
         }
         warp_top2(b1, j1, b2, j2);
         ok = b2 < T;   // T = x, the row's certification point
