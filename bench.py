@@ -159,7 +159,7 @@ def oracle_pair_seconds(pair, rows_sample=1500, desc_sample=15000, seed=0, M=300
 # workload, from one ncu capture, valid only for the kernel source it was taken
 # on (file SHA-1).
 PROFILED_TRAFFIC = {
-    "k_match_tc.cu": ("efad81b67bbf6cb74a3b77c37f5c900d472fdb95", 38.6299e6),
+    "k_match_tc.cu": ("a8f06ae411b141bf2d3920beba69ef3117608ff2", 43.92e6),
 }
 
 
