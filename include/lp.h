@@ -374,6 +374,17 @@ LP_API int lp_mlp_forward(lp_mlp* mlp, const float* feat, int64_t M_cap, const i
 LP_API int lp_mlp_train_step(lp_mlp* mlp, const float* feat, const uint8_t* label, int64_t B, float lr, float* loss,
                              void* stream);
 
+/* Failure injection for the batched distance passes of lp_stitch_pairs (BF16).
+ * The paper has no counterpart.  Those passes run in one persistent launch in
+ * which a pass-2 unit waits, for at most 2 s, until the pass-1 units of its
+ * rows have published their values.  hold > 0 adds hold to the number of
+ * completions every such wait expects, a number the launch never reaches: each
+ * wait gives up, the device status word records LP_ERR_TIMEOUT (read it with
+ * lp_sync_status), the launch drains and returns, and the context stays
+ * usable.  hold = 0 restores normal operation.  For tests of the timeout path.
+ * Errors: LP_ERR_ARG (hold < 0). */
+LP_API int lp_diag_set_batch_hold(lp_ctx* ctx, int32_t hold);
+
 /* Tile autotuning of the BF16 matcher (BASELINE's uneven-batch workload; the
  * paper has no counterpart).  on = 1: the first lp_match (or stitch call) of a
  * size class -- (ceil(log2 NA), ceil(log2 NB)) -- that runs outside stream

@@ -553,6 +553,395 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
     if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
 }
 
+// ------------------------------------------------------------------ batched passes
+// k_match_tc_batch: pass 1, the row thresholds and pass 2 of up to
+// kBatchPairs pairs in one persistent launch.  Work units (pair, pass, 128-row
+// block, column split) come from an atomic queue in a fixed order -- every
+// pass-1 unit of every pair before any pass-2 unit -- so a unit a CTA waits for
+// was taken earlier by a running CTA and every wait ends.  The producer warp
+// takes the units and hands them to the MMA and epilogue warps through a ring
+// of unit slots in shared memory.  A pass-1 epilogue warp, once its part of the
+// row block's pass-1 values is written, adds 1 (release) to the row block's
+// counter; a pass-2 unit's epilogue warps wait (bounded, 2 s, acquire) until
+// the counter reaches 8 warps x S splits (+ a diagnostic hold), then form the
+// row thresholds themselves (the arithmetic of k_row_threshold).  A wait that
+// gives up records LP_ERR_TIMEOUT; every other wait of the launch then stops at
+// its next check of the status word, and the CTAs drain and return.
+constexpr int kBatchPairs = 64;
+constexpr int kUnitSlots = 8;
+
+struct TcBatchPair {
+    long long NA, NB;
+    int nrb, S;
+    long long cps;
+    float2* pm;            // [kRanges S][NA]
+    float* thr;            // [NA] (written by pass 2 for the re-rank)
+    int32_t* cand;         // [NA][kRanges S][kSubCap]
+    int32_t* ncand;        // [NA][kRanges S]
+    int32_t* done;         // [nrb] pass-1 warps finished per row block (zero at launch)
+    const uint8_t* vA;     // [NA] query validity
+    int tstride;           // pass-1 tile stride
+};
+
+struct TcBatch {
+    CUtensorMap tA[kBatchPairs], tB[kBatchPairs];
+    TcBatchPair pr[kBatchPairs];
+    int u1[kBatchPairs + 1];   // prefix sums of pass-1 units (nrb S per pair)
+    int n;                     // pairs
+    int hold;                  // extra pass-1 completions a pass-2 unit waits for (diagnostic; 0 normally)
+    int32_t* queue;            // next unit (zero at launch)
+    int32_t* status;
+};
+
+struct BUnit {
+    int pass, pair, rb, split;
+    long long c0;
+    int ntiles, stride;
+};
+
+__device__ __forceinline__ BUnit batch_unit(const TcBatch& b, int u)
+{
+    BUnit w;
+    const int U1 = b.u1[b.n];
+    w.pass = u < U1 ? 1 : 2;
+    const int v = u < U1 ? u : u - U1;
+    int p = 0;
+    while (p + 1 < b.n && v >= b.u1[p + 1]) ++p;
+    const TcBatchPair& q = b.pr[p];
+    const int loc = v - b.u1[p];
+    w.pair = p;
+    w.rb = loc / q.S;
+    w.split = loc - w.rb * q.S;
+    w.c0 = (long long)w.split * q.cps;
+    long long c1 = w.c0 + q.cps;
+    if (c1 > q.NB) c1 = q.NB;
+    const int all = c1 > w.c0 ? (int)((c1 - w.c0 + kTileN - 1) / kTileN) : 0;
+    w.stride = w.pass == 1 ? q.tstride : 1;
+    w.ntiles = (all + w.stride - 1) / w.stride;
+    return w;
+}
+
+__device__ __forceinline__ int ld_acquire_gpu(const int32_t* p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void red_release_gpu(int32_t* p, int v)
+{
+    asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Bounded wait of one lane for *cnt >= target; false on timeout or when the
+// launch already failed (status word set).
+__device__ __forceinline__ bool wait_count(const int32_t* cnt, int target, int32_t* status, volatile int* abort_flag)
+{
+    if (ld_acquire_gpu(cnt) >= target) return true;
+    const uint64_t t0 = globaltimer();
+    for (uint32_t it = 1;; ++it) {
+        __nanosleep(200);
+        if (ld_acquire_gpu(cnt) >= target) return true;
+        if ((it & 15u) == 0) {
+            if (*abort_flag || ld_acquire_gpu(status) != 0) return false;
+            if (globaltimer() - t0 > 2000000000ull) {
+                set_status(status, DEV_TIMEOUT);
+                return false;
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kThreadsTC, 1) k_match_tc_batch(const __grid_constant__ TcBatch b)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t* sA = smem;
+    uint8_t* sB = smem + kABytes;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sB + kStages * kBBytes);
+    uint64_t* full = bars;                 // [kStages]
+    uint64_t* empty = bars + kStages;      // [kStages]
+    uint64_t* tfull = bars + 2 * kStages;  // [kTmemBufs]
+    uint64_t* tempty = tfull + kTmemBufs;  // [kTmemBufs]
+    uint64_t* afull = tempty + kTmemBufs;  // [1]
+    uint64_t* aempty = afull + 1;          // [1]
+    uint64_t* drain = aempty + 1;          // [1]
+    uint64_t* ufull = drain + 1;           // [kUnitSlots] a unit id is in the slot
+    uint64_t* uempty = ufull + kUnitSlots; // [kUnitSlots] the MMA lane and the 8 epilogue warps read it
+    int32_t* uslot = reinterpret_cast<int32_t*>(uempty + kUnitSlots);   // [kUnitSlots]
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(uslot + kUnitSlots);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int U = 2 * b.u1[b.n];
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(smem_u32(&full[s]), 1);
+            mbar_init(smem_u32(&empty[s]), 1);
+        }
+        for (int q = 0; q < kTmemBufs; ++q) {
+            mbar_init(smem_u32(&tfull[q]), 1);
+            mbar_init(smem_u32(&tempty[q]), kEpiWarps);
+        }
+        mbar_init(smem_u32(afull), 1);
+        mbar_init(smem_u32(aempty), 1);
+        mbar_init(smem_u32(drain), 1);
+        for (int q = 0; q < kUnitSlots; ++q) {
+            mbar_init(smem_u32(&ufull[q]), 1);
+            mbar_init(smem_u32(&uempty[q]), 1 + kEpiWarps);
+        }
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tmem_slot))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        // ---------------------------------------------------------- queue + TMA producer
+        if (lane == 0) {
+            long long n = 0;   // tile counter
+            int v = 0;         // A block counter
+            int armed[kStages];
+            int a_armed = -1;
+            for (int s = 0; s < kStages; ++s) armed[s] = -1;
+            bool ok = true;
+            int prev_key = -1, prev_pair = -1;
+            for (int m = 0; ok; ++m) {
+                const int slot = m % kUnitSlots;
+                ok = mbar_wait(smem_u32(&uempty[slot]), ((uint32_t)(m / kUnitSlots) & 1) ^ 1, abort_flag, b.status);
+                if (!ok) break;
+                const int u = atomicAdd(b.queue, 1);
+                uslot[slot] = u < U ? u : -1;
+                mbar_arrive(smem_u32(&ufull[slot]));
+                if (u >= U) break;
+                const BUnit w = batch_unit(b, u);
+                if (w.ntiles == 0) continue;
+                if (w.pair != prev_pair) {
+                    tma_prefetch_desc(&b.tA[w.pair]);
+                    tma_prefetch_desc(&b.tB[w.pair]);
+                    prev_pair = w.pair;
+                }
+                const int key = w.pair * 65536 + w.rb;
+                if (key != prev_key) {
+                    ok = mbar_wait(smem_u32(aempty), (v & 1) ^ 1, abort_flag, b.status);
+                    if (!ok) break;
+                    mbar_expect_tx(smem_u32(afull), kABytes);
+                    tma_load_2d(smem_u32(sA), &b.tA[w.pair], 0, w.rb * kRowsPerUnit, smem_u32(afull));
+                    tma_load_2d(smem_u32(sA + kABytes / 2), &b.tA[w.pair], 64, w.rb * kRowsPerUnit, smem_u32(afull));
+                    a_armed = v;
+                    ++v;
+                    prev_key = key;
+                }
+                const int st = w.stride;
+                for (int t = 0; t < w.ntiles; ++t, ++n) {
+                    const int s = (int)(n % kStages);
+                    const uint32_t k = (uint32_t)(n / kStages);
+                    ok = mbar_wait(smem_u32(&empty[s]), (k & 1) ^ 1, abort_flag, b.status);
+                    if (!ok) break;
+                    uint8_t* dst = sB + s * kBBytes;
+                    const int y = (int)(w.c0 + (long long)t * st * kTileN);
+                    mbar_expect_tx(smem_u32(&full[s]), kBBytes);
+                    tma_load_2d(smem_u32(dst), &b.tB[w.pair], 0, y, smem_u32(&full[s]));
+                    tma_load_2d(smem_u32(dst + kBBytes / 2), &b.tB[w.pair], 64, y, smem_u32(&full[s]));
+                    armed[s] = (int)k;
+                }
+            }
+            if (!ok) {
+                *abort_flag = 1;
+                for (int s = 0; s < kStages; ++s) {
+                    if (armed[s] < 0) continue;
+                    const uint64_t t0 = globaltimer();
+                    while (!mbar_try(smem_u32(&full[s]), (uint32_t)armed[s] & 1u) && globaltimer() - t0 < 200000000ull) {
+                    }
+                }
+                if (a_armed >= 0) {
+                    const uint64_t t0 = globaltimer();
+                    while (!mbar_try(smem_u32(afull), (uint32_t)a_armed & 1u) && globaltimer() - t0 < 200000000ull) {
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            const uint64_t dA0 = sdesc(smem_u32(sA)), dB0 = sdesc(smem_u32(sB));
+            long long n = 0;
+            int v = 0;
+            bool ok = true;
+            int prev_key = -1;
+            for (int m = 0; ok; ++m) {
+                const int slot = m % kUnitSlots;
+                ok = mbar_wait(smem_u32(&ufull[slot]), (uint32_t)(m / kUnitSlots) & 1, abort_flag, b.status);
+                if (!ok) break;
+                const int u = uslot[slot];
+                mbar_arrive(smem_u32(&uempty[slot]));
+                if (u < 0) break;
+                const BUnit w = batch_unit(b, u);
+                if (w.ntiles == 0) continue;
+                const int key = w.pair * 65536 + w.rb;
+                if (key != prev_key) {
+                    if (v > 0) mma_commit(smem_u32(aempty));
+                    ok = mbar_wait(smem_u32(afull), v & 1, abort_flag, b.status);
+                    ++v;
+                    prev_key = key;
+                    if (!ok) break;
+                    tc_fence_after();
+                }
+                for (int t = 0; t < w.ntiles; ++t, ++n) {
+                    const int s = (int)(n % kStages);
+                    const uint32_t k = (uint32_t)(n / kStages);
+                    const int bb = (int)(n % kTmemBufs);
+                    const uint32_t kb = (uint32_t)(n / kTmemBufs);
+                    ok = mbar_wait(smem_u32(&tempty[bb]), (kb & 1) ^ 1, abort_flag, b.status);
+                    if (!ok) break;
+                    ok = mbar_wait(smem_u32(&full[s]), k & 1, abort_flag, b.status);
+                    if (!ok) break;
+                    tc_fence_after();
+                    const uint64_t dB = dB0 + (uint64_t)((s * kBBytes) >> 4);
+                    const uint32_t d = tmem + (uint32_t)(bb * kTileN);
+#pragma unroll
+                    for (int h = 0; h < 2; ++h)
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk) {
+                            const uint64_t ad = dA0 + (uint64_t)((h * (kABytes / 2) + kk * 32) >> 4);
+                            const uint64_t bd = dB + (uint64_t)((h * (kBBytes / 2) + kk * 32) >> 4);
+                            mma_bf16(d, ad, bd, (h | kk) ? 1u : 0u);
+                        }
+                    mma_commit(smem_u32(&empty[s]));
+                    mma_commit(smem_u32(&tfull[bb]));
+                }
+            }
+            mma_commit(smem_u32(drain));
+            const uint64_t t0 = globaltimer();
+            while (!mbar_try(smem_u32(drain), 0) && globaltimer() - t0 < 2000000000ull) {
+            }
+        }
+    } else {
+        // ---------------------------------------------------------- epilogue
+        const int q = warp & 3;
+        const int rg = (warp - 2) >> 2;
+        const int row_in_unit = q * 32 + lane;
+        long long n = 0;
+        for (int m = 0;; ++m) {
+            const int slot = m % kUnitSlots;
+            // every lane waits; the warp acts on one decision (they differ only after a timeout)
+            if (!__all_sync(0xFFFFFFFFu, mbar_wait(smem_u32(&ufull[slot]), (uint32_t)(m / kUnitSlots) & 1, abort_flag,
+                                                   b.status)))
+                break;
+            const int u = uslot[slot];
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&uempty[slot]));
+            if (u < 0) break;
+            const BUnit w = batch_unit(b, u);
+            const TcBatchPair& pp = b.pr[w.pair];
+            long long c1 = w.c0 + pp.cps;
+            if (c1 > pp.NB) c1 = pp.NB;
+            const long long row = (long long)w.rb * kRowsPerUnit + row_in_unit;
+            const bool live = row < pp.NA;
+            const long long sub = (live ? row : 0) * (kRanges * pp.S) + w.split * kRanges + rg;
+            int32_t* const dst = pp.cand + sub * kSubCap;
+            float TD = INFINITY;
+            if (w.pass == 2) {
+                // the row block's pass-1 values: every epilogue warp of its S pass-1 units has released them
+                bool got = true;
+                if (lane == 0) got = wait_count(pp.done + w.rb, kEpiWarps * pp.S + b.hold, b.status, abort_flag);
+                if (!__shfl_sync(0xFFFFFFFFu, got, 0)) {
+                    *abort_flag = 1;
+                    break;
+                }
+                if (live) {
+                    // x = m2 + margin (k_row_threshold's arithmetic), -inf for an invalid query row
+                    float m1 = INFINITY, m2 = INFINITY;
+                    for (int s2 = 0; s2 < kRanges * pp.S; ++s2) {
+                        const float2 qv = pp.pm[(long long)s2 * pp.NA + row];
+                        const float lo = fminf(qv.x, qv.y), hi = fmaxf(qv.x, qv.y);
+                        m2 = fminf(fminf(m2, hi), fmaxf(m1, lo));
+                        m1 = fminf(m1, lo);
+                    }
+                    const float xt = pp.vA[row] ? fminf(m2 + kMargin, kCandCap) : -INFINITY;
+                    if (rg == 0) pp.thr[row] = xt;
+                    TD = 0.5f * (1.f - window_top(xt)) - 1e-6f;
+                }
+            }
+            float d1 = -INFINITY, d2 = -INFINITY;
+            int nc = 0;
+            bool ok = true;
+            for (int t = 0; t < w.ntiles; ++t, ++n) {
+                const int bb = (int)(n % kTmemBufs);
+                const uint32_t kb = (uint32_t)(n / kTmemBufs);
+                ok = mbar_wait(smem_u32(&tfull[bb]), kb & 1, abort_flag, b.status);
+                if (!__all_sync(0xFFFFFFFFu, ok)) { ok = false; break; }
+                tc_fence_after();
+                const long long cbase = w.c0 + (long long)t * w.stride * kTileN + rg * kRangeCols;
+                const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(bb * kTileN + rg * kRangeCols);
+                uint32_t r[kChunks][32];
+#pragma unroll
+                for (int ch = 0; ch < kChunks; ++ch) tmem_ld32(tbase + 32 * ch, r[ch]);
+#pragma unroll
+                for (int ch = 0; ch < kChunks; ++ch) tmem_wait(r[ch]);
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&tempty[bb]));
+#pragma unroll
+                for (int ch = 0; ch < kChunks; ++ch) {
+                    float dv[32];
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) dv[i] = __uint_as_float(r[ch][i]);
+                    const long long j0 = cbase + ch * 32;
+                    if (j0 + 32 > c1) {
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) dv[i] = j0 + i < c1 ? dv[i] : -INFINITY;
+                    }
+                    float gx[4];
+#pragma unroll
+                    for (int g = 0; g < 4; ++g)
+                        gx[g] = max3f(max3f(dv[8 * g + 0], dv[8 * g + 1], dv[8 * g + 2]),
+                                      max3f(dv[8 * g + 3], dv[8 * g + 4], dv[8 * g + 5]),
+                                      fmaxf(dv[8 * g + 6], dv[8 * g + 7]));
+                    const float cmax = max3f(gx[0], gx[1], fmaxf(gx[2], gx[3]));
+                    if (w.pass == 1) {
+                        const float lo = fminf(d1, cmax);
+                        d1 = fmaxf(d1, cmax);
+                        d2 = fmaxf(d2, lo);
+                    } else if (cmax >= TD) {
+                        uint32_t mk = 0;
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) mk |= (dv[i] >= TD ? 1u : 0u) << i;
+                        while (mk) {
+                            const int j = (int)j0 + __ffs(mk) - 1;
+                            mk &= mk - 1;
+                            if (nc < kSubCap) dst[nc] = j;
+                            ++nc;
+                        }
+                    }
+                }
+            }
+            if (!ok) break;
+            if (w.pass == 1) {
+                if (live)
+                    pp.pm[((long long)w.split * kRanges + rg) * pp.NA + row] =
+                        make_float2(1.f - 2.f * d1, 1.f - 2.f * d2);
+                __syncwarp();
+                if (lane == 0) red_release_gpu(pp.done + w.rb, 1);
+            } else if (live) {
+                pp.ncand[sub] = nc;
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+}
+
 // ------------------------------------------------------------------ re-rank
 // FP32-form value of column j for query a: exactly the FP32 kernel's
 // arithmetic (sequential fmaf over k = 0..127, then fmaf(-2, dot, |b|^2)).
@@ -868,6 +1257,129 @@ TcLayout tc_layout(long long NA, long long NB, int sms, int S_force = 0)
     return L;
 }
 
+// ---------------------------------------------------------------- batched host side
+// Words of the batch's sync block: per launch of up to kBatchPairs pairs, a
+// queue counter and one pass-1 counter per row block of each pair.
+size_t batch_sync_words_impl(const MatchArgs* args, int P)
+{
+    size_t w = 0;
+    int in_launch = 0;
+    for (int i = 0; i < P; ++i) {
+        if (args[i].NA == 0 || args[i].NB == 0) continue;
+        if (in_launch == 0) w += 1;
+        w += (size_t)((args[i].NA + kRowsPerUnit - 1) / kRowsPerUnit);
+        if (++in_launch == kBatchPairs) in_launch = 0;
+    }
+    return w;
+}
+
+}  // namespace
+
+size_t match_bf16_batch_sync_words(const MatchArgs* args, int P) { return batch_sync_words_impl(args, P); }
+
+cudaError_t launch_match_bf16_batch(const MatchArgs* args, void* const* ws, const size_t* ws_bytes, int P,
+                                    int32_t* sync, int hold, int num_sms, cudaStream_t s)
+{
+    cudaError_t e;
+    const size_t words = batch_sync_words_impl(args, P);
+    if (words == 0) return cudaSuccess;
+    if ((e = cudaMemsetAsync(sync, 0, words * sizeof(int32_t), s)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_match_tc_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTC)) !=
+        cudaSuccess)
+        return e;
+    int per_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_match_tc_batch, kThreadsTC, kSmemTC)) !=
+        cudaSuccess)
+        return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    TcBatch b;   // about 22 KB of kernel parameters; the launch copies it
+    int32_t* cursor = sync;
+    for (int i0 = 0; i0 < P;) {
+        memset(&b, 0, sizeof b);
+        b.queue = cursor++;
+        b.status = args[i0].status;
+        b.hold = hold;
+        int n = 0;
+        for (; i0 < P && n < kBatchPairs; ++i0) {
+            const MatchArgs& a = args[i0];
+            if (a.NA == 0 || a.NB == 0) continue;
+            const TcLayout L = tc_layout(a.NA, a.NB, num_sms, a.splits);
+            if (ws_bytes[i0] < L.total) return cudaErrorInvalidValue;
+            uint8_t* w = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(ws[i0]) + 255) & ~uintptr_t(255));
+            if (!make_map(&b.tA[n], a.dA16, a.NA, kRowsPerUnit) || !make_map(&b.tB[n], a.dB16, a.NB, kTileN))
+                return cudaErrorInvalidValue;
+            TcBatchPair& q = b.pr[n];
+            q.NA = a.NA;
+            q.NB = a.NB;
+            q.nrb = (int)((a.NA + kRowsPerUnit - 1) / kRowsPerUnit);
+            q.S = L.S;
+            const long long tiles = (a.NB + kTileN - 1) / kTileN;
+            q.cps = ((tiles + L.S - 1) / L.S) * kTileN;
+            q.pm = reinterpret_cast<float2*>(w + L.off_pm);
+            q.thr = reinterpret_cast<float*>(w + L.off_thr);
+            q.cand = reinterpret_cast<int32_t*>(w + L.off_cand);
+            q.ncand = reinterpret_cast<int32_t*>(w + L.off_ncand);
+            q.vA = a.vA;
+            q.tstride = a.pass1_stride > 0 ? a.pass1_stride : kPass1Stride;
+            q.done = cursor;
+            cursor += q.nrb;
+            b.u1[n + 1] = b.u1[n] + q.nrb * q.S;
+            ++n;
+        }
+        if (n == 0) break;
+        b.n = n;
+        const int U = 2 * b.u1[n];
+        k_match_tc_batch<<<(unsigned)std::min(U, per_sm * num_sms), kThreadsTC, kSmemTC, s>>>(b);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// Re-rank, re-scan and finish of a pair whose distance passes ran in
+// k_match_tc_batch (thresholds and candidate sub-lists in its workspace); the
+// row norms come in a.normA (query rows) and a.normB (+inf for invalid rows).
+cudaError_t launch_match_bf16_tail(const MatchArgs& a, void* ws, size_t ws_bytes, int num_sms, cudaStream_t s)
+{
+    if (a.NA == 0) return cudaSuccess;
+    const TcLayout L = tc_layout(a.NA, a.NB, num_sms, a.splits);
+    if (ws_bytes < L.total || !a.normA || (a.NB > 0 && !a.normB)) return cudaErrorInvalidValue;
+    uint8_t* w = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(ws) + 255) & ~uintptr_t(255));
+    const float* thr = reinterpret_cast<const float*>(w + L.off_thr);
+    const int32_t* cand = reinterpret_cast<const int32_t*>(w + L.off_cand);
+    const int32_t* ncand = reinterpret_cast<const int32_t*>(w + L.off_ncand);
+    float4* part1 = reinterpret_cast<float4*>(w + L.off_part1);
+    int32_t* rows = reinterpret_cast<int32_t*>(w + L.off_rows);
+    int32_t* cnt = reinterpret_cast<int32_t*>(w + L.off_cnt);
+    float4* part_r = reinterpret_cast<float4*>(w + L.off_part_r);
+    cudaError_t e;
+    if (a.NB == 0) {
+        k_match_finish<<<(unsigned)((a.NA + 255) / 256), 256, 0, s>>>(part1, 0, a.NA, a.normA, a.vA, a.ratio2,
+                                                                      a.delta_s2, a.match, a.d1, a.d2);
+        return cudaGetLastError();
+    }
+    if ((e = cudaMemsetAsync(cnt, 0, sizeof(int32_t), s)) != cudaSuccess) return e;
+    k_rerank<<<(unsigned)((a.NA + kRerankWarps - 1) / kRerankWarps), kRerankWarps * 32, 0, s>>>(
+        a.dA, a.vA, a.dB, a.normB, cand, ncand, kRanges * L.S, thr, a.NA, part1, rows, cnt);
+    if ((e = cudaFuncSetAttribute(k_rescan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRescanSmem)) !=
+        cudaSuccess)
+        return e;
+    k_rescan<<<(unsigned)(4 * num_sms), kRescanThreads, kRescanSmem, s>>>(a.dA, a.dB, a.normB, a.NA, a.NB, rows, cnt,
+                                                                           part_r);
+    k_rescan_merge<<<(unsigned)std::min<long long>((a.NA + 7) / 8, 2ll * num_sms), 256, 0, s>>>(part_r, a.NA, a.NB,
+                                                                                             rows, cnt, part1);
+    k_match_finish<<<(unsigned)((a.NA + 255) / 256), 256, 0, s>>>(part1, 1, a.NA, a.normA, a.vA, a.ratio2, a.delta_s2,
+                                                                  a.match, a.d1, a.d2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_row_norms(const float* d, const uint8_t* v, int64_t n, float* out, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    k_row_norms<<<(unsigned)((n * 32 + 255) / 256), 256, 0, s>>>(d, v, n, out, INFINITY);
+    return cudaGetLastError();
+}
+
+namespace {
 }  // namespace
 
 bool encode_tiled_2d(CUtensorMap* m, CUtensorMapDataType dt, const void* base, uint64_t inner, uint64_t outer,

@@ -64,12 +64,13 @@ struct lp_ctx {
     };
     std::vector<TuneEntry> tune;
     int last_S = 0;                     // column splits of the last BF16 match
+    int batch_hold = 0;                 // lp_diag_set_batch_hold: extra pass-1 completions batch waits expect
     lp::Fork fork{};                    // auxiliary streams of lp_describe (created on first use)
     bool fork_ready = false;
     cudaStream_t img_stream = nullptr;  // lp_stitch_pair: image B's detect and describe;
                                         // lp_stitch_pairs: the pairs' RANSAC
     cudaEvent_t img_ev[2] = {nullptr, nullptr};
-    cudaEvent_t pair_ev[3] = {nullptr, nullptr, nullptr};   // lp_stitch_pairs: compacted, slot 0 / 1 free
+    cudaEvent_t pair_ev[4] = {nullptr, nullptr, nullptr, nullptr};   // lp_stitch_pairs: compacted, lane slot 0..2 free
     DBuf buf[B_COUNT];
     char err[512];
 };
@@ -94,7 +95,7 @@ int ensure_fork(lp_ctx* c)
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->img_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->img_ev[0], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->img_ev[1], cudaEventDisableTiming);
-    for (int q = 0; q < 3 && e == cudaSuccess; ++q) e = cudaEventCreateWithFlags(&c->pair_ev[q], cudaEventDisableTiming);
+    for (int q = 0; q < 4 && e == cudaSuccess; ++q) e = cudaEventCreateWithFlags(&c->pair_ev[q], cudaEventDisableTiming);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(c, LP_ERR_CUDA, "auxiliary streams: %s", cudaGetErrorString(e));
@@ -457,6 +458,21 @@ int tune_match(lp_ctx* c, lp::MatchArgs& a, cudaStream_t s)
     return LP_OK;
 }
 
+// The tuned (splits, pass-1 stride) of a size class when the tuner is on and
+// the class is in the table; 0 (the built-in choice) otherwise.
+int tuned_splits(const lp_ctx* c, int64_t NA, int64_t NB, int* stride)
+{
+    *stride = 0;
+    if (!c->autotune) return 0;
+    const int ba = log2_bucket(NA), bb = log2_bucket(NB);
+    for (const auto& e : c->tune)
+        if (e.ba == ba && e.bb == bb) {
+            *stride = e.stride;
+            return e.S;
+        }
+    return 0;
+}
+
 }  // namespace
 
 int lp_match(lp_ctx* c, const float* dA, const uint16_t* dA_bf16, const uint8_t* vA, int64_t NA, const float* dB,
@@ -745,41 +761,70 @@ int lp_stitch_pairs_ids(lp_ctx* c, const lp_image* imgs, int N, const int32_t* p
         ib[i].d16 = o; o += bf ? al256(256 * (size_t)K + 16) : 0;
         ib[i].val = o; o += al256((size_t)K + 8);
     }
-    // two slots of match outputs, compacted points and inlier masks: pair q's
-    // RANSAC (and, with the learned proposal, its features and forward pass)
-    // run on the context's second stream beside the next pair's matching
-    const size_t row_slot = al256(4 * (size_t)Kmax + 8);
-    const size_t o_match = o; o += 2 * row_slot;
-    const size_t o_d1 = o; o += 2 * row_slot;
-    const size_t o_d2 = o; o += 2 * row_slot;
-    const size_t o_pts = o; o += 2 * al256(16 * (size_t)Kmax + 16);
-    const size_t o_inl = o; o += 2 * al256((size_t)Kmax + 8);
-    const size_t pts_slot = al256(16 * (size_t)Kmax + 16), inl_slot = al256((size_t)Kmax + 8);
-    const size_t o_M = o; o += al256(4 * (size_t)P + 8);
+    // kLanes slots of match outputs, compacted points, inlier masks and RANSAC
+    // workspace: pair q's RANSAC (and, with the learned proposal, its features,
+    // forward pass and guided RANSAC) runs on lane q % kLanes -- the context's
+    // image stream and its two auxiliary streams -- beside the next pairs'
+    // matching tails and each other's RANSAC
+    constexpr int kLanes = 3;
     const bool guided = c->proposal != nullptr;
-    const size_t o_rows = o; o += guided ? 2 * row_slot : 0;
+    const int Ttot = c->cfg.ransac_iters + (guided ? c->guided_iters : 0);
+    const size_t row_slot = al256(4 * (size_t)Kmax + 8);
+    const size_t o_match = o; o += kLanes * row_slot;
+    const size_t o_d1 = o; o += kLanes * row_slot;
+    const size_t o_d2 = o; o += kLanes * row_slot;
+    const size_t pts_slot = al256(16 * (size_t)Kmax + 16), inl_slot = al256((size_t)Kmax + 8);
+    const size_t o_pts = o; o += kLanes * pts_slot;
+    const size_t o_inl = o; o += kLanes * inl_slot;
+    const size_t o_M = o; o += al256(4 * (size_t)P + 8);
+    const size_t o_rows = o; o += guided ? kLanes * row_slot : 0;
     const size_t feat_slot = guided ? al256(32 * (size_t)Kmax + 32) : 0;
-    const size_t o_feat = o; o += 2 * feat_slot;
-    const size_t o_prob = o; o += guided ? al256(4 * (size_t)Kmax + 8) : 0;
+    const size_t o_feat = o; o += kLanes * feat_slot;
+    const size_t o_prob = o; o += guided ? kLanes * row_slot : 0;
+    const size_t rws_slot = al256(lp::ransac_workspace(Kmax, Ttot));
+    const size_t o_rws = o; o += kLanes * rws_slot;
+    const size_t pre_slot = guided ? al256(sizeof(unsigned long long) * (size_t)(Kmax + 1)) : 0;
+    const size_t o_pre = o; o += kLanes * pre_slot;
+    // BF16: the distance passes of every pair run first, in persistent launches
+    // over all pairs (k_match_tc_batch); each pair then keeps its thresholds and
+    // candidate lists in a workspace of its own until its tail (re-rank,
+    // re-scan, finish) runs in the pair loop.  Row norms once per image.
+    std::vector<lp::MatchArgs> margs(bf ? (size_t)P : 0);
+    std::vector<size_t> o_pws(bf ? (size_t)P : 0), pws_bytes(bf ? (size_t)P : 0);
+    std::vector<size_t> o_norm(bf ? (size_t)N : 0);
+    size_t o_sync = 0;
+    if (bf) {
+        for (int i = 0; i < N; ++i) { o_norm[i] = o; o += al256(4 * (size_t)ib[i].K + 8); }
+        for (int q = 0; q < P; ++q) {
+            const ImgBufs &A = ib[pl[2 * q]], &B = ib[pl[2 * q + 1]];
+            lp::MatchArgs& a = margs[q];
+            a.NA = A.K;
+            a.NB = B.K;
+            a.splits = tuned_splits(c, A.K, B.K, &a.pass1_stride);
+            pws_bytes[q] = lp::match_bf16_workspace(A.K, B.K, c->num_sms, a.splits);
+            o_pws[q] = o;
+            o += al256(pws_bytes[q]);
+        }
+        o_sync = o;
+        o += al256(4 * lp::match_bf16_batch_sync_words(margs.data(), P) + 8);
+    }
     int r = ensure(c, B_BATCH, o + 256);
     if (r) return r;
     if ((r = ensure_fork(c))) return r;
     size_t mws = 0;
     for (int q = 0; q < P; ++q) {
         const int64_t KA = ib[pl[2 * q]].K, KB = ib[pl[2 * q + 1]].K;
-        mws = std::max(mws, bf ? lp::match_bf16_workspace(KA, KB, c->num_sms) : lp::match_fp32_workspace(KA, KB, c->num_sms));
+        if (!bf) mws = std::max(mws, lp::match_fp32_workspace(KA, KB, c->num_sms));
     }
-    const int Ttot = c->cfg.ransac_iters + (guided ? c->guided_iters : 0);
-    if ((r = ensure(c, B_MATCH_WS, mws)) || (r = ensure(c, B_RANSAC_WS, lp::ransac_workspace(Kmax, Ttot))) ||
-        (r = ensure(c, B_COMPACT, lp::compact_workspace(Kmax))) ||
-        (guided && (r = ensure(c, B_PREFIX, sizeof(unsigned long long) * (size_t)(Kmax + 1)))))
+    if ((r = ensure(c, B_MATCH_WS, std::max<size_t>(mws, 256))) ||
+        (r = ensure(c, B_COMPACT, lp::compact_workspace(Kmax))))
         return r;
     cudaStream_t s = S(stream);
     if (!c->luts_ready && (r = build_luts(c, s))) return r;
     uint8_t* base = reinterpret_cast<uint8_t*>(al256(reinterpret_cast<uintptr_t>(c->buf[B_BATCH].p)));
     int32_t* Mbuf = M_out ? M_out : reinterpret_cast<int32_t*>(base + o_M);
 
-    std::vector<long long> key = {N, P, ch, (long long)(uintptr_t)HM, (long long)(uintptr_t)n_in,
+    std::vector<long long> key = {N, P, ch, c->batch_hold, (long long)(uintptr_t)HM, (long long)(uintptr_t)n_in,
                                   (long long)(uintptr_t)valid, (long long)(uintptr_t)Mbuf,
                                   (long long)(uintptr_t)c->buf[B_BATCH].p, (long long)(uintptr_t)c->buf[B_MATCH_WS].p,
                                   (long long)(uintptr_t)c->buf[B_RANSAC_WS].p,
@@ -820,20 +865,47 @@ int lp_stitch_pairs_ids(lp_ctx* c, const lp_image* imgs, int N, const int32_t* p
                                   bf ? (uint16_t*)(base + ib[i].d16) : nullptr, base + ib[i].val, stream)))
                 return rr;
         }
-        // RANSAC of pair q (with the learned proposal: its features, forward
-        // pass and guided RANSAC) on the second stream, beside pair q + 1's
-        // matching; every buffer they read has two slots
-        const bool overlap = true;
-        cudaStream_t sr = overlap ? c->img_stream : s;
-        if (overlap) {
-            LP_CUDA(c, cudaEventRecord(c->pair_ev[1], s));
-            LP_CUDA(c, cudaStreamWaitEvent(sr, c->pair_ev[1], 0));
-            LP_CUDA(c, cudaEventRecord(c->pair_ev[2], s));
+        if (bf) {
+            // row norms once per image, then the distance passes of every pair
+            const float ratio2 = (float)((double)c->cfg.ratio * (double)c->cfg.ratio);
+            const bool ds = c->cfg.delta_s > 0.f && isfinite(c->cfg.delta_s);
+            const float delta_s2 = ds ? (float)((double)c->cfg.delta_s * (double)c->cfg.delta_s) : INFINITY;
+            for (int i = 0; i < N; ++i)
+                LP_CUDA(c, lp::launch_row_norms((const float*)(base + ib[i].desc), base + ib[i].val, ib[i].K,
+                                                (float*)(base + o_norm[i]), s));
+            std::vector<void*> wsp((size_t)P);
+            for (int q = 0; q < P; ++q) {
+                const int a_ = pl[2 * q], b_ = pl[2 * q + 1];
+                lp::MatchArgs& a = margs[q];
+                a.dA = (const float*)(base + ib[a_].desc);
+                a.dA16 = (const uint16_t*)(base + ib[a_].d16);
+                a.vA = base + ib[a_].val;
+                a.dB = (const float*)(base + ib[b_].desc);
+                a.dB16 = (const uint16_t*)(base + ib[b_].d16);
+                a.vB = base + ib[b_].val;
+                a.ratio2 = ratio2;
+                a.delta_s2 = delta_s2;
+                a.status = c->d_status;
+                a.normA = (const float*)(base + o_norm[a_]);
+                a.normB = (const float*)(base + o_norm[b_]);
+                wsp[q] = base + o_pws[q];
+            }
+            LP_CUDA(c, lp::launch_match_bf16_batch(margs.data(), wsp.data(), pws_bytes.data(), P,
+                                                   (int32_t*)(base + o_sync), c->batch_hold, c->num_sms, s));
+        }
+        // lanes: pair q's RANSAC on stream rs[q % kLanes]; the lane's slot of
+        // buffers is reused by pair q + kLanes only after that RANSAC ended
+        cudaStream_t rs[kLanes] = {c->img_stream, c->fork.aux[0], c->fork.aux[1]};
+        LP_CUDA(c, cudaEventRecord(c->pair_ev[0], s));
+        for (int k = 0; k < kLanes; ++k) {
+            LP_CUDA(c, cudaStreamWaitEvent(rs[k], c->pair_ev[0], 0));
+            LP_CUDA(c, cudaEventRecord(c->pair_ev[1 + k], s));
         }
         for (int q = 0; q < P; ++q) {
             const int a = pl[2 * q], b = pl[2 * q + 1];
             const ImgBufs &A = ib[a], &B = ib[b];
-            const int slot = overlap ? (q & 1) : 0;
+            const int slot = q % kLanes;
+            cudaStream_t sr = rs[slot];
             float* pts = (float*)(base + o_pts + slot * pts_slot);
             uint8_t* inl = base + o_inl + slot * inl_slot;
             float* feat = (float*)(base + o_feat + slot * feat_slot);
@@ -841,44 +913,51 @@ int lp_stitch_pairs_ids(lp_ctx* c, const lp_image* imgs, int N, const int32_t* p
             float* d1 = (float*)(base + o_d1 + slot * row_slot);
             float* d2 = (float*)(base + o_d2 + slot * row_slot);
             int32_t* rows = guided ? (int32_t*)(base + o_rows + slot * row_slot) : nullptr;
-            // the slot's previous RANSAC (pair q - 2) has finished reading it
-            if (overlap) LP_CUDA(c, cudaStreamWaitEvent(s, c->pair_ev[1 + slot], 0));
+            float* prob = guided ? (float*)(base + o_prob + slot * row_slot) : nullptr;
+            void* rws = base + o_rws + slot * rws_slot;
+            auto* pre = guided ? reinterpret_cast<unsigned long long*>(base + o_pre + slot * pre_slot) : nullptr;
+            // the slot's previous RANSAC (pair q - kLanes) has finished reading it
+            LP_CUDA(c, cudaStreamWaitEvent(s, c->pair_ev[1 + slot], 0));
             if (A.K == 0) {
                 LP_CUDA(c, cudaMemsetAsync(Mbuf + q, 0, sizeof(int32_t), s));
             } else {
-                if ((rr = lp_match(c, (const float*)(base + A.desc), bf ? (const uint16_t*)(base + A.d16) : nullptr,
-                                   base + A.val, A.K, (const float*)(base + B.desc),
-                                   bf ? (const uint16_t*)(base + B.d16) : nullptr, base + B.val, B.K, mt, d1, d2,
-                                   stream)))
+                if (bf) {
+                    lp::MatchArgs ma = margs[q];
+                    ma.match = mt;
+                    ma.d1 = d1;
+                    ma.d2 = d2;
+                    LP_CUDA(c, lp::launch_match_bf16_tail(ma, base + o_pws[q], pws_bytes[q], c->num_sms, s));
+                } else if ((rr = lp_match(c, (const float*)(base + A.desc), nullptr, base + A.val, A.K,
+                                          (const float*)(base + B.desc), nullptr, base + B.val, B.K, mt, d1, d2,
+                                          stream))) {
                     return rr;
+                }
                 if ((rr = lp_compact(c, (const uint32_t*)(base + A.kp), imgs[a].W, (const uint32_t*)(base + B.kp),
                                      imgs[b].W, mt, A.K, pts, rows, Mbuf + q, stream)))
                     return rr;
             }
-            if (overlap) {
-                LP_CUDA(c, cudaEventRecord(c->pair_ev[0], s));
-                LP_CUDA(c, cudaStreamWaitEvent(sr, c->pair_ev[0], 0));
-            }
-            if (guided && A.K > 0 &&
-                (rr = lp_mlp_features(c, (const uint32_t*)(base + A.kp), base + A.ori, imgs[a].H, imgs[a].W,
-                                      (const uint32_t*)(base + B.kp), base + B.ori, imgs[b].H, imgs[b].W, mt, d1, d2,
-                                      rows, Mbuf + q, A.K, feat, sr)))
-                return rr;
+            LP_CUDA(c, cudaEventRecord(c->pair_ev[0], s));
+            LP_CUDA(c, cudaStreamWaitEvent(sr, c->pair_ev[0], 0));
             if (guided && A.K > 0) {
-                float* prob = (float*)(base + o_prob);
+                if ((rr = lp_mlp_features(c, (const uint32_t*)(base + A.kp), base + A.ori, imgs[a].H, imgs[a].W,
+                                          (const uint32_t*)(base + B.kp), base + B.ori, imgs[b].H, imgs[b].W, mt, d1,
+                                          d2, rows, Mbuf + q, A.K, feat, sr)))
+                    return rr;
                 if ((rr = lp_mlp_forward(c->proposal, feat, A.K, Mbuf + q, prob, nullptr, sr)))
                     return fail(c, rr, "lp_mlp_forward failed");
-                rr = lp_ransac_prior(c, pts, A.K, Mbuf + q, prob, c->guided_iters, pid[q], HM + 9 * (size_t)q, inl,
-                                     n_in + q, nullptr, nullptr, sr);
-            } else
-                rr = lp_ransac(c, pts, A.K, Mbuf + q, pid[q], HM + 9 * (size_t)q, inl, n_in + q, nullptr, sr);
-            if (rr) return rr;
-            if (overlap) LP_CUDA(c, cudaEventRecord(c->pair_ev[1 + slot], sr));
+                LP_CUDA(c, lp::launch_guided_prefix(prob, A.K, Mbuf + q, pre, sr));
+                LP_CUDA(c, lp::launch_ransac_prior(pts, A.K, Mbuf + q, pre, c->guided_iters, c->cfg.ransac_iters,
+                                                   c->cfg.model, c->cfg.thresh_px, c->cfg.seed, pid[q],
+                                                   c->cfg.min_inliers, HM + 9 * (size_t)q, inl, n_in + q, nullptr,
+                                                   nullptr, rws, rws_slot, sr));
+            } else {
+                LP_CUDA(c, lp::launch_ransac(pts, A.K, Mbuf + q, c->cfg.ransac_iters, c->cfg.model, c->cfg.thresh_px,
+                                             c->cfg.seed, pid[q], HM + 9 * (size_t)q, inl, n_in + q, nullptr, rws,
+                                             rws_slot, sr));
+            }
+            LP_CUDA(c, cudaEventRecord(c->pair_ev[1 + slot], sr));
         }
-        if (overlap) {
-            LP_CUDA(c, cudaEventRecord(c->pair_ev[0], sr));
-            LP_CUDA(c, cudaStreamWaitEvent(s, c->pair_ev[0], 0));
-        }
+        for (int k = 0; k < kLanes; ++k) LP_CUDA(c, cudaStreamWaitEvent(s, c->pair_ev[1 + k], 0));
         c->last = s;
         k_pair_valid<<<(P + 127) / 128, 128, 0, s>>>(n_in, P, c->cfg.min_inliers, valid);
         LP_CUDA(c, cudaGetLastError());
@@ -977,6 +1056,14 @@ int lp_mosaic_render(lp_ctx* c, const lp_image* imgs, int N, const double* G, co
     LP_CUDA(c, lp::launch_mosaic_render(imgs, N, G, round_of, canvas, canvas_w, canvas_h, canvas_pitch, cover,
                                         S(stream), &bad));
     if (bad) return fail(c, LP_ERR_ARG, "more than 64 images or a singular placement");
+    return LP_OK;
+}
+
+int lp_diag_set_batch_hold(lp_ctx* c, int32_t hold)
+{
+    if (!c) return LP_ERR_ARG;
+    if (hold < 0) return fail(c, LP_ERR_ARG, "hold must be >= 0");
+    c->batch_hold = hold;
     return LP_OK;
 }
 

@@ -82,6 +82,8 @@ struct MatchArgs {
     const Fork* fork = nullptr;                 // BF16 form: row norms run on the auxiliary streams
     int splits = 0;                             // BF16 form: column splits (0: the built-in choice)
     int pass1_stride = 0;                       // BF16 form: pass-1 tile stride (0: the built-in 3)
+    const float* normA = nullptr;               // batched BF16 form: row norms of A and of B (+inf for
+    const float* normB = nullptr;               //   invalid rows), computed once per image
 };
 size_t match_fp32_workspace(int64_t NA, int64_t NB, int num_sms);
 cudaError_t launch_match_fp32(const MatchArgs& a, void* ws, size_t ws_bytes, int num_sms, cudaStream_t s);
@@ -89,6 +91,16 @@ cudaError_t launch_match_fp32(const MatchArgs& a, void* ws, size_t ws_bytes, int
 size_t match_bf16_workspace(int64_t NA, int64_t NB, int num_sms, int S = 0);
 int match_bf16_default_splits(int64_t NA, int64_t NB, int num_sms);
 cudaError_t launch_match_bf16(const MatchArgs& a, void* ws, size_t ws_bytes, int num_sms, cudaStream_t s);
+// Batched BF16 form: the distance passes of P pairs in persistent launches of
+// up to 64 pairs (k_match_tc_batch, one atomic work queue per launch), then
+// per pair launch_match_bf16_tail.  sync: device int32[match_bf16_batch_sync_words]
+// (zeroed here); hold: extra pass-1 completions every pass-2 unit waits for
+// (diagnostic, 0 normally: a hold makes the waits give up with LP_ERR_TIMEOUT).
+size_t match_bf16_batch_sync_words(const MatchArgs* args, int P);
+cudaError_t launch_match_bf16_batch(const MatchArgs* args, void* const* ws, const size_t* ws_bytes, int P,
+                                    int32_t* sync, int hold, int num_sms, cudaStream_t s);
+cudaError_t launch_match_bf16_tail(const MatchArgs& a, void* ws, size_t ws_bytes, int num_sms, cudaStream_t s);
+cudaError_t launch_row_norms(const float* d, const uint8_t* v, int64_t n, float* out, cudaStream_t s);
 int64_t match_bf16_rescans(const void* ws, int64_t NA, int64_t NB, int num_sms, int S, cudaStream_t s);
 
 // k_ransac.cu

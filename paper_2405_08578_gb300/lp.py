@@ -49,7 +49,7 @@ SYMBOLS = ["lp_config_default", "lp_create", "lp_destroy", "lp_num_keypoints", "
            "lp_mlp_create", "lp_mlp_destroy", "lp_mlp_set_params", "lp_mlp_get_params", "lp_mlp_get_state", "lp_mlp_save",
            "lp_mlp_load", "lp_mlp_features", "lp_mlp_forward", "lp_mlp_train_step", "lp_ransac_prior",
            "lp_diag_last_ransac_counts", "lp_set_proposal", "lp_set_profiling", "lp_diag_last_match_kernel_ms",
-           "lp_set_autotune", "lp_autotune_table",
+           "lp_set_autotune", "lp_autotune_table", "lp_diag_set_batch_hold",
            "lp_mosaic_plan", "lp_mosaic_render"]
 MLP_PARAMS = 4801
 
@@ -110,6 +110,7 @@ def load(build_if_missing: bool = True):
         "lp_mosaic_render": (i32, [P, P, i32, P, P, P, i32, i32, i32, P, P]),
         "lp_diag_last_match_kernel_ms": (i32, [P, C.POINTER(C.c_float)]),
         "lp_set_autotune": (i32, [P, i32]),
+        "lp_diag_set_batch_hold": (i32, [P, i32]),
         "lp_autotune_table": (i32, [P, P, i32, C.POINTER(C.c_int32)]),
     }
     for name, (res, args) in sig.items():
@@ -277,6 +278,9 @@ class Context:
 
     def lp_set_profiling(self, on: bool = True):
         self._chk(self.lib.lp_set_profiling(self.h, int(bool(on))), "lp_set_profiling")
+
+    def lp_diag_set_batch_hold(self, hold: int):
+        self._chk(self.lib.lp_diag_set_batch_hold(self.h, int(hold)), "lp_diag_set_batch_hold")
 
     def lp_set_autotune(self, on: bool = True):
         self._chk(self.lib.lp_set_autotune(self.h, int(bool(on))), "lp_set_autotune")

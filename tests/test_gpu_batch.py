@@ -254,24 +254,34 @@ def test_degenerate_pairs_report_no_model():
     assert not HM[[0, 1, 2, 3, 5]].any()
 
 
-@pytest.mark.parametrize("case", ["gray14", "rgb5", "nonnested", "alpha"])
+@pytest.mark.parametrize("case", ["gray14", "rgb5", "nonnested", "alpha", "tma_rgb_ragged", "tma_gray_ragged",
+                                  "tiles3x3"])
 def test_detect_batch_equals_single_images(case):
     """lp_detect_batch (images sharing launches) gives every image exactly the
     peaks and intensity of lp_detect: more images than one launch takes, mixed
-    sizes, RGB widths that are not multiples of 16, and the configurations that
-    detect image by image."""
+    sizes, RGB widths that are not multiples of 16, the configurations that
+    detect image by image, the tile-streaming path on ragged sizes (partial
+    128-pixel tiles at the right and bottom) and the nine 2688x1600 RGB tiles
+    of the shuffled 3x3 batch."""
     rng = np.random.default_rng(len(case))
     Ls, alpha, ch, n = (16, 32, 64), 0.0, 1, 5
+    lo, hi = (70, 400), (70, 500)
     if case == "gray14":
         n = 14
     elif case == "rgb5":
         ch = 3
     elif case == "nonnested":
         Ls = (12, 20)
-    else:
+    elif case == "alpha":
         alpha = 1e-4
-    shapes = [(int(rng.integers(70, 400)), int(rng.integers(70, 500))) for _ in range(n)]
-    imgs = [rng.integers(0, 256, size=s + ((3,) if ch == 3 else ())).astype(np.uint8) for s in shapes]
+    elif case.startswith("tma"):
+        Ls, ch, n, lo, hi = (16, 32, 64, 128), 3 if "rgb" in case else 1, 13, (128, 700), (130, 900)
+    if case == "tiles3x3":
+        Ls, ch = (16, 32, 64, 128), 3
+        imgs = synth.batch_3x3(seed=1).images
+    else:
+        shapes = [(int(rng.integers(*lo)), int(rng.integers(*hi))) for _ in range(n)]
+        imgs = [rng.integers(0, 256, size=s + ((3,) if ch == 3 else ())).astype(np.uint8) for s in shapes]
     ctx = lp.Context(Ls=Ls, alpha=alpha)
     bufs = [lp.pitched_device(im) for im in imgs]
     images = [(b, im.shape[0], im.shape[1], p, ch) for (b, p), im in zip(bufs, imgs)]
@@ -313,3 +323,32 @@ def test_autotuned_matcher_equals_builtin_and_caches():
         assert 1 <= row["splits"] <= 16 and row["pass1_stride"] in (2, 3, 4)
         assert 0 < row["tuned_us"] <= row["builtin_us"]
     assert tun.lp_sync_status() == 0
+
+
+def test_batch_wait_gives_up_and_context_recovers():
+    """The batched distance passes run in one persistent launch in which a
+    pass-2 unit waits (at most 2 s) for its rows' pass-1 values.  A hold makes
+    every such wait expect a count the launch never reaches: the waits give up,
+    the status word reports LP_ERR_TIMEOUT, the call returns, and once the hold
+    is removed the same context gives the results of a fresh one."""
+    import time
+    Ls = (16, 32, 64, 128)
+    imgs = [synth.small_pair(300, 400, seed=s).A for s in (11, 12, 13)]
+    bufs = [lp.pitched_device(im) for im in imgs]
+    images = [(b, im.shape[0], im.shape[1], p, 1) for (b, p), im in zip(bufs, imgs)]
+    ctx = lp.Context(Ls=Ls, precision=lp.PREC_BF16)
+    HM, n_in, valid, _ = _outputs(3)
+    ctx.lp_diag_set_batch_hold(1)
+    t0 = time.time()
+    ctx.lp_stitch_pairs(images, HM, n_in, valid)
+    st = ctx.lp_sync_status()
+    assert st == 4, lp.ERR_NAMES.get(st, st)          # LP_ERR_TIMEOUT
+    assert time.time() - t0 < 60
+    ctx.lp_diag_set_batch_hold(0)
+    ctx.lp_stitch_pairs(images, HM, n_in, valid)
+    assert ctx.lp_sync_status() == 0
+    fresh = lp.Context(Ls=Ls, precision=lp.PREC_BF16)
+    HM2, n2, v2, _ = _outputs(3)
+    fresh.lp_stitch_pairs(images, HM2, n2, v2)
+    assert fresh.lp_sync_status() == 0
+    assert torch.equal(HM, HM2) and torch.equal(n_in, n2) and torch.equal(valid, v2)
