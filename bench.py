@@ -383,6 +383,7 @@ def fp32_form_and_batch(args, rank):
     out["table2"] = table2(flush)
     out["uneven_64"] = uneven_64(flush, max(3, k // 2))
     out["fp8_census"] = fp8_census()
+    out["describe"] = describe_rate(flush)
     if args.train_pairs > 0:
         out["learned_proposal"] = learned_proposal(args, bt, images, ctx, HM, ni, va, flush, k, ref)
     return out
@@ -540,6 +541,55 @@ def training_pairs(seeds):
     workers = max(1, min(16, (os.cpu_count() or 2) - 1))
     with ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
         yield from ex.map(_training_pair, seeds, chunksize=8)
+
+
+def describe_rate(flush, k=10):
+    """lp_describe on both images of the 2688x1600 pair, L2 flushed before
+    each timed call: ms per image and samples per ns, where a point of region
+    size w_s (Eq. 3-4) takes (4 w_s + 1)^2 orientation samples, (4 w_s + 2)^2
+    turned-grid interpolations and 16 w_s^2 descriptor samples."""
+    import torch
+
+    import oracle
+    from paper_2405_08578_gb300 import lp, synth
+    pair = synth.pair_2688x1600(seed=0)
+    ctx = lp.Context(Ls=LS, precision=lp.PREC_BF16)
+    K = lp.lp_num_keypoints(H_IMG, W_IMG, LS)
+    outs = []
+    for im in (pair.A, pair.B):
+        buf, pitch = lp.pitched_device(im)
+        kp = torch.empty(K, dtype=torch.int32, device="cuda")
+        g = torch.empty(H_IMG * W_IMG + 16, dtype=torch.uint8, device="cuda")
+        ctx.lp_detect(buf, H_IMG, W_IMG, pitch, 3, kp, g)
+        outs.append((g, kp, torch.empty(K, dtype=torch.uint8, device="cuda"),
+                     torch.empty((K, 128), device="cuda"), torch.empty((K, 128), dtype=torch.bfloat16, device="cuda"),
+                     torch.empty(K, dtype=torch.uint8, device="cuda")))
+    s = torch.cuda.current_stream()
+
+    def run():
+        for (g, kp, o, d, d16, v) in outs:
+            ctx.lp_describe(g, H_IMG, W_IMG, W_IMG, kp, K, o, d, d16, v)
+
+    for _ in range(3):
+        run()
+    torch.cuda.synchronize()
+    t = []
+    for _ in range(k):
+        flush()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        run()
+        e1.record(s)
+        torch.cuda.synchronize()
+        t.append(e0.elapsed_time(e1) / 2)
+    t.sort()
+    ms = t[len(t) // 2]
+    _, ws = oracle.keypoint_scales(H_IMG, W_IMG, LS)
+    ws = ws.astype(np.int64)
+    samples = int(((4 * ws + 1) ** 2 + (4 * ws + 2) ** 2 + 16 * ws ** 2).sum())
+    return {"ms_per_image": ms, "points_per_image": int(K), "samples_per_image": samples,
+            "samples_per_ns": samples / (ms * 1e6),
+            "bound": "SM issue (77% of cycles issuing, no pipe saturated; profiles/k_describe_pair_2688x1600.md)"}
 
 
 def fp8_census(chunk=4096, margin=5e-3, capacity=192):
@@ -908,6 +958,7 @@ def main():
         line["config"]["batch_3x3_fp32"] = extra["batch_3x3_fp32"]
         line["config"]["uneven_64"] = extra["uneven_64"]
         line["config"]["fp8_census"] = extra["fp8_census"]
+        line["config"]["describe"] = extra["describe"]
         line["config"]["mosaic_3x3"] = extra["mosaic_3x3"]
         line["config"]["table2"] = extra["table2"]
         line["config"]["detect_3x3"] = extra["detect_3x3"]
