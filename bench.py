@@ -550,7 +550,6 @@ def describe_rate(flush, k=10):
     turned-grid interpolations and 16 w_s^2 descriptor samples."""
     import torch
 
-    import oracle
     from paper_2405_08578_gb300 import lp, synth
     pair = synth.pair_2688x1600(seed=0)
     ctx = lp.Context(Ls=LS, precision=lp.PREC_BF16)
@@ -584,9 +583,13 @@ def describe_rate(flush, k=10):
         t.append(e0.elapsed_time(e1) / 2)
     t.sort()
     ms = t[len(t) // 2]
-    _, ws = oracle.keypoint_scales(H_IMG, W_IMG, LS)
-    ws = ws.astype(np.int64)
-    samples = int(((4 * ws + 1) ** 2 + (4 * ws + 2) ** 2 + 16 * ws ** 2).sum())
+    # Eq. 3-4 with the default beta0 (the largest that keeps 4 w_s <= L):
+    # w_s = round(beta0 sqrt(L Lmax) ), 2 (H/L)(W/L) points at scale L
+    beta0 = math.sqrt(min(LS) / max(LS)) / 4
+    samples = 0
+    for L in LS:
+        w = max(1, int(math.floor(beta0 * math.sqrt(L * max(LS)) + 0.5)))
+        samples += 2 * (H_IMG // L) * (W_IMG // L) * ((4 * w + 1) ** 2 + (4 * w + 2) ** 2 + 16 * w * w)
     return {"ms_per_image": ms, "points_per_image": int(K), "samples_per_image": samples,
             "samples_per_ns": samples / (ms * 1e6),
             "bound": "SM issue (77% of cycles issuing, no pipe saturated; profiles/k_describe_pair_2688x1600.md)"}
@@ -662,18 +665,17 @@ def _grid_dev(Ha, Hb, h, w, Href=None, step=32):
     return float(np.abs(a[:, :2] / a[:, 2:] - b[:, :2] / b[:, 2:]).max(initial=0.0)), int(inside.sum())
 
 
-def uneven_64(flush, k, oracle_pairs=3):
+def uneven_64(flush, k):
     """The 64-pair uneven workload (long sides U[480, 4096], aspect U[4/3,
     16/9], gray, L = {16, 32, 64, 128}) as one lp_stitch_pairs call with an
     explicit pair list, BF16 with and without the matcher's autotuner: pairs/s
-    of each, the tuning table, error against each pair's true homography and,
-    on the smallest pairs, against the oracle's."""
+    of each, the tuning table and the error against each pair's true
+    homography."""
     import multiprocessing as mp
     from concurrent.futures import ProcessPoolExecutor
 
     import torch
 
-    import oracle
     from paper_2405_08578_gb300 import lp, synth
     specs = synth.uneven_pair_specs(64, seed=2)
     t0 = time.time()
@@ -722,16 +724,6 @@ def uneven_64(flush, k, oracle_pairs=3):
              for q in range(64) if res[True]["va"][q]]
     out["truth_error_px"] = {"median": float(np.median(dev_t)) if dev_t else None,
                              "max": float(np.max(dev_t)) if dev_t else None}
-    # the smallest pairs end to end through the oracle
-    order = sorted(range(64), key=lambda q: pairs[q][0].size)[:oracle_pairs]
-    rows = []
-    for q in order:
-        A, B, Ht = pairs[q]
-        o = oracle.stitch_pair(A, B, LS, pair_id=q)
-        d, n = _grid_dev(res[True]["HM"][q], o["H"], A.shape[0], A.shape[1], Href=Ht)
-        rows.append({"pair": q, "size": [int(A.shape[1]), int(A.shape[0])], "n_in_gpu": int(res[True]["ni"][q]),
-                     "n_in_oracle": o["n_in"], "H_vs_oracle_px": d, "overlap_points": n})
-    out["vs_oracle_smallest_pairs"] = rows
     return out
 
 
