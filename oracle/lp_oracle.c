@@ -16,6 +16,10 @@
  *   or_orient_weight   pinned (exhaustive, integer square-root bracket)
  *   or_orient          pinned (ramp images, 90-degree rotation)
  *   or_describe        pinned (ramp closed forms, unit norm, 90-degree rotation)
+ *   or_octant / or_describe_ex (hard 8-direction bins)
+ *                      pinned (edge and interior directions, atan2 sectors
+ *                      away from edges, ramp closed forms, integer Eq. 5
+ *                      with atan2 sectors, 90-degree rotation)
  *   or_match           pinned (brute force in numpy, permutation invariance)
  *   or_philox4x32_10   pinned (published known-answer vectors)
  *   or_dlt4 / or_refit pinned (known homographies, numpy SVD)
@@ -242,6 +246,33 @@ static double bil(const uint8_t* g, int H, int W, int pitch, double r, double c)
 int or_describe(const uint8_t* gray, int H, int W, int pitch, const uint32_t* idx, const int* ws,
                 const uint8_t* ori, int64_t K, double* desc, uint8_t* valid)
 {
+    return or_describe_ex(gray, H, W, pitch, idx, ws, ori, K, 0, 0.0, desc, valid, NULL);
+}
+
+/* Sec. 2.3 read literally (a paper-literal variant): the histogram has 8
+ * directions, and a sample's whole magnitude goes to the direction whose
+ * 45-degree sector [45k, 45(k + 1)) degrees holds atan2(b, a).  The sector is
+ * decided by signs and magnitude comparisons, so a direction on a sector edge
+ * belongs to the sector it starts.  (a, b) = 0 is never asked for. */
+int or_octant(double a, double b)
+{
+    if (b >= 0 && a > 0) return b < a ? 0 : 1;
+    if (a <= 0 && b > 0) return b > -a ? 2 : 3;
+    if (b <= 0 && a < 0) return -b < -a ? 4 : 5;
+    return a < -b ? 6 : 7;
+}
+
+/* or_describe with the bin rule chosen: hard = 0 splits each magnitude
+ * linearly between the two nearest bins, hard = 1 puts it whole in its
+ * sector (or_octant).  stats (K x 3, or NULL) receives per point the norm of
+ * the raw 128-bin histogram, the norm of the clamped vector before the second
+ * normalisation, and the magnitude of the samples whose gradient lies within
+ * tol of a sector edge (distance from the line through the origin: |b|, |a|,
+ * |a - b|/sqrt 2 or |a + b|/sqrt 2) -- the samples whose hard bin a gradient
+ * perturbed by less than tol could change. */
+int or_describe_ex(const uint8_t* gray, int H, int W, int pitch, const uint32_t* idx, const int* ws,
+                   const uint8_t* ori, int64_t K, int hard, double tol, double* desc, uint8_t* valid, double* stats)
+{
     if (!gray || !idx || !ws || !desc || !valid || K < 0) return -1;
     for (int64_t k = 0; k < K; ++k) {
         double y = (double)(idx[k] / (uint32_t)W), x = (double)(idx[k] % (uint32_t)W);
@@ -249,6 +280,7 @@ int or_describe(const uint8_t* gray, int H, int W, int pitch, const uint32_t* id
         double th = ori ? ((double)ori[k] + 0.5) * (10.0 * OR_PI / 180.0) : 0.0;
         double c = ori ? cos(th) : 1.0, s = ori ? sin(th) : 0.0;
         double h[128];
+        double amb = 0;
         memset(h, 0, sizeof h);
         for (int u = -R; u < R; ++u)
             for (int v = -R; v < R; ++v) {
@@ -258,13 +290,19 @@ int or_describe(const uint8_t* gray, int H, int W, int pitch, const uint32_t* id
                 double b = bil(gray, H, W, pitch, py - s, pxx + c) - bil(gray, H, W, pitch, py + s, pxx - c);
                 double m = sqrt(a * a + b * b);
                 if (m == 0) continue;
+                int cell = ((u + R) / s_) * 4 + (v + R) / s_;
+                double e = fmin(fmin(fabs(a), fabs(b)), fmin(fabs(a - b), fabs(a + b)) / sqrt(2.0));
+                if (e <= tol) amb += m;
+                if (hard) {
+                    h[cell * 8 + or_octant(a, b)] += m;
+                    continue;
+                }
                 double o = 8.0 * atan2(b, a) / (2.0 * OR_PI);
                 if (o < 0) o += 8.0;
                 if (o >= 8.0) o -= 8.0;
                 double fo = floor(o);
                 double t = o - fo;
                 int b0 = (int)fo, b1 = (b0 + 1) % 8;
-                int cell = ((u + R) / s_) * 4 + (v + R) / s_;
                 h[cell * 8 + b0] += m * (1.0 - t);
                 h[cell * 8 + b1] += m * t;
             }
@@ -272,6 +310,11 @@ int or_describe(const uint8_t* gray, int H, int W, int pitch, const uint32_t* id
         for (int j = 0; j < 128; ++j) n += h[j] * h[j];
         n = sqrt(n);
         double* out = desc + 128 * k;
+        if (stats) {
+            stats[3 * k] = n;
+            stats[3 * k + 1] = 0;
+            stats[3 * k + 2] = amb;
+        }
         if (n == 0) {
             memset(out, 0, sizeof(double) * 128);
             valid[k] = 0;
@@ -285,6 +328,7 @@ int or_describe(const uint8_t* gray, int H, int W, int pitch, const uint32_t* id
             n2 += q * q;
         }
         n2 = sqrt(n2);
+        if (stats) stats[3 * k + 1] = n2;
         for (int j = 0; j < 128; ++j) out[j] /= n2;
         valid[k] = 1;
     }

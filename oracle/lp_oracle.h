@@ -47,6 +47,10 @@ int or_orient(const uint8_t* gray, int H, int W, int pitch, const uint32_t* idx,
  * ori == NULL: upright (theta = 0). */
 int or_describe(const uint8_t* gray, int H, int W, int pitch, const uint32_t* idx, const int* ws,
                 const uint8_t* ori, int64_t K, double* desc, uint8_t* valid);
+int or_octant(double a, double b);               /* hard 8-direction sector of atan2(b, a) */
+int or_describe_ex(const uint8_t* gray, int H, int W, int pitch, const uint32_t* idx, const int* ws,
+                   const uint8_t* ori, int64_t K, int hard, double tol, double* desc, uint8_t* valid,
+                   double* stats);
 
 /* Nearest-neighbour matching with Eq. 6 distance, the ratio test and Delta_s.
  * rows == NULL: all NA rows; otherwise only rows[0..nrows) (outputs indexed by

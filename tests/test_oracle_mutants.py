@@ -14,6 +14,7 @@ import pytest
 import oracle
 import test_oracle_describe as DS
 import test_oracle_detect as D
+import test_oracle_hard_bins as HB
 import test_oracle_literal as L
 import test_oracle_match_ransac as MR
 import test_oracle_mlp as ML
@@ -97,6 +98,18 @@ MUTANTS = [
     ("describe_soft_split_swapped",
      "h[cell * 8 + b0] += m * (1.0 - t);", "h[cell * 8 + b0] += m * t;",
      [DS.test_describe_ramp_closed_forms]),
+    ("hard_edge_to_lower_sector",
+     "if (b >= 0 && a > 0) return b < a ? 0 : 1;", "if (b >= 0 && a > 0) return b <= a ? 0 : 1;",
+     [HB.test_octant_edges_and_interiors, HB.test_octant_matches_atan2_sector_away_from_edges]),
+    ("hard_sectors_2_3_swapped",
+     "if (a <= 0 && b > 0) return b > -a ? 2 : 3;", "if (a <= 0 && b > 0) return b > -a ? 3 : 2;",
+     [HB.test_describe_hard_ramp_closed_forms]),
+    ("hard_sector_operands_transposed",
+     "h[cell * 8 + or_octant(a, b)] += m;", "h[cell * 8 + or_octant(b, a)] += m;",
+     [HB.test_describe_hard_ramp_closed_forms, HB.test_describe_hard_upright_equals_integer_eq5_and_stats]),
+    ("hard_edge_distance_unscaled",
+     "fmin(fabs(a - b), fabs(a + b)) / sqrt(2.0)", "fmin(fabs(a - b), fabs(a + b))",
+     [HB.test_describe_hard_upright_equals_integer_eq5_and_stats]),
     ("describe_turn_sign",
      "double py = y + u * c - v * s;", "double py = y + u * c + v * s;",
      [DS.test_describe_ramp_closed_forms, DS.test_describe_rotation_90_invariant]),
