@@ -80,7 +80,8 @@ def _load(path: str):
         "or_orient": (i32, [P, i32, i32, i32, P, P, i64, P, P]),
         "or_describe": (i32, [P, i32, i32, i32, P, P, P, i64, P, P]),
         "or_octant": (i32, [f64, f64]),
-        "or_describe_ex": (i32, [P, i32, i32, i32, P, P, P, i64, i32, f64, P, P, P]),
+        "or_describe_ex": (i32, [P, i32, i32, i32, P, P, P, i64, i32, P, P]),
+        "or_turn_fx": (i32, [i32, P, P]),
         "or_match": (i32, [P, P, i64, P, P, i64, f64, f64, P, i64, P, P, P, P, P]),
         "or_philox4x32_10": (None, [P, P, P]),
         "or_ransac_sample": (i32, [i64, C.c_uint64, u32, i32, P]),
@@ -179,6 +180,13 @@ def octant(a: float, b: float) -> int:
     return int(lib().or_octant(float(a), float(b)))
 
 
+def turn_fx(k: int) -> tuple[int, int]:
+    """(round(2^11 cos th), round(2^11 sin th)), th = (k + 0.5) * 10 degrees."""
+    cq, sq = C.c_int(), C.c_int()
+    assert lib().or_turn_fx(int(k), C.byref(cq), C.byref(sq)) == 0
+    return cq.value, sq.value
+
+
 def orient_weight(s: int) -> int:
     return int(lib().or_orient_weight(int(s)))
 
@@ -196,10 +204,9 @@ def orient(g: np.ndarray, idx: np.ndarray, ws: np.ndarray, want_hist: bool = Fal
 
 
 def describe(g: np.ndarray, idx: np.ndarray, ws: np.ndarray, ori: np.ndarray | None, border: bool = False,
-             hard: bool = False, tol: float | None = None):
-    """Sec. 2.3 descriptors (soft bins, or hard 8-direction sectors with
-    hard=True).  With tol given, also returns per point (histogram norm,
-    clamped-vector norm, magnitude of the samples within tol of a sector edge)."""
+             hard: bool = False):
+    """Sec. 2.3 descriptors: soft bins, or (hard=True) whole magnitudes in
+    45-degree sectors on the exact fixed-point turned grid."""
     g = _c(g, np.uint8)
     H, W = g.shape
     idx = _c(idx, np.uint32)
@@ -208,12 +215,11 @@ def describe(g: np.ndarray, idx: np.ndarray, ws: np.ndarray, ori: np.ndarray | N
     o = None if ori is None else _c(ori, np.uint8)
     desc = np.empty((K, 128), np.float64)
     valid = np.empty(K, np.uint8)
-    stats = np.empty((K, 3), np.float64) if tol is not None else None
-    assert lib().or_describe_ex(_p(g), H, W, W, _p(idx), _p(ws), _p(o), K, int(bool(hard)),
-                                float(tol or 0.0), _p(desc), _p(valid), _p(stats)) == 0
+    assert lib().or_describe_ex(_p(g), H, W, W, _p(idx), _p(ws), _p(o), K, int(bool(hard)), _p(desc),
+                                _p(valid)) == 0
     if border:
         assert lib().or_border_valid(_p(idx), _p(ws), K, H, W, _p(valid)) == 0
-    return (desc, valid, stats) if tol is not None else (desc, valid)
+    return desc, valid
 
 
 def match(dA, vA, dB, vB, ratio: float = 0.8, delta_s: float = float("inf"), rows=None):

@@ -16,10 +16,11 @@
  *   or_orient_weight   pinned (exhaustive, integer square-root bracket)
  *   or_orient          pinned (ramp images, 90-degree rotation)
  *   or_describe        pinned (ramp closed forms, unit norm, 90-degree rotation)
- *   or_octant / or_describe_ex (hard 8-direction bins)
+ *   or_octant / or_turn_fx / or_describe_ex (hard 8-direction bins)
  *                      pinned (edge and interior directions, atan2 sectors
- *                      away from edges, ramp closed forms, integer Eq. 5
- *                      with atan2 sectors, 90-degree rotation)
+ *                      away from edges, 40-digit turn table, ramp closed
+ *                      forms, integer Eq. 5 with atan2 sectors, exact
+ *                      90-degree rotation)
  *   or_match           pinned (brute force in numpy, permutation invariance)
  *   or_philox4x32_10   pinned (published known-answer vectors)
  *   or_dlt4 / or_refit pinned (known homographies, numpy SVD)
@@ -246,7 +247,7 @@ static double bil(const uint8_t* g, int H, int W, int pitch, double r, double c)
 int or_describe(const uint8_t* gray, int H, int W, int pitch, const uint32_t* idx, const int* ws,
                 const uint8_t* ori, int64_t K, double* desc, uint8_t* valid)
 {
-    return or_describe_ex(gray, H, W, pitch, idx, ws, ori, K, 0, 0.0, desc, valid, NULL);
+    return or_describe_ex(gray, H, W, pitch, idx, ws, ori, K, 0, desc, valid);
 }
 
 /* Sec. 2.3 read literally (a paper-literal variant): the histogram has 8
@@ -262,16 +263,47 @@ int or_octant(double a, double b)
     return a < -b ? 6 : 7;
 }
 
-/* or_describe with the bin rule chosen: hard = 0 splits each magnitude
- * linearly between the two nearest bins, hard = 1 puts it whole in its
- * sector (or_octant).  stats (K x 3, or NULL) receives per point the norm of
- * the raw 128-bin histogram, the norm of the clamped vector before the second
- * normalisation, and the magnitude of the samples whose gradient lies within
- * tol of a sector edge (distance from the line through the origin: |b|, |a|,
- * |a - b|/sqrt 2 or |a + b|/sqrt 2) -- the samples whose hard bin a gradient
- * perturbed by less than tol could change. */
+/* The turned grid of the hard-bin variant in fixed point: cos and sin of
+ * orientation bin k ((k + 0.5) * 10 degrees) rounded to multiples of 2^-11.
+ * A hard bin is a discontinuous function of the gradient direction, so the
+ * variant makes every sample position, intensity and gradient an exact
+ * number: offsets (u cq - v sq, u sq + v cq) are multiples of 2^-11 px and
+ * bilinear intensities multiples of 2^-22.  (The turn differs from the exact
+ * angle by less than 2.5e-4 rad.) */
+int or_turn_fx(int k, int* cq, int* sq)
+{
+    if (k < 0 || k > 35 || !cq || !sq) return -1;
+    double th = ((double)k + 0.5) * (10.0 * OR_PI / 180.0);
+    *cq = (int)floor(2048.0 * cos(th) + 0.5);
+    *sq = (int)floor(2048.0 * sin(th) + 0.5);
+    return 0;
+}
+
+static int64_t floor_div_2048(int64_t v)
+{
+    return v >= 0 ? v / 2048 : -((-v + 2047) / 2048);
+}
+
+/* 2^22 * bilinear intensity at (y + r / 2048, x + c / 2048), clamp-to-edge
+ * taps, in exact integer arithmetic. */
+static int64_t bil_fx(const uint8_t* g, int H, int W, int pitch, int y, int x, int64_t r, int64_t c)
+{
+    int64_t r0 = floor_div_2048(r), c0 = floor_div_2048(c);
+    int64_t fr = r - 2048 * r0, fc = c - 2048 * c0;
+    int yy = y + (int)r0, xx = x + (int)c0;
+    int64_t v00 = px(g, H, W, pitch, yy, xx), v01 = px(g, H, W, pitch, yy, xx + 1);
+    int64_t v10 = px(g, H, W, pitch, yy + 1, xx), v11 = px(g, H, W, pitch, yy + 1, xx + 1);
+    int64_t top = v00 * (2048 - fc) + v01 * fc;
+    int64_t bot = v10 * (2048 - fc) + v11 * fc;
+    return top * (2048 - fr) + bot * fr;
+}
+
+/* or_describe with the bin rule chosen.  hard = 0: each magnitude is split
+ * linearly between the two nearest bins (the default reading).  hard = 1: the
+ * grid is the fixed-point one of or_turn_fx, each gradient an exact integer
+ * (2^22 * Eq. 5), and its whole magnitude goes to its sector (or_octant). */
 int or_describe_ex(const uint8_t* gray, int H, int W, int pitch, const uint32_t* idx, const int* ws,
-                   const uint8_t* ori, int64_t K, int hard, double tol, double* desc, uint8_t* valid, double* stats)
+                   const uint8_t* ori, int64_t K, int hard, double* desc, uint8_t* valid)
 {
     if (!gray || !idx || !ws || !desc || !valid || K < 0) return -1;
     for (int64_t k = 0; k < K; ++k) {
@@ -280,23 +312,30 @@ int or_describe_ex(const uint8_t* gray, int H, int W, int pitch, const uint32_t*
         double th = ori ? ((double)ori[k] + 0.5) * (10.0 * OR_PI / 180.0) : 0.0;
         double c = ori ? cos(th) : 1.0, s = ori ? sin(th) : 0.0;
         double h[128];
-        double amb = 0;
         memset(h, 0, sizeof h);
+        int cq = 2048, sq = 0;
+        if (hard && ori) or_turn_fx(ori[k], &cq, &sq);
         for (int u = -R; u < R; ++u)
             for (int v = -R; v < R; ++v) {
+                int cell = ((u + R) / s_) * 4 + (v + R) / s_;
+                if (hard) {
+                    int yi = (int)y, xi = (int)x;
+                    int64_t pr = (int64_t)u * cq - (int64_t)v * sq, pc = (int64_t)u * sq + (int64_t)v * cq;
+                    int64_t ai = bil_fx(gray, H, W, pitch, yi, xi, pr + cq, pc + sq) -
+                                 bil_fx(gray, H, W, pitch, yi, xi, pr - cq, pc - sq);
+                    int64_t bi = bil_fx(gray, H, W, pitch, yi, xi, pr - sq, pc + cq) -
+                                 bil_fx(gray, H, W, pitch, yi, xi, pr + sq, pc - cq);
+                    if (ai == 0 && bi == 0) continue;
+                    double a = (double)ai, b = (double)bi;
+                    h[cell * 8 + or_octant(a, b)] += sqrt(a * a + b * b) / 4194304.0;
+                    continue;
+                }
                 double py = y + u * c - v * s;
                 double pxx = x + u * s + v * c;
                 double a = bil(gray, H, W, pitch, py + c, pxx + s) - bil(gray, H, W, pitch, py - c, pxx - s);
                 double b = bil(gray, H, W, pitch, py - s, pxx + c) - bil(gray, H, W, pitch, py + s, pxx - c);
                 double m = sqrt(a * a + b * b);
                 if (m == 0) continue;
-                int cell = ((u + R) / s_) * 4 + (v + R) / s_;
-                double e = fmin(fmin(fabs(a), fabs(b)), fmin(fabs(a - b), fabs(a + b)) / sqrt(2.0));
-                if (e <= tol) amb += m;
-                if (hard) {
-                    h[cell * 8 + or_octant(a, b)] += m;
-                    continue;
-                }
                 double o = 8.0 * atan2(b, a) / (2.0 * OR_PI);
                 if (o < 0) o += 8.0;
                 if (o >= 8.0) o -= 8.0;
@@ -310,11 +349,6 @@ int or_describe_ex(const uint8_t* gray, int H, int W, int pitch, const uint32_t*
         for (int j = 0; j < 128; ++j) n += h[j] * h[j];
         n = sqrt(n);
         double* out = desc + 128 * k;
-        if (stats) {
-            stats[3 * k] = n;
-            stats[3 * k + 1] = 0;
-            stats[3 * k + 2] = amb;
-        }
         if (n == 0) {
             memset(out, 0, sizeof(double) * 128);
             valid[k] = 0;
@@ -328,7 +362,6 @@ int or_describe_ex(const uint8_t* gray, int H, int W, int pitch, const uint32_t*
             n2 += q * q;
         }
         n2 = sqrt(n2);
-        if (stats) stats[3 * k + 1] = n2;
         for (int j = 0; j < 128; ++j) out[j] /= n2;
         valid[k] = 1;
     }

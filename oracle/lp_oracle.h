@@ -48,9 +48,9 @@ int or_orient(const uint8_t* gray, int H, int W, int pitch, const uint32_t* idx,
 int or_describe(const uint8_t* gray, int H, int W, int pitch, const uint32_t* idx, const int* ws,
                 const uint8_t* ori, int64_t K, double* desc, uint8_t* valid);
 int or_octant(double a, double b);               /* hard 8-direction sector of atan2(b, a) */
+int or_turn_fx(int k, int* cq, int* sq);         /* round(2^11 cos), round(2^11 sin) of bin k's angle */
 int or_describe_ex(const uint8_t* gray, int H, int W, int pitch, const uint32_t* idx, const int* ws,
-                   const uint8_t* ori, int64_t K, int hard, double tol, double* desc, uint8_t* valid,
-                   double* stats);
+                   const uint8_t* ori, int64_t K, int hard, double* desc, uint8_t* valid);
 
 /* Nearest-neighbour matching with Eq. 6 distance, the ratio test and Delta_s.
  * rows == NULL: all NA rows; otherwise only rows[0..nrows) (outputs indexed by

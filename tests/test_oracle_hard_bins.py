@@ -1,7 +1,6 @@
 """Pins for the paper-literal hard 8-direction histogram of Sec. 2.3 in the
-oracle: the sector rule (or_octant) and the descriptor built with it
-(or_describe_ex, hard = 1), with the per-point edge statistics that the GPU
-parity test uses to bound where an FP32 gradient may fall in the next sector."""
+oracle: the sector rule (or_octant), the fixed-point turn table (or_turn_fx)
+and the descriptor built with them (or_describe_ex, hard = 1)."""
 import math
 
 import numpy as np
@@ -77,13 +76,18 @@ def test_describe_hard_ramp_closed_forms():
     # the soft split differs on a direction inside a sector (63.4 deg)
     ds, _ = oracle.describe((yy + 2 * xx).astype(np.uint8), kp, ws, None)
     assert np.abs(ds[0] - _single_bin(1)).max() > 0.05
-    # turned grid on I = r: frame gradient (2 cos th, -2 sin th), never on an edge here
+    # turned fixed-point grid (e_u = (cq, sq) / 2048, e_v = (-sq, cq) / 2048 in
+    # (row, col)) on I = r and on I = r + 2c: bilinear sampling of a linear
+    # image is exact, so every sample has the frame gradient
+    # 2 (grad I . e_u, grad I . e_v)
     for k in (0, 7, 11, 20, 35):
         th = math.radians((k + 0.5) * 10)
-        sec, gap = _atan2_sector(2 * math.cos(th), -2 * math.sin(th))
-        assert gap > 0.05
-        d, _ = oracle.describe(yy.astype(np.uint8), kp, ws, np.array([k], np.uint8), hard=True)
-        assert np.abs(d[0] - _single_bin(sec)).max() < 1e-12, k
+        cq, sq = round(2048 * math.cos(th)), round(2048 * math.sin(th))
+        for img, gr, gc in ((yy, 1, 0), (yy + 2 * xx, 1, 2)):
+            sec, gap = _atan2_sector(gr * cq + gc * sq, -gr * sq + gc * cq)
+            assert gap > 0.05
+            d, _ = oracle.describe(img.astype(np.uint8), kp, ws, np.array([k], np.uint8), hard=True)
+            assert np.abs(d[0] - _single_bin(sec)).max() < 1e-12, (k, gc)
 
 
 def _hard_eq5(g, y, x, s):
@@ -92,83 +96,74 @@ def _hard_eq5(g, y, x, s):
     G = g.astype(np.int64)
     h = np.zeros(128)
     R = 2 * s
-    mass = {0: 0.0, 1.5: 0.0}
     for u in range(-R, R):
         for v in range(-R, R):
             a = G[y + u + 1, x + v] - G[y + u - 1, x + v]
             b = G[y + u, x + v + 1] - G[y + u, x + v - 1]
             if a == 0 and b == 0:
                 continue
-            m = math.hypot(a, b)
             if b == 0 or a == 0 or a == b or a == -b:
                 k = {(1, 0): 0, (1, 1): 1, (0, 1): 2, (-1, 1): 3, (-1, 0): 4, (-1, -1): 5, (0, -1): 6,
                      (1, -1): 7}[(int(np.sign(a)), int(np.sign(b)))]
             else:
                 k, _ = _atan2_sector(a, b)
-            h[(((u + R) // s) * 4 + (v + R) // s) * 8 + k] += m
-            e = min(abs(a), abs(b), abs(a - b) / math.sqrt(2), abs(a + b) / math.sqrt(2))
-            for t in mass:
-                if e <= t:
-                    mass[t] += m
-    n = np.linalg.norm(h)
-    c = np.minimum(h / n, 0.2)
-    nc = np.linalg.norm(c)
-    return c / nc, n, nc, mass
+            h[(((u + R) // s) * 4 + (v + R) // s) * 8 + k] += math.hypot(a, b)
+    c = np.minimum(h / np.linalg.norm(h), 0.2)
+    return c / np.linalg.norm(c)
 
 
-def test_describe_hard_upright_equals_integer_eq5_and_stats():
+def test_describe_hard_upright_equals_integer_eq5():
     rng = np.random.default_rng(19)
     H, W = 44, 48
     for levels, (y, x, s) in ((256, (21, 22, 3)), (9, (22, 23, 4)), (256, (20, 25, 2))):
         g = rng.integers(0, levels, size=(H, W)).astype(np.uint8)
-        want, n, nc, mass = _hard_eq5(g, y, x, s)
-        for tol in (0, 1.5):
-            d, v, st = oracle.describe(g, DS._kp(H, W, y, x), np.array([s], np.int32), None, hard=True, tol=tol)
-            assert v[0] == 1 and np.abs(d[0] - want).max() < 1e-12
-            assert abs(st[0, 0] - n) < 1e-9 * n and abs(st[0, 1] - nc) < 1e-12
-            assert abs(st[0, 2] - mass[tol]) < 1e-9 * max(1.0, mass[tol]), (levels, tol)
-        assert mass[1.5] > mass[0]
-        if levels == 9:
-            assert mass[0] > 0          # few levels: gradients on edges do occur
+        d, v = oracle.describe(g, DS._kp(H, W, y, x), np.array([s], np.int32), None, hard=True)
+        assert v[0] == 1 and np.abs(d[0] - _hard_eq5(g, y, x, s)).max() < 1e-12, levels
+
+
+def test_turn_table_is_rounded_2048_cos_sin():
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 40
+    for k in range(36):
+        th = (k + mpmath.mpf(1) / 2) * 10 * mpmath.pi / 180
+        cq, sq = oracle.turn_fx(k)
+        for got, exact in ((cq, 2048 * mpmath.cos(th)), (sq, 2048 * mpmath.sin(th))):
+            assert got == int(mpmath.nint(exact))
+            assert abs(abs(exact - int(mpmath.floor(exact))) - 0.5) > 1e-6    # no rounding tie
+        assert abs(math.hypot(cq, sq) / 2048 - 1) < 5e-4
+    # bin k + 9 is bin k turned by 90 degrees, exactly
+    for k in range(27):
+        cq, sq = oracle.turn_fx(k)
+        assert oracle.turn_fx(k + 9) == (-sq, cq)
 
 
 def test_describe_hard_rotation_90_invariant():
-    # The turned grids of A and of A rotated by 90 degrees read the same
-    # intensities up to FP64 rounding of the sample positions, so the hard
-    # descriptors agree wherever no sample lies within 1e-9 of a sector edge
-    # (clamped borders make exact-edge gradients common, and there the rounding
-    # decides the sector).
+    # Bin k + 9's fixed-point turn is bin k's turned by 90 degrees exactly, so
+    # A and A rotated by 90 degrees read the same intensities at every sample
+    # (clamped borders included) and give identical integer gradients.
     g, B, ia, ib, ws = DS._rot_setup(seed=8)
-    oa = np.random.default_rng(3).integers(0, 36, len(ia)).astype(np.uint8)
-    ob = ((oa.astype(int) + 9) % 36).astype(np.uint8)
-    da, va, st = oracle.describe(g, ia, ws, oa, hard=True, tol=1e-9)
+    oa = np.random.default_rng(3).integers(0, 27, len(ia)).astype(np.uint8)
+    ob = (oa.astype(int) + 9).astype(np.uint8)
+    da, va = oracle.describe(g, ia, ws, oa, hard=True)
     db, vb = oracle.describe(B, ib, ws, ob, hard=True)
     assert np.array_equal(va, vb)
-    clear = st[:, 2] == 0
-    assert clear.sum() >= 25
-    assert np.abs(da[clear] - db[clear]).max() < 1e-9
+    assert np.abs(da - db).max() < 1e-12
     # the hard rule is not the soft one on these points
     ds, _ = oracle.describe(g, ia, ws, oa)
     assert np.abs(ds - da).max() > 0.05
 
 
-def test_describe_hard_edge_mass_is_monotone_and_complete():
+def test_soft_path_unchanged_through_describe_ex():
     rng = np.random.default_rng(23)
     g = rng.integers(0, 256, size=(70, 80)).astype(np.uint8)
     idx = (rng.integers(15, 55, 30) * 80 + rng.integers(15, 65, 30)).astype(np.uint32)
     ws = rng.integers(1, 4, 30).astype(np.int32)
     ori = oracle.orient(g, idx, ws)
-    prev = None
-    for tol in (0.0, 0.05, 1.0, 10.0, 1e9):
-        d, v, st = oracle.describe(g, idx, ws, ori, hard=True, tol=tol)
-        if prev is not None:
-            assert np.all(st[:, 2] >= prev)
-        prev = st[:, 2]
-    # at an unbounded tolerance every sample counts: the edge mass is the total
-    # gradient magnitude, which bounds the histogram's norm from above and its
-    # norm times sqrt(128) from below
-    assert np.all(prev >= st[:, 0] - 1e-9) and np.all(prev <= math.sqrt(128) * st[:, 0] + 1e-9)
-    # the same soft descriptors come back through or_describe_ex
     d0, v0 = oracle.describe(g, idx, ws, ori)
-    d1, v1, _ = oracle.describe(g, idx, ws, ori, tol=0.0)
-    assert np.array_equal(d0, d1) and np.array_equal(v0, v1)
+    d1, v1 = oracle.describe(g, idx, ws, ori, hard=False)
+    dh, vh = oracle.describe(g, idx, ws, ori, hard=True)
+    assert np.array_equal(d0, d1) and np.array_equal(v0, v1) and np.array_equal(v0, vh)
+    assert np.allclose(np.linalg.norm(dh, axis=1), 1.0, atol=1e-12)
+    # the two readings give different, but related, descriptors
+    cos = (d0 * dh).sum(axis=1)
+    assert cos.max() < 0.999 and cos.mean() > 0.7

@@ -105,11 +105,18 @@ MUTANTS = [
      "if (a <= 0 && b > 0) return b > -a ? 2 : 3;", "if (a <= 0 && b > 0) return b > -a ? 3 : 2;",
      [HB.test_describe_hard_ramp_closed_forms]),
     ("hard_sector_operands_transposed",
-     "h[cell * 8 + or_octant(a, b)] += m;", "h[cell * 8 + or_octant(b, a)] += m;",
-     [HB.test_describe_hard_ramp_closed_forms, HB.test_describe_hard_upright_equals_integer_eq5_and_stats]),
-    ("hard_edge_distance_unscaled",
-     "fmin(fabs(a - b), fabs(a + b)) / sqrt(2.0)", "fmin(fabs(a - b), fabs(a + b))",
-     [HB.test_describe_hard_upright_equals_integer_eq5_and_stats]),
+     "h[cell * 8 + or_octant(a, b)] +=", "h[cell * 8 + or_octant(b, a)] +=",
+     [HB.test_describe_hard_ramp_closed_forms, HB.test_describe_hard_upright_equals_integer_eq5]),
+    ("hard_fx_weights_transposed",
+     "int64_t top = v00 * (2048 - fc) + v01 * fc;\n    int64_t bot = v10 * (2048 - fc) + v11 * fc;",
+     "int64_t top = v00 * (2048 - fr) + v01 * fr;\n    int64_t bot = v10 * (2048 - fr) + v11 * fr;",
+     [HB.test_describe_hard_ramp_closed_forms]),
+    ("hard_fx_turn_sign",
+     "int64_t pr = (int64_t)u * cq - (int64_t)v * sq,", "int64_t pr = (int64_t)u * cq + (int64_t)v * sq,",
+     [HB.test_describe_hard_ramp_closed_forms, HB.test_describe_hard_rotation_90_invariant]),
+    ("hard_turn_truncated",
+     "*cq = (int)floor(2048.0 * cos(th) + 0.5);", "*cq = (int)floor(2048.0 * cos(th));",
+     [HB.test_turn_table_is_rounded_2048_cos_sin]),
     ("describe_turn_sign",
      "double py = y + u * c - v * s;", "double py = y + u * c + v * s;",
      [DS.test_describe_ramp_closed_forms, DS.test_describe_rotation_90_invariant]),
