@@ -94,6 +94,9 @@ typedef struct lp_config {
                                      FP64, ties to the earlier raster position */
     int32_t  border;              /* 1: a point whose describe neighbourhood (radius
                                      ceil(2 sqrt(2) w_s + 1.5) + 1) leaves the image is invalid */
+    int32_t  hard_bins;           /* Sec. 2.3's 8-direction histogram: 0 = each magnitude split
+                                     linearly between the two nearest bins; 1 = all of it in the
+                                     45-degree sector [45k, 45(k+1)) holding atan2(b, a) */
 } lp_config;
 
 typedef struct lp_ctx lp_ctx;
@@ -385,16 +388,20 @@ LP_API int lp_mlp_train_step(lp_mlp* mlp, const float* feat, const uint8_t* labe
  * Errors: LP_ERR_ARG (hold < 0). */
 LP_API int lp_diag_set_batch_hold(lp_ctx* ctx, int32_t hold);
 
-/* Tile autotuning of the BF16 matcher (BASELINE's uneven-batch workload; the
- * paper has no counterpart).  on = 1: the first lp_match (or stitch call) of a
- * size class -- (ceil(log2 NA), ceil(log2 NB)) -- that runs outside stream
- * capture times a few choices of the column-split count S and the pass-1 tile
- * stride around the built-in ones on the caller's own inputs (each once,
- * after a warm-up run; the call synchronises the stream for it), keeps the
- * fastest for the class in the context and uses it from then on.  Every
- * choice is certified against the FP32 form, so outputs do not change.  Under
- * capture, classes not yet tuned run the built-in choice.  on = 0: the
- * built-in choice everywhere (the table is kept).
+/* Tile autotuning of the BF16 matcher, for batches of pairs of uneven sizes
+ * (the paper has no counterpart).  on = 1: the first lp_match of a size class
+ * -- (ceil(log2 NA), ceil(log2 NB)) -- that runs outside stream capture times
+ * a few choices of the column-split count S and the pass-1 tile stride around
+ * the built-in ones on the caller's own inputs (each once, after a warm-up
+ * run; the call synchronises the stream for it), keeps the fastest for the
+ * class in the context and uses it from then on (lp_stitch_pair tunes the
+ * same way, inside its own lp_match).  lp_stitch_pairs runs the built-in
+ * choice for a class it meets first, tunes the class on that call's
+ * descriptors once its results are complete, and uses the tuned choice from
+ * its next call on.  Every choice is certified against the FP32 form, so
+ * outputs do not change.  Under capture, classes not yet tuned run the
+ * built-in choice.  on = 0: the built-in choice everywhere (the table is
+ * kept).
  * Errors: LP_ERR_ARG. */
 LP_API int lp_set_autotune(lp_ctx* ctx, int32_t on);
 

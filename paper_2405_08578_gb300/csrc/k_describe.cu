@@ -48,6 +48,8 @@ struct DescParams {
     int wsl[LP_MAX_SCALES], Pl[LP_MAX_SCALES];
     float cs[36][2];        // cos, sin of (k + 0.5) * 10 degrees
     int upright;
+    int hard;               // 1: each magnitude whole in its 45-degree sector, fixed-point grid
+    int cq[36], sq[36];     // round(2^11 cos), round(2^11 sin) of (k + 0.5) * 10 degrees
     int warp_bytes, patch_bytes, mid_bytes;
     int word_ok;           // gray base 4-byte aligned and pitch % 4 == 0: interior patches load 32-bit words
     const uint8_t* lut_bin;
@@ -128,6 +130,54 @@ __device__ __forceinline__ void grad_polar(float a, float b, float x2, float& m,
     if (o >= 8.f) o -= 8.f;
 }
 
+// Sec. 2.3 read literally: the sector [45k, 45(k + 1)) degrees that holds
+// atan2(b, a), by signs and magnitude comparisons (a direction on an edge
+// belongs to the sector it starts); (a, b) != 0.
+template <typename T>
+__device__ __forceinline__ int octant(T a, T b)
+{
+    if (b >= 0 && a > 0) return b < a ? 0 : 1;
+    if (a <= 0 && b > 0) return b > -a ? 2 : 3;
+    if (b <= 0 && a < 0) return -b < -a ? 4 : 5;
+    return a < -b ? 6 : 7;
+}
+
+// Fixed point of the hard-bin grid: offsets in units of 2^-11 px, intensities
+// in units of 2^-22 (every value exact in 32-bit integers: 255 * 2^22 < 2^31).
+constexpr int kFx = 11;
+constexpr int kFxOne = 1 << kFx;
+constexpr float kFxInv2 = 1.f / (float)(1 << (2 * kFx));
+
+// Histogram contribution of the sample at turned-grid point g (row stride G):
+// Eq. 5 differences along the turned axes, w0 to bin b0 and w1 to bin
+// (b0 + 1) mod 8.  Soft: FP32 grid, the magnitude split linearly between the
+// two nearest bins.  Hard: exact fixed-point grid, the whole magnitude in the
+// sector of the integer gradient.  False for a zero gradient.
+__device__ __forceinline__ bool grid_sample(const float* g, int G, int hard, int& b0, float& w0, float& w1)
+{
+    if (hard) {
+        const int a = __float_as_int(g[G]) - __float_as_int(g[-G]);
+        const int b = __float_as_int(g[1]) - __float_as_int(g[-1]);
+        if ((a | b) == 0) return false;
+        b0 = octant(a, b);
+        const float fa = (float)a, fb = (float)b;
+        w0 = sqrtf(fa * fa + fb * fb) * kFxInv2;
+        w1 = 0.f;
+        return true;
+    }
+    const float a = g[G] - g[-G];
+    const float b = g[1] - g[-1];
+    const float x2 = a * a + b * b;
+    if (!(x2 > 0.f)) return false;
+    float m, o;
+    grad_polar(a, b, x2, m, o);
+    b0 = (int)o;
+    const float t = o - (float)b0;
+    w0 = m * (1.f - t);
+    w1 = m * t;
+    return true;
+}
+
 // Shared-memory row stride of an S-wide patch: room for the up-to-3-byte shift
 // of word-aligned rows.
 __host__ __device__ __forceinline__ int patch_stride(int S) { return 4 * ((S + 6) / 4); }
@@ -143,6 +193,29 @@ __device__ __forceinline__ float bilinear(const uint8_t* patch, int S, int P, fl
     const float top = v00 + fc * (v01 - v00);
     const float bot = v10 + fc * (v11 - v10);
     return top + fr * (bot - top);
+}
+
+// 2^22 * bilinear intensity at the fixed-point offset (r, c) * 2^-11 from the
+// patch centre, exact.
+__device__ __forceinline__ int bilinear_fx(const uint8_t* patch, int S, int P, int r, int c)
+{
+    const int fr = r & (kFxOne - 1), fc = c & (kFxOne - 1);
+    const uint8_t* q = patch + ((r >> kFx) + P) * S + (c >> kFx) + P;
+    const int top = (int)q[0] * (kFxOne - fc) + (int)q[1] * fc;
+    const int bot = (int)q[S] * (kFxOne - fc) + (int)q[S + 1] * fc;
+    return top * (kFxOne - fr) + bot * fr;
+}
+
+// One turned-grid value at frame offset (fu, fv): the FP32 bilinear intensity
+// at (fu c - fv s, fu s + fv c), or (hard) the exact fixed-point one at
+// (fu cq - fv sq, fu sq + fv cq) * 2^-11, its int bits kept in the float word.
+__device__ __forceinline__ void grid_value(float* dst, const uint8_t* patch, int S, int P, int fu, int fv, float c,
+                                           float s, int hard, int cq, int sq)
+{
+    if (hard)
+        *dst = __int_as_float(bilinear_fx(patch, S, P, fu * cq - fv * sq, fu * sq + fv * cq));
+    else
+        *dst = bilinear(patch, S, P, (float)fu * c - (float)fv * s, (float)fu * s + (float)fv * c);
 }
 
 // Walk the flattened index e = lane, lane + 32, ... of an n-wide 2-D range
@@ -240,15 +313,14 @@ __global__ void __launch_bounds__(kWarps * 32) k_describe_all(const DescParams p
     }
     const float c = p.upright ? 1.f : p.cs[best][0];
     const float s = p.upright ? 0.f : p.cs[best][1];
+    const int cq = p.upright ? kFxOne : p.cq[best], sq = p.upright ? 0 : p.sq[best];
 
     // ---- intensities of the turned grid, extended by one sample on each side
     const int G = 2 * R + 2;
     {
         Walk2D w(lane, G);
-        for (; w.r < G; w.next()) {
-            const float fu = (float)(w.r - R - 1), fv = (float)(w.c - R - 1);
-            grid[w.r * G + w.c] = bilinear(patch, SP, P, fu * c - fv * s, fu * s + fv * c);
-        }
+        for (; w.r < G; w.next())
+            grid_value(grid + w.r * G + w.c, patch, SP, P, w.r - R - 1, w.c - R - 1, c, s, p.hard, cq, sq);
     }
     float* mine = acc + lane * kAccStride;
 #pragma unroll
@@ -260,17 +332,11 @@ __global__ void __launch_bounds__(kWarps * 32) k_describe_all(const DescParams p
     int iu = 0, iv = lane & 1;
     while (iv >= ws) { iv -= ws; ++iu; }
     for (; iu < ws;) {
-        const float* g = grid + (cr * ws + iu + 1) * G + cc * ws + iv + 1;
-        const float a = g[G] - g[-G];
-        const float b = g[1] - g[-1];
-        const float x2 = a * a + b * b;
-        if (x2 > 0.f) {
-            float m, o;
-            grad_polar(a, b, x2, m, o);
-            const int b0 = (int)o;
-            const float t = o - (float)b0;
-            mine[b0] += m * (1.f - t);
-            mine[(b0 + 1) & 7] += m * t;
+        int b0;
+        float w0, w1;
+        if (grid_sample(grid + (cr * ws + iu + 1) * G + cc * ws + iv + 1, G, p.hard, b0, w0, w1)) {
+            mine[b0] += w0;
+            mine[(b0 + 1) & 7] += w1;
         }
         iv += 2;
         while (iv >= ws) { iv -= ws; ++iu; }
@@ -389,10 +455,10 @@ __global__ void __launch_bounds__(kCtaThreads) k_describe_cta(const DescParams p
     }
     const float c = p.upright ? 1.f : p.cs[best][0];
     const float s = p.upright ? 0.f : p.cs[best][1];
+    const int cq = p.upright ? kFxOne : p.cq[best], sq = p.upright ? 0 : p.sq[best];
     for (int e = tid; e < G * G; e += kCtaThreads) {
         const int iu = e / G, iv = e - (e / G) * G;
-        const float fu = (float)(iu - R - 1), fv = (float)(iv - R - 1);
-        grid[e] = bilinear(patch, SP, P, fu * c - fv * s, fu * s + fv * c);
+        grid_value(grid + e, patch, SP, P, iu - R - 1, iv - R - 1, c, s, p.hard, cq, sq);
     }
     __syncthreads();
     const int cell = tid >> 3, sub = tid & 7, cr = cell >> 2, cc = cell & 3;
@@ -401,19 +467,13 @@ __global__ void __launch_bounds__(kCtaThreads) k_describe_cta(const DescParams p
     for (int q = 0; q < 8; ++q) h[q] = 0.f;
     for (int i = sub; i < ws * ws; i += 8) {
         const int iu = i / ws, iv = i - (i / ws) * ws;
-        const float* g = grid + (cr * ws + iu + 1) * G + cc * ws + iv + 1;
-        const float a = g[G] - g[-G];
-        const float b = g[1] - g[-1];
-        const float x2 = a * a + b * b;
-        if (x2 > 0.f) {
-            float m, o;
-            grad_polar(a, b, x2, m, o);
-            const int b0 = (int)o;
-            const float t = o - (float)b0;
+        int b0;
+        float w0, w1;
+        if (grid_sample(grid + (cr * ws + iu + 1) * G + cc * ws + iv + 1, G, p.hard, b0, w0, w1)) {
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
-                h[q] += (q == b0) ? m * (1.f - t) : 0.f;
-                h[q] += (q == ((b0 + 1) & 7)) ? m * t : 0.f;
+                h[q] += (q == b0) ? w0 : 0.f;
+                h[q] += (q == ((b0 + 1) & 7)) ? w1 : 0.f;
             }
         }
     }
@@ -507,22 +567,40 @@ __global__ void __launch_bounds__(kWarps * 32) k_describe_global(const DescParam
     }
     const float c = p.upright ? 1.f : p.cs[best][0];
     const float s = p.upright ? 0.f : p.cs[best][1];
+    const int cq = p.upright ? kFxOne : p.cq[best], sq = p.upright ? 0 : p.sq[best];
+    auto bil_fx = [&](int r, int c_) -> int {
+        const int fr = r & (kFxOne - 1), fc = c_ & (kFxOne - 1), yi = r >> kFx, xi = c_ >> kFx;
+        const int top = px(yi, xi) * (kFxOne - fc) + px(yi, xi + 1) * fc;
+        const int bot = px(yi + 1, xi) * (kFxOne - fc) + px(yi + 1, xi + 1) * fc;
+        return top * (kFxOne - fr) + bot * fr;
+    };
     float* mine = acc + lane * kAccStride;
     for (int q = 0; q < 8; ++q) mine[q] = 0.f;
     const int cell = lane >> 1, cr = cell >> 2, cc = cell & 3;
     for (int i = lane & 1; i < ws * ws; i += 2) {
-        const float fu = (float)(-R + cr * ws + i / ws), fv = (float)(-R + cc * ws + i % ws);
-        const float dy = fu * c - fv * s, dx = fu * s + fv * c;
-        const float a = bil(dy + c, dx + s) - bil(dy - c, dx - s);
-        const float b = bil(dy - s, dx + c) - bil(dy + s, dx - c);
-        const float x2 = a * a + b * b;
-        if (x2 > 0.f) {
-            float m, o;
-            grad_polar(a, b, x2, m, o);
-            const int b0 = (int)o;
-            const float t = o - (float)b0;
-            mine[b0] += m * (1.f - t);
-            mine[(b0 + 1) & 7] += m * t;
+        const int iu = -R + cr * ws + i / ws, iv = -R + cc * ws + i % ws;
+        // the sample's four neighbours along the turned axes, as a 3 x 3 grid
+        // patch with the unused corners left out
+        float nb[9];
+        if (p.hard) {
+            const int pr = iu * cq - iv * sq, pc = iu * sq + iv * cq;
+            nb[1] = __int_as_float(bil_fx(pr - cq, pc - sq));
+            nb[7] = __int_as_float(bil_fx(pr + cq, pc + sq));
+            nb[3] = __int_as_float(bil_fx(pr + sq, pc - cq));
+            nb[5] = __int_as_float(bil_fx(pr - sq, pc + cq));
+        } else {
+            const float fu = (float)iu, fv = (float)iv;
+            const float dy = fu * c - fv * s, dx = fu * s + fv * c;
+            nb[1] = bil(dy - c, dx - s);
+            nb[7] = bil(dy + c, dx + s);
+            nb[3] = bil(dy + s, dx - c);
+            nb[5] = bil(dy - s, dx + c);
+        }
+        int b0;
+        float w0, w1;
+        if (grid_sample(nb + 4, 3, p.hard, b0, w0, w1)) {
+            mine[b0] += w0;
+            mine[(b0 + 1) & 7] += w1;
         }
     }
     __syncwarp();
@@ -647,14 +725,24 @@ __global__ void __launch_bounds__(kSplitThreads) k_desc_cell(const DescParams p)
     const int best = p.upright ? 0 : p.ori[k];
     const float c = p.upright ? 1.f : p.cs[best][0];
     const float s = p.upright ? 0.f : p.cs[best][1];
+    const int tq = p.upright ? kFxOne : p.cq[best], ts = p.upright ? 0 : p.sq[best];
     // frame points (fu, fv) = (fu0 + iu, fv0 + iv), iu, iv in [0, Gc): image
-    // offsets (dy, dx) = (fu c - fv s, fu s + fv c) from the point
+    // offsets (dy, dx) = (fu c - fv s, fu s + fv c) from the point (hard: the
+    // fixed-point turn (tq, ts) * 2^-11)
     const int fu0 = -R + cr * ws - 1, fv0 = -R + cq * ws - 1;
     float ymin = 3.4e38f, ymax = -3.4e38f, xmin = 3.4e38f, xmax = -3.4e38f;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        const float fu = (float)(fu0 + ((q & 1) ? Gc - 1 : 0)), fv = (float)(fv0 + ((q & 2) ? Gc - 1 : 0));
-        const float dy = fu * c - fv * s, dx = fu * s + fv * c;
+        const int iu = fu0 + ((q & 1) ? Gc - 1 : 0), iv = fv0 + ((q & 2) ? Gc - 1 : 0);
+        float dy, dx;
+        if (p.hard) {
+            dy = (float)((iu * tq - iv * ts) >> kFx);
+            dx = (float)((iu * ts + iv * tq) >> kFx);
+        } else {
+            const float fu = (float)iu, fv = (float)iv;
+            dy = fu * c - fv * s;
+            dx = fu * s + fv * c;
+        }
         ymin = fminf(ymin, dy); ymax = fmaxf(ymax, dy); xmin = fminf(xmin, dx); xmax = fmaxf(xmax, dx);
     }
     // one spare row and column on each side; the taps below are clamped to the box
@@ -671,6 +759,19 @@ __global__ void __launch_bounds__(kSplitThreads) k_desc_cell(const DescParams p)
     __syncthreads();
     for (int e = threadIdx.x; e < Gc * Gc; e += kSplitThreads) {
         const int iu = e / Gc, iv = e - (e / Gc) * Gc;
+        if (p.hard) {
+            // box-relative fixed-point offset (the box covers every tap; the
+            // clamp only keeps reads inside it)
+            const int rr = (fu0 + iu) * tq - (fv0 + iv) * ts - r0 * kFxOne;
+            const int cc = (fu0 + iu) * ts + (fv0 + iv) * tq - c0 * kFxOne;
+            const int ri = min(max(rr >> kFx, 0), nr - 2), ci = min(max(cc >> kFx, 0), nc - 2);
+            const int fr = rr & (kFxOne - 1), fc = cc & (kFxOne - 1);
+            const uint8_t* b0 = box + ri * SPc + ci;
+            const int top = (int)b0[0] * (kFxOne - fc) + (int)b0[1] * fc;
+            const int bot = (int)b0[SPc] * (kFxOne - fc) + (int)b0[SPc + 1] * fc;
+            grid[e] = __int_as_float(top * (kFxOne - fr) + bot * fr);
+            continue;
+        }
         const float fu = (float)(fu0 + iu), fv = (float)(fv0 + iv);
         const float rr = fu * c - fv * s - (float)r0, cc = fu * s + fv * c - (float)c0;
         const float rf = floorf(rr), cf = floorf(cc);
@@ -688,19 +789,13 @@ __global__ void __launch_bounds__(kSplitThreads) k_desc_cell(const DescParams p)
     for (int q = 0; q < 8; ++q) h[q] = 0.f;
     for (int i = threadIdx.x; i < ws * ws; i += kSplitThreads) {
         const int iu = i / ws, iv = i - (i / ws) * ws;
-        const float* g = grid + (iu + 1) * Gc + iv + 1;
-        const float a = g[Gc] - g[-Gc];
-        const float b = g[1] - g[-1];
-        const float x2 = a * a + b * b;
-        if (x2 > 0.f) {
-            float m, o;
-            grad_polar(a, b, x2, m, o);
-            const int b0 = (int)o;
-            const float t = o - (float)b0;
+        int b0;
+        float w0, w1;
+        if (grid_sample(grid + (iu + 1) * Gc + iv + 1, Gc, p.hard, b0, w0, w1)) {
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
-                h[q] += (q == b0) ? m * (1.f - t) : 0.f;
-                h[q] += (q == ((b0 + 1) & 7)) ? m * t : 0.f;
+                h[q] += (q == b0) ? w0 : 0.f;
+                h[q] += (q == ((b0 + 1) & 7)) ? w1 : 0.f;
             }
         }
     }
@@ -797,12 +892,12 @@ __global__ void k_border_reject(const uint32_t* kp, int H, int W, const BorderPa
 }
 
 cudaError_t launch_describe(const uint8_t* gray, int H, int W, int pitch, const uint32_t* kp,
-                            const ScaleTable& st, int upright, int border, const void* luts, uint8_t* ori,
+                            const ScaleTable& st, int upright, int border, int hard, const void* luts, uint8_t* ori,
                             float* desc, uint16_t* desc_bf16, uint8_t* valid, const Fork* fork, cudaStream_t s)
 {
     if (border) {
-        cudaError_t e = launch_describe(gray, H, W, pitch, kp, st, upright, 0, luts, ori, desc, desc_bf16, valid,
-                                        fork, s);
+        cudaError_t e = launch_describe(gray, H, W, pitch, kp, st, upright, 0, hard, luts, ori, desc, desc_bf16,
+                                        valid, fork, s);
         if (e != cudaSuccess) return e;
         BorderParams b;
         b.nL = st.nL;
@@ -818,8 +913,11 @@ cudaError_t launch_describe(const uint8_t* gray, int H, int W, int pitch, const 
         const double th = (k + 0.5) * 10.0 * 3.14159265358979323846 / 180.0;
         p.cs[k][0] = (float)cos(th);
         p.cs[k][1] = (float)sin(th);
+        p.cq[k] = (int)floor(2048.0 * cos(th) + 0.5);
+        p.sq[k] = (int)floor(2048.0 * sin(th) + 0.5);
     }
     p.upright = upright;
+    p.hard = hard;
     p.word_ok = ((reinterpret_cast<uintptr_t>(gray) & 3u) == 0 && (pitch & 3) == 0) ? 1 : 0;
     p.lut_w = reinterpret_cast<const uint32_t*>(luts);
     p.lut_bin = reinterpret_cast<const uint8_t*>(luts) + (((size_t)kLutWeights * 4 + 255) & ~size_t(255));

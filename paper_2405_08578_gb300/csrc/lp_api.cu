@@ -164,6 +164,7 @@ int check_cfg(lp_ctx* c, const lp_config* cfg)
     if (!(cfg->ratio >= 0.f && cfg->ratio <= 1.f)) return fail(c, LP_ERR_ARG, "ratio must be in [0, 1]");
     if (!(cfg->alpha >= 0.0 && cfg->alpha < 1e300)) return fail(c, LP_ERR_ARG, "alpha must be finite and >= 0");
     if (cfg->border != 0 && cfg->border != 1) return fail(c, LP_ERR_ARG, "border must be 0 or 1");
+    if (cfg->hard_bins != 0 && cfg->hard_bins != 1) return fail(c, LP_ERR_ARG, "hard_bins must be 0 or 1");
     if (cfg->ransac_iters < 1 || cfg->ransac_iters > 65536) return fail(c, LP_ERR_ARG, "ransac_iters outside 1..65536");
     if (!(cfg->thresh_px > 0.f)) return fail(c, LP_ERR_ARG, "thresh_px must be > 0");
     if (cfg->precision != LP_PREC_FP32 && cfg->precision != LP_PREC_BF16)
@@ -251,6 +252,7 @@ int lp_config_default(lp_config* cfg)
     cfg->model = LP_MODEL_HOMOGRAPHY;
     cfg->alpha = 0.0;
     cfg->border = 0;
+    cfg->hard_bins = 0;
     return LP_OK;
 }
 
@@ -386,7 +388,8 @@ int lp_describe(lp_ctx* c, const uint8_t* gray, int H, int W, int gray_pitch, co
     }
     if (int r = ensure_fork(c)) return r;
     LP_CUDA(c, lp::launch_describe(gray, H, W, gray_pitch, kp_idx, st, c->cfg.upright, c->cfg.border,
-                                   c->buf[B_LUTS].p, ori, desc, desc_bf16, valid, &c->fork, S(stream)));
+                                   c->cfg.hard_bins, c->buf[B_LUTS].p, ori, desc, desc_bf16, valid, &c->fork,
+                                   S(stream)));
     return LP_OK;
 }
 
@@ -824,7 +827,8 @@ int lp_stitch_pairs_ids(lp_ctx* c, const lp_image* imgs, int N, const int32_t* p
     uint8_t* base = reinterpret_cast<uint8_t*>(al256(reinterpret_cast<uintptr_t>(c->buf[B_BATCH].p)));
     int32_t* Mbuf = M_out ? M_out : reinterpret_cast<int32_t*>(base + o_M);
 
-    std::vector<long long> key = {N, P, ch, c->batch_hold, (long long)(uintptr_t)HM, (long long)(uintptr_t)n_in,
+    std::vector<long long> key = {N, P, ch, c->batch_hold, c->autotune ? (long long)c->tune.size() : -1ll,
+                                  (long long)(uintptr_t)HM, (long long)(uintptr_t)n_in,
                                   (long long)(uintptr_t)valid, (long long)(uintptr_t)Mbuf,
                                   (long long)(uintptr_t)c->buf[B_BATCH].p, (long long)(uintptr_t)c->buf[B_MATCH_WS].p,
                                   (long long)(uintptr_t)c->buf[B_RANSAC_WS].p,
@@ -966,6 +970,26 @@ int lp_stitch_pairs_ids(lp_ctx* c, const lp_image* imgs, int N, const int32_t* p
     // first call for this key: run eagerly, then record the same sequence as a
     // graph for later calls (not on the legacy default stream)
     if ((r = enqueue())) return r;
+    if (bf && c->autotune) {
+        // a size class met for the first time is tuned on this call's own
+        // descriptors, which stay in the batch buffer after the call; the next
+        // call lays its pairs out with the tuned choice (and records its graph)
+        const size_t n0 = c->tune.size();
+        for (int q = 0; q < P; ++q) {
+            int st = 0;
+            if (margs[q].NA == 0 || margs[q].NB == 0 || tuned_splits(c, margs[q].NA, margs[q].NB, &st)) continue;
+            lp::MatchArgs a = margs[q];
+            a.match = (int32_t*)(base + o_match);
+            a.d1 = (float*)(base + o_d1);
+            a.d2 = (float*)(base + o_d2);
+            a.normA = a.normB = nullptr;
+            a.fork = &c->fork;
+            a.ev0 = a.ev1 = nullptr;
+            a.splits = a.pass1_stride = 0;
+            if ((r = tune_match(c, a, s))) return r;
+        }
+        if (c->tune.size() != n0) return LP_OK;
+    }
     if (s) {
         if (c->graph_exec) { cudaGraphExecDestroy(c->graph_exec); c->graph_exec = nullptr; }
         c->graph_key.clear();

@@ -63,9 +63,10 @@ size_t describe_lut_bytes();
 cudaError_t launch_build_luts(void* luts, cudaStream_t s);
 
 // border = 1: points whose neighbourhood (radius st.pr) leaves the image are marked invalid.
+// hard = 1: each sample's magnitude goes whole to its 45-degree sector (no linear split).
 // fork (or nullptr): the scale groups run concurrently on s and the two auxiliary streams.
 cudaError_t launch_describe(const uint8_t* gray, int H, int W, int pitch, const uint32_t* kp,
-                            const ScaleTable& st, int upright, int border, const void* luts, uint8_t* ori,
+                            const ScaleTable& st, int upright, int border, int hard, const void* luts, uint8_t* ori,
                             float* desc, uint16_t* desc_bf16, uint8_t* valid, const Fork* fork, cudaStream_t s);
 cudaError_t launch_diag_orient(int32_t* bins, uint32_t* weights, cudaStream_t s);
 

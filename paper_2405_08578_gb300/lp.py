@@ -38,7 +38,8 @@ class lp_config(C.Structure):
     _fields_ = [("nL", C.c_int32), ("Ls", C.c_int32 * MAX_SCALES), ("beta0", C.c_double), ("ratio", C.c_float),
                 ("delta_s", C.c_float), ("ransac_iters", C.c_int32), ("thresh_px", C.c_float),
                 ("seed", C.c_uint64), ("min_inliers", C.c_int32), ("precision", C.c_int32),
-                ("upright", C.c_int32), ("model", C.c_int32), ("alpha", C.c_double), ("border", C.c_int32)]
+                ("upright", C.c_int32), ("model", C.c_int32), ("alpha", C.c_double), ("border", C.c_int32),
+                ("hard_bins", C.c_int32)]
 
 
 _lib = None
@@ -138,7 +139,7 @@ def _stream(stream=None):
 
 def config(Ls=(16, 32, 64, 128), beta0=0.0, ratio=0.8, delta_s=math.inf, ransac_iters=1000, thresh_px=3.0,
            seed=0, min_inliers=8, precision=PREC_FP32, upright=False, model=MODEL_HOMOGRAPHY, alpha=0.0,
-           border=False) -> lp_config:
+           border=False, hard_bins=False) -> lp_config:
     c = lp_config()
     load().lp_config_default(C.byref(c))
     Ls = list(Ls)
@@ -151,7 +152,7 @@ def config(Ls=(16, 32, 64, 128), beta0=0.0, ratio=0.8, delta_s=math.inf, ransac_
     c.ransac_iters, c.thresh_px, c.seed = int(ransac_iters), float(thresh_px), int(seed)
     c.min_inliers, c.precision, c.upright = int(min_inliers), int(precision), int(bool(upright))
     c.model = int(model)
-    c.alpha, c.border = float(alpha), int(bool(border))
+    c.alpha, c.border, c.hard_bins = float(alpha), int(bool(border)), int(bool(hard_bins))
     return c
 
 

@@ -325,6 +325,40 @@ def test_autotuned_matcher_equals_builtin_and_caches():
     assert tun.lp_sync_status() == 0
 
 
+def test_autotuned_batch_equals_builtin_and_fills_the_table():
+    """lp_stitch_pairs with the tuner on: the first call runs the built-in
+    choice and tunes every size class it met, later calls run the tuned
+    choice (a new graph); every call's outputs equal the built-in context's
+    bit for bit."""
+    Ls = (16, 32, 64, 128)
+    ps = synth.uneven_pairs(4, seed=7, long_lo=480, long_hi=1400)
+    imgs = [im for p in ps for im in (p.A, p.B)]
+    bufs = [lp.pitched_device(im) for im in imgs]
+    images = [(b, im.shape[0], im.shape[1], pt, 1) for (b, pt), im in zip(bufs, imgs)]
+    plist = [(2 * q, 2 * q + 1) for q in range(len(ps))]
+    base = lp.Context(Ls=Ls, precision=lp.PREC_BF16)
+    tun = lp.Context(Ls=Ls, precision=lp.PREC_BF16)
+    tun.lp_set_autotune(True)
+    want = _outputs(len(ps))
+    base.lp_stitch_pairs(images, *want[:3], pairs=plist, M_out=want[3])
+    torch.cuda.synchronize()
+    buckets = {int(np.ceil(np.log2(lp.lp_num_keypoints(p.A.shape[0], p.A.shape[1], Ls)))) for p in ps}
+    for call in range(3):
+        got = _outputs(len(ps))
+        tun.lp_stitch_pairs(images, *got[:3], pairs=plist, M_out=got[3])
+        torch.cuda.synchronize()
+        for x, y in zip(want, got):
+            assert torch.equal(x, y), call
+        table = tun.lp_autotune_table()
+        assert {(r["log2_NA"], r["log2_NB"]) for r in table} == {(b, b) for b in buckets}
+        if call == 0:
+            first = table
+        assert table == first
+    for row in table:
+        assert 1 <= row["splits"] <= 16 and row["pass1_stride"] in (2, 3, 4)
+    assert tun.lp_sync_status() == 0 and base.lp_sync_status() == 0
+
+
 def test_batch_wait_gives_up_and_context_recovers():
     """The batched distance passes run in one persistent launch in which a
     pass-2 unit waits (at most 2 s) for its rows' pass-1 values.  A hold makes

@@ -1,5 +1,6 @@
 """Paper-literal variants through the C ABI against the oracle: Eq. 1's finite
-alpha ramp, border rejection, and Sec. 2.4's match rule without a ratio test."""
+alpha ramp, border rejection, Sec. 2.3's hard 8-direction histogram, and
+Sec. 2.4's match rule without a ratio test."""
 from __future__ import annotations
 
 import numpy as np
@@ -57,6 +58,40 @@ def test_border_rejection_valid_flags(shape, Ls, upright):
     # the flag only removes points: without it the same points are described
     _, _, valid_all = G.describe(lp.Context(Ls=Ls, upright=upright), g, kp)
     assert not (valid.astype(bool) & ~valid_all.astype(bool)).any()
+
+
+@pytest.mark.parametrize("upright", [False, True])
+@pytest.mark.parametrize("shape,Ls", [((150, 190), (8, 16, 32)), ((480, 640), (16, 32, 64, 128)),
+                                      ((260, 330), (100, 128)), ((300, 410), (32, 40)), ((960, 1000), (900,))])
+def test_hard_bins_vs_oracle(shape, Ls, upright):
+    """Hard 8-direction histograms on the exact fixed-point turned grid: every
+    gradient is an exact integer on both sides, so every sector decision
+    agrees and every descriptor is within 1e-4 of the oracle's (scales with
+    w_s <= 15, 25, 32 and 225, i.e. the warp, CTA, per-cell and
+    global-memory kernels)."""
+    p = synth.small_pair(shape[0], shape[1], seed=shape[1] + 1)
+    g = p.A
+    H, W = g.shape
+    ctx = lp.Context(Ls=Ls, upright=upright, hard_bins=True)
+    kp = oracle.detect(g, Ls)
+    ori, desc, valid = G.describe(ctx, g, kp)
+    _, ws = oracle.keypoint_scales(H, W, Ls)
+    o_ori = None if upright else oracle.orient(g, kp, ws)
+    o_desc, o_valid = oracle.describe(g, kp, ws, o_ori, hard=True)
+    assert np.array_equal(valid, o_valid)
+    if not upright:
+        assert np.array_equal(ori, o_ori)
+    assert np.abs(desc - o_desc).max() <= DESC_TOL
+    # the variant is not the default reading
+    _, soft, _ = G.describe(lp.Context(Ls=Ls, upright=upright), g, kp)
+    assert np.abs(soft - desc).max() > 5e-3
+
+
+def test_hard_bins_flag_is_checked():
+    c = lp.config(Ls=(16,))
+    c.hard_bins = 2
+    with pytest.raises(lp.LpError):
+        lp.Context(cfg=c)
 
 
 def _unit(rng, n):
