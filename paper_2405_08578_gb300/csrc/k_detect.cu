@@ -57,20 +57,24 @@ __device__ __forceinline__ uint8_t byte_of(const uint4& v, int i)
     return (uint8_t)(w >> (8 * (i & 3)));
 }
 
-// 16 interleaved RGB pixels (48 bytes) -> 16 intensities.  Pixel p's bytes
-// are gathered into one word (R, G, B, x) and 299 R + 587 G + 114 B + 500 is
-// formed exactly with two byte dot products: 299 = 256 + 43, 587 = 512 + 75,
-// so the sum is dp(43, 75, 114, 0) + 500 + 256 dp(1, 2, 0, 0).
+// 16 interleaved RGB pixels (48 bytes, 12 words) -> 16 intensities.
+// 299 R + 587 G + 114 B + 500 is formed exactly with two dot products of
+// 16-bit weights with byte pairs (dp2a), taken straight from the interleaved
+// words: pixel 4g + j's bytes sit at byte offsets 3j .. 3j + 2 of words
+// 3g .. 3g + 2, so each pixel needs one or two words and no byte gathering.
 __device__ __forceinline__ uint4 gray16(const uint4& c0, const uint4& c1, const uint4& c2)
 {
     const uint32_t w[12] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w, c2.x, c2.y, c2.z, c2.w};
+    // weight pairs (the low 16 bits multiply the lower byte of the selected pair)
+    constexpr uint32_t kRG = 299u | (587u << 16), kB_ = 114u, k_R = 299u << 16, kGB = 587u | (114u << 16);
     uint32_t q[16];
 #pragma unroll
-    for (int p = 0; p < 16; ++p) {
-        const int i = (3 * p) >> 2, j = (3 * p) & 3;
-        const uint32_t rgb = __byte_perm(w[i], i + 1 < 12 ? w[i + 1] : w[i],
-                                         (uint32_t)(j | ((j + 1) << 4) | ((j + 2) << 8) | ((j + 3) << 12)));
-        q[p] = div1000(__dp4a(rgb, 0x00000201u, 0u) * 256u + __dp4a(rgb, 0x00724B2Bu, 500u));
+    for (int g = 0; g < 4; ++g) {
+        const uint32_t a = w[3 * g], b = w[3 * g + 1], c = w[3 * g + 2];
+        q[4 * g] = div1000(__dp2a_hi(kB_, a, __dp2a_lo(kRG, a, 500u)));          // a: R G B .
+        q[4 * g + 1] = div1000(__dp2a_lo(kGB, b, __dp2a_hi(k_R, a, 500u)));      // a: . . . R  b: G B . .
+        q[4 * g + 2] = div1000(__dp2a_lo(kB_, c, __dp2a_hi(kRG, b, 500u)));      // b: . . R G  c: B . . .
+        q[4 * g + 3] = div1000(__dp2a_hi(kGB, c, __dp2a_lo(k_R, c, 500u)));      // c: . R G B
     }
     // four intensities (each < 256) per word: bytes (q0, q1, q2, q3)
     uint32_t o[4];
@@ -293,9 +297,10 @@ __global__ void __launch_bounds__(kDetectThreads) k_detect_nested_batch(const __
 
 // ------------------------------------------------------------------ TMA-fed fast path
 // Nested scales drawn from {16, 32, 64, 128} with 16 the finest, 8-bit gray
-// or RGB input.  Persistent CTAs (one per SM) walk a flat list of 128 x 128
-// tiles of up to kDetectBatch images.
-//   warp 16     streams whole tiles into a 4-stage shared-memory ring with
+// or RGB input.  Persistent CTAs (two per SM, so that one CTA's compute
+// warps run while the other's wait on their ring) walk a flat list of
+// 128 x 128 tiles of up to kDetectBatch images.
+//   warp 16     streams whole tiles into a 2-stage shared-memory ring with
 //               cp.async.bulk.tensor (one 2-D box of 128 rows x 128 pixels,
 //               out-of-image bytes zero-filled).
 //   warps 0-15  all work on every tile: warp w holds pixel rows [8 w, 8 w + 8),
@@ -310,8 +315,15 @@ __global__ void __launch_bounds__(kDetectThreads) k_detect_nested_batch(const __
 // A window that is not full is dropped at output, so out-of-image pixels
 // never reach a kept key.  Every wait is bounded (2 s): on expiry the CTA
 // records LP_ERR_TIMEOUT, lets its copies in flight land and returns.
+#ifndef LP_DETECT_STAGES
+#define LP_DETECT_STAGES 2
+#endif
+#ifndef LP_DETECT_CTAS_PER_SM
+#define LP_DETECT_CTAS_PER_SM 2
+#endif
 constexpr int kTmaTile = 128;
-constexpr int kTmaStages = 4;
+constexpr int kTmaStages = LP_DETECT_STAGES;             // ring stages per CTA
+constexpr int kTmaMinBlocks = LP_DETECT_CTAS_PER_SM;     // resident CTAs per SM the registers allow
 constexpr int kTmaCompute = 16;                          // compute warps
 constexpr int kTmaThreads = 32 * (kTmaCompute + 2);      // + producer warp + reducer warp
 
@@ -417,11 +429,14 @@ __device__ __forceinline__ void put_key(const TmaImage& im, int l, int gx, int g
 }
 
 template <int CH>
-__global__ void __launch_bounds__(kTmaThreads, 1) k_detect_tma(const __grid_constant__ DetectTmaBatch b)
+__global__ void __launch_bounds__(kTmaThreads, kTmaMinBlocks) k_detect_tma(const __grid_constant__ DetectTmaBatch b)
 {
     constexpr uint32_t kStageBytes = kTmaTile * kTmaTile * CH;   // 48 KB (RGB) or 16 KB (gray)
     extern __shared__ uint8_t dsm_raw[];
-    uint8_t* dsm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(dsm_raw) + 1023) & ~uintptr_t(1023));
+    // 1024-byte aligned, as an offset from the shared array so that every
+    // access below stays a shared-memory access (an integer round trip would
+    // leave generic pointers)
+    uint8_t* dsm = dsm_raw + ((1024u - (d_smem_u32(dsm_raw) & 1023u)) & 1023u);
     uint64_t* full = reinterpret_cast<uint64_t*>(dsm + kTmaStages * kStageBytes);
     uint64_t* empty = full + kTmaStages;
     uint64_t* xfull = empty + kTmaStages;    // [2 buffers]: every compute warp wrote its half windows
