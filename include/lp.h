@@ -244,6 +244,27 @@ LP_API int lp_stitch_pair_host(lp_ctx* ctx, const uint8_t* imgA_host, int HA, in
                         const uint8_t* imgB_host, int HB, int WB, int pitchB, int channels,
                         uint32_t pair_id, double* H_host, int32_t* n_in_host, int32_t* M_host, void* stream);
 
+/* One independent pair in host memory, for lp_stitch_pairs_host. */
+typedef struct lp_host_pair {
+    const uint8_t* A;        /* host, HA x WA x channels, pitchA bytes per row (a multiple of 16) */
+    const uint8_t* B;        /* host, HB x WB x channels, pitchB bytes per row */
+    int32_t HA, WA, pitchA, HB, WB, pitchB;
+} lp_host_pair;
+
+/* lp_stitch_pair_host over a stream of P independent pairs (Fig. 2 for each):
+ * the two images of pair q are copied to one of two upload slots on a copy
+ * stream of the context while pair q - 1 is computed on `stream`, so with
+ * pinned host images the copies hide behind the computation.  Pair q gets
+ * pair id pair_id0 + q (its RANSAC sampling stream) and gives exactly what
+ * lp_stitch_pair_host gives for it.  Results of all pairs are copied back at
+ * the end and `stream` is synchronised before returning.
+ *  pairs      host lp_host_pair[P] (the host images must stay valid until return)
+ *  H_host     host double[9 P] (pair q's H at 9 q); n_in_host host int32[P];
+ *  M_host     host int32[P] or NULL
+ * Errors: LP_ERR_ARG (P < 0, null pointers), LP_ERR_ALIGN (pitch), as the stages. */
+LP_API int lp_stitch_pairs_host(lp_ctx* ctx, const lp_host_pair* pairs, int P, int channels, uint32_t pair_id0,
+                                double* H_host, int32_t* n_in_host, int32_t* M_host, void* stream);
+
 /* One image of a batch: device data plus its geometry (lp_detect's rules). */
 typedef struct lp_image {
     const uint8_t* data;     /* device, H x W x channels, pitch bytes per row */

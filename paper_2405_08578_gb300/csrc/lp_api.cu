@@ -23,6 +23,7 @@ enum BufId {
     B_DESC_A, B_DESC_B, B_D16_A, B_D16_B, B_VAL_A, B_VAL_B,
     B_MATCH, B_D1, B_D2, B_PTS, B_M, B_INL, B_H, B_NIN, B_BEST, B_LUTS, B_BATCH, B_PREFIX,
     B_ROWS, B_FEAT, B_PROB, B_COMPACT,
+    B_IMG_A1, B_IMG_B1, B_HSTREAM,
     B_COUNT
 };
 
@@ -71,6 +72,10 @@ struct lp_ctx {
                                         // lp_stitch_pairs: the pairs' RANSAC
     cudaEvent_t img_ev[2] = {nullptr, nullptr};
     cudaEvent_t pair_ev[4] = {nullptr, nullptr, nullptr, nullptr};   // lp_stitch_pairs: compacted, lane slot 0..2 free
+    // lp_stitch_pairs_host: upload stream; per upload slot "uploaded" and
+    // "free again" events, and the caller's start
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t up_ev[2] = {nullptr, nullptr}, free_ev[2] = {nullptr, nullptr}, start_ev = nullptr;
     DBuf buf[B_COUNT];
     char err[512];
 };
@@ -296,6 +301,12 @@ int lp_destroy(lp_ctx* c)
         cudaStreamDestroy(c->img_stream);
         for (auto& e : c->img_ev) cudaEventDestroy(e);
         for (auto& e : c->pair_ev) cudaEventDestroy(e);
+    }
+    if (c->copy_stream) {
+        cudaStreamDestroy(c->copy_stream);
+        for (auto& e : c->up_ev) cudaEventDestroy(e);
+        for (auto& e : c->free_ev) cudaEventDestroy(e);
+        cudaEventDestroy(c->start_ev);
     }
     delete c;
     return LP_OK;
@@ -700,6 +711,73 @@ int lp_stitch_pair_host(lp_ctx* c, const uint8_t* hA, int HA, int WA, int pitchA
     LP_CUDA(c, cudaStreamSynchronize(s));
     *n_in_host = tmp[0];
     if (M_host) *M_host = tmp[1];
+    return LP_OK;
+}
+
+int lp_stitch_pairs_host(lp_ctx* c, const lp_host_pair* pairs, int P, int channels, uint32_t pair_id0,
+                         double* H_host, int32_t* n_in_host, int32_t* M_host, void* stream)
+{
+    if (!c) return LP_ERR_ARG;
+    if (P < 0 || (P > 0 && (!pairs || !H_host || !n_in_host))) return fail(c, LP_ERR_ARG, "null argument or P < 0");
+    if (P == 0) return LP_OK;
+    size_t nA = 16, nB = 16;
+    for (int q = 0; q < P; ++q) {
+        const lp_host_pair& h = pairs[q];
+        if (!h.A || !h.B) return fail(c, LP_ERR_ARG, "null image of pair %d", q);
+        if (h.HA <= 0 || h.HB <= 0 || h.pitchA % 16 || h.pitchB % 16)
+            return fail(c, LP_ERR_ALIGN, "pair %d: pitch must be a multiple of 16", q);
+        nA = std::max(nA, (size_t)h.HA * h.pitchA);
+        nB = std::max(nB, (size_t)h.HB * h.pitchB);
+    }
+    int r;
+    if ((r = ensure(c, B_IMG_A, nA)) || (r = ensure(c, B_IMG_B, nB)) || (r = ensure(c, B_IMG_A1, nA)) ||
+        (r = ensure(c, B_IMG_B1, nB)) || (r = ensure(c, B_HSTREAM, (size_t)P * (9 * sizeof(double) + 8) + 64)) ||
+        (r = ensure_fork(c)))
+        return r;
+    if (!c->copy_stream) {
+        cudaError_t e = cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking);
+        for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+            e = cudaEventCreateWithFlags(&c->up_ev[k], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->free_ev[k], cudaEventDisableTiming);
+        }
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->start_ev, cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, LP_ERR_CUDA, "upload stream: %s", cudaGetErrorString(e));
+        }
+    }
+    cudaStream_t s = S(stream), cs = c->copy_stream;
+    c->last = s;
+    double* dH = (double*)c->buf[B_HSTREAM].p;
+    int32_t* dn = (int32_t*)(dH + 9 * (size_t)P);
+    void* slotA[2] = {c->buf[B_IMG_A].p, c->buf[B_IMG_A1].p};
+    void* slotB[2] = {c->buf[B_IMG_B].p, c->buf[B_IMG_B1].p};
+    // uploads start after the caller's earlier work on its stream
+    LP_CUDA(c, cudaEventRecord(c->start_ev, s));
+    LP_CUDA(c, cudaStreamWaitEvent(cs, c->start_ev, 0));
+    for (int q = 0; q < P; ++q) {
+        const lp_host_pair& h = pairs[q];
+        const int k = q & 1;
+        // slot k is free once pair q - 2 is done
+        if (q >= 2) LP_CUDA(c, cudaStreamWaitEvent(cs, c->free_ev[k], 0));
+        LP_CUDA(c, cudaMemcpyAsync(slotA[k], h.A, (size_t)h.HA * h.pitchA, cudaMemcpyHostToDevice, cs));
+        LP_CUDA(c, cudaMemcpyAsync(slotB[k], h.B, (size_t)h.HB * h.pitchB, cudaMemcpyHostToDevice, cs));
+        LP_CUDA(c, cudaEventRecord(c->up_ev[k], cs));
+        LP_CUDA(c, cudaStreamWaitEvent(s, c->up_ev[k], 0));
+        if ((r = stitch_pair_impl(c, (const uint8_t*)slotA[k], h.HA, h.WA, h.pitchA, (const uint8_t*)slotB[k], h.HB,
+                                  h.WB, h.pitchB, channels, pair_id0 + (uint32_t)q, dH + 9 * (size_t)q,
+                                  dn + 2 * (size_t)q, dn + 2 * (size_t)q + 1, stream, false)))
+            return r;
+        LP_CUDA(c, cudaEventRecord(c->free_ev[k], s));
+    }
+    std::vector<int32_t> tmp(2 * (size_t)P);
+    LP_CUDA(c, cudaMemcpyAsync(H_host, dH, 9 * sizeof(double) * (size_t)P, cudaMemcpyDeviceToHost, s));
+    LP_CUDA(c, cudaMemcpyAsync(tmp.data(), dn, 2 * sizeof(int32_t) * (size_t)P, cudaMemcpyDeviceToHost, s));
+    LP_CUDA(c, cudaStreamSynchronize(s));
+    for (int q = 0; q < P; ++q) {
+        n_in_host[q] = tmp[2 * (size_t)q];
+        if (M_host) M_host[q] = tmp[2 * (size_t)q + 1];
+    }
     return LP_OK;
 }
 

@@ -29,6 +29,11 @@ class LpError(RuntimeError):
         self.code = code
 
 
+class lp_host_pair(C.Structure):
+    _fields_ = [("A", C.c_void_p), ("B", C.c_void_p), ("HA", C.c_int32), ("WA", C.c_int32), ("pitchA", C.c_int32),
+                ("HB", C.c_int32), ("WB", C.c_int32), ("pitchB", C.c_int32)]
+
+
 class lp_image(C.Structure):
     _fields_ = [("data", C.c_void_p), ("H", C.c_int32), ("W", C.c_int32), ("pitch", C.c_int32),
                 ("channels", C.c_int32)]
@@ -45,7 +50,7 @@ class lp_config(C.Structure):
 _lib = None
 SYMBOLS = ["lp_config_default", "lp_create", "lp_destroy", "lp_num_keypoints", "lp_detect", "lp_detect_batch",
            "lp_describe",
-           "lp_match", "lp_compact", "lp_ransac", "lp_ransac_static", "lp_stitch_pair", "lp_stitch_pair_host", "lp_stitch_pairs", "lp_stitch_pairs_ids", "lp_sync_status",
+           "lp_match", "lp_compact", "lp_ransac", "lp_ransac_static", "lp_stitch_pair", "lp_stitch_pair_host", "lp_stitch_pairs_host", "lp_stitch_pairs", "lp_stitch_pairs_ids", "lp_sync_status",
            "lp_last_error", "lp_diag_last_rescans", "lp_diag_orient_bins", "lp_diag_orient_weights", "lp_diag_philox", "lp_diag_gray",
            "lp_mlp_create", "lp_mlp_destroy", "lp_mlp_set_params", "lp_mlp_get_params", "lp_mlp_get_state", "lp_mlp_save",
            "lp_mlp_load", "lp_mlp_features", "lp_mlp_forward", "lp_mlp_train_step", "lp_ransac_prior",
@@ -84,6 +89,7 @@ def load(build_if_missing: bool = True):
         "lp_ransac_static": (i32, [P, i64, P, i32, C.c_float, C.c_uint64, u32, P, P, P, P, P]),
         "lp_stitch_pair": (i32, [P, P, i32, i32, i32, P, i32, i32, i32, i32, u32, P, P, P, P]),
         "lp_stitch_pair_host": (i32, [P, P, i32, i32, i32, P, i32, i32, i32, i32, u32, P, P, P, P]),
+        "lp_stitch_pairs_host": (i32, [P, P, i32, i32, u32, P, P, P, P]),
         "lp_stitch_pairs": (i32, [P, P, i32, P, i32, P, P, P, P, P]),
         "lp_stitch_pairs_ids": (i32, [P, P, i32, P, P, i32, P, P, P, P, P]),
         "lp_sync_status": (i32, [P]),
@@ -232,6 +238,20 @@ class Context:
                                                pitchB, channels, pair_id, Hh, C.byref(n), C.byref(m),
                                                _stream(stream)), "lp_stitch_pair_host")
         return [list(Hh[0:3]), list(Hh[3:6]), list(Hh[6:9])], n.value, m.value
+
+    def lp_stitch_pairs_host(self, pairs, channels, pair_id0=0, stream=None):
+        """pairs: list of (A, HA, WA, pitchA, B, HB, WB, pitchB) with host (ideally
+        pinned) uint8 tensors.  Returns (H float64 array [P, 3, 3], n_in [P], M [P])."""
+        import numpy as np
+        P = len(pairs)
+        arr = (lp_host_pair * max(P, 1))(*[lp_host_pair(A.data_ptr(), B.data_ptr(), HA, WA, pa, HB, WB, pb)
+                                            for (A, HA, WA, pa, B, HB, WB, pb) in pairs])
+        Hh = np.zeros((max(P, 1), 3, 3), np.float64)
+        n = np.zeros(max(P, 1), np.int32)
+        m = np.zeros(max(P, 1), np.int32)
+        self._chk(self.lib.lp_stitch_pairs_host(self.h, arr, P, channels, pair_id0, Hh.ctypes.data, n.ctypes.data,
+                                                m.ctypes.data, _stream(stream)), "lp_stitch_pairs_host")
+        return Hh[:P], n[:P], m[:P]
 
     def lp_stitch_pairs(self, images, HM, n_in, valid, pairs=None, M_out=None, stream=None, pair_ids=None):
         """images: list of (device uint8 tensor, H, W, pitch, channels).  With

@@ -154,6 +154,43 @@ def test_host_buffer_pair_equals_device_pair(rgb):
 
 
 @pytest.mark.parametrize("rgb", [False, True])
+def test_host_stream_equals_host_pair_calls(rgb):
+    """lp_stitch_pairs_host (uploads of the next pair on a copy stream while
+    the current pair is computed, two alternating upload slots) gives every
+    pair exactly what lp_stitch_pair_host gives it, for pairs of different
+    sizes (slots reused, buffers grown), pageable or pinned host images, and
+    on a second call; P = 0 is a no-op and bad arguments are refused."""
+    ch = 3 if rgb else 1
+    ps = [synth.small_pair(240, 320, 1, theta_deg=3.0, shift=0.3, rgb=rgb),
+          synth.small_pair(300, 416, 2, theta_deg=-4.0, shift=0.25, rgb=rgb),
+          synth.small_pair(200, 272, 3, theta_deg=6.0, shift=0.3, rgb=rgb),
+          synth.small_pair(240, 320, 4, theta_deg=1.0, shift=0.35, rgb=rgb),
+          synth.small_pair(320, 480, 5, theta_deg=-2.0, shift=0.3, rgb=rgb)]
+    ctx = lp.Context(Ls=(8, 16, 32), precision=lp.PREC_BF16)
+    entries = []
+    for q, p in enumerate(ps):
+        a, pa = lp.pitched_device(p.A)
+        b, pb = lp.pitched_device(p.B)
+        h, w = p.A.shape[:2]
+        A, B = a.cpu(), b.cpu()
+        if q % 2:
+            A, B = A.pin_memory(), B.pin_memory()
+        entries.append((A, h, w, pa, B, h, w, pb))
+    want = [ctx.lp_stitch_pair_host(A, h, w, pa, B, h2, w2, pb, ch, 7 + q)
+            for q, (A, h, w, pa, B, h2, w2, pb) in enumerate(entries)]
+    for rep in range(2):
+        H, n, M = ctx.lp_stitch_pairs_host(entries, ch, pair_id0=7)
+        for q in range(len(ps)):
+            assert np.array_equal(H[q], np.array(want[q][0])) and n[q] == want[q][1] and M[q] == want[q][2], (rep, q)
+    assert int(n.min()) >= 8
+    H0, n0, M0 = ctx.lp_stitch_pairs_host([], ch)
+    assert len(n0) == 0
+    A, h, w, pa, B, h2, w2, pb = entries[0]
+    with pytest.raises(lp.LpError):
+        ctx.lp_stitch_pairs_host([(A, h, w, pa + 1, B, h2, w2, pb)], ch)
+
+
+@pytest.mark.parametrize("rgb", [False, True])
 def test_stitch_pairs_uneven_sizes_equal_single_pairs(rgb):
     """Images of different sizes in one batch (unequal point counts per pair):
     every H_M entry, inlier and match count equals the single-pair call's."""
