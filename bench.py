@@ -348,6 +348,35 @@ def fp32_form_and_batch(args, rank):
         t += a.elapsed_time(b) / 1e3
     out["fp32_form_pairs_per_s"] = k / t
     out["fp32_form_inliers"] = int(n.item())
+    H32 = H.clone()
+    del ctx
+    # the E4M3 form of the same pair: its pairs/s, the distance passes' time
+    # and rate against the FP8 dense peak (the measured BF16 peak x 2, the
+    # nominal ratio), the rows its filter could not certify, equality with FP32
+    ctx = lp.Context(Ls=LS, precision=lp.PREC_FP8)
+    ctx.lp_set_profiling(True)
+    for _ in range(2):
+        ctx.lp_stitch_pair(bA, H_IMG, W_IMG, pA, bB, H_IMG, W_IMG, pB, 3, rank, H, n, M)
+    torch.cuda.synchronize()
+    t, tk = 0.0, 0.0
+    for _ in range(k):
+        flush()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        ctx.lp_stitch_pair(bA, H_IMG, W_IMG, pA, bB, H_IMG, W_IMG, pB, 3, rank, H, n, M)
+        b.record(s)
+        torch.cuda.synchronize()
+        t += a.elapsed_time(b) / 1e3
+        tk += ctx.lp_diag_last_match_kernel_ms() / 1e3
+    Kp = lp.lp_num_keypoints(H_IMG, W_IMG, LS)
+    pk = peaks()[0]
+    out["fp8_form"] = {"pairs_per_s": k / t, "distance_passes_ms": 1e3 * tk / k,
+                       "distance_tflops_useful": 2.0 * Kp * Kp * 128 / (tk / k) / 1e12,
+                       "frac_of_fp8_peak": 2.0 * Kp * Kp * 128 / (tk / k) / 1e12 / (2 * pk["bf16_tflops"]),
+                       "fp8_peak_tflops": 2 * pk["bf16_tflops"], "fp8_peak_kind": "measured BF16 burst x 2 (nominal ratio)",
+                       "rescanned_rows": int(ctx.lp_diag_last_rescans()), "rows": int(Kp),
+                       "H_equals_fp32_form": bool(torch.equal(H, H32))}
+    ctx.lp_set_profiling(False)
     del ctx
     bt = synth.batch_3x3(seed=1)
     ctx = lp.Context(Ls=LS, precision=lp.PREC_BF16)
@@ -979,6 +1008,7 @@ def main():
         line["config"]["fp32_form_pairs_per_s"] = extra["fp32_form_pairs_per_s"]
         line["config"]["speedup_vs_fp32_form"] = value / world / extra["fp32_form_pairs_per_s"]
         line["config"]["fp32_form_inliers"] = extra["fp32_form_inliers"]
+        line["config"]["fp8_form"] = extra["fp8_form"]
         line["config"]["batch_3x3"] = extra["batch_3x3"]
         line["config"]["batch_3x3_fp32"] = extra["batch_3x3_fp32"]
         line["config"]["uneven_64"] = extra["uneven_64"]

@@ -56,7 +56,10 @@ typedef enum lp_status {
 
 typedef enum lp_precision {
     LP_PREC_FP32 = 0,        /* FP32 SIMT distances, exact top-2 */
-    LP_PREC_BF16 = 1         /* BF16 tcgen05 distances, top-k, FP32 re-rank */
+    LP_PREC_BF16 = 1,        /* BF16 tcgen05 distances, top-k, FP32 re-rank */
+    LP_PREC_FP8 = 2          /* E4M3 tcgen05 distances (descriptors x 2^8 rounded to E4M3 in the
+                                matcher's workspace), the same certified candidate filter with the
+                                E4M3 error bound, FP32 re-rank: results equal LP_PREC_FP32's */
 } lp_precision;
 
 /* Transform models of Sec. 2.5.  Eq. 7 maps points through a 3x3 homography
@@ -159,9 +162,10 @@ LP_API int lp_describe(lp_ctx* ctx, const uint8_t* gray, int H, int W, int gray_
  *  vA, vB           device uint8 validity
  *  match            device int32[NA]: j1 or -1
  *  d1, d2           device float[NA]: Delta1, Delta2 (FP32, +inf if none)
- * With LP_PREC_BF16 the tensor cores rank candidates, every candidate is
- * re-scored exactly in FP32 and rows whose ranking cannot be certified are
- * re-scanned in FP32, so the result is that of the FP32 form.
+ * With LP_PREC_BF16 or LP_PREC_FP8 the tensor cores rank candidates, every
+ * candidate is re-scored exactly in FP32 and rows whose ranking cannot be
+ * certified are re-scanned in FP32, so the result is that of the FP32 form.
+ * LP_PREC_FP8 converts dA and dB to E4M3 itself (the bf16 copies are unused).
  * Errors: LP_ERR_ARG, LP_ERR_ALIGN, LP_ERR_NOMEM, LP_ERR_CUDA. */
 LP_API int lp_match(lp_ctx* ctx, const float* dA, const uint16_t* dA_bf16, const uint8_t* vA, int64_t NA,
              const float* dB, const uint16_t* dB_bf16, const uint8_t* vB, int64_t NB,
@@ -468,8 +472,9 @@ LP_API const char* lp_last_error(lp_ctx* ctx);
 
 /* ---- diagnostics used by the test-suite (no paper counterpart needed) ---- */
 
-/* Rows that the last LP_PREC_BF16 lp_match of this context re-scanned in FP32
- * because their BF16 ranking could not be certified (waits for the stream). */
+/* Rows that the last LP_PREC_BF16 or LP_PREC_FP8 lp_match of this context
+ * re-scanned in FP32 because their tensor-core ranking could not be certified
+ * (waits for the stream). */
 LP_API int lp_diag_last_rescans(lp_ctx* ctx, int64_t* out);
 
 /* Attach a network to the context (NULL detaches it): lp_stitch_pair and
@@ -482,7 +487,7 @@ LP_API int lp_set_proposal(lp_ctx* ctx, lp_mlp* mlp, int32_t guided_iters);
 /* Kernel timing for benchmarks.  With profiling on, every lp_match call that
  * is not being captured into a CUDA graph records two CUDA events on its
  * stream, immediately before and after its distance kernel (the tensor-core
- * kernel of LP_PREC_BF16, the FP32 kernel of LP_PREC_FP32).
+ * passes of LP_PREC_BF16 and LP_PREC_FP8, the FP32 kernel of LP_PREC_FP32).
  * lp_diag_last_match_kernel_ms waits for the second event and returns the
  * elapsed milliseconds of the last such call.  Errors: LP_ERR_ARG (profiling
  * off, or no recorded call), LP_ERR_CUDA. */

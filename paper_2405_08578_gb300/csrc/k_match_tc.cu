@@ -50,6 +50,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 #include "lp_internal.cuh"
 
@@ -118,6 +119,39 @@ __host__ __device__ __forceinline__ float window_top(float x)
     const float r = 1.f + kNormEps - x;
     return x + kDeltaC + kDeltaK * (r > 0.f ? r : 0.f);
 }
+
+// The E4M3 form (LP_PREC_FP8).  Descriptors are scaled by kFp8Scale = 2^8 (a
+// unit descriptor's entries lie in [0, 1], so the largest becomes <= 256 <
+// 448, the E4M3 maximum) and rounded to E4M3; the accumulator then holds
+// 2^16 D.  E4M3 keeps 3 mantissa bits: u = 2^-4 for normal values, and an
+// absolute error of at most 2^-10 / kFp8Scale for the entries that fall in
+// its subnormal range.  So |v~ - v| <= kDeltaC8 + kDeltaK8 (1 + kNormEps - v)
+// with kDeltaK8 = 2u + u^2 and kDeltaC8 the BF16 allowance plus the
+// subnormal term, 2 (1 + u) (sum a + sum b) 2^-18 <= 2 * 2.2 * 11.4 * 2^-18.
+constexpr float kFp8Scale = 256.0f;
+constexpr float kFp8AccScale = 65536.0f;                  // kFp8Scale^2
+constexpr float kDeltaK8 = 2.0f / 16.0f + 1.0f / 256.0f;
+constexpr float kDeltaC8 = kDeltaC + 2.0e-4f;
+// margin of the certification point above m2 for the E4M3 form (its values
+// carry about 16 times the BF16 rounding error)
+constexpr float kMargin8 = 2.0e-2f;
+
+template <int kElem>
+__host__ __device__ __forceinline__ float window_top_e(float x)
+{
+    if (kElem == 0) return window_top(x);
+    const float r = 1.f + kNormEps - x;
+    return x + kDeltaC8 + kDeltaK8 * (r > 0.f ? r : 0.f);
+}
+
+// Operand sizes of one element type: BF16 rows are 256 bytes (two 128-byte
+// swizzle atoms, two TMA boxes), E4M3 rows 128 bytes (one of each).
+template <int kElem>
+struct Opnd {
+    static constexpr uint32_t kA = kRowsPerUnit * 128 * (kElem ? 1 : 2);
+    static constexpr uint32_t kB = kTileN * 128 * (kElem ? 1 : 2);
+    static constexpr int kBoxes = kElem ? 1 : 2;
+};
 
 // ------------------------------------------------------------------ PTX wrappers
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
@@ -227,6 +261,20 @@ __device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t a, uint64_t b,
         : "memory");
 }
 
+// Instruction descriptor, kind::f8f6f4: D = FP32, A = B = E4M3 (format 0),
+// both K-major, N = kTileN = 256, M = 128.
+constexpr uint32_t kIdesc8 = (1u << 4) | ((uint32_t)(kTileN >> 3) << 17) | ((uint32_t)(kRowsPerUnit >> 4) << 24);
+
+__device__ __forceinline__ void mma_e4m3(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.u32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}"
+        ::"r"(dtmem), "l"(a), "l"(b), "r"(kIdesc8), "r"(accumulate)
+        : "memory");
+}
+
 // Arrive on the mbarrier at `bar` when this thread's MMAs complete.
 __device__ __forceinline__ void mma_commit(uint32_t bar)
 {
@@ -300,15 +348,17 @@ __device__ __forceinline__ float max3f(float a, float b, float c)
     return r;
 }
 
-template <int kPass>
+template <int kPass, int kElem>
 __global__ void __launch_bounds__(kThreadsTC, 1)
 k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcParams p)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t* sA = smem;
-    uint8_t* sB = smem + kABytes;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(sB + kStages * kBBytes);
+    constexpr uint32_t kAB = Opnd<kElem>::kA, kBB = Opnd<kElem>::kB;
+    constexpr int kBoxes = Opnd<kElem>::kBoxes;
+    uint8_t* sB = smem + kAB;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sB + kStages * kBB);
     // barrier slots
     uint64_t* full = bars;                 // [kStages]
     uint64_t* empty = bars + kStages;      // [kStages]
@@ -372,9 +422,11 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
                 if (rb != prev_rb) {
                     ok = mbar_wait(smem_u32(aempty), (v & 1) ^ 1, abort_flag, p.status);
                     if (!ok) break;
-                    mbar_expect_tx(smem_u32(afull), kABytes);
-                    tma_load_2d(smem_u32(sA), &tmA, 0, rb * kRowsPerUnit, smem_u32(afull));
-                    tma_load_2d(smem_u32(sA + kABytes / 2), &tmA, 64, rb * kRowsPerUnit, smem_u32(afull));
+                    mbar_expect_tx(smem_u32(afull), kAB);
+#pragma unroll
+                    for (int h = 0; h < kBoxes; ++h)
+                        tma_load_2d(smem_u32(sA + h * (kAB / kBoxes)), &tmA, 64 * h, rb * kRowsPerUnit,
+                                    smem_u32(afull));
                     a_armed = v;
                     ++v;
                     prev_rb = rb;
@@ -384,11 +436,12 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
                     const uint32_t k = (uint32_t)(n / kStages);
                     ok = mbar_wait(smem_u32(&empty[s]), (k & 1) ^ 1, abort_flag, p.status);
                     if (!ok) break;
-                    uint8_t* dst = sB + s * kBBytes;
+                    uint8_t* dst = sB + s * kBB;
                     const int y = (int)(c0 + (long long)t * p.tstride * kTileN);
-                    mbar_expect_tx(smem_u32(&full[s]), kBBytes);
-                    tma_load_2d(smem_u32(dst), &tmB, 0, y, smem_u32(&full[s]));
-                    tma_load_2d(smem_u32(dst + kBBytes / 2), &tmB, 64, y, smem_u32(&full[s]));
+                    mbar_expect_tx(smem_u32(&full[s]), kBB);
+#pragma unroll
+                    for (int h = 0; h < kBoxes; ++h)
+                        tma_load_2d(smem_u32(dst + h * (kBB / kBoxes)), &tmB, 64 * h, y, smem_u32(&full[s]));
                     armed[s] = (int)k;
                 }
             }
@@ -443,15 +496,19 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
                     ok = mbar_wait(smem_u32(&full[s]), k & 1, abort_flag, p.status);
                     if (!ok) break;
                     tc_fence_after();
-                    const uint64_t dB = dB0 + (uint64_t)((s * kBBytes) >> 4);
+                    const uint64_t dB = dB0 + (uint64_t)((s * kBB) >> 4);
                     const uint32_t d = tmem + (uint32_t)(b * kTileN);
+                    // 32 bytes of K per MMA: K = 16 BF16 or K = 32 E4M3 values
 #pragma unroll
-                    for (int h = 0; h < 2; ++h)
+                    for (int h = 0; h < kBoxes; ++h)
 #pragma unroll
                         for (int kk = 0; kk < 4; ++kk) {
-                            const uint64_t ad = dA0 + (uint64_t)((h * (kABytes / 2) + kk * 32) >> 4);
-                            const uint64_t bd = dB + (uint64_t)((h * (kBBytes / 2) + kk * 32) >> 4);
-                            mma_bf16(d, ad, bd, (h | kk) ? 1u : 0u);
+                            const uint64_t ad = dA0 + (uint64_t)((h * (kAB / kBoxes) + kk * 32) >> 4);
+                            const uint64_t bd = dB + (uint64_t)((h * (kBB / kBoxes) + kk * 32) >> 4);
+                            if (kElem == 0)
+                                mma_bf16(d, ad, bd, (h | kk) ? 1u : 0u);
+                            else
+                                mma_e4m3(d, ad, bd, (h | kk) ? 1u : 0u);
                         }
                     mma_commit(smem_u32(&empty[s]));
                     mma_commit(smem_u32(&tfull[b]));
@@ -487,7 +544,12 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
             int32_t* const dst = p.cand + sub * kSubCap;
             float d1 = -INFINITY, d2 = -INFINITY;                                    // pass 1
             // pass 2: v~ = 1 - 2 D <= T  <=>  D >= (1 - T) / 2 (1e-6 lower: rounding of TD)
-            const float TD = (kPass == 2 && live) ? 0.5f * (1.f - window_top(p.thr[row])) - 1e-6f : INFINITY;
+            // (the E4M3 accumulator holds kFp8AccScale D: the threshold is scaled
+            // instead of every value, exactly, by a power of two)
+            const float TD = (kPass == 2 && live)
+                                 ? (0.5f * (1.f - window_top_e<kElem>(p.thr[row])) - 1e-6f) *
+                                       (kElem ? kFp8AccScale : 1.f)
+                                 : INFINITY;
             int nc = 0;
             for (int t = 0; t < ntiles; ++t, ++n) {
                 const int b = (int)(n % kTmemBufs);
@@ -522,7 +584,7 @@ k_match_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
                         gx[g] = max3f(max3f(dv[8 * g + 0], dv[8 * g + 1], dv[8 * g + 2]),
                                       max3f(dv[8 * g + 3], dv[8 * g + 4], dv[8 * g + 5]),
                                       fmaxf(dv[8 * g + 6], dv[8 * g + 7]));
-                    const float cmax = max3f(gx[0], gx[1], fmaxf(gx[2], gx[3]));
+                    const float cmax = max3f(gx[0], gx[1], fmaxf(gx[2], gx[3])) * (kElem && kPass == 1 ? 1.f / kFp8AccScale : 1.f);
                     if (kPass == 1) {
                         const float lo = fminf(d1, cmax);
                         d1 = fmaxf(d1, cmax);
@@ -986,7 +1048,7 @@ __device__ __forceinline__ void warp_top2(float& b1, int& j1, float& b2, int& j2
 // Per row, the certification point x = m2 + kMargin (m2 the second smallest
 // pass-1 value; capped for rows with fewer than two sampled columns), -inf for
 // an invalid query row.
-__global__ void k_row_threshold(const float2* pm, int S, long long NA, const uint8_t* vA, float* thr)
+__global__ void k_row_threshold(const float2* pm, int S, long long NA, const uint8_t* vA, float* thr, float margin)
 {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= NA) return;
@@ -997,7 +1059,7 @@ __global__ void k_row_threshold(const float2* pm, int S, long long NA, const uin
         m2 = fminf(fminf(m2, hi), fmaxf(m1, lo));
         m1 = fminf(m1, lo);
     }
-    thr[i] = vA[i] ? fminf(m2 + kMargin, kCandCap) : -INFINITY;
+    thr[i] = vA[i] ? fminf(m2 + margin, kCandCap) : -INFINITY;
 }
 
 // One warp per row: every candidate of the row's kRanges S sub-lists is re-scored
@@ -1204,10 +1266,32 @@ __global__ void k_rescan_merge(const float4* part_r, long long NA, long long NB,
     }
 }
 
+// E4M3 operands of the FP8 form: each entry times kFp8Scale, rounded to
+// nearest E4M3 (saturating; unit descriptors stay below 256 < 448).  One
+// thread converts four consecutive entries; invalid rows become zero.
+__global__ void k_to_e4m3(const float* d, const uint8_t* v, long long n, uint8_t* out)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n * 32) return;
+    const float4 x = reinterpret_cast<const float4*>(d)[t];
+    const __nv_fp8x2_storage_t lo =
+        __nv_cvt_float2_to_fp8x2(make_float2(x.x * kFp8Scale, x.y * kFp8Scale), __NV_SATFINITE, __NV_E4M3);
+    const __nv_fp8x2_storage_t hi =
+        __nv_cvt_float2_to_fp8x2(make_float2(x.z * kFp8Scale, x.w * kFp8Scale), __NV_SATFINITE, __NV_E4M3);
+    reinterpret_cast<uint32_t*>(out)[t] = v[t >> 5] ? ((uint32_t)lo | ((uint32_t)hi << 16)) : 0u;
+}
+
 // ------------------------------------------------------------------ host side
 bool make_map(CUtensorMap* m, const void* base, long long rows, uint32_t box_rows)
 {
     return encode_tiled_2d(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, base, 128, (uint64_t)rows, 256, 64, box_rows,
+                           CU_TENSOR_MAP_SWIZZLE_128B);
+}
+
+// E4M3 rows: 128 one-byte entries, one 128-byte box per row
+bool make_map8(CUtensorMap* m, const void* base, long long rows, uint32_t box_rows)
+{
+    return encode_tiled_2d(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, base, 128, (uint64_t)rows, 128, 128, box_rows,
                            CU_TENSOR_MAP_SWIZZLE_128B);
 }
 
@@ -1403,7 +1487,13 @@ bool encode_tiled_2d(CUtensorMap* m, CUtensorMapDataType dt, const void* base, u
               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-size_t match_bf16_workspace(int64_t NA, int64_t NB, int num_sms, int S) { return tc_layout(NA, NB, num_sms, S).total; }
+// The E4M3 form keeps its operand copies after the shared layout (whose offsets
+// match_bf16_rescans recomputes).
+size_t match_bf16_workspace(int64_t NA, int64_t NB, int num_sms, int S, int elem)
+{
+    const size_t t = tc_layout(NA, NB, num_sms, S).total;
+    return elem ? t + (((size_t)NA * 128 + 255) & ~size_t(255)) + (size_t)NB * 128 + 256 : t;
+}
 
 int match_bf16_default_splits(int64_t NA, int64_t NB, int num_sms) { return tc_layout(NA, NB, num_sms).S; }
 
@@ -1418,11 +1508,34 @@ int64_t match_bf16_rescans(const void* ws, int64_t NA, int64_t NB, int num_sms, 
     return c;
 }
 
+template <int kElem>
+cudaError_t launch_tc_passes(const CUtensorMap& tA, const CUtensorMap& tB, const TcParams& p, const TcParams& p1,
+                             int U, int num_sms, cudaStream_t s, const float2* pm, int nsub, long long NA,
+                             const uint8_t* vA, float* thr)
+{
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_match_tc<1, kElem>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTC)) !=
+            cudaSuccess ||
+        (e = cudaFuncSetAttribute(k_match_tc<2, kElem>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTC)) !=
+            cudaSuccess)
+        return e;
+    int per_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_match_tc<1, kElem>, kThreadsTC, kSmemTC)) !=
+        cudaSuccess)
+        return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const dim3 grid((unsigned)std::min(U, per_sm * num_sms));
+    k_match_tc<1, kElem><<<grid, kThreadsTC, kSmemTC, s>>>(tA, tB, p1);
+    k_row_threshold<<<(unsigned)((NA + 255) / 256), 256, 0, s>>>(pm, nsub, NA, vA, thr, kElem ? kMargin8 : kMargin);
+    k_match_tc<2, kElem><<<grid, kThreadsTC, kSmemTC, s>>>(tA, tB, p);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_match_bf16(const MatchArgs& a, void* ws, size_t ws_bytes, int num_sms, cudaStream_t s)
 {
     if (a.NA == 0) return cudaSuccess;
     const TcLayout L = tc_layout(a.NA, a.NB, num_sms, a.splits);
-    if (ws_bytes < L.total) return cudaErrorInvalidValue;
+    if (ws_bytes < match_bf16_workspace(a.NA, a.NB, num_sms, a.splits, a.elem)) return cudaErrorInvalidValue;
     uint8_t* w = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(ws) + 255) & ~uintptr_t(255));
     float* na = reinterpret_cast<float*>(w + L.off_na);
     float* nb32 = reinterpret_cast<float*>(w + L.off_nb32);
@@ -1453,8 +1566,17 @@ cudaError_t launch_match_bf16(const MatchArgs& a, void* ws, size_t ws_bytes, int
                                                                                                  nb32, INFINITY);
         if (forked && (e = cudaEventRecord(a.fork->join_ev[1], a.fork->aux[1])) != cudaSuccess) return e;
         CUtensorMap tA, tB;
-        if (!make_map(&tA, a.dA16, a.NA, kRowsPerUnit) || !make_map(&tB, a.dB16, a.NB, kTileN))
+        if (a.elem) {
+            // E4M3 copies of both operands, after the shared layout
+            uint8_t* a8 = w + L.total;
+            uint8_t* b8 = a8 + (((size_t)a.NA * 128 + 255) & ~size_t(255));
+            k_to_e4m3<<<(unsigned)((a.NA * 32 + 255) / 256), 256, 0, s>>>(a.dA, a.vA, a.NA, a8);
+            k_to_e4m3<<<(unsigned)((a.NB * 32 + 255) / 256), 256, 0, s>>>(a.dB, a.vB, a.NB, b8);
+            if (!make_map8(&tA, a8, a.NA, kRowsPerUnit) || !make_map8(&tB, b8, a.NB, kTileN))
+                return cudaErrorInvalidValue;
+        } else if (!make_map(&tA, a.dA16, a.NA, kRowsPerUnit) || !make_map(&tB, a.dB16, a.NB, kTileN)) {
             return cudaErrorInvalidValue;
+        }
         TcParams p;
         p.NA = a.NA;
         p.NB = a.NB;
@@ -1469,23 +1591,12 @@ cudaError_t launch_match_bf16(const MatchArgs& a, void* ws, size_t ws_bytes, int
         p.tstride = 1;
         p.status = a.status;
         const int U = p.nrb * p.S;
-        if ((e = cudaFuncSetAttribute(k_match_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTC)) !=
-                cudaSuccess ||
-            (e = cudaFuncSetAttribute(k_match_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTC)) !=
-                cudaSuccess)
-            return e;
-        int per_sm = 0;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_match_tc<1>, kThreadsTC, kSmemTC)) !=
-            cudaSuccess)
-            return e;
-        if (per_sm < 1) return cudaErrorInvalidConfiguration;
-        const dim3 grid((unsigned)std::min(U, per_sm * num_sms));
         if (a.ev0) cudaEventRecord(a.ev0, s);
         TcParams p1 = p;
         p1.tstride = a.pass1_stride > 0 ? a.pass1_stride : kPass1Stride;
-        k_match_tc<1><<<grid, kThreadsTC, kSmemTC, s>>>(tA, tB, p1);
-        k_row_threshold<<<(unsigned)((a.NA + 255) / 256), 256, 0, s>>>(pm, kRanges * L.S, a.NA, a.vA, thr);
-        k_match_tc<2><<<grid, kThreadsTC, kSmemTC, s>>>(tA, tB, p);
+        e = a.elem ? launch_tc_passes<1>(tA, tB, p, p1, U, num_sms, s, pm, kRanges * L.S, a.NA, a.vA, thr)
+                   : launch_tc_passes<0>(tA, tB, p, p1, U, num_sms, s, pm, kRanges * L.S, a.NA, a.vA, thr);
+        if (e != cudaSuccess) return e;
         if (a.ev1) cudaEventRecord(a.ev1, s);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if (forked && ((e = cudaStreamWaitEvent(s, a.fork->join_ev[1], 0)) != cudaSuccess ||

@@ -172,7 +172,7 @@ int check_cfg(lp_ctx* c, const lp_config* cfg)
     if (cfg->hard_bins != 0 && cfg->hard_bins != 1) return fail(c, LP_ERR_ARG, "hard_bins must be 0 or 1");
     if (cfg->ransac_iters < 1 || cfg->ransac_iters > 65536) return fail(c, LP_ERR_ARG, "ransac_iters outside 1..65536");
     if (!(cfg->thresh_px > 0.f)) return fail(c, LP_ERR_ARG, "thresh_px must be > 0");
-    if (cfg->precision != LP_PREC_FP32 && cfg->precision != LP_PREC_BF16)
+    if (cfg->precision != LP_PREC_FP32 && cfg->precision != LP_PREC_BF16 && cfg->precision != LP_PREC_FP8)
         return fail(c, LP_ERR_ARG, "unknown precision %d", cfg->precision);
     if (cfg->model != LP_MODEL_HOMOGRAPHY && cfg->model != LP_MODEL_RIGID)
         return fail(c, LP_ERR_ARG, "unknown model %d", cfg->model);
@@ -436,7 +436,7 @@ int tune_match(lp_ctx* c, lp::MatchArgs& a, cudaStream_t s)
     std::sort(cand.begin() + 1, cand.end());
     cand.erase(std::unique(cand.begin() + 1, cand.end()), cand.end());
     size_t ws = 0;
-    for (const auto& q : cand) ws = std::max(ws, lp::match_bf16_workspace(a.NA, a.NB, c->num_sms, q.first));
+    for (const auto& q : cand) ws = std::max(ws, lp::match_bf16_workspace(a.NA, a.NB, c->num_sms, q.first, a.elem));
     int r = ensure(c, B_MATCH_WS, ws);
     if (r) return r;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -514,14 +514,18 @@ int lp_match(lp_ctx* c, const float* dA, const uint16_t* dA_bf16, const uint8_t*
             c->prof_recorded = true;
         }
     }
-    if (c->cfg.precision == LP_PREC_BF16) {
-        if (!dA_bf16 || (NB > 0 && !dB_bf16)) return fail(c, LP_ERR_ARG, "BF16 matching needs the bf16 descriptors");
-        if (!aligned(dA_bf16, 16) || (dB_bf16 && !aligned(dB_bf16, 16))) return fail(c, LP_ERR_ALIGN, "bf16 alignment");
+    if (c->cfg.precision == LP_PREC_BF16 || c->cfg.precision == LP_PREC_FP8) {
+        const int f8 = c->cfg.precision == LP_PREC_FP8;
+        if (!f8 && (!dA_bf16 || (NB > 0 && !dB_bf16)))
+            return fail(c, LP_ERR_ARG, "BF16 matching needs the bf16 descriptors");
+        if (!f8 && (!aligned(dA_bf16, 16) || (dB_bf16 && !aligned(dB_bf16, 16))))
+            return fail(c, LP_ERR_ALIGN, "bf16 alignment");
+        a.elem = f8;
         int r;
         if ((r = ensure_fork(c))) return r;
         a.fork = &c->fork;
         if (c->autotune && NB > 0 && (r = tune_match(c, a, S(stream)))) return r;
-        r = ensure(c, B_MATCH_WS, lp::match_bf16_workspace(NA, NB, c->num_sms, a.splits));
+        r = ensure(c, B_MATCH_WS, lp::match_bf16_workspace(NA, NB, c->num_sms, a.splits, a.elem));
         if (r) return r;
         c->last_S = a.splits;
         c->last_NA = NA;
@@ -895,7 +899,9 @@ int lp_stitch_pairs_ids(lp_ctx* c, const lp_image* imgs, int N, const int32_t* p
     size_t mws = 0;
     for (int q = 0; q < P; ++q) {
         const int64_t KA = ib[pl[2 * q]].K, KB = ib[pl[2 * q + 1]].K;
-        if (!bf) mws = std::max(mws, lp::match_fp32_workspace(KA, KB, c->num_sms));
+        if (!bf)
+            mws = std::max(mws, c->cfg.precision == LP_PREC_FP8 ? lp::match_bf16_workspace(KA, KB, c->num_sms, 0, 1)
+                                                                 : lp::match_fp32_workspace(KA, KB, c->num_sms));
     }
     if ((r = ensure(c, B_MATCH_WS, std::max<size_t>(mws, 256))) ||
         (r = ensure(c, B_COMPACT, lp::compact_workspace(Kmax))))
@@ -1234,7 +1240,9 @@ int lp_diag_last_rescans(lp_ctx* c, int64_t* out)
 {
     if (!c || !out) return LP_ERR_ARG;
     *out = 0;
-    if (c->cfg.precision != LP_PREC_BF16 || !c->buf[B_MATCH_WS].p || c->last_NA == 0) return LP_OK;
+    if ((c->cfg.precision != LP_PREC_BF16 && c->cfg.precision != LP_PREC_FP8) || !c->buf[B_MATCH_WS].p ||
+        c->last_NA == 0)
+        return LP_OK;
     *out = lp::match_bf16_rescans(c->buf[B_MATCH_WS].p, c->last_NA, c->last_NB, c->num_sms, c->last_S, c->last);
     return *out < 0 ? LP_ERR_CUDA : LP_OK;
 }

@@ -85,11 +85,13 @@ struct MatchArgs {
     int pass1_stride = 0;                       // BF16 form: pass-1 tile stride (0: the built-in 3)
     const float* normA = nullptr;               // batched BF16 form: row norms of A and of B (+inf for
     const float* normB = nullptr;               //   invalid rows), computed once per image
+    int elem = 0;                               // tensor-core operands: 0 BF16 (dA16, dB16), 1 E4M3
+                                                //   (converted from dA, dB into the workspace)
 };
 size_t match_fp32_workspace(int64_t NA, int64_t NB, int num_sms);
 cudaError_t launch_match_fp32(const MatchArgs& a, void* ws, size_t ws_bytes, int num_sms, cudaStream_t s);
 // S: column splits (0: the built-in choice, match_bf16_default_splits)
-size_t match_bf16_workspace(int64_t NA, int64_t NB, int num_sms, int S = 0);
+size_t match_bf16_workspace(int64_t NA, int64_t NB, int num_sms, int S = 0, int elem = 0);
 int match_bf16_default_splits(int64_t NA, int64_t NB, int num_sms);
 cudaError_t launch_match_bf16(const MatchArgs& a, void* ws, size_t ws_bytes, int num_sms, cudaStream_t s);
 // Batched BF16 form: the distance passes of P pairs in persistent launches of

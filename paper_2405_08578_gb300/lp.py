@@ -18,7 +18,7 @@ from . import build as _build
 LP_OK = 0
 ERR_NAMES = {0: "LP_OK", 1: "LP_ERR_ARG", 2: "LP_ERR_ALIGN", 3: "LP_ERR_CUDA", 4: "LP_ERR_TIMEOUT",
              5: "LP_ERR_NOMEM", 6: "LP_ERR_DEGENERATE", 7: "LP_ERR_UNSUPPORTED", 8: "LP_ERR_DEVICE"}
-PREC_FP32, PREC_BF16 = 0, 1
+PREC_FP32, PREC_BF16, PREC_FP8 = 0, 1, 2
 MODEL_HOMOGRAPHY, MODEL_RIGID = 0, 1   # Sec. 2.5: Eq. 7 homography, Eq. 8 rigid
 MAX_SCALES = 8
 

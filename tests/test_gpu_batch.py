@@ -22,7 +22,7 @@ def _outputs(P):
             torch.zeros(P, dtype=torch.uint8, device="cuda"), torch.zeros(P, dtype=torch.int32, device="cuda"))
 
 
-@pytest.mark.parametrize("precision", [lp.PREC_FP32, lp.PREC_BF16])
+@pytest.mark.parametrize("precision", [lp.PREC_FP32, lp.PREC_BF16, lp.PREC_FP8])
 def test_stitch_pairs_equals_single_pair_path(precision):
     h, w = 240, 320
     base = synth.small_pair(h, w, seed=21, theta_deg=3.0, scale=1.02, shift=0.25)

@@ -198,7 +198,7 @@ def _unit(rng, n):
     return d / np.linalg.norm(d, axis=1, keepdims=True)
 
 
-@pytest.mark.parametrize("precision", [lp.PREC_FP32, lp.PREC_BF16])
+@pytest.mark.parametrize("precision", [lp.PREC_FP32, lp.PREC_BF16, lp.PREC_FP8])
 @pytest.mark.parametrize("NA,NB", [(1, 2), (130, 1), (300, 517), (1000, 777), (2049, 4099), (257, 129)])
 def test_match_synthetic(NA, NB, precision):
     rng = np.random.default_rng(NA + NB)
@@ -231,10 +231,11 @@ def _same(a, b):
     return np.array_equal(a, b, equal_nan=True)
 
 
+@pytest.mark.parametrize("low", [lp.PREC_BF16, lp.PREC_FP8])
 @pytest.mark.parametrize("NA,NB", [(5, 7), (700, 1300), (5000, 4500)])
-def test_match_bf16_bitidentical_to_fp32(NA, NB):
-    # the BF16 form re-ranks exactly with the FP32 form's arithmetic: identical
-    # outputs, bit for bit, on every row
+def test_match_bf16_bitidentical_to_fp32(NA, NB, low):
+    # the BF16 and E4M3 forms re-rank exactly with the FP32 form's arithmetic:
+    # identical outputs, bit for bit, on every row
     rng = np.random.default_rng(NA * 3 + NB)
     A = _unit(rng, NA)
     B = _unit(rng, NB)
@@ -244,22 +245,57 @@ def test_match_bf16_bitidentical_to_fp32(NA, NB):
     vA = (rng.uniform(size=NA) > 0.03).astype(np.uint8)
     vB = (rng.uniform(size=NB) > 0.03).astype(np.uint8)
     r32 = G.match(ctx_for((16,), precision=lp.PREC_FP32), A, vA, B, vB)
-    r16 = G.match(ctx_for((16,), precision=lp.PREC_BF16), A, vA, B, vB)
+    r16 = G.match(ctx_for((16,), precision=low), A, vA, B, vB)
     for x, y in zip(r32, r16):
         assert _same(x, y)
 
 
+def test_match_fp8_tensor_values_certify_exact_inputs():
+    """E4M3 operands whose values are exact (four entries of 1/2 per unit
+    descriptor: x 2^8 = 128, an E4M3 number): the tensor-core values equal the
+    exact ones, the certified filter keeps a few columns per row, so nearly
+    every row is decided by the E4M3 passes and the FP32 re-rank of their
+    candidates, not by the FP32 re-scan -- and the outputs equal the FP32
+    form's bit for bit (ties included)."""
+    rng = np.random.default_rng(17)
+    N = 6000
+
+    def sparse(n):
+        d = np.zeros((n, 128), np.float32)
+        for i in range(n):
+            d[i, rng.choice(128, 4, replace=False)] = 0.5
+        return d
+    A = sparse(N)
+    B = sparse(N)
+    B[: N // 2] = A[: N // 2]                   # exact duplicates for half the rows
+    vA = np.ones(N, np.uint8)
+    vB = np.ones(N, np.uint8)
+    r32 = G.match(ctx_for((16,), precision=lp.PREC_FP32), A, vA, B, vB)
+    c8 = ctx_for((16,), precision=lp.PREC_FP8)
+    r8 = G.match(c8, A, vA, B, vB)
+    for x, y in zip(r32, r8):
+        assert _same(x, y)
+    assert c8.lp_diag_last_rescans() < N // 20
+    assert (r8[0] >= 0).sum() > N // 4
+
+
 def test_match_bf16_bitidentical_2688x1600():
+    """BF16 and E4M3 forms on the 2688x1600 pair: every output equals the FP32
+    form's bit for bit.  The E4M3 filter's error bound (u = 2^-4) is 16 times
+    the BF16 one, so many more of its rows fall back to the FP32 re-scan."""
     p = synth.pair_2688x1600(0)
-    out = {}
-    for prec in (lp.PREC_FP32, lp.PREC_BF16):
+    out, rescans = {}, {}
+    for prec in (lp.PREC_FP32, lp.PREC_BF16, lp.PREC_FP8):
         ctx = ctx_for(synth.PAIR_2688x1600_LS, precision=prec)
         fa = lp.features(ctx, p.A)
         fb = lp.features(ctx, p.B)
         out[prec] = [G.host(t) for t in lp.match(ctx, fa, fb)]
-    for x, y in zip(out[lp.PREC_FP32], out[lp.PREC_BF16]):
-        assert _same(x, y)
+        rescans[prec] = ctx.lp_diag_last_rescans()
+    for low in (lp.PREC_BF16, lp.PREC_FP8):
+        for x, y in zip(out[lp.PREC_FP32], out[low]):
+            assert _same(x, y), low
     assert (out[lp.PREC_BF16][0] >= 0).sum() > 500
+    assert rescans[lp.PREC_FP8] > rescans[lp.PREC_BF16]
 
 
 def test_match_edge_cases():
