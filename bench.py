@@ -640,9 +640,24 @@ def describe_rate(flush, k=10):
     for L in LS:
         w = max(1, int(math.floor(beta0 * math.sqrt(L * max(LS)) + 0.5)))
         samples += 2 * (H_IMG // L) * (W_IMG // L) * ((4 * w + 1) ** 2 + (4 * w + 2) ** 2 + 16 * w * w)
+    # the describe stage's work model: 16 w_s^2 descriptor samples per point
+    # (4 w_s x 4 w_s region, Eq. 3-4) at about 70 FP32 operations each
+    # (bilinear taps, gradient, direction, magnitude, binning); peak: 152 SMs x
+    # 128 FP32 lanes x 2 (FMA) x the maximum SM clock
+    desc_samples = 0
+    for L in LS:
+        w = max(1, int(math.floor(beta0 * math.sqrt(L * max(LS)) + 0.5)))
+        desc_samples += 2 * (H_IMG // L) * (W_IMG // L) * 16 * w * w
+    pk = peaks()[0]
+    alu_peak = 152 * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    achieved = desc_samples * 70 / (ms * 1e-3) / 1e12
     return {"ms_per_image": ms, "points_per_image": int(K), "samples_per_image": samples,
             "samples_per_ns": samples / (ms * 1e6),
-            "bound": "SM issue (77% of cycles issuing, no pipe saturated; profiles/k_describe_pair_2688x1600.md)"}
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                         "frac": achieved / alu_peak, "work": f"{desc_samples} descriptor samples x 70 FP32 operations",
+                         "note": "the kernels are bound by instruction issue (77% of cycles issuing, no pipe saturated; "
+                                 "profiles/k_describe_pair_2688x1600.md): most of their work is integer, table and "
+                                 "shared-memory work that this FP32 operation count leaves out"}}
 
 
 def fp8_census(chunk=4096, margin=5e-3, capacity=192):
