@@ -57,11 +57,29 @@ __device__ __forceinline__ uint8_t byte_of(const uint4& v, int i)
     return (uint8_t)(w >> (8 * (i & 3)));
 }
 
+// The division by 1000 on the FP32 pipes.  The dot products start from
+// kS0 = 0x4B000000 + 500, so v = 0x4B000000 + s with s = 299 R + 587 G + 114 B
+// + 500 < 2^18: as a float, v is 2^23 + s exactly, and f = v - 2^23 = s.  Then
+// fma_rz(f, 0.001f, 2^23) = 2^23 + floor(s * 0.001f): in [2^23, 2^24) the float
+// spacing is 1 and round-toward-zero keeps the integer part.  0.001f exceeds
+// 1/1000 by less than 4.8e-11, so s * 0.001f stays below the next integer for
+// every s < 255,501 that is not a multiple of 1000 (the fraction is then at
+// most 0.999, the excess at most 1.2e-5), and floor(s * 0.001f) = floor(s /
+// 1000) for every such s (checked for all of them).  The result's low byte is
+// the intensity.
+constexpr uint32_t kS0 = 0x4B000000u + 500u;
+__device__ __forceinline__ uint32_t fdiv1000(uint32_t v)
+{
+    const float f = __int_as_float((int)v) - 8388608.0f;
+    return (uint32_t)__float_as_int(__fmaf_rz(f, 0.001f, 8388608.0f));
+}
+
 // 16 interleaved RGB pixels (48 bytes, 12 words) -> 16 intensities.
 // 299 R + 587 G + 114 B + 500 is formed exactly with two dot products of
 // 16-bit weights with byte pairs (dp2a), taken straight from the interleaved
 // words: pixel 4g + j's bytes sit at byte offsets 3j .. 3j + 2 of words
 // 3g .. 3g + 2, so each pixel needs one or two words and no byte gathering.
+// The division by 1000 runs on the FP32 pipes (fdiv1000).
 __device__ __forceinline__ uint4 gray16(const uint4& c0, const uint4& c1, const uint4& c2)
 {
     const uint32_t w[12] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w, c2.x, c2.y, c2.z, c2.w};
@@ -71,10 +89,10 @@ __device__ __forceinline__ uint4 gray16(const uint4& c0, const uint4& c1, const 
 #pragma unroll
     for (int g = 0; g < 4; ++g) {
         const uint32_t a = w[3 * g], b = w[3 * g + 1], c = w[3 * g + 2];
-        q[4 * g] = div1000(__dp2a_hi(kB_, a, __dp2a_lo(kRG, a, 500u)));          // a: R G B .
-        q[4 * g + 1] = div1000(__dp2a_lo(kGB, b, __dp2a_hi(k_R, a, 500u)));      // a: . . . R  b: G B . .
-        q[4 * g + 2] = div1000(__dp2a_lo(kB_, c, __dp2a_hi(kRG, b, 500u)));      // b: . . R G  c: B . . .
-        q[4 * g + 3] = div1000(__dp2a_hi(kGB, c, __dp2a_lo(k_R, c, 500u)));      // c: . R G B
+        q[4 * g] = fdiv1000(__dp2a_hi(kB_, a, __dp2a_lo(kRG, a, kS0)));
+        q[4 * g + 1] = fdiv1000(__dp2a_lo(kGB, b, __dp2a_hi(k_R, a, kS0)));
+        q[4 * g + 2] = fdiv1000(__dp2a_lo(kB_, c, __dp2a_hi(kRG, b, kS0)));
+        q[4 * g + 3] = fdiv1000(__dp2a_hi(kGB, c, __dp2a_lo(k_R, c, kS0)));
     }
     // four intensities (each < 256) per word: bytes (q0, q1, q2, q3)
     uint32_t o[4];
@@ -100,23 +118,26 @@ __device__ __forceinline__ uint32_t min_u16x2(uint32_t a, uint32_t b)
 }
 
 // Extreme keys of 16 consecutive pixels of one row (raster index of the first:
-// base).  Within the group, (intensity << 4) | position orders pixels exactly
-// as the key does, and two such 12-bit values share a word, so the maximum
-// and minimum run as packed 16-bit pairs.
+// base).  Within the group, (intensity << 8) | position orders pixels exactly
+// as the key does; one byte permutation builds two such 16-bit values (the
+// intensity bytes next to position bytes), so the maximum and minimum run as
+// packed 16-bit pairs.
 __device__ __forceinline__ void group_keys(const uint4& v, uint32_t base, uint32_t& kmax, uint32_t& kmin)
 {
     const uint32_t w[4] = {v.x, v.y, v.z, v.w};
     uint32_t mx = 0u, mn = 0xFFFFFFFFu;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        const uint32_t lo = __byte_perm(w[k], 0u, 0x4140u) * 16u + ((4u * k) | ((4u * k + 1u) << 16));
-        const uint32_t hi = __byte_perm(w[k], 0u, 0x4342u) * 16u + ((4u * k + 2u) | ((4u * k + 3u) << 16));
+        // positions 4k .. 4k + 3 in bytes 0 .. 3
+        const uint32_t pos = (4u * k) | ((4u * k + 1u) << 8) | ((4u * k + 2u) << 16) | ((4u * k + 3u) << 24);
+        const uint32_t lo = __byte_perm(w[k], pos, 0x1504u);   // (b0 << 8 | 4k, b1 << 8 | 4k + 1)
+        const uint32_t hi = __byte_perm(w[k], pos, 0x3726u);   // (b2 << 8 | 4k + 2, b3 << 8 | 4k + 3)
         mx = max_u16x2(mx, max_u16x2(lo, hi));
         mn = min_u16x2(mn, min_u16x2(lo, hi));
     }
     const uint32_t M = max(mx & 0xFFFFu, mx >> 16), m = min(mn & 0xFFFFu, mn >> 16);
-    kmax = ((M >> 4) << 24) | (base + (M & 15u));
-    kmin = ((m >> 4) << 24) | (base + (m & 15u));
+    kmax = ((M >> 8) << 24) | (base + (M & 15u));
+    kmin = ((m >> 8) << 24) | (base + (m & 15u));
 }
 
 // One TS x TS tile (tile column bx, tile row by) of one image.
