@@ -922,9 +922,11 @@ cudaError_t launch_describe(const uint8_t* gray, int H, int W, int pitch, const 
     p.lut_w = reinterpret_cast<const uint32_t*>(luts);
     p.lut_bin = reinterpret_cast<const uint8_t*>(luts) + (((size_t)kLutWeights * 4 + 255) & ~size_t(255));
     p.ori = ori; p.desc = desc; p.desc16 = reinterpret_cast<__nv_bfloat16*>(desc_bf16); p.valid = valid;
-    // Scales with w_s <= 15 run in launches of consecutive scales whose
-    // per-warp shared memory fits kSmallWarpBytes (high occupancy), every larger
-    // footprint in a launch of its own; larger footprints are launched first.
+    // Scales with w_s <= 15 whose per-warp shared memory fits kSmallWarpBytes
+    // run one warp per point, each scale in a launch sized for its own
+    // footprint (the smallest scale, with most of the points, gets the highest
+    // occupancy); every larger footprint runs one CTA per point.  Larger
+    // footprints are launched first.
     // Scales with w_s > 15 take the split path (many CTAs per point), or the
     // global-memory kernel when a cell's grid does not fit shared memory.
     int m = 0;
@@ -989,8 +991,8 @@ cudaError_t launch_describe(const uint8_t* gray, int H, int W, int pitch, const 
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    if (first_big > 0) {
-        cudaError_t e = launch_group(0, first_big);
+    for (int l = first_big - 1; l >= 0; --l) {
+        cudaError_t e = launch_group(l, l + 1);
         if (e != cudaSuccess) return e;
     }
     for (int l = m; l < st.nL; ++l) {
