@@ -7,10 +7,11 @@
 // 1) from the L2-resident intensity image into shared memory once.
 //
 // Orientation (integer, exact): 36-bin histogram over the upright
-// (4 w_s + 1)^2 window of Eq. 5 gradients.  Bin and weight come from two
-// tables that tabulate the exact functions below (10-degree sector of
-// atan2(b, a); round(65536*sqrt(a^2+b^2)) by integer square root), built once
-// per context on the device.  Each weight (< 2^25) is added to two 32-bit
+// (4 w_s + 1)^2 window of Eq. 5 gradients.  Bin and weight come from one
+// table word per gradient (a, b) that tabulates the exact functions below
+// (10-degree sector of atan2(b, a) in bits 25..30; round(65536*sqrt(a^2+b^2))
+// by integer square root in bits 0..24), built once per context on the
+// device: one gather per sample.  Each weight (< 2^25) is added to two 32-bit
 // shared counters per bin, its low 16 and its high 9 bits (for w_s <= 15 at
 // most 61^2 samples: no overflow), recombined in 64 bits; the argmax (lowest
 // bin on ties) is therefore exact.  Larger scales take a global-memory kernel
@@ -52,8 +53,7 @@ struct DescParams {
     int cq[36], sq[36];     // round(2^11 cos), round(2^11 sin) of (k + 0.5) * 10 degrees
     int warp_bytes, patch_bytes, mid_bytes;
     int word_ok;           // gray base 4-byte aligned and pitch % 4 == 0: interior patches load 32-bit words
-    const uint8_t* lut_bin;
-    const uint32_t* lut_w;
+    const uint32_t* lut_bw;    // (bin << 25) | weight per gradient (a, b): one gather per orientation sample
     uint8_t* ori;
     float* desc;
     __nv_bfloat16* desc16;
@@ -85,14 +85,17 @@ __device__ __forceinline__ uint32_t orient_weight(int s)
     return (uint32_t)(r + (N > r * r + r ? 1ull : 0ull));
 }
 
-__global__ void k_build_luts(uint8_t* bins, uint32_t* weights)
+// The orientation table: for every integer gradient (a, b) in [-255, 255]^2,
+// its 10-degree bin (bits 25..30) and its exact weight round(65536 sqrt(a^2 +
+// b^2)) (< 2^25, bits 0..24).
+__global__ void k_build_luts(uint32_t* bw)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < kLutBins) {
         const int a = i / 511 - 255, b = i % 511 - 255;
-        bins[i] = (uint8_t)((a == 0 && b == 0) ? 0 : orient_bin(a, b));
+        const int bin = (a == 0 && b == 0) ? 0 : orient_bin(a, b);
+        bw[i] = ((uint32_t)bin << 25) | orient_weight(a * a + b * b);
     }
-    if (i < kLutWeights) weights[i] = orient_weight(i);
 }
 
 __global__ void k_diag_orient(int32_t* bins, uint32_t* weights)
@@ -290,8 +293,9 @@ __global__ void __launch_bounds__(kWarps * 32) k_describe_all(const DescParams p
             const int a = (int)q[SP] - (int)q[-SP];
             const int b = (int)q[1] - (int)q[-1];
             if (a | b) {
-                const int bin = __ldg(p.lut_bin + (a + 255) * 511 + (b + 255));
-                const uint32_t wt = __ldg(p.lut_w + a * a + b * b);
+                const uint32_t e = __ldg(p.lut_bw + (a + 255) * 511 + (b + 255));
+                const int bin = (int)(e >> 25);
+                const uint32_t wt = e & 0x1FFFFFFu;
                 atomicAdd(&hlo[bin], wt & 0xFFFFu);
                 atomicAdd(&hhi[bin], wt >> 16);
             }
@@ -428,8 +432,9 @@ __global__ void __launch_bounds__(kCtaThreads) k_describe_cta(const DescParams p
             const int a = (int)q[SP] - (int)q[-SP];
             const int b = (int)q[1] - (int)q[-1];
             if (a | b) {
-                const int bin = __ldg(p.lut_bin + (a + 255) * 511 + (b + 255));
-                const uint32_t wt = __ldg(p.lut_w + a * a + b * b);
+                const uint32_t e = __ldg(p.lut_bw + (a + 255) * 511 + (b + 255));
+                const int bin = (int)(e >> 25);
+                const uint32_t wt = e & 0x1FFFFFFu;
                 atomicAdd(&hlo[bin], wt & 0xFFFFu);
                 atomicAdd(&hhi[bin], wt >> 16);
             }
@@ -547,7 +552,10 @@ __global__ void __launch_bounds__(kWarps * 32) k_describe_global(const DescParam
             for (int v = lane - R; v <= R; v += 32) {
                 const int a = px(u + 1, v) - px(u - 1, v);
                 const int b = px(u, v + 1) - px(u, v - 1);
-                if (a | b) hist[__ldg(p.lut_bin + (a + 255) * 511 + (b + 255)) * 32 + lane] += __ldg(p.lut_w + a * a + b * b);
+                if (a | b) {
+                    const uint32_t e = __ldg(p.lut_bw + (a + 255) * 511 + (b + 255));
+                    hist[(e >> 25) * 32 + lane] += e & 0x1FFFFFFu;
+                }
             }
         __syncwarp();
         unsigned long long t0 = 0, t1 = 0;
@@ -675,8 +683,9 @@ __global__ void __launch_bounds__(kSplitThreads) k_orient_split(const DescParams
         const int a = px(yy + 1, xx) - px(yy - 1, xx);
         const int b = px(yy, xx + 1) - px(yy, xx - 1);
         if (a | b) {
-            const int bin = __ldg(p.lut_bin + (a + 255) * 511 + (b + 255));
-            const uint32_t wt = __ldg(p.lut_w + a * a + b * b);
+            const uint32_t e = __ldg(p.lut_bw + (a + 255) * 511 + (b + 255));
+            const int bin = (int)(e >> 25);
+            const uint32_t wt = e & 0x1FFFFFFu;
             atomicAdd(&hlo[bin], wt & 0xFFFFu);
             atomicAdd(&hhi[bin], wt >> 16);
         }
@@ -858,13 +867,11 @@ __global__ void __launch_bounds__(128) k_desc_finalize(const DescParams p)
 
 }  // namespace
 
-size_t describe_lut_bytes() { return (size_t)kLutWeights * 4 + 256 + (size_t)kLutBins + 256; }
+size_t describe_lut_bytes() { return (size_t)kLutBins * 4 + 256; }
 
 cudaError_t launch_build_luts(void* luts, cudaStream_t s)
 {
-    uint32_t* w = reinterpret_cast<uint32_t*>(luts);
-    uint8_t* b = reinterpret_cast<uint8_t*>(luts) + (((size_t)kLutWeights * 4 + 255) & ~size_t(255));
-    k_build_luts<<<(kLutBins + 255) / 256, 256, 0, s>>>(b, w);
+    k_build_luts<<<(kLutBins + 255) / 256, 256, 0, s>>>(reinterpret_cast<uint32_t*>(luts));
     return cudaGetLastError();
 }
 
@@ -919,8 +926,7 @@ cudaError_t launch_describe(const uint8_t* gray, int H, int W, int pitch, const 
     p.upright = upright;
     p.hard = hard;
     p.word_ok = ((reinterpret_cast<uintptr_t>(gray) & 3u) == 0 && (pitch & 3) == 0) ? 1 : 0;
-    p.lut_w = reinterpret_cast<const uint32_t*>(luts);
-    p.lut_bin = reinterpret_cast<const uint8_t*>(luts) + (((size_t)kLutWeights * 4 + 255) & ~size_t(255));
+    p.lut_bw = reinterpret_cast<const uint32_t*>(luts);
     p.ori = ori; p.desc = desc; p.desc16 = reinterpret_cast<__nv_bfloat16*>(desc_bf16); p.valid = valid;
     // Scales with w_s <= 15 whose per-warp shared memory fits kSmallWarpBytes
     // run one warp per point, each scale in a launch sized for its own
