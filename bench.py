@@ -160,7 +160,7 @@ def oracle_pair_seconds(pair, rows_sample=1500, desc_sample=15000, seed=0, M=300
 # workload, from one ncu capture, valid only for the kernel source it was taken
 # on (file SHA-1).
 PROFILED_TRAFFIC = {
-    "k_match_tc.cu": ("a36974a497c74a897e0b1d806b716033cd65441e", 43.93e6),
+    "k_match_tc.cu": ("f647d45b6322e1b6acd2f2571908d8aeec2880ca", 44.02e6),
 }
 
 
