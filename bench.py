@@ -1001,7 +1001,12 @@ def main():
     # finish), compact 2, RANSAC 9 (hypotheses, score, recount, argmax, three
     # refit sums, solve, final); FP32 form: match 4 (two row norms, main,
     # finish) and the rest as BF16
-    launches_per_step = 28 if r["bf"] else 23
+    # liblp kernels one lp_stitch_pair launches: detect 1; describe 4 per image
+    # (two per-point-CTA scales, two warp-per-point scales); BF16 match 9 (two
+    # row-norm launches, pass 1, thresholds, pass 2, re-rank, re-scan, merge,
+    # finish) or FP32 match 4 (row norms x 2, distances, finish); compaction 2;
+    # RANSAC 4 (hypotheses, score, recount, argmax); refit 5
+    launches_per_step = 29 if r["bf"] else 24
     line = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * r["t_steps"] / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if r["bf"] else "f32", "data": "synthetic",
