@@ -50,7 +50,7 @@ typedef enum lp_status {
     LP_ERR_TIMEOUT = 4,      /* a bounded device-side wait gave up */
     LP_ERR_NOMEM = 5,        /* workspace allocation failed */
     LP_ERR_DEGENERATE = 6,   /* no model could be fitted (reported, not fatal) */
-    LP_ERR_UNSUPPORTED = 7,  /* configuration outside what this build supports */
+    LP_ERR_UNSUPPORTED = 7,  /* configuration outside what the library supports */
     LP_ERR_DEVICE = 8        /* a kernel recorded an internal inconsistency */
 } lp_status;
 
