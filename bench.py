@@ -160,7 +160,7 @@ def oracle_pair_seconds(pair, rows_sample=1500, desc_sample=15000, seed=0, M=300
 # workload, from one ncu capture, valid only for the kernel source it was taken
 # on (file SHA-1).
 PROFILED_TRAFFIC = {
-    "k_match_tc.cu": ("f647d45b6322e1b6acd2f2571908d8aeec2880ca", 44.02e6),
+    "k_match_tc.cu": ("d06d4a49ea64a19a641e36e26566ae90b93a11b6", 44.02e6),
 }
 
 

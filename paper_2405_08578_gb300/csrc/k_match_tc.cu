@@ -1,6 +1,8 @@
-// Nearest-neighbour matching (Sec. 2.4, Eq. 6) with BF16 tensor cores
-// (tcgen05) for sm_103a, re-ranked in FP32 so that every decision equals the
-// plain FP32 form's.
+// Nearest-neighbour matching (Sec. 2.4, Eq. 6) with BF16 (or E4M3) tensor
+// cores (tcgen05) for sm_103a, re-ranked in FP32 so that every decision equals
+// the plain FP32 form's.  The E4M3 form runs the same passes on 128-byte
+// operand rows with kind::f8f6f4 MMAs (K = 32) and E4M3's error bound; see the
+// constants below window_top.
 //
 // Distances: the accumulator of one MMA holds D = a~.b~ over the eight K-steps
 // of the BF16 descriptors.  Valid descriptors have unit norm, so the squared
