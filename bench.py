@@ -655,7 +655,7 @@ def describe_rate(flush, k=10):
             "samples_per_ns": samples / (ms * 1e6),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                          "frac": achieved / alu_peak, "work": f"{desc_samples} descriptor samples x 70 FP32 operations",
-                         "note": "the kernels are bound by instruction issue (77% of cycles issuing, no pipe saturated; "
+                         "note": "the kernels are bound by instruction issue (no pipe saturated; "
                                  "profiles/k_describe_pair_2688x1600.md): most of their work is integer, table and "
                                  "shared-memory work that this FP32 operation count leaves out"}}
 

@@ -114,11 +114,13 @@ __global__ void k_diag_orient(int32_t* bins, uint32_t* weights)
 // inside it, atan(t) * 4 / pi for t = min/max in [0, 1] is an odd polynomial
 // of degree 13, a least-squares fit at Chebyshev nodes (max error 5e-7 of an
 // octant in FP32).  m = x rsqrt(x) (approximate reciprocal square root).
+// The zero gradient gives m = 0 and o = 0, so callers may add its weights
+// without a test.
 __device__ __forceinline__ void grad_polar(float a, float b, float x2, float& m, float& o)
 {
-    m = x2 * rsqrtf(x2);
+    m = x2 * rsqrtf(fmaxf(x2, 1e-30f));
     const float aa = fabsf(a), ab = fabsf(b);
-    const float t = __fdividef(fminf(aa, ab), fmaxf(aa, ab));
+    const float t = __fdividef(fminf(aa, ab), fmaxf(fmaxf(aa, ab), 1e-30f));
     const float u = t * t;
     float g = 0.008711903356015682f;
     g = fmaf(g, u, -0.04294002428650856f);
@@ -227,8 +229,11 @@ struct Walk2D {
     int r, c, dr, dc, n;
     __device__ __forceinline__ Walk2D(int lane, int n_) : n(n_)
     {
-        r = lane / n_; c = lane - r * n_;
-        dr = 32 / n_; dc = 32 - dr * n_;
+        // lane / n_ and 32 / n_ (n_ <= 127): (x + 1/2) / n_ lies at least
+        // 1/(2 n_) from an integer, far above the quotient's 2-ulp error
+        const float rn = __fdividef(1.f, (float)n_);
+        r = (int)(((float)lane + 0.5f) * rn); c = lane - r * n_;
+        dr = (int)(32.5f * rn); dc = 32 - dr * n_;
     }
     __device__ __forceinline__ void next()
     {
@@ -237,6 +242,9 @@ struct Walk2D {
     }
 };
 
+// kHard: the hard 8-direction histogram on the fixed-point grid (a compile-time
+// choice, so the soft path's loops carry no test of it).
+template <int kHard>
 __global__ void __launch_bounds__(kWarps * 32) k_describe_all(const DescParams p)
 {
     extern __shared__ __align__(16) uint8_t sm[];
@@ -292,13 +300,12 @@ __global__ void __launch_bounds__(kWarps * 32) k_describe_all(const DescParams p
             const uint8_t* q = c0 + w.r * SP + w.c;
             const int a = (int)q[SP] - (int)q[-SP];
             const int b = (int)q[1] - (int)q[-1];
-            if (a | b) {
-                const uint32_t e = __ldg(p.lut_bw + (a + 255) * 511 + (b + 255));
-                const int bin = (int)(e >> 25);
-                const uint32_t wt = e & 0x1FFFFFFu;
-                atomicAdd(&hlo[bin], wt & 0xFFFFu);
-                atomicAdd(&hhi[bin], wt >> 16);
-            }
+            // the table's entry for a zero gradient is bin 0, weight 0
+            const uint32_t e = __ldg(p.lut_bw + (a + 255) * 511 + (b + 255));
+            const int bin = (int)(e >> 25);
+            const uint32_t wt = e & 0x1FFFFFFu;
+            atomicAdd(&hlo[bin], wt & 0xFFFFu);
+            atomicAdd(&hhi[bin], wt >> 16);
         }
         __syncwarp();
         unsigned long long bv = ((unsigned long long)hhi[lane] << 16) + hlo[lane];
@@ -324,7 +331,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_describe_all(const DescParams p
     {
         Walk2D w(lane, G);
         for (; w.r < G; w.next())
-            grid_value(grid + w.r * G + w.c, patch, SP, P, w.r - R - 1, w.c - R - 1, c, s, p.hard, cq, sq);
+            grid_value(grid + w.r * G + w.c, patch, SP, P, w.r - R - 1, w.c - R - 1, c, s, kHard, cq, sq);
     }
     float* mine = acc + lane * kAccStride;
 #pragma unroll
@@ -338,9 +345,18 @@ __global__ void __launch_bounds__(kWarps * 32) k_describe_all(const DescParams p
     for (; iu < ws;) {
         int b0;
         float w0, w1;
-        if (grid_sample(grid + (cr * ws + iu + 1) * G + cc * ws + iv + 1, G, p.hard, b0, w0, w1)) {
-            mine[b0] += w0;
-            mine[(b0 + 1) & 7] += w1;
+        const float* g = grid + (cr * ws + iu + 1) * G + cc * ws + iv + 1;
+        if (kHard) {
+            if (grid_sample(g, G, 1, b0, w0, w1)) mine[b0] += w0;
+        } else {
+            // a zero gradient adds zero to bin 0
+            const float a = g[G] - g[-G], b = g[1] - g[-1];
+            float m, o;
+            grad_polar(a, b, a * a + b * b, m, o);
+            b0 = (int)o;
+            const float t = o - (float)b0;
+            mine[b0] += m * (1.f - t);
+            mine[(b0 + 1) & 7] += m * t;
         }
         iv += 2;
         while (iv >= ws) { iv -= ws; ++iu; }
@@ -360,17 +376,18 @@ __global__ void __launch_bounds__(kWarps * 32) k_describe_all(const DescParams p
     for (int o = 16; o; o >>= 1) ss += __shfl_xor_sync(0xFFFFFFFFu, ss, o);
     const float nrm = sqrtf(ss);
     const bool ok = nrm > 0.f;
+    const float inv = ok ? 1.f / nrm : 0.f;
     float ss2 = 0.f;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        v[q] = ok ? fminf(v[q] / nrm, 0.2f) : 0.f;
+        v[q] = fminf(v[q] * inv, 0.2f);
         ss2 += v[q] * v[q];
     }
 #pragma unroll
     for (int o = 16; o; o >>= 1) ss2 += __shfl_xor_sync(0xFFFFFFFFu, ss2, o);
-    const float n2 = sqrtf(ss2);
+    const float inv2 = ok ? 1.f / sqrtf(ss2) : 0.f;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) v[q] = ok ? v[q] / n2 : 0.f;
+    for (int q = 0; q < 4; ++q) v[q] *= inv2;
     reinterpret_cast<float4*>(p.desc + k * 128)[lane] = make_float4(v[0], v[1], v[2], v[3]);
     if (p.desc16) {
         __nv_bfloat162 lo = __floats2bfloat162_rn(v[0], v[1]);
@@ -499,7 +516,7 @@ __global__ void __launch_bounds__(kCtaThreads) k_describe_cta(const DescParams p
     ss = red[0] + red[1] + red[2] + red[3];
     const float nrm = sqrtf(ss);
     const bool ok = nrm > 0.f;
-    v = ok ? fminf(v / nrm, 0.2f) : 0.f;
+    v = fminf(v * (ok ? 1.f / nrm : 0.f), 0.2f);
     float ss2 = v * v;
 #pragma unroll
     for (int o = 16; o; o >>= 1) ss2 += __shfl_xor_sync(0xFFFFFFFFu, ss2, o);
@@ -507,8 +524,7 @@ __global__ void __launch_bounds__(kCtaThreads) k_describe_cta(const DescParams p
     if (lane == 0) red[warp] = ss2;
     __syncthreads();
     ss2 = red[0] + red[1] + red[2] + red[3];
-    const float n2 = sqrtf(ss2);
-    v = ok ? v / n2 : 0.f;
+    v *= ok ? 1.f / sqrtf(ss2) : 0.f;
     p.desc[k * 128 + tid] = v;
     if (p.desc16) p.desc16[k * 128 + tid] = __float2bfloat16_rn(v);
     if (tid == 0) {
@@ -621,10 +637,11 @@ __global__ void __launch_bounds__(kWarps * 32) k_describe_global(const DescParam
     const float nrm = sqrtf(ss);
     const bool ok = nrm > 0.f;
     float ss2 = 0.f;
-    for (int q = 0; q < 4; ++q) { v[q] = ok ? fminf(v[q] / nrm, 0.2f) : 0.f; ss2 += v[q] * v[q]; }
+    const float inv = ok ? 1.f / nrm : 0.f;
+    for (int q = 0; q < 4; ++q) { v[q] = fminf(v[q] * inv, 0.2f); ss2 += v[q] * v[q]; }
     for (int o = 16; o; o >>= 1) ss2 += __shfl_xor_sync(0xFFFFFFFFu, ss2, o);
-    const float n2 = sqrtf(ss2);
-    for (int q = 0; q < 4; ++q) v[q] = ok ? v[q] / n2 : 0.f;
+    const float inv2 = ok ? 1.f / sqrtf(ss2) : 0.f;
+    for (int q = 0; q < 4; ++q) v[q] *= inv2;
     reinterpret_cast<float4*>(p.desc + k * 128)[lane] = make_float4(v[0], v[1], v[2], v[3]);
     if (p.desc16) {
         __nv_bfloat162 lo = __floats2bfloat162_rn(v[0], v[1]);
@@ -839,17 +856,18 @@ __global__ void __launch_bounds__(128) k_desc_finalize(const DescParams p)
     for (int o = 16; o; o >>= 1) ss += __shfl_xor_sync(0xFFFFFFFFu, ss, o);
     const float nrm = sqrtf(ss);
     const bool ok = nrm > 0.f;
+    const float inv = ok ? 1.f / nrm : 0.f;
     float ss2 = 0.f;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        v[q] = ok ? fminf(v[q] / nrm, 0.2f) : 0.f;
+        v[q] = fminf(v[q] * inv, 0.2f);
         ss2 += v[q] * v[q];
     }
 #pragma unroll
     for (int o = 16; o; o >>= 1) ss2 += __shfl_xor_sync(0xFFFFFFFFu, ss2, o);
-    const float n2 = sqrtf(ss2);
+    const float inv2 = ok ? 1.f / sqrtf(ss2) : 0.f;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) v[q] = ok ? v[q] / n2 : 0.f;
+    for (int q = 0; q < 4; ++q) v[q] *= inv2;
     reinterpret_cast<float4*>(p.desc + k * 128)[lane] = make_float4(v[0], v[1], v[2], v[3]);
     if (p.desc16) {
         __nv_bfloat162 lo = __floats2bfloat162_rn(v[0], v[1]);
@@ -974,10 +992,14 @@ cudaError_t launch_describe(const uint8_t* gray, int H, int W, int pitch, const 
         p.warp_bytes = p.patch_bytes + p.mid_bytes + 2 * 36 * 4 + kAccBytes;
         const size_t smem = (size_t)kWarps * p.warp_bytes;
         if (smem > 48 * 1024) {
-            cudaError_t e = cudaFuncSetAttribute(k_describe_all, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaError_t e = cudaFuncSetAttribute(p.hard ? k_describe_all<1> : k_describe_all<0>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
         }
-        k_describe_all<<<(unsigned)((p.n + kWarps - 1) / kWarps), kWarps * 32, smem, s>>>(p);
+        if (p.hard)
+            k_describe_all<1><<<(unsigned)((p.n + kWarps - 1) / kWarps), kWarps * 32, smem, s>>>(p);
+        else
+            k_describe_all<0><<<(unsigned)((p.n + kWarps - 1) / kWarps), kWarps * 32, smem, s>>>(p);
         return cudaGetLastError();
     };
     for (int l = m - 1; l >= first_big; --l) {
