@@ -223,6 +223,35 @@ __device__ __forceinline__ void grid_value(float* dst, const uint8_t* patch, int
         *dst = bilinear(patch, S, P, (float)fu * c - (float)fv * s, (float)fu * s + (float)fv * c);
 }
 
+// Argmax of the 36 exact orientation sums (lowest bin on ties), one warp: each
+// sum v < 2^37 becomes the key (v << 6) | (63 - bin), unique per bin, and the
+// key's maximum is taken as two 32-bit warp reductions (high word, then the low
+// word among the lanes holding the maximal high word; a real key's low word is
+// never 0).
+__device__ __forceinline__ int hist_argmax(const uint32_t* hlo, const uint32_t* hhi, int lane)
+{
+    unsigned long long key = ((((unsigned long long)hhi[lane] << 16) + hlo[lane]) << 6) | (unsigned)(63 - lane);
+    if (lane < 4) {
+        const int b1 = lane + 32;
+        const unsigned long long k1 = ((((unsigned long long)hhi[b1] << 16) + hlo[b1]) << 6) | (unsigned)(63 - b1);
+        key = k1 > key ? k1 : key;
+    }
+    const uint32_t hi = (uint32_t)(key >> 32), lo = (uint32_t)key;
+    const uint32_t top = __reduce_max_sync(0xFFFFFFFFu, hi);
+    const uint32_t low = __reduce_max_sync(0xFFFFFFFFu, hi == top ? lo : 0u);
+    return 63 - (int)(low & 63u);
+}
+
+// Row y and column x of pixel id (< 2^24) of a W-wide image: a float quotient
+// corrected by integer steps.
+__device__ __forceinline__ void pixel_yx(uint32_t id, int W, int& y, int& x)
+{
+    y = (int)__fdividef((float)id, (float)W);
+    x = (int)id - y * W;
+    while (x < 0) { --y; x += W; }
+    while (x >= W) { ++y; x -= W; }
+}
+
 // Walk the flattened index e = lane, lane + 32, ... of an n-wide 2-D range
 // without divisions.
 struct Walk2D {
@@ -263,7 +292,8 @@ __global__ void __launch_bounds__(kWarps * 32) k_describe_all(const DescParams p
     float* acc = reinterpret_cast<float*>(base + p.patch_bytes + p.mid_bytes + 2 * 36 * 4);
     const int ws = p.wsl[l], R = 2 * ws, P = p.Pl[l], S = 2 * P + 1, SP = patch_stride(S);
     const uint32_t id = __ldg(p.kp + k);
-    const int y = (int)(id / (uint32_t)p.W), x = (int)(id - (uint32_t)y * (uint32_t)p.W);
+    int y, x;
+    pixel_yx(id, p.W, y, x);
 
     // neighbourhood: aligned 32-bit words for interior points (row r of the
     // patch starts `off` bytes into shared row r), clamped bytes near the edge
@@ -308,19 +338,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_describe_all(const DescParams p
             atomicAdd(&hhi[bin], wt >> 16);
         }
         __syncwarp();
-        unsigned long long bv = ((unsigned long long)hhi[lane] << 16) + hlo[lane];
-        int bb = lane;
-        if (lane < 4) {
-            const unsigned long long t1 = ((unsigned long long)hhi[lane + 32] << 16) + hlo[lane + 32];
-            if (t1 > bv) { bv = t1; bb = lane + 32; }
-        }
-#pragma unroll
-        for (int o = 16; o; o >>= 1) {
-            const unsigned long long ov = __shfl_xor_sync(0xFFFFFFFFu, bv, o);
-            const int ob = __shfl_xor_sync(0xFFFFFFFFu, bb, o);
-            if (ov > bv || (ov == bv && ob < bb)) { bv = ov; bb = ob; }
-        }
-        best = bb;
+        best = hist_argmax(hlo, hhi, lane);
     }
     const float c = p.upright ? 1.f : p.cs[best][0];
     const float s = p.upright ? 0.f : p.cs[best][1];
@@ -421,7 +439,8 @@ __global__ void __launch_bounds__(kCtaThreads) k_describe_cta(const DescParams p
     uint8_t* patch = sm;
     float* grid = reinterpret_cast<float*>(sm + p.patch_bytes);
     const uint32_t id = __ldg(p.kp + k);
-    const int y = (int)(id / (uint32_t)p.W), x = (int)(id - (uint32_t)y * (uint32_t)p.W);
+    int y, x;
+    pixel_yx(id, p.W, y, x);
     if (p.word_ok && y >= P && y + P < p.H && x >= P && x + P + 3 < p.W) {
         const int off = (x - P) & 3, nw = (off + S + 3) >> 2;
         const uint8_t* src = p.gray + (size_t)(y - P) * p.pitch + (x - P - off);
@@ -458,18 +477,7 @@ __global__ void __launch_bounds__(kCtaThreads) k_describe_cta(const DescParams p
         }
         __syncthreads();
         if (warp == 0) {
-            unsigned long long bv = ((unsigned long long)hhi[lane] << 16) + hlo[lane];
-            int bb = lane;
-            if (lane < 4) {
-                const unsigned long long t1 = ((unsigned long long)hhi[lane + 32] << 16) + hlo[lane + 32];
-                if (t1 > bv) { bv = t1; bb = lane + 32; }
-            }
-#pragma unroll
-            for (int o = 16; o; o >>= 1) {
-                const unsigned long long ov = __shfl_xor_sync(0xFFFFFFFFu, bv, o);
-                const int ob = __shfl_xor_sync(0xFFFFFFFFu, bb, o);
-                if (ov > bv || (ov == bv && ob < bb)) { bv = ov; bb = ob; }
-            }
+            const int bb = hist_argmax(hlo, hhi, lane);
             if (lane == 0) best_s = bb;
         }
         __syncthreads();
@@ -547,7 +555,8 @@ __global__ void __launch_bounds__(kWarps * 32) k_describe_global(const DescParam
     float* acc = reinterpret_cast<float*>(sm + warp * (2 * kHistBytes + kAccBytes) + 2 * kHistBytes);
     const int ws = p.ws, R = 2 * ws;
     const uint32_t id = __ldg(p.kp + k);
-    const int y = (int)(id / (uint32_t)p.W), x = (int)(id - (uint32_t)y * (uint32_t)p.W);
+    int y, x;
+    pixel_yx(id, p.W, y, x);
     auto px = [&](int r, int c) -> int {
         const int yy = min(max(y + r, 0), p.H - 1), xx = min(max(x + c, 0), p.W - 1);
         return __ldg(p.gray + (size_t)yy * p.pitch + xx);
@@ -684,7 +693,8 @@ __global__ void __launch_bounds__(kSplitThreads) k_orient_split(const DescParams
     const long long k = p.k0 + idx;
     const int R = 2 * p.ws, n = 2 * R + 1;
     const uint32_t id = __ldg(p.kp + k);
-    const int y = (int)(id / (uint32_t)p.W), x = (int)(id - (uint32_t)y * (uint32_t)p.W);
+    int y, x;
+    pixel_yx(id, p.W, y, x);
     auto px = [&](int yy, int xx) -> int {
         yy = min(max(yy, 0), p.H - 1);
         xx = min(max(xx, 0), p.W - 1);
@@ -747,7 +757,8 @@ __global__ void __launch_bounds__(kSplitThreads) k_desc_cell(const DescParams p)
     const int ws = p.ws, R = 2 * ws, Gc = ws + 2;
     const int bmax = cell_box_side(Gc);
     const uint32_t id = __ldg(p.kp + k);
-    const int y = (int)(id / (uint32_t)p.W), x = (int)(id - (uint32_t)y * (uint32_t)p.W);
+    int y, x;
+    pixel_yx(id, p.W, y, x);
     const int best = p.upright ? 0 : p.ori[k];
     const float c = p.upright ? 1.f : p.cs[best][0];
     const float s = p.upright ? 0.f : p.cs[best][1];
