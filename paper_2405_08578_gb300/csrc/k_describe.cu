@@ -284,12 +284,15 @@ __global__ void __launch_bounds__(kWarps * 32) k_describe_all(const DescParams p
     const long long k = p.k0 + p.n - 1 - idx;
     int l = 0;
     while (l + 1 < p.nl && k >= p.off[l + 1]) ++l;
-    uint8_t* base = sm + warp * p.warp_bytes;
+    // the turned grid first, then the neighbourhood and the orientation
+    // counters; the descriptor accumulators reuse those bytes once the grid
+    // is built
+    uint8_t* const base = sm + warp * p.warp_bytes + p.mid_bytes;
     uint8_t* patch = base;
-    float* grid = reinterpret_cast<float*>(base + p.patch_bytes);
-    uint32_t* hlo = reinterpret_cast<uint32_t*>(base + p.patch_bytes + p.mid_bytes);   // [36]
-    uint32_t* hhi = hlo + 36;                                                          // [36]
-    float* acc = reinterpret_cast<float*>(base + p.patch_bytes + p.mid_bytes + 2 * 36 * 4);
+    float* grid = reinterpret_cast<float*>(sm + warp * p.warp_bytes);
+    uint32_t* hlo = reinterpret_cast<uint32_t*>(base + p.patch_bytes);   // [36]
+    uint32_t* hhi = hlo + 36;                                           // [36]
+    float* acc = reinterpret_cast<float*>(base);
     const int ws = p.wsl[l], R = 2 * ws, P = p.Pl[l], S = 2 * P + 1, SP = patch_stride(S);
     const uint32_t id = __ldg(p.kp + k);
     int y, x;
@@ -351,6 +354,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_describe_all(const DescParams p
         for (; w.r < G; w.next())
             grid_value(grid + w.r * G + w.c, patch, SP, P, w.r - R - 1, w.c - R - 1, c, s, kHard, cq, sq);
     }
+    __syncwarp();   // every lane is done with the neighbourhood
     float* mine = acc + lane * kAccStride;
 #pragma unroll
     for (int q = 0; q < 8; ++q) mine[q] = 0.f;
@@ -1000,7 +1004,9 @@ cudaError_t launch_describe(const uint8_t* gray, int H, int W, int pitch, const 
         const int S = 2 * Pmax + 1;
         p.patch_bytes = ((S * patch_stride(S) + 15) / 16) * 16;
         p.mid_bytes = ((Gmax * Gmax * 4) + 15) / 16 * 16;
-        p.warp_bytes = p.patch_bytes + p.mid_bytes + 2 * 36 * 4 + kAccBytes;
+        // the accumulators alias the neighbourhood and the counters
+        const int tail = p.patch_bytes + 2 * 36 * 4;
+        p.warp_bytes = p.mid_bytes + (tail > kAccBytes ? tail : kAccBytes);
         const size_t smem = (size_t)kWarps * p.warp_bytes;
         if (smem > 48 * 1024) {
             cudaError_t e = cudaFuncSetAttribute(p.hard ? k_describe_all<1> : k_describe_all<0>,
