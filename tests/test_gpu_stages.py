@@ -50,6 +50,8 @@ def test_orient_bins_and_weights_exhaustive():
     lp.lp_diag_orient_weights(w)
     want = np.array([oracle.orient_weight(s) for s in range(130051)], np.uint32)
     assert np.array_equal(G.host(w).view(np.uint32), want)
+    # the describe kernels add the zero gradient's entry without testing for it
+    assert G.host(bins)[255 * 511 + 255] == 0 and G.host(w)[0] == 0
 
 
 def test_philox_matches_oracle_stream():
