@@ -14,8 +14,10 @@
 // device: one gather per sample.  Each weight (< 2^25) is added to two 32-bit
 // shared counters per bin, its low 16 and its high 9 bits (for w_s <= 15 at
 // most 61^2 samples: no overflow), recombined in 64 bits; the argmax (lowest
-// bin on ties) is therefore exact.  Larger scales take a global-memory kernel
-// with per-lane 64-bit histogram columns.
+// bin on ties) is therefore exact.  Scales above w_s = 15 split each point
+// over many CTAs (64-bit bins summed with integer atomics), or take a
+// global-memory kernel with per-lane histogram columns when a cell's grid does
+// not fit in shared memory.
 //
 // Descriptor (FP32): the gradient taps p +- e_u, p +- e_v of grid point (u, v)
 // are the grid points (u +- 1, v), (u, v +- 1) of the same turned grid, so the
