@@ -209,9 +209,14 @@ namespace lp {
 
 int make_scale_table(const int* Ls_in, int nL, double beta0, int H, int W, ScaleTable* st)
 {
+    if (nL < 1 || nL > LP_MAX_SCALES) return LP_ERR_ARG;
     int Ls[LP_MAX_SCALES];
-    for (int l = 0; l < nL; ++l) Ls[l] = Ls_in[l];
-    std::sort(Ls, Ls + nL);
+    // ascending (insertion sort of at most LP_MAX_SCALES values)
+    for (int l = 0; l < nL; ++l) {
+        int k = l;
+        for (; k > 0 && Ls[k - 1] > Ls_in[l]; --k) Ls[k] = Ls[k - 1];
+        Ls[k] = Ls_in[l];
+    }
     const int Lmin = Ls[0], Lmax = Ls[nL - 1];
     // Eq. 3-4: w_s = beta*L, beta = beta0*(L/Lmax)^(-1/2); the default beta0 is
     // the largest value that keeps w = 4 w_s <= L for every L
